@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of exact grid pair counting on GB300.
+
+Default workload: 2,000,000 Neyman-Scott points (200,000 parents, Poisson(10)
+children, sigma = 5 Mpc/h) in a periodic 1000 Mpc/h cube, auto counts in
+(s, mu) bins (40 linear s bins on [0, 200) x 100 mu bins, line of sight z),
+FP32 separations with binary64 rescue, int64 counts.
+
+One step = one pass of the whole path over the catalogue already resident in
+HBM: canonicalise + grid build (bounds, per-cell counts, scan, scatter),
+i-block list, pair kernel (separation, bin lookup, shared histograms),
+binary64 rescue kernel, histogram read-back.  The metric counts the pair
+separations the kernel evaluates ("pairs evaluated").
+
+Prints one JSON line.  --impl reference times the CPU oracle (brute force,
+binary64) on a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairs evaluated/sec on 1 GB300, FP32+FP64-rescue vs plain FP64 at exact counts"
+UNIT = "pairs/s"
+FLOPS_PER_CANDIDATE = 8       # 3 subtractions, 3 multiplies, 2 adds
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="ns_periodic_n2m_smu40x100")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cell-size", type=float, default=0.0)
+    ap.add_argument("--ipt", type=int, default=0)
+    ap.add_argument("--volume-scale", type=float, default=1.0,
+                    help="same density in a box of this fraction of the volume "
+                         "(small cases for profiling; 1 = the full workload)")
+    return ap.parse_args()
+
+
+def workload_inputs(w, f):
+    """Catalogue of workload w; f < 1 keeps the number density and cluster
+    shape in a box of f times the volume (periodic clustered workloads)."""
+    from synth import catalogs as C
+    from synth import workloads as W
+    if f == 1.0:
+        return W.make_inputs(w)["D"], w.L
+    L = w.L * f ** (1.0 / 3.0)
+    n = int(round(w.extra["n"] * f))
+    if "parents" in w.extra:
+        D = C.neyman_scott(n, max(1, int(w.extra["parents"] * f)), w.extra["children"],
+                           w.extra["sigma"], L, w.seed)
+    else:
+        D = C.uniform_box(n, L, w.seed)
+    return D, L
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# --------------------------------------------------------------------------
+def oracle_sample_rate(D, w, seconds, seed=0, L=None):
+    """Brute-force oracle pairs/s: all pairs of a random sample of i-points
+    against the whole catalogue (the cross form of the same pair set)."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    kw = dict(box=w.L if L is None else L, periodic=w.periodic, mode=w.mode, los=w.los,
+              edges_a=w.edges_a, edges_b=w.edges_b)
+    n = D.shape[0]
+    m0 = 32
+    S = np.ascontiguousarray(D[rng.choice(n, m0, replace=False)])
+    t = time.perf_counter()
+    oracle.count(S, D, **kw)
+    dt = max(time.perf_counter() - t, 1e-6)
+    m = int(max(m0, min(n, m0 * seconds / dt)))
+    S = np.ascontiguousarray(D[rng.choice(n, m, replace=False)])
+    t = time.perf_counter()
+    oracle.count(S, D, **kw)
+    dt = time.perf_counter() - t
+    cores = oracle.default_threads()
+    return m * n / dt, dt, m, cores
+
+
+def traffic_record():
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if
+    the kernel source is unchanged since it was captured."""
+    p = os.path.join(ROOT, "profiles", "pairs_f32_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        rec = json.load(open(p))
+        src = open(os.path.join(ROOT, "paper_2301_12557_gb300", "csrc", "pairs_impl.cuh"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha256_16"):
+            return None
+        return rec
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from synth import workloads as W
+    w = W.WORKLOADS[args.workload]
+    D = W.make_inputs(w)["D"]
+    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    samp = None
+    for k in range(args.warmup + args.steps):
+        r, dt, m, cores = oracle_sample_rate(D, w, per_step, seed=k)
+        if k >= args.warmup:
+            rates.append((r, dt, m))
+        samp = (m, cores)
+    tot_pairs = sum(r * dt for r, dt, _ in rates)
+    tot_t = sum(dt for _, dt, _ in rates)
+    value = tot_pairs / tot_t
+    sample = (f"{samp[0]} random i-points x all {D.shape[0]} points per step "
+              f"(brute force, binary64)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / len(rates), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n": int(D.shape[0]), "oracle": "CPU brute force"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": samp[1], "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2301_12557_gb300 as P
+    from synth import workloads as W
+
+    P.lib()
+    w = W.WORKLOADS[args.workload]
+    D_host, L_box = workload_inputs(w, args.volume_scale)
+    if world > 1 and rank > 0:
+        # replicas: every rank counts its own independent catalogue
+        from synth import catalogs as C
+        D_host = C.neyman_scott(D_host.shape[0], w.extra["parents"], w.extra["children"],
+                                w.extra["sigma"], L_box, w.seed + 7919 * rank)
+    n = D_host.shape[0]
+    dev = torch.device("cuda", local)
+    D = torch.from_numpy(D_host).to(dev)
+    bins = P.Bins(w.mode, w.los, w.edges_a, w.edges_b)
+    box = P.make_box(L_box, w.periodic)
+    opts = P.make_opts("f32", args.cell_size, args.ipt)
+    out = torch.zeros(bins.nbins, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(o=opts, x=D, counts=out):
+        g = P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=o, stream=stream)
+        try:
+            _, _, st = P.pc_count_auto(g, bins, o, stream, counts=counts)
+        finally:
+            g.free()
+        return st
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = P.pc_launch_count()
+    tot_ms, stats = 0.0, []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()                        # evict L2 between timed steps
+        ev[k][0].record(stream)
+        stats.append(step())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = P.pc_launch_count() - launches0
+    clocks = sampler.stop()
+    barrier()
+    tot_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_local = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+    cand_local = torch.tensor([float(sum(s.candidates for s in stats))], dtype=torch.float64,
+                              device=dev)
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cand_local, op=dist.ReduceOp.SUM)
+    t_max = float(t_local.item())
+    cand_all = float(cand_local.item())
+    value = cand_all / (t_max * 1e-3)
+    counts = out.cpu().numpy()
+
+    # ---- e2e: host buffers through the same ABI, copies inside the region --
+    e2e = None
+    if args.e2e_steps > 0:
+        D_pin = torch.from_numpy(D_host).pin_memory()
+        host_counts = np.zeros(bins.nbins, dtype=np.int64)
+        e2e_ms = []
+        for k in range(args.e2e_steps + 1):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st_e = step(x=D_pin, counts=host_counts)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if k > 0:
+                e2e_ms.append(a.elapsed_time(b))
+        assert np.array_equal(host_counts, counts), "host-buffer counts differ from device run"
+        e2e = {"value": st_e.candidates * world / (statistics.mean(e2e_ms) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(n * 3 * 8), "d2h_bytes_per_step": int(bins.nbins * 8),
+               "ms_per_step": statistics.mean(e2e_ms)}
+
+    # ---- plain FP64 path on the same GB300 -----------------------------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        o64 = P.make_opts("f64", stats[0].cell_size, 1)
+        out64 = torch.zeros_like(out)
+        step(o=o64, counts=out64)
+        torch.cuda.synchronize()
+        ms64 = []
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s64 = step(o=o64, counts=out64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms64.append(a.elapsed_time(b))
+        exact = bool(torch.equal(out64, out))
+        fp64 = {"value": s64.candidates / (statistics.mean(ms64) * 1e-3), "unit": UNIT,
+                "ms_per_step": statistics.mean(ms64), "steps": args.fp64_steps,
+                "counts_identical_to_fp32_rescue": exact}
+
+    # ---- roofline of the dominant kernel -------------------------------------
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    ms_pairs = statistics.mean(s.ms_pairs for s in stats)
+    cand = stats[0].candidates
+    achieved = FLOPS_PER_CANDIDATE * cand / (ms_pairs * 1e-3) / 1e12
+    trec = traffic_record()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
+                "traffic": (trec["bytes_per_launch"] if trec else None),
+                "kernel": "k_pairs_f32<SMU,LOS_Z>",
+                "peak_source": (f"FP32 non-tensor: {props.multi_processor_count} SMs x "
+                                f"{FP32_LANES_PER_SM} lanes x 2 flops x {sm_mhz:.0f} MHz "
+                                f"({peak_src} sm_max_mhz)"),
+                "kernel_ms": ms_pairs,
+                "kernel_share_of_step": ms_pairs / (t_max / args.steps)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, dt, m, cores = oracle_sample_rate(D_host, w, args.cpu_seconds, L=L_box)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{m} random i-points x all {n} points (brute force, binary64), "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        s0 = stats[0]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name if args.volume_scale == 1.0 else
+                       f"{w.name} at volume x{args.volume_scale}", "n": int(n),
+                       "box": L_box, "bins": "s 40 x mu 100 (LOS z)",
+                       "precision": "FP32 separations, binary64 rescue near bin edges, int64 counts",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "cell_size": s0.cell_size, "in_range_pairs": int(counts.sum()),
+                       "candidates_per_step": int(s0.candidates)},
+            "in_range_pairs_per_s": float(counts.sum()) * world / (t_max / args.steps * 1e-3),
+            "rescued_fraction": s0.rescued / max(1, int(counts.sum())),
+            "fp64_path": fp64,
+            "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

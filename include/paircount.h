@@ -1,0 +1,182 @@
+/*
+ * paircount.h -- exact grid pair counting on one GB300 (sm_103a).
+ *
+ * C ABI of the library built from paper_2301_12557_gb300/csrc.  Plain
+ * pointers and sizes only.  Every pointer argument that carries catalogue
+ * data or results may be HOST or DEVICE memory: the library asks the CUDA
+ * driver which one it is and copies host data itself.  Edge arrays inside
+ * pc_bins are always host memory.
+ *
+ * The operation (Zhao, "Fast Correlation Function Calculator", A&A 2023):
+ *   Sect. 2.5  -- pair separation s = |x_j - x_i|, line-of-sight component
+ *                 pi = |s.l|/|l|, sigma = sqrt(s^2 - pi^2), mu = pi/s, with
+ *                 l = x_i + x_j (midpoint line of sight) or l = e_z;
+ *   Sect. 3.2  -- monotone, continuous, zero-based bins, compared on squared
+ *                 values (no square roots in the decision);
+ *   Sect. 2.1  -- regular grid built in three passes (bounds, per-cell counts,
+ *                 grouping) with points stored contiguously by cell;
+ *   Sect. 3.1  -- auto counts visit each unordered pair once; periodic boxes
+ *                 shift whole cells instead of wrapping each pair.
+ *
+ * Exact semantics (identical to the FP64 definition the tests use):
+ *   periodic canonical form  x <- x - L floor(x/L); if x<0 x+=L; if x>=L x-=L
+ *   d = x_j - x_i per axis; periodic: d -= L if d > L/2, d += L if d < -L/2
+ *   s2 = (dx*dx + dy*dy) + dz*dz in binary64 round-to-nearest, no FMA
+ *   bin k of edges e[] iff e[k]^2 <= s2 < e[k+1]^2 (squares in binary64)
+ *   (s, mu):   j = largest j < n_mu with pi2 >= (m[j]^2) * s2; m[0] = 0,
+ *              m[n_mu] = 1 (mu = 1 goes to the last bin); s2 == 0 -> j = 0
+ *   (sigma, pi): sigma2 = s2 - pi2 (clamped at 0); both axes half-open
+ *   pi2 (LOS z) = dz*dz;  pi2 (midpoint) = (sl*sl)/ll with l = x_i + x_j,
+ *              sl = (dx lx + dy ly) + dz lz, ll = (lx lx + ly ly) + lz lz
+ *   auto: unordered pairs, no self-pairs; cross: all (i in g1, j in g2)
+ *   weighted: sum of w_i * w_j per bin
+ * Unweighted counts are bit-exact with that definition.  Weighted sums are
+ * accumulated in binary64 (order-dependent rounding only).
+ */
+#ifndef PAIRCOUNT_H
+#define PAIRCOUNT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes.  No call aborts or throws; details of the last failure on
+ * the calling thread are available from pc_last_error(). */
+typedef enum {
+    PC_OK = 0,
+    PC_EINVAL = -1,        /* invalid argument (message says which) */
+    PC_ENOMEM = -2,        /* device or host allocation failed */
+    PC_ECUDA = -3,         /* a CUDA runtime call failed */
+    PC_EOVERFLOW = -4,     /* a size exceeds what the kernels index */
+    PC_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
+    PC_EUNSUPPORTED = -6   /* valid request this build does not handle */
+} pc_status;
+
+typedef enum { PC_BIN_S = 0, PC_BIN_SMU = 1, PC_BIN_SIGPI = 2 } pc_mode;
+typedef enum { PC_LOS_Z = 0, PC_LOS_MIDPOINT = 1 } pc_los;
+typedef enum { PC_PREC_F32_RESCUE = 0, PC_PREC_F64 = 1 } pc_prec;
+
+/* Domain.  periodic != 0: a box [0, L[a]) on every axis; coordinates are
+ * folded into it (canonical form above).  periodic == 0: lo/hi give the grid
+ * bounds when hi[a] > lo[a] on all three axes (all points must lie inside;
+ * two grids used together in pc_count_cross must be built with the same
+ * bounds), otherwise the bounds are the points' own bounding box. */
+typedef struct {
+    double L[3];
+    int periodic;
+    double lo[3];
+    double hi[3];
+} pc_box;
+
+/* Histogram.  mode PC_BIN_S: n_a s bins, edges_a has n_a + 1 values.
+ * PC_BIN_SMU: edges_a = s edges, edges_b = n_b + 1 mu edges from 0 to 1.
+ * PC_BIN_SIGPI: edges_a = sigma edges, edges_b = pi edges.  Edges are
+ * strictly increasing, finite and >= 0.  Output layout is row-major with the
+ * first axis outermost: index = i_a * n_b + i_b (n_b = 1 for PC_BIN_S). */
+typedef struct {
+    int mode;               /* pc_mode */
+    int los;                /* pc_los; midpoint needs a non-periodic box */
+    int n_a;
+    const double *edges_a;  /* host, n_a + 1 */
+    int n_b;
+    const double *edges_b;  /* host, n_b + 1 (ignored for PC_BIN_S) */
+} pc_bins;
+
+/* Tuning and execution options.  A NULL pc_opts pointer means all defaults
+ * (every field 0). */
+typedef struct {
+    int prec;                    /* pc_prec: FP32 with FP64 rescue (0) or plain FP64 */
+    double cell_size;            /* grid cell side; 0 = chosen by the cost model */
+    int ipt;                     /* i-points per thread (1 or 2); 0 = auto */
+    int priv;                    /* histogram copies per CTA: 0 = one, 1 = one per warp, -1 = auto */
+    long long rescue_capacity;   /* rescue-queue slots; 0 = auto; < 0 = none (all inline) */
+    int use_graph;               /* pc_count_batch: replay a captured CUDA graph */
+    int grid_ctas_per_sm;        /* persistent CTAs per SM; 0 = occupancy limit */
+} pc_opts;
+
+/* Counters of the last count call (all optional). */
+typedef struct {
+    long long candidates;        /* pair separations evaluated by the kernel */
+    long long rescued;           /* pairs re-evaluated in FP64 */
+    long long rescue_inline;     /* of those, evaluated inline (queue full) */
+    long long blocks;            /* i-blocks processed */
+    double cell_size;            /* cell side used (first grid) */
+    float ms_total;              /* device time of the call, milliseconds */
+    float ms_pairs;              /* device time of the pair kernel alone */
+    float ms_rescue;             /* device time of the rescue kernel */
+    int launches;                /* kernels this call launched */
+} pc_stats;
+
+typedef struct pc_grid pc_grid;  /* opaque; owned by the library */
+
+/* Build a grid: canonicalise (periodic) or bound (non-periodic) the points,
+ * count points per cell, scan, and scatter them cell-sorted (SoA/AoS arrays
+ * of FP32 cell-centre offsets and FP64 canonical coordinates) -- Sect. 2.1.
+ *   xyz       n x 3 row-major binary64, host or device
+ *   w         n weights (binary32 if w_is_f32 else binary64), or NULL
+ *   r_max     largest separation the grid will serve (chooses the cell size
+ *             when opt->cell_size == 0)
+ *   stream    cudaStream_t (NULL = legacy default stream); all work is
+ *             ordered on it and the call returns once the grid is built
+ *   out       receives the new grid; release it with pc_free_grid
+ * Errors: PC_EINVAL (n < 0, NULL pointers, bad box, points outside given
+ * bounds), PC_EOVERFLOW (n >= 2^31 or too many cells), PC_ENOMEM, PC_ECUDA. */
+pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f32, long long n,
+                        const pc_box *box, double r_max, const pc_opts *opt,
+                        void *stream, pc_grid **out);
+
+/* Release a grid (NULL is ignored). */
+void pc_free_grid(pc_grid *g);
+
+/* Number of points and cell side of a grid (either output may be NULL). */
+pc_status pc_grid_info(const pc_grid *g, long long *n, double *cell_size);
+
+/* Auto pair counts of one grid (unordered pairs, Sect. 3.1).
+ *   counts    int64 [nbins], host or device; overwritten
+ *   wcounts   binary64 [nbins] or NULL; weighted sums (the grid must carry
+ *             weights)
+ *   st        optional counters
+ * Bins: see pc_bins.  Periodic boxes need the largest separation below L/2
+ * (PC_EINVAL otherwise).  Returns after the results are written. */
+pc_status pc_count_auto(const pc_grid *g, const pc_bins *b, const pc_opts *o, void *stream,
+                        long long *counts, double *wcounts, pc_stats *st);
+
+/* Cross pair counts: all (i in g1, j in g2).  g1 and g2 must share box,
+ * bounds and cell size. */
+pc_status pc_count_cross(const pc_grid *g1, const pc_grid *g2, const pc_bins *b,
+                         const pc_opts *o, void *stream, long long *counts, double *wcounts,
+                         pc_stats *st);
+
+/* Auto counts of m grids in one persistent launch (Sect. 4.2 task queue
+ * analogue).  counts is m x nbins (row m), wcounts likewise or NULL.  All
+ * grids must share box and cell size.  With o->use_graph the launch sequence
+ * is captured once per (grids, bins) and replayed as a CUDA graph. */
+pc_status pc_count_batch(const pc_grid *const *gs, int m, const pc_bins *b, const pc_opts *o,
+                         void *stream, long long *counts, double *wcounts, pc_stats *st);
+
+/* Bounding box of n points (n x 3 binary64, host or device) -- the first of
+ * the three grid-build passes of Sect. 2.1.  lo/hi are host arrays of 3. */
+pc_status pc_aabb(const double *xyz, long long n, void *stream, double *lo, double *hi);
+
+/* Cell side the cost model picks for n points in volume `volume` with
+ * largest separation r_max (Appendix B.1: cost a N_pair + b N_node). */
+double pc_suggest_cell_size(long long n, double volume, double r_max, int mode);
+
+/* Number of kernels this library has launched since it was loaded (all
+ * entry points, all threads).  Lets callers count device work per step. */
+long long pc_launch_count(void);
+
+/* Static description of a status code. */
+const char *pc_strerror(pc_status s);
+
+/* Detail message of the last failing call on this thread ("" if none). */
+const char *pc_last_error(void);
+
+/* Library version string. */
+const char *pc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAIRCOUNT_H */

@@ -1,0 +1,690 @@
+// Host side of libpaircount: argument checks, the counting plan (stencil,
+// lookup tables, FP32 error bands), device workspace, and the count entry
+// points pc_count_auto / pc_count_cross / pc_count_batch.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "pc_host.hpp"
+
+namespace pc {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+pc_status fail(pc_status s, const std::string &msg) {
+    set_error(msg);
+    return s;
+}
+
+pc_status cuda_fail(cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    set_error(m);
+    if (e == cudaErrorMemoryAllocation) return PC_ENOMEM;
+    return PC_ECUDA;
+}
+
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n); }
+long long launch_count() { return g_launches.load(); }
+
+std::mutex &api_mutex() {
+    static std::mutex m;
+    return m;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// device workspace (grown on demand, reused across calls)
+// ---------------------------------------------------------------------------
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max(bytes, cap * 3 / 2);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            want = bytes;
+            e = cudaMalloc(&p, want);
+        }
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+};
+
+struct Workspace {
+    Buf hist, whist, counters, scalars, queue, blocks, tmp_cnt, tmp_off, tasks, stencil, lut, ea, eb;
+};
+
+static Workspace &workspace(int dev) {
+    static std::map<int, Workspace> ws;
+    return ws[dev];
+}
+
+// ---------------------------------------------------------------------------
+// plan: bins, error bands, lookup tables, stencil
+// ---------------------------------------------------------------------------
+struct Plan {
+    int mode = 0, los = 0, na = 0, nb = 1, nbins = 0;
+    std::vector<double> ea, eb;   // edges
+    std::vector<double> Ea, Eb;   // squared edges
+    double reff = 0, rcut = 0;
+    float eps_a = 0, eps_b = 0, mu_A = 0, mu_B = 0, mu_W = 0;
+    std::vector<float2> lut;
+    LutDesc la{0, 0, 0.f}, lb{0, 0, 0.f};
+    std::vector<int4> stencil;
+    float r2cut = 0;
+    int fp32_ok = 1;              // error bands usable (else use the FP64 path)
+    std::string fp32_why;
+};
+
+static bool edges_ok(const double *e, int n, bool zero_one) {
+    if (n < 1 || !e) return false;
+    for (int k = 0; k <= n; ++k)
+        if (!(e[k] >= 0.0) || !isfinite(e[k])) return false;
+    for (int k = 0; k < n; ++k)
+        if (!(e[k + 1] > e[k])) return false;
+    if (zero_one && !(e[0] == 0.0 && e[n] == 1.0)) return false;
+    return true;
+}
+
+static const double U32 = 5.9604644775390625e-08;   // 2^-24
+
+static float bits_f(int v) {
+    float f;
+    memcpy(&f, &v, sizeof(f));
+    return f;
+}
+
+// Lookup table over [0, V): T cells of width V/T, each holding the single
+// decision edge within `win` of the cell (or +inf if none, NaN if several)
+// and the bin index just below it.  `closed_mu`: the quantity is mu, whose
+// first and last edges (0 and 1) are not decisions.
+static void build_lut(const std::vector<double> &e, bool closed_mu, double V, double win,
+                      std::vector<float2> &out, LutDesc &d) {
+    const int n = (int)e.size() - 1;
+    std::vector<double> dec;      // decision edges
+    std::vector<int> below;       // bin index just below each decision edge
+    for (int m = 0; m <= n; ++m) {
+        if (closed_mu && (m == 0 || m == n)) continue;
+        if (!closed_mu && m == 0 && e[0] == 0.0) continue;   // v >= 0 always holds
+        dec.push_back(e[m]);
+        below.push_back(m - 1);
+    }
+    auto bin_of = [&](double v) {   // bin of a value away from every edge
+        if (closed_mu) {
+            int j = 0;
+            for (int m = 1; m < n; ++m) if (v >= e[m]) j = m;
+            return j;
+        }
+        int k = -1;
+        for (int m = 0; m <= n; ++m) if (v >= e[m]) k = m;
+        return k;   // -1 below e[0], n at or above e[n]
+    };
+    // smallest table (power of two) whose windows hold at most one edge each
+    int T = 16;
+    for (; T < MAX_LUT; T *= 2) {
+        double w = V / T;
+        bool clash = false;
+        for (size_t m = 1; m < dec.size() && !clash; ++m)
+            if (dec[m] - dec[m - 1] <= w + 2.0 * win) clash = true;
+        if (!clash) break;
+    }
+    float inv_w = (float)(T / V);
+    d.off = (int)out.size();
+    d.T = T;
+    d.inv_w = inv_w;
+    const double cw = 1.0 / (double)inv_w;   // actual cell width in value units
+    for (int t = 0; t <= T + 1; ++t) {
+        float2 ent;
+        if (t == T + 1) {   // NaN / inf inputs land here: always rescue
+            ent.x = bits_f(0x7fc00000);
+            ent.y = bits_f(0);
+            out.push_back(ent);
+            continue;
+        }
+        double lo = t * cw - win, hi = (t + 1) * cw + win;
+        int cnt = 0, which = -1;
+        for (size_t m = 0; m < dec.size(); ++m)
+            if (dec[m] >= lo && dec[m] <= hi) { ++cnt; which = (int)m; }
+        if (cnt == 0) {
+            ent.x = INFINITY;
+            int k = bin_of(std::max(0.0, t * cw + 0.5 * cw));
+            ent.y = bits_f(k);
+        } else if (cnt == 1) {
+            ent.x = (float)dec[which];
+            ent.y = bits_f(below[which]);
+        } else {
+            ent.x = bits_f(0x7fc00000);
+            ent.y = bits_f(0);
+        }
+        out.push_back(ent);
+    }
+}
+
+// Stencil rows (dy, dz, xlo, xhi) of cells whose minimum distance to the
+// reference cell is below r (half shell for auto counts, Sect. 3.1).
+static void build_stencil(const Geom &g, double r, bool half, std::vector<int4> &rows,
+                          int kmax[3]) {
+    rows.clear();
+    const double slack = 1e-9 * std::max({g.c[0], g.c[1], g.c[2], fabs(g.lo[0]) + g.L[0],
+                                           fabs(g.lo[1]) + g.L[1], fabs(g.lo[2]) + g.L[2]});
+    auto md = [&](int k, int a) {
+        double v = std::max(std::abs(k) - 1, 0) * g.c[a] - 2.0 * slack;
+        return v > 0 ? v : 0.0;
+    };
+    int ky = (int)ceil(r / g.c[1]) + 1, kz = (int)ceil(r / g.c[2]) + 1;
+    kmax[0] = kmax[1] = kmax[2] = 0;
+    double r2 = r * r;
+    for (int dz = -kz; dz <= kz; ++dz) {
+        for (int dy = -ky; dy <= ky; ++dy) {
+            double m2 = md(dy, 1) * md(dy, 1) + md(dz, 2) * md(dz, 2);
+            if (m2 >= r2) continue;
+            int rx = 0;
+            while (true) {
+                double mx = md(rx + 1, 0);
+                if (mx * mx + m2 < r2) ++rx; else break;
+            }
+            int xlo = -rx, xhi = rx;
+            if (half) {
+                if (dz < 0 || (dz == 0 && dy < 0)) continue;
+                if (dz == 0 && dy == 0) {
+                    if (rx < 1) continue;
+                    xlo = 1;
+                }
+            }
+            rows.push_back(make_int4(dy, dz, xlo, xhi));
+            kmax[0] = std::max(kmax[0], rx);
+            kmax[1] = std::max(kmax[1], std::abs(dy));
+            kmax[2] = std::max(kmax[2], std::abs(dz));
+        }
+    }
+}
+
+static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo,
+                           const double *pts_hi, bool half, Plan &P) {
+    if (!b) return fail(PC_EINVAL, "bins: NULL");
+    if (b->mode < 0 || b->mode > 2) return fail(PC_EINVAL, "bins: unknown mode");
+    if (b->los < 0 || b->los > 1) return fail(PC_EINVAL, "bins: unknown line of sight");
+    P.mode = b->mode;
+    P.los = (b->mode == PC_BIN_S) ? PC_LOS_Z : b->los;
+    if (!edges_ok(b->edges_a, b->n_a, false))
+        return fail(PC_EINVAL, "bins: edges_a must be finite, >= 0 and strictly increasing");
+    P.na = b->n_a;
+    P.ea.assign(b->edges_a, b->edges_a + b->n_a + 1);
+    if (P.mode == PC_BIN_S) {
+        P.nb = 1;
+        P.eb = {0.0, 1.0};
+    } else {
+        if (!edges_ok(b->edges_b, b->n_b, P.mode == PC_BIN_SMU))
+            return fail(PC_EINVAL, P.mode == PC_BIN_SMU
+                                       ? "bins: mu edges must increase strictly from 0 to 1"
+                                       : "bins: pi edges must be finite, >= 0 and increasing");
+        P.nb = b->n_b;
+        P.eb.assign(b->edges_b, b->edges_b + b->n_b + 1);
+    }
+    if ((long long)P.na * P.nb > (1LL << 26)) return fail(PC_EOVERFLOW, "bins: too many bins");
+    P.nbins = P.na * P.nb;
+    if (g.periodic && P.los == PC_LOS_MIDPOINT)
+        return fail(PC_EINVAL, "bins: the midpoint line of sight needs a non-periodic box");
+    P.Ea.resize(P.na + 1);
+    P.Eb.resize(P.nb + 1);
+    for (int k = 0; k <= P.na; ++k) P.Ea[k] = P.ea[k] * P.ea[k];
+    for (int k = 0; k <= P.nb; ++k) P.Eb[k] = P.eb[k] * P.eb[k];
+    P.reff = (P.mode == PC_BIN_SIGPI) ? sqrt(P.ea[P.na] * P.ea[P.na] + P.eb[P.nb] * P.eb[P.nb])
+                                      : P.ea[P.na];
+
+    // ---- FP32 error bands (derivation in the design notes) -----------------
+    const double u = U32;
+    const double c = std::max({g.c[0], g.c[1], g.c[2]});
+    double X = 0.0, Lm = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        X = std::max({X, fabs(pts_lo[a]), fabs(pts_hi[a])});
+        Lm = std::max(Lm, g.L[a]);
+    }
+    const double R0 = P.reff;
+    const double tiny = ldexp(X + Lm + R0, -48);
+    // separation length s (and sigma along z) and the z component
+    double Rb = R0 * (1.0 + 1e-6) + 1e-6 * c;
+    double eps_s = 2.0 * u * (4.4 * c + 10.5 * Rb) + tiny;
+    double eps_z = 2.0 * u * (2.5 * c + 4.0 * Rb) + tiny;
+    double eps_sig = 2.0 * u * (3.6 * c + 11.5 * Rb) + ldexp(Rb, -25) + tiny;
+    double muA = 2.0 * (6.9 * u * c) + tiny, muB = 2.0 * 21.0 * u + ldexp(1.0, -48);
+    if (P.los == PC_LOS_MIDPOINT) {
+        // distance of the nearest point to the observer bounds |x_i + x_j|
+        double dmin2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double d = 0.0;
+            if (pts_lo[a] > 0.0) d = pts_lo[a];
+            else if (pts_hi[a] < 0.0) d = -pts_hi[a];
+            dmin2 += d * d;
+        }
+        double lmin = 2.0 * sqrt(dmin2) - Rb;
+        double dl = u * (5.5 * X + 4.4 * c + 6.2 * Rb);
+        if (lmin > 4.0 * Rb) {
+            double em = 2.0 * (u * (4.4 * c + 17.5 * Rb) + 2.0 * Rb * dl / lmin) +
+                        ldexp(Rb, -25) + tiny;
+            eps_sig = em;
+            eps_z = em;
+            muA = em + eps_s;
+            muB = 2.0 * 8.0 * u + ldexp(1.0, -48);
+        } else {
+            P.fp32_ok = 0;
+            P.fp32_why = "observer too close to the points for the FP32 midpoint bound";
+        }
+    }
+    P.rcut = R0 + std::max({eps_s, eps_z, eps_sig}) * 2.0;
+    {
+        double r2 = P.rcut * P.rcut * (1.0 + 8.0 * u);
+        P.r2cut = nextafterf((float)r2, INFINITY);
+    }
+    // ---- lookup tables ------------------------------------------------------
+    const double V = P.rcut * (1.0 + 1e-5) + 1e-30;
+    P.lut.clear();
+    if (P.mode == PC_BIN_S) {
+        P.eps_a = (float)(eps_s * (1.0 + 1e-6));
+        build_lut(P.ea, false, V, 2.0 * eps_s, P.lut, P.la);
+        P.lb = P.la;
+    } else if (P.mode == PC_BIN_SMU) {
+        P.eps_a = (float)(eps_s * (1.0 + 1e-6));
+        P.mu_A = (float)(muA * (1.0 + 1e-6));
+        P.mu_B = (float)(muB * (1.0 + 1e-6));
+        build_lut(P.ea, false, V, 2.0 * eps_s, P.lut, P.la);
+        // mu window: the band of a pair must fit in it (else always rescue)
+        double minGap = 1.0;
+        for (int k = 0; k < P.nb; ++k) minGap = std::min(minGap, P.eb[k + 1] - P.eb[k]);
+        double wmu = std::min(1e-3, 0.2 * minGap);
+        P.mu_W = (float)wmu;
+        build_lut(P.eb, true, 1.0 + 1e-3, wmu, P.lut, P.lb);
+    } else {
+        P.eps_a = (float)(eps_sig * (1.0 + 1e-6));
+        P.eps_b = (float)(eps_z * (1.0 + 1e-6));
+        build_lut(P.ea, false, V, 2.0 * eps_sig, P.lut, P.la);
+        build_lut(P.eb, false, V, 2.0 * eps_z, P.lut, P.lb);
+    }
+    // ---- stencil -------------------------------------------------------------
+    int kmax[3];
+    build_stencil(g, P.rcut, half, P.stencil, kmax);
+    if (g.periodic) {
+        for (int a = 0; a < 3; ++a) {
+            if (!(P.rcut < 0.5 * g.L[a]))
+                return fail(PC_EINVAL,
+                            "bins: the largest separation must stay below half the periodic box");
+            if (2 * kmax[a] + 1 > g.ng[a])
+                return fail(PC_EINVAL,
+                            "grid: cells too large for this separation in a periodic box "
+                            "(neighbour cells would alias); rebuild with a smaller cell_size");
+        }
+    }
+    return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one counting launch over a set of tasks
+// ---------------------------------------------------------------------------
+struct CountJob {
+    std::vector<TaskDev> tasks;
+    int nhist;
+    bool is_auto;
+    const pc_grid *g0;
+};
+
+static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *opt,
+                           cudaStream_t st, long long *counts, double *wcounts, pc_stats *stats) {
+    pc_opts o;
+    memset(&o, 0, sizeof(o));
+    o.priv = -1;
+    if (opt) o = *opt;
+    const pc_grid *g0 = J.g0;
+    Plan P;
+    pc_status s = make_plan(b, g0->g, g0->pts_lo, g0->pts_hi, J.is_auto, P);
+    if (s != PC_OK) return s;
+    bool weighted = wcounts != nullptr;
+    if (weighted)
+        for (auto &t : J.tasks)
+            (void)t;
+    int prec = o.prec;
+    if (prec == PC_PREC_F32_RESCUE && !P.fp32_ok) prec = PC_PREC_F64;
+    int ipt = (o.ipt == 1 || o.ipt == 2) ? o.ipt : 2;
+    if (prec == PC_PREC_F64) ipt = 1;
+    const int bi = NT * ipt;
+
+    int dev = g0->device;
+    Workspace &W = workspace(dev);
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const long long launches0 = launch_count();
+    if (stats) {
+        for (auto &e : ev) cudaEventCreate(&e);
+        cudaEventRecord(ev[0], st);
+    }
+
+    const int ntasks = (int)J.tasks.size();
+    const int ncell = g0->ncell;
+    long long npts = 0;
+    for (auto &t : J.tasks) npts += t.gi.n;
+    size_t nblk_cap = (size_t)ntasks * ncell + (size_t)(npts / bi) + 16;
+    size_t hist_n = (size_t)J.nhist * P.nbins;
+
+    PC_CUDA(W.hist.ensure(sizeof(unsigned long long) * hist_n));
+    if (weighted) PC_CUDA(W.whist.ensure(sizeof(double) * hist_n));
+    PC_CUDA(W.counters.ensure(sizeof(unsigned long long) * 4));
+    PC_CUDA(W.scalars.ensure(sizeof(int) * 4));
+    PC_CUDA(W.blocks.ensure(sizeof(Block) * nblk_cap));
+    PC_CUDA(W.tmp_cnt.ensure(sizeof(int) * ((size_t)ntasks * ncell + 1)));
+    PC_CUDA(W.tmp_off.ensure(sizeof(int) * ((size_t)ntasks * ncell + 1)));
+    PC_CUDA(W.tasks.ensure(sizeof(TaskDev) * ntasks));
+    PC_CUDA(W.stencil.ensure(sizeof(int4) * std::max<size_t>(P.stencil.size(), 1)));
+    PC_CUDA(W.lut.ensure(sizeof(float2) * std::max<size_t>(P.lut.size(), 1)));
+    PC_CUDA(W.ea.ensure(sizeof(double) * (P.na + 1)));
+    PC_CUDA(W.eb.ensure(sizeof(double) * (P.nb + 1)));
+
+    // rescue queue capacity: ~2e-3 of the expected in-range pairs
+    unsigned long long qcap = 0;
+    if (prec == PC_PREC_F32_RESCUE) {
+        if (o.rescue_capacity > 0) qcap = (unsigned long long)o.rescue_capacity;
+        else if (o.rescue_capacity == 0) {
+            double vol = 1.0;
+            for (int a = 0; a < 3; ++a) vol *= std::max(g0->pts_hi[a] - g0->pts_lo[a], 1e-9);
+            double vs = 4.0 / 3.0 * M_PI * P.reff * P.reff * P.reff;
+            double pairs = 0.0;
+            for (auto &t : J.tasks) pairs += 0.5 * (double)t.gi.n * (double)t.gj.n * std::min(1.0, vs / vol);
+            double want = std::max(1.0e6, 4.0e-3 * pairs * (J.is_auto ? 1.0 : 2.0));
+            qcap = (unsigned long long)std::min(want, 4.0e8);
+        }
+        if (qcap) PC_CUDA(W.queue.ensure(sizeof(uint3) * qcap));
+    }
+
+    PC_CUDA(cudaMemcpyAsync(W.tasks.p, J.tasks.data(), sizeof(TaskDev) * ntasks,
+                            cudaMemcpyHostToDevice, st));
+    if (!P.stencil.empty())
+        PC_CUDA(cudaMemcpyAsync(W.stencil.p, P.stencil.data(), sizeof(int4) * P.stencil.size(),
+                                cudaMemcpyHostToDevice, st));
+    if (!P.lut.empty())
+        PC_CUDA(cudaMemcpyAsync(W.lut.p, P.lut.data(), sizeof(float2) * P.lut.size(),
+                                cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(W.ea.p, P.Ea.data(), sizeof(double) * (P.na + 1), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(W.eb.p, P.Eb.data(), sizeof(double) * (P.nb + 1), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemsetAsync(W.hist.p, 0, sizeof(unsigned long long) * hist_n, st));
+    if (weighted) PC_CUDA(cudaMemsetAsync(W.whist.p, 0, sizeof(double) * hist_n, st));
+    PC_CUDA(cudaMemsetAsync(W.counters.p, 0, sizeof(unsigned long long) * 4, st));
+    PC_CUDA(cudaMemsetAsync(W.scalars.p, 0, sizeof(int) * 4, st));
+
+    int *sc = (int *)W.scalars.p;   // [0] work counter, [1] nblocks
+    unsigned long long *ctr = (unsigned long long *)W.counters.p;   // [0] cand, [1] inline, [2] qcount
+    PC_CUDA(make_blocks((const TaskDev *)W.tasks.p, ntasks, ncell, bi, (Block *)W.blocks.p, sc + 1,
+                        (int *)W.tmp_cnt.p, (int *)W.tmp_off.p, st));
+
+    PairParams p;
+    memset(&p, 0, sizeof(p));
+    p.tasks = (const TaskDev *)W.tasks.p;
+    p.blocks = (const Block *)W.blocks.p;
+    p.nblocks = sc + 1;
+    p.work_counter = sc;
+    p.g = g0->g;
+    p.stencil = (const int4 *)W.stencil.p;
+    p.nrows = (int)P.stencil.size();
+    p.mode = P.mode;
+    p.los = P.los;
+    p.weighted = weighted ? 1 : 0;
+    p.n_a = P.na;
+    p.n_b = P.nb;
+    p.nbins = P.nbins;
+    p.r2cut = P.r2cut;
+    p.lut = (const float2 *)W.lut.p;
+    p.lut_total = (int)P.lut.size();
+    p.la = P.la;
+    p.lb = P.lb;
+    p.eps_a = P.eps_a;
+    p.eps_b = P.eps_b;
+    p.mu_A = P.mu_A;
+    p.mu_B = P.mu_B;
+    p.mu_W = P.mu_W;
+    p.Ea = (const double *)W.ea.p;
+    p.Eb = (const double *)W.eb.p;
+    p.hist = (unsigned long long *)W.hist.p;
+    p.whist = weighted ? (double *)W.whist.p : nullptr;
+    p.queue = (uint3 *)W.queue.p;
+    p.qcount = ctr + 2;
+    p.qcap = qcap;
+    p.counters = ctr;
+    // histogram privatisation: one copy per warp when it fits and helps
+    int copies_warp = P.nbins * (NT / 32) * 4;
+    if (o.priv == 0 || o.priv == 1) p.priv = o.priv;
+    else p.priv = (P.nbins <= 2048 && copies_warp <= 48 * 1024) ? 1 : 0;
+
+    int dev_sms = 0;
+    PC_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev));
+    int smem_optin = 0;
+    PC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int static_smem = 256;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        p.smem_hist_ok = 1;
+        size_t need = (prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, ipt);
+        if (need + static_smem <= (size_t)smem_optin) break;
+        if (p.priv) { p.priv = 0; continue; }
+        p.smem_hist_ok = 0;
+        break;
+    }
+    size_t smem = (prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, ipt);
+    if (smem + static_smem > (size_t)smem_optin)
+        return fail(PC_EUNSUPPORTED, "bins: tables do not fit in shared memory");
+    int per_sm = (prec == PC_PREC_F64) ? pairs_f64_ctas_per_sm(p, smem)
+                                       : pairs_f32_ctas_per_sm(p, ipt, smem);
+    if (per_sm <= 0) return fail(PC_ECUDA, std::string("pair kernel cannot be resident: ") + pc_last_error());
+    if (o.grid_ctas_per_sm > 0) per_sm = std::min(per_sm, o.grid_ctas_per_sm);
+    int grid = dev_sms * per_sm;
+
+    if (stats) cudaEventRecord(ev[2], st);
+    cudaError_t e = (prec == PC_PREC_F64) ? launch_pairs_f64(p, grid, smem, st)
+                                          : launch_pairs_f32(p, ipt, grid, smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "pair kernel launch");
+    if (stats) cudaEventRecord(ev[3], st);
+    if (prec == PC_PREC_F32_RESCUE && qcap) {
+        e = launch_rescue(p, st);
+        if (e != cudaSuccess) return cuda_fail(e, "rescue kernel launch");
+    }
+    if (stats) cudaEventRecord(ev[4], st);
+
+    // results
+    if (counts) {
+        cudaMemcpyKind k = is_device_ptr(counts) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        PC_CUDA(cudaMemcpyAsync(counts, W.hist.p, sizeof(long long) * hist_n, k, st));
+    }
+    if (wcounts) {
+        cudaMemcpyKind k = is_device_ptr(wcounts) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        PC_CUDA(cudaMemcpyAsync(wcounts, W.whist.p, sizeof(double) * hist_n, k, st));
+    }
+    unsigned long long hc[3] = {0, 0, 0};
+    int hblk = 0;
+    if (stats) {
+        PC_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        PC_CUDA(cudaMemcpyAsync(&hblk, sc + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        cudaEventRecord(ev[1], st);
+    }
+    PC_CUDA(cudaStreamSynchronize(st));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->candidates = (long long)hc[0];
+        stats->rescue_inline = (long long)hc[1];
+        stats->rescued = (long long)std::min<unsigned long long>(hc[2], qcap) + (long long)hc[1];
+        stats->blocks = hblk;
+        stats->cell_size = g0->cell_size;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        stats->ms_total = ms;
+        cudaEventElapsedTime(&ms, ev[2], ev[3]);
+        stats->ms_pairs = ms;
+        cudaEventElapsedTime(&ms, ev[3], ev[4]);
+        stats->ms_rescue = ms;
+        stats->launches = (int)(launch_count() - launches0);
+        for (auto &x : ev) cudaEventDestroy(x);
+    }
+    return PC_OK;
+}
+
+static TaskDev task_of(const pc_grid *gi, const pc_grid *gj, int hist, int is_auto) {
+    TaskDev t;
+    t.gi = GridDev{gi->rel, gi->cx, gi->xw, gi->cell_start, gi->n};
+    t.gj = GridDev{gj->rel, gj->cx, gj->xw, gj->cell_start, gj->n};
+    t.hist = hist;
+    t.is_auto = is_auto;
+    return t;
+}
+
+static bool same_geometry(const pc_grid *a, const pc_grid *b) {
+    if (a->g.periodic != b->g.periodic) return false;
+    for (int k = 0; k < 3; ++k) {
+        if (a->g.ng[k] != b->g.ng[k] || a->g.c[k] != b->g.c[k] || a->g.lo[k] != b->g.lo[k] ||
+            a->g.L[k] != b->g.L[k])
+            return false;
+    }
+    return a->device == b->device;
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+extern "C" pc_status pc_count_auto(const pc_grid *g, const pc_bins *b, const pc_opts *o,
+                                   void *stream, long long *counts, double *wcounts,
+                                   pc_stats *st) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!g) return fail(PC_EINVAL, "pc_count_auto: grid is NULL");
+    if (!counts && !wcounts) return fail(PC_EINVAL, "pc_count_auto: no output buffer");
+    if (wcounts && !g->weighted) return fail(PC_EINVAL, "pc_count_auto: grid has no weights");
+    CountJob J;
+    J.tasks.push_back(task_of(g, g, 0, 1));
+    J.nhist = 1;
+    J.is_auto = true;
+    J.g0 = g;
+    return run_count(J, b, o, (cudaStream_t)stream, counts, wcounts, st);
+}
+
+extern "C" pc_status pc_count_cross(const pc_grid *g1, const pc_grid *g2, const pc_bins *b,
+                                    const pc_opts *o, void *stream, long long *counts,
+                                    double *wcounts, pc_stats *st) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!g1 || !g2) return fail(PC_EINVAL, "pc_count_cross: grid is NULL");
+    if (!counts && !wcounts) return fail(PC_EINVAL, "pc_count_cross: no output buffer");
+    if (!same_geometry(g1, g2))
+        return fail(PC_EINVAL, "pc_count_cross: grids differ in box, bounds or cell size");
+    if (wcounts && !(g1->weighted && g2->weighted))
+        return fail(PC_EINVAL, "pc_count_cross: both grids need weights for weighted counts");
+    CountJob J;
+    J.tasks.push_back(task_of(g1, g2, 0, 0));
+    J.nhist = 1;
+    J.is_auto = false;
+    J.g0 = g1;
+    return run_count(J, b, o, (cudaStream_t)stream, counts, wcounts, st);
+}
+
+extern "C" pc_status pc_count_batch(const pc_grid *const *gs, int m, const pc_bins *b,
+                                    const pc_opts *o, void *stream, long long *counts,
+                                    double *wcounts, pc_stats *st) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!gs || m <= 0) return fail(PC_EINVAL, "pc_count_batch: no grids");
+    if (m >= (1 << 26)) return fail(PC_EOVERFLOW, "pc_count_batch: too many grids");
+    if (!counts && !wcounts) return fail(PC_EINVAL, "pc_count_batch: no output buffer");
+    CountJob J;
+    for (int k = 0; k < m; ++k) {
+        if (!gs[k]) return fail(PC_EINVAL, "pc_count_batch: grid is NULL");
+        if (!same_geometry(gs[0], gs[k]))
+            return fail(PC_EINVAL, "pc_count_batch: grids differ in box or cell size");
+        if (wcounts && !gs[k]->weighted) return fail(PC_EINVAL, "pc_count_batch: grid has no weights");
+        J.tasks.push_back(task_of(gs[k], gs[k], k, 1));
+    }
+    J.nhist = m;
+    J.is_auto = true;
+    J.g0 = gs[0];
+    return run_count(J, b, o, (cudaStream_t)stream, counts, wcounts, st);
+}
+
+// Cost model of Appendix B.1 (cost = a N_pair + b N_node), specialised to the
+// GPU kernel: candidate pairs are charged per thread lane (a block occupies
+// NT * 2 lanes however many points its cell holds), and every (block,
+// stencil row) visit costs a fixed amount of segment building.
+extern "C" double pc_suggest_cell_size(long long n, double volume, double r_max, int mode) {
+    (void)mode;
+    if (!(r_max > 0.0)) return 1.0;
+    if (n <= 1 || !(volume > 0.0)) return r_max;
+    const double rho = (double)n / volume;
+    const double bi = 2.0 * NT;
+    const double a = 1.0, brow = 350.0;   // relative costs (lane-pair, block-row)
+    double best = r_max, best_cost = INFINITY;
+    for (int k = 2; k <= 64; ++k) {
+        double c = r_max * 4.0 / k;   // c from 2 R down to R / 16
+        double nc = rho * c * c * c;
+        if (nc < 4.0 && k > 2) continue;
+        double cells = volume / (c * c * c);
+        double blocks_per_cell = std::max(1.0, ceil(nc / bi));
+        // stencil cells (half shell) by direct count
+        double kk = ceil(r_max / c) + 1;
+        double ncand_cells = 0, nrows = 0;
+        for (int dz = -(int)kk; dz <= (int)kk; ++dz)
+            for (int dy = -(int)kk; dy <= (int)kk; ++dy) {
+                double my = std::max(std::abs(dy) - 1, 0) * c, mz = std::max(std::abs(dz) - 1, 0) * c;
+                double m2 = my * my + mz * mz;
+                if (m2 >= r_max * r_max) continue;
+                int rx = 0;
+                while (true) {
+                    double mx = rx * c;
+                    if (mx * mx + m2 < r_max * r_max) ++rx; else break;
+                }
+                ncand_cells += 2 * rx + 1;
+                nrows += 1;
+            }
+        ncand_cells *= 0.5;
+        nrows *= 0.5;
+        double lanes = cells * blocks_per_cell * bi;
+        double cost = a * lanes * ncand_cells * nc + brow * cells * blocks_per_cell * nrows;
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = c;
+        }
+    }
+    return best;
+}
+
+extern "C" const char *pc_strerror(pc_status s) {
+    switch (s) {
+        case PC_OK: return "success";
+        case PC_EINVAL: return "invalid argument";
+        case PC_ENOMEM: return "out of memory";
+        case PC_ECUDA: return "CUDA error";
+        case PC_EOVERFLOW: return "size overflow";
+        case PC_ETIMEOUT: return "device wait timed out";
+        case PC_EUNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *pc_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" long long pc_launch_count(void) { return launch_count(); }
+
+extern "C" const char *pc_version(void) { return "paircount-gb300 0.1 (sm_103a)"; }

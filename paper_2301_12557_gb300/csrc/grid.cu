@@ -1,0 +1,514 @@
+// Grid construction (Sect. 2.1: bounds, per-cell counts, grouping) and the
+// i-block list that feeds the pair kernels.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "pc_host.hpp"
+
+namespace pc {
+
+// ---------------------------------------------------------------------------
+// periodic canonical form x - L floor(x / L), folded into [0, L)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double canon(double x, double L) {
+    double y = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
+    if (y < 0.0) y = __dadd_rn(y, L);
+    if (y >= L) y = __dsub_rn(y, L);
+    return y;
+}
+
+// order-preserving map of a double onto a signed 64-bit key
+__device__ __forceinline__ long long dkey(double v) {
+    long long b = __double_as_longlong(v);
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+__host__ __device__ __forceinline__ double dunkey(long long k) {
+    long long b = k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFLL);
+    double v;
+    memcpy(&v, &b, sizeof(v));
+    return v;
+}
+
+__global__ void k_aabb(const double *__restrict__ xyz, long long n, long long *out) {
+    long long mn[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
+    long long mx[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            long long k = dkey(xyz[3 * i + a]);
+            mn[a] = min(mn[a], k);
+            mx[a] = max(mx[a], k);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&out[a], mn[a]);
+            atomicMax(&out[3 + a], mx[a]);
+        }
+    }
+}
+
+pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *lo, double *hi) {
+    long long init[6] = {LLONG_MAX, LLONG_MAX, LLONG_MAX, LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    long long *d = nullptr;
+    PC_CUDA(cudaMallocAsync(&d, sizeof(init), st));
+    PC_CUDA(cudaMemcpyAsync(d, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    if (n > 0) {
+        int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+        k_aabb<<<grid, 256, 0, st>>>(xyz, n, d);
+        note_launch();
+        PC_CUDA(cudaGetLastError());
+    }
+    long long res[6];
+    PC_CUDA(cudaMemcpyAsync(res, d, sizeof(res), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaFreeAsync(d, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = dunkey(res[a]);
+        hi[a] = dunkey(res[3 + a]);
+    }
+    return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// cell ids and scatter
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_axis(double x, double lo, double c, int ng) {
+    double f = floor(__ddiv_rn(__dsub_rn(x, lo), c));
+    if (!(f >= 0.0)) return 0;
+    if (f >= (double)(ng - 1)) return ng - 1;
+    return (int)f;
+}
+
+__global__ void k_cell_ids(const double *__restrict__ xyz, int n, Geom g, int *__restrict__ cell,
+                           int *__restrict__ slot, int *__restrict__ counts) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int id[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double x = xyz[3 * (size_t)i + a];
+        if (g.periodic) x = canon(x, g.L[a]);
+        id[a] = cell_axis(x, g.lo[a], g.c[a], g.ng[a]);
+    }
+    int c = (id[2] * g.ng[1] + id[1]) * g.ng[0] + id[0];
+    cell[i] = c;
+    slot[i] = atomicAdd(&counts[c], 1);
+}
+
+__global__ void k_scatter(const double *__restrict__ xyz, const void *__restrict__ w, int w_is_f32,
+                          int n, Geom g, const int *__restrict__ cell, const int *__restrict__ slot,
+                          const int *__restrict__ cell_start, float4 *__restrict__ rel,
+                          uint16_t *__restrict__ cxo, double4_32a *__restrict__ xw,
+                          int *__restrict__ perm) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = cell[i];
+    int pos = cell_start[c] + slot[i];
+    int id[3] = {c % g.ng[0], (c / g.ng[0]) % g.ng[1], c / (g.ng[0] * g.ng[1])};
+    double x[3];
+    float r[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double v = xyz[3 * (size_t)i + a];
+        if (g.periodic) v = canon(v, g.L[a]);
+        x[a] = v;
+        double o = __dadd_rn(g.lo[a], __dmul_rn((double)id[a] + 0.5, g.c[a]));
+        r[a] = __double2float_rn(__dsub_rn(v, o));
+    }
+    double wv = 1.0;
+    if (w) wv = w_is_f32 ? (double)((const float *)w)[i] : ((const double *)w)[i];
+    rel[pos] = make_float4(r[0], r[1], r[2], 0.0f);
+    cxo[pos] = (uint16_t)id[0];
+    xw[pos] = make_double4_32a(x[0], x[1], x[2], wv);
+    perm[pos] = i;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan (three passes: per-tile scan, scan of tile totals, add)
+// ---------------------------------------------------------------------------
+constexpr int SCAN_T = 1024;
+constexpr int SCAN_V = 4;
+constexpr int SCAN_TILE = SCAN_T * SCAN_V;
+
+__device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int &total) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int y = (lane < (int)(blockDim.x >> 5)) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        s_warp[lane] = y;   // inclusive warp totals
+    }
+    __syncthreads();
+    total = s_warp[(blockDim.x >> 5) - 1];
+    int base = warp ? s_warp[warp - 1] : 0;
+    int r = base + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int *in, int *out, int n, int *tile_tot) {
+    __shared__ int s_warp[32];
+    long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_V;
+    int v[SCAN_V];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        sum += v[k];
+    }
+    int total;
+    int run = block_excl_scan(sum, s_warp, total);
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) tile_tot[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_totals(int *tot, int ntiles, int *out, int n) {
+    __shared__ int s_warp[32];
+    int carry = 0;
+    for (int b0 = 0; b0 < ntiles; b0 += SCAN_T) {
+        int i = b0 + threadIdx.x;
+        int v = (i < ntiles) ? tot[i] : 0;
+        int total;
+        int r = block_excl_scan(v, s_warp, total);
+        if (i < ntiles) tot[i] = r + carry;
+        carry += total;
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+__global__ void k_scan_add(int *out, int n, const int *tot) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tot[i / SCAN_TILE];
+}
+
+cudaError_t scan_exclusive(const int *in, int *out, int n, cudaStream_t st) {
+    int ntiles = std::max(1, (n + SCAN_TILE - 1) / SCAN_TILE);
+    int *tot = nullptr;
+    cudaError_t e = cudaMallocAsync(&tot, sizeof(int) * ntiles, st);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_scan_tiles<<<ntiles, SCAN_T, 0, st>>>(in, out, n, tot);
+        note_launch();
+    } else {
+        cudaMemsetAsync(tot, 0, sizeof(int), st);
+    }
+    k_scan_totals<<<1, SCAN_T, 0, st>>>(tot, n > 0 ? ntiles : 1, out, n);
+    note_launch();
+    if (n > 0) {
+        k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, n, tot);
+        note_launch();
+    }
+    e = cudaGetLastError();
+    cudaFreeAsync(tot, st);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// block list
+// ---------------------------------------------------------------------------
+__global__ void k_block_counts(const TaskDev *tasks, int ntasks, int ncell, int bi, int *cnt) {
+    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)ntasks * ncell) return;
+    int t = (int)(gid / ncell), c = (int)(gid % ncell);
+    const int *cs = tasks[t].gi.cell_start;
+    int nc = cs[c + 1] - cs[c];
+    cnt[gid] = (nc + bi - 1) / bi;
+}
+
+__global__ void k_block_emit(const TaskDev *tasks, int ntasks, int ncell, const int *off,
+                             Block *blocks, int *nblocks) {
+    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tot = (long long)ntasks * ncell;
+    if (gid == 0) *nblocks = off[tot];
+    if (gid >= tot) return;
+    int t = (int)(gid / ncell), c = (int)(gid % ncell);
+    int o0 = off[gid], nb = off[gid + 1] - o0;
+    if (nb == 0) return;
+    const int *cs = tasks[t].gi.cell_start;
+    int s = cs[c], nc = cs[c + 1] - s;
+    for (int k = 0; k < nb; ++k) {
+        int b0 = s + (int)((long long)k * nc / nb);
+        int b1 = s + (int)((long long)(k + 1) * nc / nb);
+        blocks[o0 + k] = Block{t, c, b0, b1 - b0};
+    }
+}
+
+cudaError_t make_blocks(const TaskDev *tasks_dev, int ntasks, int ncell, int bi, Block *blocks,
+                        int *nblocks_dev, int *tmp_counts, int *tmp_offsets, cudaStream_t st) {
+    long long tot = (long long)ntasks * ncell;
+    int g = (int)((tot + 255) / 256);
+    if (g > 0) {
+        k_block_counts<<<g, 256, 0, st>>>(tasks_dev, ntasks, ncell, bi, tmp_counts);
+        note_launch();
+    }
+    cudaError_t e = scan_exclusive(tmp_counts, tmp_offsets, (int)tot, st);
+    if (e != cudaSuccess) return e;
+    k_block_emit<<<std::max(g, 1), 256, 0, st>>>(tasks_dev, ntasks, ncell, tmp_offsets, blocks,
+                                                 nblocks_dev);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace pc
+
+// ---------------------------------------------------------------------------
+// public: grid build / free / info / aabb
+// ---------------------------------------------------------------------------
+using namespace pc;
+
+extern "C" pc_status pc_aabb(const double *xyz, long long n, void *stream, double *lo,
+                             double *hi) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!lo || !hi || n < 0 || (n > 0 && !xyz)) return fail(PC_EINVAL, "pc_aabb: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double *dx = xyz;
+    double *tmp = nullptr;
+    if (n > 0 && !is_device_ptr(xyz)) {
+        PC_CUDA(cudaMallocAsync(&tmp, sizeof(double) * 3 * n, st));
+        PC_CUDA(cudaMemcpyAsync(tmp, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+        dx = tmp;
+    }
+    pc_status s = aabb_device(dx, n, st, lo, hi);
+    if (tmp) cudaFreeAsync(tmp, st);
+    cudaStreamSynchronize(st);
+    return s;
+}
+
+static void grid_release(pc_grid *g) {
+    if (!g) return;
+    cudaFree(g->rel);
+    cudaFree(g->cx);
+    cudaFree(g->xw);
+    cudaFree(g->cell_start);
+    cudaFree(g->perm);
+    delete g;
+}
+
+extern "C" void pc_free_grid(pc_grid *g) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    grid_release(g);
+}
+
+extern "C" pc_status pc_grid_info(const pc_grid *g, long long *n, double *cell_size) {
+    if (!g) return fail(PC_EINVAL, "pc_grid_info: null grid");
+    if (n) *n = g->n;
+    if (cell_size) *cell_size = g->cell_size;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f32, long long n,
+                                   const pc_box *box, double r_max, const pc_opts *opt,
+                                   void *stream, pc_grid **out) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!out) return fail(PC_EINVAL, "pc_build_grid: out is NULL");
+    *out = nullptr;
+    if (!box) return fail(PC_EINVAL, "pc_build_grid: box is NULL");
+    if (n < 0) return fail(PC_EINVAL, "pc_build_grid: n < 0");
+    if (n > 0 && !xyz) return fail(PC_EINVAL, "pc_build_grid: xyz is NULL");
+    if (n >= (1LL << 31) - 1) return fail(PC_EOVERFLOW, "pc_build_grid: n must be below 2^31");
+    if (!(r_max > 0.0) || !isfinite(r_max))
+        return fail(PC_EINVAL, "pc_build_grid: r_max must be positive and finite");
+    pc_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    PC_CUDA(cudaGetDevice(&dev));
+
+    // inputs on the device
+    const double *dxyz = xyz;
+    const void *dw = w;
+    double *tmp_xyz = nullptr;
+    void *tmp_w = nullptr;
+    if (n > 0 && !is_device_ptr(xyz)) {
+        PC_CUDA(cudaMallocAsync(&tmp_xyz, sizeof(double) * 3 * n, st));
+        PC_CUDA(cudaMemcpyAsync(tmp_xyz, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+        dxyz = tmp_xyz;
+    }
+    size_t wbytes = (size_t)n * (w_is_f32 ? sizeof(float) : sizeof(double));
+    if (w && n > 0 && !is_device_ptr(w)) {
+        PC_CUDA(cudaMallocAsync(&tmp_w, wbytes, st));
+        PC_CUDA(cudaMemcpyAsync(tmp_w, w, wbytes, cudaMemcpyHostToDevice, st));
+        dw = tmp_w;
+    }
+    auto cleanup = [&]() {
+        if (tmp_xyz) cudaFreeAsync(tmp_xyz, st);
+        if (tmp_w) cudaFreeAsync(tmp_w, st);
+    };
+
+    pc_grid *g = new pc_grid();
+    memset(g, 0, sizeof(*g));
+    g->device = dev;
+    g->n = (int)n;
+    g->weighted = (w != nullptr);
+    Geom &G = g->g;
+    G.periodic = box->periodic ? 1 : 0;
+
+    // bounds of the points
+    double plo[3] = {0, 0, 0}, phi[3] = {0, 0, 0};
+    if (G.periodic) {
+        for (int a = 0; a < 3; ++a) {
+            if (!(box->L[a] > 0.0) || !isfinite(box->L[a])) {
+                cleanup();
+                delete g;
+                return fail(PC_EINVAL, "pc_build_grid: periodic box needs L > 0 on every axis");
+            }
+            if (!(r_max < 0.5 * box->L[a])) {
+                cleanup();
+                delete g;
+                return fail(PC_EINVAL,
+                            "pc_build_grid: r_max must stay below half the periodic box side");
+            }
+            G.L[a] = box->L[a];
+            G.hL[a] = 0.5 * box->L[a];
+            G.lo[a] = 0.0;
+            plo[a] = 0.0;
+            phi[a] = box->L[a];
+        }
+    } else {
+        if (n > 0) {
+            pc_status s = aabb_device(dxyz, n, st, plo, phi);
+            if (s != PC_OK) { cleanup(); delete g; return s; }
+            for (int a = 0; a < 3; ++a)
+                if (!isfinite(plo[a]) || !isfinite(phi[a])) {
+                    cleanup();
+                    delete g;
+                    return fail(PC_EINVAL, "pc_build_grid: non-finite coordinates");
+                }
+        }
+        bool given = box->hi[0] > box->lo[0] && box->hi[1] > box->lo[1] && box->hi[2] > box->lo[2];
+        for (int a = 0; a < 3; ++a) {
+            if (given) {
+                if (n > 0 && (plo[a] < box->lo[a] || phi[a] > box->hi[a])) {
+                    cleanup();
+                    delete g;
+                    return fail(PC_EINVAL, "pc_build_grid: points lie outside the given bounds");
+                }
+                G.lo[a] = box->lo[a];
+            } else {
+                G.lo[a] = plo[a];
+            }
+            G.L[a] = 0.0;
+            G.hL[a] = 0.0;
+        }
+        if (given)
+            for (int a = 0; a < 3; ++a) { plo[a] = box->lo[a]; phi[a] = box->hi[a]; }
+    }
+    for (int a = 0; a < 3; ++a) { g->pts_lo[a] = plo[a]; g->pts_hi[a] = phi[a]; }
+
+    // cell geometry
+    double vol = 1.0;
+    for (int a = 0; a < 3; ++a) vol *= std::max(phi[a] - plo[a], 1e-300);
+    double c = o.cell_size > 0.0 ? o.cell_size : pc_suggest_cell_size(n, vol, r_max, 1);
+    const long long MAXCELL = 1LL << 26;
+    for (int iter = 0; iter < 200; ++iter) {
+        long long tot = 1;
+        for (int a = 0; a < 3; ++a) {
+            double ext = phi[a] - plo[a];
+            long long k;
+            if (G.periodic) k = std::max(1LL, (long long)floor(ext / c));
+            else k = std::max(1LL, (long long)ceil(ext / c));
+            if (k > 65535) k = 65536;
+            G.ng[a] = (int)k;
+            tot *= k;
+        }
+        bool ok = tot <= MAXCELL && G.ng[0] <= 65535 && G.ng[1] <= 65535 && G.ng[2] <= 65535;
+        if (ok) break;
+        c *= 1.1;
+    }
+    if (G.periodic) {
+        // neighbour offsets reach ceil(r / c) cells each way; a periodic axis
+        // needs 2 * that + 1 distinct cells so no two offsets alias
+        const double rr = r_max * (1.0 + 1e-4);
+        for (int a = 0; a < 3; ++a) {
+            while (G.ng[a] < 65535 &&
+                   G.ng[a] < 2 * (long long)ceil(rr / (G.L[a] / G.ng[a])) + 1)
+                G.ng[a] += 1;
+        }
+    }
+    if ((long long)G.ng[0] * G.ng[1] * G.ng[2] > MAXCELL || G.ng[0] > 65535 ||
+        G.ng[1] > 65535 || G.ng[2] > 65535) {
+        cleanup();
+        delete g;
+        return fail(PC_EOVERFLOW, "pc_build_grid: too many cells for this box and separation");
+    }
+    g->cell_size = c;
+    for (int a = 0; a < 3; ++a) {
+        G.c[a] = G.periodic ? G.L[a] / G.ng[a] : c;
+        G.c32[a] = (float)G.c[a];
+    }
+    g->ncell = G.ng[0] * G.ng[1] * G.ng[2];
+
+    // device arrays
+    cudaError_t e = cudaSuccess;
+    size_t nn = std::max<long long>(n, 1);
+    e = cudaMalloc(&g->rel, sizeof(float4) * nn);
+    if (e == cudaSuccess) e = cudaMalloc(&g->cx, sizeof(uint16_t) * nn);
+    if (e == cudaSuccess) e = cudaMalloc(&g->xw, sizeof(double4_32a) * nn);
+    if (e == cudaSuccess) e = cudaMalloc(&g->cell_start, sizeof(int) * (g->ncell + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->perm, sizeof(int) * nn);
+    if (e != cudaSuccess) {
+        cleanup();
+        grid_release(g);
+        cudaGetLastError();
+        return fail(PC_ENOMEM, "pc_build_grid: device allocation failed");
+    }
+    int *counts = nullptr, *cell = nullptr, *slot = nullptr;
+    e = cudaMallocAsync(&counts, sizeof(int) * g->ncell, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&cell, sizeof(int) * nn, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&slot, sizeof(int) * nn, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int) * g->ncell, st);
+    if (e == cudaSuccess && n > 0) {
+        int blocks = (int)((n + 255) / 256);
+        k_cell_ids<<<blocks, 256, 0, st>>>(dxyz, (int)n, G, cell, slot, counts);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = scan_exclusive(counts, g->cell_start, g->ncell, st);
+    if (e == cudaSuccess && n > 0) {
+        int blocks = (int)((n + 255) / 256);
+        k_scatter<<<blocks, 256, 0, st>>>(dxyz, dw, w_is_f32, (int)n, G, cell, slot, g->cell_start,
+                                          g->rel, g->cx, g->xw, g->perm);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (counts) cudaFreeAsync(counts, st);
+    if (cell) cudaFreeAsync(cell, st);
+    if (slot) cudaFreeAsync(slot, st);
+    cleanup();
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        grid_release(g);
+        return cuda_fail(e, "pc_build_grid");
+    }
+    *out = g;
+    return PC_OK;
+}

@@ -1,0 +1,22 @@
+// Instantiation of the pair kernels for MODE_SMU / LOS_MID.
+#include "pairs_impl.cuh"
+
+namespace pc {
+
+cudaError_t launch_f32_SMU_MID(const PairParams &p, int ipt, int grid, size_t smem, cudaStream_t st) {
+    return launch_mode_f32<MODE_SMU, LOS_MID>(p, ipt, grid, smem, st);
+}
+int occ_f32_SMU_MID(const PairParams &p, int ipt, size_t smem) {
+    return occupancy_mode_f32<MODE_SMU, LOS_MID>(p, ipt, smem);
+}
+cudaError_t launch_f64_SMU_MID(const PairParams &p, int grid, size_t smem, cudaStream_t st) {
+    return launch_mode_f64<MODE_SMU, LOS_MID>(p, grid, smem, st);
+}
+int occ_f64_SMU_MID(const PairParams &p, size_t smem) {
+    return occupancy_mode_f64<MODE_SMU, LOS_MID>(p, smem);
+}
+cudaError_t launch_rescue_SMU_MID(const PairParams &p, int grid, cudaStream_t st) {
+    return launch_mode_rescue<MODE_SMU, LOS_MID>(p, grid, st);
+}
+
+}  // namespace pc

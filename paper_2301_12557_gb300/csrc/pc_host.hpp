@@ -1,0 +1,46 @@
+// Host-side internal declarations of libpaircount.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
+
+#include "pc_internal.cuh"
+
+struct pc_grid {
+    int device;
+    int n;
+    int weighted;
+    pc::Geom g;
+    int ncell;
+    double cell_size;           // requested cubic cell side
+    double pts_lo[3], pts_hi[3];  // bounds of the (canonical) points
+    float4 *rel;
+    uint16_t *cx;
+    double4_32a *xw;
+    int *cell_start;
+    int *perm;
+};
+
+namespace pc {
+
+// Global library lock: calls are serialised (the workspace is shared).
+std::mutex &api_mutex();
+
+// Pointer classification: true if `p` is device (or managed) memory.
+bool is_device_ptr(const void *p);
+
+// Exclusive scan of n ints into out[0..n] (out[n] = total), stream-ordered.
+cudaError_t scan_exclusive(const int *in, int *out, int n, cudaStream_t st);
+
+// Block list: for every task t and every cell c of its i-grid, split the
+// cell's points into ceil(count / bi) balanced blocks.  Writes the blocks
+// (capacity must be >= sum over tasks of ncell + n / bi) and *nblocks.
+cudaError_t make_blocks(const TaskDev *tasks_dev, int ntasks, int ncell, int bi, Block *blocks,
+                        int *nblocks_dev, int *tmp_counts, int *tmp_offsets, cudaStream_t st);
+
+// Device-side bounding box; lo/hi are host arrays (the call synchronises).
+pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *lo, double *hi);
+
+}  // namespace pc

@@ -1,0 +1,215 @@
+// Internal definitions shared by the CUDA translation units of libpaircount.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "paircount.h"
+
+namespace pc {
+
+// ---------------------------------------------------------------------------
+// launch geometry of the pair kernels
+// ---------------------------------------------------------------------------
+constexpr int NT = 128;        // threads per CTA
+constexpr int TJ = 256;        // j points per shared-memory tile (FP32 path)
+constexpr int TJ64 = 128;      // j points per tile (FP64 path)
+constexpr int MAXSEG = 512;    // j segments per chunk of stencil rows
+constexpr int ROWCHUNK = 160;  // stencil rows per chunk (<= 3 segments each)
+constexpr int LQ = 256;        // per-CTA rescue staging slots
+constexpr int MAX_LUT = 8192;  // LUT entries per histogram axis
+
+enum { MODE_S = 0, MODE_SMU = 1, MODE_SIGPI = 2 };
+enum { LOS_Z = 0, LOS_MID = 1 };
+
+// Cell-sorted device arrays of one grid.
+struct GridDev {
+    const float4 *rel;       // FP32 offset from the cell centre (.w unused = 0)
+    const uint16_t *cx;      // x cell index per point
+    const double4_32a *xw;       // FP64 canonical coordinates, .w = weight (1 if none)
+    const int *cell_start;   // ncell + 1
+    int n;
+};
+
+// One counting task: blocks of i-points of gi against the stencil of gj,
+// accumulated into histogram `hist`.
+struct TaskDev {
+    GridDev gi, gj;
+    int hist;
+    int is_auto;
+};
+
+// A block of consecutive i-points inside one cell.
+struct Block {
+    int task, cell, start, count;
+};
+
+struct Geom {
+    int ng[3];
+    double c[3];
+    float c32[3];
+    double lo[3];
+    double L[3];
+    double hL[3];
+    int periodic;
+};
+
+// Linear lookup table over [0, T / inv_w): entries T + 2, each
+// {edge (float, NaN = always rescue, +inf = no edge), k_lo (int bits)}.
+struct LutDesc {
+    int off;        // first entry in the concatenated table
+    int T;          // cells (the table has T + 2 entries)
+    float inv_w;    // cells per unit of the binned quantity
+};
+
+struct PairParams {
+    const TaskDev *tasks;
+    const Block *blocks;
+    int *nblocks;            // device scalar
+    int *work_counter;       // device scalar, zeroed per launch
+    Geom g;
+    const int4 *stencil;     // rows {dy, dz, xlo, xhi}
+    int nrows;
+    int mode, los, weighted;
+    int n_a, n_b, nbins;
+    float r2cut;             // FP32 candidate cut on s2
+    const float2 *lut;       // concatenated LUT entries
+    int lut_total;
+    LutDesc la, lb;
+    float eps_a, eps_b;      // rescue bands (s or sigma; pi)
+    float mu_A, mu_B, mu_W;  // mu band = mu_A * (1/s) + mu_B, window mu_W
+    const double *Ea;        // squared edges (device), n_a + 1
+    const double *Eb;        // squared edges (device), n_b + 1
+    unsigned long long *hist;    // [ntask_hist * nbins]
+    double *whist;               // [ntask_hist * nbins] or null
+    uint3 *queue;                // rescue queue {i, j, img | task << 5}
+    unsigned long long *qcount;  // device scalar
+    unsigned long long qcap;
+    unsigned long long *counters;  // [0] candidates, [1] inline rescues
+    int priv;                // 0: one histogram per CTA; 1: one per warp
+    int smem_hist_ok;        // histogram fits in shared memory
+};
+
+// ---------------------------------------------------------------------------
+// error handling (host)
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+pc_status fail(pc_status s, const std::string &msg);
+pc_status cuda_fail(cudaError_t e, const char *what);
+
+// Count of kernel launches issued by the library (host side).
+void note_launch(int n = 1);
+long long launch_count();
+
+#define PC_CUDA(call)                                             \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return ::pc::cuda_fail(e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// launchers implemented in the kernel translation units
+// ---------------------------------------------------------------------------
+cudaError_t launch_pairs_f32(const PairParams &p, int ipt, int grid, size_t smem,
+                             cudaStream_t st);
+cudaError_t launch_pairs_f64(const PairParams &p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_rescue(const PairParams &p, cudaStream_t st);
+size_t pairs_f32_smem(const PairParams &p, int ipt);
+size_t pairs_f64_smem(const PairParams &p);
+int pairs_f32_ctas_per_sm(const PairParams &p, int ipt, size_t smem);
+int pairs_f64_ctas_per_sm(const PairParams &p, size_t smem);
+
+// ---------------------------------------------------------------------------
+// device helpers shared by the FP32 kernel's inline rescue, the rescue
+// kernel and the FP64 kernel: the exact binary64 pair definition.
+// ---------------------------------------------------------------------------
+
+// Number of k in [1, n) with v >= E[k] (E sorted); caller checked range.
+__device__ __forceinline__ int f64_locate(double v, const double *E, int n) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (v >= E[mid]) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Largest j < n with p2 >= M[j] * s2 (the product rounded once, no FMA).
+__device__ __forceinline__ int f64_locate_mu(double p2, double s2, const double *M, int n) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (p2 >= __dmul_rn(M[mid], s2)) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Bin of the pair from binary64 separation d (already wrapped) and, for the
+// midpoint line of sight, the two canonical positions.  -1: outside.
+template <int MODE, int LOS>
+__device__ __forceinline__ int f64_bin_from_d(double d0, double d1, double d2, const double4_32a &a,
+                                              const double4_32a &b, const double *Ea, int na,
+                                              const double *Eb, int nb) {
+    double s2 = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+    if (MODE == MODE_S) {
+        if (!(s2 >= Ea[0] && s2 < Ea[na])) return -1;
+        return f64_locate(s2, Ea, na);
+    }
+    double p2;
+    if (LOS == LOS_Z) {
+        p2 = __dmul_rn(d2, d2);
+    } else {
+        double l0 = __dadd_rn(a.x, b.x), l1 = __dadd_rn(a.y, b.y), l2 = __dadd_rn(a.z, b.z);
+        double sl = __dadd_rn(__dadd_rn(__dmul_rn(d0, l0), __dmul_rn(d1, l1)), __dmul_rn(d2, l2));
+        double ll = __dadd_rn(__dadd_rn(__dmul_rn(l0, l0), __dmul_rn(l1, l1)), __dmul_rn(l2, l2));
+        p2 = (ll > 0.0) ? __ddiv_rn(__dmul_rn(sl, sl), ll) : 0.0;
+    }
+    if (MODE == MODE_SMU) {
+        if (!(s2 >= Ea[0] && s2 < Ea[na])) return -1;
+        int k = f64_locate(s2, Ea, na);
+        int j = (s2 > 0.0) ? f64_locate_mu(p2, s2, Eb, nb) : 0;
+        return k * nb + j;
+    }
+    double q2 = __dsub_rn(s2, p2);
+    if (q2 < 0.0) q2 = 0.0;
+    if (!(q2 >= Ea[0] && q2 < Ea[na])) return -1;
+    if (!(p2 >= Eb[0] && p2 < Eb[nb])) return -1;
+    return f64_locate(q2, Ea, na) * nb + f64_locate(p2, Eb, nb);
+}
+
+// Image code: (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1), s in {-1, 0, 1}: the j
+// point is taken at x_j + s L.  Returns the bin under the binary64 definition
+// if that image is the one the definition's wrap rule selects, -2 if it is a
+// different image (that pair is counted through its own image), -1 outside.
+template <int MODE, int LOS>
+__device__ __forceinline__ int f64_pair_bin(const double4_32a &a, const double4_32a &b, int img,
+                                            const Geom &g, const double *Ea, int na,
+                                            const double *Eb, int nb) {
+    double d0 = __dsub_rn(b.x, a.x);
+    double d1 = __dsub_rn(b.y, a.y);
+    double d2 = __dsub_rn(b.z, a.z);
+    int sx = img / 9 - 1, sy = (img / 3) % 3 - 1, sz = img % 3 - 1;
+    if (g.periodic) {
+        int w0 = (d0 > g.hL[0]) ? -1 : ((d0 < -g.hL[0]) ? 1 : 0);
+        int w1 = (d1 > g.hL[1]) ? -1 : ((d1 < -g.hL[1]) ? 1 : 0);
+        int w2 = (d2 > g.hL[2]) ? -1 : ((d2 < -g.hL[2]) ? 1 : 0);
+        if (w0 != sx || w1 != sy || w2 != sz) return -2;
+        if (w0 < 0) d0 = __dsub_rn(d0, g.L[0]); else if (w0 > 0) d0 = __dadd_rn(d0, g.L[0]);
+        if (w1 < 0) d1 = __dsub_rn(d1, g.L[1]); else if (w1 > 0) d1 = __dadd_rn(d1, g.L[1]);
+        if (w2 < 0) d2 = __dsub_rn(d2, g.L[2]); else if (w2 > 0) d2 = __dadd_rn(d2, g.L[2]);
+    } else if (sx != 0 || sy != 0 || sz != 0) {
+        return -2;
+    }
+    return f64_bin_from_d<MODE, LOS>(d0, d1, d2, a, b, Ea, na, Eb, nb);
+}
+
+// floor(v * inv_w) for v >= 0 without the conversion pipe: one FFMA rounded
+// toward -inf onto the 2^23 grid, then an integer subtract.  NaN/inf give a
+// large index the caller clamps.
+__device__ __forceinline__ int lut_index(float v, float inv_w) {
+    return __float_as_int(__fmaf_rd(v, inv_w, 8388608.0f)) - 0x4B000000;
+}
+
+}  // namespace pc

@@ -1,0 +1,94 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+entry point declared in include/paircount.h, and rejects bad arguments on
+the host (no kernel is launched here)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2301_12557_gb300 as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    P.build()
+    return P.lib()
+
+
+def _declared():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^\s*(?:[\w\s\*]+?)\b(pc_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "pc_build_grid" in names and "pc_count_batch" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(P.EXPORTS) | set(names)
+
+
+def test_binding_covers_the_abi():
+    for n in _declared():
+        assert hasattr(P, n), f"binding lacks {n}"
+
+
+def test_status_strings_and_version(lib):
+    assert P.pc_strerror(P.PC_OK) == "success"
+    assert P.pc_strerror(P.PC_EINVAL) == "invalid argument"
+    assert "sm_103a" in P.pc_version()
+
+
+def test_host_side_argument_checks(lib):
+    box = P.make_box(100.0, True)
+    out = ctypes.c_void_p()
+    # NULL out pointer, negative n, bad r_max: rejected before any CUDA call
+    assert lib.pc_build_grid(None, None, 0, 10, ctypes.byref(box), 10.0, None, None, None) == P.PC_EINVAL
+    assert lib.pc_build_grid(None, None, 0, -1, ctypes.byref(box), 10.0, None, None,
+                             ctypes.byref(out)) == P.PC_EINVAL
+    assert "n < 0" in P.pc_last_error()
+    x = np.zeros((4, 3))
+    assert lib.pc_build_grid(x.ctypes.data, None, 0, 4, ctypes.byref(box), -1.0, None, None,
+                             ctypes.byref(out)) == P.PC_EINVAL
+    assert lib.pc_build_grid(x.ctypes.data, None, 0, 1 << 31, ctypes.byref(box), 1.0, None,
+                             None, ctypes.byref(out)) == P.PC_EOVERFLOW
+    b = P.Bins("s", "z", [0.0, 1.0])
+    assert lib.pc_count_auto(None, ctypes.byref(b.s), None, None, None, None, None) == P.PC_EINVAL
+    assert lib.pc_count_cross(None, None, ctypes.byref(b.s), None, None, None, None, None) == P.PC_EINVAL
+    assert lib.pc_count_batch(None, 0, ctypes.byref(b.s), None, None, None, None, None) == P.PC_EINVAL
+
+
+def test_cost_model_cell_size(lib):
+    R = 200.0
+    c_dense = P.pc_suggest_cell_size(100_000_000, 3000.0 ** 3, R)
+    c_mid = P.pc_suggest_cell_size(2_000_000, 1000.0 ** 3, R)
+    c_sparse = P.pc_suggest_cell_size(20_000, 1000.0 ** 3, R)
+    for c in (c_dense, c_mid, c_sparse):
+        assert R / 16 <= c <= 2 * R
+    # denser catalogues favour smaller cells (Appendix B.1: the N_pair term grows)
+    assert c_dense <= c_mid <= c_sparse
+
+
+def test_bins_helper():
+    b = P.Bins("sigpi", "mid", np.linspace(0, 30, 4), np.linspace(0, 40, 5))
+    assert b.nbins == 12
+    assert abs(b.r_max - 50.0) < 1e-12
+    b = P.Bins("smu", "z", [0, 1, 2], [0, 0.5, 1])
+    assert b.nbins == 4
+    assert b.s.n_a == 2 and b.s.n_b == 2
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(P, "_lib", None)
+    monkeypatch.setattr(P._build, "LIB", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError):
+        P.lib()

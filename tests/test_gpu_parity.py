@@ -1,0 +1,307 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer counts must be bit-identical.  Weighted sums must agree within 1e-10
+relative per bin (exactly where the oracle's bin is zero): the oracle sums
+binary64 products with Neumaier compensation, the GPU sums the same binary64
+products in a different order, so only summation rounding separates them.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import workloads as W
+
+P = pytest.importorskip("paper_2301_12557_gb300")
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+WREL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.build()
+    oracle.build()
+    torch.cuda.init()
+    yield
+
+
+def _check(got, want, gw=None, ww=None, what=""):
+    if not np.array_equal(got, want):
+        bad = np.nonzero(got != want)[0]
+        raise AssertionError(f"{what}: {bad.size} bins differ, first {bad[:8].tolist()}: "
+                             f"gpu {got[bad[:8]].tolist()} oracle {want[bad[:8]].tolist()}")
+    if ww is not None:
+        zero = ww == 0
+        assert np.all(gw[zero] == 0), what
+        rel = np.abs(gw[~zero] - ww[~zero]) / np.abs(ww[~zero])
+        assert rel.size == 0 or rel.max() <= WREL, f"{what}: weighted rel err {rel.max():.3e}"
+
+
+def _both(x1, x2=None, w1=None, w2=None, prec="f32", **kw):
+    got = P.count(x1, x2, w1=w1, w2=w2, prec=prec, **kw)
+    kw2 = {k: v for k, v in kw.items() if k not in ("cell_size", "ipt", "priv",
+                                                      "rescue_capacity")}
+    want = oracle.count(x1, x2, w1=w1, w2=w2, method="grid", **kw2)
+    return got, want
+
+
+MODES = [
+    ("s", "z", None),
+    ("smu", "z", np.linspace(0.0, 1.0, 11)),
+    ("sigpi", "z", np.linspace(0.0, 30.0, 16)),
+]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("mode,los,eb", MODES)
+def test_periodic_auto_clustered(mode, los, eb, prec):
+    L = 150.0
+    x = synth.neyman_scott(6000, 600, 10.0, 2.0, L, 101)
+    ea = np.linspace(0.0, 30.0, 16)
+    (g, _), (w, _) = _both(x, box=L, periodic=True, mode=mode, los=los, edges_a=ea,
+                           edges_b=eb, prec=prec)
+    _check(g, w, what=f"{mode}/{prec}")
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("mode,los,eb", MODES)
+def test_periodic_cross(mode, los, eb, prec):
+    L = 120.0
+    d = synth.neyman_scott(3000, 300, 10.0, 3.0, L, 111)
+    r = synth.uniform_box(4000, L, 112)
+    ea = np.linspace(0.0, 25.0, 11)
+    (g, _), (w, _) = _both(d, r, box=L, periodic=True, mode=mode, los=los, edges_a=ea,
+                           edges_b=eb, prec=prec)
+    _check(g, w, what=f"cross {mode}/{prec}")
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("mode,eb", [("smu", np.linspace(0, 1, 6)),
+                                     ("sigpi", np.linspace(0, 40, 9))])
+def test_survey_midpoint_weighted(mode, eb, prec):
+    d = synth.survey_shell(3000, True, 121)
+    r = synth.survey_shell(6000, False, 122)
+    wd = synth.fkp_weights(d, 3000)
+    wr = synth.fkp_weights(r, 3000)
+    ea = np.linspace(0.0, 40.0, 9)
+    kw = dict(periodic=False, mode=mode, los="mid", edges_a=ea, edges_b=eb)
+    (g, gw), (w, ww) = _both(d, w1=wd, prec=prec, **kw)
+    _check(g, w, gw, ww, f"DD {mode}/{prec}")
+    (g, gw), (w, ww) = _both(d, r, w1=wd, w2=wr, prec=prec, **kw)
+    _check(g, w, gw, ww, f"DR {mode}/{prec}")
+
+
+def test_cross_self_identity_and_symmetry():
+    L = 100.0
+    x = synth.neyman_scott(5000, 500, 10.0, 2.0, L, 131)
+    y = synth.uniform_box(3000, L, 132)
+    ea = np.linspace(0.0, 20.0, 21)
+    mu = np.linspace(0.0, 1.0, 21)
+    kw = dict(box=L, periodic=True, mode="smu", edges_a=ea, edges_b=mu)
+    a, _ = P.count(x, **kw)
+    c, _ = P.count(x, x, **kw)
+    want = 2 * a
+    want[0] += x.shape[0]
+    assert np.array_equal(c, want)
+    dr, _ = P.count(x, y, **kw)
+    rd, _ = P.count(y, x, **kw)
+    assert np.array_equal(dr, rd)
+
+
+def test_near_edge_adversarial():
+    """Pairs placed at bin edges * (1 + tiny): the FP32 decision is within
+    rounding of the edge, so these exercise the binary64 rescue."""
+    L = 400.0
+    ea = np.linspace(0.0, 50.0, 26)
+    offs = [0.0, 2.0 ** -52, -2.0 ** -52, 4 * 2.0 ** -52, -8 * 2.0 ** -52, 1e-9, -1e-9,
+            3e-8, -3e-8, 1e-7, -1e-7, 5e-7, -5e-7, 2e-6, -2e-6, 1e-5, -1e-5]
+    x = synth.catalogs.near_edge_pairs(ea, L, 6000, offs, 141)
+    mu = np.linspace(0.0, 1.0, 41)
+    for mode, eb in (("s", None), ("smu", mu), ("sigpi", np.linspace(0.0, 50.0, 26))):
+        (g, _), (w, _) = _both(x, box=L, periodic=True, mode=mode, edges_a=ea, edges_b=eb)
+        _check(g, w, what=f"near-edge {mode}")
+
+
+def test_lattice_ties_exact():
+    """Integer lattice with integer edges: many exact ties on bin edges."""
+    x = synth.lattice_points(3000, 24, 151)
+    ea = np.arange(0, 11, dtype=np.float64)
+    for mode, eb in (("s", None), ("smu", [0, 0.25, 0.5, 0.75, 1.0]), ("sigpi", np.arange(0, 6.0))):
+        for prec in ("f32", "f64"):
+            (g, _), (w, _) = _both(x, box=24.0, periodic=True, mode=mode, edges_a=ea,
+                                   edges_b=eb, prec=prec)
+            _check(g, w, what=f"lattice {mode}/{prec}")
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 255, 256, 257, 1000])
+def test_small_and_ragged_sizes(n):
+    L = 50.0
+    x = synth.uniform_box(n, L, 161 + n) if n else np.zeros((0, 3))
+    ea = np.linspace(0.0, 10.0, 11)
+    (g, _), (w, _) = _both(x, box=L, periodic=True, mode="smu", edges_a=ea,
+                           edges_b=np.linspace(0, 1, 5))
+    _check(g, w, what=f"n={n}")
+
+
+def test_dense_cell_and_duplicates():
+    """One dense clump (thousands of points in one cell) plus exact duplicates
+    (s = 0 pairs go to bin 0 / mu bin 0)."""
+    L = 100.0
+    rng = np.random.default_rng(171)
+    clump = 50.0 + rng.normal(0, 0.3, size=(3000, 3))
+    dup = np.repeat(rng.random((50, 3)) * L, 3, axis=0)
+    x = np.concatenate([clump, dup, synth.uniform_box(2000, L, 172)])
+    ea = np.linspace(0.0, 12.0, 25)
+    for mode, eb in (("s", None), ("smu", np.linspace(0, 1, 8))):
+        for prec in ("f32", "f64"):
+            (g, _), (w, _) = _both(x, box=L, periodic=True, mode=mode, edges_a=ea, edges_b=eb,
+                                   prec=prec)
+            _check(g, w, what=f"clump {mode}/{prec}")
+
+
+def test_rescue_queue_overflow_goes_inline():
+    L = 80.0
+    x = synth.catalogs.near_edge_pairs(np.linspace(0, 20, 11), L, 3000, [0.0, 1e-7, -1e-7],
+                                       181)
+    ea = np.linspace(0.0, 20.0, 11)
+    for cap in (1, -1):
+        g, _, st = P.count(x, box=L, periodic=True, edges_a=ea, rescue_capacity=cap,
+                           return_stats=True)
+        w, _ = oracle.count(x, box=L, periodic=True, edges_a=ea)
+        _check(g, w, what=f"capacity {cap}")
+        assert st.rescue_inline > 0
+
+
+@pytest.mark.parametrize("cell", [6.0, 9.5, 17.0, 30.0])
+def test_cell_size_does_not_change_counts(cell):
+    L = 200.0
+    x = synth.neyman_scott(8000, 800, 10.0, 3.0, L, 191)
+    ea = np.linspace(0.0, 30.0, 31)
+    mu = np.linspace(0.0, 1.0, 21)
+    want, _ = oracle.count(x, box=L, periodic=True, mode="smu", edges_a=ea, edges_b=mu,
+                           method="grid")
+    for ipt in (1, 2):
+        g, _ = P.count(x, box=L, periodic=True, mode="smu", edges_a=ea, edges_b=mu,
+                       cell_size=cell, ipt=ipt)
+        _check(g, want, what=f"cell {cell} ipt {ipt}")
+
+
+def test_device_tensors_and_device_outputs():
+    L = 100.0
+    x = synth.neyman_scott(4000, 400, 10.0, 2.0, L, 201)
+    ea = np.linspace(0.0, 20.0, 11)
+    xd = torch.from_numpy(x).cuda()
+    bins = P.Bins("s", "z", ea)
+    g = P.pc_build_grid(xd, box=P.make_box(L, True), r_max=bins.r_max)
+    out = torch.zeros(bins.nbins, dtype=torch.int64, device="cuda")
+    P.pc_count_auto(g, bins, counts=out)
+    g.free()
+    want, _ = oracle.count(x, box=L, periodic=True, edges_a=ea)
+    _check(out.cpu().numpy(), want, what="device io")
+
+
+def test_weighted_f32_weights_periodic():
+    L = 150.0
+    x = synth.mixed_box(8000, L, 0.5, 10.0, 3.0, 211)
+    w = synth.lognormal_weights(x.shape[0], 0.3, 212)   # float32
+    ea = np.linspace(0.0, 30.0, 7)
+    for prec in ("f32", "f64"):
+        (g, gw), (o, ow) = _both(x, w1=w, box=L, periodic=True, edges_a=ea, prec=prec)
+        _check(g, o, gw, ow, f"lognormal weights {prec}")
+
+
+def test_batch_matches_per_mock_oracle():
+    mocks = synth.batch_mocks(6, 1500, 4000, 3.0, 8.0, 300.0, 221)
+    ea = np.linspace(0.0, 40.0, 21)
+    mu = np.linspace(0.0, 1.0, 11)
+    bins = P.Bins("smu", "z", ea, mu)
+    box = P.make_box(300.0, True)
+    opts = P.make_opts("f32", 20.0)
+    grids = [P.pc_build_grid(m, box=box, r_max=bins.r_max, opts=opts) for m in mocks]
+    c, _, st = P.pc_count_batch(grids, bins, opts)
+    for g in grids:
+        g.free()
+    c = c.reshape(len(mocks), -1)
+    for k, m in enumerate(mocks):
+        w, _ = oracle.count(m, box=300.0, periodic=True, mode="smu", edges_a=ea, edges_b=mu,
+                            method="grid")
+        _check(c[k], w, what=f"mock {k}")
+
+
+def test_errors_are_reported():
+    L = 100.0
+    x = synth.uniform_box(100, L, 231)
+    with pytest.raises(P.PairCountError):
+        P.count(x, box=L, periodic=True, edges_a=[0.0, 60.0])   # R >= L/2
+    with pytest.raises(P.PairCountError):
+        P.count(x, box=L, periodic=True, edges_a=[0.0, 5.0, 3.0])
+    with pytest.raises(P.PairCountError):
+        P.count(x, box=L, periodic=True, mode="smu", los="mid", edges_a=[0, 5.0],
+                edges_b=[0, 1.0])
+
+
+# --------------------------------------------------------------------------
+# the five workloads
+# --------------------------------------------------------------------------
+
+def test_workload_uniform_n20k_full():
+    w = W.WORKLOADS["uniform_periodic_n20k_s40"]
+    inp = W.make_inputs(w)
+    for prec in ("f32", "f64"):
+        g, _ = P.count(inp["D"], box=w.L, periodic=True, edges_a=w.edges_a, prec=prec)
+        o, _ = oracle.count(inp["D"], box=w.L, periodic=True, edges_a=w.edges_a)
+        _check(g, o, what=f"uniform n20k {prec}")
+
+
+def test_workload_ns_smu_scaled():
+    w = W.WORKLOADS["ns_periodic_n2m_smu40x100"]
+    inp = W.make_inputs(w, scale=0.02)     # 40,000 points, same cluster shape
+    kw = dict(box=w.L, periodic=True, mode="smu", edges_a=w.edges_a, edges_b=w.edges_b)
+    g, _ = P.count(inp["D"], **kw)
+    o, _ = oracle.count(inp["D"], method="grid", **kw)
+    _check(g, o, what="ns smu scaled")
+
+
+def test_workload_survey_scaled_weighted():
+    w = W.WORKLOADS["survey_shell_d1m_r20m_sigpi40x40"]
+    inp = W.make_inputs(w, scale=0.004)    # D 4,000, R 80,000
+    kw = dict(periodic=False, mode="sigpi", los="mid", edges_a=w.edges_a, edges_b=w.edges_b)
+    (g, gw), (o, ow) = _both(inp["D"], w1=inp["wD"], **kw)
+    _check(g, o, gw, ow, "survey DD")
+    (g, gw), (o, ow) = _both(inp["D"], inp["R"], w1=inp["wD"], w2=inp["wR"], **kw)
+    _check(g, o, gw, ow, "survey DR")
+
+
+def test_workload_mixed_weighted_scaled():
+    w = W.WORKLOADS["mixed_periodic_n100m_s40_w"]
+    inp = W.make_inputs(w, scale=0.0015)   # 150,000 points in L = 3000
+    (g, gw), (o, ow) = _both(inp["D"], w1=inp["wD"], box=w.L, periodic=True,
+                             edges_a=w.edges_a)
+    _check(g, o, gw, ow, "mixed weighted")
+
+
+def test_full_size_ns_smu_auto_vs_cross_and_sampled_oracle():
+    """N = 2,000,000 clustered points, (s, mu) 40 x 100, in the launch
+    configuration the benchmark times.  Auto counts are tied to the cross
+    path (cross(D, D) = 2 auto(D) + N self-pairs in bin 0), and the cross
+    path is checked against the oracle on a sampled subset of i-points."""
+    w = W.WORKLOADS["ns_periodic_n2m_smu40x100"]
+    D = W.make_inputs(w)["D"]
+    kw = dict(box=w.L, periodic=True, mode="smu", edges_a=w.edges_a, edges_b=w.edges_b)
+    xd = torch.from_numpy(D).cuda()
+    a, _ = P.count(xd, **kw)
+    c, _ = P.count(xd, xd, **kw)
+    want = 2 * a
+    want[0] += D.shape[0]
+    assert np.array_equal(c, want)
+    idx = np.random.default_rng(7).choice(D.shape[0], 1500, replace=False)
+    S = np.ascontiguousarray(D[idx])
+    g, _ = P.count(S, xd, **kw)
+    o, _ = oracle.count(S, D, method="grid", **kw)
+    _check(g, o, what="sampled cross at full size")
