@@ -87,7 +87,7 @@ typedef struct {
 typedef struct {
     int prec;                    /* pc_prec: FP32 with FP64 rescue (0) or plain FP64 */
     double cell_size;            /* grid cell side; 0 = chosen by the cost model */
-    int ipt;                     /* i-points per thread (1 or 2); 0 = auto */
+    int ipt;                     /* i-points per thread (2 or 4); 0 = auto */
     int priv;                    /* histogram copies per CTA: 0 = one, 1 = one per warp, -1 = auto */
     long long rescue_capacity;   /* rescue-queue slots; 0 = auto; < 0 = none (all inline) */
     int use_graph;               /* pc_count_batch: replay a captured CUDA graph */

@@ -101,6 +101,9 @@ struct Plan {
     float r2cut = 0;
     int fp32_ok = 1;              // error bands usable (else use the FP64 path)
     std::string fp32_why;
+    // evenly spaced edges: bins by floor (see PairParams::lin*)
+    int lin = 0;
+    float lin_invA = 0, lin_offA = 0, lin_thrA = 0, lin_nB = 0, lin_mA = 0, lin_cB = 0;
 };
 
 static bool edges_ok(const double *e, int n, bool zero_one) {
@@ -327,6 +330,42 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
         build_lut(P.ea, false, V, 2.0 * eps_sig, P.lut, P.la);
         build_lut(P.eb, false, V, 2.0 * eps_z, P.lut, P.lb);
     }
+    // ---- evenly spaced edges: floor-based bins ------------------------------
+    // s (and mu along z): bin = floor(t), t = (s - e0) / D, with the band
+    // moved into t units plus the rounding of t itself (scaling factor and
+    // offset rounded to FP32, one FMA) and the edges' distance from exact
+    // even spacing.
+    {
+        const double e0 = P.ea[0], D = (P.ea[P.na] - P.ea[0]) / P.na;
+        double dev = 0.0;
+        for (int k = 0; k <= P.na; ++k) dev = std::max(dev, fabs(P.ea[k] - (e0 + k * D)));
+        bool lin_s = dev <= 1e-9 * D;
+        bool lin_mu = true;
+        double devm = 0.0;
+        if (P.mode == PC_BIN_SMU) {
+            for (int k = 0; k <= P.nb; ++k) devm = std::max(devm, fabs(P.eb[k] - (double)k / P.nb));
+            lin_mu = (P.los == PC_LOS_Z) && devm <= 1e-12;
+        }
+        bool mode_ok = P.mode == PC_BIN_S || (P.mode == PC_BIN_SMU && P.los == PC_LOS_Z);
+        if (lin_s && lin_mu && mode_ok && (P.rcut - e0) / D < 4.0e6) {
+            double ts_max = (P.rcut - e0) / D + 1.0;
+            double eps_t = (eps_s + dev) / D + 4.0 * u * (ts_max + fabs(e0) / D);
+            if (eps_t < 0.25) {
+                P.lin = 1;
+                P.lin_invA = (float)(1.0 / D);
+                P.lin_offA = (float)(-e0 / D);
+                P.lin_thrA = nextafterf((float)(0.5 - eps_t), 0.0f);
+                if (P.mode == PC_BIN_SMU) {
+                    const double nb = P.nb;
+                    P.lin_nB = (float)nb;
+                    P.lin_mA = (float)(muA * nb * (1.0 + 1e-6));
+                    double cB = 0.5 - (muB + 4.0 * u + devm) * nb;
+                    P.lin_cB = nextafterf((float)cB, 0.0f);
+                    if (!(cB > 0.25)) P.lin = 0;
+                }
+            }
+        }
+    }
     // ---- stencil -------------------------------------------------------------
     int kmax[3];
     build_stencil(g, P.rcut, half, P.stencil, kmax);
@@ -370,7 +409,7 @@ static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *o
             (void)t;
     int prec = o.prec;
     if (prec == PC_PREC_F32_RESCUE && !P.fp32_ok) prec = PC_PREC_F64;
-    int ipt = (o.ipt == 1 || o.ipt == 2) ? o.ipt : 2;
+    int ipt = (o.ipt == 4) ? 4 : 2;
     if (prec == PC_PREC_F64) ipt = 1;
     const int bi = NT * ipt;
 
@@ -476,6 +515,13 @@ static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *o
     int copies_warp = P.nbins * (NT / 32) * 4;
     if (o.priv == 0 || o.priv == 1) p.priv = o.priv;
     else p.priv = (P.nbins <= 2048 && copies_warp <= 48 * 1024) ? 1 : 0;
+    p.lin = (prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
+    p.lin_invA = P.lin_invA;
+    p.lin_offA = P.lin_offA;
+    p.lin_thrA = P.lin_thrA;
+    p.lin_nB = P.lin_nB;
+    p.lin_mA = P.lin_mA;
+    p.lin_cB = P.lin_cB;
 
     int dev_sms = 0;
     PC_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev));

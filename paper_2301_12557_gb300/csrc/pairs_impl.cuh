@@ -52,9 +52,9 @@ __host__ __device__ inline SmemLayout smem_layout(const PairParams &p, bool f64)
     o = align_up(o + (size_t)MAXSEG * sizeof(int4), 16);
     int tj = f64 ? TJ64 : TJ;
     L.tile = o;
-    o = align_up(o + (size_t)2 * tj * (f64 ? sizeof(double4_32a) : sizeof(float4)), 16);
+    o = align_up(o + (size_t)2 * tj * (f64 ? sizeof(double4_32a) : 3 * sizeof(float)), 16);
     L.meta = o;
-    o = align_up(o + (size_t)2 * tj * sizeof(int2), 16);
+    if (f64) o = align_up(o + (size_t)2 * tj * sizeof(int2), 16);
     L.tw = o;
     if (p.weighted && !f64) o = align_up(o + (size_t)2 * tj * sizeof(double), 16);
     L.q = o;
@@ -228,34 +228,49 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
 // ---------------------------------------------------------------------------
 // FP32 binning of one in-range candidate
 // ---------------------------------------------------------------------------
+// Binning scalars, read from the kernel parameters once and kept in registers.
+struct BinCtx {
+    const float2 *lutA, *lutB;   // tables in shared memory
+    float invA, invB;            // table cells per unit
+    unsigned TA1, TB1;           // index of each table's sentinel cell
+    float epsA, epsB;            // rescue bands of the two binned quantities
+    float muA, muB, muW;         // mu band = muA / s + muB, table window muW
+    unsigned nA, nB;
+};
+
 struct Bin32 {
     int bin;     // histogram index, valid only if ok
     bool ok;     // falls inside the histogram
     bool near;   // within an error band: needs the binary64 definition
 };
 
-__device__ __forceinline__ void lut_locate(const float2 *lut, const LutDesc &d, float v, int &k,
-                                           float &edge) {
+__device__ __forceinline__ void lut_locate(const float2 *lut, float inv, unsigned t1, float v,
+                                           int &k, float &edge) {
     // v >= 0 by construction; the unsigned clamp also sends any negative
     // index to the always-rescue sentinel cell
-    int t = (int)min((unsigned)lut_index(v, d.inv_w), (unsigned)(d.T + 1));
-    float2 e = lut[d.off + t];
+    unsigned t = min((unsigned)lut_index(v, inv), t1);
+    float2 e = lut[t];
     edge = e.x;
     k = __float_as_int(e.y) + (v >= e.x ? 1 : 0);
 }
 
+// Within eps of the table edge (a NaN edge -- several edges in the cell's
+// window -- always counts as near).
+__device__ __forceinline__ bool is_near(float v, float e, float eps) {
+    return !(fabsf(v - e) >= eps);
+}
+
 template <int MODE, int LOS>
-__device__ __forceinline__ Bin32 bin_f32(const PairParams &p, const float2 *lut, float dx,
-                                         float dy, float dz, float qxy, float s2, float ax_,
-                                         float ay_, float az_) {
+__device__ __forceinline__ Bin32 bin_f32(const BinCtx &c, float dx, float dy, float dz,
+                                         float qxy, float s2, float ax_, float ay_, float az_) {
     Bin32 r;
     if (MODE == MODE_S) {
         float rs = rsqrtf(s2);
         float s = s2 * rs;
         int k; float e;
-        lut_locate(lut, p.la, s, k, e);
-        r.near = !(fabsf(s - e) >= p.eps_a);
-        r.ok = (unsigned)k < (unsigned)p.n_a;
+        lut_locate(c.lutA, c.invA, c.TA1, s, k, e);
+        r.near = is_near(s, e, c.epsA);
+        r.ok = (unsigned)k < c.nA;
         r.bin = k;
         return r;
     }
@@ -265,23 +280,23 @@ __device__ __forceinline__ Bin32 bin_f32(const PairParams &p, const float2 *lut,
             float s = s2 * rs;
             float mu = fabsf(dz) * rs;
             int k, j; float e, em;
-            lut_locate(lut, p.la, s, k, e);
-            lut_locate(lut, p.lb, mu, j, em);
-            float epsm = fmaf(p.mu_A, rs, p.mu_B);
-            r.near = !(fabsf(s - e) >= p.eps_a) || !(fabsf(mu - em) >= epsm) || (epsm > p.mu_W);
-            r.ok = (unsigned)k < (unsigned)p.n_a;
-            r.bin = k * p.n_b + j;
+            lut_locate(c.lutA, c.invA, c.TA1, s, k, e);
+            lut_locate(c.lutB, c.invB, c.TB1, mu, j, em);
+            float epsm = fmaf(c.muA, rs, c.muB);
+            r.near = is_near(s, e, c.epsA) || is_near(mu, em, epsm) || (epsm > c.muW);
+            r.ok = (unsigned)k < c.nA;
+            r.bin = k * (int)c.nB + j;
             return r;
         }
         // (sigma, pi) along z
         float sg = qxy * rsqrtf(qxy);
         float pz = fabsf(dz);
         int k, j; float e, ep;
-        lut_locate(lut, p.la, sg, k, e);
-        lut_locate(lut, p.lb, pz, j, ep);
-        r.near = !(fabsf(sg - e) >= p.eps_a) || !(fabsf(pz - ep) >= p.eps_b);
-        r.ok = ((unsigned)k < (unsigned)p.n_a) && ((unsigned)j < (unsigned)p.n_b);
-        r.bin = k * p.n_b + j;
+        lut_locate(c.lutA, c.invA, c.TA1, sg, k, e);
+        lut_locate(c.lutB, c.invB, c.TB1, pz, j, ep);
+        r.near = is_near(sg, e, c.epsA) || is_near(pz, ep, c.epsB);
+        r.ok = ((unsigned)k < c.nA) && ((unsigned)j < c.nB);
+        r.bin = k * (int)c.nB + j;
         return r;
     }
     // midpoint line of sight: l = 2 x_i + d
@@ -295,12 +310,12 @@ __device__ __forceinline__ Bin32 bin_f32(const PairParams &p, const float2 *lut,
         float s = s2 * rs;
         float mu = pi * rs;
         int k, j; float e, em;
-        lut_locate(lut, p.la, s, k, e);
-        lut_locate(lut, p.lb, mu, j, em);
-        float epsm = fmaf(p.mu_A, rs, p.mu_B);
-        r.near = !(fabsf(s - e) >= p.eps_a) || !(fabsf(mu - em) >= epsm) || (epsm > p.mu_W);
-        r.ok = (unsigned)k < (unsigned)p.n_a;
-        r.bin = k * p.n_b + j;
+        lut_locate(c.lutA, c.invA, c.TA1, s, k, e);
+        lut_locate(c.lutB, c.invB, c.TB1, mu, j, em);
+        float epsm = fmaf(c.muA, rs, c.muB);
+        r.near = is_near(s, e, c.epsA) || is_near(mu, em, epsm) || (epsm > c.muW);
+        r.ok = (unsigned)k < c.nA;
+        r.bin = k * (int)c.nB + j;
         return r;
     }
     // sigma = |d x l| / |l|
@@ -310,19 +325,306 @@ __device__ __forceinline__ Bin32 bin_f32(const PairParams &p, const float2 *lut,
     float cc = fmaf(czp, czp, fmaf(cyp, cyp, cxp * cxp));
     float sg = cc * rsqrtf(cc) * rl;
     int k, j; float e, ep;
-    lut_locate(lut, p.la, sg, k, e);
-    lut_locate(lut, p.lb, pi, j, ep);
-    r.near = !(fabsf(sg - e) >= p.eps_a) || !(fabsf(pi - ep) >= p.eps_b);
-    r.ok = ((unsigned)k < (unsigned)p.n_a) && ((unsigned)j < (unsigned)p.n_b);
-    r.bin = k * p.n_b + j;
+    lut_locate(c.lutA, c.invA, c.TA1, sg, k, e);
+    lut_locate(c.lutB, c.invB, c.TB1, pi, j, ep);
+    r.near = is_near(sg, e, c.epsA) || is_near(pi, ep, c.epsB);
+    r.ok = ((unsigned)k < c.nA) && ((unsigned)j < c.nB);
+    r.bin = k * (int)c.nB + j;
     return r;
+}
+
+// Evenly spaced s bins (and mu bins for (s, mu) along z): bin = floor of a
+// scaled value; the pair is near an edge when that value's fractional part
+// is within the band of 0 or 1.
+struct LinCtx {
+    float invA, offA, thrA;   // s scaling and band threshold
+    float nB, mA, cB;         // mu scaling and per-pair band threshold
+    unsigned nA, nB_u;
+};
+
+// floor(t) for t in [-2^22, 2^23): the sum rounded toward -inf onto the
+// 2^23 grid; also returns floor(t) as a float
+__device__ __forceinline__ float floor_grid(float t, float &fl) {
+    float f = __fadd_rd(t, 8388608.0f);
+    fl = f - 8388608.0f;
+    return f;
+}
+
+template <int MODE>
+__device__ __forceinline__ Bin32 bin_lin(const LinCtx &c, float dz, float s2) {
+    Bin32 r;
+    const float rs = rsqrtf(s2);
+    const float s = s2 * rs;
+    const float ts = fmaf(s, c.invA, c.offA);
+    float fls;
+    const float fs = floor_grid(ts, fls);
+    const int k = __float_as_int(fs) - 0x4B000000;
+    // NaN (coincident points: s2 = 0) compares false, so it is near
+    bool near = !(fabsf((ts - fls) - 0.5f) < c.thrA);
+    r.ok = (unsigned)k < c.nA;
+    if (MODE == MODE_S) {
+        r.near = near;
+        r.bin = k;
+        return r;
+    }
+    const float tm = fabsf(dz) * rs * c.nB;
+    float flm;
+    const float fm = floor_grid(tm, flm);
+    const int j = min(__float_as_int(fm) - 0x4B000000, (int)c.nB_u - 1);
+    near = near || !(fabsf((tm - flm) - 0.5f) < fmaf(-c.mA, rs, c.cB));
+    r.near = near;
+    r.bin = k * (int)c.nB_u + j;
+    return r;
+}
+
+// Shared-memory reduction at a 32-bit shared-window address, issued only
+// when `on` is set (one predicated instruction, no branch).
+__device__ __forceinline__ void red_shared_u32_if(unsigned addr, bool on) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}"
+        ::"r"(addr), "r"((unsigned)on));
+}
+__device__ __forceinline__ void red_shared_f64_if(unsigned addr, double v, bool on) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p red.shared.add.f64 [%0], %1;\n\t}"
+        ::"r"(addr), "d"(v), "r"((unsigned)on));
+}
+
+// Rare path: stage one near-edge pair for the binary64 rescue.
+template <int MODE, int LOS>
+__device__ __noinline__ void rescue_push(const PairParams &p, uint3 *s_q, int *s_qn,
+                                         const int4 *s_seg, int nseg, int f0, int jj,
+                                         int bstart, int i, unsigned task_bits) {
+    int jidx, img;
+    if (f0 < 0) {
+        jidx = bstart + jj;
+        img = 13;
+    } else {
+        int f = f0 + jj;
+        int4 sg = s_seg[seg_find(s_seg, nseg, f)];
+        jidx = sg.x + (f - sg.y);
+        img = sg.w;
+    }
+    push_rescue<MODE, LOS>(p, s_q, s_qn,
+                           make_uint3((unsigned)i, (unsigned)jidx, (unsigned)img | task_bits));
+}
+
+// Everything the inner loop needs, in registers.
+template <int RI>
+struct IPts {
+    float x[RI], y[RI], z[RI];     // offsets from the i-cell centre (far away if unused)
+    float xa[RI], ya[RI], za[RI];  // absolute positions (midpoint line of sight)
+    double w[RI];
+    int idx[RI];
+};
+
+// A staged tile of j-points (structure of arrays, even length, shifted into
+// the i-cell's frame).
+struct Tile {
+    const float *x, *y, *z;
+    const double *w;
+};
+
+// Table-based bins, one pair at a time (every mode and line of sight).
+// MASK: the tile holds the block's own points and only pairs j > i count.
+template <int MODE, int LOS, bool W, int RI, bool MASK>
+__device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int len,
+                                              const IPts<RI> &I, const BinCtx &bc, float r2cut,
+                                              unsigned hist_sa, unsigned whist_sa, uint3 *s_q,
+                                              int *s_qn, const int4 *s_seg, int nseg, int f0,
+                                              int bstart, unsigned task_bits) {
+#pragma unroll 2
+    for (int jj = 0; jj < len; ++jj) {
+        const float qx = tb.x[jj], qy = tb.y[jj], qz = tb.z[jj];
+        float dxv[RI], dyv[RI], dzv[RI], qv[RI], s2v[RI];
+        bool inr[RI];
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            dxv[r] = qx - I.x[r];
+            dyv[r] = qy - I.y[r];
+            dzv[r] = qz - I.z[r];
+            qv[r] = fmaf(dyv[r], dyv[r], dxv[r] * dxv[r]);
+            s2v[r] = fmaf(dzv[r], dzv[r], qv[r]);
+            inr[r] = s2v[r] < r2cut;
+            if (MASK) inr[r] = inr[r] && (bstart + jj > I.idx[r]);
+            any = any || inr[r];
+        }
+        if (__any_sync(0xffffffffu, any)) {
+            double wj = 0.0;
+            if (W) wj = tb.w[jj];
+            bool resc[RI];
+            bool anyr = false;
+#pragma unroll
+            for (int r = 0; r < RI; ++r) {
+                Bin32 b = bin_f32<MODE, LOS>(bc, dxv[r], dyv[r], dzv[r], qv[r], s2v[r], I.xa[r],
+                                             I.ya[r], I.za[r]);
+                const bool add = inr[r] && b.ok && !b.near;
+                red_shared_u32_if(hist_sa + 4u * (unsigned)b.bin, add);
+                if (W) red_shared_f64_if(whist_sa + 8u * (unsigned)b.bin, __dmul_rn(I.w[r], wj), add);
+                resc[r] = inr[r] && b.near;
+                anyr = anyr || resc[r];
+            }
+            if (__any_sync(0xffffffffu, anyr)) {
+#pragma unroll
+                for (int r = 0; r < RI; ++r)
+                    if (resc[r])
+                        rescue_push<MODE, LOS>(p, s_q, s_qn, s_seg, nseg, f0, jj, bstart, I.idx[r],
+                                               task_bits);
+            }
+        }
+    }
+}
+
+// Evenly spaced bins, two j-points per step in packed FP32 (s, and (s, mu)
+// along z).  For each pair: t_s = (s - e0) / D, bin = floor(t_s); the pair
+// is near an edge unless |frac(t_s) - 1/2| < thrA; mu likewise with its
+// per-pair band.  Histogram addresses are formed from the float bits of
+// floor(t) + 2^23, with the 2^23 bias folded into the base address.
+template <int MODE, bool W, int RI, bool MASK>
+__device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int len,
+                                               const IPts<RI> &I, const LinCtx &lc, float r2cut,
+                                               unsigned hist_sa, unsigned whist_sa, uint3 *s_q,
+                                               int *s_qn, const int4 *s_seg, int nseg, int f0,
+                                               int bstart, unsigned task_bits) {
+    const float2 C23 = make_float2(8388608.0f, 8388608.0f);
+    const float2 NC23H = make_float2(-8388608.0f + 0.5f, -8388608.0f + 0.5f);
+    const float2 M1 = make_float2(-1.0f, -1.0f);
+    const float2 INVA = make_float2(lc.invA, lc.invA);
+    const float2 OFFA = make_float2(lc.offA, lc.offA);
+    const float2 NB = make_float2(lc.nB, lc.nB);
+    const float2 NMA = make_float2(-lc.mA, -lc.mA);
+    const float2 CB = make_float2(lc.cB, lc.cB);
+    const float halfA = 0.5f * (float)lc.nA;
+    const float2 NHALFA = make_float2(-halfA, -halfA);
+    const float thrA = lc.thrA;
+    const int nb1 = (int)lc.nB_u - 1;
+    const unsigned nbu = (MODE == MODE_SMU) ? lc.nB_u : 1u;
+    // bias of the float bits of floor(t_s) + 2^23, folded into the bases
+    const unsigned bias = 0x4B000000u * nbu;
+    const unsigned hbase = hist_sa - 4u * bias;
+    const unsigned wbase = whist_sa - 8u * bias;
+    float2 NX[RI], NY[RI], NZ[RI];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        NX[r] = make_float2(-I.x[r], -I.x[r]);
+        NY[r] = make_float2(-I.y[r], -I.y[r]);
+        NZ[r] = make_float2(-I.z[r], -I.z[r]);
+    }
+#pragma unroll 1
+    for (int jj = 0; jj < len; jj += 2) {
+        const float2 X = *reinterpret_cast<const float2 *>(tb.x + jj);
+        const float2 Y = *reinterpret_cast<const float2 *>(tb.y + jj);
+        const float2 Z = *reinterpret_cast<const float2 *>(tb.z + jj);
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const float2 dx = __fadd2_rn(X, NX[r]);
+            const float2 dy = __fadd2_rn(Y, NY[r]);
+            const float2 dz = __fadd2_rn(Z, NZ[r]);
+            const float2 s2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            bool i0 = s2.x < r2cut, i1 = s2.y < r2cut;
+            if (MASK) {
+                i0 = i0 && (bstart + jj > I.idx[r]);
+                i1 = i1 && (bstart + jj + 1 > I.idx[r]);
+            }
+            if (__any_sync(0xffffffffu, i0 || i1)) {
+                const float2 rs = make_float2(rsqrtf(s2.x), rsqrtf(s2.y));
+                const float2 ts = __ffma2_rn(__fmul2_rn(s2, rs), INVA, OFFA);
+                const float2 f = __fadd2_rd(ts, C23);
+                const float2 d = __ffma2_rn(__fadd2_rn(f, NC23H), M1, ts);   // frac - 1/2
+                const float2 o = __fadd2_rn(ts, NHALFA);
+                const bool ok0 = fabsf(o.x) < halfA, ok1 = fabsf(o.y) < halfA;
+                // NaN (s2 = 0) compares false: such pairs are near
+                bool n0 = !(fabsf(d.x) < thrA), n1 = !(fabsf(d.y) < thrA);
+                unsigned b0 = (unsigned)__float_as_int(f.x), b1 = (unsigned)__float_as_int(f.y);
+                if (MODE == MODE_SMU) {
+                    const float2 adz = make_float2(fabsf(dz.x), fabsf(dz.y));
+                    const float2 tm = __fmul2_rn(adz, __fmul2_rn(rs, NB));
+                    const float2 fm = __fadd2_rd(tm, C23);
+                    const float2 dm = __ffma2_rn(__fadd2_rn(fm, NC23H), M1, tm);
+                    const float2 thm = __ffma2_rn(NMA, rs, CB);
+                    n0 = n0 || !(fabsf(dm.x) < thm.x);
+                    n1 = n1 || !(fabsf(dm.y) < thm.y);
+                    const int j0 = min(__float_as_int(fm.x) - 0x4B000000, nb1);
+                    const int j1 = min(__float_as_int(fm.y) - 0x4B000000, nb1);
+                    b0 = b0 * nbu + (unsigned)j0;
+                    b1 = b1 * nbu + (unsigned)j1;
+                }
+                const bool a0 = i0 && ok0 && !n0, a1 = i1 && ok1 && !n1;
+                red_shared_u32_if(hbase + 4u * b0, a0);
+                red_shared_u32_if(hbase + 4u * b1, a1);
+                if (W) {
+                    const double2 wj = *reinterpret_cast<const double2 *>(tb.w + jj);
+                    red_shared_f64_if(wbase + 8u * b0, __dmul_rn(I.w[r], wj.x), a0);
+                    red_shared_f64_if(wbase + 8u * b1, __dmul_rn(I.w[r], wj.y), a1);
+                }
+                const bool r0 = i0 && n0, r1 = i1 && n1;
+                if (__any_sync(0xffffffffu, r0 || r1)) {
+                    if (r0)
+                        rescue_push<MODE, LOS_Z>(p, s_q, s_qn, s_seg, nseg, f0, jj, bstart,
+                                                 I.idx[r], task_bits);
+                    if (r1)
+                        rescue_push<MODE, LOS_Z>(p, s_q, s_qn, s_seg, nseg, f0, jj + 1, bstart,
+                                                 I.idx[r], task_bits);
+                }
+            }
+        }
+    }
+}
+
+// Global-histogram variant for histograms too large for shared memory.
+template <int MODE, int LOS, bool W, int RI, bool MASK>
+__device__ __forceinline__ void pair_tile_global(const PairParams &p, Tile tb, int len,
+                                                 const IPts<RI> &I, const BinCtx &bc, float r2cut,
+                                                 size_t hbase, uint3 *s_q, int *s_qn,
+                                                 const int4 *s_seg, int nseg, int f0, int bstart,
+                                                 unsigned task_bits) {
+    for (int jj = 0; jj < len; ++jj) {
+        const float qx = tb.x[jj], qy = tb.y[jj], qz = tb.z[jj];
+        for (int r = 0; r < RI; ++r) {
+            float dx = qx - I.x[r], dy = qy - I.y[r], dz = qz - I.z[r];
+            float qxy = fmaf(dy, dy, dx * dx);
+            float s2 = fmaf(dz, dz, qxy);
+            bool inr = s2 < r2cut;
+            if (MASK) inr = inr && (bstart + jj > I.idx[r]);
+            if (!inr) continue;
+            Bin32 b = bin_f32<MODE, LOS>(bc, dx, dy, dz, qxy, s2, I.xa[r], I.ya[r], I.za[r]);
+            if (b.near) {
+                rescue_push<MODE, LOS>(p, s_q, s_qn, s_seg, nseg, f0, jj, bstart, I.idx[r],
+                                       task_bits);
+            } else if (b.ok) {
+                atomicAdd(p.hist + hbase + b.bin, 1ull);
+                if (W) atomicAdd(p.whist + hbase + b.bin, __dmul_rn(I.w[r], tb.w[jj]));
+            }
+        }
+    }
+}
+
+// One tile through the variant that applies.
+template <int MODE, int LOS, bool W, int RI, bool LIN, bool MASK>
+__device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, Tile tb, int len,
+                                          const IPts<RI> &I, const BinCtx &bc, const LinCtx &lc,
+                                          float r2cut, unsigned hist_sa, unsigned whist_sa,
+                                          size_t hbase, uint3 *s_q, int *s_qn, const int4 *s_seg,
+                                          int nseg, int f0, int bstart, unsigned task_bits) {
+    if (!smem_hist) {
+        pair_tile_global<MODE, LOS, W, RI, MASK>(p, tb, len, I, bc, r2cut, hbase, s_q, s_qn, s_seg,
+                                                 nseg, f0, bstart, task_bits);
+    } else if (LIN) {
+        pair_tile_lin2<MODE, W, RI, MASK>(p, tb, len, I, lc, r2cut, hist_sa, whist_sa, s_q, s_qn,
+                                          s_seg, nseg, f0, bstart, task_bits);
+    } else {
+        pair_tile_lut<MODE, LOS, W, RI, MASK>(p, tb, len, I, bc, r2cut, hist_sa, whist_sa, s_q,
+                                              s_qn, s_seg, nseg, f0, bstart, task_bits);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // FP32 kernel
 // ---------------------------------------------------------------------------
-template <int MODE, int LOS, bool W, int RI>
-__global__ void __launch_bounds__(NT) k_pairs_f32(const PairParams p) {
+template <int MODE, int LOS, bool W, int RI, bool LIN>
+__global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
+    k_pairs_f32(const __grid_constant__ PairParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ CtaShared cs;
     __shared__ int s_tmp[8];
@@ -333,22 +635,53 @@ __global__ void __launch_bounds__(NT) k_pairs_f32(const PairParams p) {
     int *s_hist = (int *)(smem + Ly.hist);
     double *s_whist = (double *)(smem + Ly.whist);
     int4 *s_seg = (int4 *)(smem + Ly.seg);
-    float4 *s_tile = (float4 *)(smem + Ly.tile);
-    int2 *s_meta = (int2 *)(smem + Ly.meta);
+    float *s_tx = (float *)(smem + Ly.tile);     // [2][TJ] each
+    float *s_ty = s_tx + 2 * TJ;
+    float *s_tz = s_ty + 2 * TJ;
     double *s_tw = (double *)(smem + Ly.tw);
     uint3 *s_q = (uint3 *)(smem + Ly.q);
 
     const int tid = threadIdx.x;
     for (int k = tid; k < p.lut_total; k += NT) s_lut[k] = p.lut[k];
-    if (p.smem_hist_ok) {
+    const int nbins = p.nbins;
+    const bool smem_hist = p.smem_hist_ok != 0;
+    if (smem_hist) {
         const int copies = p.priv ? NT / 32 : 1;
-        for (int k = tid; k < p.nbins * copies; k += NT) s_hist[k] = 0;
-        if (W) for (int k = tid; k < p.nbins; k += NT) s_whist[k] = 0.0;
+        for (int k = tid; k < nbins * copies; k += NT) s_hist[k] = 0;
+        if (W) for (int k = tid; k < nbins; k += NT) s_whist[k] = 0.0;
     }
     if (tid == 0) cs.qn = 0;
-    int *my_hist = s_hist + (p.priv ? (tid >> 5) * p.nbins : 0);
+
+    BinCtx bc;
+    bc.lutA = s_lut + p.la.off;
+    bc.lutB = s_lut + p.lb.off;
+    bc.invA = p.la.inv_w;
+    bc.invB = p.lb.inv_w;
+    bc.TA1 = (unsigned)(p.la.T + 1);
+    bc.TB1 = (unsigned)(p.lb.T + 1);
+    bc.epsA = p.eps_a;
+    bc.epsB = p.eps_b;
+    bc.muA = p.mu_A;
+    bc.muB = p.mu_B;
+    bc.muW = p.mu_W;
+    bc.nA = (unsigned)p.n_a;
+    bc.nB = (unsigned)p.n_b;
+    LinCtx lc;
+    lc.invA = p.lin_invA;
+    lc.offA = p.lin_offA;
+    lc.thrA = p.lin_thrA;
+    lc.nB = p.lin_nB;
+    lc.mA = p.lin_mA;
+    lc.cB = p.lin_cB;
+    lc.nA = (unsigned)p.n_a;
+    lc.nB_u = (unsigned)p.n_b;
+    const float r2cut = p.r2cut;
+    const unsigned hist_sa = (unsigned)__cvta_generic_to_shared(s_hist) +
+                             (p.priv ? (unsigned)((tid >> 5) * nbins * 4) : 0u);
+    const unsigned whist_sa = (unsigned)__cvta_generic_to_shared(s_whist);
 
     const int nx = p.g.ng[0], ny = p.g.ng[1];
+    const float c32x = p.g.c32[0], c32y = p.g.c32[1], c32z = p.g.c32[2];
     const int nblocks = *p.nblocks;
     unsigned long long cand_local = 0;    // thread 0 only
     unsigned long long since_flush = 0;   // CTA-uniform
@@ -367,78 +700,47 @@ __global__ void __launch_bounds__(NT) k_pairs_f32(const PairParams p) {
             cur_hist = T.hist;
             since_flush = 0;
         }
-        const size_t hbase = (size_t)T.hist * p.nbins;
+        const size_t hbase = (size_t)T.hist * nbins;
+        const unsigned task_bits = (unsigned)B.task << 5;
         const int ax = B.cell % nx, ay = (B.cell / nx) % ny, az = B.cell / (nx * ny);
 
-        // i-points in registers
-        float xi[RI], yi[RI], zi[RI], xa[RI], ya[RI], za[RI];
-        double wi[RI];
-        int ii[RI];
+        IPts<RI> I;
 #pragma unroll
         for (int r = 0; r < RI; ++r) {
             const int loc = tid + r * NT;
-            ii[r] = B.start + loc;
-            xa[r] = ya[r] = za[r] = 0.f;
-            wi[r] = 0.0;
+            I.idx[r] = B.start + loc;
+            I.xa[r] = I.ya[r] = I.za[r] = 0.f;
+            I.w[r] = 0.0;
+            I.x[r] = I.y[r] = I.z[r] = -1.0e18f;  // unused lane: far from every j (and from the +1e18 pad slot)
             if (loc < B.count) {
-                float4 q = T.gi.rel[ii[r]];
-                xi[r] = q.x; yi[r] = q.y; zi[r] = q.z;
+                float4 q = T.gi.rel[I.idx[r]];
+                I.x[r] = q.x; I.y[r] = q.y; I.z[r] = q.z;
                 if (LOS == LOS_MID || W) {
-                    double4_32a a = T.gi.xw[ii[r]];
-                    xa[r] = (float)a.x; ya[r] = (float)a.y; za[r] = (float)a.z;
-                    wi[r] = a.w;
+                    double4_32a a = T.gi.xw[I.idx[r]];
+                    I.xa[r] = (float)a.x; I.ya[r] = (float)a.y; I.za[r] = (float)a.z;
+                    I.w[r] = a.w;
                 }
-            } else {
-                xi[r] = yi[r] = zi[r] = 1.0e18f;   // never within range
             }
         }
 
-        // one candidate pair (i-point r, staged j-point qj); the j metadata
-        // is read only when the pair needs the binary64 definition
-        auto count_pair = [&](int r, const float4 &qj, const int2 *mj, const double *wj) {
-            float dx = qj.x - xi[r], dy = qj.y - yi[r], dz = qj.z - zi[r];
-            float qxy = fmaf(dy, dy, dx * dx);
-            float s2 = fmaf(dz, dz, qxy);
-            if (s2 < p.r2cut) {
-                Bin32 b = bin_f32<MODE, LOS>(p, s_lut, dx, dy, dz, qxy, s2, xa[r], ya[r], za[r]);
-                if (!b.near) {
-                    if (b.ok) {
-                        if (p.smem_hist_ok) {
-                            atomicAdd(&my_hist[b.bin], 1);
-                            if (W) atomicAdd(&s_whist[b.bin], __dmul_rn(wi[r], *wj));
-                        } else {
-                            atomicAdd(&p.hist[hbase + b.bin], 1ull);
-                            if (W) atomicAdd(&p.whist[hbase + b.bin], __dmul_rn(wi[r], *wj));
-                        }
-                    }
-                } else {
-                    int2 m = *mj;
-                    push_rescue<MODE, LOS>(p, s_q, &cs.qn,
-                                           make_uint3((unsigned)ii[r], (unsigned)m.x,
-                                                      (unsigned)m.y | ((unsigned)B.task << 5)));
-                }
-            }
-        };
-
         // ---- phase A (auto): pairs inside the block, j > i ------------------
         if (T.is_auto) {
-            float4 *tb = s_tile;
-            int2 *mb = s_meta;
-            for (int f = tid; f < B.count; f += NT) {
-                int pj = B.start + f;
-                float4 q = T.gj.rel[pj];
-                tb[f] = make_float4(q.x, q.y, q.z, 0.f);
-                mb[f] = make_int2(pj, 13);
-                if (W) s_tw[f] = T.gj.xw[pj].w;
+            const int lenA = (B.count + 1) & ~1;    // even; the pad slot is far away
+            for (int f = tid; f < lenA; f += NT) {
+                if (f < B.count) {
+                    int pj = B.start + f;
+                    float4 q = T.gj.rel[pj];
+                    s_tx[f] = q.x; s_ty[f] = q.y; s_tz[f] = q.z;
+                    if (W) s_tw[f] = T.gj.xw[pj].w;
+                } else {
+                    s_tx[f] = s_ty[f] = s_tz[f] = 1.0e18f;
+                    if (W) s_tw[f] = 0.0;
+                }
             }
             __syncthreads();
-            for (int jj = 0; jj < B.count; ++jj) {
-                float4 qj = tb[jj];
-                const int jidx = B.start + jj;
-#pragma unroll
-                for (int r = 0; r < RI; ++r)
-                    if (jidx > ii[r]) count_pair(r, qj, mb + jj, s_tw + jj);
-            }
+            pair_tile<MODE, LOS, W, RI, LIN, true>(p, smem_hist, Tile{s_tx, s_ty, s_tz, s_tw}, lenA,
+                                                   I, bc, lc, r2cut, hist_sa, whist_sa, hbase, s_q,
+                                                   &cs.qn, s_seg, 0, -1, B.start, task_bits);
             if (tid == 0) cand_local += (unsigned long long)B.count * (B.count - 1) / 2;
             since_flush += (unsigned long long)B.count * B.count;
             __syncthreads();
@@ -468,43 +770,49 @@ __global__ void __launch_bounds__(NT) k_pairs_f32(const PairParams p) {
             // staging registers (TJ / NT slots per thread)
             constexpr int SPT = TJ / NT;
             float4 rq[SPT];
-            int2 rm[SPT];
             double rw[SPT];
-            int rcx[SPT], rmeta[SPT];
+            int rcx[SPT], rmeta[SPT], rimg[SPT];
+            bool rv[SPT];
             auto load_tile = [&](int t) {
 #pragma unroll
                 for (int s = 0; s < SPT; ++s) {
                     int f = t * TJ + tid + s * NT;
-                    rm[s].x = -1;
-                    if (f < total) {
-                        int k = seg_find(s_seg, nseg, f);
-                        int4 sg = s_seg[k];
+                    rv[s] = f < total;
+                    if (rv[s]) {
+                        int4 sg = s_seg[seg_find(s_seg, nseg, f)];
                         int pj = sg.x + (f - sg.y);
                         rq[s] = T.gj.rel[pj];
                         rcx[s] = T.gj.cx[pj];
                         rmeta[s] = sg.z;
-                        rm[s] = make_int2(pj, sg.w);
+                        rimg[s] = sg.w;
                         if (W) rw[s] = T.gj.xw[pj].w;
                     }
                 }
             };
-            auto store_tile = [&](int buf) {
+            auto store_tile = [&](int t) {
+                const int buf = t & 1;
+                const int len = min(TJ, total - t * TJ);
 #pragma unroll
                 for (int s = 0; s < SPT; ++s) {
-                    if (rm[s].x < 0) continue;
-                    int slot = tid + s * NT;
-                    int wrapx = rm[s].y / 9 - 1;
-                    int dxc = rcx[s] - ax + wrapx * nx;
-                    int dyc = (int)(short)(rmeta[s] & 0xFFFF);
-                    int dzc = rmeta[s] >> 16;
-                    float4 v;
-                    v.x = fmaf((float)dxc, p.g.c32[0], rq[s].x);
-                    v.y = fmaf((float)dyc, p.g.c32[1], rq[s].y);
-                    v.z = fmaf((float)dzc, p.g.c32[2], rq[s].z);
-                    v.w = 0.f;
-                    s_tile[buf * TJ + slot] = v;
-                    s_meta[buf * TJ + slot] = rm[s];
-                    if (W) s_tw[buf * TJ + slot] = rw[s];
+                    const int slot = tid + s * NT;
+                    float x = 1.0e18f, y = 1.0e18f, z = 1.0e18f;   // pad slot
+                    double wv = 0.0;
+                    if (rv[s]) {
+                        int wrapx = rimg[s] / 9 - 1;
+                        int dxc = rcx[s] - ax + wrapx * nx;
+                        int dyc = (int)(short)(rmeta[s] & 0xFFFF);
+                        int dzc = rmeta[s] >> 16;
+                        x = fmaf((float)dxc, c32x, rq[s].x);
+                        y = fmaf((float)dyc, c32y, rq[s].y);
+                        z = fmaf((float)dzc, c32z, rq[s].z);
+                        wv = rw[s];
+                    } else if (slot != len) {
+                        continue;
+                    }
+                    s_tx[buf * TJ + slot] = x;
+                    s_ty[buf * TJ + slot] = y;
+                    s_tz[buf * TJ + slot] = z;
+                    if (W) s_tw[buf * TJ + slot] = wv;
                 }
             };
 
@@ -515,18 +823,13 @@ __global__ void __launch_bounds__(NT) k_pairs_f32(const PairParams p) {
                 const int buf = t & 1;
                 const int len = min(TJ, total - t * TJ);
                 if (t + 1 < ntiles) load_tile(t + 1);
-                const float4 *tb = s_tile + buf * TJ;
-                const int2 *mb = s_meta + buf * TJ;
-                const double *wb = s_tw + buf * TJ;
-#pragma unroll 2
-                for (int jj = 0; jj < len; ++jj) {
-                    float4 qj = tb[jj];
-#pragma unroll
-                    for (int r = 0; r < RI; ++r) count_pair(r, qj, mb + jj, wb + jj);
-                }
+                pair_tile<MODE, LOS, W, RI, LIN, false>(
+                    p, smem_hist, Tile{s_tx + buf * TJ, s_ty + buf * TJ, s_tz + buf * TJ, s_tw + buf * TJ},
+                    (len + 1) & ~1, I, bc, lc, r2cut, hist_sa, whist_sa, hbase, s_q, &cs.qn, s_seg,
+                    nseg, t * TJ, B.start, task_bits);
                 if (tid == 0) cand_local += (unsigned long long)len * B.count;
                 since_flush += (unsigned long long)len * B.count;
-                if (t + 1 < ntiles) store_tile(buf ^ 1);
+                if (t + 1 < ntiles) store_tile(t + 1);
                 __syncthreads();
                 if (cs.qn >= LQ / 2) drain_rescue<MODE, LOS>(p, s_q, cs, &s_base);
                 if (since_flush > FLUSH_LIMIT) {
@@ -548,7 +851,7 @@ __global__ void __launch_bounds__(NT) k_pairs_f32(const PairParams p) {
 // plain FP64 kernel: the binary64 definition for every candidate pair
 // ---------------------------------------------------------------------------
 template <int MODE, int LOS, bool W>
-__global__ void __launch_bounds__(NT) k_pairs_f64(const PairParams p) {
+__global__ void __launch_bounds__(NT) k_pairs_f64(const __grid_constant__ PairParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ CtaShared cs;
     __shared__ int s_tmp[8];
@@ -670,7 +973,7 @@ __global__ void __launch_bounds__(NT) k_pairs_f64(const PairParams p) {
 // rescue kernel: binary64 definition for every queued pair
 // ---------------------------------------------------------------------------
 template <int MODE, int LOS>
-__global__ void __launch_bounds__(256) k_rescue(const PairParams p) {
+__global__ void __launch_bounds__(256) k_rescue(const __grid_constant__ PairParams p) {
     const unsigned long long n = min(*p.qcount, p.qcap);
     for (unsigned long long k = blockIdx.x * 256ull + threadIdx.x; k < n;
          k += (unsigned long long)gridDim.x * 256ull) {
@@ -692,10 +995,25 @@ __global__ void __launch_bounds__(256) k_rescue(const PairParams p) {
 // instantiation helpers
 // ---------------------------------------------------------------------------
 template <int MODE, int LOS>
+using PairKernel = void (*)(PairParams);
+
+// Kernel variant for (weighted, i-points per thread, linear bins).  Linear
+// bins are specialised only where they apply: s, and (s, mu) along z.
+template <int MODE, int LOS>
+PairKernel<MODE, LOS> pick_f32(const PairParams &p, int ipt) {
+    constexpr bool LINOK = (MODE == MODE_S) || (MODE == MODE_SMU && LOS == LOS_Z);
+    const bool lin = LINOK && p.lin;
+    if (p.weighted) {
+        if (ipt == 4) return lin ? k_pairs_f32<MODE, LOS, true, 4, LINOK> : k_pairs_f32<MODE, LOS, true, 4, false>;
+        return lin ? k_pairs_f32<MODE, LOS, true, 2, LINOK> : k_pairs_f32<MODE, LOS, true, 2, false>;
+    }
+    if (ipt == 4) return lin ? k_pairs_f32<MODE, LOS, false, 4, LINOK> : k_pairs_f32<MODE, LOS, false, 4, false>;
+    return lin ? k_pairs_f32<MODE, LOS, false, 2, LINOK> : k_pairs_f32<MODE, LOS, false, 2, false>;
+}
+
+template <int MODE, int LOS>
 cudaError_t launch_mode_f32(const PairParams &p, int ipt, int grid, size_t smem, cudaStream_t st) {
-    void (*k)(PairParams);
-    if (p.weighted) k = (ipt == 2) ? k_pairs_f32<MODE, LOS, true, 2> : k_pairs_f32<MODE, LOS, true, 1>;
-    else k = (ipt == 2) ? k_pairs_f32<MODE, LOS, false, 2> : k_pairs_f32<MODE, LOS, false, 1>;
+    PairKernel<MODE, LOS> k = pick_f32<MODE, LOS>(p, ipt);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) return cudaSuccess;
@@ -706,9 +1024,7 @@ cudaError_t launch_mode_f32(const PairParams &p, int ipt, int grid, size_t smem,
 
 template <int MODE, int LOS>
 int occupancy_mode_f32(const PairParams &p, int ipt, size_t smem) {
-    void (*k)(PairParams);
-    if (p.weighted) k = (ipt == 2) ? k_pairs_f32<MODE, LOS, true, 2> : k_pairs_f32<MODE, LOS, true, 1>;
-    else k = (ipt == 2) ? k_pairs_f32<MODE, LOS, false, 2> : k_pairs_f32<MODE, LOS, false, 1>;
+    PairKernel<MODE, LOS> k = pick_f32<MODE, LOS>(p, ipt);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;

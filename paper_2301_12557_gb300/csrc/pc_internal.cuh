@@ -16,8 +16,8 @@ namespace pc {
 constexpr int NT = 128;        // threads per CTA
 constexpr int TJ = 256;        // j points per shared-memory tile (FP32 path)
 constexpr int TJ64 = 128;      // j points per tile (FP64 path)
-constexpr int MAXSEG = 512;    // j segments per chunk of stencil rows
-constexpr int ROWCHUNK = 160;  // stencil rows per chunk (<= 3 segments each)
+constexpr int MAXSEG = 320;    // j segments per chunk of stencil rows
+constexpr int ROWCHUNK = 96;   // stencil rows per chunk (<= 3 segments each)
 constexpr int LQ = 256;        // per-CTA rescue staging slots
 constexpr int MAX_LUT = 8192;  // LUT entries per histogram axis
 
@@ -90,6 +90,12 @@ struct PairParams {
     unsigned long long *counters;  // [0] candidates, [1] inline rescues
     int priv;                // 0: one histogram per CTA; 1: one per warp
     int smem_hist_ok;        // histogram fits in shared memory
+    // evenly spaced s (and mu) edges: bins by floor instead of tables
+    int lin;
+    float lin_invA, lin_offA;    // t_s = s * lin_invA + lin_offA, bin = floor(t_s)
+    float lin_thrA;              // not near an edge iff |frac(t_s) - 1/2| < lin_thrA
+    float lin_nB;                // t_mu = mu * lin_nB
+    float lin_mA, lin_cB;        // not near iff |frac(t_mu) - 1/2| < lin_cB - lin_mA / s
 };
 
 // ---------------------------------------------------------------------------

@@ -186,7 +186,7 @@ def test_cell_size_does_not_change_counts(cell):
     mu = np.linspace(0.0, 1.0, 21)
     want, _ = oracle.count(x, box=L, periodic=True, mode="smu", edges_a=ea, edges_b=mu,
                            method="grid")
-    for ipt in (1, 2):
+    for ipt in (2, 4):
         g, _ = P.count(x, box=L, periodic=True, mode="smu", edges_a=ea, edges_b=mu,
                        cell_size=cell, ipt=ipt)
         _check(g, want, what=f"cell {cell} ipt {ipt}")
