@@ -228,6 +228,15 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
 // ---------------------------------------------------------------------------
 // FP32 binning of one in-range candidate
 // ---------------------------------------------------------------------------
+// Reciprocal square root: one MUFU.RSQ (PTX rsqrt.approx.ftz.f32, documented
+// maximum relative error 2^-22.9; the rescue bands budget 2^-22).  +0 gives
+// +inf, so coincident points produce NaN separations and are rescued.
+__device__ __forceinline__ float rsqrt_fast(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Binning scalars, read from the kernel parameters once and kept in registers.
 struct BinCtx {
     const float2 *lutA, *lutB;   // tables in shared memory
@@ -265,7 +274,7 @@ __device__ __forceinline__ Bin32 bin_f32(const BinCtx &c, float dx, float dy, fl
                                          float qxy, float s2, float ax_, float ay_, float az_) {
     Bin32 r;
     if (MODE == MODE_S) {
-        float rs = rsqrtf(s2);
+        float rs = rsqrt_fast(s2);
         float s = s2 * rs;
         int k; float e;
         lut_locate(c.lutA, c.invA, c.TA1, s, k, e);
@@ -276,7 +285,7 @@ __device__ __forceinline__ Bin32 bin_f32(const BinCtx &c, float dx, float dy, fl
     }
     if (LOS == LOS_Z) {
         if (MODE == MODE_SMU) {
-            float rs = rsqrtf(s2);
+            float rs = rsqrt_fast(s2);
             float s = s2 * rs;
             float mu = fabsf(dz) * rs;
             int k, j; float e, em;
@@ -289,7 +298,7 @@ __device__ __forceinline__ Bin32 bin_f32(const BinCtx &c, float dx, float dy, fl
             return r;
         }
         // (sigma, pi) along z
-        float sg = qxy * rsqrtf(qxy);
+        float sg = qxy * rsqrt_fast(qxy);
         float pz = fabsf(dz);
         int k, j; float e, ep;
         lut_locate(c.lutA, c.invA, c.TA1, sg, k, e);
@@ -303,10 +312,10 @@ __device__ __forceinline__ Bin32 bin_f32(const BinCtx &c, float dx, float dy, fl
     float lx = fmaf(2.0f, ax_, dx), ly = fmaf(2.0f, ay_, dy), lz = fmaf(2.0f, az_, dz);
     float sl = fmaf(dz, lz, fmaf(dy, ly, dx * lx));
     float ll = fmaf(lz, lz, fmaf(ly, ly, lx * lx));
-    float rl = rsqrtf(ll);
+    float rl = rsqrt_fast(ll);
     float pi = fabsf(sl) * rl;
     if (MODE == MODE_SMU) {
-        float rs = rsqrtf(s2);
+        float rs = rsqrt_fast(s2);
         float s = s2 * rs;
         float mu = pi * rs;
         int k, j; float e, em;
@@ -323,7 +332,7 @@ __device__ __forceinline__ Bin32 bin_f32(const BinCtx &c, float dx, float dy, fl
     float cyp = fmaf(dz, lx, -dx * lz);
     float czp = fmaf(dx, ly, -dy * lx);
     float cc = fmaf(czp, czp, fmaf(cyp, cyp, cxp * cxp));
-    float sg = cc * rsqrtf(cc) * rl;
+    float sg = cc * rsqrt_fast(cc) * rl;
     int k, j; float e, ep;
     lut_locate(c.lutA, c.invA, c.TA1, sg, k, e);
     lut_locate(c.lutB, c.invB, c.TB1, pi, j, ep);
@@ -353,7 +362,7 @@ __device__ __forceinline__ float floor_grid(float t, float &fl) {
 template <int MODE>
 __device__ __forceinline__ Bin32 bin_lin(const LinCtx &c, float dz, float s2) {
     Bin32 r;
-    const float rs = rsqrtf(s2);
+    const float rs = rsqrt_fast(s2);
     const float s = s2 * rs;
     const float ts = fmaf(s, c.invA, c.offA);
     float fls;
@@ -516,19 +525,30 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
         const float2 X = *reinterpret_cast<const float2 *>(tb.x + jj);
         const float2 Y = *reinterpret_cast<const float2 *>(tb.y + jj);
         const float2 Z = *reinterpret_cast<const float2 *>(tb.z + jj);
+        float2 S2[RI], DZ[RI];
+        bool in0[RI], in1[RI];
+        bool any = false;
 #pragma unroll
         for (int r = 0; r < RI; ++r) {
             const float2 dx = __fadd2_rn(X, NX[r]);
             const float2 dy = __fadd2_rn(Y, NY[r]);
-            const float2 dz = __fadd2_rn(Z, NZ[r]);
-            const float2 s2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            bool i0 = s2.x < r2cut, i1 = s2.y < r2cut;
+            DZ[r] = __fadd2_rn(Z, NZ[r]);
+            S2[r] = __ffma2_rn(DZ[r], DZ[r], __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            in0[r] = S2[r].x < r2cut;
+            in1[r] = S2[r].y < r2cut;
             if (MASK) {
-                i0 = i0 && (bstart + jj > I.idx[r]);
-                i1 = i1 && (bstart + jj + 1 > I.idx[r]);
+                in0[r] = in0[r] && (bstart + jj > I.idx[r]);
+                in1[r] = in1[r] && (bstart + jj + 1 > I.idx[r]);
             }
-            if (__any_sync(0xffffffffu, i0 || i1)) {
-                const float2 rs = make_float2(rsqrtf(s2.x), rsqrtf(s2.y));
+            any = any || in0[r] || in1[r];
+        }
+        if (__any_sync(0xffffffffu, any)) {
+            bool re0[RI], re1[RI];
+            bool anyr = false;
+#pragma unroll
+            for (int r = 0; r < RI; ++r) {
+                const float2 s2 = S2[r];
+                const float2 rs = make_float2(rsqrt_fast(s2.x), rsqrt_fast(s2.y));
                 const float2 ts = __ffma2_rn(__fmul2_rn(s2, rs), INVA, OFFA);
                 const float2 f = __fadd2_rd(ts, C23);
                 const float2 d = __ffma2_rn(__fadd2_rn(f, NC23H), M1, ts);   // frac - 1/2
@@ -538,7 +558,7 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                 bool n0 = !(fabsf(d.x) < thrA), n1 = !(fabsf(d.y) < thrA);
                 unsigned b0 = (unsigned)__float_as_int(f.x), b1 = (unsigned)__float_as_int(f.y);
                 if (MODE == MODE_SMU) {
-                    const float2 adz = make_float2(fabsf(dz.x), fabsf(dz.y));
+                    const float2 adz = make_float2(fabsf(DZ[r].x), fabsf(DZ[r].y));
                     const float2 tm = __fmul2_rn(adz, __fmul2_rn(rs, NB));
                     const float2 fm = __fadd2_rd(tm, C23);
                     const float2 dm = __ffma2_rn(__fadd2_rn(fm, NC23H), M1, tm);
@@ -550,7 +570,7 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                     b0 = b0 * nbu + (unsigned)j0;
                     b1 = b1 * nbu + (unsigned)j1;
                 }
-                const bool a0 = i0 && ok0 && !n0, a1 = i1 && ok1 && !n1;
+                const bool a0 = in0[r] && ok0 && !n0, a1 = in1[r] && ok1 && !n1;
                 red_shared_u32_if(hbase + 4u * b0, a0);
                 red_shared_u32_if(hbase + 4u * b1, a1);
                 if (W) {
@@ -558,12 +578,17 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                     red_shared_f64_if(wbase + 8u * b0, __dmul_rn(I.w[r], wj.x), a0);
                     red_shared_f64_if(wbase + 8u * b1, __dmul_rn(I.w[r], wj.y), a1);
                 }
-                const bool r0 = i0 && n0, r1 = i1 && n1;
-                if (__any_sync(0xffffffffu, r0 || r1)) {
-                    if (r0)
+                re0[r] = in0[r] && n0;
+                re1[r] = in1[r] && n1;
+                anyr = anyr || re0[r] || re1[r];
+            }
+            if (__any_sync(0xffffffffu, anyr)) {
+#pragma unroll
+                for (int r = 0; r < RI; ++r) {
+                    if (re0[r])
                         rescue_push<MODE, LOS_Z>(p, s_q, s_qn, s_seg, nseg, f0, jj, bstart,
                                                  I.idx[r], task_bits);
-                    if (r1)
+                    if (re1[r])
                         rescue_push<MODE, LOS_Z>(p, s_q, s_qn, s_seg, nseg, f0, jj + 1, bstart,
                                                  I.idx[r], task_bits);
                 }

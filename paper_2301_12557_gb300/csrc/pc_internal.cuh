@@ -14,7 +14,7 @@ namespace pc {
 // launch geometry of the pair kernels
 // ---------------------------------------------------------------------------
 constexpr int NT = 128;        // threads per CTA
-constexpr int TJ = 256;        // j points per shared-memory tile (FP32 path)
+constexpr int TJ = 512;        // j points per shared-memory tile (FP32 path)
 constexpr int TJ64 = 128;      // j points per tile (FP64 path)
 constexpr int MAXSEG = 320;    // j segments per chunk of stencil rows
 constexpr int ROWCHUNK = 96;   // stencil rows per chunk (<= 3 segments each)
