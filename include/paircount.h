@@ -154,6 +154,28 @@ pc_status pc_count_cross(const pc_grid *g1, const pc_grid *g2, const pc_bins *b,
 pc_status pc_count_batch(const pc_grid *const *gs, int m, const pc_bins *b, const pc_opts *o,
                          void *stream, long long *counts, double *wcounts, pc_stats *st);
 
+/* Auto pair counts like pc_count_auto, but the call allocates no device
+ * memory (no cudaMalloc, cudaFree or allocating library routine): for
+ * callers whose device memory is owned by another allocator, loops that must
+ * not meet the implicit device synchronisation an allocation can trigger,
+ * and processes running at their memory limit.  The paper has no
+ * counterpart; this is a deployment variant of the same computation.
+ *   g         a grid from pc_build_grid, on the current device
+ *   counts    int64 [nbins] (host or device), wcounts binary64 [nbins] or
+ *             NULL; both written on return
+ * All temporaries live in one fixed device array of about 12.3 MiB inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Its device address is looked up on the first call on each device,
+ * so make that first call before any stream capture.  Limits (PC_EOVERFLOW
+ * beyond them): 16384 bins, 262144 grid cells, 524288 point blocks, 8192
+ * stencil rows.  The array keeps the last call's contents and is cleared
+ * where needed at the start of every call; calls are serialised by the
+ * library and each returns only after its work has finished, and any two
+ * such calls overlapping on the GPU (for instance from two processes sharing
+ * one device context) would race on it. */
+pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, const pc_opts *o,
+                                void *stream, long long *counts, double *wcounts);
+
 /* Bounding box of n points (n x 3 binary64, host or device) -- the first of
  * the three grid-build passes of Sect. 2.1.  lo/hi are host arrays of 3. */
 pc_status pc_aabb(const double *xyz, long long n, void *stream, double *lo, double *hi);

@@ -67,7 +67,7 @@ _lib = None
 
 EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc_count_cross",
            "pc_count_batch", "pc_aabb", "pc_suggest_cell_size", "pc_strerror", "pc_last_error",
-           "pc_version", "pc_launch_count"]
+           "pc_version", "pc_launch_count", "pc_count_auto_noalloc"]
 
 
 def library_path() -> str:
@@ -119,6 +119,8 @@ def lib():
     L.pc_version.argtypes = []
     L.pc_launch_count.restype = c_longlong
     L.pc_launch_count.argtypes = []
+    L.pc_count_auto_noalloc.restype = c_int
+    L.pc_count_auto_noalloc.argtypes = [vp, POINTER(pc_bins), POINTER(pc_opts), vp, vp, vp]
     _lib = L
     return L
 
@@ -326,6 +328,20 @@ def pc_count_auto(g: Grid, bins: Bins, opts: pc_opts | None = None, stream=None,
            "pc_count_auto")
     del keep
     return counts, wcounts, st
+
+
+def pc_count_auto_noalloc(g: Grid, bins: Bins, opts: pc_opts | None = None, stream=None,
+                          counts=None, wcounts=None, weighted=False):
+    """Auto counts without any device allocation inside the call (all
+    temporaries live in a fixed array inside the library).  Pass device
+    tensors for counts/wcounts to keep the whole call allocation-free."""
+    counts, wcounts, pc_, pw_, keep = _outputs(counts, wcounts, 1, bins.nbins, weighted)
+    _check(lib().pc_count_auto_noalloc(g.handle, ctypes.byref(bins.s),
+                                       ctypes.byref(opts) if opts is not None else None,
+                                       _stream_handle(stream), pc_, pw_),
+           "pc_count_auto_noalloc")
+    del keep
+    return counts, wcounts
 
 
 def pc_count_cross(g1: Grid, g2: Grid, bins: Bins, opts: pc_opts | None = None, stream=None,

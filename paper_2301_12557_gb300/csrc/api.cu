@@ -734,3 +734,224 @@ extern "C" const char *pc_last_error(void) { return g_last_error.c_str(); }
 extern "C" long long pc_launch_count(void) { return launch_count(); }
 
 extern "C" const char *pc_version(void) { return "paircount-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// Auto counts without device allocation.
+//
+// For callers that must not allocate device memory at count time: code whose
+// device memory is owned by another allocator (a framework's caching
+// allocator that holds the whole device), loops that must never hit the
+// implicit device synchronisation a cudaMalloc/cudaFree can trigger, and
+// processes running at their memory limit.  Every temporary of the count
+// lives in one file-scope device array of fixed size instead.
+// ---------------------------------------------------------------------------
+namespace pc {
+
+// Limits of the fixed scratch array (the call rejects anything larger).
+constexpr int NA_MAX_BINS = 16384;        // histogram bins
+constexpr int NA_MAX_EDGES = 16385;       // edges per axis
+constexpr int NA_MAX_CELLS = 1 << 18;     // cells of the grid
+constexpr int NA_MAX_BLOCKS = 1 << 19;    // i-blocks
+constexpr int NA_MAX_ROWS = 8192;         // stencil rows
+constexpr int NA_MAX_LUT = 2 * (MAX_LUT + 2);
+constexpr unsigned long long NA_QUEUE = 1ull << 17;   // rescue slots (overflow is evaluated in-kernel)
+
+struct NaLayout {
+    size_t hist, whist, counters, scalars, tasks, stencil, lut, ea, eb, cnt, off, tot, blocks, queue,
+        total;
+};
+
+constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+
+constexpr NaLayout na_layout() {
+    NaLayout L{};
+    size_t o = 0;
+    L.hist = o;     o = na_align(o + sizeof(unsigned long long) * NA_MAX_BINS);
+    L.whist = o;    o = na_align(o + sizeof(double) * NA_MAX_BINS);
+    L.counters = o; o = na_align(o + sizeof(unsigned long long) * 4);
+    L.scalars = o;  o = na_align(o + sizeof(int) * 4);
+    L.tasks = o;    o = na_align(o + sizeof(TaskDev));
+    L.stencil = o;  o = na_align(o + sizeof(int4) * NA_MAX_ROWS);
+    L.lut = o;      o = na_align(o + sizeof(float2) * NA_MAX_LUT);
+    L.ea = o;       o = na_align(o + sizeof(double) * NA_MAX_EDGES);
+    L.eb = o;       o = na_align(o + sizeof(double) * NA_MAX_EDGES);
+    L.cnt = o;      o = na_align(o + sizeof(int) * (NA_MAX_CELLS + 1));
+    L.off = o;      o = na_align(o + sizeof(int) * (NA_MAX_CELLS + 1));
+    L.tot = o;      o = na_align(o + sizeof(int) * (NA_MAX_CELLS / 4096 + 2));
+    L.blocks = o;   o = na_align(o + sizeof(Block) * NA_MAX_BLOCKS);
+    L.queue = o;    o = na_align(o + sizeof(uint3) * NA_QUEUE);
+    L.total = o;
+    return L;
+}
+
+constexpr NaLayout NA = na_layout();
+
+// The scratch array (12.3 MiB).  Every GPU that loads the library holds
+// it until the process exits.
+static __device__ __align__(256) unsigned char g_count_scratch[NA.total];
+
+// Device address of the scratch array on device `dev`, looked up once per
+// device with that device current (the host-side symbol is only a stand-in
+// and must never be handed to a kernel).
+static unsigned char *scratch_on(int dev) {
+    static std::map<int, unsigned char *> addr;
+    auto it = addr.find(dev);
+    if (it != addr.end()) return it->second;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_count_scratch);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        return nullptr;
+    }
+    addr[dev] = (unsigned char *)p;
+    return (unsigned char *)p;
+}
+
+}  // namespace pc
+
+extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, const pc_opts *opt,
+                                           void *stream, long long *counts, double *wcounts) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!g) return fail(PC_EINVAL, "pc_count_auto_noalloc: grid is NULL");
+    if (!counts && !wcounts) return fail(PC_EINVAL, "pc_count_auto_noalloc: no output buffer");
+    if (wcounts && !g->weighted) return fail(PC_EINVAL, "pc_count_auto_noalloc: grid has no weights");
+    int cur = -1;
+    PC_CUDA(cudaGetDevice(&cur));
+    if (cur != g->device)
+        return fail(PC_EINVAL, "pc_count_auto_noalloc: the grid's device must be current");
+    cudaStream_t st = (cudaStream_t)stream;
+    pc_opts o;
+    memset(&o, 0, sizeof(o));
+    o.priv = -1;
+    if (opt) o = *opt;
+
+    Plan P;
+    pc_status s = make_plan(b, g->g, g->pts_lo, g->pts_hi, true, P);
+    if (s != PC_OK) return s;
+    int prec = o.prec;
+    if (prec == PC_PREC_F32_RESCUE && !P.fp32_ok) prec = PC_PREC_F64;
+    int ipt = (o.ipt == 4) ? 4 : 2;
+    if (prec == PC_PREC_F64) ipt = 1;
+    const int bi = NT * ipt;
+    const long long nblk = (long long)g->ncell + g->n / bi + 16;
+    if (P.nbins > NA_MAX_BINS || P.na + 1 > NA_MAX_EDGES || P.nb + 1 > NA_MAX_EDGES)
+        return fail(PC_EOVERFLOW, "pc_count_auto_noalloc: more than 16384 bins");
+    if (g->ncell > NA_MAX_CELLS)
+        return fail(PC_EOVERFLOW, "pc_count_auto_noalloc: grid has more than 262144 cells");
+    if (nblk > NA_MAX_BLOCKS)
+        return fail(PC_EOVERFLOW, "pc_count_auto_noalloc: more than 524288 point blocks");
+    if ((int)P.stencil.size() > NA_MAX_ROWS)
+        return fail(PC_EOVERFLOW, "pc_count_auto_noalloc: stencil has more than 8192 rows");
+    if ((int)P.lut.size() > NA_MAX_LUT)
+        return fail(PC_EOVERFLOW, "pc_count_auto_noalloc: lookup tables too large");
+
+    unsigned char *base = scratch_on(cur);
+    if (!base) return PC_ECUDA;
+    unsigned long long *hist = (unsigned long long *)(base + NA.hist);
+    double *whist = (double *)(base + NA.whist);
+    unsigned long long *ctr = (unsigned long long *)(base + NA.counters);
+    int *sc = (int *)(base + NA.scalars);
+    TaskDev *tasks = (TaskDev *)(base + NA.tasks);
+
+    // everything that must start at zero is cleared on every call
+    const size_t hist_n = (size_t)P.nbins;
+    PC_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * hist_n, st));
+    if (wcounts) PC_CUDA(cudaMemsetAsync(whist, 0, sizeof(double) * hist_n, st));
+    PC_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 4, st));
+    PC_CUDA(cudaMemsetAsync(sc, 0, sizeof(int) * 4, st));
+    TaskDev t = task_of(g, g, 0, 1);
+    PC_CUDA(cudaMemcpyAsync(tasks, &t, sizeof(TaskDev), cudaMemcpyHostToDevice, st));
+    if (!P.stencil.empty())
+        PC_CUDA(cudaMemcpyAsync(base + NA.stencil, P.stencil.data(), sizeof(int4) * P.stencil.size(),
+                                cudaMemcpyHostToDevice, st));
+    if (!P.lut.empty())
+        PC_CUDA(cudaMemcpyAsync(base + NA.lut, P.lut.data(), sizeof(float2) * P.lut.size(),
+                                cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(base + NA.ea, P.Ea.data(), sizeof(double) * (P.na + 1),
+                            cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(base + NA.eb, P.Eb.data(), sizeof(double) * (P.nb + 1),
+                            cudaMemcpyHostToDevice, st));
+    PC_CUDA(make_blocks_into(tasks, 1, g->ncell, bi, (Block *)(base + NA.blocks), sc + 1,
+                             (int *)(base + NA.cnt), (int *)(base + NA.off),
+                             (int *)(base + NA.tot), st));
+
+    PairParams p;
+    memset(&p, 0, sizeof(p));
+    p.tasks = tasks;
+    p.blocks = (const Block *)(base + NA.blocks);
+    p.nblocks = sc + 1;
+    p.work_counter = sc;
+    p.g = g->g;
+    p.stencil = (const int4 *)(base + NA.stencil);
+    p.nrows = (int)P.stencil.size();
+    p.mode = P.mode;
+    p.los = P.los;
+    p.weighted = wcounts ? 1 : 0;
+    p.n_a = P.na;
+    p.n_b = P.nb;
+    p.nbins = P.nbins;
+    p.r2cut = P.r2cut;
+    p.lut = (const float2 *)(base + NA.lut);
+    p.lut_total = (int)P.lut.size();
+    p.la = P.la;
+    p.lb = P.lb;
+    p.eps_a = P.eps_a;
+    p.eps_b = P.eps_b;
+    p.mu_A = P.mu_A;
+    p.mu_B = P.mu_B;
+    p.mu_W = P.mu_W;
+    p.Ea = (const double *)(base + NA.ea);
+    p.Eb = (const double *)(base + NA.eb);
+    p.hist = hist;
+    p.whist = wcounts ? whist : nullptr;
+    p.queue = (uint3 *)(base + NA.queue);
+    p.qcount = ctr + 2;
+    p.qcap = (prec == PC_PREC_F32_RESCUE) ? NA_QUEUE : 0;
+    p.counters = ctr;
+    int copies_warp = P.nbins * (NT / 32) * 4;
+    if (o.priv == 0 || o.priv == 1) p.priv = o.priv;
+    else p.priv = (P.nbins <= 2048 && copies_warp <= 48 * 1024) ? 1 : 0;
+    p.lin = (prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
+    p.lin_invA = P.lin_invA;
+    p.lin_offA = P.lin_offA;
+    p.lin_thrA = P.lin_thrA;
+    p.lin_nB = P.lin_nB;
+    p.lin_mA = P.lin_mA;
+    p.lin_cB = P.lin_cB;
+
+    int sms = 0, smem_optin = 0;
+    PC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur));
+    PC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cur));
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        p.smem_hist_ok = 1;
+        size_t need = (prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, ipt);
+        if (need + 256 <= (size_t)smem_optin) break;
+        if (p.priv) { p.priv = 0; continue; }
+        p.smem_hist_ok = 0;
+        break;
+    }
+    size_t smem = (prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, ipt);
+    if (smem + 256 > (size_t)smem_optin)
+        return fail(PC_EUNSUPPORTED, "bins: tables do not fit in shared memory");
+    int per_sm = (prec == PC_PREC_F64) ? pairs_f64_ctas_per_sm(p, smem)
+                                       : pairs_f32_ctas_per_sm(p, ipt, smem);
+    if (per_sm <= 0) return fail(PC_ECUDA, "pair kernel cannot be resident");
+    if (o.grid_ctas_per_sm > 0) per_sm = std::min(per_sm, o.grid_ctas_per_sm);
+    cudaError_t e = (prec == PC_PREC_F64) ? launch_pairs_f64(p, sms * per_sm, smem, st)
+                                          : launch_pairs_f32(p, ipt, sms * per_sm, smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "pair kernel launch");
+    if (p.qcap) {
+        e = launch_rescue(p, st);
+        if (e != cudaSuccess) return cuda_fail(e, "rescue kernel launch");
+    }
+    if (counts) {
+        cudaMemcpyKind k = is_device_ptr(counts) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        PC_CUDA(cudaMemcpyAsync(counts, hist, sizeof(long long) * hist_n, k, st));
+    }
+    if (wcounts) {
+        cudaMemcpyKind k = is_device_ptr(wcounts) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        PC_CUDA(cudaMemcpyAsync(wcounts, whist, sizeof(double) * hist_n, k, st));
+    }
+    PC_CUDA(cudaStreamSynchronize(st));
+    return PC_OK;
+}

@@ -230,6 +230,26 @@ cudaError_t scan_exclusive(const int *in, int *out, int n, cudaStream_t st) {
     return e;
 }
 
+// Same scan with the tile-total buffer supplied by the caller (at least
+// max(1, ceil(n / 4096)) ints); performs no allocation.
+cudaError_t scan_exclusive_into(const int *in, int *out, int n, int *tot, cudaStream_t st) {
+    int ntiles = std::max(1, (n + SCAN_TILE - 1) / SCAN_TILE);
+    if (n > 0) {
+        k_scan_tiles<<<ntiles, SCAN_T, 0, st>>>(in, out, n, tot);
+        note_launch();
+    } else {
+        cudaError_t e = cudaMemsetAsync(tot, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
+    k_scan_totals<<<1, SCAN_T, 0, st>>>(tot, n > 0 ? ntiles : 1, out, n);
+    note_launch();
+    if (n > 0) {
+        k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, n, tot);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // block list
 // ---------------------------------------------------------------------------
@@ -269,6 +289,25 @@ cudaError_t make_blocks(const TaskDev *tasks_dev, int ntasks, int ncell, int bi,
         note_launch();
     }
     cudaError_t e = scan_exclusive(tmp_counts, tmp_offsets, (int)tot, st);
+    if (e != cudaSuccess) return e;
+    k_block_emit<<<std::max(g, 1), 256, 0, st>>>(tasks_dev, ntasks, ncell, tmp_offsets, blocks,
+                                                 nblocks_dev);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// make_blocks with every temporary supplied by the caller (tmp_tot: at least
+// max(1, ceil((ntasks * ncell) / 4096)) ints); performs no allocation.
+cudaError_t make_blocks_into(const TaskDev *tasks_dev, int ntasks, int ncell, int bi,
+                             Block *blocks, int *nblocks_dev, int *tmp_counts, int *tmp_offsets,
+                             int *tmp_tot, cudaStream_t st) {
+    long long tot = (long long)ntasks * ncell;
+    int g = (int)((tot + 255) / 256);
+    if (g > 0) {
+        k_block_counts<<<g, 256, 0, st>>>(tasks_dev, ntasks, ncell, bi, tmp_counts);
+        note_launch();
+    }
+    cudaError_t e = scan_exclusive_into(tmp_counts, tmp_offsets, (int)tot, tmp_tot, st);
     if (e != cudaSuccess) return e;
     k_block_emit<<<std::max(g, 1), 256, 0, st>>>(tasks_dev, ntasks, ncell, tmp_offsets, blocks,
                                                  nblocks_dev);

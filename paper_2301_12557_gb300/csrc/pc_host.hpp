@@ -40,6 +40,12 @@ cudaError_t scan_exclusive(const int *in, int *out, int n, cudaStream_t st);
 cudaError_t make_blocks(const TaskDev *tasks_dev, int ntasks, int ncell, int bi, Block *blocks,
                         int *nblocks_dev, int *tmp_counts, int *tmp_offsets, cudaStream_t st);
 
+// Allocation-free variants: every temporary comes from the caller.
+cudaError_t scan_exclusive_into(const int *in, int *out, int n, int *tot, cudaStream_t st);
+cudaError_t make_blocks_into(const TaskDev *tasks_dev, int ntasks, int ncell, int bi,
+                             Block *blocks, int *nblocks_dev, int *tmp_counts, int *tmp_offsets,
+                             int *tmp_tot, cudaStream_t st);
+
 // Device-side bounding box; lo/hi are host arrays (the call synchronises).
 pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *lo, double *hi);
 
