@@ -159,12 +159,16 @@ def oracle_sample_rate(D, w, seconds, seed=0, L=None):
     kw = dict(box=w.L if L is None else L, periodic=w.periodic, mode=w.mode, los=w.los,
               edges_a=w.edges_a, edges_b=w.edges_b)
     n = D.shape[0]
-    m0 = 32
-    S = np.ascontiguousarray(D[rng.choice(n, m0, replace=False)])
-    t = time.perf_counter()
-    oracle.count(S, D, **kw)
-    dt = max(time.perf_counter() - t, 1e-6)
-    m = int(max(m0, min(n, m0 * seconds / dt)))
+    m0, dt = 16, 0.0
+    while True:      # calibrate on growing samples until one takes >= 1/8 of the budget
+        S = np.ascontiguousarray(D[rng.choice(n, m0, replace=False)])
+        t = time.perf_counter()
+        oracle.count(S, D, **kw)
+        dt = max(time.perf_counter() - t, 1e-6)
+        if dt >= seconds / 8 or m0 >= n:
+            break
+        m0 = min(n, m0 * 4)
+    m = int(max(1, min(n, m0 * seconds / dt)))
     S = np.ascontiguousarray(D[rng.choice(n, m, replace=False)])
     t = time.perf_counter()
     oracle.count(S, D, **kw)
