@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -78,7 +79,8 @@ struct Buf {
 };
 
 struct Workspace {
-    Buf hist, whist, counters, scalars, queue, blocks, tmp_cnt, tmp_off, tasks, stencil, lut, ea, eb;
+    Buf hist, whist, counters, scalars, queue, blocks, tmp_cnt, tmp_off, tmp_tot, tasks, stencil, lut,
+        ea, eb;
 };
 
 static Workspace &workspace(int dev) {
@@ -393,108 +395,142 @@ struct CountJob {
     const pc_grid *g0;
 };
 
-static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *opt,
-                           cudaStream_t st, long long *counts, double *wcounts, pc_stats *stats) {
-    pc_opts o;
-    memset(&o, 0, sizeof(o));
-    o.priv = -1;
-    if (opt) o = *opt;
-    const pc_grid *g0 = J.g0;
+// Everything decided on the host before any device work.
+struct CountSetup {
     Plan P;
-    pc_status s = make_plan(b, g0->g, g0->pts_lo, g0->pts_hi, J.is_auto, P);
+    pc_opts o;
+    int prec = 0, ipt = 2, bi = 256, dev = 0, ntasks = 0, ncell = 0;
+    bool weighted = false;
+    size_t nblk_cap = 0, hist_n = 0;
+    unsigned long long qcap = 0;
+};
+
+// Device buffers of one count (raw pointers into a Workspace).
+struct DevBufs {
+    unsigned long long *hist = nullptr;
+    double *whist = nullptr;
+    unsigned long long *ctr = nullptr;   // [0] candidates, [1] inline rescues, [2] queue count
+    int *sc = nullptr;                   // [0] work counter, [1] number of blocks
+    uint3 *queue = nullptr;
+    Block *blocks = nullptr;
+    int *cnt = nullptr, *off = nullptr, *tot = nullptr;
+    TaskDev *tasks = nullptr;
+    int4 *stencil = nullptr;
+    float2 *lut = nullptr;
+    double *ea = nullptr, *eb = nullptr;
+};
+
+static pc_status setup_count(const CountJob &J, const pc_bins *b, const pc_opts *opt,
+                             bool weighted, CountSetup &S) {
+    memset(&S.o, 0, sizeof(S.o));
+    S.o.priv = -1;
+    if (opt) S.o = *opt;
+    const pc_grid *g0 = J.g0;
+    pc_status s = make_plan(b, g0->g, g0->pts_lo, g0->pts_hi, J.is_auto, S.P);
     if (s != PC_OK) return s;
-    bool weighted = wcounts != nullptr;
-    if (weighted)
-        for (auto &t : J.tasks)
-            (void)t;
-    int prec = o.prec;
-    if (prec == PC_PREC_F32_RESCUE && !P.fp32_ok) prec = PC_PREC_F64;
-    int ipt = (o.ipt == 4) ? 4 : 2;
-    if (prec == PC_PREC_F64) ipt = 1;
-    const int bi = NT * ipt;
-
-    int dev = g0->device;
-    Workspace &W = workspace(dev);
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    const long long launches0 = launch_count();
-    if (stats) {
-        for (auto &e : ev) cudaEventCreate(&e);
-        cudaEventRecord(ev[0], st);
-    }
-
-    const int ntasks = (int)J.tasks.size();
-    const int ncell = g0->ncell;
+    S.weighted = weighted;
+    S.prec = S.o.prec;
+    if (S.prec == PC_PREC_F32_RESCUE && !S.P.fp32_ok) S.prec = PC_PREC_F64;
+    S.ipt = (S.o.ipt == 4) ? 4 : 2;
+    if (S.prec == PC_PREC_F64) S.ipt = 1;
+    S.bi = NT * S.ipt;
+    S.dev = g0->device;
+    S.ntasks = (int)J.tasks.size();
+    S.ncell = g0->ncell;
     long long npts = 0;
     for (auto &t : J.tasks) npts += t.gi.n;
-    size_t nblk_cap = (size_t)ntasks * ncell + (size_t)(npts / bi) + 16;
-    size_t hist_n = (size_t)J.nhist * P.nbins;
-
-    PC_CUDA(W.hist.ensure(sizeof(unsigned long long) * hist_n));
-    if (weighted) PC_CUDA(W.whist.ensure(sizeof(double) * hist_n));
-    PC_CUDA(W.counters.ensure(sizeof(unsigned long long) * 4));
-    PC_CUDA(W.scalars.ensure(sizeof(int) * 4));
-    PC_CUDA(W.blocks.ensure(sizeof(Block) * nblk_cap));
-    PC_CUDA(W.tmp_cnt.ensure(sizeof(int) * ((size_t)ntasks * ncell + 1)));
-    PC_CUDA(W.tmp_off.ensure(sizeof(int) * ((size_t)ntasks * ncell + 1)));
-    PC_CUDA(W.tasks.ensure(sizeof(TaskDev) * ntasks));
-    PC_CUDA(W.stencil.ensure(sizeof(int4) * std::max<size_t>(P.stencil.size(), 1)));
-    PC_CUDA(W.lut.ensure(sizeof(float2) * std::max<size_t>(P.lut.size(), 1)));
-    PC_CUDA(W.ea.ensure(sizeof(double) * (P.na + 1)));
-    PC_CUDA(W.eb.ensure(sizeof(double) * (P.nb + 1)));
-
-    // rescue queue capacity: ~2e-3 of the expected in-range pairs
-    unsigned long long qcap = 0;
-    if (prec == PC_PREC_F32_RESCUE) {
-        if (o.rescue_capacity > 0) qcap = (unsigned long long)o.rescue_capacity;
-        else if (o.rescue_capacity == 0) {
+    S.nblk_cap = (size_t)S.ntasks * S.ncell + (size_t)(npts / S.bi) + 16;
+    S.hist_n = (size_t)J.nhist * S.P.nbins;
+    // rescue queue capacity: ~4e-3 of the expected in-range pairs (overflow
+    // is evaluated inside the pair kernel, so this only sets the fast case)
+    S.qcap = 0;
+    if (S.prec == PC_PREC_F32_RESCUE) {
+        if (S.o.rescue_capacity > 0) S.qcap = (unsigned long long)S.o.rescue_capacity;
+        else if (S.o.rescue_capacity == 0) {
             double vol = 1.0;
             for (int a = 0; a < 3; ++a) vol *= std::max(g0->pts_hi[a] - g0->pts_lo[a], 1e-9);
-            double vs = 4.0 / 3.0 * M_PI * P.reff * P.reff * P.reff;
+            double vs = 4.0 / 3.0 * M_PI * S.P.reff * S.P.reff * S.P.reff;
             double pairs = 0.0;
-            for (auto &t : J.tasks) pairs += 0.5 * (double)t.gi.n * (double)t.gj.n * std::min(1.0, vs / vol);
+            for (auto &t : J.tasks)
+                pairs += 0.5 * (double)t.gi.n * (double)t.gj.n * std::min(1.0, vs / vol);
             double want = std::max(1.0e6, 4.0e-3 * pairs * (J.is_auto ? 1.0 : 2.0));
-            qcap = (unsigned long long)std::min(want, 4.0e8);
+            S.qcap = (unsigned long long)std::min(want, 4.0e8);
         }
-        if (qcap) PC_CUDA(W.queue.ensure(sizeof(uint3) * qcap));
     }
+    return PC_OK;
+}
 
-    PC_CUDA(cudaMemcpyAsync(W.tasks.p, J.tasks.data(), sizeof(TaskDev) * ntasks,
+static pc_status ensure_bufs(Workspace &W, const CountSetup &S, DevBufs &B) {
+    const size_t cells = (size_t)S.ntasks * S.ncell + 1;
+    PC_CUDA(W.hist.ensure(sizeof(unsigned long long) * S.hist_n));
+    if (S.weighted) PC_CUDA(W.whist.ensure(sizeof(double) * S.hist_n));
+    PC_CUDA(W.counters.ensure(sizeof(unsigned long long) * 4));
+    PC_CUDA(W.scalars.ensure(sizeof(int) * 4));
+    PC_CUDA(W.blocks.ensure(sizeof(Block) * S.nblk_cap));
+    PC_CUDA(W.tmp_cnt.ensure(sizeof(int) * cells));
+    PC_CUDA(W.tmp_off.ensure(sizeof(int) * cells));
+    PC_CUDA(W.tmp_tot.ensure(sizeof(int) * (cells / 4096 + 2)));
+    PC_CUDA(W.tasks.ensure(sizeof(TaskDev) * S.ntasks));
+    PC_CUDA(W.stencil.ensure(sizeof(int4) * std::max<size_t>(S.P.stencil.size(), 1)));
+    PC_CUDA(W.lut.ensure(sizeof(float2) * std::max<size_t>(S.P.lut.size(), 1)));
+    PC_CUDA(W.ea.ensure(sizeof(double) * (S.P.na + 1)));
+    PC_CUDA(W.eb.ensure(sizeof(double) * (S.P.nb + 1)));
+    if (S.qcap) PC_CUDA(W.queue.ensure(sizeof(uint3) * S.qcap));
+    B.hist = (unsigned long long *)W.hist.p;
+    B.whist = S.weighted ? (double *)W.whist.p : nullptr;
+    B.ctr = (unsigned long long *)W.counters.p;
+    B.sc = (int *)W.scalars.p;
+    B.queue = (uint3 *)W.queue.p;
+    B.blocks = (Block *)W.blocks.p;
+    B.cnt = (int *)W.tmp_cnt.p;
+    B.off = (int *)W.tmp_off.p;
+    B.tot = (int *)W.tmp_tot.p;
+    B.tasks = (TaskDev *)W.tasks.p;
+    B.stencil = (int4 *)W.stencil.p;
+    B.lut = (float2 *)W.lut.p;
+    B.ea = (double *)W.ea.p;
+    B.eb = (double *)W.eb.p;
+    return PC_OK;
+}
+
+// Host-built tables of the count (tasks, stencil, lookup tables, edges).
+static pc_status upload_tables(const CountJob &J, const CountSetup &S, const DevBufs &B,
+                               cudaStream_t st) {
+    PC_CUDA(cudaMemcpyAsync(B.tasks, J.tasks.data(), sizeof(TaskDev) * S.ntasks,
                             cudaMemcpyHostToDevice, st));
-    if (!P.stencil.empty())
-        PC_CUDA(cudaMemcpyAsync(W.stencil.p, P.stencil.data(), sizeof(int4) * P.stencil.size(),
+    if (!S.P.stencil.empty())
+        PC_CUDA(cudaMemcpyAsync(B.stencil, S.P.stencil.data(), sizeof(int4) * S.P.stencil.size(),
                                 cudaMemcpyHostToDevice, st));
-    if (!P.lut.empty())
-        PC_CUDA(cudaMemcpyAsync(W.lut.p, P.lut.data(), sizeof(float2) * P.lut.size(),
+    if (!S.P.lut.empty())
+        PC_CUDA(cudaMemcpyAsync(B.lut, S.P.lut.data(), sizeof(float2) * S.P.lut.size(),
                                 cudaMemcpyHostToDevice, st));
-    PC_CUDA(cudaMemcpyAsync(W.ea.p, P.Ea.data(), sizeof(double) * (P.na + 1), cudaMemcpyHostToDevice, st));
-    PC_CUDA(cudaMemcpyAsync(W.eb.p, P.Eb.data(), sizeof(double) * (P.nb + 1), cudaMemcpyHostToDevice, st));
-    PC_CUDA(cudaMemsetAsync(W.hist.p, 0, sizeof(unsigned long long) * hist_n, st));
-    if (weighted) PC_CUDA(cudaMemsetAsync(W.whist.p, 0, sizeof(double) * hist_n, st));
-    PC_CUDA(cudaMemsetAsync(W.counters.p, 0, sizeof(unsigned long long) * 4, st));
-    PC_CUDA(cudaMemsetAsync(W.scalars.p, 0, sizeof(int) * 4, st));
+    PC_CUDA(cudaMemcpyAsync(B.ea, S.P.Ea.data(), sizeof(double) * (S.P.na + 1),
+                            cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(B.eb, S.P.Eb.data(), sizeof(double) * (S.P.nb + 1),
+                            cudaMemcpyHostToDevice, st));
+    return PC_OK;
+}
 
-    int *sc = (int *)W.scalars.p;   // [0] work counter, [1] nblocks
-    unsigned long long *ctr = (unsigned long long *)W.counters.p;   // [0] cand, [1] inline, [2] qcount
-    PC_CUDA(make_blocks((const TaskDev *)W.tasks.p, ntasks, ncell, bi, (Block *)W.blocks.p, sc + 1,
-                        (int *)W.tmp_cnt.p, (int *)W.tmp_off.p, st));
-
-    PairParams p;
+// Kernel parameters and launch shape.
+static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBufs &B,
+                             PairParams &p, int &grid, size_t &smem) {
+    const Plan &P = S.P;
     memset(&p, 0, sizeof(p));
-    p.tasks = (const TaskDev *)W.tasks.p;
-    p.blocks = (const Block *)W.blocks.p;
-    p.nblocks = sc + 1;
-    p.work_counter = sc;
-    p.g = g0->g;
-    p.stencil = (const int4 *)W.stencil.p;
+    p.tasks = B.tasks;
+    p.blocks = B.blocks;
+    p.nblocks = B.sc + 1;
+    p.work_counter = B.sc;
+    p.g = J.g0->g;
+    p.stencil = B.stencil;
     p.nrows = (int)P.stencil.size();
     p.mode = P.mode;
     p.los = P.los;
-    p.weighted = weighted ? 1 : 0;
+    p.weighted = S.weighted ? 1 : 0;
     p.n_a = P.na;
     p.n_b = P.nb;
     p.nbins = P.nbins;
     p.r2cut = P.r2cut;
-    p.lut = (const float2 *)W.lut.p;
+    p.lut = B.lut;
     p.lut_total = (int)P.lut.size();
     p.la = P.la;
     p.lb = P.lb;
@@ -503,19 +539,19 @@ static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *o
     p.mu_A = P.mu_A;
     p.mu_B = P.mu_B;
     p.mu_W = P.mu_W;
-    p.Ea = (const double *)W.ea.p;
-    p.Eb = (const double *)W.eb.p;
-    p.hist = (unsigned long long *)W.hist.p;
-    p.whist = weighted ? (double *)W.whist.p : nullptr;
-    p.queue = (uint3 *)W.queue.p;
-    p.qcount = ctr + 2;
-    p.qcap = qcap;
-    p.counters = ctr;
+    p.Ea = B.ea;
+    p.Eb = B.eb;
+    p.hist = B.hist;
+    p.whist = B.whist;
+    p.queue = B.queue;
+    p.qcount = B.ctr + 2;
+    p.qcap = S.qcap;
+    p.counters = B.ctr;
     // histogram privatisation: one copy per warp when it fits and helps
     int copies_warp = P.nbins * (NT / 32) * 4;
-    if (o.priv == 0 || o.priv == 1) p.priv = o.priv;
+    if (S.o.priv == 0 || S.o.priv == 1) p.priv = S.o.priv;
     else p.priv = (P.nbins <= 2048 && copies_warp <= 48 * 1024) ? 1 : 0;
-    p.lin = (prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
+    p.lin = (S.prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
     p.lin_invA = P.lin_invA;
     p.lin_offA = P.lin_offA;
     p.lin_thrA = P.lin_thrA;
@@ -523,73 +559,290 @@ static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *o
     p.lin_mA = P.lin_mA;
     p.lin_cB = P.lin_cB;
 
-    int dev_sms = 0;
-    PC_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev));
-    int smem_optin = 0;
-    PC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int dev_sms = 0, smem_optin = 0;
+    PC_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, S.dev));
+    PC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S.dev));
     const int static_smem = 256;
     for (int attempt = 0; attempt < 3; ++attempt) {
         p.smem_hist_ok = 1;
-        size_t need = (prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, ipt);
+        size_t need = (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
         if (need + static_smem <= (size_t)smem_optin) break;
         if (p.priv) { p.priv = 0; continue; }
         p.smem_hist_ok = 0;
         break;
     }
-    size_t smem = (prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, ipt);
+    smem = (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
     if (smem + static_smem > (size_t)smem_optin)
         return fail(PC_EUNSUPPORTED, "bins: tables do not fit in shared memory");
-    int per_sm = (prec == PC_PREC_F64) ? pairs_f64_ctas_per_sm(p, smem)
-                                       : pairs_f32_ctas_per_sm(p, ipt, smem);
-    if (per_sm <= 0) return fail(PC_ECUDA, std::string("pair kernel cannot be resident: ") + pc_last_error());
-    if (o.grid_ctas_per_sm > 0) per_sm = std::min(per_sm, o.grid_ctas_per_sm);
-    int grid = dev_sms * per_sm;
+    int per_sm = (S.prec == PC_PREC_F64) ? pairs_f64_ctas_per_sm(p, smem)
+                                         : pairs_f32_ctas_per_sm(p, S.ipt, smem);
+    if (per_sm <= 0)
+        return fail(PC_ECUDA, std::string("pair kernel cannot be resident: ") + pc_last_error());
+    if (S.o.grid_ctas_per_sm > 0) per_sm = std::min(per_sm, S.o.grid_ctas_per_sm);
+    grid = dev_sms * per_sm;
+    return PC_OK;
+}
 
-    if (stats) cudaEventRecord(ev[2], st);
-    cudaError_t e = (prec == PC_PREC_F64) ? launch_pairs_f64(p, grid, smem, st)
-                                          : launch_pairs_f32(p, ipt, grid, smem, st);
+// Device work of one count, in stream order (also what a captured graph
+// replays): clear, block list, pair kernel, rescue kernel.
+static pc_status enqueue_count(const CountSetup &S, const DevBufs &B, const PairParams &p, int grid,
+                               size_t smem, cudaStream_t st, cudaEvent_t ev_pairs,
+                               cudaEvent_t ev_rescue, cudaEvent_t ev_done) {
+    PC_CUDA(cudaMemsetAsync(B.hist, 0, sizeof(unsigned long long) * S.hist_n, st));
+    if (S.weighted) PC_CUDA(cudaMemsetAsync(B.whist, 0, sizeof(double) * S.hist_n, st));
+    PC_CUDA(cudaMemsetAsync(B.ctr, 0, sizeof(unsigned long long) * 4, st));
+    PC_CUDA(cudaMemsetAsync(B.sc, 0, sizeof(int) * 4, st));
+    PC_CUDA(make_blocks_into(B.tasks, S.ntasks, S.ncell, S.bi, B.blocks, B.sc + 1, B.cnt, B.off,
+                             B.tot, st));
+    if (ev_pairs) PC_CUDA(cudaEventRecord(ev_pairs, st));
+    cudaError_t e = (S.prec == PC_PREC_F64) ? launch_pairs_f64(p, grid, smem, st)
+                                            : launch_pairs_f32(p, S.ipt, grid, smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "pair kernel launch");
-    if (stats) cudaEventRecord(ev[3], st);
-    if (prec == PC_PREC_F32_RESCUE && qcap) {
+    if (ev_rescue) PC_CUDA(cudaEventRecord(ev_rescue, st));
+    if (S.prec == PC_PREC_F32_RESCUE && S.qcap) {
         e = launch_rescue(p, st);
         if (e != cudaSuccess) return cuda_fail(e, "rescue kernel launch");
     }
-    if (stats) cudaEventRecord(ev[4], st);
+    if (ev_done) PC_CUDA(cudaEventRecord(ev_done, st));
+    return PC_OK;
+}
 
-    // results
-    if (counts) {
-        cudaMemcpyKind k = is_device_ptr(counts) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-        PC_CUDA(cudaMemcpyAsync(counts, W.hist.p, sizeof(long long) * hist_n, k, st));
+static void copy_out(void *dst, const void *src, size_t bytes, cudaStream_t st, cudaError_t &e) {
+    if (!dst || e != cudaSuccess) return;
+    cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    e = cudaMemcpyAsync(dst, src, bytes, k, st);
+}
+
+static void fill_stats(pc_stats *stats, const CountSetup &S, const pc_grid *g0,
+                       const unsigned long long hc[3], int hblk, float ms_total, float ms_pairs,
+                       float ms_rescue, long long launches) {
+    if (!stats) return;
+    memset(stats, 0, sizeof(*stats));
+    stats->candidates = (long long)hc[0];
+    stats->rescue_inline = (long long)hc[1];
+    stats->rescued = (long long)std::min<unsigned long long>(hc[2], S.qcap) + (long long)hc[1];
+    stats->blocks = hblk;
+    stats->cell_size = g0->cell_size;
+    stats->ms_total = ms_total;
+    stats->ms_pairs = ms_pairs;
+    stats->ms_rescue = ms_rescue;
+    stats->launches = (int)launches;
+}
+
+struct Events {
+    cudaEvent_t e[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool on = false;
+    explicit Events(bool want) : on(want) {
+        if (on) for (auto &x : e) cudaEventCreate(&x);
     }
-    if (wcounts) {
-        cudaMemcpyKind k = is_device_ptr(wcounts) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-        PC_CUDA(cudaMemcpyAsync(wcounts, W.whist.p, sizeof(double) * hist_n, k, st));
+    ~Events() {
+        if (on) for (auto &x : e) cudaEventDestroy(x);
     }
+    float ms(int a, int b) const {
+        float m = 0.f;
+        if (on) cudaEventElapsedTime(&m, e[a], e[b]);
+        return m;
+    }
+};
+
+static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *opt,
+                           cudaStream_t st, long long *counts, double *wcounts, pc_stats *stats) {
+    CountSetup S;
+    pc_status s = setup_count(J, b, opt, wcounts != nullptr, S);
+    if (s != PC_OK) return s;
+    DevBufs B;
+    s = ensure_bufs(workspace(S.dev), S, B);
+    if (s != PC_OK) return s;
+    PairParams p;
+    int grid = 0;
+    size_t smem = 0;
+    s = make_params(J, S, B, p, grid, smem);
+    if (s != PC_OK) return s;
+    Events ev(stats != nullptr);
+    const long long launches0 = launch_count();
+    if (ev.on) PC_CUDA(cudaEventRecord(ev.e[0], st));
+    s = upload_tables(J, S, B, st);
+    if (s != PC_OK) return s;
+    s = enqueue_count(S, B, p, grid, smem, st, ev.e[1], ev.e[2], ev.e[3]);
+    if (s != PC_OK) return s;
+    cudaError_t e = cudaSuccess;
+    copy_out(counts, B.hist, sizeof(long long) * S.hist_n, st, e);
+    copy_out(wcounts, B.whist, sizeof(double) * S.hist_n, st, e);
+    if (e != cudaSuccess) return cuda_fail(e, "result copy");
     unsigned long long hc[3] = {0, 0, 0};
     int hblk = 0;
-    if (stats) {
-        PC_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
-        PC_CUDA(cudaMemcpyAsync(&hblk, sc + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-        cudaEventRecord(ev[1], st);
+    if (ev.on) {
+        PC_CUDA(cudaMemcpyAsync(hc, B.ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        PC_CUDA(cudaMemcpyAsync(&hblk, B.sc + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PC_CUDA(cudaEventRecord(ev.e[4], st));
     }
     PC_CUDA(cudaStreamSynchronize(st));
-    if (stats) {
-        memset(stats, 0, sizeof(*stats));
-        stats->candidates = (long long)hc[0];
-        stats->rescue_inline = (long long)hc[1];
-        stats->rescued = (long long)std::min<unsigned long long>(hc[2], qcap) + (long long)hc[1];
-        stats->blocks = hblk;
-        stats->cell_size = g0->cell_size;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        stats->ms_total = ms;
-        cudaEventElapsedTime(&ms, ev[2], ev[3]);
-        stats->ms_pairs = ms;
-        cudaEventElapsedTime(&ms, ev[3], ev[4]);
-        stats->ms_rescue = ms;
-        stats->launches = (int)(launch_count() - launches0);
-        for (auto &x : ev) cudaEventDestroy(x);
+    fill_stats(stats, S, J.g0, hc, hblk, ev.ms(0, 4), ev.ms(1, 2), ev.ms(2, 3),
+               launch_count() - launches0);
+    return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// captured count graphs (pc_count_batch with use_graph)
+// ---------------------------------------------------------------------------
+// A graph owns its buffers: the shared workspace may be reallocated by other
+// calls, and a graph must keep the addresses it was captured with.
+struct GraphEntry {
+    int dev = 0;
+    std::vector<const pc_grid *> grids;
+    int mode = 0, los = 0;
+    std::vector<double> ea, eb;
+    pc_opts o;
+    bool weighted = false;
+    Workspace W;
+    CountSetup S;
+    DevBufs B;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long *h_hist = nullptr;   // pinned copies written by the graph
+    double *h_whist = nullptr;
+    unsigned long long *h_ctr = nullptr;
+    int *h_blocks = nullptr;
+    long long kernels = 0;                  // kernel launches inside the graph
+    ~GraphEntry() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaFreeHost(h_hist);
+        cudaFreeHost(h_whist);
+        cudaFreeHost(h_ctr);
+        cudaFreeHost(h_blocks);
+        for (Buf *b : {&W.hist, &W.whist, &W.counters, &W.scalars, &W.queue, &W.blocks, &W.tmp_cnt,
+                       &W.tmp_off, &W.tmp_tot, &W.tasks, &W.stencil, &W.lut, &W.ea, &W.eb})
+            if (b->p) cudaFree(b->p);
     }
+};
+
+static std::vector<std::unique_ptr<GraphEntry>> &graph_cache() {
+    static std::vector<std::unique_ptr<GraphEntry>> c;
+    return c;
+}
+
+// Drop every cached graph that uses grid g (called when g is freed).
+void forget_grid(const pc_grid *g) {
+    auto &c = graph_cache();
+    for (size_t k = 0; k < c.size();) {
+        bool uses = false;
+        for (auto *x : c[k]->grids) uses = uses || (x == g);
+        if (uses) c.erase(c.begin() + k); else ++k;
+    }
+}
+
+static bool same_opts(const pc_opts &a, const pc_opts &b) {
+    return a.prec == b.prec && a.cell_size == b.cell_size && a.ipt == b.ipt && a.priv == b.priv &&
+           a.rescue_capacity == b.rescue_capacity && a.grid_ctas_per_sm == b.grid_ctas_per_sm;
+}
+
+static pc_status run_count_graph(const CountJob &J, const std::vector<const pc_grid *> &grids,
+                                 const pc_bins *b, const pc_opts *opt, cudaStream_t st,
+                                 long long *counts, double *wcounts, pc_stats *stats) {
+    pc_opts o;
+    memset(&o, 0, sizeof(o));
+    o.priv = -1;
+    if (opt) o = *opt;
+    const bool weighted = wcounts != nullptr;
+    if (!b || !b->edges_a || (b->mode != PC_BIN_S && !b->edges_b))
+        return fail(PC_EINVAL, "bins: missing edges");
+    std::vector<double> ea(b->edges_a, b->edges_a + std::max(b->n_a, 0) + 1);
+    std::vector<double> eb;
+    if (b->mode != PC_BIN_S) eb.assign(b->edges_b, b->edges_b + std::max(b->n_b, 0) + 1);
+    GraphEntry *G = nullptr;
+    for (auto &c : graph_cache())
+        if (c->dev == J.g0->device && c->grids == grids && c->mode == b->mode && c->los == b->los &&
+            c->ea == ea && c->eb == eb && same_opts(c->o, o) && c->weighted == weighted)
+            G = c.get();
+    const long long launches0 = launch_count();
+    if (!G) {
+        std::unique_ptr<GraphEntry> N(new GraphEntry());
+        N->dev = J.g0->device;
+        N->grids = grids;
+        N->mode = b->mode;
+        N->los = b->los;
+        N->ea = ea;
+        N->eb = eb;
+        N->o = o;
+        N->weighted = weighted;
+        pc_status s = setup_count(J, b, &o, weighted, N->S);
+        if (s != PC_OK) return s;
+        s = ensure_bufs(N->W, N->S, N->B);
+        if (s != PC_OK) return s;
+        PairParams p;
+        int grid = 0;
+        size_t smem = 0;
+        s = make_params(J, N->S, N->B, p, grid, smem);
+        if (s != PC_OK) return s;
+        const size_t hb = N->S.hist_n;
+        PC_CUDA(cudaMallocHost(&N->h_hist, sizeof(unsigned long long) * hb));
+        if (weighted) PC_CUDA(cudaMallocHost(&N->h_whist, sizeof(double) * hb));
+        PC_CUDA(cudaMallocHost(&N->h_ctr, sizeof(unsigned long long) * 4));
+        PC_CUDA(cudaMallocHost(&N->h_blocks, sizeof(int)));
+        cudaStream_t cap = nullptr;
+        PC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        s = upload_tables(J, N->S, N->B, cap);
+        if (s == PC_OK) {
+            cudaError_t e = cudaStreamSynchronize(cap);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) s = cuda_fail(e, "graph capture");
+        }
+        if (s == PC_OK) {
+            const long long k0 = launch_count();
+            s = enqueue_count(N->S, N->B, p, grid, smem, cap, nullptr, nullptr, nullptr);
+            N->kernels = launch_count() - k0;
+            cudaError_t e = cudaSuccess;
+            if (s == PC_OK) {
+                e = cudaMemcpyAsync(N->h_hist, N->B.hist, sizeof(unsigned long long) * hb,
+                                    cudaMemcpyDeviceToHost, cap);
+                if (e == cudaSuccess && weighted)
+                    e = cudaMemcpyAsync(N->h_whist, N->B.whist, sizeof(double) * hb,
+                                        cudaMemcpyDeviceToHost, cap);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(N->h_ctr, N->B.ctr, sizeof(unsigned long long) * 4,
+                                        cudaMemcpyDeviceToHost, cap);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(N->h_blocks, N->B.sc + 1, sizeof(int),
+                                        cudaMemcpyDeviceToHost, cap);
+            }
+            cudaError_t e2 = cudaStreamEndCapture(cap, &N->graph);
+            if (s == PC_OK && e != cudaSuccess) s = cuda_fail(e, "graph capture copy");
+            if (s == PC_OK && e2 != cudaSuccess) s = cuda_fail(e2, "graph capture end");
+            if (s == PC_OK) {
+                e = cudaGraphInstantiate(&N->exec, N->graph, 0);
+                if (e != cudaSuccess) s = cuda_fail(e, "graph instantiate");
+            }
+        }
+        cudaStreamDestroy(cap);
+        if (s != PC_OK) return s;
+        graph_cache().push_back(std::move(N));
+        G = graph_cache().back().get();
+    }
+    Events ev(stats != nullptr);
+    if (ev.on) PC_CUDA(cudaEventRecord(ev.e[0], st));
+    PC_CUDA(cudaGraphLaunch(G->exec, st));
+    note_launch((int)G->kernels);   // a replay launches the captured kernels again
+    if (ev.on) PC_CUDA(cudaEventRecord(ev.e[4], st));
+    PC_CUDA(cudaStreamSynchronize(st));
+    const size_t hb = G->S.hist_n;
+    cudaError_t e = cudaSuccess;
+    if (counts) {
+        if (is_device_ptr(counts))
+            e = cudaMemcpy(counts, G->h_hist, sizeof(long long) * hb, cudaMemcpyHostToDevice);
+        else
+            memcpy(counts, G->h_hist, sizeof(long long) * hb);
+    }
+    if (wcounts && e == cudaSuccess) {
+        if (is_device_ptr(wcounts))
+            e = cudaMemcpy(wcounts, G->h_whist, sizeof(double) * hb, cudaMemcpyHostToDevice);
+        else
+            memcpy(wcounts, G->h_whist, sizeof(double) * hb);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "result copy");
+    unsigned long long hc[3] = {G->h_ctr[0], G->h_ctr[1], G->h_ctr[2]};
+    fill_stats(stats, G->S, J.g0, hc, *G->h_blocks, ev.ms(0, 4), 0.f, 0.f,
+               launch_count() - launches0);
     return PC_OK;
 }
 
@@ -667,6 +920,10 @@ extern "C" pc_status pc_count_batch(const pc_grid *const *gs, int m, const pc_bi
     J.nhist = m;
     J.is_auto = true;
     J.g0 = gs[0];
+    if (o && o->use_graph) {
+        std::vector<const pc_grid *> grids(gs, gs + m);
+        return run_count_graph(J, grids, b, o, (cudaStream_t)stream, counts, wcounts, st);
+    }
     return run_count(J, b, o, (cudaStream_t)stream, counts, wcounts, st);
 }
 

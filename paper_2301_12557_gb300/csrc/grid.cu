@@ -352,6 +352,7 @@ static void grid_release(pc_grid *g) {
 
 extern "C" void pc_free_grid(pc_grid *g) {
     std::lock_guard<std::mutex> lk(api_mutex());
+    if (g) forget_grid(g);
     grid_release(g);
 }
 

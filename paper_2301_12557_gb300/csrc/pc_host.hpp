@@ -46,6 +46,9 @@ cudaError_t make_blocks_into(const TaskDev *tasks_dev, int ntasks, int ncell, in
                              Block *blocks, int *nblocks_dev, int *tmp_counts, int *tmp_offsets,
                              int *tmp_tot, cudaStream_t st);
 
+// Forget cached count graphs that use grid g (the grid is being freed).
+void forget_grid(const pc_grid *g);
+
 // Device-side bounding box; lo/hi are host arrays (the call synchronises).
 pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *lo, double *hi);
 

@@ -234,6 +234,33 @@ def test_batch_matches_per_mock_oracle():
         _check(c[k], w, what=f"mock {k}")
 
 
+def test_batch_graph_replay_matches_and_survives_free():
+    mocks = synth.batch_mocks(5, 1200, 3000, 3.0, 8.0, 300.0, 225)
+    ea = np.linspace(0.0, 40.0, 21)
+    mu = np.linspace(0.0, 1.0, 11)
+    bins = P.Bins("smu", "z", ea, mu)
+    box = P.make_box(300.0, True)
+    opts = P.make_opts("f32", 20.0)
+    opts.use_graph = 1
+    grids = [P.pc_build_grid(m, box=box, r_max=bins.r_max, opts=opts) for m in mocks]
+    want = np.concatenate([oracle.count(m, box=300.0, periodic=True, mode="smu", edges_a=ea,
+                                        edges_b=mu, method="grid")[0] for m in mocks])
+    for _ in range(3):   # capture once, then replay
+        c, _, st = P.pc_count_batch(grids, bins, opts)
+        _check(c, want, what="graph batch")
+        assert st.launches >= 3
+    dev = torch.zeros(bins.nbins * len(mocks), dtype=torch.int64, device="cuda")
+    P.pc_count_batch(grids, bins, opts, counts=dev)
+    _check(dev.cpu().numpy(), want, what="graph batch, device output")
+    grids[2].free()          # drops the cached graph that uses it
+    rest = [g for k, g in enumerate(grids) if k != 2]
+    c, _, _ = P.pc_count_batch(rest, bins, opts)
+    want_rest = np.concatenate([want.reshape(len(mocks), -1)[k] for k in range(len(mocks)) if k != 2])
+    _check(c, want_rest, what="graph batch after free")
+    for g in rest:
+        g.free()
+
+
 def test_errors_are_reported():
     L = 100.0
     x = synth.uniform_box(100, L, 231)
