@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cell-size", type=float, default=0.0)
     ap.add_argument("--ipt", type=int, default=0)
+    ap.add_argument("--shard", action="store_true",
+                    help="with --gpus N > 1: split one catalogue's point blocks across the ranks "
+                         "and sum the histograms once at the end (strong scaling) instead of "
+                         "one independent catalogue per rank (replicas, weak scaling)")
     ap.add_argument("--volume-scale", type=float, default=1.0,
                     help="same density in a box of this fraction of the volume "
                          "(small cases for profiling; 1 = the full workload)")
@@ -242,7 +246,7 @@ def run_ours(args):
     P.lib()
     w = W.WORKLOADS[args.workload]
     D_host, L_box = workload_inputs(w, args.volume_scale)
-    if world > 1 and rank > 0:
+    if world > 1 and rank > 0 and not args.shard:
         # replicas: every rank counts its own independent catalogue
         from synth import catalogs as C
         D_host = C.neyman_scott(D_host.shape[0], w.extra["parents"], w.extra["children"],
@@ -253,6 +257,9 @@ def run_ours(args):
     bins = P.Bins(w.mode, w.los, w.edges_a, w.edges_b)
     box = P.make_box(L_box, w.periodic)
     opts = P.make_opts("f32", args.cell_size, args.ipt)
+    if args.shard and world > 1:
+        from paper_2301_12557_gb300 import shard
+        shard.shard_opts(opts, rank, world)
     out = torch.zeros(bins.nbins, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -298,6 +305,9 @@ def run_ours(args):
     t_max = float(t_local.item())
     cand_all = float(cand_local.item())
     value = cand_all / (t_max * 1e-3)
+    if args.shard and dist is not None:
+        from paper_2301_12557_gb300 import shard
+        out = shard.sum_histograms(out)      # the one collective: the final histogram sum
     counts = out.cpu().numpy()
 
     # ---- e2e: host buffers through the same ABI, copies inside the region --
@@ -373,16 +383,20 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong" if (args.shard and world > 1) else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name if args.volume_scale == 1.0 else
                        f"{w.name} at volume x{args.volume_scale}", "n": int(n),
                        "box": L_box, "bins": "s 40 x mu 100 (LOS z)",
                        "precision": "FP32 separations, binary64 rescue near bin edges, int64 counts",
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "parallelism": (f"block shards x{world} + one histogram sum"
+                                       if args.shard else f"replicas x{world}")
+                                      if world > 1 else "1 GPU",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "cell_size": s0.cell_size, "in_range_pairs": int(counts.sum()),
                        "candidates_per_step": int(s0.candidates)},
-            "in_range_pairs_per_s": float(counts.sum()) * world / (t_max / args.steps * 1e-3),
+            "in_range_pairs_per_s": float(counts.sum()) * (1 if args.shard else world)
+                                    / (t_max / args.steps * 1e-3),
             "rescued_fraction": s0.rescued / max(1, int(counts.sum())),
             "fp64_path": fp64,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,

@@ -92,6 +92,9 @@ typedef struct {
     long long rescue_capacity;   /* rescue-queue slots; 0 = auto; < 0 = none (all inline) */
     int use_graph;               /* pc_count_batch: replay a captured CUDA graph */
     int grid_ctas_per_sm;        /* persistent CTAs per SM; 0 = occupancy limit */
+    int shard_index;             /* with shard_count > 1: count only the i-blocks whose */
+    int shard_count;             /* index % shard_count == shard_index (multi-GPU shards;
+                                    the int64 counts of all shards sum to the full count) */
 } pc_opts;
 
 /* Counters of the last count call (all optional). */

@@ -47,7 +47,7 @@ class pc_bins(ctypes.Structure):
 class pc_opts(ctypes.Structure):
     _fields_ = [("prec", c_int), ("cell_size", c_double), ("ipt", c_int), ("priv", c_int),
                 ("rescue_capacity", c_longlong), ("use_graph", c_int),
-                ("grid_ctas_per_sm", c_int)]
+                ("grid_ctas_per_sm", c_int), ("shard_index", c_int), ("shard_count", c_int)]
 
 
 class pc_stats(ctypes.Structure):
@@ -233,7 +233,7 @@ class Bins:
 
 
 def make_opts(prec="f32", cell_size=0.0, ipt=0, priv=-1, rescue_capacity=0, use_graph=0,
-              grid_ctas_per_sm=0) -> pc_opts:
+              grid_ctas_per_sm=0, shard_index=0, shard_count=0) -> pc_opts:
     o = pc_opts()
     o.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
     o.cell_size = float(cell_size)
@@ -242,6 +242,8 @@ def make_opts(prec="f32", cell_size=0.0, ipt=0, priv=-1, rescue_capacity=0, use_
     o.rescue_capacity = int(rescue_capacity)
     o.use_graph = int(use_graph)
     o.grid_ctas_per_sm = int(grid_ctas_per_sm)
+    o.shard_index = int(shard_index)
+    o.shard_count = int(shard_count)
     return o
 
 

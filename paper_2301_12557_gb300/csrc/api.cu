@@ -425,6 +425,8 @@ static pc_status setup_count(const CountJob &J, const pc_bins *b, const pc_opts 
     memset(&S.o, 0, sizeof(S.o));
     S.o.priv = -1;
     if (opt) S.o = *opt;
+    if (S.o.shard_count > 1 && (S.o.shard_index < 0 || S.o.shard_index >= S.o.shard_count))
+        return fail(PC_EINVAL, "opts: shard_index must lie in [0, shard_count)");
     const pc_grid *g0 = J.g0;
     pc_status s = make_plan(b, g0->g, g0->pts_lo, g0->pts_hi, J.is_auto, S.P);
     if (s != PC_OK) return s;
@@ -547,6 +549,8 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     p.qcount = B.ctr + 2;
     p.qcap = S.qcap;
     p.counters = B.ctr;
+    p.shard_count = S.o.shard_count > 1 ? S.o.shard_count : 1;
+    p.shard_index = S.o.shard_count > 1 ? S.o.shard_index : 0;
     // histogram privatisation: one copy per warp when it fits and helps
     int copies_warp = P.nbins * (NT / 32) * 4;
     if (S.o.priv == 0 || S.o.priv == 1) p.priv = S.o.priv;
@@ -734,7 +738,8 @@ void forget_grid(const pc_grid *g) {
 
 static bool same_opts(const pc_opts &a, const pc_opts &b) {
     return a.prec == b.prec && a.cell_size == b.cell_size && a.ipt == b.ipt && a.priv == b.priv &&
-           a.rescue_capacity == b.rescue_capacity && a.grid_ctas_per_sm == b.grid_ctas_per_sm;
+           a.rescue_capacity == b.rescue_capacity && a.grid_ctas_per_sm == b.grid_ctas_per_sm &&
+           a.shard_index == b.shard_index && a.shard_count == b.shard_count;
 }
 
 static pc_status run_count_graph(const CountJob &J, const std::vector<const pc_grid *> &grids,
@@ -1082,6 +1087,8 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
     o.priv = -1;
     if (opt) o = *opt;
 
+    if (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count))
+        return fail(PC_EINVAL, "opts: shard_index must lie in [0, shard_count)");
     Plan P;
     pc_status s = make_plan(b, g->g, g->pts_lo, g->pts_hi, true, P);
     if (s != PC_OK) return s;
@@ -1165,6 +1172,8 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
     p.qcount = ctr + 2;
     p.qcap = (prec == PC_PREC_F32_RESCUE) ? NA_QUEUE : 0;
     p.counters = ctr;
+    p.shard_count = o.shard_count > 1 ? o.shard_count : 1;
+    p.shard_index = o.shard_count > 1 ? o.shard_index : 0;
     int copies_warp = P.nbins * (NT / 32) * 4;
     if (o.priv == 0 || o.priv == 1) p.priv = o.priv;
     else p.priv = (P.nbins <= 2048 && copies_warp <= 48 * 1024) ? 1 : 0;

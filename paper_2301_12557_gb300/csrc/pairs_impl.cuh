@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     __syncthreads();
 
     for (;;) {
-        if (tid == 0) cs.blk = atomicAdd(p.work_counter, 1);
+        if (tid == 0) cs.blk = atomicAdd(p.work_counter, 1) * p.shard_count + p.shard_index;
         __syncthreads();
         const int bidx = cs.blk;
         if (bidx >= nblocks) break;
@@ -906,7 +906,7 @@ __global__ void __launch_bounds__(NT) k_pairs_f64(const __grid_constant__ PairPa
     __syncthreads();
 
     for (;;) {
-        if (tid == 0) cs.blk = atomicAdd(p.work_counter, 1);
+        if (tid == 0) cs.blk = atomicAdd(p.work_counter, 1) * p.shard_count + p.shard_index;
         __syncthreads();
         const int bidx = cs.blk;
         if (bidx >= nblocks) break;

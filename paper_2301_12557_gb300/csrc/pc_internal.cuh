@@ -88,6 +88,7 @@ struct PairParams {
     unsigned long long *qcount;  // device scalar
     unsigned long long qcap;
     unsigned long long *counters;  // [0] candidates, [1] inline rescues
+    int shard_index, shard_count;   // this launch counts blocks index * count + shard
     int priv;                // 0: one histogram per CTA; 1: one per warp
     int smem_hist_ok;        // histogram fits in shared memory
     // evenly spaced s (and mu) edges: bins by floor instead of tables

@@ -261,6 +261,35 @@ def test_batch_graph_replay_matches_and_survives_free():
         g.free()
 
 
+@pytest.mark.parametrize("nshard", [2, 3])
+def test_block_shards_sum_to_the_full_count(nshard):
+    """Multi-GPU shards (pc_opts.shard_index/count) run one after the other on
+    one GPU; their int64 histograms must sum to the unsharded count."""
+    L = 150.0
+    x = synth.neyman_scott(9000, 900, 10.0, 3.0, L, 241)
+    y = synth.uniform_box(5000, L, 242)
+    bins = P.Bins("smu", "z", np.linspace(0.0, 30.0, 16), np.linspace(0.0, 1.0, 11))
+    box = P.make_box(L, True)
+    o = P.make_opts("f32", 10.0)
+    gx = P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=o)
+    gy = P.pc_build_grid(y, box=box, r_max=bins.r_max, opts=o)
+    full_a, _, _ = P.pc_count_auto(gx, bins, o)
+    full_c, _, _ = P.pc_count_cross(gx, gy, bins, o)
+    part_a = np.zeros_like(full_a)
+    part_c = np.zeros_like(full_c)
+    for r in range(nshard):
+        so = P.make_opts("f32", 10.0, shard_index=r, shard_count=nshard)
+        part_a += P.pc_count_auto(gx, bins, so)[0]
+        part_c += P.pc_count_cross(gx, gy, bins, so)[0]
+    gx.free()
+    gy.free()
+    assert np.array_equal(part_a, full_a)
+    assert np.array_equal(part_c, full_c)
+    w, _ = oracle.count(x, box=L, periodic=True, mode="smu", edges_a=bins.ea, edges_b=bins.eb,
+                        method="grid")
+    _check(full_a, w, what="unsharded")
+
+
 def test_errors_are_reported():
     L = 100.0
     x = synth.uniform_box(100, L, 231)
