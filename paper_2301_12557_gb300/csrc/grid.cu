@@ -91,31 +91,60 @@ __device__ __forceinline__ int cell_axis(double x, double lo, double c, int ng) 
     return (int)f;
 }
 
-__global__ void k_cell_ids(const double *__restrict__ xyz, int n, Geom g, int *__restrict__ cell,
-                           int *__restrict__ slot, int *__restrict__ counts) {
+// Sort key of a point: its cell, then (with sub_bits > 0) the Morton code of
+// its sub-cell inside the cell, 2^sub_bits sub-cells per axis.  Points of one
+// cell stay contiguous and neighbouring points end up close in memory, so a
+// warp's consecutive points (and consecutive j-points) are spatially compact.
+__device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z, int bits) {
+    unsigned m = 0;
+    for (int b = 0; b < bits; ++b)
+        m |= (((x >> b) & 1u) << (3 * b)) | (((y >> b) & 1u) << (3 * b + 1)) |
+             (((z >> b) & 1u) << (3 * b + 2));
+    return m;
+}
+
+__global__ void k_cell_ids(const double *__restrict__ xyz, int n, Geom g, int sub_bits,
+                           int *__restrict__ cell, int *__restrict__ slot,
+                           int *__restrict__ counts) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int id[3];
+    unsigned sub[3];
+    const int S = 1 << sub_bits;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double x = xyz[3 * (size_t)i + a];
         if (g.periodic) x = canon(x, g.L[a]);
         id[a] = cell_axis(x, g.lo[a], g.c[a], g.ng[a]);
+        double f = __ddiv_rn(__dsub_rn(__dsub_rn(x, g.lo[a]), __dmul_rn((double)id[a], g.c[a])), g.c[a]);
+        int sa = (int)floor(f * S);
+        sub[a] = (unsigned)min(max(sa, 0), S - 1);
     }
     int c = (id[2] * g.ng[1] + id[1]) * g.ng[0] + id[0];
-    cell[i] = c;
-    slot[i] = atomicAdd(&counts[c], 1);
+    int key = (c << (3 * sub_bits)) | (int)morton3(sub[0], sub[1], sub[2], sub_bits);
+    cell[i] = key;
+    slot[i] = atomicAdd(&counts[key], 1);
+}
+
+// Cell starts from the starts of the sorted keys.
+__global__ void k_cell_starts(const int *__restrict__ key_start, int ncell, int sub_bits,
+                              int *__restrict__ cell_start) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ncell) return;
+    cell_start[c] = key_start[(size_t)c << (3 * sub_bits)];
 }
 
 __global__ void k_scatter(const double *__restrict__ xyz, const void *__restrict__ w, int w_is_f32,
-                          int n, Geom g, const int *__restrict__ cell, const int *__restrict__ slot,
-                          const int *__restrict__ cell_start, float4 *__restrict__ rel,
+                          int n, Geom g, int sub_bits, const int *__restrict__ cell,
+                          const int *__restrict__ slot, const int *__restrict__ key_start,
+                          float4 *__restrict__ rel,
                           uint16_t *__restrict__ cxo, double4_32a *__restrict__ xw,
                           int *__restrict__ perm) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int c = cell[i];
-    int pos = cell_start[c] + slot[i];
+    int key = cell[i];
+    int pos = key_start[key] + slot[i];
+    int c = key >> (3 * sub_bits);
     int id[3] = {c % g.ng[0], (c / g.ng[0]) % g.ng[1], c / (g.ng[0] * g.ng[1])};
     double x[3];
     float r[3];
@@ -520,25 +549,39 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
         cudaGetLastError();
         return fail(PC_ENOMEM, "pc_build_grid: device allocation failed");
     }
-    int *counts = nullptr, *cell = nullptr, *slot = nullptr;
-    e = cudaMallocAsync(&counts, sizeof(int) * g->ncell, st);
+    // sub-cell order inside cells: 8 or 64 Morton sub-cells when cells hold
+    // enough points for them to matter
+    const double per_cell = (double)n / g->ncell;
+    int sub_bits = per_cell >= 128.0 ? 2 : (per_cell >= 16.0 ? 1 : 0);
+    while (sub_bits > 0 && ((long long)g->ncell << (3 * sub_bits)) > (1LL << 28)) --sub_bits;
+    const int nkey = g->ncell << (3 * sub_bits);
+    int *counts = nullptr, *cell = nullptr, *slot = nullptr, *key_start = nullptr;
+    e = cudaMallocAsync(&counts, sizeof(int) * nkey, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&key_start, sizeof(int) * ((size_t)nkey + 1), st);
     if (e == cudaSuccess) e = cudaMallocAsync(&cell, sizeof(int) * nn, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&slot, sizeof(int) * nn, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int) * g->ncell, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int) * nkey, st);
     if (e == cudaSuccess && n > 0) {
         int blocks = (int)((n + 255) / 256);
-        k_cell_ids<<<blocks, 256, 0, st>>>(dxyz, (int)n, G, cell, slot, counts);
+        k_cell_ids<<<blocks, 256, 0, st>>>(dxyz, (int)n, G, sub_bits, cell, slot, counts);
         note_launch();
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = scan_exclusive(counts, g->cell_start, g->ncell, st);
-    if (e == cudaSuccess && n > 0) {
-        int blocks = (int)((n + 255) / 256);
-        k_scatter<<<blocks, 256, 0, st>>>(dxyz, dw, w_is_f32, (int)n, G, cell, slot, g->cell_start,
-                                          g->rel, g->cx, g->xw, g->perm);
+    if (e == cudaSuccess) e = scan_exclusive(counts, key_start, nkey, st);
+    if (e == cudaSuccess) {
+        k_cell_starts<<<(g->ncell + 1 + 255) / 256, 256, 0, st>>>(key_start, g->ncell, sub_bits,
+                                                                  g->cell_start);
         note_launch();
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && n > 0) {
+        int blocks = (int)((n + 255) / 256);
+        k_scatter<<<blocks, 256, 0, st>>>(dxyz, dw, w_is_f32, (int)n, G, sub_bits, cell, slot,
+                                          key_start, g->rel, g->cx, g->xw, g->perm);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (key_start) cudaFreeAsync(key_start, st);
     if (counts) cudaFreeAsync(counts, st);
     if (cell) cudaFreeAsync(cell, st);
     if (slot) cudaFreeAsync(slot, st);

@@ -729,10 +729,12 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
         const unsigned task_bits = (unsigned)B.task << 5;
         const int ax = B.cell % nx, ay = (B.cell / nx) % ny, az = B.cell / (nx * ny);
 
+        // thread t holds the block's points RI t .. RI t + RI - 1: a warp covers
+        // 32 RI consecutive (sub-cell ordered, so spatially compact) points
         IPts<RI> I;
 #pragma unroll
         for (int r = 0; r < RI; ++r) {
-            const int loc = tid + r * NT;
+            const int loc = RI * tid + r;
             I.idx[r] = B.start + loc;
             I.xa[r] = I.ya[r] = I.za[r] = 0.f;
             I.w[r] = 0.0;
