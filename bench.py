@@ -34,8 +34,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "pairs evaluated/sec on 1 GB300, FP32+FP64-rescue vs plain FP64 at exact counts"
-UNIT = "pairs/s"
-FLOPS_PER_CANDIDATE = 8       # 3 subtractions, 3 multiplies, 2 adds
+UNIT = "pairs/s"                 # in-range pairs binned per second (every arm)
+FLOPS_PER_CANDIDATE = 8          # separation: 3 subtractions, 3 multiplies, 2 adds
+FLOPS_PER_IN_RANGE = 6           # bin locate per in-range pair
 FP32_LANES_PER_SM = 128
 
 
@@ -155,8 +156,10 @@ class ClockSampler:
 # CPU oracle on a bounded sample
 # --------------------------------------------------------------------------
 def oracle_sample_rate(D, w, seconds, seed=0, L=None):
-    """Brute-force oracle pairs/s: all pairs of a random sample of i-points
-    against the whole catalogue (the cross form of the same pair set)."""
+    """Oracle throughput in in-range pairs binned per second: brute force over
+    all pairs of a random sample of i-points against the whole catalogue (the
+    cross form of the same pair set), self-pairs excluded.  Returns (rate,
+    seconds, sample size, cores, pair evaluations per second)."""
     import oracle
     oracle.build()
     rng = np.random.default_rng(seed)
@@ -175,10 +178,11 @@ def oracle_sample_rate(D, w, seconds, seed=0, L=None):
     m = int(max(1, min(n, m0 * seconds / dt)))
     S = np.ascontiguousarray(D[rng.choice(n, m, replace=False)])
     t = time.perf_counter()
-    oracle.count(S, D, **kw)
+    c, _ = oracle.count(S, D, **kw)
     dt = time.perf_counter() - t
     cores = oracle.default_threads()
-    return m * n / dt, dt, m, cores
+    in_range = int(c.sum()) - m        # each sampled point pairs with itself at s = 0
+    return in_range / dt, dt, m, cores, m * n / dt
 
 
 def traffic_record():
@@ -209,7 +213,7 @@ def run_reference(args):
     rates = []
     samp = None
     for k in range(args.warmup + args.steps):
-        r, dt, m, cores = oracle_sample_rate(D, w, per_step, seed=k)
+        r, dt, m, cores, _ = oracle_sample_rate(D, w, per_step, seed=k)
         if k >= args.warmup:
             rates.append((r, dt, m))
         samp = (m, cores)
@@ -217,7 +221,7 @@ def run_reference(args):
     tot_t = sum(dt for _, dt, _ in rates)
     value = tot_pairs / tot_t
     sample = (f"{samp[0]} random i-points x all {D.shape[0]} points per step "
-              f"(brute force, binary64)")
+              f"(brute force, binary64); in-range pairs found per second")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -256,13 +260,22 @@ def run_ours(args):
     D = torch.from_numpy(D_host).to(dev)
     bins = P.Bins(w.mode, w.los, w.edges_a, w.edges_b)
     box = P.make_box(L_box, w.periodic)
-    opts = P.make_opts("f32", args.cell_size, args.ipt)
+    stream = torch.cuda.current_stream()
+    tuning = None
+    if args.cell_size > 0 or args.ipt > 0:
+        opts = P.make_opts("f32", args.cell_size, args.ipt)
+    else:
+        # measured autotuning on this catalogue, once, before the timed steps
+        t0 = time.perf_counter()
+        opts, trials = P.pc_tune(D, box=box, bins=bins, stream=stream)
+        tuning = {"seconds": time.perf_counter() - t0,
+                  "trials": [{"cell_size": round(c, 3), "ipt": i, "priv": pv, "ms": round(ms, 3)}
+                             for c, i, pv, ms in trials]}
     if args.shard and world > 1:
         from paper_2301_12557_gb300 import shard
         shard.shard_opts(opts, rank, world)
     out = torch.zeros(bins.nbins, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
 
     def step(o=opts, x=D, counts=out):
         g = P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=o, stream=stream)
@@ -297,14 +310,18 @@ def run_ours(args):
     barrier()
     tot_ms = sum(a.elapsed_time(b) for a, b in ev)
     t_local = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-    cand_local = torch.tensor([float(sum(s.candidates for s in stats))], dtype=torch.float64,
-                              device=dev)
+    # every step bins the same pairs: this rank's in-range pairs (its shard's
+    # share under block shards) times the steps
+    inr_step = float(out.sum().item())
+    work_local = torch.tensor([inr_step * args.steps,
+                               float(sum(s.candidates for s in stats))],
+                              dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-        dist.all_reduce(cand_local, op=dist.ReduceOp.SUM)
+        dist.all_reduce(work_local, op=dist.ReduceOp.SUM)
     t_max = float(t_local.item())
-    cand_all = float(cand_local.item())
-    value = cand_all / (t_max * 1e-3)
+    inr_all, cand_all = (float(v) for v in work_local.tolist())
+    value = inr_all / (t_max * 1e-3)
     if args.shard and dist is not None:
         from paper_2301_12557_gb300 import shard
         out = shard.sum_histograms(out)      # the one collective: the final histogram sum
@@ -326,14 +343,16 @@ def run_ours(args):
             if k > 0:
                 e2e_ms.append(a.elapsed_time(b))
         assert np.array_equal(host_counts, counts), "host-buffer counts differ from device run"
-        e2e = {"value": st_e.candidates * world / (statistics.mean(e2e_ms) * 1e-3), "unit": UNIT,
+        e2e = {"value": inr_step * world / (statistics.mean(e2e_ms) * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(n * 3 * 8), "d2h_bytes_per_step": int(bins.nbins * 8),
                "ms_per_step": statistics.mean(e2e_ms)}
 
     # ---- plain FP64 path on the same GB300 -----------------------------------
     fp64 = None
     if args.fp64_steps > 0:
-        o64 = P.make_opts("f64", stats[0].cell_size, 1)
+        # the FP64 kernel has no group pruning: its own cost-model cell side
+        vol = float(np.prod(np.broadcast_to(np.asarray(L_box, dtype=np.float64), (3,))))
+        o64 = P.make_opts("f64", P.pc_suggest_cell_size(n, vol, bins.r_max), 1)
         out64 = torch.zeros_like(out)
         step(o=o64, counts=out64)
         torch.cuda.synchronize()
@@ -347,7 +366,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             ms64.append(a.elapsed_time(b))
         exact = bool(torch.equal(out64, out))
-        fp64 = {"value": s64.candidates / (statistics.mean(ms64) * 1e-3), "unit": UNIT,
+        fp64 = {"value": float(out64.sum().item()) / (statistics.mean(ms64) * 1e-3), "unit": UNIT,
+                "cell_size": o64.cell_size,
                 "ms_per_step": statistics.mean(ms64), "steps": args.fp64_steps,
                 "counts_identical_to_fp32_rescue": exact}
 
@@ -358,12 +378,18 @@ def run_ours(args):
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     ms_pairs = statistics.mean(s.ms_pairs for s in stats)
     cand = stats[0].candidates
-    achieved = FLOPS_PER_CANDIDATE * cand / (ms_pairs * 1e-3) / 1e12
+    evaluated = cand - stats[0].pruned       # pairs the kernel separated one by one
+    flops = FLOPS_PER_CANDIDATE * evaluated + FLOPS_PER_IN_RANGE * inr_step
+    achieved = flops / (ms_pairs * 1e-3) / 1e12
     trec = traffic_record()
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
                 "traffic": (trec["bytes_per_launch"] if trec else None),
                 "kernel": "k_pairs_f32<SMU,LOS_Z>",
+                "flops_per_launch": flops,
+                "flops_definition": (f"{FLOPS_PER_CANDIDATE} per pair evaluated one by one "
+                                     f"({evaluated:.4g}) + {FLOPS_PER_IN_RANGE} per in-range "
+                                     f"pair ({inr_step:.4g})"),
                 "peak_source": (f"FP32 non-tensor: {props.multi_processor_count} SMs x "
                                 f"{FP32_LANES_PER_SM} lanes x 2 flops x {sm_mhz:.0f} MHz "
                                 f"({peak_src} sm_max_mhz)"),
@@ -372,10 +398,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, dt, m, cores = oracle_sample_rate(D_host, w, args.cpu_seconds, L=L_box)
+        r, dt, m, cores, evals = oracle_sample_rate(D_host, w, args.cpu_seconds, L=L_box)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{m} random i-points x all {n} points (brute force, binary64), "
-                         f"{dt:.1f} s"}
+                         f"{dt:.1f} s; in-range pairs found per second",
+               "pair_evaluations_per_s": evals}
 
     if rank == 0:
         s0 = stats[0]
@@ -393,10 +420,13 @@ def run_ours(args):
                                        if args.shard else f"replicas x{world}")
                                       if world > 1 else "1 GPU",
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "cell_size": s0.cell_size, "in_range_pairs": int(counts.sum()),
-                       "candidates_per_step": int(s0.candidates)},
-            "in_range_pairs_per_s": float(counts.sum()) * (1 if args.shard else world)
-                                    / (t_max / args.steps * 1e-3),
+                       "unit_of_work": "in-range pairs binned (each pair in exactly one bin)",
+                       "cell_size": s0.cell_size, "ipt": opts.ipt, "priv": opts.priv,
+                       "tuning": tuning,
+                       "in_range_pairs": int(counts.sum()),
+                       "candidates_per_step": int(s0.candidates),
+                       "pruned_per_step": int(s0.pruned)},
+            "candidate_pairs_per_s": cand_all / (t_max * 1e-3),
             "rescued_fraction": s0.rescued / max(1, int(counts.sum())),
             "fp64_path": fp64,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
@@ -436,13 +466,23 @@ def run_batch(args):
     n_tot = sum(x.shape[0] for x in mocks)
     bins = P.Bins(w.mode, w.los, w.edges_a, w.edges_b)
     box = P.make_box(w.L, True)
-    vol = w.L ** 3
-    cell = args.cell_size or P.pc_suggest_cell_size(n_tot // m, vol, bins.r_max)
-    opts = P.make_opts("f32", cell, args.ipt)
+    stream = torch.cuda.current_stream()
+    tuning = None
+    if args.cell_size > 0 or args.ipt > 0:
+        cell = args.cell_size or P.pc_suggest_cell_size(n_tot // m, w.L ** 3, bins.r_max)
+        opts = P.make_opts("f32", cell, args.ipt)
+    else:
+        # measured autotuning once, on the mock of median size; all mocks share it
+        med = sorted(range(m), key=lambda k: X[k].shape[0])[m // 2]
+        t0 = time.perf_counter()
+        opts, trials = P.pc_tune(X[med], box=box, bins=bins, stream=stream)
+        tuning = {"seconds": time.perf_counter() - t0, "on_mock_n": int(X[med].shape[0]),
+                  "trials": [{"cell_size": round(c, 3), "ipt": i, "priv": pv, "ms": round(ms, 3)}
+                             for c, i, pv, ms in trials]}
+        cell = opts.cell_size
     opts.use_graph = 1
     out = torch.zeros(m * bins.nbins, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
 
     def step(xs=X, counts=out, batched=True):
         gs = [P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=opts, stream=stream) for x in xs]
@@ -484,12 +524,15 @@ def run_batch(args):
     launches = P.pc_launch_count() - l0
     clocks = sampler.stop()
     t_local = torch.tensor([sum(ms)], dtype=torch.float64, device=dev)
-    c_local = torch.tensor([float(cand) * args.steps], dtype=torch.float64, device=dev)
+    inr_step = float(out.sum().item())       # in-range pairs of all mocks, every step
+    c_local = torch.tensor([inr_step * args.steps, float(cand) * args.steps],
+                           dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
         dist.all_reduce(c_local, op=dist.ReduceOp.SUM)
     t_max = float(t_local.item())
-    value = float(c_local.item()) / (t_max * 1e-3)
+    inr_all, cand_all = (float(v) for v in c_local.tolist())
+    value = inr_all / (t_max * 1e-3)
     batched_counts = out.clone()
     loop_ms, _ = timed(1, batched=False)
     same = bool(torch.equal(out, batched_counts))
@@ -497,9 +540,9 @@ def run_batch(args):
     if args.e2e_steps > 0:
         Xh = [torch.from_numpy(x).pin_memory() for x in mocks]
         host = np.zeros(m * bins.nbins, dtype=np.int64)
-        e_ms, e_cand = timed(args.e2e_steps, xs=Xh, counts=host)
+        e_ms, _ = timed(args.e2e_steps, xs=Xh, counts=host)
         assert np.array_equal(host, batched_counts.cpu().numpy())
-        e2e = {"value": e_cand * world / (statistics.mean(e_ms) * 1e-3), "unit": UNIT,
+        e2e = {"value": inr_step * world / (statistics.mean(e_ms) * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(n_tot * 24), "d2h_bytes_per_step": int(m * bins.nbins * 8),
                "ms_per_step": statistics.mean(e_ms)}
     if rank == 0:
@@ -509,11 +552,15 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": w.name if m == w.extra["m"] else f"{w.name} ({m} mocks)",
-                       "mocks": m, "n_total": int(n_tot), "cell_size": cell,
+                       "mocks": m, "n_total": int(n_tot), "cell_size": cell, "ipt": opts.ipt,
+                       "priv": opts.priv, "tuning": tuning,
+                       "unit_of_work": "in-range pairs binned (each pair in exactly one bin)",
+                       "in_range_pairs": int(inr_step), "candidates_per_step": int(cand),
                        "bins": "s 40 x mu 100 (LOS z)",
                        "precision": "FP32 separations, binary64 rescue near bin edges, int64 counts",
                        "launch": "one persistent pair-kernel launch over all mocks, replayed as a CUDA graph",
                        "l2": "flushed between timed steps (256 MiB write)"},
+            "candidate_pairs_per_s": cand_all / (t_max * 1e-3),
             "loop_of_single_counts_ms": loop_ms[0],
             "batched_speedup_vs_loop": loop_ms[0] / (t_max / args.steps),
             "loop_counts_identical": same,

@@ -108,6 +108,8 @@ typedef struct {
     float ms_pairs;              /* device time of the pair kernel alone */
     float ms_rescue;             /* device time of the rescue kernel */
     int launches;                /* kernels this call launched */
+    long long pruned;            /* of the candidates, pairs the FP32 kernel decided out of
+                                    range by one bounding-box test per point group */
 } pc_stats;
 
 typedef struct pc_grid pc_grid;  /* opaque; owned by the library */
@@ -178,6 +180,32 @@ pc_status pc_count_batch(const pc_grid *const *gs, int m, const pc_bins *b, cons
  * one device context) would race on it. */
 pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, const pc_opts *o,
                                 void *stream, long long *counts, double *wcounts);
+
+/* One configuration timed by pc_tune. */
+typedef struct {
+    double cell_size;   /* requested cell side */
+    int ipt;            /* i-points per thread */
+    int priv;           /* histogram copies: 0 one per CTA, 1 one per warp */
+    float ms;           /* device time of the sampled pair and rescue kernels */
+} pc_tune_trial;
+
+/* Measured autotuner for the options of a count (the cost model of Appendix
+ * B.1 gives the starting cell side).  Builds the catalogue's grid at cell
+ * sides 0.8 to 2 times the model's choice, times the pair and rescue kernels
+ * on an evenly spaced sample of the point blocks for 2 and 4 i-points per
+ * thread, then per-warp histogram copies at the best of those, and writes
+ * the fastest options to *out (base's other fields are kept).
+ *   xyz, w, w_is_f32, n, box   the catalogue, as for pc_build_grid
+ *   b                          the bins the counts will use
+ *   base                       starting options (NULL = defaults); priv != 0
+ *                              there keeps the caller's privatisation
+ *   trials                     optional host array of max_trials records;
+ *                              *n_trials receives how many were written
+ * Takes a few full-size kernel times.  Errors as pc_build_grid and
+ * pc_count_auto; a cell side that needs too many cells is skipped. */
+pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, long long n, const pc_box *box,
+                  const pc_bins *b, const pc_opts *base, void *stream, pc_opts *out,
+                  pc_tune_trial *trials, int max_trials, int *n_trials);
 
 /* Bounding box of n points (n x 3 binary64, host or device) -- the first of
  * the three grid-build passes of Sect. 2.1.  lo/hi are host arrays of 3. */

@@ -54,7 +54,12 @@ class pc_stats(ctypes.Structure):
     _fields_ = [("candidates", c_longlong), ("rescued", c_longlong),
                 ("rescue_inline", c_longlong), ("blocks", c_longlong),
                 ("cell_size", c_double), ("ms_total", c_float), ("ms_pairs", c_float),
-                ("ms_rescue", c_float), ("launches", c_int)]
+                ("ms_rescue", c_float), ("launches", c_int),
+                ("pruned", c_longlong)]
+
+
+class pc_tune_trial(ctypes.Structure):
+    _fields_ = [("cell_size", c_double), ("ipt", c_int), ("priv", c_int), ("ms", c_float)]
 
 
 class PairCountError(RuntimeError):
@@ -67,7 +72,7 @@ _lib = None
 
 EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc_count_cross",
            "pc_count_batch", "pc_aabb", "pc_suggest_cell_size", "pc_strerror", "pc_last_error",
-           "pc_version", "pc_launch_count", "pc_count_auto_noalloc"]
+           "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune"]
 
 
 def library_path() -> str:
@@ -119,6 +124,10 @@ def lib():
     L.pc_version.argtypes = []
     L.pc_launch_count.restype = c_longlong
     L.pc_launch_count.argtypes = []
+    L.pc_tune.restype = c_int
+    L.pc_tune.argtypes = [vp, vp, c_int, c_longlong, POINTER(pc_box), POINTER(pc_bins),
+                          POINTER(pc_opts), vp, POINTER(pc_opts), POINTER(pc_tune_trial), c_int,
+                          POINTER(c_int)]
     L.pc_count_auto_noalloc.restype = c_int
     L.pc_count_auto_noalloc.argtypes = [vp, POINTER(pc_bins), POINTER(pc_opts), vp, vp, vp]
     _lib = L
@@ -296,6 +305,31 @@ def pc_build_grid(xyz, w=None, *, box: pc_box, r_max: float, opts: pc_opts | Non
                                     _stream_handle(stream), ctypes.byref(out)), "pc_build_grid")
     del st, keep_x, keep_w
     return Grid(out, n)
+
+
+def pc_tune(xyz, w=None, *, box: pc_box, bins: Bins, opts: pc_opts | None = None, stream=None,
+            max_trials: int = 32):
+    """Measured autotuning of cell side, i-points per thread and histogram
+    privatisation; returns (tuned pc_opts, list of (cell_size, ipt, priv, ms))."""
+    px, keep_x, n = _ptr(xyz, np.float64, 3)
+    w_is_f32 = 0
+    pw, keep_w = None, None
+    if w is not None:
+        t = _torch()
+        is32 = (getattr(w, "dtype", None) == np.float32 or
+                (t is not None and isinstance(w, t.Tensor) and w.dtype == t.float32))
+        w_is_f32 = 1 if is32 else 0
+        pw, keep_w, nw = _ptr(w, np.float32 if is32 else np.float64)
+        if nw != n:
+            raise ValueError("weights and positions differ in length")
+    out = pc_opts()
+    trials = (pc_tune_trial * max_trials)()
+    nt = c_int(0)
+    _check(lib().pc_tune(px, pw, w_is_f32, n, ctypes.byref(box), ctypes.byref(bins.s),
+                         ctypes.byref(opts) if opts is not None else None, _stream_handle(stream),
+                         ctypes.byref(out), trials, max_trials, ctypes.byref(nt)), "pc_tune")
+    del keep_x, keep_w
+    return out, [(t.cell_size, t.ipt, t.priv, t.ms) for t in trials[:nt.value]]
 
 
 def pc_free_grid(g: Grid):

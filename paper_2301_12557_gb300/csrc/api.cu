@@ -409,7 +409,8 @@ struct CountSetup {
 struct DevBufs {
     unsigned long long *hist = nullptr;
     double *whist = nullptr;
-    unsigned long long *ctr = nullptr;   // [0] candidates, [1] inline rescues, [2] queue count
+    unsigned long long *ctr = nullptr;   // [0] candidates, [1] inline rescues, [2] queue count,
+                                         // [3] pairs pruned by group bounds
     int *sc = nullptr;                   // [0] work counter, [1] number of blocks
     uint3 *queue = nullptr;
     Block *blocks = nullptr;
@@ -618,12 +619,13 @@ static void copy_out(void *dst, const void *src, size_t bytes, cudaStream_t st, 
 }
 
 static void fill_stats(pc_stats *stats, const CountSetup &S, const pc_grid *g0,
-                       const unsigned long long hc[3], int hblk, float ms_total, float ms_pairs,
+                       const unsigned long long hc[4], int hblk, float ms_total, float ms_pairs,
                        float ms_rescue, long long launches) {
     if (!stats) return;
     memset(stats, 0, sizeof(*stats));
     stats->candidates = (long long)hc[0];
     stats->rescue_inline = (long long)hc[1];
+    stats->pruned = (long long)hc[3];
     stats->rescued = (long long)std::min<unsigned long long>(hc[2], S.qcap) + (long long)hc[1];
     stats->blocks = hblk;
     stats->cell_size = g0->cell_size;
@@ -673,7 +675,7 @@ static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *o
     copy_out(counts, B.hist, sizeof(long long) * S.hist_n, st, e);
     copy_out(wcounts, B.whist, sizeof(double) * S.hist_n, st, e);
     if (e != cudaSuccess) return cuda_fail(e, "result copy");
-    unsigned long long hc[3] = {0, 0, 0};
+    unsigned long long hc[4] = {0, 0, 0, 0};
     int hblk = 0;
     if (ev.on) {
         PC_CUDA(cudaMemcpyAsync(hc, B.ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
@@ -845,7 +847,7 @@ static pc_status run_count_graph(const CountJob &J, const std::vector<const pc_g
             memcpy(wcounts, G->h_whist, sizeof(double) * hb);
     }
     if (e != cudaSuccess) return cuda_fail(e, "result copy");
-    unsigned long long hc[3] = {G->h_ctr[0], G->h_ctr[1], G->h_ctr[2]};
+    unsigned long long hc[4] = {G->h_ctr[0], G->h_ctr[1], G->h_ctr[2], G->h_ctr[3]};
     fill_stats(stats, G->S, J.g0, hc, *G->h_blocks, ev.ms(0, 4), 0.f, 0.f,
                launch_count() - launches0);
     return PC_OK;

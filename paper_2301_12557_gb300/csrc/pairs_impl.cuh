@@ -71,7 +71,53 @@ struct CtaShared {
     int nseg;
     int total;
     int qn;
+    unsigned long long pruned;   // candidate pairs decided by group bounds
 };
+
+// Axis-aligned box of a group of points in the i-cell's FP32 frame.
+struct GBox {
+    float4 lo, hi;
+};
+constexpr int JG = 32;           // j-points per bounding-box group
+static_assert(TJ % JG == 0 && TJ / JG <= 32, "group masks are one 32-bit ballot");
+static_assert(NT % JG == 0, "each warp stages whole groups");
+
+// Order-preserving map of binary32 onto int32 (its own inverse): a < b as
+// floats iff fkey(a) < fkey(b) as signed integers.
+__device__ __forceinline__ int fkey(float f) {
+    const int b = __float_as_int(f);
+    return b ^ ((b >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float fkey_inv(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7fffffff)); }
+__device__ __forceinline__ float warp_minf(float v) {
+    return fkey_inv(__reduce_min_sync(0xffffffffu, fkey(v)));
+}
+__device__ __forceinline__ float warp_maxf(float v) {
+    return fkey_inv(__reduce_max_sync(0xffffffffu, fkey(v)));
+}
+
+// Groups of the staged tile that may hold a pair in range of this warp's
+// i-points.  Bit g is clear only if, for every i of the warp and every j of
+// group g, the kernel's own FP32 value fl(fl(dz dz + fl(dy dy + fl(dx dx))))
+// would be >= r2cut: |fl(x_j - x_i)| >= fl(gap) per axis because rounding is
+// monotone, and the same operations on the gaps give a lower bound of s2.
+// So the skipped pairs are exactly pairs the kernel would reject one by one.
+__device__ __forceinline__ unsigned group_mask(const GBox *gb, const GBox &ib, int len, int ni,
+                                               float r2cut, unsigned long long *pruned) {
+    const int lane = threadIdx.x & 31;
+    const int ngroups = (len + JG - 1) / JG;
+    bool keep = false;
+    if (lane < ngroups) {
+        const GBox g = gb[lane];
+        const float gx = fmaxf(fmaxf(g.lo.x - ib.hi.x, ib.lo.x - g.hi.x), 0.f);
+        const float gy = fmaxf(fmaxf(g.lo.y - ib.hi.y, ib.lo.y - g.hi.y), 0.f);
+        const float gz = fmaxf(fmaxf(g.lo.z - ib.hi.z, ib.lo.z - g.hi.z), 0.f);
+        keep = fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < r2cut;
+        if (!keep && ni > 0)
+            atomicAdd(pruned, (unsigned long long)min(JG, len - lane * JG) * (unsigned)ni);
+    }
+    return __ballot_sync(0xffffffffu, keep);
+}
 
 // Exclusive prefix over the segment lengths held in seg[k].y (in place);
 // returns the total.  All NT threads call it.
@@ -437,13 +483,16 @@ struct Tile {
 // Table-based bins, one pair at a time (every mode and line of sight).
 // MASK: the tile holds the block's own points and only pairs j > i count.
 template <int MODE, int LOS, bool W, int RI, bool MASK>
-__device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int len,
+__device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int len, unsigned gmask,
                                               const IPts<RI> &I, const BinCtx &bc, float r2cut,
                                               unsigned hist_sa, unsigned whist_sa, uint3 *s_q,
                                               int *s_qn, const int4 *s_seg, int nseg, int f0,
                                               int bstart, unsigned task_bits) {
+#pragma unroll 1
+    for (unsigned gm = gmask; gm; gm &= gm - 1) {
+    const int j0 = (__ffs(gm) - 1) * JG, j1 = min(j0 + JG, len);
 #pragma unroll 2
-    for (int jj = 0; jj < len; ++jj) {
+    for (int jj = j0; jj < j1; ++jj) {
         const float qx = tb.x[jj], qy = tb.y[jj], qz = tb.z[jj];
         float dxv[RI], dyv[RI], dzv[RI], qv[RI], s2v[RI];
         bool inr[RI];
@@ -483,6 +532,7 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
             }
         }
     }
+    }
 }
 
 // Evenly spaced bins, two j-points per step in packed FP32 (s, and (s, mu)
@@ -491,7 +541,7 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
 // per-pair band.  Histogram addresses are formed from the float bits of
 // floor(t) + 2^23, with the 2^23 bias folded into the base address.
 template <int MODE, bool W, int RI, bool MASK>
-__device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int len,
+__device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int len, unsigned gmask,
                                                const IPts<RI> &I, const LinCtx &lc, float r2cut,
                                                unsigned hist_sa, unsigned whist_sa, uint3 *s_q,
                                                int *s_qn, const int4 *s_seg, int nseg, int f0,
@@ -521,7 +571,10 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
         NZ[r] = make_float2(-I.z[r], -I.z[r]);
     }
 #pragma unroll 1
-    for (int jj = 0; jj < len; jj += 2) {
+    for (unsigned gm = gmask; gm; gm &= gm - 1) {
+    const int j0 = (__ffs(gm) - 1) * JG, j1 = min(j0 + JG, len);
+#pragma unroll 1
+    for (int jj = j0; jj < j1; jj += 2) {
         const float2 X = *reinterpret_cast<const float2 *>(tb.x + jj);
         const float2 Y = *reinterpret_cast<const float2 *>(tb.y + jj);
         const float2 Z = *reinterpret_cast<const float2 *>(tb.z + jj);
@@ -595,16 +648,19 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
             }
         }
     }
+    }
 }
 
 // Global-histogram variant for histograms too large for shared memory.
 template <int MODE, int LOS, bool W, int RI, bool MASK>
-__device__ __forceinline__ void pair_tile_global(const PairParams &p, Tile tb, int len,
+__device__ __forceinline__ void pair_tile_global(const PairParams &p, Tile tb, int len, unsigned gmask,
                                                  const IPts<RI> &I, const BinCtx &bc, float r2cut,
                                                  size_t hbase, uint3 *s_q, int *s_qn,
                                                  const int4 *s_seg, int nseg, int f0, int bstart,
                                                  unsigned task_bits) {
-    for (int jj = 0; jj < len; ++jj) {
+    for (unsigned gm = gmask; gm; gm &= gm - 1) {
+    const int j0 = (__ffs(gm) - 1) * JG, j1 = min(j0 + JG, len);
+    for (int jj = j0; jj < j1; ++jj) {
         const float qx = tb.x[jj], qy = tb.y[jj], qz = tb.z[jj];
         for (int r = 0; r < RI; ++r) {
             float dx = qx - I.x[r], dy = qy - I.y[r], dz = qz - I.z[r];
@@ -623,23 +679,25 @@ __device__ __forceinline__ void pair_tile_global(const PairParams &p, Tile tb, i
             }
         }
     }
+    }
 }
 
 // One tile through the variant that applies.
 template <int MODE, int LOS, bool W, int RI, bool LIN, bool MASK>
 __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, Tile tb, int len,
+                                          unsigned gmask,
                                           const IPts<RI> &I, const BinCtx &bc, const LinCtx &lc,
                                           float r2cut, unsigned hist_sa, unsigned whist_sa,
                                           size_t hbase, uint3 *s_q, int *s_qn, const int4 *s_seg,
                                           int nseg, int f0, int bstart, unsigned task_bits) {
     if (!smem_hist) {
-        pair_tile_global<MODE, LOS, W, RI, MASK>(p, tb, len, I, bc, r2cut, hbase, s_q, s_qn, s_seg,
+        pair_tile_global<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hbase, s_q, s_qn, s_seg,
                                                  nseg, f0, bstart, task_bits);
     } else if (LIN) {
-        pair_tile_lin2<MODE, W, RI, MASK>(p, tb, len, I, lc, r2cut, hist_sa, whist_sa, s_q, s_qn,
+        pair_tile_lin2<MODE, W, RI, MASK>(p, tb, len, gmask, I, lc, r2cut, hist_sa, whist_sa, s_q, s_qn,
                                           s_seg, nseg, f0, bstart, task_bits);
     } else {
-        pair_tile_lut<MODE, LOS, W, RI, MASK>(p, tb, len, I, bc, r2cut, hist_sa, whist_sa, s_q,
+        pair_tile_lut<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hist_sa, whist_sa, s_q,
                                               s_qn, s_seg, nseg, f0, bstart, task_bits);
     }
 }
@@ -654,6 +712,8 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     __shared__ CtaShared cs;
     __shared__ int s_tmp[8];
     __shared__ unsigned long long s_base;
+    __shared__ GBox s_gbox[2][TJ / JG];   // bounding boxes of the staged j-groups
+    __shared__ GBox s_ibox[NT / 32];      // bounding box of each warp's i-points
 
     const SmemLayout Ly = smem_layout(p, false);
     float2 *s_lut = (float2 *)(smem + Ly.lut);
@@ -675,7 +735,10 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
         for (int k = tid; k < nbins * copies; k += NT) s_hist[k] = 0;
         if (W) for (int k = tid; k < nbins; k += NT) s_whist[k] = 0.0;
     }
-    if (tid == 0) cs.qn = 0;
+    if (tid == 0) {
+        cs.qn = 0;
+        cs.pruned = 0;
+    }
 
     BinCtx bc;
     bc.lutA = s_lut + p.la.off;
@@ -749,6 +812,22 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                 }
             }
         }
+        {   // the warp's i-box (empty box if the warp holds no point)
+            float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+            float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+#pragma unroll
+            for (int r = 0; r < RI; ++r)
+                if (RI * tid + r < B.count) {
+                    lx = fminf(lx, I.x[r]); hx = fmaxf(hx, I.x[r]);
+                    ly = fminf(ly, I.y[r]); hy = fmaxf(hy, I.y[r]);
+                    lz = fminf(lz, I.z[r]); hz = fmaxf(hz, I.z[r]);
+                }
+            lx = warp_minf(lx); ly = warp_minf(ly); lz = warp_minf(lz);
+            hx = warp_maxf(hx); hy = warp_maxf(hy); hz = warp_maxf(hz);
+            if ((tid & 31) == 0)
+                s_ibox[tid >> 5] = GBox{make_float4(lx, ly, lz, 0.f), make_float4(hx, hy, hz, 0.f)};
+        }
+        const int ni_w = min(max(B.count - (tid >> 5) * 32 * RI, 0), 32 * RI);
 
         // ---- phase A (auto): pairs inside the block, j > i ------------------
         if (T.is_auto) {
@@ -765,8 +844,9 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                 }
             }
             __syncthreads();
+            const int ngA = (lenA + JG - 1) / JG;    // <= 8 groups, all evaluated
             pair_tile<MODE, LOS, W, RI, LIN, true>(p, smem_hist, Tile{s_tx, s_ty, s_tz, s_tw}, lenA,
-                                                   I, bc, lc, r2cut, hist_sa, whist_sa, hbase, s_q,
+                                                   (1u << ngA) - 1u, I, bc, lc, r2cut, hist_sa, whist_sa, hbase, s_q,
                                                    &cs.qn, s_seg, 0, -1, B.start, task_bits);
             if (tid == 0) cand_local += (unsigned long long)B.count * (B.count - 1) / 2;
             since_flush += (unsigned long long)B.count * B.count;
@@ -833,13 +913,23 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                         y = fmaf((float)dyc, c32y, rq[s].y);
                         z = fmaf((float)dzc, c32z, rq[s].z);
                         wv = rw[s];
-                    } else if (slot != len) {
-                        continue;
                     }
-                    s_tx[buf * TJ + slot] = x;
-                    s_ty[buf * TJ + slot] = y;
-                    s_tz[buf * TJ + slot] = z;
-                    if (W) s_tw[buf * TJ + slot] = wv;
+                    if (rv[s] || slot == len) {
+                        s_tx[buf * TJ + slot] = x;
+                        s_ty[buf * TJ + slot] = y;
+                        s_tz[buf * TJ + slot] = z;
+                        if (W) s_tw[buf * TJ + slot] = wv;
+                    }
+                    // box of the warp's 32 consecutive slots = one j-group
+                    const float lx = warp_minf(rv[s] ? x : INFINITY);
+                    const float ly = warp_minf(rv[s] ? y : INFINITY);
+                    const float lz = warp_minf(rv[s] ? z : INFINITY);
+                    const float hx = warp_maxf(rv[s] ? x : -INFINITY);
+                    const float hy = warp_maxf(rv[s] ? y : -INFINITY);
+                    const float hz = warp_maxf(rv[s] ? z : -INFINITY);
+                    if ((tid & 31) == 0)
+                        s_gbox[buf][slot / JG] = GBox{make_float4(lx, ly, lz, 0.f),
+                                                      make_float4(hx, hy, hz, 0.f)};
                 }
             };
 
@@ -850,9 +940,11 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                 const int buf = t & 1;
                 const int len = min(TJ, total - t * TJ);
                 if (t + 1 < ntiles) load_tile(t + 1);
+                const unsigned gm = group_mask(s_gbox[buf], s_ibox[tid >> 5], len, ni_w, r2cut,
+                                               &cs.pruned);
                 pair_tile<MODE, LOS, W, RI, LIN, false>(
                     p, smem_hist, Tile{s_tx + buf * TJ, s_ty + buf * TJ, s_tz + buf * TJ, s_tw + buf * TJ},
-                    (len + 1) & ~1, I, bc, lc, r2cut, hist_sa, whist_sa, hbase, s_q, &cs.qn, s_seg,
+                    (len + 1) & ~1, gm, I, bc, lc, r2cut, hist_sa, whist_sa, hbase, s_q, &cs.qn, s_seg,
                     nseg, t * TJ, B.start, task_bits);
                 if (tid == 0) cand_local += (unsigned long long)len * B.count;
                 since_flush += (unsigned long long)len * B.count;
@@ -872,6 +964,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     drain_rescue<MODE, LOS>(p, s_q, cs, &s_base);
     flush_hist(p, s_hist, s_whist, cur_hist);
     if (tid == 0 && cand_local) atomicAdd(&p.counters[0], cand_local);
+    if (tid == 0 && cs.pruned) atomicAdd(&p.counters[3], cs.pruned);
 }
 
 // ---------------------------------------------------------------------------

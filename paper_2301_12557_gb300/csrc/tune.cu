@@ -1,0 +1,174 @@
+// Measured autotuner: cell side, i-points per thread and histogram privatisation.
+//
+// The cost model of Appendix B.1 (pc_suggest_cell_size) gives a starting cell
+// side; the tuner then builds the grid at a few sides around it and times the
+// FP32 pair kernel (plus rescue) on an evenly spaced sample of the point
+// blocks -- the block-shard mechanism of the multi-GPU path with one shard --
+// for i-points-per-thread 2 and 4, then one histogram copy per CTA against
+// one per warp, and returns the fastest combination.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pc_host.hpp"
+
+using namespace pc;
+
+namespace {
+
+// Largest separation any bin can hold (Sect. 2.5: sqrt(sigma^2 + pi^2) for
+// (sigma, pi) bins).
+double bins_reach(const pc_bins *b) {
+    const double a = b->edges_a[b->n_a];
+    if (b->mode == PC_BIN_SIGPI) {
+        const double p = b->edges_b[b->n_b];
+        return sqrt(a * a + p * p);
+    }
+    return a;
+}
+
+// Cells per axis the grid build would use for a cell side c (before its
+// periodic no-alias adjustment, which is the same for equal inputs).
+void grid_dims(const pc_box *box, const double lo[3], const double hi[3], double c, long long ng[3]) {
+    for (int a = 0; a < 3; ++a) {
+        const double ext = hi[a] - lo[a];
+        ng[a] = box->periodic ? std::max(1LL, (long long)floor(ext / c))
+                              : std::max(1LL, (long long)ceil(ext / c));
+    }
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+}  // namespace
+
+extern "C" pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, long long n,
+                             const pc_box *box, const pc_bins *b, const pc_opts *base,
+                             void *stream, pc_opts *out, pc_tune_trial *trials, int max_trials,
+                             int *n_trials) {
+    if (n_trials) *n_trials = 0;
+    if (!box || !b || !out || n < 0 || (n > 0 && !xyz) || max_trials < 0 ||
+        (max_trials > 0 && !trials))
+        return fail(PC_EINVAL, "pc_tune: bad arguments");
+    if (b->n_a < 1 || !b->edges_a || (b->mode != PC_BIN_S && (b->n_b < 1 || !b->edges_b)))
+        return fail(PC_EINVAL, "pc_tune: bad bins");
+    pc_opts o;
+    memset(&o, 0, sizeof(o));
+    if (base) o = *base;
+    const double reach = bins_reach(b);
+    if (!(reach > 0.0) || !std::isfinite(reach)) return fail(PC_EINVAL, "pc_tune: bad bins");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    double lo[3], hi[3];
+    const bool given = box->hi[0] > box->lo[0] && box->hi[1] > box->lo[1] && box->hi[2] > box->lo[2];
+    if (box->periodic) {
+        for (int a = 0; a < 3; ++a) { lo[a] = 0.0; hi[a] = box->L[a]; }
+    } else if (given) {
+        for (int a = 0; a < 3; ++a) { lo[a] = box->lo[a]; hi[a] = box->hi[a]; }
+    } else {
+        pc_status s = pc_aabb(xyz, n, stream, lo, hi);
+        if (s != PC_OK) return s;
+    }
+    double vol = 1.0;
+    for (int a = 0; a < 3; ++a) vol *= std::max(hi[a] - lo[a], 1e-300);
+    const double c0 = pc_suggest_cell_size(n, vol, reach, b->mode);
+    *out = o;
+    out->cell_size = c0;
+    if (out->ipt == 0) out->ipt = 2;
+    if (n < 2) return PC_OK;
+
+    int dev = 0, sms = 1;
+    PC_CUDA(cudaGetDevice(&dev));
+    PC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // sample every S-th point block so that each trial still gives every
+    // persistent CTA several blocks
+    const double blocks_est = (double)n / (NT * 4);
+    const int S = std::max(1, (int)(blocks_est / (4.0 * 5.0 * sms)));
+
+    const int nbins = b->n_a * (b->mode == PC_BIN_S ? 1 : b->n_b);
+    DevBuf dc, dw;
+    PC_CUDA(cudaMalloc(&dc.p, sizeof(long long) * nbins));
+    if (w) PC_CUDA(cudaMalloc(&dw.p, sizeof(double) * nbins));
+
+    const double factors[] = {0.8, 1.0, 1.25, 1.6, 2.0};
+    const int ipts[] = {2, 4};
+    const bool fp32 = o.prec == PC_PREC_F32_RESCUE;
+    std::vector<long long> seen;
+    float best_ms = INFINITY;
+    int nt = 0;
+    for (double f : factors) {
+        const double c = c0 * f;
+        if (c > 2.0 * reach || c < reach / 16.0) continue;
+        long long ng[3];
+        grid_dims(box, lo, hi, c, ng);
+        const long long key = (ng[0] * 65537LL + ng[1]) * 65537LL + ng[2];
+        if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+        seen.push_back(key);
+        pc_opts oc = o;
+        oc.cell_size = c;
+        pc_grid *g = nullptr;
+        pc_status s = pc_build_grid(xyz, w, w_is_f32, n, box, reach, &oc, stream, &g);
+        if (s == PC_EOVERFLOW) continue;   // too many cells at this side
+        if (s != PC_OK) return s;
+        for (int ipt : ipts) {
+            if (!fp32 && ipt != 2) continue;   // the FP64 kernel holds one point per thread
+            pc_opts ot = oc;
+            ot.ipt = ipt;
+            ot.shard_index = 0;
+            ot.shard_count = S;
+            float ms = INFINITY;
+            for (int rep = 0; rep < 2 && s == PC_OK; ++rep) {
+                pc_stats sts;
+                s = pc_count_auto(g, b, &ot, stream, (long long *)dc.p, (double *)dw.p, &sts);
+                if (s == PC_OK) ms = std::min(ms, sts.ms_pairs + sts.ms_rescue);
+            }
+            if (s != PC_OK) {
+                pc_free_grid(g);
+                return s;
+            }
+            if (nt < max_trials) trials[nt] = pc_tune_trial{c, ipt, o.priv, ms};
+            ++nt;
+            if (ms < best_ms) {
+                best_ms = ms;
+                out->cell_size = c;
+                out->ipt = ipt;
+            }
+        }
+        pc_free_grid(g);
+    }
+    // histogram privatisation (one shared copy vs one per warp) at the best
+    // cell side and i-tile, unless the caller fixed it
+    if (o.priv == 0 && std::isfinite(best_ms)) {
+        pc_opts oc = *out;
+        pc_grid *g = nullptr;
+        pc_status s = pc_build_grid(xyz, w, w_is_f32, n, box, reach, &oc, stream, &g);
+        if (s != PC_OK) return s;
+        pc_opts ot = oc;
+        ot.priv = 1;
+        ot.shard_index = 0;
+        ot.shard_count = S;
+        float ms = INFINITY;
+        for (int rep = 0; rep < 2 && s == PC_OK; ++rep) {
+            pc_stats sts;
+            s = pc_count_auto(g, b, &ot, stream, (long long *)dc.p, (double *)dw.p, &sts);
+            if (s == PC_OK) ms = std::min(ms, sts.ms_pairs + sts.ms_rescue);
+        }
+        pc_free_grid(g);
+        if (s != PC_OK) return s;
+        if (nt < max_trials) trials[nt] = pc_tune_trial{out->cell_size, out->ipt, 1, ms};
+        ++nt;
+        if (ms < best_ms) {
+            best_ms = ms;
+            out->priv = 1;
+        }
+    }
+    if (n_trials) *n_trials = std::min(nt, max_trials);
+    PC_CUDA(cudaStreamSynchronize(st));
+    return PC_OK;
+}

@@ -92,3 +92,21 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(P._build, "LIB", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError):
         P.lib()
+
+
+def test_tune_host_side_checks(lib):
+    box = P.make_box(100.0, True)
+    bins = P.Bins("s", "z", np.linspace(0.0, 20.0, 5))
+    out = P.pc_opts()
+    x = np.zeros((1, 3))
+    # missing output / bad trial array: rejected before any CUDA call
+    assert lib.pc_tune(x.ctypes.data, None, 0, 1, ctypes.byref(box), ctypes.byref(bins.s), None,
+                       None, None, None, 0, None) == P.PC_EINVAL
+    assert lib.pc_tune(x.ctypes.data, None, 0, 1, ctypes.byref(box), ctypes.byref(bins.s), None,
+                       None, ctypes.byref(out), None, 4, None) == P.PC_EINVAL
+    # fewer than two points: nothing to time, the cost model's cell side is returned
+    nt = ctypes.c_int(-1)
+    assert lib.pc_tune(x.ctypes.data, None, 0, 1, ctypes.byref(box), ctypes.byref(bins.s), None,
+                       None, ctypes.byref(out), None, 0, ctypes.byref(nt)) == P.PC_OK
+    assert nt.value == 0 and out.ipt == 2
+    assert out.cell_size == pytest.approx(P.pc_suggest_cell_size(1, 1e6, 20.0, 0))

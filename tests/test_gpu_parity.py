@@ -342,16 +342,50 @@ def test_workload_mixed_weighted_scaled():
     _check(g, o, gw, ow, "mixed weighted")
 
 
+def test_tuned_options_keep_counts_and_pruning_is_sound():
+    """pc_tune's choice counts exactly like the oracle, and every pair the
+    group bounds pruned is out of range: in-range pairs <= candidates - pruned."""
+    L = 400.0
+    x = synth.neyman_scott(60000, 6000, 10.0, 4.0, L, 311)
+    ea = np.linspace(0.0, 40.0, 41)
+    mu = np.linspace(0.0, 1.0, 51)
+    box = P.make_box(L, True)
+    bins = P.Bins("smu", "z", ea, mu)
+    opts, trials = P.pc_tune(x, box=box, bins=bins)
+    assert len(trials) >= 3
+    assert opts.ipt in (2, 4) and opts.priv in (0, 1)
+    assert any(t[0] == opts.cell_size and t[1] == opts.ipt for t in trials)
+    assert all(np.isfinite(t[3]) and t[3] > 0 for t in trials)
+    want, _ = oracle.count(x, box=L, periodic=True, mode="smu", edges_a=ea, edges_b=mu,
+                           method="grid")
+    g = P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=opts)
+    got, _, st = P.pc_count_auto(g, bins, opts)
+    g.free()
+    _check(got, want, what=f"tuned {opts.cell_size} ipt {opts.ipt} priv {opts.priv}")
+    assert st.pruned > 0
+    assert int(want.sum()) <= st.candidates - st.pruned
+
+
+def _bench_opts(D, w, bins):
+    """The options the benchmark times: pc_tune on the same catalogue."""
+    opts, _ = P.pc_tune(D, box=P.make_box(w.L, True), bins=bins)
+    return dict(cell_size=opts.cell_size, ipt=opts.ipt, priv=opts.priv)
+
+
 def test_full_size_ns_smu_auto_vs_cross_and_sampled_oracle():
     """N = 2,000,000 clustered points, (s, mu) 40 x 100, in the launch
-    configuration the benchmark times.  Auto counts are tied to the cross
-    path (cross(D, D) = 2 auto(D) + N self-pairs in bin 0), and the cross
-    path is checked against the oracle on a sampled subset of i-points."""
+    configuration the benchmark times (the tuned options).  Auto counts are
+    tied to the cross path (cross(D, D) = 2 auto(D) + N self-pairs in bin 0),
+    and the cross path is checked against the oracle on a sampled subset of
+    i-points."""
     w = W.WORKLOADS["ns_periodic_n2m_smu40x100"]
     D = W.make_inputs(w)["D"]
     kw = dict(box=w.L, periodic=True, mode="smu", edges_a=w.edges_a, edges_b=w.edges_b)
     xd = torch.from_numpy(D).cuda()
-    a, _ = P.count(xd, **kw)
+    tuned = _bench_opts(xd, w, P.Bins("smu", "z", w.edges_a, w.edges_b))
+    a, _ = P.count(xd, **kw, **tuned)
+    a0, _ = P.count(xd, **kw)
+    assert np.array_equal(a, a0)
     c, _ = P.count(xd, xd, **kw)
     want = 2 * a
     want[0] += D.shape[0]
