@@ -88,7 +88,10 @@ typedef struct {
     int prec;                    /* pc_prec: FP32 with FP64 rescue (0) or plain FP64 */
     double cell_size;            /* grid cell side; 0 = chosen by the cost model */
     int ipt;                     /* i-points per thread (2 or 4); 0 = auto */
-    int priv;                    /* histogram copies per CTA: 0 = one, 1 = one per warp, -1 = auto */
+    int priv;                    /* shared-histogram replication: 1 = one count copy per warp,
+                                    2 = one shared copy, other values = automatic (up to 32
+                                    lane copies, lane l updating copy l % k, when they fit
+                                    16 KB: few bins then never collide within a warp) */
     long long rescue_capacity;   /* rescue-queue slots; 0 = auto; < 0 = none (all inline) */
     int use_graph;               /* pc_count_batch: replay a captured CUDA graph */
     int grid_ctas_per_sm;        /* persistent CTAs per SM; 0 = occupancy limit */
@@ -110,6 +113,9 @@ typedef struct {
     int launches;                /* kernels this call launched */
     long long pruned;            /* of the candidates, pairs the FP32 kernel decided out of
                                     range by one bounding-box test per point group */
+    int prec;                    /* pc_prec that ran: PC_PREC_F64 also when FP32 was asked
+                                    for but its error bound does not hold (midpoint line of
+                                    sight with the observer too close to the points) */
 } pc_stats;
 
 typedef struct pc_grid pc_grid;  /* opaque; owned by the library */
@@ -185,7 +191,7 @@ pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, const pc_opt
 typedef struct {
     double cell_size;   /* requested cell side */
     int ipt;            /* i-points per thread */
-    int priv;           /* histogram copies: 0 one per CTA, 1 one per warp */
+    int priv;           /* replication: 0 automatic, 1 one count copy per warp */
     float ms;           /* device time of the sampled pair and rescue kernels */
 } pc_tune_trial;
 
@@ -201,8 +207,10 @@ typedef struct {
  *                              there keeps the caller's privatisation
  *   trials                     optional host array of max_trials records;
  *                              *n_trials receives how many were written
- * Takes a few full-size kernel times.  Errors as pc_build_grid and
- * pc_count_auto; a cell side that needs too many cells is skipped. */
+ * Each trial runs on every S-th block, S chosen so that a trial takes about
+ * 40 ms while every persistent CTA still gets two blocks or more.  Errors as
+ * pc_build_grid and pc_count_auto; a cell side that needs too many cells is
+ * skipped. */
 pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, long long n, const pc_box *box,
                   const pc_bins *b, const pc_opts *base, void *stream, pc_opts *out,
                   pc_tune_trial *trials, int max_trials, int *n_trials);

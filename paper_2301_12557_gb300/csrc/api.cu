@@ -232,7 +232,7 @@ static void build_stencil(const Geom &g, double r, bool half, std::vector<int4> 
 }
 
 static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo,
-                           const double *pts_hi, bool half, Plan &P) {
+                           const double *pts_hi, double rmin, bool half, Plan &P) {
     if (!b) return fail(PC_EINVAL, "bins: NULL");
     if (b->mode < 0 || b->mode > 2) return fail(PC_EINVAL, "bins: unknown mode");
     if (b->los < 0 || b->los > 1) return fail(PC_EINVAL, "bins: unknown line of sight");
@@ -281,7 +281,10 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
     double eps_sig = 2.0 * u * (3.6 * c + 11.5 * Rb) + ldexp(Rb, -25) + tiny;
     double muA = 2.0 * (6.9 * u * c) + tiny, muB = 2.0 * 21.0 * u + ldexp(1.0, -48);
     if (P.los == PC_LOS_MIDPOINT) {
-        // distance of the nearest point to the observer bounds |x_i + x_j|
+        // distance of the nearest point to the observer bounds |x_i + x_j|:
+        // the larger of the bounding box's distance and the points' own
+        // smallest radius (a shell is far from the observer although its
+        // bounding box may come close)
         double dmin2 = 0.0;
         for (int a = 0; a < 3; ++a) {
             double d = 0.0;
@@ -289,7 +292,8 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
             else if (pts_hi[a] < 0.0) d = -pts_hi[a];
             dmin2 += d * d;
         }
-        double lmin = 2.0 * sqrt(dmin2) - Rb;
+        const double dmin = std::max(sqrt(dmin2) * (1.0 - 1e-12), rmin);
+        double lmin = 2.0 * dmin - Rb;
         double dl = u * (5.5 * X + 4.4 * c + 6.2 * Rb);
         if (lmin > 4.0 * Rb) {
             double em = 2.0 * (u * (4.4 * c + 17.5 * Rb) + 2.0 * Rb * dl / lmin) +
@@ -388,12 +392,51 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
 // ---------------------------------------------------------------------------
 // one counting launch over a set of tasks
 // ---------------------------------------------------------------------------
+// Histogram replication from pc_opts.priv: 1 = one count copy per warp,
+// 2 = a single shared copy, otherwise automatic: lane copies (lane l updates
+// copy l % k) as many as fit a 16 KB budget, so the lanes of a warp do not
+// collide on the few bins of a small histogram.
+static void choose_replication(int mode, int nbins, bool weighted, int &priv, int &hist_k) {
+    priv = 0;
+    hist_k = 1;
+    if (mode == 1) { priv = 1; return; }
+    if (mode == 2) return;
+    const long long per_copy = (long long)nbins * (4 + (weighted ? 8 : 0));
+    while (hist_k < 32 && per_copy * hist_k * 2 <= 16384) hist_k *= 2;
+}
+
+// Shared-memory fallback: fewer lane copies, then no warp copies, then the
+// global histogram.  Returns false when nothing is left to give up.
+static bool shrink_replication(PairParams &p) {
+    if (p.hist_k > 1) { p.hist_k /= 2; return true; }
+    if (p.priv) { p.priv = 0; return true; }
+    return false;
+}
+
 struct CountJob {
     std::vector<TaskDev> tasks;
     int nhist;
     bool is_auto;
     const pc_grid *g0;
+    // bounds of the points of every grid involved, and a lower bound of |x|
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    double rmin = 0.0;
 };
+
+// Lower bound of |x| over the points of a grid (0 when unknown or periodic).
+static double grid_rmin(const pc_grid *g) {
+    if (g->g.periodic || !(g->r2min > 0.0)) return 0.0;
+    return sqrt(g->r2min) * (1.0 - 1e-12);
+}
+
+// Fold grid g into the job's point bounds (the first grid initialises them).
+static void job_add_bounds(CountJob &J, const pc_grid *g, bool first) {
+    for (int a = 0; a < 3; ++a) {
+        J.lo[a] = first ? g->pts_lo[a] : std::min(J.lo[a], g->pts_lo[a]);
+        J.hi[a] = first ? g->pts_hi[a] : std::max(J.hi[a], g->pts_hi[a]);
+    }
+    J.rmin = first ? grid_rmin(g) : std::min(J.rmin, grid_rmin(g));
+}
 
 // Everything decided on the host before any device work.
 struct CountSetup {
@@ -429,7 +472,7 @@ static pc_status setup_count(const CountJob &J, const pc_bins *b, const pc_opts 
     if (S.o.shard_count > 1 && (S.o.shard_index < 0 || S.o.shard_index >= S.o.shard_count))
         return fail(PC_EINVAL, "opts: shard_index must lie in [0, shard_count)");
     const pc_grid *g0 = J.g0;
-    pc_status s = make_plan(b, g0->g, g0->pts_lo, g0->pts_hi, J.is_auto, S.P);
+    pc_status s = make_plan(b, g0->g, J.lo, J.hi, J.rmin, J.is_auto, S.P);
     if (s != PC_OK) return s;
     S.weighted = weighted;
     S.prec = S.o.prec;
@@ -552,10 +595,7 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     p.counters = B.ctr;
     p.shard_count = S.o.shard_count > 1 ? S.o.shard_count : 1;
     p.shard_index = S.o.shard_count > 1 ? S.o.shard_index : 0;
-    // histogram privatisation: one copy per warp when it fits and helps
-    int copies_warp = P.nbins * (NT / 32) * 4;
-    if (S.o.priv == 0 || S.o.priv == 1) p.priv = S.o.priv;
-    else p.priv = (P.nbins <= 2048 && copies_warp <= 48 * 1024) ? 1 : 0;
+    choose_replication(S.o.priv, P.nbins, S.weighted, p.priv, p.hist_k);
     p.lin = (S.prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
     p.lin_invA = P.lin_invA;
     p.lin_offA = P.lin_offA;
@@ -568,11 +608,11 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     PC_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, S.dev));
     PC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S.dev));
     const int static_smem = 256;
-    for (int attempt = 0; attempt < 3; ++attempt) {
+    for (;;) {
         p.smem_hist_ok = 1;
         size_t need = (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
         if (need + static_smem <= (size_t)smem_optin) break;
-        if (p.priv) { p.priv = 0; continue; }
+        if (shrink_replication(p)) continue;
         p.smem_hist_ok = 0;
         break;
     }
@@ -626,6 +666,7 @@ static void fill_stats(pc_stats *stats, const CountSetup &S, const pc_grid *g0,
     stats->candidates = (long long)hc[0];
     stats->rescue_inline = (long long)hc[1];
     stats->pruned = (long long)hc[3];
+    stats->prec = S.prec;
     stats->rescued = (long long)std::min<unsigned long long>(hc[2], S.qcap) + (long long)hc[1];
     stats->blocks = hblk;
     stats->cell_size = g0->cell_size;
@@ -888,6 +929,7 @@ extern "C" pc_status pc_count_auto(const pc_grid *g, const pc_bins *b, const pc_
     J.nhist = 1;
     J.is_auto = true;
     J.g0 = g;
+    job_add_bounds(J, g, true);
     return run_count(J, b, o, (cudaStream_t)stream, counts, wcounts, st);
 }
 
@@ -906,6 +948,8 @@ extern "C" pc_status pc_count_cross(const pc_grid *g1, const pc_grid *g2, const 
     J.nhist = 1;
     J.is_auto = false;
     J.g0 = g1;
+    job_add_bounds(J, g1, true);
+    job_add_bounds(J, g2, false);
     return run_count(J, b, o, (cudaStream_t)stream, counts, wcounts, st);
 }
 
@@ -923,6 +967,7 @@ extern "C" pc_status pc_count_batch(const pc_grid *const *gs, int m, const pc_bi
             return fail(PC_EINVAL, "pc_count_batch: grids differ in box or cell size");
         if (wcounts && !gs[k]->weighted) return fail(PC_EINVAL, "pc_count_batch: grid has no weights");
         J.tasks.push_back(task_of(gs[k], gs[k], k, 1));
+        job_add_bounds(J, gs[k], k == 0);
     }
     J.nhist = m;
     J.is_auto = true;
@@ -1092,7 +1137,7 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
     if (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count))
         return fail(PC_EINVAL, "opts: shard_index must lie in [0, shard_count)");
     Plan P;
-    pc_status s = make_plan(b, g->g, g->pts_lo, g->pts_hi, true, P);
+    pc_status s = make_plan(b, g->g, g->pts_lo, g->pts_hi, grid_rmin(g), true, P);
     if (s != PC_OK) return s;
     int prec = o.prec;
     if (prec == PC_PREC_F32_RESCUE && !P.fp32_ok) prec = PC_PREC_F64;
@@ -1176,9 +1221,7 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
     p.counters = ctr;
     p.shard_count = o.shard_count > 1 ? o.shard_count : 1;
     p.shard_index = o.shard_count > 1 ? o.shard_index : 0;
-    int copies_warp = P.nbins * (NT / 32) * 4;
-    if (o.priv == 0 || o.priv == 1) p.priv = o.priv;
-    else p.priv = (P.nbins <= 2048 && copies_warp <= 48 * 1024) ? 1 : 0;
+    choose_replication(o.priv, P.nbins, wcounts != nullptr, p.priv, p.hist_k);
     p.lin = (prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
     p.lin_invA = P.lin_invA;
     p.lin_offA = P.lin_offA;
@@ -1190,11 +1233,11 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
     int sms = 0, smem_optin = 0;
     PC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur));
     PC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cur));
-    for (int attempt = 0; attempt < 3; ++attempt) {
+    for (;;) {
         p.smem_hist_ok = 1;
         size_t need = (prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, ipt);
         if (need + 256 <= (size_t)smem_optin) break;
-        if (p.priv) { p.priv = 0; continue; }
+        if (shrink_replication(p)) continue;
         p.smem_hist_ok = 0;
         break;
     }

@@ -32,17 +32,26 @@ __host__ __device__ __forceinline__ double dunkey(long long k) {
     return v;
 }
 
+// Bounds per axis and the smallest squared distance from the origin (the
+// observer of the midpoint line of sight), as order-preserving keys:
+// out[0..2] min, out[3..5] max, out[6] min of x^2 + y^2 + z^2 (rounded down
+// so it never exceeds the exact value).
 __global__ void k_aabb(const double *__restrict__ xyz, long long n, long long *out) {
     long long mn[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
     long long mx[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    long long r2min = LLONG_MAX;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
+        double r2 = 0.0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            long long k = dkey(xyz[3 * i + a]);
+            const double x = xyz[3 * i + a];
+            long long k = dkey(x);
             mn[a] = min(mn[a], k);
             mx[a] = max(mx[a], k);
+            r2 = __fma_rd(x, x, r2);
         }
+        r2min = min(r2min, dkey(r2));
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -51,16 +60,20 @@ __global__ void k_aabb(const double *__restrict__ xyz, long long n, long long *o
             mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
         }
     }
+    for (int o = 16; o > 0; o >>= 1) r2min = min(r2min, __shfl_xor_sync(0xffffffffu, r2min, o));
     if ((threadIdx.x & 31) == 0) {
         for (int a = 0; a < 3; ++a) {
             atomicMin(&out[a], mn[a]);
             atomicMax(&out[3 + a], mx[a]);
         }
+        atomicMin(&out[6], r2min);
     }
 }
 
-pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *lo, double *hi) {
-    long long init[6] = {LLONG_MAX, LLONG_MAX, LLONG_MAX, LLONG_MIN, LLONG_MIN, LLONG_MIN};
+pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *lo, double *hi,
+                      double *r2min) {
+    long long init[7] = {LLONG_MAX, LLONG_MAX, LLONG_MAX, LLONG_MIN, LLONG_MIN, LLONG_MIN,
+                         LLONG_MAX};
     long long *d = nullptr;
     PC_CUDA(cudaMallocAsync(&d, sizeof(init), st));
     PC_CUDA(cudaMemcpyAsync(d, init, sizeof(init), cudaMemcpyHostToDevice, st));
@@ -70,7 +83,7 @@ pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *l
         note_launch();
         PC_CUDA(cudaGetLastError());
     }
-    long long res[6];
+    long long res[7];
     PC_CUDA(cudaMemcpyAsync(res, d, sizeof(res), cudaMemcpyDeviceToHost, st));
     PC_CUDA(cudaFreeAsync(d, st));
     PC_CUDA(cudaStreamSynchronize(st));
@@ -78,6 +91,7 @@ pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *l
         lo[a] = dunkey(res[a]);
         hi[a] = dunkey(res[3 + a]);
     }
+    if (r2min) *r2min = n > 0 ? dunkey(res[6]) : 0.0;
     return PC_OK;
 }
 
@@ -463,7 +477,7 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
         }
     } else {
         if (n > 0) {
-            pc_status s = aabb_device(dxyz, n, st, plo, phi);
+            pc_status s = aabb_device(dxyz, n, st, plo, phi, &g->r2min);
             if (s != PC_OK) { cleanup(); delete g; return s; }
             for (int a = 0; a < 3; ++a)
                 if (!isfinite(plo[a]) || !isfinite(phi[a])) {

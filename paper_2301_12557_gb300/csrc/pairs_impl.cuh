@@ -43,11 +43,12 @@ __host__ __device__ inline SmemLayout smem_layout(const PairParams &p, bool f64)
     o = align_up(o + (size_t)(p.n_a + 1) * sizeof(double), 16);
     L.eb = o;
     o = align_up(o + (size_t)(p.n_b + 1) * sizeof(double), 16);
-    int copies = p.priv ? NT / 32 : 1;
+    int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
     L.hist = o;
     if (p.smem_hist_ok) o = align_up(o + (size_t)p.nbins * copies * sizeof(int), 16);
     L.whist = o;
-    if (p.smem_hist_ok && p.weighted) o = align_up(o + (size_t)p.nbins * sizeof(double), 16);
+    if (p.smem_hist_ok && p.weighted)
+        o = align_up(o + (size_t)p.nbins * p.hist_k * sizeof(double), 16);
     L.seg = o;
     o = align_up(o + (size_t)MAXSEG * sizeof(int4), 16);
     int tj = f64 ? TJ64 : TJ;
@@ -229,7 +230,9 @@ __device__ __forceinline__ void push_rescue(const PairParams &p, uint3 *s_q, int
     else inline_rescue<MODE, LOS>(p, e);
 }
 
-// Drain the CTA's staged rescue entries to the global queue (all threads).
+// Drain the CTA's staged rescue entries to the global queue.  All threads
+// call it, after a barrier that follows their last push, so every thread
+// reads the same count.
 template <int MODE, int LOS>
 __device__ __forceinline__ void drain_rescue(const PairParams &p, uint3 *s_q, CtaShared &cs,
                                              unsigned long long *s_base) {
@@ -253,17 +256,22 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
                                            int h) {
     __syncthreads();
     if (p.smem_hist_ok && h >= 0) {
-        const int copies = p.priv ? NT / 32 : 1;
+        // layout [warp copy][bin][lane copy]
+        const int copies = p.priv ? NT / 32 : 1, K = p.hist_k;
         for (int b = threadIdx.x; b < p.nbins; b += NT) {
             long long v = 0;
-            for (int c = 0; c < copies; ++c) {
-                v += s_hist[c * p.nbins + b];
-                s_hist[c * p.nbins + b] = 0;
-            }
+            for (int c = 0; c < copies; ++c)
+                for (int k = 0; k < K; ++k) {
+                    v += s_hist[(c * p.nbins + b) * K + k];
+                    s_hist[(c * p.nbins + b) * K + k] = 0;
+                }
             if (v) atomicAdd(&p.hist[(size_t)h * p.nbins + b], (unsigned long long)v);
             if (p.weighted) {
-                double w = s_whist[b];
-                s_whist[b] = 0.0;
+                double w = 0.0;
+                for (int k = 0; k < K; ++k) {
+                    w += s_whist[b * K + k];
+                    s_whist[b * K + k] = 0.0;
+                }
                 if (w != 0.0) atomicAdd(&p.whist[(size_t)h * p.nbins + b], w);
             }
         }
@@ -485,9 +493,9 @@ struct Tile {
 template <int MODE, int LOS, bool W, int RI, bool MASK>
 __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int len, unsigned gmask,
                                               const IPts<RI> &I, const BinCtx &bc, float r2cut,
-                                              unsigned hist_sa, unsigned whist_sa, uint3 *s_q,
-                                              int *s_qn, const int4 *s_seg, int nseg, int f0,
-                                              int bstart, unsigned task_bits) {
+                                              unsigned hist_sa, unsigned whist_sa, unsigned hk4,
+                                              uint3 *s_q, int *s_qn, const int4 *s_seg, int nseg,
+                                              int f0, int bstart, unsigned task_bits) {
 #pragma unroll 1
     for (unsigned gm = gmask; gm; gm &= gm - 1) {
     const int j0 = (__ffs(gm) - 1) * JG, j1 = min(j0 + JG, len);
@@ -518,8 +526,8 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
                 Bin32 b = bin_f32<MODE, LOS>(bc, dxv[r], dyv[r], dzv[r], qv[r], s2v[r], I.xa[r],
                                              I.ya[r], I.za[r]);
                 const bool add = inr[r] && b.ok && !b.near;
-                red_shared_u32_if(hist_sa + 4u * (unsigned)b.bin, add);
-                if (W) red_shared_f64_if(whist_sa + 8u * (unsigned)b.bin, __dmul_rn(I.w[r], wj), add);
+                red_shared_u32_if(hist_sa + hk4 * (unsigned)b.bin, add);
+                if (W) red_shared_f64_if(whist_sa + 2u * hk4 * (unsigned)b.bin, __dmul_rn(I.w[r], wj), add);
                 resc[r] = inr[r] && b.near;
                 anyr = anyr || resc[r];
             }
@@ -543,9 +551,9 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
 template <int MODE, bool W, int RI, bool MASK>
 __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int len, unsigned gmask,
                                                const IPts<RI> &I, const LinCtx &lc, float r2cut,
-                                               unsigned hist_sa, unsigned whist_sa, uint3 *s_q,
-                                               int *s_qn, const int4 *s_seg, int nseg, int f0,
-                                               int bstart, unsigned task_bits) {
+                                               unsigned hist_sa, unsigned whist_sa, unsigned hk4,
+                                               uint3 *s_q, int *s_qn, const int4 *s_seg, int nseg,
+                                               int f0, int bstart, unsigned task_bits) {
     const float2 C23 = make_float2(8388608.0f, 8388608.0f);
     const float2 NC23H = make_float2(-8388608.0f + 0.5f, -8388608.0f + 0.5f);
     const float2 M1 = make_float2(-1.0f, -1.0f);
@@ -561,8 +569,8 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
     const unsigned nbu = (MODE == MODE_SMU) ? lc.nB_u : 1u;
     // bias of the float bits of floor(t_s) + 2^23, folded into the bases
     const unsigned bias = 0x4B000000u * nbu;
-    const unsigned hbase = hist_sa - 4u * bias;
-    const unsigned wbase = whist_sa - 8u * bias;
+    const unsigned hbase = hist_sa - hk4 * bias;
+    const unsigned wbase = whist_sa - 2u * hk4 * bias;
     float2 NX[RI], NY[RI], NZ[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
@@ -624,12 +632,12 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                     b1 = b1 * nbu + (unsigned)j1;
                 }
                 const bool a0 = in0[r] && ok0 && !n0, a1 = in1[r] && ok1 && !n1;
-                red_shared_u32_if(hbase + 4u * b0, a0);
-                red_shared_u32_if(hbase + 4u * b1, a1);
+                red_shared_u32_if(hbase + hk4 * b0, a0);
+                red_shared_u32_if(hbase + hk4 * b1, a1);
                 if (W) {
                     const double2 wj = *reinterpret_cast<const double2 *>(tb.w + jj);
-                    red_shared_f64_if(wbase + 8u * b0, __dmul_rn(I.w[r], wj.x), a0);
-                    red_shared_f64_if(wbase + 8u * b1, __dmul_rn(I.w[r], wj.y), a1);
+                    red_shared_f64_if(wbase + 2u * hk4 * b0, __dmul_rn(I.w[r], wj.x), a0);
+                    red_shared_f64_if(wbase + 2u * hk4 * b1, __dmul_rn(I.w[r], wj.y), a1);
                 }
                 re0[r] = in0[r] && n0;
                 re1[r] = in1[r] && n1;
@@ -688,16 +696,19 @@ __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, T
                                           unsigned gmask,
                                           const IPts<RI> &I, const BinCtx &bc, const LinCtx &lc,
                                           float r2cut, unsigned hist_sa, unsigned whist_sa,
-                                          size_t hbase, uint3 *s_q, int *s_qn, const int4 *s_seg,
+                                          unsigned hk4, size_t hbase, uint3 *s_q, int *s_qn,
+                                          const int4 *s_seg,
                                           int nseg, int f0, int bstart, unsigned task_bits) {
     if (!smem_hist) {
         pair_tile_global<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hbase, s_q, s_qn, s_seg,
                                                  nseg, f0, bstart, task_bits);
     } else if (LIN) {
-        pair_tile_lin2<MODE, W, RI, MASK>(p, tb, len, gmask, I, lc, r2cut, hist_sa, whist_sa, s_q, s_qn,
+        pair_tile_lin2<MODE, W, RI, MASK>(p, tb, len, gmask, I, lc, r2cut, hist_sa, whist_sa, hk4,
+                                          s_q, s_qn,
                                           s_seg, nseg, f0, bstart, task_bits);
     } else {
-        pair_tile_lut<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hist_sa, whist_sa, s_q,
+        pair_tile_lut<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hist_sa, whist_sa,
+                                              hk4, s_q,
                                               s_qn, s_seg, nseg, f0, bstart, task_bits);
     }
 }
@@ -731,9 +742,9 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     const int nbins = p.nbins;
     const bool smem_hist = p.smem_hist_ok != 0;
     if (smem_hist) {
-        const int copies = p.priv ? NT / 32 : 1;
+        const int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
         for (int k = tid; k < nbins * copies; k += NT) s_hist[k] = 0;
-        if (W) for (int k = tid; k < nbins; k += NT) s_whist[k] = 0.0;
+        if (W) for (int k = tid; k < nbins * p.hist_k; k += NT) s_whist[k] = 0.0;
     }
     if (tid == 0) {
         cs.qn = 0;
@@ -764,9 +775,13 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     lc.nA = (unsigned)p.n_a;
     lc.nB_u = (unsigned)p.n_b;
     const float r2cut = p.r2cut;
+    // this thread's copy: warp copy (priv) and lane copy (tid % hist_k); bins
+    // are hist_k entries apart
+    const unsigned lane_copy = (unsigned)(tid & (p.hist_k - 1));
+    const unsigned hk4 = 4u * (unsigned)p.hist_k;
     const unsigned hist_sa = (unsigned)__cvta_generic_to_shared(s_hist) +
-                             (p.priv ? (unsigned)((tid >> 5) * nbins * 4) : 0u);
-    const unsigned whist_sa = (unsigned)__cvta_generic_to_shared(s_whist);
+                             (p.priv ? (unsigned)((tid >> 5) * nbins * 4) : 0u) + 4u * lane_copy;
+    const unsigned whist_sa = (unsigned)__cvta_generic_to_shared(s_whist) + 8u * lane_copy;
 
     const int nx = p.g.ng[0], ny = p.g.ng[1];
     const float c32x = p.g.c32[0], c32y = p.g.c32[1], c32z = p.g.c32[2];
@@ -846,7 +861,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
             __syncthreads();
             const int ngA = (lenA + JG - 1) / JG;    // <= 8 groups, all evaluated
             pair_tile<MODE, LOS, W, RI, LIN, true>(p, smem_hist, Tile{s_tx, s_ty, s_tz, s_tw}, lenA,
-                                                   (1u << ngA) - 1u, I, bc, lc, r2cut, hist_sa, whist_sa, hbase, s_q,
+                                                   (1u << ngA) - 1u, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q,
                                                    &cs.qn, s_seg, 0, -1, B.start, task_bits);
             if (tid == 0) cand_local += (unsigned long long)B.count * (B.count - 1) / 2;
             since_flush += (unsigned long long)B.count * B.count;
@@ -870,6 +885,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
             build_segments(p, T.gj, ax, ay, az, r0, r1, s_seg, &cs.nseg);
             __syncthreads();
             const int nseg = cs.nseg;
+            __syncthreads();                 // every thread has read nseg before it changes
             if (nseg == 0) continue;
             const int total = seg_scan(s_seg, nseg, s_tmp);
             const int ntiles = (total + TJ - 1) / TJ;
@@ -944,13 +960,16 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                                                &cs.pruned);
                 pair_tile<MODE, LOS, W, RI, LIN, false>(
                     p, smem_hist, Tile{s_tx + buf * TJ, s_ty + buf * TJ, s_tz + buf * TJ, s_tw + buf * TJ},
-                    (len + 1) & ~1, gm, I, bc, lc, r2cut, hist_sa, whist_sa, hbase, s_q, &cs.qn, s_seg,
+                    (len + 1) & ~1, gm, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q, &cs.qn, s_seg,
                     nseg, t * TJ, B.start, task_bits);
                 if (tid == 0) cand_local += (unsigned long long)len * B.count;
                 since_flush += (unsigned long long)len * B.count;
                 if (t + 1 < ntiles) store_tile(t + 1);
-                __syncthreads();
-                if (cs.qn >= LQ / 2) drain_rescue<MODE, LOS>(p, s_q, cs, &s_base);
+                // one decision for the whole CTA, taken at the barrier: read
+                // after it, the count could already include pushes of the next
+                // tile by a faster warp, and the drain holds barriers itself
+                if (__syncthreads_or(cs.qn >= LQ / 2))
+                    drain_rescue<MODE, LOS>(p, s_q, cs, &s_base);
                 if (since_flush > FLUSH_LIMIT) {
                     flush_hist(p, s_hist, s_whist, cur_hist);
                     since_flush = 0;
@@ -989,11 +1008,13 @@ __global__ void __launch_bounds__(NT) k_pairs_f64(const __grid_constant__ PairPa
     for (int k = tid; k <= p.n_a; k += NT) s_Ea[k] = p.Ea[k];
     for (int k = tid; k <= p.n_b; k += NT) s_Eb[k] = p.Eb[k];
     if (p.smem_hist_ok) {
-        const int copies = p.priv ? NT / 32 : 1;
+        const int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
         for (int k = tid; k < p.nbins * copies; k += NT) s_hist[k] = 0;
-        if (W) for (int k = tid; k < p.nbins; k += NT) s_whist[k] = 0.0;
+        if (W) for (int k = tid; k < p.nbins * p.hist_k; k += NT) s_whist[k] = 0.0;
     }
-    int *my_hist = s_hist + (p.priv ? (tid >> 5) * p.nbins : 0);
+    const int K = p.hist_k, lane_copy = tid & (K - 1);
+    int *my_hist = s_hist + (p.priv ? (tid >> 5) * p.nbins * K : 0) + lane_copy;
+    double *my_whist = s_whist + lane_copy;
     const int nx = p.g.ng[0], ny = p.g.ng[1];
     const int nblocks = *p.nblocks;
     unsigned long long cand_local = 0, since_flush = 0;
@@ -1020,8 +1041,8 @@ __global__ void __launch_bounds__(NT) k_pairs_f64(const __grid_constant__ PairPa
 
         auto add = [&](int bin, double wj) {
             if (p.smem_hist_ok) {
-                atomicAdd(&my_hist[bin], 1);
-                if (W) atomicAdd(&s_whist[bin], __dmul_rn(a.w, wj));
+                atomicAdd(&my_hist[bin * K], 1);
+                if (W) atomicAdd(&my_whist[bin * K], __dmul_rn(a.w, wj));
             } else {
                 atomicAdd(&p.hist[hbase + bin], 1ull);
                 if (W) atomicAdd(&p.whist[hbase + bin], __dmul_rn(a.w, wj));
@@ -1060,6 +1081,7 @@ __global__ void __launch_bounds__(NT) k_pairs_f64(const __grid_constant__ PairPa
             build_segments(p, T.gj, ax, ay, az, r0, r1, s_seg, &cs.nseg);
             __syncthreads();
             const int nseg = cs.nseg;
+            __syncthreads();                 // every thread has read nseg before it changes
             if (nseg == 0) continue;
             const int total = seg_scan(s_seg, nseg, s_tmp);
             for (int t0 = 0; t0 < total; t0 += TJ64) {

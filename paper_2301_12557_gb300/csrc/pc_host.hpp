@@ -16,6 +16,7 @@ struct pc_grid {
     int ncell;
     double cell_size;           // requested cubic cell side
     double pts_lo[3], pts_hi[3];  // bounds of the (canonical) points
+    double r2min = 0.0;           // non-periodic: lower bound of min |x|^2 over the points
     float4 *rel;
     uint16_t *cx;
     double4_32a *xw;
@@ -50,6 +51,8 @@ cudaError_t make_blocks_into(const TaskDev *tasks_dev, int ntasks, int ncell, in
 void forget_grid(const pc_grid *g);
 
 // Device-side bounding box; lo/hi are host arrays (the call synchronises).
-pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *lo, double *hi);
+// r2min (optional) receives a lower bound of min |x|^2 over the points.
+pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *lo, double *hi,
+                      double *r2min = nullptr);
 
 }  // namespace pc

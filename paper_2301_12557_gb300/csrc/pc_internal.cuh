@@ -90,6 +90,8 @@ struct PairParams {
     unsigned long long *counters;  // [0] candidates, [1] inline rescues
     int shard_index, shard_count;   // this launch counts blocks index * count + shard
     int priv;                // 0: one histogram per CTA; 1: one per warp
+    int hist_k = 1;          // lane copies of the shared histograms (power of 2, <= 32):
+                             // lane l updates copy l % hist_k, stored [bin][copy]
     int smem_hist_ok;        // histogram fits in shared memory
     // evenly spaced s (and mu) edges: bins by floor instead of tables
     int lin;

@@ -86,19 +86,44 @@ extern "C" pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, lon
     int dev = 0, sms = 1;
     PC_CUDA(cudaGetDevice(&dev));
     PC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // sample every S-th point block so that each trial still gives every
-    // persistent CTA several blocks
-    const double blocks_est = (double)n / (NT * 4);
-    const int S = std::max(1, (int)(blocks_est / (4.0 * 5.0 * sms)));
-
     const int nbins = b->n_a * (b->mode == PC_BIN_S ? 1 : b->n_b);
     DevBuf dc, dw;
     PC_CUDA(cudaMalloc(&dc.p, sizeof(long long) * nbins));
     if (w) PC_CUDA(cudaMalloc(&dw.p, sizeof(double) * nbins));
 
+    // Sample every S-th point block.  S starts where every persistent CTA
+    // still gets about four blocks, and grows (after one calibration run at
+    // the model's cell side) until a trial takes about TRIAL_MS, but never so
+    // far that a CTA gets fewer than two blocks.
+    const double ctas = 5.0 * sms;
+    const double blocks_est = std::max(1.0, (double)n / (NT * 4));
+    const int S_min = std::max(1, (int)(blocks_est / (4.0 * ctas)));
+    const int S_max = std::max(S_min, (int)(blocks_est / (2.0 * ctas)));
+    const float TRIAL_MS = 40.f;
+    int S = S_min;
+    {
+        pc_opts oc = o;
+        oc.cell_size = c0;
+        pc_grid *g = nullptr;
+        pc_status s = pc_build_grid(xyz, w, w_is_f32, n, box, reach, &oc, stream, &g);
+        if (s != PC_OK) return s;
+        oc.ipt = 2;
+        oc.shard_index = 0;
+        oc.shard_count = S;
+        pc_stats sts;
+        s = pc_count_auto(g, b, &oc, stream, (long long *)dc.p, (double *)dw.p, &sts);
+        pc_free_grid(g);
+        if (s != PC_OK) return s;
+        const float ms = sts.ms_pairs + sts.ms_rescue;
+        if (ms > TRIAL_MS)
+            S = std::min(S_max, (int)std::min(1e9, ceil(S * (double)ms / TRIAL_MS)));
+    }
+
     const double factors[] = {0.8, 1.0, 1.25, 1.6, 2.0};
     const int ipts[] = {2, 4};
     const bool fp32 = o.prec == PC_PREC_F32_RESCUE;
+    const bool fixed_priv = o.priv == 1 || o.priv == 2;
+    if (!fixed_priv) out->priv = 0;
     std::vector<long long> seen;
     float best_ms = INFINITY;
     int nt = 0;
@@ -127,12 +152,13 @@ extern "C" pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, lon
                 pc_stats sts;
                 s = pc_count_auto(g, b, &ot, stream, (long long *)dc.p, (double *)dw.p, &sts);
                 if (s == PC_OK) ms = std::min(ms, sts.ms_pairs + sts.ms_rescue);
+                if (ms > 4.f * TRIAL_MS) break;   // long trials: one repetition
             }
             if (s != PC_OK) {
                 pc_free_grid(g);
                 return s;
             }
-            if (nt < max_trials) trials[nt] = pc_tune_trial{c, ipt, o.priv, ms};
+            if (nt < max_trials) trials[nt] = pc_tune_trial{c, ipt, fixed_priv ? o.priv : 0, ms};
             ++nt;
             if (ms < best_ms) {
                 best_ms = ms;
@@ -142,9 +168,9 @@ extern "C" pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, lon
         }
         pc_free_grid(g);
     }
-    // histogram privatisation (one shared copy vs one per warp) at the best
-    // cell side and i-tile, unless the caller fixed it
-    if (o.priv == 0 && std::isfinite(best_ms)) {
+    // histogram replication (automatic vs one copy per warp) at the best cell
+    // side and i-tile, unless the caller fixed it
+    if (!fixed_priv && std::isfinite(best_ms)) {
         pc_opts oc = *out;
         pc_grid *g = nullptr;
         pc_status s = pc_build_grid(xyz, w, w_is_f32, n, box, reach, &oc, stream, &g);
@@ -158,6 +184,7 @@ extern "C" pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, lon
             pc_stats sts;
             s = pc_count_auto(g, b, &ot, stream, (long long *)dc.p, (double *)dw.p, &sts);
             if (s == PC_OK) ms = std::min(ms, sts.ms_pairs + sts.ms_rescue);
+            if (ms > 4.f * TRIAL_MS) break;
         }
         pc_free_grid(g);
         if (s != PC_OK) return s;

@@ -192,6 +192,23 @@ def test_cell_size_does_not_change_counts(cell):
         _check(g, want, what=f"cell {cell} ipt {ipt}")
 
 
+@pytest.mark.parametrize("nb", [8, 40, 400])
+def test_histogram_replication_modes(nb):
+    """Automatic lane copies (up to 32), one count copy per warp and one shared
+    copy all give the oracle's counts and weighted sums; few bins stress the
+    collisions that the lane copies remove."""
+    L = 300.0
+    x = synth.neyman_scott(20000, 2000, 10.0, 3.0, L, 211)
+    w = synth.lognormal_weights(x.shape[0], 0.3, 212)
+    ea = np.linspace(0.0, 30.0, nb + 1)
+    want, wantw = oracle.count(x, w1=w, box=L, periodic=True, edges_a=ea, method="grid")
+    for priv in (0, 1, 2):
+        got, gotw = P.count(x, w1=w, box=L, periodic=True, edges_a=ea, priv=priv)
+        _check(got, want, gotw, wantw, f"{nb} bins, priv {priv}")
+        got64, gotw64 = P.count(x, w1=w, box=L, periodic=True, edges_a=ea, priv=priv, prec="f64")
+        _check(got64, want, gotw64, wantw, f"{nb} bins, priv {priv}, f64")
+
+
 def test_device_tensors_and_device_outputs():
     L = 100.0
     x = synth.neyman_scott(4000, 400, 10.0, 2.0, L, 201)
@@ -325,13 +342,33 @@ def test_workload_ns_smu_scaled():
 
 
 def test_workload_survey_scaled_weighted():
+    """The survey shell: its bounding box comes within ~430 Mpc/h of the
+    observer, but every point lies at r >= 1000, so the FP32 midpoint bound
+    holds and the FP32 path must run (stats.prec == 0)."""
     w = W.WORKLOADS["survey_shell_d1m_r20m_sigpi40x40"]
     inp = W.make_inputs(w, scale=0.004)    # D 4,000, R 80,000
     kw = dict(periodic=False, mode="sigpi", los="mid", edges_a=w.edges_a, edges_b=w.edges_b)
-    (g, gw), (o, ow) = _both(inp["D"], w1=inp["wD"], **kw)
+    g, gw, st = P.count(inp["D"], w1=inp["wD"], return_stats=True, **kw)
+    o, ow = oracle.count(inp["D"], w1=inp["wD"], method="grid", **kw)
+    assert st.prec == P.PC_PREC_F32_RESCUE
     _check(g, o, gw, ow, "survey DD")
-    (g, gw), (o, ow) = _both(inp["D"], inp["R"], w1=inp["wD"], w2=inp["wR"], **kw)
+    g, gw, st = P.count(inp["D"], inp["R"], w1=inp["wD"], w2=inp["wR"], return_stats=True, **kw)
+    o, ow = oracle.count(inp["D"], inp["R"], w1=inp["wD"], w2=inp["wR"], method="grid", **kw)
+    assert st.prec == P.PC_PREC_F32_RESCUE
     _check(g, o, gw, ow, "survey DR")
+
+
+def test_midpoint_near_observer_runs_fp64():
+    """Points around the observer: |x_i + x_j| has no useful lower bound, the
+    FP32 error band does not hold, and the library runs the FP64 path."""
+    rng = np.random.default_rng(404)
+    x = rng.uniform(-60.0, 60.0, size=(3000, 3))
+    kw = dict(periodic=False, mode="sigpi", los="mid", edges_a=np.linspace(0, 20, 5),
+              edges_b=np.linspace(0, 20, 5))
+    g, _, st = P.count(x, return_stats=True, **kw)
+    o, _ = oracle.count(x, method="grid", **kw)
+    assert st.prec == P.PC_PREC_F64
+    _check(g, o, what="midpoint near the observer")
 
 
 def test_workload_mixed_weighted_scaled():
