@@ -106,6 +106,7 @@ struct Plan {
     // evenly spaced edges: bins by floor (see PairParams::lin*)
     int lin = 0;
     float lin_invA = 0, lin_offA = 0, lin_thrA = 0, lin_nB = 0, lin_mA = 0, lin_cB = 0;
+    int lin_norange = 0;
 };
 
 static bool edges_ok(const double *e, int n, bool zero_one) {
@@ -361,6 +362,9 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
                 P.lin_invA = (float)(1.0 / D);
                 P.lin_offA = (float)(-e0 / D);
                 P.lin_thrA = nextafterf((float)(0.5 - eps_t), 0.0f);
+                // e_0 = 0: t_s = s / D >= 0; and every candidate has t_s below
+                // n_a + 1/2 (plus rounding), so floor(t_s) <= n_a
+                P.lin_norange = (e0 == 0.0 && ts_max - 1.0 <= P.na + 0.5) ? 1 : 0;
                 if (P.mode == PC_BIN_SMU) {
                     const double nb = P.nb;
                     P.lin_nB = (float)nb;
@@ -597,6 +601,8 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     p.shard_index = S.o.shard_count > 1 ? S.o.shard_index : 0;
     choose_replication(S.o.priv, P.nbins, S.weighted, p.priv, p.hist_k);
     p.lin = (S.prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
+    p.lin_norange = p.lin ? P.lin_norange : 0;
+    p.nbins_smem = P.nbins + (p.lin_norange ? (P.mode == PC_BIN_S ? 1 : P.nb) : 0);
     p.lin_invA = P.lin_invA;
     p.lin_offA = P.lin_offA;
     p.lin_thrA = P.lin_thrA;
@@ -1223,6 +1229,8 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
     p.shard_index = o.shard_count > 1 ? o.shard_index : 0;
     choose_replication(o.priv, P.nbins, wcounts != nullptr, p.priv, p.hist_k);
     p.lin = (prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
+    p.lin_norange = p.lin ? P.lin_norange : 0;
+    p.nbins_smem = P.nbins + (p.lin_norange ? (P.mode == PC_BIN_S ? 1 : P.nb) : 0);
     p.lin_invA = P.lin_invA;
     p.lin_offA = P.lin_offA;
     p.lin_thrA = P.lin_thrA;

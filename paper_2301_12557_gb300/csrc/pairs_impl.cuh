@@ -45,10 +45,10 @@ __host__ __device__ inline SmemLayout smem_layout(const PairParams &p, bool f64)
     o = align_up(o + (size_t)(p.n_b + 1) * sizeof(double), 16);
     int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
     L.hist = o;
-    if (p.smem_hist_ok) o = align_up(o + (size_t)p.nbins * copies * sizeof(int), 16);
+    if (p.smem_hist_ok) o = align_up(o + (size_t)p.nbins_smem * copies * sizeof(int), 16);
     L.whist = o;
     if (p.smem_hist_ok && p.weighted)
-        o = align_up(o + (size_t)p.nbins * p.hist_k * sizeof(double), 16);
+        o = align_up(o + (size_t)p.nbins_smem * p.hist_k * sizeof(double), 16);
     L.seg = o;
     o = align_up(o + (size_t)MAXSEG * sizeof(int4), 16);
     int tj = f64 ? TJ64 : TJ;
@@ -256,15 +256,21 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
                                            int h) {
     __syncthreads();
     if (p.smem_hist_ok && h >= 0) {
-        // layout [warp copy][bin][lane copy]
-        const int copies = p.priv ? NT / 32 : 1, K = p.hist_k;
-        for (int b = threadIdx.x; b < p.nbins; b += NT) {
+        // layout [warp copy][bin][lane copy]; bins past nbins form the
+        // discarded row of lin_norange and are only cleared
+        const int copies = p.priv ? NT / 32 : 1, K = p.hist_k, nbs = p.nbins_smem;
+        for (int b = threadIdx.x; b < nbs; b += NT) {
             long long v = 0;
             for (int c = 0; c < copies; ++c)
                 for (int k = 0; k < K; ++k) {
-                    v += s_hist[(c * p.nbins + b) * K + k];
-                    s_hist[(c * p.nbins + b) * K + k] = 0;
+                    v += s_hist[(c * nbs + b) * K + k];
+                    s_hist[(c * nbs + b) * K + k] = 0;
                 }
+            if (b >= p.nbins) {
+                if (p.weighted)
+                    for (int k = 0; k < K; ++k) s_whist[b * K + k] = 0.0;
+                continue;
+            }
             if (v) atomicAdd(&p.hist[(size_t)h * p.nbins + b], (unsigned long long)v);
             if (p.weighted) {
                 double w = 0.0;
@@ -548,7 +554,7 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
 // is near an edge unless |frac(t_s) - 1/2| < thrA; mu likewise with its
 // per-pair band.  Histogram addresses are formed from the float bits of
 // floor(t) + 2^23, with the 2^23 bias folded into the base address.
-template <int MODE, bool W, int RI, bool MASK>
+template <int MODE, bool W, int RI, bool MASK, bool CHK>
 __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int len, unsigned gmask,
                                                const IPts<RI> &I, const LinCtx &lc, float r2cut,
                                                unsigned hist_sa, unsigned whist_sa, unsigned hk4,
@@ -565,10 +571,11 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
     const float halfA = 0.5f * (float)lc.nA;
     const float2 NHALFA = make_float2(-halfA, -halfA);
     const float thrA = lc.thrA;
-    const int nb1 = (int)lc.nB_u - 1;
+    const unsigned jmax = 0x4B000000u + lc.nB_u - 1u;   // float bits of 2^23 + n_mu - 1
     const unsigned nbu = (MODE == MODE_SMU) ? lc.nB_u : 1u;
-    // bias of the float bits of floor(t_s) + 2^23, folded into the bases
-    const unsigned bias = 0x4B000000u * nbu;
+    // biases of the float bits of floor(t_s) + 2^23 (and floor(t_mu) + 2^23),
+    // folded into the bases
+    const unsigned bias = 0x4B000000u * nbu + ((MODE == MODE_SMU) ? 0x4B000000u : 0u);
     const unsigned hbase = hist_sa - hk4 * bias;
     const unsigned wbase = whist_sa - 2u * hk4 * bias;
     float2 NX[RI], NY[RI], NZ[RI];
@@ -613,8 +620,12 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                 const float2 ts = __ffma2_rn(__fmul2_rn(s2, rs), INVA, OFFA);
                 const float2 f = __fadd2_rd(ts, C23);
                 const float2 d = __ffma2_rn(__fadd2_rn(f, NC23H), M1, ts);   // frac - 1/2
-                const float2 o = __fadd2_rn(ts, NHALFA);
-                const bool ok0 = fabsf(o.x) < halfA, ok1 = fabsf(o.y) < halfA;
+                bool ok0 = true, ok1 = true;
+                if (CHK) {
+                    const float2 o = __fadd2_rn(ts, NHALFA);
+                    ok0 = fabsf(o.x) < halfA;
+                    ok1 = fabsf(o.y) < halfA;
+                }
                 // NaN (s2 = 0) compares false: such pairs are near
                 bool n0 = !(fabsf(d.x) < thrA), n1 = !(fabsf(d.y) < thrA);
                 unsigned b0 = (unsigned)__float_as_int(f.x), b1 = (unsigned)__float_as_int(f.y);
@@ -626,10 +637,11 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                     const float2 thm = __ffma2_rn(NMA, rs, CB);
                     n0 = n0 || !(fabsf(dm.x) < thm.x);
                     n1 = n1 || !(fabsf(dm.y) < thm.y);
-                    const int j0 = min(__float_as_int(fm.x) - 0x4B000000, nb1);
-                    const int j1 = min(__float_as_int(fm.y) - 0x4B000000, nb1);
-                    b0 = b0 * nbu + (unsigned)j0;
-                    b1 = b1 * nbu + (unsigned)j1;
+                    // mu = 1 (t_mu = n_mu) goes to the last bin; NaN bits clamp too
+                    const unsigned j0 = min((unsigned)__float_as_int(fm.x), jmax);
+                    const unsigned j1 = min((unsigned)__float_as_int(fm.y), jmax);
+                    b0 = b0 * nbu + j0;
+                    b1 = b1 * nbu + j1;
                 }
                 const bool a0 = in0[r] && ok0 && !n0, a1 = in1[r] && ok1 && !n1;
                 red_shared_u32_if(hbase + hk4 * b0, a0);
@@ -703,8 +715,13 @@ __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, T
         pair_tile_global<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hbase, s_q, s_qn, s_seg,
                                                  nseg, f0, bstart, task_bits);
     } else if (LIN) {
-        pair_tile_lin2<MODE, W, RI, MASK>(p, tb, len, gmask, I, lc, r2cut, hist_sa, whist_sa, hk4,
-                                          s_q, s_qn,
+        if (p.lin_norange)
+            pair_tile_lin2<MODE, W, RI, MASK, false>(p, tb, len, gmask, I, lc, r2cut, hist_sa,
+                                                     whist_sa, hk4, s_q, s_qn, s_seg, nseg, f0,
+                                                     bstart, task_bits);
+        else
+            pair_tile_lin2<MODE, W, RI, MASK, true>(p, tb, len, gmask, I, lc, r2cut, hist_sa,
+                                                    whist_sa, hk4, s_q, s_qn,
                                           s_seg, nseg, f0, bstart, task_bits);
     } else {
         pair_tile_lut<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hist_sa, whist_sa,
@@ -743,8 +760,8 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     const bool smem_hist = p.smem_hist_ok != 0;
     if (smem_hist) {
         const int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
-        for (int k = tid; k < nbins * copies; k += NT) s_hist[k] = 0;
-        if (W) for (int k = tid; k < nbins * p.hist_k; k += NT) s_whist[k] = 0.0;
+        for (int k = tid; k < p.nbins_smem * copies; k += NT) s_hist[k] = 0;
+        if (W) for (int k = tid; k < p.nbins_smem * p.hist_k; k += NT) s_whist[k] = 0.0;
     }
     if (tid == 0) {
         cs.qn = 0;
@@ -780,7 +797,8 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     const unsigned lane_copy = (unsigned)(tid & (p.hist_k - 1));
     const unsigned hk4 = 4u * (unsigned)p.hist_k;
     const unsigned hist_sa = (unsigned)__cvta_generic_to_shared(s_hist) +
-                             (p.priv ? (unsigned)((tid >> 5) * nbins * 4) : 0u) + 4u * lane_copy;
+                             (p.priv ? (unsigned)((tid >> 5) * p.nbins_smem * p.hist_k * 4) : 0u) +
+                             4u * lane_copy;
     const unsigned whist_sa = (unsigned)__cvta_generic_to_shared(s_whist) + 8u * lane_copy;
 
     const int nx = p.g.ng[0], ny = p.g.ng[1];
@@ -1009,11 +1027,11 @@ __global__ void __launch_bounds__(NT) k_pairs_f64(const __grid_constant__ PairPa
     for (int k = tid; k <= p.n_b; k += NT) s_Eb[k] = p.Eb[k];
     if (p.smem_hist_ok) {
         const int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
-        for (int k = tid; k < p.nbins * copies; k += NT) s_hist[k] = 0;
-        if (W) for (int k = tid; k < p.nbins * p.hist_k; k += NT) s_whist[k] = 0.0;
+        for (int k = tid; k < p.nbins_smem * copies; k += NT) s_hist[k] = 0;
+        if (W) for (int k = tid; k < p.nbins_smem * p.hist_k; k += NT) s_whist[k] = 0.0;
     }
     const int K = p.hist_k, lane_copy = tid & (K - 1);
-    int *my_hist = s_hist + (p.priv ? (tid >> 5) * p.nbins * K : 0) + lane_copy;
+    int *my_hist = s_hist + (p.priv ? (tid >> 5) * p.nbins_smem * K : 0) + lane_copy;
     double *my_whist = s_whist + lane_copy;
     const int nx = p.g.ng[0], ny = p.g.ng[1];
     const int nblocks = *p.nblocks;

@@ -99,6 +99,11 @@ struct PairParams {
     float lin_thrA;              // not near an edge iff |frac(t_s) - 1/2| < lin_thrA
     float lin_nB;                // t_mu = mu * lin_nB
     float lin_mA, lin_cB;        // not near iff |frac(t_mu) - 1/2| < lin_cB - lin_mA / s
+    // lin with e_0 = 0 and every candidate below n_a + 1 bin widths: t_s >= 0,
+    // floor(t_s) <= n_a, so the s-range test is replaced by one discarded row
+    // (row n_a) of the shared histogram
+    int lin_norange;
+    int nbins_smem;              // bins per shared copy: nbins, plus n_b with lin_norange
 };
 
 // ---------------------------------------------------------------------------
