@@ -614,12 +614,17 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     PC_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, S.dev));
     PC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S.dev));
     const int static_smem = 256;
+    const int lut_size = p.lut_total;
     for (;;) {
         p.smem_hist_ok = 1;
+        // the floor-based bins need no tables (they serve only the global-
+        // histogram variant)
+        p.lut_total = p.lin ? 0 : lut_size;
         size_t need = (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
         if (need + static_smem <= (size_t)smem_optin) break;
         if (shrink_replication(p)) continue;
         p.smem_hist_ok = 0;
+        p.lut_total = lut_size;
         break;
     }
     smem = (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
@@ -1241,12 +1246,15 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
     int sms = 0, smem_optin = 0;
     PC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur));
     PC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cur));
+    const int lut_size = p.lut_total;
     for (;;) {
         p.smem_hist_ok = 1;
+        p.lut_total = p.lin ? 0 : lut_size;
         size_t need = (prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, ipt);
         if (need + 256 <= (size_t)smem_optin) break;
         if (shrink_replication(p)) continue;
         p.smem_hist_ok = 0;
+        p.lut_total = lut_size;
         break;
     }
     size_t smem = (prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, ipt);

@@ -16,8 +16,9 @@ namespace pc {
 constexpr int NT = 128;        // threads per CTA
 constexpr int TJ = 512;        // j points per shared-memory tile (FP32 path)
 constexpr int TJ64 = 128;      // j points per tile (FP64 path)
-constexpr int MAXSEG = 320;    // j segments per chunk of stencil rows
-constexpr int ROWCHUNK = 96;   // stencil rows per chunk (<= 3 segments each)
+constexpr int MAXSEG = 256;    // j segments per chunk of stencil rows
+constexpr int ROWCHUNK = 84;   // stencil rows per chunk (<= 3 segments each)
+static_assert(3 * ROWCHUNK + 1 <= MAXSEG, "a chunk's segments (and the own-cell rest) fit");
 constexpr int LQ = 256;        // per-CTA rescue staging slots
 constexpr int MAX_LUT = 8192;  // LUT entries per histogram axis
 
