@@ -59,7 +59,8 @@ def parse():
                          "one independent catalogue per rank (replicas, weak scaling)")
     ap.add_argument("--volume-scale", type=float, default=1.0,
                     help="same density in a box of this fraction of the volume "
-                         "(small cases for profiling; 1 = the full workload)")
+                         "(small cases for profiling; 1 = the full workload); for the "
+                         "weighted and multi-catalogue workloads: N scaled in the same volume")
     return ap.parse_args()
 
 
@@ -573,12 +574,154 @@ def run_batch(args):
     return 0
 
 
+def run_sets(args):
+    """Workloads with weights and several pair kinds (the survey shell's DD,
+    DR and RR; the 100M-point weighted cube): every step builds every
+    catalogue's grid and runs every count, weighted sums in binary64."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2301_12557_gb300 as P
+    from synth import workloads as W
+
+    P.lib()
+    w = W.WORKLOADS[args.workload]
+    inp = W.make_inputs(w, scale=args.volume_scale)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    names = ["D"] + (["R"] if "R" in inp else [])
+    host = {k: (inp[k], inp.get("w" + k)) for k in names}
+    devc = {k: (torch.from_numpy(x).to(dev), torch.from_numpy(wt).to(dev) if wt is not None else None)
+            for k, (x, wt) in host.items()}
+    bins = P.Bins(w.mode, w.los, w.edges_a, w.edges_b)
+    if w.periodic:
+        box = P.make_box(w.L, True)
+    else:
+        lo = np.full(3, np.inf)
+        hi = np.full(3, -np.inf)
+        for k in names:
+            a, b = P.pc_aabb(devc[k][0])
+            lo, hi = np.minimum(lo, a), np.maximum(hi, b)
+        box = P.make_box(None, False, lo, hi)
+    big = max(names, key=lambda k: host[k][0].shape[0])
+    tuning = None
+    if args.cell_size > 0 or args.ipt > 0:
+        opts = P.make_opts("f32", args.cell_size, args.ipt)
+    else:
+        t0 = time.perf_counter()
+        opts, trials = P.pc_tune(devc[big][0], devc[big][1], box=box, bins=bins, stream=stream)
+        tuning = {"seconds": time.perf_counter() - t0, "on": big,
+                  "trials": [{"cell_size": round(c, 3), "ipt": i, "priv": pv, "ms": round(ms, 3)}
+                             for c, i, pv, ms in trials]}
+    kinds = list(w.pair_kinds)
+    outs = {k: (torch.zeros(bins.nbins, dtype=torch.int64, device=dev),
+                torch.zeros(bins.nbins, dtype=torch.float64, device=dev)) for k in kinds}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(cats=devc, results=outs):
+        gs = {k: P.pc_build_grid(x, wt, box=box, r_max=bins.r_max, opts=opts, stream=stream)
+              for k, (x, wt) in cats.items()}
+        stats = {}
+        try:
+            for kind in kinds:
+                a, b = gs[kind[0]], gs[kind[1]]
+                c, wc = results[kind]
+                if kind[0] == kind[1]:
+                    _, _, st = P.pc_count_auto(a, bins, opts, stream, counts=c, wcounts=wc)
+                else:
+                    _, _, st = P.pc_count_cross(a, b, bins, opts, stream, counts=c, wcounts=wc)
+                stats[kind] = st
+        finally:
+            for g in gs.values():
+                g.free()
+        return stats
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = P.pc_launch_count()
+    ms, stats = [], None
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        stats = step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    launches = P.pc_launch_count() - l0
+    clocks = sampler.stop()
+    t_step = statistics.mean(ms)
+    inr = {k: int(outs[k][0].sum().item()) for k in kinds}
+    value = sum(inr.values()) / (t_step * 1e-3)
+
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned = {k: (torch.from_numpy(x).pin_memory(),
+                      torch.from_numpy(wt).pin_memory() if wt is not None else None)
+                  for k, (x, wt) in host.items()}
+        hout = {k: (np.zeros(bins.nbins, dtype=np.int64), np.zeros(bins.nbins, dtype=np.float64))
+                for k in kinds}
+        e_ms = []
+        for _ in range(args.e2e_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(pinned, hout)
+            b.record(stream)
+            torch.cuda.synchronize()
+            e_ms.append(a.elapsed_time(b))
+        for k in kinds:
+            assert np.array_equal(hout[k][0], outs[k][0].cpu().numpy()), k
+        h2d = sum(x.nbytes + (wt.nbytes if wt is not None else 0) for x, wt in host.values())
+        e2e = {"value": sum(inr.values()) / (statistics.mean(e_ms) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(len(kinds) * bins.nbins * 16),
+               "ms_per_step": statistics.mean(e_ms)}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        x, wt = host[big]
+        r, dt, m, cores, evals = oracle_sample_rate(x, w, args.cpu_seconds, L=w.L)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{m} random {big} points x all {x.shape[0]} {big} points (brute force, "
+                         f"binary64, unweighted), {dt:.1f} s; in-range pairs found per second",
+               "pair_evaluations_per_s": evals}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name if args.volume_scale == 1.0 else
+                   f"{w.name} at N x{args.volume_scale}",
+                   "catalogues": {k: int(host[k][0].shape[0]) for k in names},
+                   "pair_kinds": kinds, "weighted": bool(w.weighted),
+                   "precision": "FP32 separations, binary64 rescue near bin edges, int64 counts, "
+                                "binary64 weighted sums",
+                   "unit_of_work": "in-range pairs binned over all pair kinds",
+                   "cell_size": opts.cell_size, "ipt": opts.ipt, "priv": opts.priv,
+                   "tuning": tuning, "l2": "flushed between timed steps (256 MiB write)"},
+        "per_kind": {k: {"in_range_pairs": inr[k], "ms_pairs": stats[k].ms_pairs,
+                         "ms_total": stats[k].ms_total, "candidates": stats[k].candidates,
+                         "pruned": stats[k].pruned, "rescued": stats[k].rescued,
+                         "prec": "f32+rescue" if stats[k].prec == 0 else "f64"} for k in kinds},
+        "roofline": None,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload.startswith("mocks"):
         return run_batch(args)
+    from synth import workloads as W
+    w = W.WORKLOADS[args.workload]
+    if w.weighted or len(w.pair_kinds) > 1:
+        return run_sets(args)
     return run_ours(args)
 
 
