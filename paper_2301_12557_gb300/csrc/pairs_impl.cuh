@@ -81,7 +81,7 @@ struct GBox {
 };
 constexpr int JG = 32;           // j-points per bounding-box group
 static_assert(TJ % JG == 0 && TJ / JG <= 32, "group masks are one 32-bit ballot");
-static_assert(NT % JG == 0, "each warp stages whole groups");
+static_assert(NT % JG == 0 && (JG == 16 || JG == 32), "each warp stages whole groups");
 
 // Order-preserving map of binary32 onto int32 (its own inverse): a < b as
 // floats iff fkey(a) < fkey(b) as signed integers.
@@ -95,6 +95,28 @@ __device__ __forceinline__ float warp_minf(float v) {
 }
 __device__ __forceinline__ float warp_maxf(float v) {
     return fkey_inv(__reduce_max_sync(0xffffffffu, fkey(v)));
+}
+
+// Box of the JG consecutive lanes that hold one staged j-group (lanes
+// without a point pass valid = false); every lane gets its group's box.
+__device__ __forceinline__ GBox lane_group_box(float x, float y, float z, bool valid) {
+    float lx = valid ? x : INFINITY, ly = valid ? y : INFINITY, lz = valid ? z : INFINITY;
+    float hx = valid ? x : -INFINITY, hy = valid ? y : -INFINITY, hz = valid ? z : -INFINITY;
+    if (JG == 32) {
+        lx = warp_minf(lx); ly = warp_minf(ly); lz = warp_minf(lz);
+        hx = warp_maxf(hx); hy = warp_maxf(hy); hz = warp_maxf(hz);
+    } else {
+#pragma unroll
+        for (int o = JG / 2; o > 0; o >>= 1) {   // stays inside each half-warp
+            lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+            ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+            lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+            hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+            hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+            hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        }
+    }
+    return GBox{make_float4(lx, ly, lz, 0.f), make_float4(hx, hy, hz, 0.f)};
 }
 
 // Groups of the staged tile that may hold a pair in range of this warp's
@@ -877,9 +899,10 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                 }
             }
             __syncthreads();
-            const int ngA = (lenA + JG - 1) / JG;    // <= 8 groups, all evaluated
+            const int ngA = (lenA + JG - 1) / JG;    // all groups evaluated
+            const unsigned maskA = ngA >= 32 ? 0xffffffffu : (1u << ngA) - 1u;
             pair_tile<MODE, LOS, W, RI, LIN, true>(p, smem_hist, Tile{s_tx, s_ty, s_tz, s_tw}, lenA,
-                                                   (1u << ngA) - 1u, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q,
+                                                   maskA, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q,
                                                    &cs.qn, s_seg, 0, -1, B.start, task_bits);
             if (tid == 0) cand_local += (unsigned long long)B.count * (B.count - 1) / 2;
             since_flush += (unsigned long long)B.count * B.count;
@@ -954,16 +977,9 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                         s_tz[buf * TJ + slot] = z;
                         if (W) s_tw[buf * TJ + slot] = wv;
                     }
-                    // box of the warp's 32 consecutive slots = one j-group
-                    const float lx = warp_minf(rv[s] ? x : INFINITY);
-                    const float ly = warp_minf(rv[s] ? y : INFINITY);
-                    const float lz = warp_minf(rv[s] ? z : INFINITY);
-                    const float hx = warp_maxf(rv[s] ? x : -INFINITY);
-                    const float hy = warp_maxf(rv[s] ? y : -INFINITY);
-                    const float hz = warp_maxf(rv[s] ? z : -INFINITY);
-                    if ((tid & 31) == 0)
-                        s_gbox[buf][slot / JG] = GBox{make_float4(lx, ly, lz, 0.f),
-                                                      make_float4(hx, hy, hz, 0.f)};
+                    // boxes of the j-groups (JG consecutive slots each)
+                    const GBox gb = lane_group_box(x, y, z, rv[s]);
+                    if ((tid & (JG - 1)) == 0) s_gbox[buf][slot / JG] = gb;
                 }
             };
 
