@@ -610,7 +610,7 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
 #pragma unroll 1
     for (unsigned gm = gmask; gm; gm &= gm - 1) {
     const int j0 = (__ffs(gm) - 1) * JG, j1 = min(j0 + JG, len);
-#pragma unroll 2
+#pragma unroll 4
     for (int jj = j0; jj < j1; jj += 2) {
         const float2 X = *reinterpret_cast<const float2 *>(tb.x + jj);
         const float2 Y = *reinterpret_cast<const float2 *>(tb.y + jj);
