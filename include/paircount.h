@@ -116,6 +116,12 @@ typedef struct {
     int prec;                    /* pc_prec that ran: PC_PREC_F64 also when FP32 was asked
                                     for but its error bound does not hold (midpoint line of
                                     sight with the observer too close to the points) */
+    int wsum;                    /* weighted sums: 0 none; 1 binary64 products w_i w_j;
+                                    2 exact products of binary32 significands accumulated
+                                    as integers (evenly spaced bins, small histograms, every
+                                    weight a non-negative normal binary32 value or zero and
+                                    the two grids' weight exponents spanning at most 12;
+                                    truncation below 2^-34 relative), flushed in binary64 */
 } pc_stats;
 
 typedef struct pc_grid pc_grid;  /* opaque; owned by the library */

@@ -55,7 +55,7 @@ class pc_stats(ctypes.Structure):
                 ("rescue_inline", c_longlong), ("blocks", c_longlong),
                 ("cell_size", c_double), ("ms_total", c_float), ("ms_pairs", c_float),
                 ("ms_rescue", c_float), ("launches", c_int),
-                ("pruned", c_longlong), ("prec", c_int)]
+                ("pruned", c_longlong), ("prec", c_int), ("wsum", c_int)]
 
 
 class pc_tune_trial(ctypes.Structure):

@@ -425,7 +425,19 @@ struct CountJob {
     // bounds of the points of every grid involved, and a lower bound of |x|
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     double rmin = 0.0;
+    bool wint_ok = true;   // every task's grids allow the integer weight path
 };
+
+// Integer weight products are truncated by at most 2^(k_i + k_j - 46)
+// relative, k the exponent offset of a weight below its grid's largest; the
+// exponent spans of the two grids are limited so that this stays below
+// 2^-34 (6e-11) per product and hence per bin.
+constexpr int WINT_MAX_SPAN = 12;
+static void job_add_wint(CountJob &J, const pc_grid *gi, const pc_grid *gj) {
+    if (!gi->wint || !gj->wint ||
+        (gi->wemax - gi->wemin) + (gj->wemax - gj->wemin) > WINT_MAX_SPAN)
+        J.wint_ok = false;
+}
 
 // Lower bound of |x| over the points of a grid (0 when unknown or periodic).
 static double grid_rmin(const pc_grid *g) {
@@ -448,6 +460,7 @@ struct CountSetup {
     pc_opts o;
     int prec = 0, ipt = 2, bi = 256, dev = 0, ntasks = 0, ncell = 0;
     bool weighted = false;
+    int wsum = 0;   // weighted sums: 0 none, 1 binary64 products, 2 integer products
     size_t nblk_cap = 0, hist_n = 0;
     unsigned long long qcap = 0;
 };
@@ -628,6 +641,10 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
         break;
     }
     smem = (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
+    // integer weight products need floor bins, shared histograms and enough
+    // lane copies that a u64 copy is flushed no more often than every 8 tiles
+    p.wint = (S.weighted && p.lin && p.smem_hist_ok && !p.priv && p.hist_k >= 16 && J.wint_ok &&
+              S.prec == PC_PREC_F32_RESCUE) ? 1 : 0;
     if (smem + static_smem > (size_t)smem_optin)
         return fail(PC_EUNSUPPORTED, "bins: tables do not fit in shared memory");
     int per_sm = (S.prec == PC_PREC_F64) ? pairs_f64_ctas_per_sm(p, smem)
@@ -678,6 +695,7 @@ static void fill_stats(pc_stats *stats, const CountSetup &S, const pc_grid *g0,
     stats->rescue_inline = (long long)hc[1];
     stats->pruned = (long long)hc[3];
     stats->prec = S.prec;
+    stats->wsum = S.wsum;
     stats->rescued = (long long)std::min<unsigned long long>(hc[2], S.qcap) + (long long)hc[1];
     stats->blocks = hblk;
     stats->cell_size = g0->cell_size;
@@ -716,6 +734,7 @@ static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *o
     size_t smem = 0;
     s = make_params(J, S, B, p, grid, smem);
     if (s != PC_OK) return s;
+    S.wsum = p.wint ? 2 : (S.weighted ? 1 : 0);
     Events ev(stats != nullptr);
     const long long launches0 = launch_count();
     if (ev.on) PC_CUDA(cudaEventRecord(ev.e[0], st));
@@ -834,6 +853,7 @@ static pc_status run_count_graph(const CountJob &J, const std::vector<const pc_g
         size_t smem = 0;
         s = make_params(J, N->S, N->B, p, grid, smem);
         if (s != PC_OK) return s;
+        N->S.wsum = p.wint ? 2 : (N->S.weighted ? 1 : 0);
         const size_t hb = N->S.hist_n;
         PC_CUDA(cudaMallocHost(&N->h_hist, sizeof(unsigned long long) * hb));
         if (weighted) PC_CUDA(cudaMallocHost(&N->h_whist, sizeof(double) * hb));
@@ -911,6 +931,9 @@ static TaskDev task_of(const pc_grid *gi, const pc_grid *gj, int hist, int is_au
     t.gj = GridDev{gj->rel, gj->cx, gj->xw, gj->cell_start, gj->n};
     t.hist = hist;
     t.is_auto = is_auto;
+    // one unit of the integer weight products: 2^(emax_i + emax_j - 300)
+    // (w = M 2^(e - 150) with the 24-bit significand M and biased exponent e)
+    t.wscale = (gi->wint && gj->wint) ? ldexp(1.0, gi->wemax + gj->wemax - 300) : 0.0;
     return t;
 }
 
@@ -941,6 +964,7 @@ extern "C" pc_status pc_count_auto(const pc_grid *g, const pc_bins *b, const pc_
     J.is_auto = true;
     J.g0 = g;
     job_add_bounds(J, g, true);
+    job_add_wint(J, g, g);
     return run_count(J, b, o, (cudaStream_t)stream, counts, wcounts, st);
 }
 
@@ -961,6 +985,7 @@ extern "C" pc_status pc_count_cross(const pc_grid *g1, const pc_grid *g2, const 
     J.g0 = g1;
     job_add_bounds(J, g1, true);
     job_add_bounds(J, g2, false);
+    job_add_wint(J, g1, g2);
     return run_count(J, b, o, (cudaStream_t)stream, counts, wcounts, st);
 }
 
@@ -979,6 +1004,7 @@ extern "C" pc_status pc_count_batch(const pc_grid *const *gs, int m, const pc_bi
         if (wcounts && !gs[k]->weighted) return fail(PC_EINVAL, "pc_count_batch: grid has no weights");
         J.tasks.push_back(task_of(gs[k], gs[k], k, 1));
         job_add_bounds(J, gs[k], k == 0);
+        job_add_wint(J, gs[k], gs[k]);
     }
     J.nhist = m;
     J.is_auto = true;

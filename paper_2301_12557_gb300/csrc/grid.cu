@@ -148,8 +148,52 @@ __global__ void k_cell_starts(const int *__restrict__ key_start, int ncell, int 
     cell_start[c] = key_start[(size_t)c << (3 * sub_bits)];
 }
 
+// Weight statistics for the integer weight path: out[0] counts weights that
+// are not finite, negative, subnormal or not exactly a binary32 value;
+// out[1] / out[2] receive the largest / smallest biased binary32 exponent
+// of the non-zero weights.
+__global__ void k_wstats(const void *__restrict__ w, int w_is_f32, int n, int *out) {
+    int bad = 0, emax = -1, emin = 1000;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float f;
+        if (w_is_f32) {
+            f = ((const float *)w)[i];
+        } else {
+            const double d = ((const double *)w)[i];
+            f = __double2float_rn(d);
+            if ((double)f != d) { ++bad; continue; }
+        }
+        const unsigned b = __float_as_uint(f);
+        const int e = (int)((b >> 23) & 0xFF);
+        if ((b >> 31) || e == 0xFF || (e == 0 && (b & 0x7FFFFF))) { ++bad; continue; }
+        if (e == 0) continue;   // +0 (and -0 above counts as negative)
+        emax = max(emax, e);
+        emin = min(emin, e);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+        emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(&out[0], bad);
+        atomicMax(&out[1], emax);
+        atomicMin(&out[2], emin);
+    }
+}
+
+// Packed integer weight (stored in the w lane of the FP32 point record):
+// bits 0-23 the binary32 significand M with its leading one (w = M 2^(e-150)),
+// bits 24-31 the shift emax - e.  Zero weights pack to 0.
+__device__ __forceinline__ unsigned pack_weight(double wv, int emax) {
+    const unsigned b = __float_as_uint(__double2float_rn(wv));
+    const int e = (int)((b >> 23) & 0xFF);
+    if (e == 0) return 0u;
+    return ((unsigned)(emax - e) << 24) | (b & 0x7FFFFFu) | 0x800000u;
+}
+
 __global__ void k_scatter(const double *__restrict__ xyz, const void *__restrict__ w, int w_is_f32,
-                          int n, Geom g, int sub_bits, const int *__restrict__ cell,
+                          int wpack_emax, int n, Geom g, int sub_bits, const int *__restrict__ cell,
                           const int *__restrict__ slot, const int *__restrict__ key_start,
                           float4 *__restrict__ rel,
                           uint16_t *__restrict__ cxo, double4_32a *__restrict__ xw,
@@ -172,7 +216,8 @@ __global__ void k_scatter(const double *__restrict__ xyz, const void *__restrict
     }
     double wv = 1.0;
     if (w) wv = w_is_f32 ? (double)((const float *)w)[i] : ((const double *)w)[i];
-    rel[pos] = make_float4(r[0], r[1], r[2], 0.0f);
+    const unsigned wp = (w && wpack_emax > 0) ? pack_weight(wv, wpack_emax) : 0u;
+    rel[pos] = make_float4(r[0], r[1], r[2], __uint_as_float(wp));
     cxo[pos] = (uint16_t)id[0];
     xw[pos] = make_double4_32a(x[0], x[1], x[2], wv);
     perm[pos] = i;
@@ -549,6 +594,35 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     }
     g->ncell = G.ng[0] * G.ng[1] * G.ng[2];
 
+    // weights usable by the integer weight path: every weight exactly a
+    // non-negative normal binary32 value (or zero); exponent range recorded
+    g->wint = 0;
+    if (dw && n > 0) {
+        int init[3] = {0, -1, 1000}, res[3];
+        int *ws = nullptr;
+        cudaError_t e1 = cudaMallocAsync(&ws, sizeof(init), st);
+        if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(ws, init, sizeof(init), cudaMemcpyHostToDevice, st);
+        if (e1 == cudaSuccess) {
+            int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+            k_wstats<<<blocks, 256, 0, st>>>(dw, w_is_f32, (int)n, ws);
+            note_launch();
+            e1 = cudaGetLastError();
+        }
+        if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(res, ws, sizeof(res), cudaMemcpyDeviceToHost, st);
+        if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
+        if (ws) cudaFreeAsync(ws, st);
+        if (e1 != cudaSuccess) {
+            cleanup();
+            delete g;
+            return cuda_fail(e1, "pc_build_grid: weight statistics");
+        }
+        if (res[0] == 0) {
+            g->wint = 1;
+            g->wemax = res[1] >= 0 ? res[1] : 1;      // all zero: any exponent works
+            g->wemin = res[1] >= 0 ? res[2] : 1;
+        }
+    }
+
     // device arrays
     cudaError_t e = cudaSuccess;
     size_t nn = std::max<long long>(n, 1);
@@ -590,8 +664,9 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     }
     if (e == cudaSuccess && n > 0) {
         int blocks = (int)((n + 255) / 256);
-        k_scatter<<<blocks, 256, 0, st>>>(dxyz, dw, w_is_f32, (int)n, G, sub_bits, cell, slot,
-                                          key_start, g->rel, g->cx, g->xw, g->perm);
+        k_scatter<<<blocks, 256, 0, st>>>(dxyz, dw, w_is_f32, g->wint ? g->wemax : 0, (int)n, G,
+                                          sub_bits, cell, slot, key_start, g->rel, g->cx, g->xw,
+                                          g->perm);
         note_launch();
         e = cudaGetLastError();
     }

@@ -26,6 +26,8 @@
 namespace pc {
 
 constexpr unsigned long long FLUSH_LIMIT = 1ull << 30;
+// integer weight path: products (each < 2^48) per u64 shared copy between flushes
+constexpr unsigned long long WINT_LIMIT = 1ull << 16;
 
 struct SmemLayout {
     size_t lut, ea, eb, hist, whist, seg, tile, meta, tw, q, total;
@@ -275,7 +277,7 @@ __device__ __forceinline__ void drain_rescue(const PairParams &p, uint3 *s_q, Ct
 
 // Add the CTA's shared histogram(s) into histogram `h` and clear them.
 __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, double *s_whist,
-                                           int h) {
+                                           int h, double wscale = 0.0) {
     __syncthreads();
     if (p.smem_hist_ok && h >= 0) {
         // layout [warp copy][bin][lane copy]; bins past nbins form the
@@ -296,9 +298,19 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
             if (v) atomicAdd(&p.hist[(size_t)h * p.nbins + b], (unsigned long long)v);
             if (p.weighted) {
                 double w = 0.0;
-                for (int k = 0; k < K; ++k) {
-                    w += s_whist[b * K + k];
-                    s_whist[b * K + k] = 0.0;
+                if (p.wint) {
+                    // u64 lane copies of exact integer products (each < 2^64)
+                    unsigned long long *u = reinterpret_cast<unsigned long long *>(s_whist);
+                    for (int k = 0; k < K; ++k) {
+                        w += (double)u[b * K + k];
+                        u[b * K + k] = 0ull;
+                    }
+                    w *= wscale;
+                } else {
+                    for (int k = 0; k < K; ++k) {
+                        w += s_whist[b * K + k];
+                        s_whist[b * K + k] = 0.0;
+                    }
                 }
                 if (w != 0.0) atomicAdd(&p.whist[(size_t)h * p.nbins + b], w);
             }
@@ -475,6 +487,11 @@ __device__ __forceinline__ void red_shared_u32_if(unsigned addr, bool on) {
         "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}"
         ::"r"(addr), "r"((unsigned)on));
 }
+__device__ __forceinline__ void red_shared_u64_if(unsigned addr, unsigned long long v, bool on) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p red.shared.add.u64 [%0], %1;\n\t}"
+        ::"r"(addr), "l"(v), "r"((unsigned)on));
+}
 __device__ __forceinline__ void red_shared_f64_if(unsigned addr, double v, bool on) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p red.shared.add.f64 [%0], %1;\n\t}"
@@ -506,6 +523,7 @@ struct IPts {
     float x[RI], y[RI], z[RI];     // offsets from the i-cell centre (far away if unused)
     float xa[RI], ya[RI], za[RI];  // absolute positions (midpoint line of sight)
     double w[RI];
+    unsigned wm[RI];               // packed integer weight (integer weight path)
     int idx[RI];
 };
 
@@ -513,12 +531,13 @@ struct IPts {
 // the i-cell's frame).
 struct Tile {
     const float *x, *y, *z;
-    const double *w;
+    const double *w;               // binary64 weights (W == 1)
+    const unsigned *wm;            // packed integer weights (W == 2), same storage
 };
 
 // Table-based bins, one pair at a time (every mode and line of sight).
 // MASK: the tile holds the block's own points and only pairs j > i count.
-template <int MODE, int LOS, bool W, int RI, bool MASK>
+template <int MODE, int LOS, int W, int RI, bool MASK>
 __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int len, unsigned gmask,
                                               const IPts<RI> &I, const BinCtx &bc, float r2cut,
                                               unsigned hist_sa, unsigned whist_sa, unsigned hk4,
@@ -546,7 +565,7 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
         }
         if (__any_sync(0xffffffffu, any)) {
             double wj = 0.0;
-            if (W) wj = tb.w[jj];
+            if (W == 1) wj = tb.w[jj];
             bool resc[RI];
             bool anyr = false;
 #pragma unroll
@@ -555,7 +574,7 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
                                              I.ya[r], I.za[r]);
                 const bool add = inr[r] && b.ok && !b.near;
                 red_shared_u32_if(hist_sa + hk4 * (unsigned)b.bin, add);
-                if (W) red_shared_f64_if(whist_sa + 2u * hk4 * (unsigned)b.bin, __dmul_rn(I.w[r], wj), add);
+                if (W == 1) red_shared_f64_if(whist_sa + 2u * hk4 * (unsigned)b.bin, __dmul_rn(I.w[r], wj), add);
                 resc[r] = inr[r] && b.near;
                 anyr = anyr || resc[r];
             }
@@ -576,7 +595,7 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
 // is near an edge unless |frac(t_s) - 1/2| < thrA; mu likewise with its
 // per-pair band.  Histogram addresses are formed from the float bits of
 // floor(t) + 2^23, with the 2^23 bias folded into the base address.
-template <int MODE, bool W, int RI, bool MASK, bool CHK>
+template <int MODE, int W, int RI, bool MASK, bool CHK>
 __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int len, unsigned gmask,
                                                const IPts<RI> &I, const LinCtx &lc, float r2cut,
                                                unsigned hist_sa, unsigned whist_sa, unsigned hk4,
@@ -668,10 +687,21 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                 const bool a0 = in0[r] && ok0 && !n0, a1 = in1[r] && ok1 && !n1;
                 red_shared_u32_if(hbase + hk4 * b0, a0);
                 red_shared_u32_if(hbase + hk4 * b1, a1);
-                if (W) {
+                if (W == 1) {
                     const double2 wj = *reinterpret_cast<const double2 *>(tb.w + jj);
                     red_shared_f64_if(wbase + 2u * hk4 * b0, __dmul_rn(I.w[r], wj.x), a0);
                     red_shared_f64_if(wbase + 2u * hk4 * b1, __dmul_rn(I.w[r], wj.y), a1);
+                } else if (W == 2) {
+                    // exact 48-bit significand product, shifted down by both
+                    // exponent offsets (truncation < 2^(k_i + k_j - 46) relative)
+                    const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
+                    const unsigned mi = I.wm[r] & 0xFFFFFFu, ki = I.wm[r] >> 24;
+                    const unsigned long long p0 =
+                        ((unsigned long long)mi * (wj.x & 0xFFFFFFu)) >> (ki + (wj.x >> 24));
+                    const unsigned long long p1 =
+                        ((unsigned long long)mi * (wj.y & 0xFFFFFFu)) >> (ki + (wj.y >> 24));
+                    red_shared_u64_if(wbase + 2u * hk4 * b0, p0, a0);
+                    red_shared_u64_if(wbase + 2u * hk4 * b1, p1, a1);
                 }
                 re0[r] = in0[r] && n0;
                 re1[r] = in1[r] && n1;
@@ -694,7 +724,7 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
 }
 
 // Global-histogram variant for histograms too large for shared memory.
-template <int MODE, int LOS, bool W, int RI, bool MASK>
+template <int MODE, int LOS, int W, int RI, bool MASK>
 __device__ __forceinline__ void pair_tile_global(const PairParams &p, Tile tb, int len, unsigned gmask,
                                                  const IPts<RI> &I, const BinCtx &bc, float r2cut,
                                                  size_t hbase, uint3 *s_q, int *s_qn,
@@ -717,7 +747,7 @@ __device__ __forceinline__ void pair_tile_global(const PairParams &p, Tile tb, i
                                        task_bits);
             } else if (b.ok) {
                 atomicAdd(p.hist + hbase + b.bin, 1ull);
-                if (W) atomicAdd(p.whist + hbase + b.bin, __dmul_rn(I.w[r], tb.w[jj]));
+                if (W == 1) atomicAdd(p.whist + hbase + b.bin, __dmul_rn(I.w[r], tb.w[jj]));
             }
         }
     }
@@ -725,7 +755,7 @@ __device__ __forceinline__ void pair_tile_global(const PairParams &p, Tile tb, i
 }
 
 // One tile through the variant that applies.
-template <int MODE, int LOS, bool W, int RI, bool LIN, bool MASK>
+template <int MODE, int LOS, int W, int RI, bool LIN, bool MASK>
 __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, Tile tb, int len,
                                           unsigned gmask,
                                           const IPts<RI> &I, const BinCtx &bc, const LinCtx &lc,
@@ -733,6 +763,7 @@ __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, T
                                           unsigned hk4, size_t hbase, uint3 *s_q, int *s_qn,
                                           const int4 *s_seg,
                                           int nseg, int f0, int bstart, unsigned task_bits) {
+    static_assert(W != 2 || LIN, "integer weights run only with floor-based bins");
     if (!smem_hist) {
         pair_tile_global<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hbase, s_q, s_qn, s_seg,
                                                  nseg, f0, bstart, task_bits);
@@ -755,7 +786,8 @@ __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, T
 // ---------------------------------------------------------------------------
 // FP32 kernel
 // ---------------------------------------------------------------------------
-template <int MODE, int LOS, bool W, int RI, bool LIN>
+// W: 0 unweighted, 1 binary64 weighted sums, 2 integer weight products.
+template <int MODE, int LOS, int W, int RI, bool LIN>
 __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     k_pairs_f32(const __grid_constant__ PairParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -774,6 +806,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     float *s_ty = s_tx + 2 * TJ;
     float *s_tz = s_ty + 2 * TJ;
     double *s_tw = (double *)(smem + Ly.tw);
+    unsigned *s_twm = (unsigned *)(smem + Ly.tw);   // packed weights share the storage
     uint3 *s_q = (uint3 *)(smem + Ly.q);
 
     const int tid = threadIdx.x;
@@ -828,7 +861,21 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     const int nblocks = *p.nblocks;
     unsigned long long cand_local = 0;    // thread 0 only
     unsigned long long since_flush = 0;   // CTA-uniform
+    unsigned long long wterms = 0;        // CTA-uniform bound of products per u64 copy (W == 2)
     int cur_hist = -1;
+    double cur_wscale = 0.0;
+    // integer weights: before n more j-points, flush if a u64 copy could
+    // exceed WINT_LIMIT products (NT / hist_k threads share a copy)
+    auto wint_room = [&](int n) {
+        if (W != 2) return;
+        const unsigned long long add = (unsigned long long)(NT / p.hist_k) * RI * (unsigned)n;
+        if (wterms + add > WINT_LIMIT) {
+            flush_hist(p, s_hist, s_whist, cur_hist, cur_wscale);
+            since_flush = 0;
+            wterms = 0;
+        }
+        wterms += add;
+    };
     __syncthreads();
 
     for (;;) {
@@ -838,10 +885,12 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
         if (bidx >= nblocks) break;
         const Block B = p.blocks[bidx];
         const TaskDev &T = p.tasks[B.task];
-        if (T.hist != cur_hist) {
-            flush_hist(p, s_hist, s_whist, cur_hist);
+        if (T.hist != cur_hist || (W == 2 && T.wscale != cur_wscale)) {
+            flush_hist(p, s_hist, s_whist, cur_hist, cur_wscale);
             cur_hist = T.hist;
+            cur_wscale = T.wscale;
             since_flush = 0;
+            wterms = 0;
         }
         const size_t hbase = (size_t)T.hist * nbins;
         const unsigned task_bits = (unsigned)B.task << 5;
@@ -856,11 +905,13 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
             I.idx[r] = B.start + loc;
             I.xa[r] = I.ya[r] = I.za[r] = 0.f;
             I.w[r] = 0.0;
+            I.wm[r] = 0u;
             I.x[r] = I.y[r] = I.z[r] = -1.0e18f;  // unused lane: far from every j (and from the +1e18 pad slot)
             if (loc < B.count) {
                 float4 q = T.gi.rel[I.idx[r]];
                 I.x[r] = q.x; I.y[r] = q.y; I.z[r] = q.z;
-                if (LOS == LOS_MID || W) {
+                I.wm[r] = __float_as_uint(q.w);
+                if (LOS == LOS_MID || W == 1) {
                     double4_32a a = T.gi.xw[I.idx[r]];
                     I.xa[r] = (float)a.x; I.ya[r] = (float)a.y; I.za[r] = (float)a.z;
                     I.w[r] = a.w;
@@ -892,16 +943,19 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                     int pj = B.start + f;
                     float4 q = T.gj.rel[pj];
                     s_tx[f] = q.x; s_ty[f] = q.y; s_tz[f] = q.z;
-                    if (W) s_tw[f] = T.gj.xw[pj].w;
+                    if (W == 1) s_tw[f] = T.gj.xw[pj].w;
+                    if (W == 2) s_twm[f] = __float_as_uint(q.w);
                 } else {
                     s_tx[f] = s_ty[f] = s_tz[f] = 1.0e18f;
-                    if (W) s_tw[f] = 0.0;
+                    if (W == 1) s_tw[f] = 0.0;
+                    if (W == 2) s_twm[f] = 0u;
                 }
             }
             __syncthreads();
+            wint_room(lenA);
             const int ngA = (lenA + JG - 1) / JG;    // all groups evaluated
             const unsigned maskA = ngA >= 32 ? 0xffffffffu : (1u << ngA) - 1u;
-            pair_tile<MODE, LOS, W, RI, LIN, true>(p, smem_hist, Tile{s_tx, s_ty, s_tz, s_tw}, lenA,
+            pair_tile<MODE, LOS, W, RI, LIN, true>(p, smem_hist, Tile{s_tx, s_ty, s_tz, s_tw, s_twm}, lenA,
                                                    maskA, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q,
                                                    &cs.qn, s_seg, 0, -1, B.start, task_bits);
             if (tid == 0) cand_local += (unsigned long long)B.count * (B.count - 1) / 2;
@@ -949,7 +1003,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                         rcx[s] = T.gj.cx[pj];
                         rmeta[s] = sg.z;
                         rimg[s] = sg.w;
-                        if (W) rw[s] = T.gj.xw[pj].w;
+                        if (W == 1) rw[s] = T.gj.xw[pj].w;
                     }
                 }
             };
@@ -975,7 +1029,8 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                         s_tx[buf * TJ + slot] = x;
                         s_ty[buf * TJ + slot] = y;
                         s_tz[buf * TJ + slot] = z;
-                        if (W) s_tw[buf * TJ + slot] = wv;
+                        if (W == 1) s_tw[buf * TJ + slot] = wv;
+                        if (W == 2) s_twm[buf * TJ + slot] = rv[s] ? __float_as_uint(rq[s].w) : 0u;
                     }
                     // boxes of the j-groups (JG consecutive slots each)
                     const GBox gb = lane_group_box(x, y, z, rv[s]);
@@ -990,10 +1045,13 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                 const int buf = t & 1;
                 const int len = min(TJ, total - t * TJ);
                 if (t + 1 < ntiles) load_tile(t + 1);
+                wint_room(len);
                 const unsigned gm = group_mask(s_gbox[buf], s_ibox[tid >> 5], len, ni_w, r2cut,
                                                &cs.pruned);
                 pair_tile<MODE, LOS, W, RI, LIN, false>(
-                    p, smem_hist, Tile{s_tx + buf * TJ, s_ty + buf * TJ, s_tz + buf * TJ, s_tw + buf * TJ},
+                    p, smem_hist,
+                    Tile{s_tx + buf * TJ, s_ty + buf * TJ, s_tz + buf * TJ, s_tw + buf * TJ,
+                         s_twm + buf * TJ},
                     (len + 1) & ~1, gm, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q, &cs.qn, s_seg,
                     nseg, t * TJ, B.start, task_bits);
                 if (tid == 0) cand_local += (unsigned long long)len * B.count;
@@ -1005,8 +1063,9 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                 if (__syncthreads_or(cs.qn >= LQ / 2))
                     drain_rescue<MODE, LOS>(p, s_q, cs, &s_base);
                 if (since_flush > FLUSH_LIMIT) {
-                    flush_hist(p, s_hist, s_whist, cur_hist);
+                    flush_hist(p, s_hist, s_whist, cur_hist, cur_wscale);
                     since_flush = 0;
+                    wterms = 0;
                 }
             }
             __syncthreads();
@@ -1015,7 +1074,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
         __syncthreads();
     }
     drain_rescue<MODE, LOS>(p, s_q, cs, &s_base);
-    flush_hist(p, s_hist, s_whist, cur_hist);
+    flush_hist(p, s_hist, s_whist, cur_hist, cur_wscale);
     if (tid == 0 && cand_local) atomicAdd(&p.counters[0], cand_local);
     if (tid == 0 && cs.pruned) atomicAdd(&p.counters[3], cs.pruned);
 }
@@ -1180,11 +1239,15 @@ PairKernel<MODE, LOS> pick_f32(const PairParams &p, int ipt) {
     constexpr bool LINOK = (MODE == MODE_S) || (MODE == MODE_SMU && LOS == LOS_Z);
     const bool lin = LINOK && p.lin;
     if (p.weighted) {
-        if (ipt == 4) return lin ? k_pairs_f32<MODE, LOS, true, 4, LINOK> : k_pairs_f32<MODE, LOS, true, 4, false>;
-        return lin ? k_pairs_f32<MODE, LOS, true, 2, LINOK> : k_pairs_f32<MODE, LOS, true, 2, false>;
+        if constexpr (LINOK) {
+            if (lin && p.wint) return ipt == 4 ? k_pairs_f32<MODE, LOS, 2, 4, true>
+                                               : k_pairs_f32<MODE, LOS, 2, 2, true>;
+        }
+        if (ipt == 4) return lin ? k_pairs_f32<MODE, LOS, 1, 4, LINOK> : k_pairs_f32<MODE, LOS, 1, 4, false>;
+        return lin ? k_pairs_f32<MODE, LOS, 1, 2, LINOK> : k_pairs_f32<MODE, LOS, 1, 2, false>;
     }
-    if (ipt == 4) return lin ? k_pairs_f32<MODE, LOS, false, 4, LINOK> : k_pairs_f32<MODE, LOS, false, 4, false>;
-    return lin ? k_pairs_f32<MODE, LOS, false, 2, LINOK> : k_pairs_f32<MODE, LOS, false, 2, false>;
+    if (ipt == 4) return lin ? k_pairs_f32<MODE, LOS, 0, 4, LINOK> : k_pairs_f32<MODE, LOS, 0, 4, false>;
+    return lin ? k_pairs_f32<MODE, LOS, 0, 2, LINOK> : k_pairs_f32<MODE, LOS, 0, 2, false>;
 }
 
 template <int MODE, int LOS>

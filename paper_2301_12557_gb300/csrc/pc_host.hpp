@@ -17,6 +17,10 @@ struct pc_grid {
     double cell_size;           // requested cubic cell side
     double pts_lo[3], pts_hi[3];  // bounds of the (canonical) points
     double r2min = 0.0;           // non-periodic: lower bound of min |x|^2 over the points
+    // integer weight path: every weight a non-negative normal binary32 value or
+    // zero (wint), with biased exponents in [wemin, wemax]; the FP32 records
+    // then carry the packed weights
+    int wint = 0, wemax = 0, wemin = 0;
     float4 *rel;
     uint16_t *cx;
     double4_32a *xw;

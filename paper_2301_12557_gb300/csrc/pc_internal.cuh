@@ -40,6 +40,7 @@ struct TaskDev {
     GridDev gi, gj;
     int hist;
     int is_auto;
+    double wscale;   // integer weight path: value of one unit of the product accumulators
 };
 
 // A block of consecutive i-points inside one cell.
@@ -105,6 +106,10 @@ struct PairParams {
     // (row n_a) of the shared histogram
     int lin_norange;
     int nbins_smem;              // bins per shared copy: nbins, plus n_b with lin_norange
+    // weighted sums from exact integer products of the packed binary32 weights
+    // (significand product shifted by both exponent offsets, accumulated in
+    // u64 lane copies, flushed as binary64 times the task's wscale)
+    int wint;
 };
 
 // ---------------------------------------------------------------------------

@@ -209,6 +209,50 @@ def test_histogram_replication_modes(nb):
         _check(got64, want, gotw64, wantw, f"{nb} bins, priv {priv}, f64")
 
 
+def test_integer_weight_products_match_binary64():
+    """binary32 weights on floor-based bins with few bins run the integer
+    product path (stats.wsum == 2) and stay within 1e-10 of the binary64
+    oracle; zero weights, a cross count of grids with different exponent
+    ranges and the exponent-span limit are covered."""
+    L = 300.0
+    rng = np.random.default_rng(515)
+    x = synth.neyman_scott(20000, 2000, 10.0, 3.0, L, 516)
+    y = synth.neyman_scott(15000, 1500, 10.0, 3.0, L, 517)
+    ea = np.linspace(0.0, 30.0, 31)
+    kw = dict(box=L, periodic=True, edges_a=ea)
+    # lognormal weights with some exact zeros
+    wx = synth.lognormal_weights(x.shape[0], 0.3, 518)
+    wx[rng.choice(x.shape[0], 500, replace=False)] = 0.0
+    g, gw, st = P.count(x, w1=wx, return_stats=True, **kw)
+    o, ow = oracle.count(x, w1=wx, method="grid", **kw)
+    assert st.wsum == 2
+    _check(g, o, gw, ow, "integer weights, auto")
+    # cross count: the two grids' weights sit in different binades
+    wy = (2.0 + 2.0 * rng.random(y.shape[0])).astype(np.float32)
+    g, gw, st = P.count(x, y, w1=wx, w2=wy, return_stats=True, **kw)
+    o, ow = oracle.count(x, y, w1=wx, w2=wy, method="grid", **kw)
+    assert st.wsum == 2
+    _check(g, o, gw, ow, "integer weights, cross")
+    # exponent spans 6 + 6: at the limit, still integer
+    w6 = np.exp2(rng.uniform(-3.0, 3.0, x.shape[0])).astype(np.float32)
+    g, gw, st = P.count(x, w1=w6, return_stats=True, **kw)
+    o, ow = oracle.count(x, w1=w6, method="grid", **kw)
+    assert st.wsum == 2
+    _check(g, o, gw, ow, "integer weights, span 12")
+    # spans 12 + 12: beyond the limit, binary64 products
+    w12 = np.exp2(rng.uniform(-6.0, 6.0, x.shape[0])).astype(np.float32)
+    g, gw, st = P.count(x, w1=w12, return_stats=True, **kw)
+    o, ow = oracle.count(x, w1=w12, method="grid", **kw)
+    assert st.wsum == 1
+    _check(g, o, gw, ow, "wide weights, binary64")
+    # binary64 weights that are not binary32 values: binary64 products
+    w64 = rng.uniform(0.5, 1.5, x.shape[0])
+    g, gw, st = P.count(x, w1=w64, return_stats=True, **kw)
+    o, ow = oracle.count(x, w1=w64, method="grid", **kw)
+    assert st.wsum == 1
+    _check(g, o, gw, ow, "binary64 weights")
+
+
 def test_device_tensors_and_device_outputs():
     L = 100.0
     x = synth.neyman_scott(4000, 400, 10.0, 2.0, L, 201)
