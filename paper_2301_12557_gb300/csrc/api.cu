@@ -218,10 +218,18 @@ static void build_stencil(const Geom &g, double r, bool half, std::vector<int4> 
             }
             int xlo = -rx, xhi = rx;
             if (half) {
-                if (dz < 0 || (dz == 0 && dy < 0)) continue;
+                // Sect. 3.1 duplicate removal: of every row pair (dy, dz),
+                // (-dy, -dz) exactly one is visited.  The kept member alternates
+                // with the parity of dy + dz (the parity is the same for both),
+                // so the visited half reaches equally far up and down: every
+                // warp's i-points then see the same volume wherever they sit in
+                // the cell, and the warps of a CTA stay balanced.
                 if (dz == 0 && dy == 0) {
                     if (rx < 1) continue;
                     xlo = 1;
+                } else {
+                    const bool upper = dz > 0 || (dz == 0 && dy > 0);
+                    if (upper == (((dy + dz) & 1) != 0)) continue;
                 }
             }
             rows.push_back(make_int4(dy, dz, xlo, xhi));
