@@ -127,10 +127,12 @@ __device__ __forceinline__ GBox lane_group_box(float x, float y, float z, bool v
 // would be >= r2cut: |fl(x_j - x_i)| >= fl(gap) per axis because rounding is
 // monotone, and the same operations on the gaps give a lower bound of s2.
 // So the skipped pairs are exactly pairs the kernel would reject one by one.
-__device__ __forceinline__ unsigned group_mask(const GBox *gb, const GBox &ib, int len, int ni,
+// Group g of tile `tile` is the chunk's group g * fstride + tile; the last
+// group of the chunk may hold fewer than JG points (of `total`).
+__device__ __forceinline__ unsigned group_mask(const GBox *gb, const GBox &ib, int ngroups,
+                                               int tile, int fstride, int total, int ni,
                                                float r2cut, unsigned long long *pruned) {
     const int lane = threadIdx.x & 31;
-    const int ngroups = (len + JG - 1) / JG;
     bool keep = false;
     if (lane < ngroups) {
         const GBox g = gb[lane];
@@ -138,8 +140,10 @@ __device__ __forceinline__ unsigned group_mask(const GBox *gb, const GBox &ib, i
         const float gy = fmaxf(fmaxf(g.lo.y - ib.hi.y, ib.lo.y - g.hi.y), 0.f);
         const float gz = fmaxf(fmaxf(g.lo.z - ib.hi.z, ib.lo.z - g.hi.z), 0.f);
         keep = fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < r2cut;
-        if (!keep && ni > 0)
-            atomicAdd(pruned, (unsigned long long)min(JG, len - lane * JG) * (unsigned)ni);
+        if (!keep && ni > 0) {
+            const int first = (lane * fstride + tile) * JG;
+            atomicAdd(pruned, (unsigned long long)min(JG, total - first) * (unsigned)ni);
+        }
     }
     return __ballot_sync(0xffffffffu, keep);
 }
@@ -501,14 +505,15 @@ __device__ __forceinline__ void red_shared_f64_if(unsigned addr, double v, bool 
 // Rare path: stage one near-edge pair for the binary64 rescue.
 template <int MODE, int LOS>
 __device__ __noinline__ void rescue_push(const PairParams &p, uint3 *s_q, int *s_qn,
-                                         const int4 *s_seg, int nseg, int f0, int jj,
+                                         const int4 *s_seg, int nseg, int f0, int fstride, int jj,
                                          int bstart, int i, unsigned task_bits) {
     int jidx, img;
     if (f0 < 0) {
         jidx = bstart + jj;
         img = 13;
     } else {
-        int f = f0 + jj;
+        // tile f0 holds the chunk's j-groups f0, f0 + fstride, f0 + 2 fstride, ...
+        const int f = ((jj / JG) * fstride + f0) * JG + (jj % JG);
         int4 sg = s_seg[seg_find(s_seg, nseg, f)];
         jidx = sg.x + (f - sg.y);
         img = sg.w;
@@ -542,7 +547,7 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
                                               const IPts<RI> &I, const BinCtx &bc, float r2cut,
                                               unsigned hist_sa, unsigned whist_sa, unsigned hk4,
                                               uint3 *s_q, int *s_qn, const int4 *s_seg, int nseg,
-                                              int f0, int bstart, unsigned task_bits) {
+                                              int f0, int fstride, int bstart, unsigned task_bits) {
 #pragma unroll 1
     for (unsigned gm = gmask; gm; gm &= gm - 1) {
     const int j0 = (__ffs(gm) - 1) * JG, j1 = min(j0 + JG, len);
@@ -582,7 +587,7 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
 #pragma unroll
                 for (int r = 0; r < RI; ++r)
                     if (resc[r])
-                        rescue_push<MODE, LOS>(p, s_q, s_qn, s_seg, nseg, f0, jj, bstart, I.idx[r],
+                        rescue_push<MODE, LOS>(p, s_q, s_qn, s_seg, nseg, f0, fstride, jj, bstart, I.idx[r],
                                                task_bits);
             }
         }
@@ -600,7 +605,7 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                                                const IPts<RI> &I, const LinCtx &lc, float r2cut,
                                                unsigned hist_sa, unsigned whist_sa, unsigned hk4,
                                                uint3 *s_q, int *s_qn, const int4 *s_seg, int nseg,
-                                               int f0, int bstart, unsigned task_bits) {
+                                               int f0, int fstride, int bstart, unsigned task_bits) {
     const float2 C23 = make_float2(8388608.0f, 8388608.0f);
     const float2 NC23H = make_float2(-8388608.0f + 0.5f, -8388608.0f + 0.5f);
     const float2 M1 = make_float2(-1.0f, -1.0f);
@@ -711,10 +716,10 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
 #pragma unroll
                 for (int r = 0; r < RI; ++r) {
                     if (re0[r])
-                        rescue_push<MODE, LOS_Z>(p, s_q, s_qn, s_seg, nseg, f0, jj, bstart,
+                        rescue_push<MODE, LOS_Z>(p, s_q, s_qn, s_seg, nseg, f0, fstride, jj, bstart,
                                                  I.idx[r], task_bits);
                     if (re1[r])
-                        rescue_push<MODE, LOS_Z>(p, s_q, s_qn, s_seg, nseg, f0, jj + 1, bstart,
+                        rescue_push<MODE, LOS_Z>(p, s_q, s_qn, s_seg, nseg, f0, fstride, jj + 1, bstart,
                                                  I.idx[r], task_bits);
                 }
             }
@@ -728,7 +733,7 @@ template <int MODE, int LOS, int W, int RI, bool MASK>
 __device__ __forceinline__ void pair_tile_global(const PairParams &p, Tile tb, int len, unsigned gmask,
                                                  const IPts<RI> &I, const BinCtx &bc, float r2cut,
                                                  size_t hbase, uint3 *s_q, int *s_qn,
-                                                 const int4 *s_seg, int nseg, int f0, int bstart,
+                                                 const int4 *s_seg, int nseg, int f0, int fstride, int bstart,
                                                  unsigned task_bits) {
     for (unsigned gm = gmask; gm; gm &= gm - 1) {
     const int j0 = (__ffs(gm) - 1) * JG, j1 = min(j0 + JG, len);
@@ -743,7 +748,7 @@ __device__ __forceinline__ void pair_tile_global(const PairParams &p, Tile tb, i
             if (!inr) continue;
             Bin32 b = bin_f32<MODE, LOS>(bc, dx, dy, dz, qxy, s2, I.xa[r], I.ya[r], I.za[r]);
             if (b.near) {
-                rescue_push<MODE, LOS>(p, s_q, s_qn, s_seg, nseg, f0, jj, bstart, I.idx[r],
+                rescue_push<MODE, LOS>(p, s_q, s_qn, s_seg, nseg, f0, fstride, jj, bstart, I.idx[r],
                                        task_bits);
             } else if (b.ok) {
                 atomicAdd(p.hist + hbase + b.bin, 1ull);
@@ -762,24 +767,24 @@ __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, T
                                           float r2cut, unsigned hist_sa, unsigned whist_sa,
                                           unsigned hk4, size_t hbase, uint3 *s_q, int *s_qn,
                                           const int4 *s_seg,
-                                          int nseg, int f0, int bstart, unsigned task_bits) {
+                                          int nseg, int f0, int fstride, int bstart, unsigned task_bits) {
     static_assert(W != 2 || LIN, "integer weights run only with floor-based bins");
     if (!smem_hist) {
         pair_tile_global<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hbase, s_q, s_qn, s_seg,
-                                                 nseg, f0, bstart, task_bits);
+                                                 nseg, f0, fstride, bstart, task_bits);
     } else if (LIN) {
         if (p.lin_norange)
             pair_tile_lin2<MODE, W, RI, MASK, false>(p, tb, len, gmask, I, lc, r2cut, hist_sa,
-                                                     whist_sa, hk4, s_q, s_qn, s_seg, nseg, f0,
+                                                     whist_sa, hk4, s_q, s_qn, s_seg, nseg, f0, fstride,
                                                      bstart, task_bits);
         else
             pair_tile_lin2<MODE, W, RI, MASK, true>(p, tb, len, gmask, I, lc, r2cut, hist_sa,
                                                     whist_sa, hk4, s_q, s_qn,
-                                          s_seg, nseg, f0, bstart, task_bits);
+                                          s_seg, nseg, f0, fstride, bstart, task_bits);
     } else {
         pair_tile_lut<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hist_sa, whist_sa,
                                               hk4, s_q,
-                                              s_qn, s_seg, nseg, f0, bstart, task_bits);
+                                              s_qn, s_seg, nseg, f0, fstride, bstart, task_bits);
     }
 }
 
@@ -957,7 +962,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
             const unsigned maskA = ngA >= 32 ? 0xffffffffu : (1u << ngA) - 1u;
             pair_tile<MODE, LOS, W, RI, LIN, true>(p, smem_hist, Tile{s_tx, s_ty, s_tz, s_tw, s_twm}, lenA,
                                                    maskA, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q,
-                                                   &cs.qn, s_seg, 0, -1, B.start, task_bits);
+                                                   &cs.qn, s_seg, 0, -1, 0, B.start, task_bits);
             if (tid == 0) cand_local += (unsigned long long)B.count * (B.count - 1) / 2;
             since_flush += (unsigned long long)B.count * B.count;
             __syncthreads();
@@ -983,7 +988,15 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
             __syncthreads();                 // every thread has read nseg before it changes
             if (nseg == 0) continue;
             const int total = seg_scan(s_seg, nseg, s_tmp);
-            const int ntiles = (total + TJ - 1) / TJ;
+            // The chunk's j-points form ngt groups of JG; tile t holds the
+            // groups t, t + ntiles, t + 2 ntiles, ...: every tile mixes all rows
+            // of the chunk, so the warps (each pruning against its own i-box)
+            // get similar work per tile.
+            constexpr int GPT = TJ / JG;
+            const int ngt = (total + JG - 1) / JG;
+            const int ntiles = (ngt + GPT - 1) / GPT;
+            auto tile_groups = [&](int t) { return (ngt - t + ntiles - 1) / ntiles; };
+            if (tid == 0) cand_local += (unsigned long long)total * B.count;
 
             // staging registers (TJ / NT slots per thread)
             constexpr int SPT = TJ / NT;
@@ -994,8 +1007,9 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
             auto load_tile = [&](int t) {
 #pragma unroll
                 for (int s = 0; s < SPT; ++s) {
-                    int f = t * TJ + tid + s * NT;
-                    rv[s] = f < total;
+                    const int slot = tid + s * NT;
+                    const int f = ((slot / JG) * ntiles + t) * JG + (slot % JG);
+                    rv[s] = f < total && slot / JG < tile_groups(t);
                     if (rv[s]) {
                         int4 sg = s_seg[seg_find(s_seg, nseg, f)];
                         int pj = sg.x + (f - sg.y);
@@ -1009,7 +1023,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
             };
             auto store_tile = [&](int t) {
                 const int buf = t & 1;
-                const int len = min(TJ, total - t * TJ);
+                const int len = tile_groups(t) * JG;   // whole groups; missing points are pads
 #pragma unroll
                 for (int s = 0; s < SPT; ++s) {
                     const int slot = tid + s * NT;
@@ -1025,7 +1039,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                         z = fmaf((float)dzc, c32z, rq[s].z);
                         wv = rw[s];
                     }
-                    if (rv[s] || slot == len) {
+                    if (slot < len) {
                         s_tx[buf * TJ + slot] = x;
                         s_ty[buf * TJ + slot] = y;
                         s_tz[buf * TJ + slot] = z;
@@ -1043,18 +1057,17 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
             __syncthreads();
             for (int t = 0; t < ntiles; ++t) {
                 const int buf = t & 1;
-                const int len = min(TJ, total - t * TJ);
+                const int len = tile_groups(t) * JG;
                 if (t + 1 < ntiles) load_tile(t + 1);
                 wint_room(len);
-                const unsigned gm = group_mask(s_gbox[buf], s_ibox[tid >> 5], len, ni_w, r2cut,
-                                               &cs.pruned);
+                const unsigned gm = group_mask(s_gbox[buf], s_ibox[tid >> 5], len / JG, t, ntiles,
+                                               total, ni_w, r2cut, &cs.pruned);
                 pair_tile<MODE, LOS, W, RI, LIN, false>(
                     p, smem_hist,
                     Tile{s_tx + buf * TJ, s_ty + buf * TJ, s_tz + buf * TJ, s_tw + buf * TJ,
                          s_twm + buf * TJ},
-                    (len + 1) & ~1, gm, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q, &cs.qn, s_seg,
-                    nseg, t * TJ, B.start, task_bits);
-                if (tid == 0) cand_local += (unsigned long long)len * B.count;
+                    len, gm, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q, &cs.qn, s_seg,
+                    nseg, t, ntiles, B.start, task_bits);
                 since_flush += (unsigned long long)len * B.count;
                 if (t + 1 < ntiles) store_tile(t + 1);
                 // one decision for the whole CTA, taken at the barrier: read
