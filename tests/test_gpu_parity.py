@@ -128,6 +128,35 @@ def test_near_edge_adversarial():
         _check(g, w, what=f"near-edge {mode}")
 
 
+@pytest.mark.parametrize("mode", ["s", "smu"])
+def test_log_bins_clustered_and_near_edges(mode):
+    """Logarithmic s bins in [0.1, R) (the other binning scheme of the paper,
+    Sect. 3.2: monotone non-uniform edges through the table path), on a
+    clustered catalogue and on pairs planted at the log edges * (1 + tiny)."""
+    L = 300.0
+    ea = np.geomspace(0.1, 30.0, 25)
+    eb = np.linspace(0.0, 1.0, 11) if mode == "smu" else None
+    x = synth.neyman_scott(30000, 1500, 20.0, 1.0, L, 601)
+    (g, _), (w, _) = _both(x, box=L, periodic=True, mode=mode, edges_a=ea, edges_b=eb)
+    _check(g, w, what=f"log bins {mode}")
+    offs = [0.0, 2.0 ** -52, -2.0 ** -52, 1e-9, -1e-9, 1e-7, -1e-7, 2e-6, -2e-6]
+    y = synth.catalogs.near_edge_pairs(ea, L, 6000, offs, 602)
+    (g, _), (w, _) = _both(y, box=L, periodic=True, mode=mode, edges_a=ea, edges_b=eb)
+    _check(g, w, what=f"log bins near edges {mode}")
+
+
+def test_headline_binning_200x120_scaled():
+    """The paper's headline binning, 200 s bins x 120 mu bins (24,000 bins,
+    a histogram larger than the 16 KB shared budget), on a scaled clustered
+    periodic catalogue with the separation range scaled to fit the box."""
+    L = 400.0
+    x = synth.neyman_scott(40000, 4000, 10.0, 2.0, L, 603)
+    ea = np.linspace(0.0, 40.0, 201)
+    eb = np.linspace(0.0, 1.0, 121)
+    (g, _), (w, _) = _both(x, box=L, periodic=True, mode="smu", edges_a=ea, edges_b=eb)
+    _check(g, w, what="200 x 120 bins")
+
+
 def test_lattice_ties_exact():
     """Integer lattice with integer edges: many exact ties on bin edges."""
     x = synth.lattice_points(3000, 24, 151)
