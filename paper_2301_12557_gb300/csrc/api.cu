@@ -106,7 +106,9 @@ struct Plan {
     // evenly spaced edges: bins by floor (see PairParams::lin*)
     int lin = 0;
     float lin_invA = 0, lin_offA = 0, lin_thrA = 0, lin_nB = 0, lin_mA = 0, lin_cB = 0;
-    int lin_norange = 0;
+    int lin_norange = 0, lin_log = 0;
+    float lin_offA1 = 0;         // lin_offA + 1, rounded once
+    float lin_mS = 0;
 };
 
 static bool edges_ok(const double *e, int n, bool zero_one) {
@@ -369,6 +371,7 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
                 P.lin = 1;
                 P.lin_invA = (float)(1.0 / D);
                 P.lin_offA = (float)(-e0 / D);
+                P.lin_offA1 = (float)(1.0 - e0 / D);
                 P.lin_thrA = nextafterf((float)(0.5 - eps_t), 0.0f);
                 // e_0 = 0: t_s = s / D >= 0; and every candidate has t_s below
                 // n_a + 1/2 (plus rounding), so floor(t_s) <= n_a
@@ -380,6 +383,59 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
                     double cB = 0.5 - (muB + 4.0 * u + devm) * nb;
                     P.lin_cB = nextafterf((float)cB, 0.0f);
                     if (!(cB > 0.25)) P.lin = 0;
+                }
+            }
+        }
+    }
+    // ---- logarithmic s edges: floor of a scaled base-2 logarithm -----------
+    // e_k = e_0 q^k: bin = floor(t), t = log_q(s / e_0) = A log2(s^2) + B with
+    // A = 1 / (2 log2 q), B = -log2(e_0) / log2 q (Sect. 3.2's log mapping).
+    // Band in t units (each term times 2 below, like the linear case):
+    //  - the separation vector's error u (4.33 c + 3 s) + 2^-51 X (c the cell
+    //    side) is relative in log2(s^2): 2 (4.33 u c + 2^-51 X) / (s ln 2) plus
+    //    6u / ln 2, and the three roundings of s^2 add 3u / ln 2 -- the 1/s
+    //    part is applied per pair through rsqrt(s^2);
+    //  - the hardware base-2 logarithm errs by at most 2^-21 max(1, |log2 x|)
+    //    (twice the largest error over every positive normal binary32 input,
+    //    measured exhaustively on the device by the test suite);
+    //  - A, B rounded to binary32 and the FMA add u (A |L| + |B| + |t|);
+    //  - the edges' distance from an exact geometric sequence (in t units),
+    //    and the oracle's binary64 roundings (2^-45 A).
+    if (!P.lin && P.ea[0] > 0.0) {
+        const double e0 = P.ea[0], lq = log2(P.ea[P.na] / e0) / P.na;
+        bool lin_mu = true;
+        double devm = 0.0;
+        if (P.mode == PC_BIN_SMU) {
+            for (int k = 0; k <= P.nb; ++k) devm = std::max(devm, fabs(P.eb[k] - (double)k / P.nb));
+            lin_mu = (P.los == PC_LOS_Z) && devm <= 1e-12;
+        }
+        bool mode_ok = P.mode == PC_BIN_S || (P.mode == PC_BIN_SMU && P.los == PC_LOS_Z);
+        double dev = 0.0;
+        for (int k = 0; k <= P.na; ++k) dev = std::max(dev, fabs(log2(P.ea[k] / e0) / lq - k));
+        if (mode_ok && lin_mu && lq > 0.0 && dev <= 1e-6 && P.na < (1 << 20)) {
+            const double ln2 = log(2.0), A = 1.0 / (2.0 * lq), B = -log2(e0) / lq;
+            const double Lmax = std::max(fabs(log2(P.rcut * P.rcut)), fabs(log2(0.25 * e0 * e0)));
+            const double tmax = A * Lmax + fabs(B) + 1.0;
+            const double C1 = A * 2.0 * (4.4 * u * c + ldexp(X + Lm + R0, -51)) / ln2 * 1.01;
+            const double C0 = A * 9.0 * u / ln2 * 1.01 + A * ldexp(1.0, -21) * std::max(1.0, Lmax) +
+                              u * (A * Lmax + fabs(B) + tmax) * 2.0 + dev + A * ldexp(1.0, -45);
+            if (2.0 * C0 < 0.25) {
+                P.lin = 1;
+                P.lin_log = 1;
+                P.lin_invA = (float)A;
+                P.lin_offA = (float)B;
+                P.lin_offA1 = (float)(B + 1.0);
+                P.lin_thrA = nextafterf((float)(0.5 - 2.0 * C0), 0.0f);
+                // rsqrt(s^2) >= (1 - 2^-22) / s: scale the 1/s term up to cover it
+                P.lin_mS = nextafterf((float)(2.0 * C1 * (1.0 + 1e-6)), INFINITY);
+                P.lin_norange = 0;
+                if (P.mode == PC_BIN_SMU) {
+                    const double nb = P.nb;
+                    P.lin_nB = (float)nb;
+                    P.lin_mA = (float)(muA * nb * (1.0 + 1e-6));
+                    double cB = 0.5 - (muB + 4.0 * u + devm) * nb;
+                    P.lin_cB = nextafterf((float)cB, 0.0f);
+                    if (!(cB > 0.25)) P.lin = P.lin_log = 0;
                 }
             }
         }
@@ -623,9 +679,12 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     choose_replication(S.o.priv, P.nbins, S.weighted, p.priv, p.hist_k);
     p.lin = (S.prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
     p.lin_norange = p.lin ? P.lin_norange : 0;
+    p.lin_log = p.lin ? P.lin_log : 0;
+    p.lin_mS = P.lin_mS;
     p.nbins_smem = P.nbins + (p.lin_norange ? (P.mode == PC_BIN_S ? 1 : P.nb) : 0);
     p.lin_invA = P.lin_invA;
-    p.lin_offA = P.lin_offA;
+    // the range-tested floor bins take t_s + 1 (exact floors down to t_s = -1)
+    p.lin_offA = P.lin_norange ? P.lin_offA : P.lin_offA1;
     p.lin_thrA = P.lin_thrA;
     p.lin_nB = P.lin_nB;
     p.lin_mA = P.lin_mA;
@@ -1269,9 +1328,12 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
     choose_replication(o.priv, P.nbins, wcounts != nullptr, p.priv, p.hist_k);
     p.lin = (prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
     p.lin_norange = p.lin ? P.lin_norange : 0;
+    p.lin_log = p.lin ? P.lin_log : 0;
+    p.lin_mS = P.lin_mS;
     p.nbins_smem = P.nbins + (p.lin_norange ? (P.mode == PC_BIN_S ? 1 : P.nb) : 0);
     p.lin_invA = P.lin_invA;
-    p.lin_offA = P.lin_offA;
+    // the range-tested floor bins take t_s + 1 (exact floors down to t_s = -1)
+    p.lin_offA = P.lin_norange ? P.lin_offA : P.lin_offA1;
     p.lin_thrA = P.lin_thrA;
     p.lin_nB = P.lin_nB;
     p.lin_mA = P.lin_mA;

@@ -329,6 +329,16 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
 // Reciprocal square root: one MUFU.RSQ (PTX rsqrt.approx.ftz.f32, documented
 // maximum relative error 2^-22.9; the rescue bands budget 2^-22).  +0 gives
 // +inf, so coincident points produce NaN separations and are rescued.
+// Base-2 logarithm: one MUFU.LG2 (PTX lg2.approx.ftz.f32).  Its error, at
+// most 2.3e-7 max(1, |log2 x|) over every positive normal binary32 input
+// (measured exhaustively; the log-bin bands budget 2^-21 max(1, |log2 x|)),
+// is checked on the device by the test suite.  +0 gives -inf.
+__device__ __forceinline__ float lg2_fast(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float rsqrt_fast(float x) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -445,6 +455,7 @@ __device__ __forceinline__ Bin32 bin_f32(const BinCtx &c, float dx, float dy, fl
 // is within the band of 0 or 1.
 struct LinCtx {
     float invA, offA, thrA;   // s scaling and band threshold
+    float mS;                 // logarithmic s: band term per 1/s
     float nB, mA, cB;         // mu scaling and per-pair band threshold
     unsigned nA, nB_u;
 };
@@ -600,7 +611,7 @@ __device__ __forceinline__ void pair_tile_lut(const PairParams &p, Tile tb, int 
 // is near an edge unless |frac(t_s) - 1/2| < thrA; mu likewise with its
 // per-pair band.  Histogram addresses are formed from the float bits of
 // floor(t) + 2^23, with the 2^23 bias folded into the base address.
-template <int MODE, int W, int RI, bool MASK, bool CHK>
+template <int MODE, int W, int RI, bool MASK, bool CHK, bool LOGS>
 __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int len, unsigned gmask,
                                                const IPts<RI> &I, const LinCtx &lc, float r2cut,
                                                unsigned hist_sa, unsigned whist_sa, unsigned hk4,
@@ -614,14 +625,22 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
     const float2 NB = make_float2(lc.nB, lc.nB);
     const float2 NMA = make_float2(-lc.mA, -lc.mA);
     const float2 CB = make_float2(lc.cB, lc.cB);
+    // With the range test (CHK) the offset carries +1 (host side): t_s + 1 >= 0
+    // for every t_s >= -1, where adding 2^23 and rounding down is an exact
+    // floor (below 2^23 the float spacing is 1/2); values below -1 are out of
+    // range whatever their floor.  The extra row is removed in the base.
     const float halfA = 0.5f * (float)lc.nA;
-    const float2 NHALFA = make_float2(-halfA, -halfA);
+    const float hA1 = CHK ? halfA + 1.0f : halfA;
+    const float2 NHALFA = make_float2(-hA1, -hA1);
     const float thrA = lc.thrA;
+    const float2 THRA = make_float2(lc.thrA, lc.thrA);
+    const float2 NMS = make_float2(-lc.mS, -lc.mS);
     const unsigned jmax = 0x4B000000u + lc.nB_u - 1u;   // float bits of 2^23 + n_mu - 1
     const unsigned nbu = (MODE == MODE_SMU) ? lc.nB_u : 1u;
     // biases of the float bits of floor(t_s) + 2^23 (and floor(t_mu) + 2^23),
     // folded into the bases
-    const unsigned bias = 0x4B000000u * nbu + ((MODE == MODE_SMU) ? 0x4B000000u : 0u);
+    const unsigned bias = 0x4B000000u * nbu + ((MODE == MODE_SMU) ? 0x4B000000u : 0u) +
+                          (CHK ? nbu : 0u);
     const unsigned hbase = hist_sa - hk4 * bias;
     const unsigned wbase = whist_sa - 2u * hk4 * bias;
     float2 NX[RI], NY[RI], NZ[RI];
@@ -663,7 +682,10 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
             for (int r = 0; r < RI; ++r) {
                 const float2 s2 = S2[r];
                 const float2 rs = make_float2(rsqrt_fast(s2.x), rsqrt_fast(s2.y));
-                const float2 ts = __ffma2_rn(__fmul2_rn(s2, rs), INVA, OFFA);
+                // t_s = (s - e0) / D, or log_q(s / e0) = A log2(s^2) + B
+                const float2 ts =
+                    LOGS ? __ffma2_rn(make_float2(lg2_fast(s2.x), lg2_fast(s2.y)), INVA, OFFA)
+                         : __ffma2_rn(__fmul2_rn(s2, rs), INVA, OFFA);
                 const float2 f = __fadd2_rd(ts, C23);
                 const float2 d = __ffma2_rn(__fadd2_rn(f, NC23H), M1, ts);   // frac - 1/2
                 bool ok0 = true, ok1 = true;
@@ -672,8 +694,10 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                     ok0 = fabsf(o.x) < halfA;
                     ok1 = fabsf(o.y) < halfA;
                 }
-                // NaN (s2 = 0) compares false: such pairs are near
-                bool n0 = !(fabsf(d.x) < thrA), n1 = !(fabsf(d.y) < thrA);
+                // NaN (s2 = 0) compares false: such pairs are near.  Log edges:
+                // the band grows as 1/s
+                const float2 ths = LOGS ? __ffma2_rn(NMS, rs, THRA) : THRA;
+                bool n0 = !(fabsf(d.x) < ths.x), n1 = !(fabsf(d.y) < ths.y);
                 unsigned b0 = (unsigned)__float_as_int(f.x), b1 = (unsigned)__float_as_int(f.y);
                 if (MODE == MODE_SMU) {
                     const float2 adz = make_float2(fabsf(DZ[r].x), fabsf(DZ[r].y));
@@ -773,12 +797,16 @@ __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, T
         pair_tile_global<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hbase, s_q, s_qn, s_seg,
                                                  nseg, f0, fstride, bstart, task_bits);
     } else if (LIN) {
-        if (p.lin_norange)
-            pair_tile_lin2<MODE, W, RI, MASK, false>(p, tb, len, gmask, I, lc, r2cut, hist_sa,
+        if (p.lin_log)
+            pair_tile_lin2<MODE, W, RI, MASK, true, true>(p, tb, len, gmask, I, lc, r2cut, hist_sa,
+                                                          whist_sa, hk4, s_q, s_qn, s_seg, nseg,
+                                                          f0, fstride, bstart, task_bits);
+        else if (p.lin_norange)
+            pair_tile_lin2<MODE, W, RI, MASK, false, false>(p, tb, len, gmask, I, lc, r2cut, hist_sa,
                                                      whist_sa, hk4, s_q, s_qn, s_seg, nseg, f0, fstride,
                                                      bstart, task_bits);
         else
-            pair_tile_lin2<MODE, W, RI, MASK, true>(p, tb, len, gmask, I, lc, r2cut, hist_sa,
+            pair_tile_lin2<MODE, W, RI, MASK, true, false>(p, tb, len, gmask, I, lc, r2cut, hist_sa,
                                                     whist_sa, hk4, s_q, s_qn,
                                           s_seg, nseg, f0, fstride, bstart, task_bits);
     } else {
@@ -846,6 +874,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
     lc.invA = p.lin_invA;
     lc.offA = p.lin_offA;
     lc.thrA = p.lin_thrA;
+    lc.mS = p.lin_mS;
     lc.nB = p.lin_nB;
     lc.mA = p.lin_mA;
     lc.cB = p.lin_cB;

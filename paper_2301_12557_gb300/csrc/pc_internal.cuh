@@ -105,6 +105,10 @@ struct PairParams {
     // floor(t_s) <= n_a, so the s-range test is replaced by one discarded row
     // (row n_a) of the shared histogram
     int lin_norange;
+    // lin with logarithmic s edges: t_s = lin_invA log2(s^2) + lin_offA, and the
+    // s band grows as 1/s: not near iff |frac(t_s) - 1/2| < lin_thrA - lin_mS / s
+    int lin_log;
+    float lin_mS;
     int nbins_smem;              // bins per shared copy: nbins, plus n_b with lin_norange
     // weighted sums from exact integer products of the packed binary32 weights
     // (significand product shifted by both exponent offsets, accumulated in

@@ -126,6 +126,13 @@ def test_near_edge_adversarial():
     for mode, eb in (("s", None), ("smu", mu), ("sigpi", np.linspace(0.0, 50.0, 26))):
         (g, _), (w, _) = _both(x, box=L, periodic=True, mode=mode, edges_a=ea, edges_b=eb)
         _check(g, w, what=f"near-edge {mode}")
+    # evenly spaced edges starting above zero: pairs just below the first edge
+    # fall below the histogram, pairs just above it into bin 0
+    ea5 = np.linspace(5.0, 50.0, 19)
+    x5 = synth.catalogs.near_edge_pairs(ea5[:3], L, 3000, offs, 142)
+    for mode, eb in (("s", None), ("smu", mu)):
+        (g, _), (w, _) = _both(x5, box=L, periodic=True, mode=mode, edges_a=ea5, edges_b=eb)
+        _check(g, w, what=f"near-edge {mode}, e0 > 0")
 
 
 @pytest.mark.parametrize("mode", ["s", "smu"])
@@ -143,6 +150,14 @@ def test_log_bins_clustered_and_near_edges(mode):
     y = synth.catalogs.near_edge_pairs(ea, L, 6000, offs, 602)
     (g, _), (w, _) = _both(y, box=L, periodic=True, mode=mode, edges_a=ea, edges_b=eb)
     _check(g, w, what=f"log bins near edges {mode}")
+    # edges a little off a geometric sequence: the table path instead
+    eap = ea.copy()
+    eap[1:-1] *= 1.0 + 1e-5 * np.cos(np.arange(1, ea.size - 1))
+    (g, _), (w, _) = _both(x, box=L, periodic=True, mode=mode, edges_a=eap, edges_b=eb)
+    _check(g, w, what=f"near-log bins {mode}")
+    y = synth.catalogs.near_edge_pairs(eap, L, 6000, offs, 604)
+    (g, _), (w, _) = _both(y, box=L, periodic=True, mode=mode, edges_a=eap, edges_b=eb)
+    _check(g, w, what=f"near-log bins near edges {mode}")
 
 
 def test_headline_binning_200x120_scaled():
