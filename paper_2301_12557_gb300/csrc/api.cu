@@ -643,6 +643,7 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
                              PairParams &p, int &grid, size_t &smem) {
     const Plan &P = S.P;
     memset(&p, 0, sizeof(p));
+    p.groups = 1;
     p.tasks = B.tasks;
     p.blocks = B.blocks;
     p.nblocks = B.sc + 1;
@@ -716,6 +717,21 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
         return fail(PC_EUNSUPPORTED, "bins: tables do not fit in shared memory");
     int per_sm = (S.prec == PC_PREC_F64) ? pairs_f64_ctas_per_sm(p, smem)
                                          : pairs_f32_ctas_per_sm(p, S.ipt, smem);
+    // A shared histogram so large that at most two CTAs of NT threads fit an
+    // SM: run CTAs of four independent thread groups sharing one histogram
+    // (single-histogram jobs, floor bins, binary64 or no weights, 2 i-points)
+    if (S.prec == PC_PREC_F32_RESCUE && p.smem_hist_ok && p.lin && !p.wint && !p.priv &&
+        J.nhist == 1 && S.ipt == 2 && per_sm <= 2) {
+        p.groups = 4;
+        const size_t smem4 = pairs_f32_smem(p, S.ipt);
+        const int per4 = (smem4 + 8192 <= (size_t)smem_optin) ? pairs_f32_ctas_per_sm(p, S.ipt, smem4) : 0;
+        if (per4 >= 1) {
+            smem = smem4;
+            per_sm = per4;
+        } else {
+            p.groups = 1;
+        }
+    }
     if (per_sm <= 0)
         return fail(PC_ECUDA, std::string("pair kernel cannot be resident: ") + pc_last_error());
     if (S.o.grid_ctas_per_sm > 0) per_sm = std::min(per_sm, S.o.grid_ctas_per_sm);
@@ -1292,6 +1308,7 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
 
     PairParams p;
     memset(&p, 0, sizeof(p));
+    p.groups = 1;
     p.tasks = tasks;
     p.blocks = (const Block *)(base + NA.blocks);
     p.nblocks = sc + 1;

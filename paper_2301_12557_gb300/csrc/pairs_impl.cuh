@@ -31,6 +31,7 @@ constexpr unsigned long long WINT_LIMIT = 1ull << 16;
 
 struct SmemLayout {
     size_t lut, ea, eb, hist, whist, seg, tile, meta, tw, q, total;
+    size_t gstride;   // per-group area [seg, q end): group g's copy is g * gstride further
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -62,8 +63,37 @@ __host__ __device__ inline SmemLayout smem_layout(const PairParams &p, bool f64)
     if (p.weighted && !f64) o = align_up(o + (size_t)2 * tj * sizeof(double), 16);
     L.q = o;
     o = align_up(o + (size_t)LQ * sizeof(uint3), 16);
-    L.total = o;
+    L.gstride = o - L.seg;
+    L.total = L.seg + (size_t)(f64 ? 1 : p.groups) * L.gstride;
     return L;
+}
+
+// ---------------------------------------------------------------------------
+// thread groups: a CTA of G groups of NT threads; each group works on its own
+// blocks and synchronises only with itself (named barrier 1 + group)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int gtid() { return (int)(threadIdx.x % NT); }
+
+template <int G>
+__device__ __forceinline__ void gsync() {
+    if (G == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / NT)), "r"(NT) : "memory");
+    }
+}
+
+template <int G>
+__device__ __forceinline__ bool gsync_or(bool v) {
+    if (G == 1) return __syncthreads_or(v) != 0;
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)v), "r"(1 + (int)(threadIdx.x / NT)), "r"(NT)
+        : "memory");
+    return r != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -150,9 +180,10 @@ __device__ __forceinline__ unsigned group_mask(const GBox *gb, const GBox &ib, i
 
 // Exclusive prefix over the segment lengths held in seg[k].y (in place);
 // returns the total.  All NT threads call it.
+template <int G = 1>
 __device__ __forceinline__ int seg_scan(int4 *seg, int nseg, int *s_tmp) {
     // each thread owns a contiguous run of ceil(nseg / NT) segments
-    const int tid = threadIdx.x;
+    const int tid = gtid();
     const int per = (nseg + NT - 1) / NT;
     int b0 = tid * per, b1 = min(b0 + per, nseg);
     int local = 0;
@@ -166,7 +197,7 @@ __device__ __forceinline__ int seg_scan(int4 *seg, int nseg, int *s_tmp) {
         if (lane >= o) v += t;
     }
     if (lane == 31) s_tmp[warp] = v;
-    __syncthreads();
+    gsync<G>();
     int wbase = 0;
     for (int w = 0; w < warp; ++w) wbase += s_tmp[w];
     int total = s_tmp[0] + s_tmp[1] + s_tmp[2] + s_tmp[3];
@@ -176,7 +207,7 @@ __device__ __forceinline__ int seg_scan(int4 *seg, int nseg, int *s_tmp) {
         seg[k].y = run;
         run += len;
     }
-    __syncthreads();
+    gsync<G>();
     return total;
 }
 
@@ -196,7 +227,7 @@ __device__ __forceinline__ void build_segments(const PairParams &p, const GridDe
                                                int ay, int az, int r0, int r1, int4 *seg,
                                                int *s_nseg) {
     const int nx = p.g.ng[0], ny = p.g.ng[1], nz = p.g.ng[2];
-    for (int row = r0 + (int)threadIdx.x; row < r1; row += NT) {
+    for (int row = r0 + gtid(); row < r1; row += NT) {
         int4 st = p.stencil[row];
         int dy = st.x, dz = st.y;
         int y = ay + dy, z = az + dz, wy = 0, wz = 0;
@@ -261,42 +292,65 @@ __device__ __forceinline__ void push_rescue(const PairParams &p, uint3 *s_q, int
 // Drain the CTA's staged rescue entries to the global queue.  All threads
 // call it, after a barrier that follows their last push, so every thread
 // reads the same count.
-template <int MODE, int LOS>
+template <int MODE, int LOS, int G = 1>
 __device__ __forceinline__ void drain_rescue(const PairParams &p, uint3 *s_q, CtaShared &cs,
                                              unsigned long long *s_base) {
     int n = min(cs.qn, LQ);
     if (n == 0) return;
-    if (threadIdx.x == 0) *s_base = atomicAdd(p.qcount, (unsigned long long)n);
-    __syncthreads();
+    const int tid = gtid();
+    if (tid == 0) *s_base = atomicAdd(p.qcount, (unsigned long long)n);
+    gsync<G>();
     unsigned long long base = *s_base;
-    for (int k = threadIdx.x; k < n; k += NT) {
+    for (int k = tid; k < n; k += NT) {
         unsigned long long g = base + k;
         if (g < p.qcap) p.queue[g] = s_q[k];
         else inline_rescue<MODE, LOS>(p, s_q[k]);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) cs.qn = 0;
-    __syncthreads();
+    gsync<G>();
+    if (tid == 0) cs.qn = 0;
+    gsync<G>();
 }
 
-// Add the CTA's shared histogram(s) into histogram `h` and clear them.
+// Read a shared counter and clear it.  With several thread groups sharing
+// the histogram another group may be adding to it meanwhile: exchange.
+template <int G>
+__device__ __forceinline__ int take_i32(int *a) {
+    if (G == 1) {
+        const int v = *a;
+        *a = 0;
+        return v;
+    }
+    return atomicExch(a, 0);
+}
+template <int G>
+__device__ __forceinline__ unsigned long long take_u64(unsigned long long *a) {
+    if (G == 1) {
+        const unsigned long long v = *a;
+        *a = 0ull;
+        return v;
+    }
+    return atomicExch(a, 0ull);
+}
+
+// Add the shared histogram(s) into histogram `h` and clear them (all threads
+// of the calling group; with G > 1 each group flushes whatever has been
+// added so far, which the exchanges take exactly once).
+template <int G = 1>
 __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, double *s_whist,
                                            int h, double wscale = 0.0) {
-    __syncthreads();
+    gsync<G>();
     if (p.smem_hist_ok && h >= 0) {
         // layout [warp copy][bin][lane copy]; bins past nbins form the
         // discarded row of lin_norange and are only cleared
         const int copies = p.priv ? NT / 32 : 1, K = p.hist_k, nbs = p.nbins_smem;
-        for (int b = threadIdx.x; b < nbs; b += NT) {
+        unsigned long long *u = reinterpret_cast<unsigned long long *>(s_whist);
+        for (int b = gtid(); b < nbs; b += NT) {
             long long v = 0;
             for (int c = 0; c < copies; ++c)
-                for (int k = 0; k < K; ++k) {
-                    v += s_hist[(c * nbs + b) * K + k];
-                    s_hist[(c * nbs + b) * K + k] = 0;
-                }
+                for (int k = 0; k < K; ++k) v += take_i32<G>(&s_hist[(c * nbs + b) * K + k]);
             if (b >= p.nbins) {
                 if (p.weighted)
-                    for (int k = 0; k < K; ++k) s_whist[b * K + k] = 0.0;
+                    for (int k = 0; k < K; ++k) take_u64<G>(&u[b * K + k]);
                 continue;
             }
             if (v) atomicAdd(&p.hist[(size_t)h * p.nbins + b], (unsigned long long)v);
@@ -304,23 +358,18 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
                 double w = 0.0;
                 if (p.wint) {
                     // u64 lane copies of exact integer products (each < 2^64)
-                    unsigned long long *u = reinterpret_cast<unsigned long long *>(s_whist);
-                    for (int k = 0; k < K; ++k) {
-                        w += (double)u[b * K + k];
-                        u[b * K + k] = 0ull;
-                    }
+                    for (int k = 0; k < K; ++k) w += (double)take_u64<G>(&u[b * K + k]);
                     w *= wscale;
                 } else {
-                    for (int k = 0; k < K; ++k) {
-                        w += s_whist[b * K + k];
-                        s_whist[b * K + k] = 0.0;
-                    }
+                    // binary64 sums, exchanged as their bit patterns
+                    for (int k = 0; k < K; ++k)
+                        w += __longlong_as_double((long long)take_u64<G>(&u[b * K + k]));
                 }
                 if (w != 0.0) atomicAdd(&p.whist[(size_t)h * p.nbins + b], w);
             }
         }
     }
-    __syncthreads();
+    gsync<G>();
 }
 
 // ---------------------------------------------------------------------------
@@ -820,36 +869,46 @@ __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, T
 // FP32 kernel
 // ---------------------------------------------------------------------------
 // W: 0 unweighted, 1 binary64 weighted sums, 2 integer weight products.
-template <int MODE, int LOS, int W, int RI, bool LIN>
-__global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
+// G: independent groups of NT threads per CTA that share the histograms (a
+// large histogram then keeps G x 4 warps per SM busy instead of 4).
+template <int MODE, int LOS, int W, int RI, bool LIN, int G = 1>
+__global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     k_pairs_f32(const __grid_constant__ PairParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ CtaShared cs;
-    __shared__ int s_tmp[8];
-    __shared__ unsigned long long s_base;
-    __shared__ GBox s_gbox[2][TJ / JG];   // bounding boxes of the staged j-groups
-    __shared__ GBox s_ibox[NT / 32];      // bounding box of each warp's i-points
+    __shared__ CtaShared cs_g[G];
+    __shared__ int s_tmp_g[G][8];
+    __shared__ unsigned long long s_base_g[G];
+    __shared__ GBox s_gbox_g[G][2][TJ / JG];   // bounding boxes of the staged j-groups
+    __shared__ GBox s_ibox_g[G][NT / 32];      // bounding box of each warp's i-points
+    const int grp = (int)(threadIdx.x / NT);
+    CtaShared &cs = cs_g[grp];
+    int *s_tmp = s_tmp_g[grp];
+    unsigned long long &s_base = s_base_g[grp];
+    GBox(*s_gbox)[TJ / JG] = s_gbox_g[grp];
+    GBox *s_ibox = s_ibox_g[grp];
 
     const SmemLayout Ly = smem_layout(p, false);
     float2 *s_lut = (float2 *)(smem + Ly.lut);
     int *s_hist = (int *)(smem + Ly.hist);
     double *s_whist = (double *)(smem + Ly.whist);
-    int4 *s_seg = (int4 *)(smem + Ly.seg);
-    float *s_tx = (float *)(smem + Ly.tile);     // [2][TJ] each
+    unsigned char *gsm = smem + (size_t)grp * Ly.gstride;   // this group's own area
+    int4 *s_seg = (int4 *)(gsm + Ly.seg);
+    float *s_tx = (float *)(gsm + Ly.tile);     // [2][TJ] each
     float *s_ty = s_tx + 2 * TJ;
     float *s_tz = s_ty + 2 * TJ;
-    double *s_tw = (double *)(smem + Ly.tw);
-    unsigned *s_twm = (unsigned *)(smem + Ly.tw);   // packed weights share the storage
-    uint3 *s_q = (uint3 *)(smem + Ly.q);
+    double *s_tw = (double *)(gsm + Ly.tw);
+    unsigned *s_twm = (unsigned *)(gsm + Ly.tw);   // packed weights share the storage
+    uint3 *s_q = (uint3 *)(gsm + Ly.q);
 
-    const int tid = threadIdx.x;
-    for (int k = tid; k < p.lut_total; k += NT) s_lut[k] = p.lut[k];
+    const int tid = gtid();
+    for (int k = threadIdx.x; k < p.lut_total; k += NT * G) s_lut[k] = p.lut[k];
     const int nbins = p.nbins;
     const bool smem_hist = p.smem_hist_ok != 0;
     if (smem_hist) {
         const int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
-        for (int k = tid; k < p.nbins_smem * copies; k += NT) s_hist[k] = 0;
-        if (W) for (int k = tid; k < p.nbins_smem * p.hist_k; k += NT) s_whist[k] = 0.0;
+        for (int k = threadIdx.x; k < p.nbins_smem * copies; k += NT * G) s_hist[k] = 0;
+        if (W)
+            for (int k = threadIdx.x; k < p.nbins_smem * p.hist_k; k += NT * G) s_whist[k] = 0.0;
     }
     if (tid == 0) {
         cs.qn = 0;
@@ -904,23 +963,23 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
         if (W != 2) return;
         const unsigned long long add = (unsigned long long)(NT / p.hist_k) * RI * (unsigned)n;
         if (wterms + add > WINT_LIMIT) {
-            flush_hist(p, s_hist, s_whist, cur_hist, cur_wscale);
+            flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
             since_flush = 0;
             wterms = 0;
         }
         wterms += add;
     };
-    __syncthreads();
+    __syncthreads();   // CTA-wide: shared histograms are clear
 
     for (;;) {
         if (tid == 0) cs.blk = atomicAdd(p.work_counter, 1) * p.shard_count + p.shard_index;
-        __syncthreads();
+        gsync<G>();
         const int bidx = cs.blk;
         if (bidx >= nblocks) break;
         const Block B = p.blocks[bidx];
         const TaskDev &T = p.tasks[B.task];
         if (T.hist != cur_hist || (W == 2 && T.wscale != cur_wscale)) {
-            flush_hist(p, s_hist, s_whist, cur_hist, cur_wscale);
+            flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
             cur_hist = T.hist;
             cur_wscale = T.wscale;
             since_flush = 0;
@@ -985,7 +1044,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                     if (W == 2) s_twm[f] = 0u;
                 }
             }
-            __syncthreads();
+            gsync<G>();
             wint_room(lenA);
             const int ngA = (lenA + JG - 1) / JG;    // all groups evaluated
             const unsigned maskA = ngA >= 32 ? 0xffffffffu : (1u << ngA) - 1u;
@@ -994,7 +1053,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                                                    &cs.qn, s_seg, 0, -1, 0, B.start, task_bits);
             if (tid == 0) cand_local += (unsigned long long)B.count * (B.count - 1) / 2;
             since_flush += (unsigned long long)B.count * B.count;
-            __syncthreads();
+            gsync<G>();
         }
 
         // ---- phase B: stencil rows, in chunks --------------------------------
@@ -1010,13 +1069,13 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                 }
                 cs.nseg = ns;
             }
-            __syncthreads();
+            gsync<G>();
             build_segments(p, T.gj, ax, ay, az, r0, r1, s_seg, &cs.nseg);
-            __syncthreads();
+            gsync<G>();
             const int nseg = cs.nseg;
-            __syncthreads();                 // every thread has read nseg before it changes
+            gsync<G>();                 // every thread has read nseg before it changes
             if (nseg == 0) continue;
-            const int total = seg_scan(s_seg, nseg, s_tmp);
+            const int total = seg_scan<G>(s_seg, nseg, s_tmp);
             // The chunk's j-points form ngt groups of JG; tile t holds the
             // groups t, t + ntiles, t + 2 ntiles, ...: every tile mixes all rows
             // of the chunk, so the warps (each pruning against its own i-box)
@@ -1083,7 +1142,7 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
 
             load_tile(0);
             store_tile(0);
-            __syncthreads();
+            gsync<G>();
             for (int t = 0; t < ntiles; ++t) {
                 const int buf = t & 1;
                 const int len = tile_groups(t) * JG;
@@ -1102,21 +1161,21 @@ __global__ void __launch_bounds__(NT, (RI <= 2 ? 5 : 4))
                 // one decision for the whole CTA, taken at the barrier: read
                 // after it, the count could already include pushes of the next
                 // tile by a faster warp, and the drain holds barriers itself
-                if (__syncthreads_or(cs.qn >= LQ / 2))
-                    drain_rescue<MODE, LOS>(p, s_q, cs, &s_base);
-                if (since_flush > FLUSH_LIMIT) {
-                    flush_hist(p, s_hist, s_whist, cur_hist, cur_wscale);
+                if (gsync_or<G>(cs.qn >= LQ / 2))
+                    drain_rescue<MODE, LOS, G>(p, s_q, cs, &s_base);
+                if (since_flush > FLUSH_LIMIT / G) {
+                    flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
                     since_flush = 0;
                     wterms = 0;
                 }
             }
-            __syncthreads();
+            gsync<G>();
         }
-        drain_rescue<MODE, LOS>(p, s_q, cs, &s_base);
-        __syncthreads();
+        drain_rescue<MODE, LOS, G>(p, s_q, cs, &s_base);
+        gsync<G>();
     }
-    drain_rescue<MODE, LOS>(p, s_q, cs, &s_base);
-    flush_hist(p, s_hist, s_whist, cur_hist, cur_wscale);
+    drain_rescue<MODE, LOS, G>(p, s_q, cs, &s_base);
+    flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
     if (tid == 0 && cand_local) atomicAdd(&p.counters[0], cand_local);
     if (tid == 0 && cs.pruned) atomicAdd(&p.counters[3], cs.pruned);
 }
@@ -1280,6 +1339,11 @@ template <int MODE, int LOS>
 PairKernel<MODE, LOS> pick_f32(const PairParams &p, int ipt) {
     constexpr bool LINOK = (MODE == MODE_S) || (MODE == MODE_SMU && LOS == LOS_Z);
     const bool lin = LINOK && p.lin;
+    if constexpr (LINOK) {
+        // several thread groups per CTA (large histograms): floor bins, 2 i-points
+        if (p.groups > 1 && lin && !p.wint)
+            return p.weighted ? k_pairs_f32<MODE, LOS, 1, 2, true, 4> : k_pairs_f32<MODE, LOS, 0, 2, true, 4>;
+    }
     if (p.weighted) {
         if constexpr (LINOK) {
             if (lin && p.wint) return ipt == 4 ? k_pairs_f32<MODE, LOS, 2, 4, true>
@@ -1298,7 +1362,7 @@ cudaError_t launch_mode_f32(const PairParams &p, int ipt, int grid, size_t smem,
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) return cudaSuccess;
-    k<<<grid, NT, smem, st>>>(p);
+    k<<<grid, NT * p.groups, smem, st>>>(p);
     note_launch();
     return cudaGetLastError();
 }
@@ -1309,7 +1373,7 @@ int occupancy_mode_f32(const PairParams &p, int ipt, size_t smem) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT * p.groups, smem) != cudaSuccess) return 0;
     return nb;
 }
 

@@ -91,6 +91,8 @@ struct PairParams {
     unsigned long long qcap;
     unsigned long long *counters;  // [0] candidates, [1] inline rescues
     int shard_index, shard_count;   // this launch counts blocks index * count + shard
+    int groups = 1;          // FP32 kernel: independent groups of NT threads per CTA sharing
+                             // one shared histogram (large histograms)
     int priv;                // 0: one histogram per CTA; 1: one per warp
     int hist_k = 1;          // lane copies of the shared histograms (power of 2, <= 32):
                              // lane l updates copy l % hist_k, stored [bin][copy]

@@ -172,6 +172,19 @@ def test_headline_binning_200x120_scaled():
     _check(g, w, what="200 x 120 bins")
 
 
+def test_large_weighted_histogram_grouped_ctas():
+    """6,000 (s, mu) bins with binary64 weighted sums: counts plus sums fill
+    72 KB of shared memory, so the kernel runs CTAs of four thread groups
+    sharing one histogram; counts and sums match the oracle."""
+    L = 400.0
+    x = synth.neyman_scott(30000, 3000, 10.0, 2.0, L, 605)
+    w = synth.lognormal_weights(x.shape[0], 0.3, 606)
+    ea = np.linspace(0.0, 40.0, 61)
+    eb = np.linspace(0.0, 1.0, 101)
+    (g, gw), (o, ow) = _both(x, w1=w, box=L, periodic=True, mode="smu", edges_a=ea, edges_b=eb)
+    _check(g, o, gw, ow, "6000 bins weighted")
+
+
 def test_lattice_ties_exact():
     """Integer lattice with integer edges: many exact ties on bin edges."""
     x = synth.lattice_points(3000, 24, 151)
