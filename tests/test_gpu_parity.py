@@ -533,3 +533,24 @@ def test_full_size_ns_smu_auto_vs_cross_and_sampled_oracle():
     g, _ = P.count(S, xd, **kw)
     o, _ = oracle.count(S, D, method="grid", **kw)
     _check(g, o, what="sampled cross at full size")
+
+
+def test_estimators_on_gpu_counts_of_uniform_randoms():
+    """End to end: GPU pair counts of uniform periodic randoms give a
+    Peebles-Hauser xi (with the analytic RR) and a Landy-Szalay xi (with a
+    second random catalogue) that vanish within Poisson noise."""
+    from paper_2301_12557_gb300 import estimators as E
+    L, n = 500.0, 60000
+    d = synth.uniform_box(n, L, 801)
+    r = synth.uniform_box(2 * n, L, 802)
+    ea = np.linspace(0.0, 50.0, 11)
+    kw = dict(box=L, periodic=True, edges_a=ea)
+    dd, _ = P.count(d, **kw)
+    dr, _ = P.count(d, r, **kw)
+    rr, _ = P.count(r, **kw)
+    ndd, ndr, nrr = (E.normalise(dd, E.pair_norm(n)), E.normalise(dr, E.pair_norm(n, 2 * n, auto=False)),
+                     E.normalise(rr, E.pair_norm(2 * n)))
+    rr_a = E.analytic_rr(ea, box=L)
+    sig = 1.0 / np.sqrt(rr_a * E.pair_norm(n))          # relative Poisson noise of DD
+    assert np.all(np.abs(E.peebles_hauser(ndd, rr_a)) <= 5 * sig)
+    assert np.all(np.abs(E.landy_szalay(ndd, ndr, nrr)) <= 5 * sig)
