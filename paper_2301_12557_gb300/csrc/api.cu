@@ -377,10 +377,14 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
                 // n_a + 1/2 (plus rounding), so floor(t_s) <= n_a
                 P.lin_norange = (e0 == 0.0 && ts_max - 1.0 <= P.na + 0.5) ? 1 : 0;
                 if (P.mode == PC_BIN_SMU) {
+                    // t_mu = mu n_mu (1 - 2^-21): below n_mu for every pair (mu
+                    // = |dz| rsqrt(s^2) exceeds 1 by at most ~3e-7), so mu = 1
+                    // lands in the last bin without a clamp; the scale's shift
+                    // of up to 2^-21 n_mu joins the band
                     const double nb = P.nb;
-                    P.lin_nB = (float)nb;
+                    P.lin_nB = nextafterf((float)(nb * (1.0 - ldexp(1.0, -21))), 0.0f);
                     P.lin_mA = (float)(muA * nb * (1.0 + 1e-6));
-                    double cB = 0.5 - (muB + 4.0 * u + devm) * nb;
+                    double cB = 0.5 - (muB + 4.0 * u + devm + ldexp(1.0, -21)) * nb;
                     P.lin_cB = nextafterf((float)cB, 0.0f);
                     if (!(cB > 0.25)) P.lin = 0;
                 }
@@ -430,10 +434,10 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
                 P.lin_mS = nextafterf((float)(2.0 * C1 * (1.0 + 1e-6)), INFINITY);
                 P.lin_norange = 0;
                 if (P.mode == PC_BIN_SMU) {
-                    const double nb = P.nb;
-                    P.lin_nB = (float)nb;
+                    const double nb = P.nb;   // mu scale and band as for linear s bins
+                    P.lin_nB = nextafterf((float)(nb * (1.0 - ldexp(1.0, -21))), 0.0f);
                     P.lin_mA = (float)(muA * nb * (1.0 + 1e-6));
-                    double cB = 0.5 - (muB + 4.0 * u + devm) * nb;
+                    double cB = 0.5 - (muB + 4.0 * u + devm + ldexp(1.0, -21)) * nb;
                     P.lin_cB = nextafterf((float)cB, 0.0f);
                     if (!(cB > 0.25)) P.lin = P.lin_log = 0;
                 }

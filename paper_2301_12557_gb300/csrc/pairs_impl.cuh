@@ -509,40 +509,7 @@ struct LinCtx {
     unsigned nA, nB_u;
 };
 
-// floor(t) for t in [-2^22, 2^23): the sum rounded toward -inf onto the
-// 2^23 grid; also returns floor(t) as a float
-__device__ __forceinline__ float floor_grid(float t, float &fl) {
-    float f = __fadd_rd(t, 8388608.0f);
-    fl = f - 8388608.0f;
-    return f;
-}
 
-template <int MODE>
-__device__ __forceinline__ Bin32 bin_lin(const LinCtx &c, float dz, float s2) {
-    Bin32 r;
-    const float rs = rsqrt_fast(s2);
-    const float s = s2 * rs;
-    const float ts = fmaf(s, c.invA, c.offA);
-    float fls;
-    const float fs = floor_grid(ts, fls);
-    const int k = __float_as_int(fs) - 0x4B000000;
-    // NaN (coincident points: s2 = 0) compares false, so it is near
-    bool near = !(fabsf((ts - fls) - 0.5f) < c.thrA);
-    r.ok = (unsigned)k < c.nA;
-    if (MODE == MODE_S) {
-        r.near = near;
-        r.bin = k;
-        return r;
-    }
-    const float tm = fabsf(dz) * rs * c.nB;
-    float flm;
-    const float fm = floor_grid(tm, flm);
-    const int j = min(__float_as_int(fm) - 0x4B000000, (int)c.nB_u - 1);
-    near = near || !(fabsf((tm - flm) - 0.5f) < fmaf(-c.mA, rs, c.cB));
-    r.near = near;
-    r.bin = k * (int)c.nB_u + j;
-    return r;
-}
 
 // Shared-memory reduction at a 32-bit shared-window address, issued only
 // when `on` is set (one predicated instruction, no branch).
@@ -684,7 +651,6 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
     const float thrA = lc.thrA;
     const float2 THRA = make_float2(lc.thrA, lc.thrA);
     const float2 NMS = make_float2(-lc.mS, -lc.mS);
-    const unsigned jmax = 0x4B000000u + lc.nB_u - 1u;   // float bits of 2^23 + n_mu - 1
     const unsigned nbu = (MODE == MODE_SMU) ? lc.nB_u : 1u;
     // biases of the float bits of floor(t_s) + 2^23 (and floor(t_mu) + 2^23),
     // folded into the bases
@@ -756,9 +722,10 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                     const float2 thm = __ffma2_rn(NMA, rs, CB);
                     n0 = n0 || !(fabsf(dm.x) < thm.x);
                     n1 = n1 || !(fabsf(dm.y) < thm.y);
-                    // mu = 1 (t_mu = n_mu) goes to the last bin; NaN bits clamp too
-                    const unsigned j0 = min((unsigned)__float_as_int(fm.x), jmax);
-                    const unsigned j1 = min((unsigned)__float_as_int(fm.y), jmax);
+                    // t_mu < n_mu (scale below n_mu): mu = 1 is in the last bin;
+                    // a NaN index is never used (such pairs are near)
+                    const unsigned j0 = (unsigned)__float_as_int(fm.x);
+                    const unsigned j1 = (unsigned)__float_as_int(fm.y);
                     b0 = b0 * nbu + j0;
                     b1 = b1 * nbu + j1;
                 }
