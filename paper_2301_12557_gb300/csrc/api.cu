@@ -107,6 +107,7 @@ struct Plan {
     int lin = 0;
     float lin_invA = 0, lin_offA = 0, lin_thrA = 0, lin_nB = 0, lin_mA = 0, lin_cB = 0;
     int lin_norange = 0, lin_log = 0;
+    float lin_invB2 = 0, lin_thrB = 0;
     float lin_offA1 = 0;         // lin_offA + 1, rounded once
     float lin_mS = 0;
 };
@@ -444,6 +445,31 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
             }
         }
     }
+    // ---- (sigma, pi) with evenly spaced edges from 0: floors of both ------
+    // t_sigma = sigma / D_a, t_pi = pi / D_b, sigma and pi formed as on the
+    // table path, so their bands eps_sig and eps_z apply (in t units), plus
+    // the rounding of the scale and product (2u t) and the edges' distance
+    // from even spacing.
+    if (!P.lin && P.mode == PC_BIN_SIGPI && P.fp32_ok && P.ea[0] == 0.0 && P.eb[0] == 0.0) {
+        const double Da = P.ea[P.na] / P.na, Db = P.eb[P.nb] / P.nb;
+        double deva = 0.0, devb = 0.0;
+        for (int k = 0; k <= P.na; ++k) deva = std::max(deva, fabs(P.ea[k] - k * Da));
+        for (int k = 0; k <= P.nb; ++k) devb = std::max(devb, fabs(P.eb[k] - k * Db));
+        const double tma = P.rcut / Da + 1.0, tmb = P.rcut / Db + 1.0;
+        const double eta = (eps_sig + deva) / Da + 4.0 * u * tma;
+        const double etb = (eps_z + devb) / Db + 4.0 * u * tmb;
+        if (deva <= 1e-9 * Da && devb <= 1e-9 * Db && tma < 4.0e6 && tmb < 4.0e6 && eta < 0.25 &&
+            etb < 0.25) {
+            P.lin = 1;
+            P.lin_invA = (float)(1.0 / Da);
+            P.lin_offA = 0.0f;
+            P.lin_offA1 = 0.0f;
+            P.lin_thrA = nextafterf((float)(0.5 - eta), 0.0f);
+            P.lin_invB2 = (float)(1.0 / Db);
+            P.lin_thrB = nextafterf((float)(0.5 - etb), 0.0f);
+            P.lin_norange = 0;
+        }
+    }
     // ---- stencil -------------------------------------------------------------
     int kmax[3];
     build_stencil(g, P.rcut, half, P.stencil, kmax);
@@ -686,6 +712,8 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     p.lin_norange = p.lin ? P.lin_norange : 0;
     p.lin_log = p.lin ? P.lin_log : 0;
     p.lin_mS = P.lin_mS;
+    p.lin_invB2 = P.lin_invB2;
+    p.lin_thrB = P.lin_thrB;
     p.nbins_smem = P.nbins + (p.lin_norange ? (P.mode == PC_BIN_S ? 1 : P.nb) : 0);
     p.lin_invA = P.lin_invA;
     // the range-tested floor bins take t_s + 1 (exact floors down to t_s = -1)
@@ -1351,6 +1379,8 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
     p.lin_norange = p.lin ? P.lin_norange : 0;
     p.lin_log = p.lin ? P.lin_log : 0;
     p.lin_mS = P.lin_mS;
+    p.lin_invB2 = P.lin_invB2;
+    p.lin_thrB = P.lin_thrB;
     p.nbins_smem = P.nbins + (p.lin_norange ? (P.mode == PC_BIN_S ? 1 : P.nb) : 0);
     p.lin_invA = P.lin_invA;
     // the range-tested floor bins take t_s + 1 (exact floors down to t_s = -1)

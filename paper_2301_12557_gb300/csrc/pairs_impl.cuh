@@ -505,6 +505,7 @@ __device__ __forceinline__ Bin32 bin_f32(const BinCtx &c, float dx, float dy, fl
 struct LinCtx {
     float invA, offA, thrA;   // s scaling and band threshold
     float mS;                 // logarithmic s: band term per 1/s
+    float invB2, thrB;        // (sigma, pi): pi scaling and band threshold
     float nB, mA, cB;         // mu scaling and per-pair band threshold
     unsigned nA, nB_u;
 };
@@ -768,6 +769,141 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
     }
 }
 
+// (sigma, pi) bins, both axes evenly spaced from 0, two j-points per step in
+// packed FP32.  sigma and pi are formed exactly as in the table path (so the
+// same bands apply): along z, sigma = q rsqrt(q) with q = dx^2 + dy^2 and
+// pi = |dz|; for the midpoint line of sight l = 2 x_i + d, pi = |d.l| / |l|
+// and sigma = |d x l| / |l|.  Both indices are floors on the 2^23 grid; the
+// pair counts only if both lie below their axis' bin count (pi may exceed
+// pi_max while s is still below the reach sqrt(sigma_max^2 + pi_max^2)).
+template <int LOS, int W, int RI, bool MASK>
+__device__ __forceinline__ void pair_tile_sigpi2(const PairParams &p, Tile tb, int len, unsigned gmask,
+                                                 const IPts<RI> &I, const LinCtx &lc, float r2cut,
+                                                 unsigned hist_sa, unsigned whist_sa, unsigned hk4,
+                                                 uint3 *s_q, int *s_qn, const int4 *s_seg, int nseg,
+                                                 int f0, int fstride, int bstart,
+                                                 unsigned task_bits) {
+    const float2 C23 = make_float2(8388608.0f, 8388608.0f);
+    const float2 NC23H = make_float2(-8388608.0f + 0.5f, -8388608.0f + 0.5f);
+    const float2 M1 = make_float2(-1.0f, -1.0f);
+    const float2 TWO = make_float2(2.0f, 2.0f);
+    const float2 INVA = make_float2(lc.invA, lc.invA);
+    const float2 INVB = make_float2(lc.invB2, lc.invB2);
+    const float thrA = lc.thrA, thrB = lc.thrB;
+    const unsigned nbu = lc.nB_u;
+    const unsigned limA = 0x4B000000u + lc.nA, limB = 0x4B000000u + lc.nB_u;
+    const unsigned bias = 0x4B000000u * nbu + 0x4B000000u;
+    const unsigned hbase = hist_sa - hk4 * bias;
+    const unsigned wbase = whist_sa - 2u * hk4 * bias;
+    float2 NX[RI], NY[RI], NZ[RI];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        NX[r] = make_float2(-I.x[r], -I.x[r]);
+        NY[r] = make_float2(-I.y[r], -I.y[r]);
+        NZ[r] = make_float2(-I.z[r], -I.z[r]);
+    }
+#pragma unroll 1
+    for (unsigned gm = gmask; gm; gm &= gm - 1) {
+    const int j0 = (__ffs(gm) - 1) * JG, j1 = min(j0 + JG, len);
+#pragma unroll 2
+    for (int jj = j0; jj < j1; jj += 2) {
+        const float2 X = *reinterpret_cast<const float2 *>(tb.x + jj);
+        const float2 Y = *reinterpret_cast<const float2 *>(tb.y + jj);
+        const float2 Z = *reinterpret_cast<const float2 *>(tb.z + jj);
+        float2 S2[RI];
+        bool in0[RI], in1[RI];
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const float2 dx = __fadd2_rn(X, NX[r]);
+            const float2 dy = __fadd2_rn(Y, NY[r]);
+            const float2 dz = __fadd2_rn(Z, NZ[r]);
+            S2[r] = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            in0[r] = S2[r].x < r2cut;
+            in1[r] = S2[r].y < r2cut;
+            if (MASK) {
+                in0[r] = in0[r] && (bstart + jj > I.idx[r]);
+                in1[r] = in1[r] && (bstart + jj + 1 > I.idx[r]);
+            }
+            any = any || in0[r] || in1[r];
+        }
+        if (__any_sync(0xffffffffu, any)) {
+            bool re0[RI], re1[RI];
+            bool anyr = false;
+#pragma unroll
+            for (int r = 0; r < RI; ++r) {
+                const float2 dx = __fadd2_rn(X, NX[r]);
+                const float2 dy = __fadd2_rn(Y, NY[r]);
+                const float2 dz = __fadd2_rn(Z, NZ[r]);
+                float2 sg, pz;
+                if (LOS == LOS_Z) {
+                    const float2 q = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+                    sg = __fmul2_rn(q, make_float2(rsqrt_fast(q.x), rsqrt_fast(q.y)));
+                    pz = make_float2(fabsf(dz.x), fabsf(dz.y));
+                } else {
+                    const float2 lx = __ffma2_rn(TWO, make_float2(I.xa[r], I.xa[r]), dx);
+                    const float2 ly = __ffma2_rn(TWO, make_float2(I.ya[r], I.ya[r]), dy);
+                    const float2 lz = __ffma2_rn(TWO, make_float2(I.za[r], I.za[r]), dz);
+                    const float2 sl = __ffma2_rn(dz, lz, __ffma2_rn(dy, ly, __fmul2_rn(dx, lx)));
+                    const float2 ll = __ffma2_rn(lz, lz, __ffma2_rn(ly, ly, __fmul2_rn(lx, lx)));
+                    const float2 rl = make_float2(rsqrt_fast(ll.x), rsqrt_fast(ll.y));
+                    pz = __fmul2_rn(make_float2(fabsf(sl.x), fabsf(sl.y)), rl);
+                    const float2 ndx = make_float2(-dx.x, -dx.y), ndy = make_float2(-dy.x, -dy.y),
+                                 ndz = make_float2(-dz.x, -dz.y);
+                    const float2 cx = __ffma2_rn(dy, lz, __fmul2_rn(ndz, ly));
+                    const float2 cy = __ffma2_rn(dz, lx, __fmul2_rn(ndx, lz));
+                    const float2 cz = __ffma2_rn(dx, ly, __fmul2_rn(ndy, lx));
+                    const float2 cc = __ffma2_rn(cz, cz, __ffma2_rn(cy, cy, __fmul2_rn(cx, cx)));
+                    sg = __fmul2_rn(__fmul2_rn(cc, make_float2(rsqrt_fast(cc.x), rsqrt_fast(cc.y))), rl);
+                }
+                const float2 ta = __fmul2_rn(sg, INVA), tb2 = __fmul2_rn(pz, INVB);
+                const float2 fa = __fadd2_rd(ta, C23), fb = __fadd2_rd(tb2, C23);
+                const float2 da = __ffma2_rn(__fadd2_rn(fa, NC23H), M1, ta);   // frac - 1/2
+                const float2 db = __ffma2_rn(__fadd2_rn(fb, NC23H), M1, tb2);
+                // NaN (s = 0 or l = 0) compares false: near
+                const bool n0 = !(fabsf(da.x) < thrA) || !(fabsf(db.x) < thrB);
+                const bool n1 = !(fabsf(da.y) < thrA) || !(fabsf(db.y) < thrB);
+                const unsigned ba0 = (unsigned)__float_as_int(fa.x), ba1 = (unsigned)__float_as_int(fa.y);
+                const unsigned bb0 = (unsigned)__float_as_int(fb.x), bb1 = (unsigned)__float_as_int(fb.y);
+                const bool ok0 = ba0 < limA && bb0 < limB, ok1 = ba1 < limA && bb1 < limB;
+                const unsigned b0 = ba0 * nbu + bb0, b1 = ba1 * nbu + bb1;
+                const bool a0 = in0[r] && ok0 && !n0, a1 = in1[r] && ok1 && !n1;
+                red_shared_u32_if(hbase + hk4 * b0, a0);
+                red_shared_u32_if(hbase + hk4 * b1, a1);
+                if (W == 1) {
+                    const double2 wj = *reinterpret_cast<const double2 *>(tb.w + jj);
+                    red_shared_f64_if(wbase + 2u * hk4 * b0, __dmul_rn(I.w[r], wj.x), a0);
+                    red_shared_f64_if(wbase + 2u * hk4 * b1, __dmul_rn(I.w[r], wj.y), a1);
+                } else if (W == 2) {
+                    const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
+                    const unsigned mi = I.wm[r] & 0xFFFFFFu, ki = I.wm[r] >> 24;
+                    const unsigned long long p0 =
+                        ((unsigned long long)mi * (wj.x & 0xFFFFFFu)) >> (ki + (wj.x >> 24));
+                    const unsigned long long p1 =
+                        ((unsigned long long)mi * (wj.y & 0xFFFFFFu)) >> (ki + (wj.y >> 24));
+                    red_shared_u64_if(wbase + 2u * hk4 * b0, p0, a0);
+                    red_shared_u64_if(wbase + 2u * hk4 * b1, p1, a1);
+                }
+                re0[r] = in0[r] && n0;
+                re1[r] = in1[r] && n1;
+                anyr = anyr || re0[r] || re1[r];
+            }
+            if (__any_sync(0xffffffffu, anyr)) {
+#pragma unroll
+                for (int r = 0; r < RI; ++r) {
+                    if (re0[r])
+                        rescue_push<MODE_SIGPI, LOS>(p, s_q, s_qn, s_seg, nseg, f0, fstride, jj,
+                                                     bstart, I.idx[r], task_bits);
+                    if (re1[r])
+                        rescue_push<MODE_SIGPI, LOS>(p, s_q, s_qn, s_seg, nseg, f0, fstride, jj + 1,
+                                                     bstart, I.idx[r], task_bits);
+                }
+            }
+        }
+    }
+    }
+}
+
 // Global-histogram variant for histograms too large for shared memory.
 template <int MODE, int LOS, int W, int RI, bool MASK>
 __device__ __forceinline__ void pair_tile_global(const PairParams &p, Tile tb, int len, unsigned gmask,
@@ -812,7 +948,10 @@ __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, T
     if (!smem_hist) {
         pair_tile_global<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hbase, s_q, s_qn, s_seg,
                                                  nseg, f0, fstride, bstart, task_bits);
-    } else if (LIN) {
+    } else if constexpr (LIN && MODE == MODE_SIGPI) {
+        pair_tile_sigpi2<LOS, W, RI, MASK>(p, tb, len, gmask, I, lc, r2cut, hist_sa, whist_sa, hk4,
+                                           s_q, s_qn, s_seg, nseg, f0, fstride, bstart, task_bits);
+    } else if constexpr (LIN) {
         if (p.lin_log)
             pair_tile_lin2<MODE, W, RI, MASK, true, true>(p, tb, len, gmask, I, lc, r2cut, hist_sa,
                                                           whist_sa, hk4, s_q, s_qn, s_seg, nseg,
@@ -901,6 +1040,8 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     lc.offA = p.lin_offA;
     lc.thrA = p.lin_thrA;
     lc.mS = p.lin_mS;
+    lc.invB2 = p.lin_invB2;
+    lc.thrB = p.lin_thrB;
     lc.nB = p.lin_nB;
     lc.mA = p.lin_mA;
     lc.cB = p.lin_cB;
@@ -1304,7 +1445,7 @@ using PairKernel = void (*)(PairParams);
 // bins are specialised only where they apply: s, and (s, mu) along z.
 template <int MODE, int LOS>
 PairKernel<MODE, LOS> pick_f32(const PairParams &p, int ipt) {
-    constexpr bool LINOK = (MODE == MODE_S) || (MODE == MODE_SMU && LOS == LOS_Z);
+    constexpr bool LINOK = (MODE == MODE_S) || (MODE == MODE_SMU && LOS == LOS_Z) || MODE == MODE_SIGPI;
     const bool lin = LINOK && p.lin;
     if constexpr (LINOK) {
         // several thread groups per CTA (large histograms): floor bins, 2 i-points

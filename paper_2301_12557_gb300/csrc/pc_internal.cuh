@@ -111,6 +111,10 @@ struct PairParams {
     // s band grows as 1/s: not near iff |frac(t_s) - 1/2| < lin_thrA - lin_mS / s
     int lin_log;
     float lin_mS;
+    // lin for (sigma, pi) bins (both axes evenly spaced from 0): t_sigma =
+    // sigma lin_invA, t_pi = pi lin_invB2, not near iff |frac - 1/2| is below
+    // lin_thrA and lin_thrB
+    float lin_invB2, lin_thrB;
     int nbins_smem;              // bins per shared copy: nbins, plus n_b with lin_norange
     // weighted sums from exact integer products of the packed binary32 weights
     // (significand product shifted by both exponent offsets, accumulated in
