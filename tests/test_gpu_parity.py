@@ -206,6 +206,68 @@ def test_small_and_ragged_sizes(n):
     _check(g, w, what=f"n={n}")
 
 
+@pytest.mark.parametrize("n1,n2", [(0, 500), (500, 0), (1, 500), (500, 1), (1, 1)])
+def test_cross_with_empty_and_single_catalogues(n1, n2):
+    L = 60.0
+    x1 = synth.uniform_box(n1, L, 171) if n1 else np.zeros((0, 3))
+    x2 = synth.uniform_box(n2, L, 172) if n2 else np.zeros((0, 3))
+    ea = np.linspace(0.0, 20.0, 11)
+    (g, _), (w, _) = _both(x1, x2, box=L, periodic=True, mode="smu", edges_a=ea,
+                           edges_b=np.linspace(0, 1, 5))
+    _check(g, w, what=f"cross {n1} x {n2}")
+
+
+def test_batch_with_empty_and_single_mocks():
+    L = 100.0
+    ea = np.linspace(0.0, 20.0, 11)
+    eb = np.linspace(0.0, 1.0, 6)
+    bins = P.Bins("smu", "z", ea, eb)
+    box = P.make_box(L, True)
+    cats = [np.zeros((0, 3)), synth.uniform_box(1, L, 181), synth.uniform_box(3000, L, 182),
+            np.zeros((0, 3)), synth.neyman_scott(2000, 200, 10.0, 2.0, L, 183)]
+    opts = P.make_opts("f32", 25.0)
+    gs = [P.pc_build_grid(c, box=box, r_max=bins.r_max, opts=opts) for c in cats]
+    try:
+        for use_graph in (0, 1):
+            opts.use_graph = use_graph
+            got, _, _ = P.pc_count_batch(gs, bins, opts)
+            got = got.reshape(len(cats), -1)
+            for k, c in enumerate(cats):
+                want, _ = oracle.count(c, box=L, periodic=True, mode="smu", edges_a=ea,
+                                       edges_b=eb, method="grid")
+                _check(got[k], want, what=f"batch mock {k} (graph {use_graph})")
+    finally:
+        for g in gs:
+            g.free()
+
+
+def test_periodic_coordinates_on_and_outside_the_box():
+    """Coordinates at 0, at L, just inside and outside [0, L) and several box
+    lengths away are folded into the box (canonical form) on both sides."""
+    L = 80.0
+    rng = np.random.default_rng(191)
+    base = synth.uniform_box(3000, L, 192)
+    special = np.array([[0.0, 0.0, 0.0], [L, L, L], [L - 1e-12, 0.5, 79.9], [-1e-12, 40.0, 40.0],
+                        [-L, 2 * L, 3 * L + 1.0], [1.0, -0.5, L + 0.5], [0.0, 0.0, 1e-9]])
+    shifted = base + L * rng.integers(-3, 4, size=base.shape)
+    x = np.vstack([base[:1500], shifted[1500:], special])
+    ea = np.linspace(0.0, 30.0, 16)
+    for mode, eb in (("s", None), ("smu", np.linspace(0, 1, 9)), ("sigpi", np.linspace(0, 20, 5))):
+        (g, _), (w, _) = _both(x, box=L, periodic=True, mode=mode, edges_a=ea, edges_b=eb)
+        _check(g, w, what=f"folded coordinates {mode}")
+
+
+def test_catalogue_far_from_the_origin():
+    """A non-periodic catalogue offset by 1e5 Mpc/h: the FP32 path works on
+    cell-relative offsets, and its band carries the coordinate magnitude."""
+    x = synth.neyman_scott(6000, 600, 10.0, 2.0, 200.0, 193) + np.array([1.0e5, -2.5e5, 7.0e4])
+    ea = np.linspace(0.0, 25.0, 26)
+    for mode, los, eb in (("s", "z", None), ("smu", "z", np.linspace(0, 1, 11)),
+                          ("sigpi", "mid", np.linspace(0, 20, 11))):
+        (g, _), (w, _) = _both(x, periodic=False, mode=mode, los=los, edges_a=ea, edges_b=eb)
+        _check(g, w, what=f"far catalogue {mode}/{los}")
+
+
 def test_dense_cell_and_duplicates():
     """One dense clump (thousands of points in one cell) plus exact duplicates
     (s = 0 pairs go to bin 0 / mu bin 0)."""
