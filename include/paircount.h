@@ -202,15 +202,16 @@ typedef struct {
 } pc_tune_trial;
 
 /* Measured autotuner for the options of a count (the cost model of Appendix
- * B.1 gives the starting cell side).  Builds the catalogue's grid at cell
- * sides 0.8 to 2 times the model's choice, times the pair and rescue kernels
- * on an evenly spaced sample of the point blocks for 2 and 4 i-points per
- * thread, then per-warp histogram copies at the best of those, and writes
- * the fastest options to *out (base's other fields are kept).
+ * B.1 gives the starting cell side).  Times the pair and rescue kernels on an
+ * evenly spaced sample of the point blocks: 2 and 4 i-points per thread at
+ * the model's cell side, then the better of those at cell sides in
+ * quarter-octave steps from 0.7 to 2 times it (distinct grids only), then one
+ * count copy per warp at the best; writes the fastest options to *out
+ * (base's other fields are kept).
  *   xyz, w, w_is_f32, n, box   the catalogue, as for pc_build_grid
  *   b                          the bins the counts will use
- *   base                       starting options (NULL = defaults); priv != 0
- *                              there keeps the caller's privatisation
+ *   base                       starting options (NULL = defaults); priv 1 or
+ *                              2 there keeps the caller's replication
  *   trials                     optional host array of max_trials records;
  *                              *n_trials receives how many were written
  * Each trial runs on every S-th block, S chosen so that a trial takes about

@@ -1,11 +1,11 @@
 // Measured autotuner: cell side, i-points per thread and histogram privatisation.
 //
 // The cost model of Appendix B.1 (pc_suggest_cell_size) gives a starting cell
-// side; the tuner then builds the grid at a few sides around it and times the
-// FP32 pair kernel (plus rescue) on an evenly spaced sample of the point
-// blocks -- the block-shard mechanism of the multi-GPU path with one shard --
-// for i-points-per-thread 2 and 4, then one histogram copy per CTA against
-// one per warp, and returns the fastest combination.
+// side; the tuner times the FP32 pair kernel (plus rescue) on an evenly spaced
+// sample of the point blocks -- the block-shard mechanism of the multi-GPU
+// path with one shard -- first for 2 and 4 i-points per thread at that side,
+// then at cell sides in quarter-octave steps from 0.7 to 2 times it, then
+// with one count copy per warp, and returns the fastest combination.
 #include <math.h>
 #include <string.h>
 
@@ -119,17 +119,67 @@ extern "C" pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, lon
             S = std::min(S_max, (int)std::min(1e9, ceil(S * (double)ms / TRIAL_MS)));
     }
 
-    const double factors[] = {0.8, 1.0, 1.25, 1.6, 2.0};
-    const int ipts[] = {2, 4};
     const bool fp32 = o.prec == PC_PREC_F32_RESCUE;
     const bool fixed_priv = o.priv == 1 || o.priv == 2;
     if (!fixed_priv) out->priv = 0;
-    std::vector<long long> seen;
     float best_ms = INFINITY;
     int nt = 0;
-    for (double f : factors) {
-        const double c = c0 * f;
-        if (c > 2.0 * reach || c < reach / 16.0) continue;
+    // one timed trial: the sampled pair and rescue kernels of grid g
+    auto trial = [&](pc_grid *g, const pc_opts &oc, float &ms) -> pc_status {
+        pc_opts ot = oc;
+        ot.shard_index = 0;
+        ot.shard_count = S;
+        ms = INFINITY;
+        pc_status s = PC_OK;
+        for (int rep = 0; rep < 2 && s == PC_OK; ++rep) {
+            pc_stats sts;
+            s = pc_count_auto(g, b, &ot, stream, (long long *)dc.p, (double *)dw.p, &sts);
+            if (s == PC_OK) ms = std::min(ms, sts.ms_pairs + sts.ms_rescue);
+            if (ms > 4.f * TRIAL_MS) break;   // long trials: one repetition
+        }
+        return s;
+    };
+    auto record = [&](double c, int ipt, float ms) {
+        if (nt < max_trials) trials[nt] = pc_tune_trial{c, ipt, fixed_priv ? o.priv : 0, ms};
+        ++nt;
+        if (ms < best_ms) {
+            best_ms = ms;
+            out->cell_size = c;
+            out->ipt = ipt;
+        }
+    };
+    // 1. i-points per thread at the model's cell side
+    int ipt_best = 2;
+    {
+        pc_opts oc = o;
+        oc.cell_size = c0;
+        pc_grid *g = nullptr;
+        pc_status s = pc_build_grid(xyz, w, w_is_f32, n, box, reach, &oc, stream, &g);
+        if (s != PC_OK) return s;
+        float ms2 = INFINITY, ms4 = INFINITY;
+        oc.ipt = 2;
+        s = trial(g, oc, ms2);
+        if (s == PC_OK && fp32) {   // the FP64 kernel holds one point per thread
+            oc.ipt = 4;
+            s = trial(g, oc, ms4);
+        }
+        pc_free_grid(g);
+        if (s != PC_OK) return s;
+        record(c0, 2, ms2);
+        if (fp32) record(c0, 4, ms4);
+        ipt_best = ms4 < ms2 ? 4 : 2;
+    }
+    // 2. cell sides in quarter-octave steps from 0.7 to 2 times the model's
+    //    (distinct grids only; the model's own side was timed above)
+    std::vector<long long> seen;
+    {
+        long long ng[3];
+        grid_dims(box, lo, hi, c0, ng);
+        seen.push_back((ng[0] * 65537LL + ng[1]) * 65537LL + ng[2]);
+    }
+    for (int k = -2; k <= 4; ++k) {
+        const double c = c0 * exp2(0.25 * k);
+        if (k == 0 || c > 2.0 * reach || c < reach / 16.0) continue;
         long long ng[3];
         grid_dims(box, lo, hi, c, ng);
         const long long key = (ng[0] * 65537LL + ng[1]) * 65537LL + ng[2];
@@ -137,36 +187,16 @@ extern "C" pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, lon
         seen.push_back(key);
         pc_opts oc = o;
         oc.cell_size = c;
+        oc.ipt = ipt_best;
         pc_grid *g = nullptr;
         pc_status s = pc_build_grid(xyz, w, w_is_f32, n, box, reach, &oc, stream, &g);
         if (s == PC_EOVERFLOW) continue;   // too many cells at this side
         if (s != PC_OK) return s;
-        for (int ipt : ipts) {
-            if (!fp32 && ipt != 2) continue;   // the FP64 kernel holds one point per thread
-            pc_opts ot = oc;
-            ot.ipt = ipt;
-            ot.shard_index = 0;
-            ot.shard_count = S;
-            float ms = INFINITY;
-            for (int rep = 0; rep < 2 && s == PC_OK; ++rep) {
-                pc_stats sts;
-                s = pc_count_auto(g, b, &ot, stream, (long long *)dc.p, (double *)dw.p, &sts);
-                if (s == PC_OK) ms = std::min(ms, sts.ms_pairs + sts.ms_rescue);
-                if (ms > 4.f * TRIAL_MS) break;   // long trials: one repetition
-            }
-            if (s != PC_OK) {
-                pc_free_grid(g);
-                return s;
-            }
-            if (nt < max_trials) trials[nt] = pc_tune_trial{c, ipt, fixed_priv ? o.priv : 0, ms};
-            ++nt;
-            if (ms < best_ms) {
-                best_ms = ms;
-                out->cell_size = c;
-                out->ipt = ipt;
-            }
-        }
+        float ms = INFINITY;
+        s = trial(g, oc, ms);
         pc_free_grid(g);
+        if (s != PC_OK) return s;
+        record(c, ipt_best, ms);
     }
     // histogram replication (automatic vs one copy per warp) at the best cell
     // side and i-tile, unless the caller fixed it
