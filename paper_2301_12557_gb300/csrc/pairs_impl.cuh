@@ -2,23 +2,27 @@
 // mode in pairs_*.cu).
 //
 // Work decomposition (grid traversal of Sect. 2.1 with the half-shell
-// duplicate removal of Sect. 3.1): a persistent CTA repeatedly takes a block
-// of up to NT * RI consecutive points of one cell (the i-points, kept in
-// registers) and streams every candidate j-point of the neighbouring cells
-// through shared memory.  Neighbours are visited row by row: for a stencil
-// row (dy, dz) the cells (ax + xlo .. ax + xhi, ay + dy, az + dz) are
-// contiguous in the cell-sorted arrays, so each row is one index range
-// (split at most in three by periodic wrapping).  Periodic images are
+// duplicate removal of Sect. 3.1): a persistent CTA (or each of its thread
+// groups) repeatedly takes a block of up to NT * RI consecutive points of one
+// cell (the i-points, kept in registers) and streams every candidate j-point
+// of the neighbouring cells through shared memory.  Neighbours are visited row
+// by row: for a stencil row (dy, dz) the cells (ax + xlo .. ax + xhi, ay + dy,
+// az + dz) are contiguous in the cell-sorted arrays, so each row is one index
+// range (split at most in three by periodic wrapping).  Periodic images are
 // handled by shifting whole cells (Sect. 3.1), never by testing each pair.
+// Runs of 32 staged j-points are skipped per warp when their bounding box is
+// out of reach of the warp's i-points.
 //
 // FP32 path: the j-point is staged as its offset from the i-cell centre,
 // rel_j + delta * c, so a pair costs three subtractions and three
 // multiply-adds.  The squared separation selects candidates; in-range pairs
-// are binned through lookup tables over s, mu, sigma or pi (Sect. 3.2.3),
-// each entry holding the single bin edge near that table cell.  A pair whose
-// value lies within the proven FP32 error band of that edge is re-evaluated
-// with the exact binary64 definition (queued for the rescue kernel), so the
-// integer counts equal the binary64 definition exactly.
+// are binned by floors of scaled values (evenly spaced or logarithmic s,
+// evenly spaced mu, sigma and pi; Sect. 3.2.2) or through lookup tables for
+// other edges (Sect. 3.2.3), each table entry holding the single bin edge
+// near that table cell.  A pair whose value lies within the proven FP32 error
+// band of an edge is re-evaluated with the exact binary64 definition (queued
+// for the rescue kernel), so the integer counts equal the binary64 definition
+// exactly.
 #pragma once
 
 #include "pc_internal.cuh"

@@ -13,13 +13,13 @@ namespace pc {
 // ---------------------------------------------------------------------------
 // launch geometry of the pair kernels
 // ---------------------------------------------------------------------------
-constexpr int NT = 128;        // threads per CTA
+constexpr int NT = 128;        // threads per CTA (per thread group with grouped CTAs)
 constexpr int TJ = 512;        // j points per shared-memory tile (FP32 path)
 constexpr int TJ64 = 128;      // j points per tile (FP64 path)
 constexpr int MAXSEG = 256;    // j segments per chunk of stencil rows
 constexpr int ROWCHUNK = 84;   // stencil rows per chunk (<= 3 segments each)
 static_assert(3 * ROWCHUNK + 1 <= MAXSEG, "a chunk's segments (and the own-cell rest) fit");
-constexpr int LQ = 256;        // per-CTA rescue staging slots
+constexpr int LQ = 256;        // rescue staging slots per CTA (per thread group)
 constexpr int MAX_LUT = 8192;  // LUT entries per histogram axis
 
 enum { MODE_S = 0, MODE_SMU = 1, MODE_SIGPI = 2 };
@@ -27,7 +27,8 @@ enum { LOS_Z = 0, LOS_MID = 1 };
 
 // Cell-sorted device arrays of one grid.
 struct GridDev {
-    const float4 *rel;       // FP32 offset from the cell centre (.w unused = 0)
+    const float4 *rel;       // FP32 offset from the cell centre; .w: packed integer weight
+                             // (integer weight path) or 0
     const uint16_t *cx;      // x cell index per point
     const double4_32a *xw;       // FP64 canonical coordinates, .w = weight (1 if none)
     const int *cell_start;   // ncell + 1
