@@ -59,6 +59,16 @@ def _load():
                 ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
                 ctypes.c_int, dp, ctypes.c_int, dp,
                 ctypes.c_int, ctypes.c_int, i64p, dp]
+            lib.oracle_count_kdtree.restype = ctypes.c_int
+            lib.oracle_count_kdtree.argtypes = [
+                dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int64,
+                ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
+                ctypes.c_int, dp, ctypes.c_int, dp,
+                ctypes.c_int, i64p, dp]
+            ip = ctypes.POINTER(ctypes.c_int)
+            lib.oracle_kdtree.restype = ctypes.c_int
+            lib.oracle_kdtree.argtypes = [dp, ctypes.c_int64, ctypes.c_int, dp, ctypes.c_int,
+                                          ctypes.c_int64, i64p, i64p, ip, dp, i64p]
             lib.oracle_pair_bin.restype = ctypes.c_int
             lib.oracle_pair_bin.argtypes = [dp, dp, ctypes.c_int, dp, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp]
@@ -95,12 +105,14 @@ def nbins_of(mode: str, edges_a, edges_b) -> int:
 
 def count(x1, x2=None, *, w1=None, w2=None, box=None, periodic=False,
           mode="s", los="z", edges_a, edges_b=None, method="brute",
-          threads=None, weighted=None):
+          threads=None, weighted=None, n_leaf=8):
     """Exact pair counts of catalogue x1 (auto) or x1 x x2 (cross).
 
     Returns (counts int64 [nbins], wcounts float64 [nbins] or None).  The bin
     layout is row-major with the s (or sigma) index outermost.
-    ``method`` is "brute" (all pairs) or "grid" (cell list, same semantics).
+    ``method`` is "brute" (all pairs), "grid" (cell list, same semantics) or
+    "kdtree" (k-d tree of Alg. 1 with leaves of at most ``n_leaf`` points and
+    the dual-tree traversal of Alg. 3; one thread).
     """
     lib = _load()
     x1 = _f64(x1, (-1, 3))
@@ -121,6 +133,17 @@ def count(x1, x2=None, *, w1=None, w2=None, box=None, periodic=False,
     nb = nbins_of(mode, ea, eb)
     counts = np.zeros(nb, dtype=np.int64)
     wc = np.zeros(nb, dtype=np.float64) if weighted else None
+    if method == "kdtree":
+        rc = lib.oracle_count_kdtree(
+            _dptr(x1), _dptr(w1), x1.shape[0],
+            _dptr(x2), _dptr(w2), 0 if x2 is None else x2.shape[0],
+            int(bool(periodic)), _dptr(L), MODES[mode], LOS[los],
+            ea.size - 1, _dptr(ea), eb.size - 1, _dptr(eb), int(n_leaf),
+            counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            _dptr(wc) if wc is not None else None)
+        if rc != 0:
+            raise ValueError("oracle_count_kdtree rejected its arguments")
+        return counts, wc
     rc = lib.oracle_count(
         _dptr(x1), _dptr(w1), x1.shape[0],
         _dptr(x2), _dptr(w2), 0 if x2 is None else x2.shape[0],
@@ -132,6 +155,40 @@ def count(x1, x2=None, *, w1=None, w2=None, box=None, periodic=False,
     if rc != 0:
         raise ValueError("oracle_count rejected its arguments")
     return counts, wc
+
+
+def kdtree(x, *, n_leaf=8, box=None, periodic=False) -> dict:
+    """The k-d tree of Alg. 1 over x (canonical coordinates when periodic).
+
+    Heap order (children of slot h: 2h + 1, 2h + 2).  Returns a dict with
+    ``depth``, ``start``, ``count`` (-1 in empty slots), ``axis`` (-1 for
+    leaves and empty slots), ``box`` ([slots, 6]: lo, hi) and ``ord`` (tree
+    position -> point index).
+    """
+    lib = _load()
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    L = _f64(box if box is not None else [0.0, 0.0, 0.0], (-1,))
+    if L.size == 1:
+        L = np.repeat(L, 3)
+    d, m = 0, n
+    while m > n_leaf:
+        m = (m + 1) // 2
+        d += 1
+    slots = (2 << d) - 1
+    start = np.zeros(slots, dtype=np.int64)
+    count = np.zeros(slots, dtype=np.int64)
+    axis = np.zeros(slots, dtype=np.int32)
+    bx = np.zeros((slots, 6), dtype=np.float64)
+    order = np.zeros(n, dtype=np.int64)
+    i64 = ctypes.POINTER(ctypes.c_int64)
+    rc = lib.oracle_kdtree(_dptr(x), n, int(bool(periodic)), _dptr(L), int(n_leaf), slots,
+                           start.ctypes.data_as(i64), count.ctypes.data_as(i64),
+                           axis.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(bx),
+                           order.ctypes.data_as(i64))
+    if rc < 0:
+        raise ValueError("oracle_kdtree rejected its arguments")
+    return {"depth": rc, "start": start, "count": count, "axis": axis, "box": bx, "ord": order}
 
 
 def pair_bin(a, b, *, box=None, periodic=False, mode="s", los="z", edges_a,

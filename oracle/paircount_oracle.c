@@ -33,12 +33,14 @@
  *   weights                  pair weight w_i * w_j, summed per bin with
  *                            Neumaier compensation
  *
- * Two drivers share that pair definition: a brute-force O(N1 N2) loop, and a
+ * Three drivers share that pair definition: a brute-force O(N1 N2) loop, a
  * cell list with cells no smaller than the largest separation of interest
  * (Sect. 2.1: three passes -- bounds, per-cell counts, grouping -- then visit
- * each cell and its neighbours).  Threads work on disjoint rows or cells with
- * private histograms that are summed at the end, so integer counts do not
- * depend on the thread count.
+ * each cell and its neighbours), and a k-d tree with the dual-tree traversal
+ * (Sect. 2.2, Alg. 1 and Sect. 3.1, Alg. 3).  Threads work on disjoint rows
+ * or cells with private histograms that are summed at the end, so integer
+ * counts do not depend on the thread count; the tree driver runs on one
+ * thread.
  */
 #include <math.h>
 #include <pthread.h>
@@ -432,4 +434,361 @@ int oracle_pair_bin(const double *a, const double *b, int periodic, const double
         pb[q] = periodic ? canon(b[q], c.L[q]) : b[q];
     }
     return pair_bin(&c, pa, pb);
+}
+
+/* ------------------------------------------------------------------------ */
+/* k-d tree (Sect. 2.2, Alg. 1) and dual-tree traversal (Sect. 3.1, Alg. 3)  */
+/* ------------------------------------------------------------------------ */
+
+/* Nodes are kept in heap order: the root is slot 0 and the children of slot
+ * h are 2h + 1 (left) and 2h + 2 (right).  Every split gives the left child
+ * floor(n / 2) points, so all nodes of one level hold n_d or n_d + 1 points
+ * and the tree is balanced. */
+typedef struct {
+    int depth;            /* deepest level holding a node */
+    int64_t nslots;       /* 2^(depth + 1) - 1 */
+    int64_t *start;       /* first position of the node in ord */
+    int64_t *count;       /* points of the node; -1 in an empty slot */
+    int *axis;            /* split axis, -1 for a leaf or an empty slot */
+    double *box;          /* lo[3], hi[3] of the node's points (minimum AABB) */
+    int64_t *ord;         /* tree order: position -> point index */
+} otree;
+
+typedef struct {
+    double v;
+    int64_t i;
+} keyed;
+
+static int keyed_cmp(const void *pa, const void *pb)
+{
+    const keyed *a = (const keyed *)pa, *b = (const keyed *)pb;
+    if (a->v < b->v) return -1;
+    if (a->v > b->v) return 1;
+    return (a->i > b->i) - (a->i < b->i);
+}
+
+/* Levels below the root until every node holds at most n_leaf points: the
+ * largest node of a level holds ceil(n / 2^d) points. */
+static int kd_depth(int64_t n, int n_leaf)
+{
+    int d = 0;
+    int64_t m = n;
+    while (m > n_leaf) {
+        m = (m + 1) / 2;
+        d++;
+    }
+    return d;
+}
+
+static void kd_node(otree *t, const double *x, int64_t h, int64_t start, int64_t count,
+                    int n_leaf, keyed *tmp)
+{
+    t->start[h] = start;
+    t->count[h] = count;
+    double *bx = t->box + 6 * h;
+    for (int a = 0; a < 3; a++) {
+        bx[a] = INFINITY;
+        bx[3 + a] = -INFINITY;
+    }
+    for (int64_t p = start; p < start + count; p++)
+        for (int a = 0; a < 3; a++) {
+            double v = x[3 * t->ord[p] + a];
+            if (v < bx[a]) bx[a] = v;
+            if (v > bx[3 + a]) bx[3 + a] = v;
+        }
+    if (count <= n_leaf) {
+        t->axis[h] = -1;
+        return;
+    }
+    /* axis of the largest coordinate variance (two passes: mean, then the
+     * mean squared deviation); the first such axis on a tie */
+    int best = 0;
+    double bestvar = -1.0;
+    for (int a = 0; a < 3; a++) {
+        double m = 0.0;
+        for (int64_t p = start; p < start + count; p++) m += x[3 * t->ord[p] + a];
+        m /= (double)count;
+        double v = 0.0;
+        for (int64_t p = start; p < start + count; p++) {
+            double d = x[3 * t->ord[p] + a] - m;
+            v += d * d;
+        }
+        v /= (double)count;
+        if (v > bestvar) {
+            bestvar = v;
+            best = a;
+        }
+    }
+    t->axis[h] = best;
+    /* median split: the floor(n / 2) points with the smallest coordinate
+     * along that axis go left (point index breaks ties) */
+    for (int64_t k = 0; k < count; k++) {
+        tmp[k].v = x[3 * t->ord[start + k] + best];
+        tmp[k].i = t->ord[start + k];
+    }
+    qsort(tmp, (size_t)count, sizeof(keyed), keyed_cmp);
+    for (int64_t k = 0; k < count; k++) t->ord[start + k] = tmp[k].i;
+    int64_t nl = count / 2;
+    kd_node(t, x, 2 * h + 1, start, nl, n_leaf, tmp);
+    kd_node(t, x, 2 * h + 2, start + nl, count - nl, n_leaf, tmp);
+}
+
+static int kd_build(otree *t, const double *x, int64_t n, int n_leaf)
+{
+    memset(t, 0, sizeof(*t));
+    if (n < 1 || n_leaf < 1) return -1;
+    t->depth = kd_depth(n, n_leaf);
+    if (t->depth > 30) return -1;
+    t->nslots = ((int64_t)2 << t->depth) - 1;
+    t->start = (int64_t *)malloc(sizeof(int64_t) * (size_t)t->nslots);
+    t->count = (int64_t *)malloc(sizeof(int64_t) * (size_t)t->nslots);
+    t->axis = (int *)malloc(sizeof(int) * (size_t)t->nslots);
+    t->box = (double *)malloc(sizeof(double) * 6 * (size_t)t->nslots);
+    t->ord = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    keyed *tmp = (keyed *)malloc(sizeof(keyed) * (size_t)n);
+    for (int64_t h = 0; h < t->nslots; h++) {
+        t->start[h] = 0;
+        t->count[h] = -1;
+        t->axis[h] = -1;
+    }
+    for (int64_t i = 0; i < n; i++) t->ord[i] = i;
+    kd_node(t, x, 0, 0, n, n_leaf, tmp);
+    free(tmp);
+    return 0;
+}
+
+static void kd_free(otree *t)
+{
+    free(t->start);
+    free(t->count);
+    free(t->axis);
+    free(t->box);
+    free(t->ord);
+}
+
+/* Bounds of the squared separations of the pairs of two nodes, from their
+ * boxes: per axis the gap between the intervals and the largest distance
+ * between their ends.  Periodic axes take the smallest gap over the images
+ * b - L, b, b + L, and the largest distance is at most L / 2 after the wrap. */
+static void kd_dist_range(const octx *c, const double *A, const double *B, double *dmin2,
+                          double *dmax2)
+{
+    double lo2 = 0.0, hi2 = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double gap = INFINITY, far;
+        int ns = c->periodic ? 3 : 1;
+        for (int k = 0; k < ns; k++) {
+            double sh = (k == 0) ? 0.0 : (k == 1 ? c->L[a] : -c->L[a]);
+            double g = B[a] + sh - A[3 + a];
+            double g2 = A[a] - (B[3 + a] + sh);
+            if (g2 > g) g = g2;
+            if (g < 0.0) g = 0.0;
+            if (g < gap) gap = g;
+        }
+        far = B[3 + a] - A[a];
+        if (A[3 + a] - B[a] > far) far = A[3 + a] - B[a];
+        if (c->periodic && far > c->hL[a]) far = c->hL[a];
+        lo2 += gap * gap;
+        hi2 += far * far;
+    }
+    *dmin2 = lo2;
+    *dmax2 = hi2;
+}
+
+typedef struct {
+    int64_t a, b;
+} npair;
+
+/* Dual-tree count (Alg. 3) with an explicit stack of node pairs.  A pair
+ * whose separation range misses the range of interest is dropped; one that
+ * lies inside it, or a pair of leaves, has all its point pairs evaluated;
+ * otherwise the non-leaf nodes are split.  For an auto count only one of
+ * {a, b} and {b, a} is visited: a node paired with itself is split into
+ * (left, left), (left, right) and (right, right). */
+static void kd_dual(job *jb, const otree *t1, const otree *t2, double s2lo, double s2hi)
+{
+    const octx *c = jb->c;
+    int64_t cap = 1024, top = 0;
+    npair *st = (npair *)malloc(sizeof(npair) * (size_t)cap);
+    st[top++] = (npair){0, 0};
+    while (top > 0) {
+        npair q = st[--top];
+        const double *A = t1->box + 6 * q.a, *B = t2->box + 6 * q.b;
+        double dmin2, dmax2;
+        kd_dist_range(c, A, B, &dmin2, &dmax2);
+        /* bounds carry rounding: prune and accept with a relative margin */
+        if (dmin2 > s2hi * (1.0 + 1e-9) || dmax2 < s2lo * (1.0 - 1e-9)) continue;
+        int self = jb->is_auto && q.a == q.b;
+        int leaf1 = t1->axis[q.a] < 0, leaf2 = t2->axis[q.b] < 0;
+        int inside = dmin2 >= s2lo * (1.0 + 1e-9) && dmax2 < s2hi * (1.0 - 1e-9);
+        if (inside || (leaf1 && leaf2)) {
+            int64_t a0 = t1->start[q.a], a1 = a0 + t1->count[q.a];
+            int64_t b0 = t2->start[q.b], b1 = b0 + t2->count[q.b];
+            for (int64_t p = a0; p < a1; p++)
+                for (int64_t r = self ? p + 1 : b0; r < b1; r++)
+                    add_pair(jb, t1->ord[p], t2->ord[r]);
+            continue;
+        }
+        if (top + 4 > cap) {
+            cap *= 2;
+            st = (npair *)realloc(st, sizeof(npair) * (size_t)cap);
+        }
+        if (self) {
+            st[top++] = (npair){2 * q.a + 2, 2 * q.a + 2};
+            st[top++] = (npair){2 * q.a + 1, 2 * q.a + 2};
+            st[top++] = (npair){2 * q.a + 1, 2 * q.a + 1};
+        } else if (!leaf1 && !leaf2) {
+            st[top++] = (npair){2 * q.a + 2, 2 * q.b + 2};
+            st[top++] = (npair){2 * q.a + 2, 2 * q.b + 1};
+            st[top++] = (npair){2 * q.a + 1, 2 * q.b + 2};
+            st[top++] = (npair){2 * q.a + 1, 2 * q.b + 1};
+        } else if (leaf1) {
+            st[top++] = (npair){q.a, 2 * q.b + 2};
+            st[top++] = (npair){q.a, 2 * q.b + 1};
+        } else {
+            st[top++] = (npair){2 * q.a + 2, q.b};
+            st[top++] = (npair){2 * q.a + 1, q.b};
+        }
+    }
+    free(st);
+}
+
+/* Range of squared separations that can fall in a bin: [E_0, E_n) on s for
+ * s and (s, mu) bins; below sigma_max^2 + pi_max^2 for (sigma, pi) bins. */
+static void kd_s2_range(const octx *c, double *lo, double *hi)
+{
+    if (c->mode == MODE_SIGPI) {
+        *lo = 0.0;
+        *hi = c->Ea[c->na] + c->Eb[c->nb];
+    } else {
+        *lo = c->Ea[0];
+        *hi = c->Ea[c->na];
+    }
+}
+
+/*
+ * Pair counts through the k-d tree and the dual-tree traversal; the same
+ * arguments and results as oracle_count (one thread).  Returns 0, or -1 on
+ * invalid arguments.
+ */
+int oracle_count_kdtree(const double *x1, const double *w1, int64_t n1,
+                        const double *x2, const double *w2, int64_t n2,
+                        int periodic, const double *L, int mode, int los,
+                        int na, const double *ea, int nb, const double *eb,
+                        int n_leaf, int64_t *counts, double *wcounts)
+{
+    if (mode < 0 || mode > 2 || los < 0 || los > 1 || n_leaf < 1) return -1;
+    if (!check_edges(ea, na, 0)) return -1;
+    if (mode != MODE_S && !check_edges(eb, nb, mode == MODE_SMU)) return -1;
+    if (periodic && los == LOS_MID && mode != MODE_S) return -1;
+    if (n1 < 0 || n2 < 0) return -1;
+    int is_auto = (x2 == NULL);
+    if (is_auto) { x2 = x1; w2 = w1; n2 = n1; }
+    int weighted = (wcounts != NULL) && w1 && w2;
+
+    octx c;
+    memset(&c, 0, sizeof(c));
+    c.periodic = periodic;
+    c.mode = mode;
+    c.los = los;
+    c.na = na;
+    c.nb = (mode == MODE_S) ? 1 : nb;
+    c.nbins = na * c.nb;
+    for (int a = 0; a < 3; a++) {
+        c.L[a] = periodic ? L[a] : 0.0;
+        c.hL[a] = 0.5 * c.L[a];
+        if (periodic && !(L[a] > 0.0)) return -1;
+    }
+    c.Ea = (double *)malloc(sizeof(double) * (size_t)(na + 1));
+    c.Eb = (double *)malloc(sizeof(double) * (size_t)(c.nb + 1));
+    for (int k = 0; k <= na; k++) c.Ea[k] = ea[k] * ea[k];
+    if (mode == MODE_S) { c.Eb[0] = 0.0; c.Eb[1] = 1.0; }
+    else for (int k = 0; k <= nb; k++) c.Eb[k] = eb[k] * eb[k];
+
+    double *c1 = NULL, *c2 = NULL;
+    if (periodic) {
+        c1 = (double *)malloc(sizeof(double) * (size_t)(3 * (n1 > 0 ? n1 : 1)));
+        for (int64_t i = 0; i < n1; i++)
+            for (int a = 0; a < 3; a++) c1[3 * i + a] = canon(x1[3 * i + a], c.L[a]);
+        if (is_auto) c2 = c1;
+        else {
+            c2 = (double *)malloc(sizeof(double) * (size_t)(3 * (n2 > 0 ? n2 : 1)));
+            for (int64_t i = 0; i < n2; i++)
+                for (int a = 0; a < 3; a++) c2[3 * i + a] = canon(x2[3 * i + a], c.L[a]);
+        }
+        x1 = c1;
+        x2 = c2;
+    }
+
+    for (int b = 0; b < c.nbins; b++) counts[b] = 0;
+    job jb;
+    memset(&jb, 0, sizeof(jb));
+    jb.c = &c;
+    jb.x1 = x1; jb.w1 = w1; jb.x2 = x2; jb.w2 = w2;
+    jb.n1 = n1; jb.n2 = n2;
+    jb.is_auto = is_auto;
+    jb.cnt = counts;
+    double *fc = NULL;
+    if (weighted) {
+        for (int b = 0; b < c.nbins; b++) wcounts[b] = 0.0;
+        fc = (double *)calloc((size_t)(na > 0 ? c.nbins : 1), sizeof(double));
+        jb.wsum = wcounts;
+        jb.wcomp = fc;
+    }
+    if (n1 > 0 && n2 > 0) {
+        otree t1, t2;
+        kd_build(&t1, x1, n1, n_leaf);
+        if (is_auto) t2 = t1;
+        else kd_build(&t2, x2, n2, n_leaf);
+        double s2lo, s2hi;
+        kd_s2_range(&c, &s2lo, &s2hi);
+        kd_dual(&jb, &t1, &t2, s2lo, s2hi);
+        kd_free(&t1);
+        if (!is_auto) kd_free(&t2);
+    }
+    if (weighted)
+        for (int b = 0; b < c.nbins; b++) wcounts[b] += fc[b];
+    else if (wcounts)
+        for (int b = 0; b < c.nbins; b++) wcounts[b] = (double)counts[b];
+    free(fc);
+    if (c2 != c1) free(c2);
+    free(c1);
+    free(c.Ea); free(c.Eb);
+    return 0;
+}
+
+/*
+ * The k-d tree of Alg. 1 over n points (canonicalised first when periodic),
+ * in heap order.  Returns the depth (deepest level), or -1 on invalid
+ * arguments or when the tree has more than max_slots slots.  With nslots =
+ * 2^(depth + 1) - 1 <= max_slots the arrays receive: start[h], count[h]
+ * (-1: empty slot), axis[h] (-1: leaf or empty), box[6 h .. 6 h + 5] (lo,
+ * hi), and ord[n] (tree position -> point index).
+ */
+int oracle_kdtree(const double *x, int64_t n, int periodic, const double *L, int n_leaf,
+                  int64_t max_slots, int64_t *start, int64_t *count, int *axis, double *box,
+                  int64_t *ord)
+{
+    if (n < 1 || n_leaf < 1) return -1;
+    int d = kd_depth(n, n_leaf);
+    if (d > 30 || ((int64_t)2 << d) - 1 > max_slots) return -1;
+    double *cx = NULL;
+    if (periodic) {
+        for (int a = 0; a < 3; a++)
+            if (!(L[a] > 0.0)) return -1;
+        cx = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+        for (int64_t i = 0; i < n; i++)
+            for (int a = 0; a < 3; a++) cx[3 * i + a] = canon(x[3 * i + a], L[a]);
+        x = cx;
+    }
+    otree t;
+    if (kd_build(&t, x, n, n_leaf) != 0) { free(cx); return -1; }
+    memcpy(start, t.start, sizeof(int64_t) * (size_t)t.nslots);
+    memcpy(count, t.count, sizeof(int64_t) * (size_t)t.nslots);
+    memcpy(axis, t.axis, sizeof(int) * (size_t)t.nslots);
+    memcpy(box, t.box, sizeof(double) * 6 * (size_t)t.nslots);
+    memcpy(ord, t.ord, sizeof(int64_t) * (size_t)n);
+    kd_free(&t);
+    free(cx);
+    return d;
 }
