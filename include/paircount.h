@@ -122,6 +122,8 @@ typedef struct {
                                     weight a non-negative normal binary32 value or zero and
                                     the two grids' weight exponents spanning at most 12;
                                     truncation below 2^-34 relative), flushed in binary64 */
+    long long tree_pairs;        /* pc_count_tree: block pairs listed by the traversal */
+    float ms_traverse;           /* pc_count_tree: device-and-host time of the traversal */
 } pc_stats;
 
 typedef struct pc_grid pc_grid;  /* opaque; owned by the library */
@@ -221,6 +223,69 @@ typedef struct {
 pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, long long n, const pc_box *box,
                   const pc_bins *b, const pc_opts *base, void *stream, pc_opts *out,
                   pc_tune_trial *trials, int max_trials, int *n_trials);
+
+/* ---- k-d tree path (Sect. 2.2, Alg. 1; Sect. 3.1, Alg. 3) ---------------- */
+typedef struct pc_tree pc_tree;  /* opaque; owned by the library */
+
+/* Build the k-d tree of Alg. 1 on the GPU: the root holds all points; a node
+ * of more than n_leaf points is split at the median along the axis of its
+ * largest coordinate variance, the floor(n / 2) points of smallest coordinate
+ * going to the left child, so the tree is balanced and all nodes of a level
+ * hold the same share of the points to within one; every node keeps the
+ * minimum bounding box (AABB) of its points.  Points are stored in tree order
+ * (every node contiguous) as FP64 canonical coordinates and FP32 offsets from
+ * the centre of their block, the tree level whose nodes hold at most 256
+ * points.
+ *   xyz, w, w_is_f32, n   as for pc_build_grid; n >= 1
+ *   box                   periodic and L as for pc_build_grid (lo / hi are
+ *                         not used: the tree bounds its own points)
+ *   n_leaf                leaf capacity, 1..128
+ *   stream                cudaStream_t; returns once the tree is built
+ *   out                   the new tree; release it with pc_free_tree
+ * Errors: PC_EINVAL (NULL pointers, n < 1, bad n_leaf, bad box, non-finite
+ * coordinates), PC_EOVERFLOW (n >= 2^31, more than 2^28 heap slots),
+ * PC_ENOMEM, PC_ECUDA. */
+pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f32, long long n,
+                        const pc_box *box, int n_leaf, void *stream, pc_tree **out);
+
+/* Release a tree (NULL is ignored). */
+void pc_free_tree(pc_tree *t);
+
+/* Size of a tree (any output may be NULL): points, deepest level, block
+ * level, heap slots 2^(depth + 1) - 1. */
+pc_status pc_tree_info(const pc_tree *t, long long *n, int *depth, int *block_level,
+                       long long *slots);
+
+/* Copy the tree structure to HOST arrays (any may be NULL), heap order
+ * (children of slot h: 2h + 1, 2h + 2):
+ *   start, count  [slots] first tree position and points of each node;
+ *                 count -1 marks an empty slot (below a leaf)
+ *   axis          [slots] split axis, -1 for leaves and empty slots
+ *   box           [6 slots] lo x, y, z, hi x, y, z of each node's points
+ *   ord           [n] tree position -> input index */
+pc_status pc_tree_export(const pc_tree *t, long long *start, long long *count, int *axis,
+                         double *box, long long *ord);
+
+/* Pair counts through the dual-tree traversal (Alg. 3): auto counts of t1
+ * (t2 == NULL; unordered pairs) or cross counts of t1 x t2.  Node pairs
+ * whose boxes lie farther apart than the largest separation (or, for s and
+ * (s, mu) bins, all of whose pairs are closer than the first edge) are
+ * dropped; the rest descend to pairs of block nodes, whose points are
+ * evaluated by the same FP32 + binary64-rescue kernels as the grid path, so
+ * the results follow the same exact definition.  Periodic boxes: every node
+ * pair is taken under each periodic image of the second node.
+ *   counts, wcounts, st   as for pc_count_auto (st adds tree_pairs and
+ *                         ms_traverse; cell_size reports the largest block
+ *                         extent)
+ *   o                     prec, priv, rescue_capacity and grid_ctas_per_sm
+ *                         apply; ipt is 2
+ * Errors: PC_EINVAL (trees of different boxes or devices, missing weights,
+ * bad bins, a periodic separation of L/2 or more), PC_EUNSUPPORTED (plain
+ * FP64 asked for, or forced by a midpoint line of sight too close to the
+ * observer; block shards), PC_EOVERFLOW, PC_ENOMEM, PC_ECUDA. */
+pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const pc_bins *b,
+                        const pc_opts *o, void *stream, long long *counts, double *wcounts,
+                        pc_stats *st);
 
 /* Bounding box of n points (n x 3 binary64, host or device) -- the first of
  * the three grid-build passes of Sect. 2.1.  lo/hi are host arrays of 3. */

@@ -55,7 +55,8 @@ class pc_stats(ctypes.Structure):
                 ("rescue_inline", c_longlong), ("blocks", c_longlong),
                 ("cell_size", c_double), ("ms_total", c_float), ("ms_pairs", c_float),
                 ("ms_rescue", c_float), ("launches", c_int),
-                ("pruned", c_longlong), ("prec", c_int), ("wsum", c_int)]
+                ("pruned", c_longlong), ("prec", c_int), ("wsum", c_int),
+                ("tree_pairs", c_longlong), ("ms_traverse", c_float)]
 
 
 class pc_tune_trial(ctypes.Structure):
@@ -72,7 +73,8 @@ _lib = None
 
 EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc_count_cross",
            "pc_count_batch", "pc_aabb", "pc_suggest_cell_size", "pc_strerror", "pc_last_error",
-           "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune"]
+           "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune",
+           "pc_build_tree", "pc_free_tree", "pc_tree_info", "pc_tree_export", "pc_count_tree"]
 
 
 def library_path() -> str:
@@ -130,6 +132,19 @@ def lib():
                           POINTER(c_int)]
     L.pc_count_auto_noalloc.restype = c_int
     L.pc_count_auto_noalloc.argtypes = [vp, POINTER(pc_bins), POINTER(pc_opts), vp, vp, vp]
+    L.pc_build_tree.restype = c_int
+    L.pc_build_tree.argtypes = [vp, vp, c_int, c_longlong, POINTER(pc_box), c_int, vp,
+                                POINTER(vp)]
+    L.pc_free_tree.restype = None
+    L.pc_free_tree.argtypes = [vp]
+    L.pc_tree_info.restype = c_int
+    L.pc_tree_info.argtypes = [vp, POINTER(c_longlong), POINTER(c_int), POINTER(c_int),
+                               POINTER(c_longlong)]
+    L.pc_tree_export.restype = c_int
+    L.pc_tree_export.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.pc_count_tree.restype = c_int
+    L.pc_count_tree.argtypes = [vp, vp, POINTER(pc_bins), POINTER(pc_opts), vp, vp, vp,
+                                POINTER(pc_stats)]
     _lib = L
     return L
 
@@ -406,6 +421,95 @@ def pc_count_batch(grids, bins: Bins, opts: pc_opts | None = None, stream=None, 
     return counts, wcounts, st
 
 
+class Tree:
+    """Owner of a pc_tree handle (freed with the object)."""
+
+    def __init__(self, handle, n):
+        self.handle = handle
+        self.n = n
+
+    def info(self):
+        """(points, depth, block level, heap slots)."""
+        return pc_tree_info(self)
+
+    def free(self):
+        if self.handle:
+            lib().pc_free_tree(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _weights_arg(w, n):
+    if w is None:
+        return None, None, 0
+    t = _torch()
+    is32 = (getattr(w, "dtype", None) == np.float32 or
+            (t is not None and isinstance(w, t.Tensor) and w.dtype == t.float32))
+    pw, keep_w, nw = _ptr(w, np.float32 if is32 else np.float64)
+    if nw != n:
+        raise ValueError("weights and positions differ in length")
+    return pw, keep_w, 1 if is32 else 0
+
+
+def pc_build_tree(xyz, w=None, *, box: pc_box, n_leaf: int = 32, stream=None) -> Tree:
+    """k-d tree of Alg. 1 built on the GPU (see paircount.h)."""
+    px, keep_x, n = _ptr(xyz, np.float64, 3)
+    pw, keep_w, w_is_f32 = _weights_arg(w, n)
+    out = c_void_p()
+    _check(lib().pc_build_tree(px, pw, w_is_f32, n, ctypes.byref(box), int(n_leaf),
+                               _stream_handle(stream), ctypes.byref(out)), "pc_build_tree")
+    del keep_x, keep_w
+    return Tree(out, n)
+
+
+def pc_free_tree(t: Tree):
+    t.free()
+
+
+def pc_tree_info(t: Tree):
+    n = c_longlong()
+    d = c_int()
+    b = c_int()
+    s = c_longlong()
+    _check(lib().pc_tree_info(t.handle, ctypes.byref(n), ctypes.byref(d), ctypes.byref(b),
+                              ctypes.byref(s)), "pc_tree_info")
+    return n.value, d.value, b.value, s.value
+
+
+def pc_tree_export(t: Tree) -> dict:
+    """Tree structure in heap order: start, count (-1: empty slot), axis
+    (-1: leaf or empty), box [slots, 6] and ord (tree position -> index)."""
+    n, depth, blevel, slots = pc_tree_info(t)
+    start = np.zeros(slots, dtype=np.int64)
+    count = np.zeros(slots, dtype=np.int64)
+    axis = np.zeros(slots, dtype=np.int32)
+    bx = np.zeros((slots, 6), dtype=np.float64)
+    order = np.zeros(n, dtype=np.int64)
+    _check(lib().pc_tree_export(t.handle, start.ctypes.data, count.ctypes.data, axis.ctypes.data,
+                                bx.ctypes.data, order.ctypes.data), "pc_tree_export")
+    return {"depth": depth, "block_level": blevel, "start": start, "count": count,
+            "axis": axis, "box": bx, "ord": order}
+
+
+def pc_count_tree(t1: Tree, t2, bins: Bins, opts: pc_opts | None = None, stream=None,
+                  counts=None, wcounts=None, weighted=False):
+    """Auto (t2 None) or cross counts through the dual-tree traversal."""
+    counts, wcounts, pc_, pw_, keep = _outputs(counts, wcounts, 1, bins.nbins, weighted)
+    st = pc_stats()
+    _check(lib().pc_count_tree(t1.handle, t2.handle if t2 is not None else None,
+                               ctypes.byref(bins.s),
+                               ctypes.byref(opts) if opts is not None else None,
+                               _stream_handle(stream), pc_, pw_, ctypes.byref(st)),
+           "pc_count_tree")
+    del keep
+    return counts, wcounts, st
+
+
 def pc_aabb(xyz, stream=None):
     px, keep, n = _ptr(xyz, np.float64, 3)
     lo = (c_double * 3)()
@@ -460,6 +564,33 @@ def count(x1, x2=None, *, w1=None, w2=None, box=None, periodic=False, mode="s", 
                 g2.free()
     finally:
         g1.free()
+    if return_stats:
+        return c, wc, st
+    return c, wc
+
+
+def count_tree(x1, x2=None, *, w1=None, w2=None, box=None, periodic=False, mode="s", los="z",
+               edges_a, edges_b=None, n_leaf=32, priv=-1, rescue_capacity=0, weighted=None,
+               stream=None, return_stats=False):
+    """Auto (x2 None) or cross pair counts through the k-d tree path (build
+    the trees, count, free); same results as ``count``."""
+    bins = Bins(mode, los, edges_a, edges_b)
+    if weighted is None:
+        weighted = w1 is not None
+    opts = make_opts("f32", 0.0, 2, priv, rescue_capacity)
+    b = make_box(box, True) if periodic else make_box(None, False)
+    t1 = pc_build_tree(x1, w1 if weighted else None, box=b, n_leaf=n_leaf, stream=stream)
+    try:
+        if x2 is None:
+            c, wc, st = pc_count_tree(t1, None, bins, opts, stream, weighted=weighted)
+        else:
+            t2 = pc_build_tree(x2, w2 if weighted else None, box=b, n_leaf=n_leaf, stream=stream)
+            try:
+                c, wc, st = pc_count_tree(t1, t2, bins, opts, stream, weighted=weighted)
+            finally:
+                t2.free()
+    finally:
+        t1.free()
     if return_stats:
         return c, wc, st
     return c, wc

@@ -244,7 +244,8 @@ static void build_stencil(const Geom &g, double r, bool half, std::vector<int4> 
 }
 
 static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo,
-                           const double *pts_hi, double rmin, bool half, Plan &P) {
+                           const double *pts_hi, double rmin, bool half, Plan &P,
+                           bool with_stencil = true) {
     if (!b) return fail(PC_EINVAL, "bins: NULL");
     if (b->mode < 0 || b->mode > 2) return fail(PC_EINVAL, "bins: unknown mode");
     if (b->los < 0 || b->los > 1) return fail(PC_EINVAL, "bins: unknown line of sight");
@@ -471,14 +472,15 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
         }
     }
     // ---- stencil -------------------------------------------------------------
-    int kmax[3];
-    build_stencil(g, P.rcut, half, P.stencil, kmax);
+    int kmax[3] = {0, 0, 0};
+    P.stencil.clear();
+    if (with_stencil) build_stencil(g, P.rcut, half, P.stencil, kmax);
     if (g.periodic) {
         for (int a = 0; a < 3; ++a) {
             if (!(P.rcut < 0.5 * g.L[a]))
                 return fail(PC_EINVAL,
                             "bins: the largest separation must stay below half the periodic box");
-            if (2 * kmax[a] + 1 > g.ng[a])
+            if (with_stencil && 2 * kmax[a] + 1 > g.ng[a])
                 return fail(PC_EINVAL,
                             "grid: cells too large for this separation in a periodic box "
                             "(neighbour cells would alias); rebuild with a smaller cell_size");
@@ -515,7 +517,14 @@ struct CountJob {
     std::vector<TaskDev> tasks;
     int nhist;
     bool is_auto;
-    const pc_grid *g0;
+    const pc_grid *g0 = nullptr;
+    // geometry of the count (the first grid's, or the trees')
+    Geom geom;
+    int device = 0;
+    int ncell = 0;               // cells per grid, or i-blocks of a tree count
+    double plo[3] = {0, 0, 0}, phi[3] = {0, 0, 0};   // first grid's point bounds
+    double cell_size = 0.0;
+    bool tree = false;
     // bounds of the points of every grid involved, and a lower bound of |x|
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     double rmin = 0.0;
@@ -537,6 +546,19 @@ static void job_add_wint(CountJob &J, const pc_grid *gi, const pc_grid *gj) {
 static double grid_rmin(const pc_grid *g) {
     if (g->g.periodic || !(g->r2min > 0.0)) return 0.0;
     return sqrt(g->r2min) * (1.0 - 1e-12);
+}
+
+// The job's geometry from its first grid.
+static void job_set_grid(CountJob &J, const pc_grid *g) {
+    J.g0 = g;
+    J.geom = g->g;
+    J.device = g->device;
+    J.ncell = g->ncell;
+    for (int a = 0; a < 3; ++a) {
+        J.plo[a] = g->pts_lo[a];
+        J.phi[a] = g->pts_hi[a];
+    }
+    J.cell_size = g->cell_size;
 }
 
 // Fold grid g into the job's point bounds (the first grid initialises them).
@@ -582,8 +604,7 @@ static pc_status setup_count(const CountJob &J, const pc_bins *b, const pc_opts 
     if (opt) S.o = *opt;
     if (S.o.shard_count > 1 && (S.o.shard_index < 0 || S.o.shard_index >= S.o.shard_count))
         return fail(PC_EINVAL, "opts: shard_index must lie in [0, shard_count)");
-    const pc_grid *g0 = J.g0;
-    pc_status s = make_plan(b, g0->g, J.lo, J.hi, J.rmin, J.is_auto, S.P);
+    pc_status s = make_plan(b, J.geom, J.lo, J.hi, J.rmin, J.is_auto, S.P, !J.tree);
     if (s != PC_OK) return s;
     S.weighted = weighted;
     S.prec = S.o.prec;
@@ -591,9 +612,9 @@ static pc_status setup_count(const CountJob &J, const pc_bins *b, const pc_opts 
     S.ipt = (S.o.ipt == 4) ? 4 : 2;
     if (S.prec == PC_PREC_F64) S.ipt = 1;
     S.bi = NT * S.ipt;
-    S.dev = g0->device;
+    S.dev = J.device;
     S.ntasks = (int)J.tasks.size();
-    S.ncell = g0->ncell;
+    S.ncell = J.ncell;
     long long npts = 0;
     for (auto &t : J.tasks) npts += t.gi.n;
     S.nblk_cap = (size_t)S.ntasks * S.ncell + (size_t)(npts / S.bi) + 16;
@@ -605,7 +626,7 @@ static pc_status setup_count(const CountJob &J, const pc_bins *b, const pc_opts 
         if (S.o.rescue_capacity > 0) S.qcap = (unsigned long long)S.o.rescue_capacity;
         else if (S.o.rescue_capacity == 0) {
             double vol = 1.0;
-            for (int a = 0; a < 3; ++a) vol *= std::max(g0->pts_hi[a] - g0->pts_lo[a], 1e-9);
+            for (int a = 0; a < 3; ++a) vol *= std::max(J.phi[a] - J.plo[a], 1e-9);
             double vs = 4.0 / 3.0 * M_PI * S.P.reff * S.P.reff * S.P.reff;
             double pairs = 0.0;
             for (auto &t : J.tasks)
@@ -674,11 +695,12 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     const Plan &P = S.P;
     memset(&p, 0, sizeof(p));
     p.groups = 1;
+    p.tree = J.tree ? 1 : 0;
     p.tasks = B.tasks;
     p.blocks = B.blocks;
     p.nblocks = B.sc + 1;
     p.work_counter = B.sc;
-    p.g = J.g0->g;
+    p.g = J.geom;
     p.stencil = B.stencil;
     p.nrows = (int)P.stencil.size();
     p.mode = P.mode;
@@ -753,7 +775,7 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     // SM: run CTAs of four independent thread groups sharing one histogram
     // (single-histogram jobs, floor bins, binary64 or no weights, 2 i-points)
     if (S.prec == PC_PREC_F32_RESCUE && p.smem_hist_ok && p.lin && !p.wint && !p.priv &&
-        J.nhist == 1 && S.ipt == 2 && per_sm <= 2) {
+        J.nhist == 1 && S.ipt == 2 && per_sm <= 2 && !p.tree) {
         p.groups = 4;
         const size_t smem4 = pairs_f32_smem(p, S.ipt);
         const int per4 = (smem4 + 8192 <= (size_t)smem_optin) ? pairs_f32_ctas_per_sm(p, S.ipt, smem4) : 0;
@@ -775,13 +797,17 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
 // replays): clear, block list, pair kernel, rescue kernel.
 static pc_status enqueue_count(const CountSetup &S, const DevBufs &B, const PairParams &p, int grid,
                                size_t smem, cudaStream_t st, cudaEvent_t ev_pairs,
-                               cudaEvent_t ev_rescue, cudaEvent_t ev_done) {
+                               cudaEvent_t ev_rescue, cudaEvent_t ev_done,
+                               const pc_tree *blk_tree = nullptr) {
     PC_CUDA(cudaMemsetAsync(B.hist, 0, sizeof(unsigned long long) * S.hist_n, st));
     if (S.weighted) PC_CUDA(cudaMemsetAsync(B.whist, 0, sizeof(double) * S.hist_n, st));
     PC_CUDA(cudaMemsetAsync(B.ctr, 0, sizeof(unsigned long long) * 4, st));
     PC_CUDA(cudaMemsetAsync(B.sc, 0, sizeof(int) * 4, st));
-    PC_CUDA(make_blocks_into(B.tasks, S.ntasks, S.ncell, S.bi, B.blocks, B.sc + 1, B.cnt, B.off,
-                             B.tot, st));
+    if (blk_tree)   // tree count: one block per i-block node
+        PC_CUDA(tree_blocks(blk_tree, B.blocks, B.sc + 1, st));
+    else
+        PC_CUDA(make_blocks_into(B.tasks, S.ntasks, S.ncell, S.bi, B.blocks, B.sc + 1, B.cnt,
+                                 B.off, B.tot, st));
     if (ev_pairs) PC_CUDA(cudaEventRecord(ev_pairs, st));
     cudaError_t e = (S.prec == PC_PREC_F64) ? launch_pairs_f64(p, grid, smem, st)
                                             : launch_pairs_f32(p, S.ipt, grid, smem, st);
@@ -801,7 +827,7 @@ static void copy_out(void *dst, const void *src, size_t bytes, cudaStream_t st, 
     e = cudaMemcpyAsync(dst, src, bytes, k, st);
 }
 
-static void fill_stats(pc_stats *stats, const CountSetup &S, const pc_grid *g0,
+static void fill_stats(pc_stats *stats, const CountSetup &S, double cell_size,
                        const unsigned long long hc[4], int hblk, float ms_total, float ms_pairs,
                        float ms_rescue, long long launches) {
     if (!stats) return;
@@ -813,7 +839,7 @@ static void fill_stats(pc_stats *stats, const CountSetup &S, const pc_grid *g0,
     stats->wsum = S.wsum;
     stats->rescued = (long long)std::min<unsigned long long>(hc[2], S.qcap) + (long long)hc[1];
     stats->blocks = hblk;
-    stats->cell_size = g0->cell_size;
+    stats->cell_size = cell_size;
     stats->ms_total = ms_total;
     stats->ms_pairs = ms_pairs;
     stats->ms_rescue = ms_rescue;
@@ -869,7 +895,7 @@ static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *o
         PC_CUDA(cudaEventRecord(ev.e[4], st));
     }
     PC_CUDA(cudaStreamSynchronize(st));
-    fill_stats(stats, S, J.g0, hc, hblk, ev.ms(0, 4), ev.ms(1, 2), ev.ms(2, 3),
+    fill_stats(stats, S, J.cell_size, hc, hblk, ev.ms(0, 4), ev.ms(1, 2), ev.ms(2, 3),
                launch_count() - launches0);
     return PC_OK;
 }
@@ -945,13 +971,13 @@ static pc_status run_count_graph(const CountJob &J, const std::vector<const pc_g
     if (b->mode != PC_BIN_S) eb.assign(b->edges_b, b->edges_b + std::max(b->n_b, 0) + 1);
     GraphEntry *G = nullptr;
     for (auto &c : graph_cache())
-        if (c->dev == J.g0->device && c->grids == grids && c->mode == b->mode && c->los == b->los &&
+        if (c->dev == J.device && c->grids == grids && c->mode == b->mode && c->los == b->los &&
             c->ea == ea && c->eb == eb && same_opts(c->o, o) && c->weighted == weighted)
             G = c.get();
     const long long launches0 = launch_count();
     if (!G) {
         std::unique_ptr<GraphEntry> N(new GraphEntry());
-        N->dev = J.g0->device;
+        N->dev = J.device;
         N->grids = grids;
         N->mode = b->mode;
         N->los = b->los;
@@ -1035,7 +1061,7 @@ static pc_status run_count_graph(const CountJob &J, const std::vector<const pc_g
     }
     if (e != cudaSuccess) return cuda_fail(e, "result copy");
     unsigned long long hc[4] = {G->h_ctr[0], G->h_ctr[1], G->h_ctr[2], G->h_ctr[3]};
-    fill_stats(stats, G->S, J.g0, hc, *G->h_blocks, ev.ms(0, 4), 0.f, 0.f,
+    fill_stats(stats, G->S, J.cell_size, hc, *G->h_blocks, ev.ms(0, 4), 0.f, 0.f,
                launch_count() - launches0);
     return PC_OK;
 }
@@ -1077,7 +1103,7 @@ extern "C" pc_status pc_count_auto(const pc_grid *g, const pc_bins *b, const pc_
     J.tasks.push_back(task_of(g, g, 0, 1));
     J.nhist = 1;
     J.is_auto = true;
-    J.g0 = g;
+    job_set_grid(J, g);
     job_add_bounds(J, g, true);
     job_add_wint(J, g, g);
     return run_count(J, b, o, (cudaStream_t)stream, counts, wcounts, st);
@@ -1097,7 +1123,7 @@ extern "C" pc_status pc_count_cross(const pc_grid *g1, const pc_grid *g2, const 
     J.tasks.push_back(task_of(g1, g2, 0, 0));
     J.nhist = 1;
     J.is_auto = false;
-    J.g0 = g1;
+    job_set_grid(J, g1);
     job_add_bounds(J, g1, true);
     job_add_bounds(J, g2, false);
     job_add_wint(J, g1, g2);
@@ -1123,12 +1149,138 @@ extern "C" pc_status pc_count_batch(const pc_grid *const *gs, int m, const pc_bi
     }
     J.nhist = m;
     J.is_auto = true;
-    J.g0 = gs[0];
+    job_set_grid(J, gs[0]);
     if (o && o->use_graph) {
         std::vector<const pc_grid *> grids(gs, gs + m);
         return run_count_graph(J, grids, b, o, (cudaStream_t)stream, counts, wcounts, st);
     }
     return run_count(J, b, o, (cudaStream_t)stream, counts, wcounts, st);
+}
+
+// ---------------------------------------------------------------------------
+// k-d tree counts (Alg. 3): the traversal lists the block pairs, then the
+// same pair and rescue kernels as the grid path run over them
+// ---------------------------------------------------------------------------
+static bool same_tree_geometry(const pc_tree *a, const pc_tree *b) {
+    if (a->g.periodic != b->g.periodic || a->device != b->device) return false;
+    for (int k = 0; k < 3; ++k)
+        if (a->g.L[k] != b->g.L[k]) return false;
+    return true;
+}
+
+static double tree_rmin(const pc_tree *t) {
+    if (t->g.periodic || !(t->r2min > 0.0)) return 0.0;
+    return sqrt(t->r2min) * (1.0 - 1e-12);
+}
+
+extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const pc_bins *b,
+                                   const pc_opts *opt, void *stream, long long *counts,
+                                   double *wcounts, pc_stats *stats) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!t1) return fail(PC_EINVAL, "pc_count_tree: tree is NULL");
+    if (!counts && !wcounts) return fail(PC_EINVAL, "pc_count_tree: no output buffer");
+    const bool is_auto = (t2 == nullptr);
+    const pc_tree *tj = is_auto ? t1 : t2;
+    if (!same_tree_geometry(t1, tj))
+        return fail(PC_EINVAL, "pc_count_tree: trees differ in box or device");
+    if (wcounts && !(t1->weighted && tj->weighted))
+        return fail(PC_EINVAL, "pc_count_tree: weighted counts need weights on every tree");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    CountJob J;
+    TaskDev T;
+    T.gi = GridDev{t1->rel, nullptr, t1->xw, nullptr, t1->n};
+    T.gj = GridDev{tj->rel, nullptr, tj->xw, nullptr, tj->n};
+    T.hist = 0;
+    T.is_auto = is_auto ? 1 : 0;
+    T.wscale = (t1->wint && tj->wint) ? ldexp(1.0, t1->wemax + tj->wemax - 300) : 0.0;
+    J.tasks.push_back(T);
+    J.nhist = 1;
+    J.is_auto = is_auto;
+    J.tree = true;
+    // the error bands take the largest block extent where the grid takes
+    // the cell side (point offsets from their block centre are at most half
+    // of it)
+    J.geom = t1->g;
+    const double cb = std::max(t1->bext, tj->bext);
+    for (int a = 0; a < 3; ++a) {
+        J.geom.c[a] = std::max(cb, 1e-300);
+        J.geom.c32[a] = (float)J.geom.c[a];
+        J.lo[a] = std::min(t1->pts_lo[a], tj->pts_lo[a]);
+        J.hi[a] = std::max(t1->pts_hi[a], tj->pts_hi[a]);
+        J.plo[a] = J.lo[a];
+        J.phi[a] = J.hi[a];
+    }
+    J.rmin = std::min(tree_rmin(t1), tree_rmin(tj));
+    J.device = t1->device;
+    J.ncell = 1 << t1->blevel;
+    J.cell_size = cb;
+    if (!t1->wint || !tj->wint ||
+        (t1->wemax - t1->wemin) + (tj->wemax - tj->wemin) > WINT_MAX_SPAN)
+        J.wint_ok = false;
+
+    pc_opts o;
+    memset(&o, 0, sizeof(o));
+    o.priv = -1;
+    if (opt) o = *opt;
+    o.ipt = 2;
+    if (o.shard_count > 1)
+        return fail(PC_EUNSUPPORTED, "pc_count_tree: block shards are a grid-path option");
+    CountSetup S;
+    pc_status s = setup_count(J, b, &o, wcounts != nullptr, S);
+    if (s != PC_OK) return s;
+    if (S.prec != PC_PREC_F32_RESCUE)
+        return fail(PC_EUNSUPPORTED,
+                    "pc_count_tree: runs the FP32 + rescue kernel only (the plain FP64 path, "
+                    "asked for or forced by a midpoint line of sight close to the observer, "
+                    "is a grid-path option)");
+    DevBufs B;
+    s = ensure_bufs(workspace(S.dev), S, B);
+    if (s != PC_OK) return s;
+    PairParams p;
+    int grid = 0;
+    size_t smem = 0;
+    s = make_params(J, S, B, p, grid, smem);
+    if (s != PC_OK) return s;
+    S.wsum = p.wint ? 2 : (S.weighted ? 1 : 0);
+    Events ev(stats != nullptr);
+    const long long launches0 = launch_count();
+    if (ev.on) PC_CUDA(cudaEventRecord(ev.e[0], st));
+    // node pairs closer than the candidate cut, farther than the smallest
+    // s edge (the box bounds are exact up to rounding: relative margins)
+    const double r2hi = (double)S.P.r2cut * (1.0 + 1e-9);
+    const double r2lo = (S.P.mode != PC_BIN_SIGPI) ? S.P.Ea[0] * (1.0 - 1e-9) : 0.0;
+    TreeLists TL;
+    s = tree_traverse(t1, tj, is_auto, r2hi, r2lo, st, TL);
+    if (s != PC_OK) return s;
+    p.tseg = TL.seg;
+    p.tseg_off = TL.seg_off;
+    p.tblk_j = tj->brng;
+    p.tcen_i = t1->bcen;
+    p.tcen_j = tj->bcen;
+    s = upload_tables(J, S, B, st);
+    if (s != PC_OK) return s;
+    s = enqueue_count(S, B, p, grid, smem, st, ev.e[1], ev.e[2], ev.e[3], t1);
+    if (s != PC_OK) return s;
+    cudaError_t e = cudaSuccess;
+    copy_out(counts, B.hist, sizeof(long long) * S.hist_n, st, e);
+    copy_out(wcounts, B.whist, sizeof(double) * S.hist_n, st, e);
+    if (e != cudaSuccess) return cuda_fail(e, "result copy");
+    unsigned long long hc[4] = {0, 0, 0, 0};
+    int hblk = 0;
+    if (ev.on) {
+        PC_CUDA(cudaMemcpyAsync(hc, B.ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        PC_CUDA(cudaMemcpyAsync(&hblk, B.sc + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PC_CUDA(cudaEventRecord(ev.e[4], st));
+    }
+    PC_CUDA(cudaStreamSynchronize(st));
+    fill_stats(stats, S, J.cell_size, hc, hblk, ev.ms(0, 4), ev.ms(1, 2), ev.ms(2, 3),
+               launch_count() - launches0);
+    if (stats) {
+        stats->tree_pairs = TL.npairs;
+        stats->ms_traverse = ev.ms(0, 1);
+    }
+    return PC_OK;
 }
 
 // Cost model of Appendix B.1 (cost = a N_pair + b N_node), specialised to the

@@ -182,6 +182,24 @@ __global__ void k_wstats(const void *__restrict__ w, int w_is_f32, int n, int *o
     }
 }
 
+pc_status weight_stats(const void *w, int w_is_f32, int n, cudaStream_t st, int r[3]) {
+    int init[3] = {0, -1, 1000};
+    int *ws = nullptr;
+    cudaError_t e = cudaMallocAsync(&ws, sizeof(init), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n > 0) {
+        int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+        k_wstats<<<blocks, 256, 0, st>>>(w, w_is_f32, n, ws);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r, ws, sizeof(int) * 3, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (ws) cudaFreeAsync(ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "weight statistics");
+    return PC_OK;
+}
+
 // Packed integer weight (stored in the w lane of the FP32 point record):
 // bits 0-23 the binary32 significand M with its leading one (w = M 2^(e-150)),
 // bits 24-31 the shift emax - e.  Zero weights pack to 0.
@@ -598,23 +616,12 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     // non-negative normal binary32 value (or zero); exponent range recorded
     g->wint = 0;
     if (dw && n > 0) {
-        int init[3] = {0, -1, 1000}, res[3];
-        int *ws = nullptr;
-        cudaError_t e1 = cudaMallocAsync(&ws, sizeof(init), st);
-        if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(ws, init, sizeof(init), cudaMemcpyHostToDevice, st);
-        if (e1 == cudaSuccess) {
-            int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
-            k_wstats<<<blocks, 256, 0, st>>>(dw, w_is_f32, (int)n, ws);
-            note_launch();
-            e1 = cudaGetLastError();
-        }
-        if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(res, ws, sizeof(res), cudaMemcpyDeviceToHost, st);
-        if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
-        if (ws) cudaFreeAsync(ws, st);
-        if (e1 != cudaSuccess) {
+        int res[3];
+        pc_status ws = weight_stats(dw, w_is_f32, (int)n, st, res);
+        if (ws != PC_OK) {
             cleanup();
             delete g;
-            return cuda_fail(e1, "pc_build_grid: weight statistics");
+            return ws;
         }
         if (res[0] == 0) {
             g->wint = 1;

@@ -63,6 +63,7 @@ __host__ __device__ inline SmemLayout smem_layout(const PairParams &p, bool f64)
     o = align_up(o + (size_t)2 * tj * (f64 ? sizeof(double4_32a) : 3 * sizeof(float)), 16);
     L.meta = o;
     if (f64) o = align_up(o + (size_t)2 * tj * sizeof(int2), 16);
+    else if (p.tree) o = align_up(o + (size_t)MAXSEG * sizeof(float4), 16);   // segment offsets
     L.tw = o;
     if (p.weighted && !f64) o = align_up(o + (size_t)2 * tj * sizeof(double), 16);
     L.q = o;
@@ -981,9 +982,12 @@ __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, T
 // W: 0 unweighted, 1 binary64 weighted sums, 2 integer weight products.
 // G: independent groups of NT threads per CTA that share the histograms (a
 // large histogram then keeps G x 4 warps per SM busy instead of 4).
-template <int MODE, int LOS, int W, int RI, bool LIN, int G = 1>
+// TREE: blocks are k-d tree nodes and their j-segments come from the list of
+// the dual-tree traversal instead of the stencil rows.
+template <int MODE, int LOS, int W, int RI, bool LIN, int G = 1, bool TREE = false>
 __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     k_pairs_f32(const __grid_constant__ PairParams p) {
+    static_assert(!TREE || G == 1, "the tree variant runs one thread group per CTA");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ CtaShared cs_g[G];
     __shared__ int s_tmp_g[G][8];
@@ -1009,6 +1013,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     double *s_tw = (double *)(gsm + Ly.tw);
     unsigned *s_twm = (unsigned *)(gsm + Ly.tw);   // packed weights share the storage
     uint3 *s_q = (uint3 *)(gsm + Ly.q);
+    float4 *s_soff = (float4 *)(gsm + Ly.meta);   // tree: offset of each segment's block centre
 
     const int tid = gtid();
     for (int k = threadIdx.x; k < p.lut_total; k += NT * G) s_lut[k] = p.lut[k];
@@ -1168,22 +1173,52 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
             gsync<G>();
         }
 
-        // ---- phase B: stencil rows, in chunks --------------------------------
-        const int cell_end = T.gi.cell_start[B.cell + 1];
-        for (int r0 = 0; r0 < p.nrows; r0 += ROWCHUNK) {
-            const int r1 = min(r0 + ROWCHUNK, p.nrows);
-            if (tid == 0) {
-                int ns = 0;
-                if (T.is_auto && r0 == 0 && cell_end > B.start + B.count) {
-                    // rest of the own cell after this block (j > i for all)
-                    s_seg[0] = make_int4(B.start + B.count, cell_end - B.start - B.count, 0, 13);
-                    ns = 1;
+        // ---- phase B: j-segments, in chunks ---------------------------------
+        // grid: the stencil rows, ROWCHUNK at a time; tree: the i-block's list
+        // of (j-block, image) pairs, MAXSEG at a time
+        const int ts0 = TREE ? p.tseg_off[B.cell] : 0;
+        const int ts1 = TREE ? p.tseg_off[B.cell + 1] : 0;
+        const int nchunk = TREE ? (ts1 - ts0 + MAXSEG - 1) / MAXSEG
+                                : (p.nrows + ROWCHUNK - 1) / ROWCHUNK;
+        for (int ch = 0; ch < nchunk; ++ch) {
+            if constexpr (TREE) {
+                // segment k: the j-block's points, staged relative to the
+                // i-block's centre through the offset of the two centres
+                const int c0 = ts0 + ch * MAXSEG;
+                const int ns = min(MAXSEG, ts1 - c0);
+                const double *ci = p.tcen_i + 3 * (size_t)B.cell;
+                for (int k = tid; k < ns; k += NT) {
+                    const int2 e = p.tseg[c0 + k];
+                    const int2 r = p.tblk_j[e.x];
+                    const double *cj = p.tcen_j + 3 * (size_t)e.x;
+                    const double sx = (double)(e.y / 9 - 1), sy = (double)((e.y / 3) % 3 - 1),
+                                 sz = (double)(e.y % 3 - 1);
+                    s_soff[k] = make_float4(
+                        __double2float_rn(__dsub_rn(__dadd_rn(cj[0], __dmul_rn(sx, p.g.L[0])), ci[0])),
+                        __double2float_rn(__dsub_rn(__dadd_rn(cj[1], __dmul_rn(sy, p.g.L[1])), ci[1])),
+                        __double2float_rn(__dsub_rn(__dadd_rn(cj[2], __dmul_rn(sz, p.g.L[2])), ci[2])),
+                        0.f);
+                    s_seg[k] = make_int4(r.x, r.y, k, e.y);
                 }
-                cs.nseg = ns;
+                if (tid == 0) cs.nseg = ns;
+                gsync<G>();
+            } else {
+                const int r0 = ch * ROWCHUNK;
+                const int r1 = min(r0 + ROWCHUNK, p.nrows);
+                if (tid == 0) {
+                    int ns = 0;
+                    const int cell_end = T.gi.cell_start[B.cell + 1];
+                    if (T.is_auto && r0 == 0 && cell_end > B.start + B.count) {
+                        // rest of the own cell after this block (j > i for all)
+                        s_seg[0] = make_int4(B.start + B.count, cell_end - B.start - B.count, 0, 13);
+                        ns = 1;
+                    }
+                    cs.nseg = ns;
+                }
+                gsync<G>();
+                build_segments(p, T.gj, ax, ay, az, r0, r1, s_seg, &cs.nseg);
+                gsync<G>();
             }
-            gsync<G>();
-            build_segments(p, T.gj, ax, ay, az, r0, r1, s_seg, &cs.nseg);
-            gsync<G>();
             const int nseg = cs.nseg;
             gsync<G>();                 // every thread has read nseg before it changes
             if (nseg == 0) continue;
@@ -1214,7 +1249,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
                         int4 sg = s_seg[seg_find(s_seg, nseg, f)];
                         int pj = sg.x + (f - sg.y);
                         rq[s] = T.gj.rel[pj];
-                        rcx[s] = T.gj.cx[pj];
+                        if constexpr (!TREE) rcx[s] = T.gj.cx[pj];
                         rmeta[s] = sg.z;
                         rimg[s] = sg.w;
                         if (W == 1) rw[s] = T.gj.xw[pj].w;
@@ -1230,13 +1265,20 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
                     float x = 1.0e18f, y = 1.0e18f, z = 1.0e18f;   // pad slot
                     double wv = 0.0;
                     if (rv[s]) {
-                        int wrapx = rimg[s] / 9 - 1;
-                        int dxc = rcx[s] - ax + wrapx * nx;
-                        int dyc = (int)(short)(rmeta[s] & 0xFFFF);
-                        int dzc = rmeta[s] >> 16;
-                        x = fmaf((float)dxc, c32x, rq[s].x);
-                        y = fmaf((float)dyc, c32y, rq[s].y);
-                        z = fmaf((float)dzc, c32z, rq[s].z);
+                        if constexpr (TREE) {
+                            const float4 o = s_soff[rmeta[s]];
+                            x = o.x + rq[s].x;
+                            y = o.y + rq[s].y;
+                            z = o.z + rq[s].z;
+                        } else {
+                            int wrapx = rimg[s] / 9 - 1;
+                            int dxc = rcx[s] - ax + wrapx * nx;
+                            int dyc = (int)(short)(rmeta[s] & 0xFFFF);
+                            int dzc = rmeta[s] >> 16;
+                            x = fmaf((float)dxc, c32x, rq[s].x);
+                            y = fmaf((float)dyc, c32y, rq[s].y);
+                            z = fmaf((float)dzc, c32z, rq[s].z);
+                        }
                         wv = rw[s];
                     }
                     if (slot < len) {
@@ -1468,9 +1510,23 @@ PairKernel<MODE, LOS> pick_f32(const PairParams &p, int ipt) {
     return lin ? k_pairs_f32<MODE, LOS, 0, 2, LINOK> : k_pairs_f32<MODE, LOS, 0, 2, false>;
 }
 
+// Tree variant (2 i-points per thread, one thread group).
 template <int MODE, int LOS>
-cudaError_t launch_mode_f32(const PairParams &p, int ipt, int grid, size_t smem, cudaStream_t st) {
-    PairKernel<MODE, LOS> k = pick_f32<MODE, LOS>(p, ipt);
+PairKernel<MODE, LOS> pick_f32_tree(const PairParams &p) {
+    constexpr bool LINOK = (MODE == MODE_S) || (MODE == MODE_SMU && LOS == LOS_Z) || MODE == MODE_SIGPI;
+    const bool lin = LINOK && p.lin;
+    if (p.weighted) {
+        if constexpr (LINOK) {
+            if (lin && p.wint) return k_pairs_f32<MODE, LOS, 2, 2, true, 1, true>;
+        }
+        return lin ? k_pairs_f32<MODE, LOS, 1, 2, LINOK, 1, true> : k_pairs_f32<MODE, LOS, 1, 2, false, 1, true>;
+    }
+    return lin ? k_pairs_f32<MODE, LOS, 0, 2, LINOK, 1, true> : k_pairs_f32<MODE, LOS, 0, 2, false, 1, true>;
+}
+
+template <int MODE, int LOS>
+cudaError_t launch_kernel_f32(PairKernel<MODE, LOS> k, const PairParams &p, int grid, size_t smem,
+                              cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) return cudaSuccess;
@@ -1480,13 +1536,32 @@ cudaError_t launch_mode_f32(const PairParams &p, int ipt, int grid, size_t smem,
 }
 
 template <int MODE, int LOS>
-int occupancy_mode_f32(const PairParams &p, int ipt, size_t smem) {
-    PairKernel<MODE, LOS> k = pick_f32<MODE, LOS>(p, ipt);
+int occupancy_kernel_f32(PairKernel<MODE, LOS> k, const PairParams &p, size_t smem) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT * p.groups, smem) != cudaSuccess) return 0;
     return nb;
+}
+
+template <int MODE, int LOS>
+cudaError_t launch_mode_f32(const PairParams &p, int ipt, int grid, size_t smem, cudaStream_t st) {
+    return launch_kernel_f32<MODE, LOS>(pick_f32<MODE, LOS>(p, ipt), p, grid, smem, st);
+}
+
+template <int MODE, int LOS>
+int occupancy_mode_f32(const PairParams &p, int ipt, size_t smem) {
+    return occupancy_kernel_f32<MODE, LOS>(pick_f32<MODE, LOS>(p, ipt), p, smem);
+}
+
+template <int MODE, int LOS>
+cudaError_t launch_mode_f32_tree(const PairParams &p, int grid, size_t smem, cudaStream_t st) {
+    return launch_kernel_f32<MODE, LOS>(pick_f32_tree<MODE, LOS>(p), p, grid, smem, st);
+}
+
+template <int MODE, int LOS>
+int occupancy_mode_f32_tree(const PairParams &p, size_t smem) {
+    return occupancy_kernel_f32<MODE, LOS>(pick_f32_tree<MODE, LOS>(p), p, smem);
 }
 
 template <int MODE, int LOS>

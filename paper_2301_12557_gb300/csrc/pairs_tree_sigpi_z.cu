@@ -1,0 +1,13 @@
+// Instantiation of the tree variant of the FP32 pair kernel for MODE_SIGPI / LOS_Z.
+#include "pairs_impl.cuh"
+
+namespace pc {
+
+cudaError_t launch_f32t_SIGPI_Z(const PairParams &p, int grid, size_t smem, cudaStream_t st) {
+    return launch_mode_f32_tree<MODE_SIGPI, LOS_Z>(p, grid, smem, st);
+}
+int occ_f32t_SIGPI_Z(const PairParams &p, size_t smem) {
+    return occupancy_mode_f32_tree<MODE_SIGPI, LOS_Z>(p, smem);
+}
+
+}  // namespace pc

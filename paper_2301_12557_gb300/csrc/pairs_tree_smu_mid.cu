@@ -1,0 +1,13 @@
+// Instantiation of the tree variant of the FP32 pair kernel for MODE_SMU / LOS_MID.
+#include "pairs_impl.cuh"
+
+namespace pc {
+
+cudaError_t launch_f32t_SMU_MID(const PairParams &p, int grid, size_t smem, cudaStream_t st) {
+    return launch_mode_f32_tree<MODE_SMU, LOS_MID>(p, grid, smem, st);
+}
+int occ_f32t_SMU_MID(const PairParams &p, size_t smem) {
+    return occupancy_mode_f32_tree<MODE_SMU, LOS_MID>(p, smem);
+}
+
+}  // namespace pc

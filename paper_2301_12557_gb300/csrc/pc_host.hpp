@@ -28,7 +28,61 @@ struct pc_grid {
     int *perm;
 };
 
+// k-d tree of Alg. 1 (tree.cu).  Nodes in heap order: slot 0 is the root,
+// the children of slot h are 2h + 1 and 2h + 2; all nodes of one level hold
+// floor or ceil of the same share of the points.
+struct pc_tree {
+    int device;
+    int n;
+    int weighted;
+    int n_leaf;
+    int depth;                  // deepest level (every node there: <= n_leaf points)
+    int blevel;                 // block level: its nodes hold at most TREE_BLOCK points
+    long long nslots;           // 2^(depth + 1) - 1
+    pc::Geom g;                 // periodic and L; c = largest block extent
+    double pts_lo[3], pts_hi[3];
+    double r2min = 0.0;         // non-periodic: lower bound of min |x|^2
+    int wint = 0, wemax = 0, wemin = 0;   // as pc_grid
+    double bext = 0.0;          // largest extent (any axis) of a block node's box
+    float4 *rel;                // tree order: FP32 offset from the block centre, .w packed weight
+    double4_32a *xw;            // tree order: FP64 canonical coordinates, weight
+    int *perm;                  // tree position -> input index
+    int2 *vnode;                // every slot's range by the halving rule
+    int2 *node;                 // {start, count} of present slots; count -1: empty slot
+    double *nbox;               // lo[3], hi[3] per slot (present slots)
+    signed char *naxis;         // split axis per slot, -1: leaf or empty
+    double *bcen;               // block centres, 3 per block
+    int2 *brng;                 // block ranges {start, count}
+};
+
 namespace pc {
+
+constexpr int TREE_BLOCK = 256;   // points per i-block (NT threads x 2 i-points)
+
+// Block pairs listed by the dual-tree traversal, grouped by i-block.
+struct TreeLists {
+    const int2 *seg = nullptr;     // {j-block, image code}
+    const int *seg_off = nullptr;  // i-block -> first entry (n_i-blocks + 1)
+    long long npairs = 0;
+    int levels = 0;
+    int nblk_i = 0;
+};
+
+// Dual-tree traversal (Alg. 3) of t1 against t2 (t1 itself for an auto
+// count): node pairs whose boxes are farther apart than sqrt(r2hi), or all
+// of whose pairs are closer than sqrt(r2lo), are dropped; the rest descend
+// to block pairs.  The lists live in a per-device workspace valid until the
+// next traversal.  Synchronises the stream once per tree level.
+pc_status tree_traverse(const pc_tree *t1, const pc_tree *t2, bool is_auto, double r2hi,
+                        double r2lo, cudaStream_t st, TreeLists &out);
+
+// The pair kernel's block list of a tree count (one block per i-block).
+cudaError_t tree_blocks(const pc_tree *t, Block *blocks, int *nblocks_dev, cudaStream_t st);
+
+// Weight checks for the integer weight path: r[0] counts weights that are
+// not a non-negative normal binary32 value or zero, r[1] / r[2] the largest /
+// smallest biased exponent of the non-zero ones.  Synchronises the stream.
+pc_status weight_stats(const void *w, int w_is_f32, int n, cudaStream_t st, int r[3]);
 
 // Global library lock: calls are serialised (the workspace is shared).
 std::mutex &api_mutex();

@@ -121,6 +121,14 @@ struct PairParams {
     // (significand product shifted by both exponent offsets, accumulated in
     // u64 lane copies, flushed as binary64 times the task's wscale)
     int wint;
+    // k-d tree path (Alg. 3): each i-block (a tree node at the block level)
+    // pairs with the j-blocks listed for it by the dual-tree traversal
+    int tree;
+    const int2 *tseg;        // {j-block, image code} per listed pair, grouped by i-block
+    const int *tseg_off;     // i-block -> first entry in tseg (n_iblocks + 1)
+    const int2 *tblk_j;      // j-block -> {first point, count}
+    const double *tcen_i;    // i-block centres (x, y, z; binary64): the origin of rel
+    const double *tcen_j;    // j-block centres
 };
 
 // ---------------------------------------------------------------------------
@@ -144,7 +152,7 @@ long long launch_count();
 // launchers implemented in the kernel translation units
 // ---------------------------------------------------------------------------
 cudaError_t launch_pairs_f32(const PairParams &p, int ipt, int grid, size_t smem,
-                             cudaStream_t st);
+                             cudaStream_t st);   // p.tree selects the tree variant
 cudaError_t launch_pairs_f64(const PairParams &p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_rescue(const PairParams &p, cudaStream_t st);
 size_t pairs_f32_smem(const PairParams &p, int ipt);

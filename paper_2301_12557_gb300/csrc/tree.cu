@@ -1,0 +1,891 @@
+// k-d tree on the GPU (Sect. 2.2, Alg. 1) and the dual-tree traversal
+// (Sect. 3.1, Alg. 3) that lists, for every i-block, the j-blocks (and
+// periodic images) whose bounding boxes come within the largest separation.
+//
+// The tree is balanced (a split gives the left child floor(n / 2) points),
+// so the nodes are kept in heap order: slot 0 is the root and the children
+// of slot h are 2h + 1 and 2h + 2.  Every level is built by one pass of
+// node statistics (sums, sums of squares and bounds per node, for the axis
+// of largest variance and the minimum bounding box) and one stable radix
+// sort of all points on the key (node at this level, coordinate along its
+// split axis): after the sort each node's points are ordered along that
+// axis and its first floor(n / 2) points are the left child.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "pc_host.hpp"
+
+namespace pc {
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (u64 key, u32 value) pairs, 8 bits per pass
+// ---------------------------------------------------------------------------
+constexpr int RS_T = 256;                 // threads per tile
+constexpr int RS_I = 8;                   // keys per thread
+constexpr int RS_TILE = RS_T * RS_I;      // keys per tile
+constexpr int RS_W = RS_T / 32;           // warps per tile (each: RS_I * 32 consecutive keys)
+
+__global__ void __launch_bounds__(RS_T) k_rs_hist(const unsigned long long *__restrict__ keys, int n,
+                                                  int shift, int ntiles, int *__restrict__ cnt) {
+    __shared__ int s_c[256];
+    s_c[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * RS_TILE;
+    for (int k = 0; k < RS_I; ++k) {
+        const long long i = base + (long long)k * RS_T + threadIdx.x;
+        if (i < n) atomicAdd(&s_c[(int)((keys[i] >> shift) & 255ull)], 1);
+    }
+    __syncthreads();
+    cnt[(size_t)threadIdx.x * ntiles + blockIdx.x] = s_c[threadIdx.x];
+}
+
+// Scatter of one tile.  Keys keep their order inside a digit: warp w holds
+// the tile's keys [w * 256, w * 256 + 256) in rounds of 32, a key's place is
+// the digit's global offset for this tile + the digit's count in earlier
+// warps + its count earlier in its own warp (earlier rounds, lower lanes).
+__global__ void __launch_bounds__(RS_T) k_rs_scatter(const unsigned long long *__restrict__ kin,
+                                                     const unsigned *__restrict__ vin,
+                                                     unsigned long long *__restrict__ kout,
+                                                     unsigned *__restrict__ vout, int n, int shift,
+                                                     int ntiles, const int *__restrict__ off) {
+    __shared__ int s_wc[RS_W][256];
+    __shared__ int s_base[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < RS_W * 256; k += RS_T) (&s_wc[0][0])[k] = 0;
+    s_base[threadIdx.x] = off[(size_t)threadIdx.x * ntiles + blockIdx.x];
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * RS_TILE + (long long)warp * (RS_I * 32);
+    const unsigned below = (1u << lane) - 1u;
+    unsigned long long key[RS_I];
+    unsigned val[RS_I];
+    int dig[RS_I], loc[RS_I];
+#pragma unroll
+    for (int it = 0; it < RS_I; ++it) {
+        const long long i = base + it * 32 + lane;
+        const bool ok = i < n;
+        key[it] = ok ? kin[i] : 0ull;
+        val[it] = ok ? vin[i] : 0u;
+        const int d = ok ? (int)((key[it] >> shift) & 255ull) : 256 + lane;   // pads match nothing
+        dig[it] = d;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int prev = ok ? s_wc[warp][d] : 0;
+        __syncwarp();
+        if (ok && (peers & below) == 0u) s_wc[warp][d] = prev + __popc(peers);
+        __syncwarp();
+        loc[it] = prev + __popc(peers & below);
+    }
+    __syncthreads();
+    {   // per digit: exclusive prefix of the warps' counts
+        int run = 0;
+        for (int w = 0; w < RS_W; ++w) {
+            const int c = s_wc[w][threadIdx.x];
+            s_wc[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < RS_I; ++it) {
+        const long long i = base + it * 32 + lane;
+        if (i < n) {
+            const int d = dig[it];
+            const int pos = s_base[d] + s_wc[warp][d] + loc[it];
+            kout[pos] = key[it];
+            vout[pos] = val[it];
+        }
+    }
+}
+
+// Sort n pairs on key bits [0, bits); (ka, va) in and out, (kb, vb) scratch.
+// cnt / off: 256 * ceil(n / RS_TILE) + 1 ints; tot: scan tile totals.
+static cudaError_t radix_sort(unsigned long long *ka, unsigned *va, unsigned long long *kb,
+                              unsigned *vb, int n, int bits, int *cnt, int *off, int *tot,
+                              cudaStream_t st) {
+    if (n <= 1) return cudaSuccess;
+    const int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    unsigned long long *k0 = ka, *k1 = kb;
+    unsigned *v0 = va, *v1 = vb;
+    int passes = 0;
+    for (int shift = 0; shift < bits; shift += 8, ++passes) {
+        k_rs_hist<<<ntiles, RS_T, 0, st>>>(k0, n, shift, ntiles, cnt);
+        note_launch();
+        cudaError_t e = scan_exclusive_into(cnt, off, 256 * ntiles, tot, st);
+        if (e != cudaSuccess) return e;
+        k_rs_scatter<<<ntiles, RS_T, 0, st>>>(k0, v0, k1, v1, n, shift, ntiles, off);
+        note_launch();
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    if (passes & 1) {
+        cudaError_t e = cudaMemcpyAsync(ka, k0, sizeof(unsigned long long) * n,
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(va, v0, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// per-level node statistics
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double canon_t(double x, double L) {
+    double y = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
+    if (y < 0.0) y = __dadd_rn(y, L);
+    if (y >= L) y = __dsub_rn(y, L);
+    return y;
+}
+__device__ __forceinline__ long long okey(double v) {   // order-preserving signed key
+    long long b = __double_as_longlong(v);
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double unokey(long long k) {
+    long long b = k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFLL);
+    return __longlong_as_double(b);
+}
+__device__ __forceinline__ unsigned long long ukey(double v) {   // order-preserving unsigned key
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// canonical coordinates (periodic: folded into [0, L)) of the input points
+__global__ void k_tree_canon(const double *__restrict__ xyz, int n, Geom g, double *__restrict__ x) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3LL * n) return;
+    const int a = (int)(i % 3);
+    double v = xyz[i];
+    if (g.periodic) v = canon_t(v, g.L[a]);
+    x[i] = v;
+}
+
+struct NodeAcc {
+    double s[3], q[3];          // sums and sums of squares of (x - shift)
+    long long mn[3], mx[3];     // bounds (order-preserving keys)
+};
+
+__global__ void k_acc_init(NodeAcc *acc, int m) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    NodeAcc a;
+    for (int d = 0; d < 3; ++d) {
+        a.s[d] = a.q[d] = 0.0;
+        a.mn[d] = LLONG_MAX;
+        a.mx[d] = LLONG_MIN;
+    }
+    acc[k] = a;
+}
+
+__device__ __forceinline__ void acc_add(NodeAcc *A, const double *s, const double *q,
+                                        const long long *mn, const long long *mx) {
+    for (int d = 0; d < 3; ++d) {
+        atomicAdd(&A->s[d], s[d]);
+        atomicAdd(&A->q[d], q[d]);
+        atomicMin(&A->mn[d], mn[d]);
+        atomicMax(&A->mx[d], mx[d]);
+    }
+}
+
+// Statistics of the level's nodes: a warp takes 256 consecutive positions
+// (nid, the node of each position at this level, never decreases along the
+// positions).  A warp inside one node sums in registers and adds once; a
+// warp that spans nodes reduces each round of 32 by node segments.
+__global__ void k_node_stats(const double *__restrict__ x, const unsigned *__restrict__ perm,
+                             const int *__restrict__ nid, int n, double3 shift, NodeAcc *acc) {
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long base = gw * 256;
+    if (base >= n) return;
+    const long long last = min(base + 255, (long long)n - 1);
+    const int n0 = nid[base], n1 = nid[last];
+    const double sh[3] = {shift.x, shift.y, shift.z};
+    if (n0 == n1) {
+        double s[3] = {0, 0, 0}, q[3] = {0, 0, 0};
+        long long mn[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, mx[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+        for (int it = 0; it < 8; ++it) {
+            const long long i = base + it * 32 + lane;
+            if (i > last) break;
+            const unsigned p = perm[i];
+            for (int d = 0; d < 3; ++d) {
+                const double v = x[3 * (size_t)p + d];
+                const double t = v - sh[d];
+                s[d] += t;
+                q[d] = fma(t, t, q[d]);
+                mn[d] = min(mn[d], okey(v));
+                mx[d] = max(mx[d], okey(v));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            for (int d = 0; d < 3; ++d) {
+                s[d] += __shfl_xor_sync(0xffffffffu, s[d], o);
+                q[d] += __shfl_xor_sync(0xffffffffu, q[d], o);
+                mn[d] = min(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+                mx[d] = max(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+            }
+        if (lane == 0) acc_add(&acc[n0], s, q, mn, mx);
+        return;
+    }
+    for (int it = 0; it < 8; ++it) {
+        const long long i = base + it * 32 + lane;
+        const bool ok = i <= last;
+        const int node = ok ? nid[i] : -1;     // pads: one trailing segment, never added
+        double s[3] = {0, 0, 0}, q[3] = {0, 0, 0};
+        long long mn[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, mx[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+        if (ok) {
+            const unsigned p = perm[i];
+            for (int d = 0; d < 3; ++d) {
+                const double v = x[3 * (size_t)p + d];
+                const double t = v - sh[d];
+                s[d] = t;
+                q[d] = t * t;
+                mn[d] = mx[d] = okey(v);
+            }
+        }
+        // segmented suffix reduction: lane l ends with its segment's values
+        // over [l, segment end]; segments are runs of equal node
+        for (int o = 1; o < 32; o <<= 1) {
+            const int on = __shfl_down_sync(0xffffffffu, node, o);
+            const bool take = lane + o < 32 && on == node;
+            for (int d = 0; d < 3; ++d) {
+                const double ts = __shfl_down_sync(0xffffffffu, s[d], o);
+                const double tq = __shfl_down_sync(0xffffffffu, q[d], o);
+                const long long tn = __shfl_down_sync(0xffffffffu, mn[d], o);
+                const long long tx = __shfl_down_sync(0xffffffffu, mx[d], o);
+                if (take) {
+                    s[d] += ts;
+                    q[d] += tq;
+                    mn[d] = min(mn[d], tn);
+                    mx[d] = max(mx[d], tx);
+                }
+            }
+        }
+        const int up = __shfl_up_sync(0xffffffffu, node, 1);
+        const bool head = ok && (lane == 0 || up != node);
+        if (head) acc_add(&acc[node], s, q, mn, mx);
+    }
+}
+
+// Bounds and split axis of the level's nodes (present slots only).
+__global__ void k_node_finish(const NodeAcc *__restrict__ acc, int level, const int2 *__restrict__ node,
+                              int n_leaf, double *__restrict__ box, signed char *__restrict__ axis) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (1 << level)) return;
+    const long long h = (1LL << level) - 1 + k;
+    const int2 nd = node[h];
+    if (nd.y < 0) return;
+    const NodeAcc A = acc[k];
+    for (int d = 0; d < 3; ++d) {
+        box[6 * h + d] = unokey(A.mn[d]);
+        box[6 * h + 3 + d] = unokey(A.mx[d]);
+    }
+    int best = -1;
+    if (nd.y > n_leaf) {
+        // variance x count = sum (x - c)^2 - (sum (x - c))^2 / count; first maximum
+        double bv = -1.0;
+        for (int d = 0; d < 3; ++d) {
+            const double v = A.q[d] - A.s[d] * A.s[d] / (double)nd.y;
+            if (v > bv) {
+                bv = v;
+                best = d;
+            }
+        }
+    }
+    axis[h] = (signed char)best;
+}
+
+// Sort keys of level d: the node's index in its level on the high d bits,
+// the coordinate along the node's split axis below (a node that is not
+// split keeps its order: coordinate bits 0).
+__global__ void k_tree_keys(const double *__restrict__ x, const unsigned *__restrict__ perm,
+                            const int *__restrict__ nid, int n, int level,
+                            const signed char *__restrict__ axis,
+                            unsigned long long *__restrict__ keys) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = nid[i];
+    const long long h = (1LL << level) - 1 + k;
+    const int ax = axis[h];
+    unsigned long long ck = 0ull;
+    if (ax >= 0) ck = ukey(x[3 * (size_t)perm[i] + ax]) >> level;
+    keys[i] = level ? (((unsigned long long)k << (64 - level)) | ck) : ck;
+}
+
+// Node of each position one level down (the halving rule of every slot).
+__global__ void k_nid_next(const int2 *__restrict__ vnode, int n, int level, int *__restrict__ nid) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = nid[i];
+    const int2 v = vnode[(1LL << level) - 1 + k];
+    nid[i] = 2 * k + ((i - v.x) >= v.y / 2 ? 1 : 0);
+}
+
+// Block centres (midpoints of the block nodes' boxes), block ranges and the
+// largest block extent (as an order-preserving key).
+__global__ void k_block_info(const double *__restrict__ box, const int2 *__restrict__ vnode, int blevel,
+                             double *__restrict__ cen, int2 *__restrict__ rng,
+                             long long *__restrict__ ext_key) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (1 << blevel)) return;
+    const long long h = (1LL << blevel) - 1 + b;
+    double e = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double lo = box[6 * h + d], hi = box[6 * h + 3 + d];
+        cen[3 * (size_t)b + d] = __dmul_rn(0.5, __dadd_rn(lo, hi));
+        e = fmax(e, __dsub_rn(hi, lo));
+    }
+    rng[b] = vnode[h];
+    atomicMax(ext_key, okey(e));
+}
+
+__device__ __forceinline__ unsigned pack_weight_t(double wv, int emax) {
+    const unsigned b = __float_as_uint(__double2float_rn(wv));
+    const int e = (int)((b >> 23) & 0xFF);
+    if (e == 0) return 0u;
+    return ((unsigned)(emax - e) << 24) | (b & 0x7FFFFFu) | 0x800000u;
+}
+
+// Point records in tree order: FP32 offset from the block centre (.w the
+// packed integer weight or 0), FP64 canonical coordinates and weight.
+__global__ void k_tree_scatter(const double *__restrict__ x, const void *__restrict__ w, int w_is_f32,
+                               int wpack_emax, const unsigned *__restrict__ perm,
+                               const int *__restrict__ bid, const double *__restrict__ cen, int n,
+                               float4 *__restrict__ rel, double4_32a *__restrict__ xw,
+                               int *__restrict__ perm_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned p = perm[i];
+    const int b = bid[i];
+    double v[3];
+    float r[3];
+    for (int d = 0; d < 3; ++d) {
+        v[d] = x[3 * (size_t)p + d];
+        r[d] = __double2float_rn(__dsub_rn(v[d], cen[3 * (size_t)b + d]));
+    }
+    double wv = 1.0;
+    if (w) wv = w_is_f32 ? (double)((const float *)w)[p] : ((const double *)w)[p];
+    const unsigned wp = (w && wpack_emax > 0) ? pack_weight_t(wv, wpack_emax) : 0u;
+    rel[i] = make_float4(r[0], r[1], r[2], __uint_as_float(wp));
+    xw[i] = make_double4_32a(v[0], v[1], v[2], wv);
+    perm_out[i] = (int)p;
+}
+
+// Levels below the root until every node holds at most cap points.
+static int tree_depth(long long n, int cap) {
+    int d = 0;
+    long long m = n;
+    while (m > cap) {
+        m = (m + 1) / 2;
+        ++d;
+    }
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// dual-tree traversal (Alg. 3), one level of node pairs per launch
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int slot_level(int h) { return 31 - __clz(h + 1); }
+
+__device__ __forceinline__ void push_pairs(int2 *out, int *n_out, const int2 *v, int m) {
+    const int k = atomicAdd(n_out, m);
+    for (int q = 0; q < m; ++q) out[k + q] = v[q];
+}
+
+// A node pair {a, b | image << 24}: dropped when the boxes (b shifted by
+// the image) are farther apart than the largest separation or all pairs
+// are closer than the smallest; listed when both are block nodes (an auto
+// count leaves a block paired with itself to the pair kernel's own-block
+// pass, and lists the pair from the side that balances the blocks' loads);
+// otherwise split into the children pairs (a node paired with itself into
+// (left, left), (left, right), (right, right)).  Splits stop at the block
+// level of each tree.
+__global__ void k_dual_level(const int2 *__restrict__ in, int n_in, int2 *__restrict__ out,
+                             int *n_out, int2 *__restrict__ emit, int *n_emit,
+                             const double *__restrict__ box1, const double *__restrict__ box2,
+                             int blev1, int blev2, Geom g, double r2hi, double r2lo, int is_auto) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_in) return;
+    const int2 e = in[i];
+    const int a = e.x, b = e.y & 0xFFFFFF, img = e.y >> 24;
+    const int s3[3] = {img / 9 - 1, (img / 3) % 3 - 1, img % 3 - 1};
+    double dmin2 = 0.0, dmax2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double sh = g.periodic ? (double)s3[d] * g.L[d] : 0.0;
+        const double alo = box1[6 * (size_t)a + d], ahi = box1[6 * (size_t)a + 3 + d];
+        const double blo = box2[6 * (size_t)b + d] + sh, bhi = box2[6 * (size_t)b + 3 + d] + sh;
+        const double gap = fmax(0.0, fmax(blo - ahi, alo - bhi));
+        const double far = fmax(bhi - alo, ahi - blo);
+        dmin2 += gap * gap;
+        dmax2 += far * far;
+    }
+    if (dmin2 > r2hi || dmax2 < r2lo) return;
+    const bool ab = slot_level(a) >= blev1, bb = slot_level(b) >= blev2;
+    const bool self = is_auto && a == b && img == 13;
+    if (ab && bb) {
+        if (self) return;
+        int ea = a, eb = b, ei = img;
+        if (is_auto && ((a ^ b) & 1)) {
+            ea = b;
+            eb = a;
+            ei = 26 - img;
+        }
+        emit[atomicAdd(n_emit, 1)] = make_int2(ea, eb | (ei << 24));
+        return;
+    }
+    const int tag = img << 24;
+    int2 v[4];
+    if (self) {
+        v[0] = make_int2(2 * a + 1, (2 * a + 1) | tag);
+        v[1] = make_int2(2 * a + 1, (2 * a + 2) | tag);
+        v[2] = make_int2(2 * a + 2, (2 * a + 2) | tag);
+        push_pairs(out, n_out, v, 3);
+    } else if (!ab && !bb) {
+        v[0] = make_int2(2 * a + 1, (2 * b + 1) | tag);
+        v[1] = make_int2(2 * a + 1, (2 * b + 2) | tag);
+        v[2] = make_int2(2 * a + 2, (2 * b + 1) | tag);
+        v[3] = make_int2(2 * a + 2, (2 * b + 2) | tag);
+        push_pairs(out, n_out, v, 4);
+    } else if (ab) {
+        v[0] = make_int2(a, (2 * b + 1) | tag);
+        v[1] = make_int2(a, (2 * b + 2) | tag);
+        push_pairs(out, n_out, v, 2);
+    } else {
+        v[0] = make_int2(2 * a + 1, b | tag);
+        v[1] = make_int2(2 * a + 2, b | tag);
+        push_pairs(out, n_out, v, 2);
+    }
+}
+
+// Group the listed block pairs by i-block: counts, then (after a scan) the
+// entries {j-block, image}; the order inside a group is arbitrary.
+__global__ void k_group_count(const int2 *__restrict__ emit, int ne, int blk0, int *__restrict__ cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ne) atomicAdd(&cnt[emit[i].x - blk0], 1);
+}
+__global__ void k_group_fill(const int2 *__restrict__ emit, int ne, int blk0_i, int blk0_j,
+                             int *__restrict__ cursor, int2 *__restrict__ seg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const int2 e = emit[i];
+    const int pos = atomicAdd(&cursor[e.x - blk0_i], 1);
+    seg[pos] = make_int2((e.y & 0xFFFFFF) - blk0_j, e.y >> 24);
+}
+
+// The pair kernel's blocks: one per i-block ("cell" = i-block index).
+__global__ void k_tree_blocks(const int2 *__restrict__ rng, int nblk, Block *__restrict__ blocks,
+                              int *__restrict__ nblocks) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0) *nblocks = nblk;
+    if (b >= nblk) return;
+    blocks[b] = Block{0, b, rng[b].x, rng[b].y};
+}
+
+// Growable device array of the traversal workspace (reused across calls;
+// the first `keep` bytes survive a growth).
+struct DArr {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes, cudaStream_t st, size_t keep = 0) {
+        if (bytes <= cap) return cudaSuccess;
+        size_t want = std::max(bytes, cap * 2);
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, want);
+        if (e != cudaSuccess) return e;
+        if (keep && p) {
+            e = cudaMemcpyAsync(q, p, keep, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                cudaFree(q);
+                return e;
+            }
+        }
+        if (p) cudaFree(p);
+        p = q;
+        cap = want;
+        return cudaSuccess;
+    }
+};
+
+static void swap_arr(DArr &a, DArr &b) {
+    std::swap(a.p, b.p);
+    std::swap(a.cap, b.cap);
+}
+
+struct TraversalWs {
+    DArr la, lb, emit, seg, cnt, off, cursor, tot, scal;
+};
+
+static TraversalWs &traversal_ws(int dev) {
+    static std::map<int, TraversalWs> ws;
+    return ws[dev];
+}
+
+pc_status tree_traverse(const pc_tree *t1, const pc_tree *t2, bool is_auto, double r2hi,
+                        double r2lo, cudaStream_t st, TreeLists &out) {
+    TraversalWs &W = traversal_ws(t1->device);
+    const Geom &g = t1->g;
+    // initial node pairs: the roots under every periodic image (an auto
+    // count: the identity and the half of the images with code > 13, whose
+    // mirror images would give the same pairs again)
+    std::vector<int2> init;
+    for (int img = 0; img < 27; ++img) {
+        if (!g.periodic && img != 13) continue;
+        if (is_auto && img < 13) continue;
+        init.push_back(make_int2(0, img << 24));
+    }
+    size_t n_in = init.size();
+    PC_CUDA(W.la.ensure(sizeof(int2) * n_in, st));
+    PC_CUDA(W.scal.ensure(sizeof(int) * 2, st));
+    PC_CUDA(cudaMemcpyAsync(W.la.p, init.data(), sizeof(int2) * n_in, cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemsetAsync(W.scal.p, 0, sizeof(int) * 2, st));
+    int *d_nout = (int *)W.scal.p, *d_nemit = d_nout + 1;
+    long long n_emit = 0;
+    int levels = 0;
+    while (n_in > 0) {
+        const size_t out_cap = 4 * n_in;
+        if (out_cap > (size_t)INT_MAX || (size_t)n_emit + n_in > (size_t)INT_MAX)
+            return fail(PC_EOVERFLOW, "tree traversal: too many node pairs");
+        PC_CUDA(W.lb.ensure(sizeof(int2) * out_cap, st));
+        PC_CUDA(W.emit.ensure(sizeof(int2) * ((size_t)n_emit + n_in), st, sizeof(int2) * n_emit));
+        PC_CUDA(cudaMemsetAsync(d_nout, 0, sizeof(int), st));
+        k_dual_level<<<(unsigned)((n_in + 255) / 256), 256, 0, st>>>(
+            (const int2 *)W.la.p, (int)n_in, (int2 *)W.lb.p, d_nout, (int2 *)W.emit.p, d_nemit,
+            t1->nbox, t2->nbox, t1->blevel, t2->blevel, g, r2hi, r2lo, is_auto ? 1 : 0);
+        note_launch();
+        PC_CUDA(cudaGetLastError());
+        int h[2];
+        PC_CUDA(cudaMemcpyAsync(h, W.scal.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+        PC_CUDA(cudaStreamSynchronize(st));
+        n_in = (size_t)h[0];
+        n_emit = h[1];
+        swap_arr(W.la, W.lb);
+        ++levels;
+    }
+    // group by i-block
+    const int nbi = 1 << t1->blevel;
+    const int blk0_i = nbi - 1, blk0_j = (1 << t2->blevel) - 1;
+    const size_t ne = (size_t)n_emit;
+    PC_CUDA(W.seg.ensure(sizeof(int2) * std::max<size_t>(ne, 1), st));
+    PC_CUDA(W.cnt.ensure(sizeof(int) * (nbi + 1), st));
+    PC_CUDA(W.off.ensure(sizeof(int) * (nbi + 1), st));
+    PC_CUDA(W.cursor.ensure(sizeof(int) * (nbi + 1), st));
+    PC_CUDA(W.tot.ensure(sizeof(int) * ((nbi + 1) / 4096 + 2), st));
+    PC_CUDA(cudaMemsetAsync(W.cnt.p, 0, sizeof(int) * (nbi + 1), st));
+    if (ne > 0) {
+        k_group_count<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>((const int2 *)W.emit.p, (int)ne,
+                                                                     blk0_i, (int *)W.cnt.p);
+        note_launch();
+    }
+    PC_CUDA(scan_exclusive_into((const int *)W.cnt.p, (int *)W.off.p, nbi, (int *)W.tot.p, st));
+    PC_CUDA(cudaMemcpyAsync(W.cursor.p, W.off.p, sizeof(int) * (nbi + 1), cudaMemcpyDeviceToDevice, st));
+    if (ne > 0) {
+        k_group_fill<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+            (const int2 *)W.emit.p, (int)ne, blk0_i, blk0_j, (int *)W.cursor.p, (int2 *)W.seg.p);
+        note_launch();
+    }
+    PC_CUDA(cudaGetLastError());
+    out.seg = (const int2 *)W.seg.p;
+    out.seg_off = (const int *)W.off.p;
+    out.npairs = (long long)ne;
+    out.levels = levels;
+    out.nblk_i = nbi;
+    return PC_OK;
+}
+
+cudaError_t tree_blocks(const pc_tree *t, Block *blocks, int *nblocks_dev, cudaStream_t st) {
+    const int nb = 1 << t->blevel;
+    k_tree_blocks<<<(nb + 255) / 256, 256, 0, st>>>(t->brng, nb, blocks, nblocks_dev);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace pc
+
+// ---------------------------------------------------------------------------
+// public: tree build / free / info / export
+// ---------------------------------------------------------------------------
+using namespace pc;
+
+static void tree_release(pc_tree *t) {
+    if (!t) return;
+    cudaFree(t->rel);
+    cudaFree(t->xw);
+    cudaFree(t->perm);
+    cudaFree(t->vnode);
+    cudaFree(t->node);
+    cudaFree(t->nbox);
+    cudaFree(t->naxis);
+    cudaFree(t->bcen);
+    cudaFree(t->brng);
+    delete t;
+}
+
+extern "C" void pc_free_tree(pc_tree *t) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    tree_release(t);
+}
+
+extern "C" pc_status pc_tree_info(const pc_tree *t, long long *n, int *depth, int *block_level,
+                                  long long *slots) {
+    if (!t) return fail(PC_EINVAL, "pc_tree_info: null tree");
+    if (n) *n = t->n;
+    if (depth) *depth = t->depth;
+    if (block_level) *block_level = t->blevel;
+    if (slots) *slots = t->nslots;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_tree_export(const pc_tree *t, long long *start, long long *count, int *axis,
+                                    double *box, long long *ord) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!t) return fail(PC_EINVAL, "pc_tree_export: null tree");
+    const size_t ns = (size_t)t->nslots;
+    if (start || count) {
+        std::vector<int2> nd(ns);
+        PC_CUDA(cudaMemcpy(nd.data(), t->node, sizeof(int2) * ns, cudaMemcpyDeviceToHost));
+        for (size_t h = 0; h < ns; ++h) {
+            if (start) start[h] = nd[h].y >= 0 ? nd[h].x : 0;
+            if (count) count[h] = nd[h].y;
+        }
+    }
+    if (axis) {
+        std::vector<signed char> ax(ns);
+        PC_CUDA(cudaMemcpy(ax.data(), t->naxis, ns, cudaMemcpyDeviceToHost));
+        for (size_t h = 0; h < ns; ++h) axis[h] = ax[h];
+    }
+    if (box) PC_CUDA(cudaMemcpy(box, t->nbox, sizeof(double) * 6 * ns, cudaMemcpyDeviceToHost));
+    if (ord && t->n > 0) {
+        std::vector<int> pm(t->n);
+        PC_CUDA(cudaMemcpy(pm.data(), t->perm, sizeof(int) * t->n, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < t->n; ++i) ord[i] = pm[i];
+    }
+    return PC_OK;
+}
+
+extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f32, long long n,
+                                   const pc_box *box, int n_leaf, void *stream, pc_tree **out) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!out) return fail(PC_EINVAL, "pc_build_tree: out is NULL");
+    *out = nullptr;
+    if (!box) return fail(PC_EINVAL, "pc_build_tree: box is NULL");
+    if (n < 1) return fail(PC_EINVAL, "pc_build_tree: a tree needs at least one point");
+    if (!xyz) return fail(PC_EINVAL, "pc_build_tree: xyz is NULL");
+    if (n >= (1LL << 31) - 1) return fail(PC_EOVERFLOW, "pc_build_tree: n must be below 2^31");
+    if (n_leaf < 1 || n_leaf > 128) return fail(PC_EINVAL, "pc_build_tree: n_leaf must lie in [1, 128]");
+    const int depth = tree_depth(n, n_leaf);
+    const int blevel = tree_depth(n, TREE_BLOCK);
+    if (depth > 27) return fail(PC_EOVERFLOW, "pc_build_tree: more than 2^28 tree slots");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    PC_CUDA(cudaGetDevice(&dev));
+
+    pc_tree *t = new pc_tree();
+    memset(t, 0, sizeof(*t));
+    t->device = dev;
+    t->n = (int)n;
+    t->weighted = (w != nullptr);
+    t->n_leaf = n_leaf;
+    t->depth = depth;
+    t->blevel = blevel;
+    t->nslots = (2LL << depth) - 1;
+    Geom &G = t->g;
+    G.periodic = box->periodic ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+        if (G.periodic) {
+            if (!(box->L[a] > 0.0) || !isfinite(box->L[a])) {
+                delete t;
+                return fail(PC_EINVAL, "pc_build_tree: periodic box needs L > 0 on every axis");
+            }
+            G.L[a] = box->L[a];
+            G.hL[a] = 0.5 * box->L[a];
+        }
+        G.ng[a] = 1;
+    }
+
+    // temporaries
+    std::vector<void *> tmp;
+    auto talloc = [&](void **p, size_t bytes) {
+        cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+        if (e == cudaSuccess) tmp.push_back(*p);
+        return e;
+    };
+    auto cleanup = [&]() {
+        for (void *p : tmp) cudaFreeAsync(p, st);
+        cudaStreamSynchronize(st);
+    };
+    auto bail = [&](pc_status s) {
+        cleanup();
+        tree_release(t);
+        return s;
+    };
+    const double *dxyz = xyz;
+    const void *dw = w;
+    cudaError_t e = cudaSuccess;
+    if (!is_device_ptr(xyz)) {
+        void *q = nullptr;
+        e = talloc(&q, sizeof(double) * 3 * n);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(q, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st);
+        dxyz = (const double *)q;
+    }
+    const size_t wbytes = (size_t)n * (w_is_f32 ? sizeof(float) : sizeof(double));
+    if (e == cudaSuccess && w && !is_device_ptr(w)) {
+        void *q = nullptr;
+        e = talloc(&q, wbytes);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(q, w, wbytes, cudaMemcpyHostToDevice, st);
+        dw = q;
+    }
+    double *x = nullptr;
+    if (e == cudaSuccess) e = talloc((void **)&x, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) {
+        k_tree_canon<<<(unsigned)((3 * n + 255) / 256), 256, 0, st>>>(dxyz, (int)n, G, x);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return bail(cuda_fail(e, "pc_build_tree: inputs"));
+
+    // bounds of the canonical points and, non-periodic, the smallest radius
+    double plo[3], phi[3];
+    {
+        pc_status s = aabb_device(x, n, st, plo, phi, G.periodic ? nullptr : &t->r2min);
+        if (s != PC_OK) return bail(s);
+        for (int a = 0; a < 3; ++a)
+            if (!isfinite(plo[a]) || !isfinite(phi[a]))
+                return bail(fail(PC_EINVAL, "pc_build_tree: non-finite coordinates"));
+        for (int a = 0; a < 3; ++a) {
+            t->pts_lo[a] = G.periodic ? 0.0 : plo[a];
+            t->pts_hi[a] = G.periodic ? G.L[a] : phi[a];
+            G.lo[a] = t->pts_lo[a];
+        }
+    }
+    // weights usable by the integer weight path
+    if (dw) {
+        int r[3];
+        pc_status s = weight_stats(dw, w_is_f32, (int)n, st, r);
+        if (s != PC_OK) return bail(s);
+        if (r[0] == 0) {
+            t->wint = 1;
+            t->wemax = r[1] >= 0 ? r[1] : 1;
+            t->wemin = r[1] >= 0 ? r[2] : 1;
+        }
+    }
+
+    // slot ranges by the halving rule (also below leaves: "virtual" ranges
+    // keep those points in place during the sorts); present slots: the root
+    // and the children of split nodes
+    const size_t ns = (size_t)t->nslots;
+    std::vector<int2> vnode(ns), node(ns);
+    vnode[0] = make_int2(0, (int)n);
+    node[0] = vnode[0];
+    for (size_t h = 0; 2 * h + 2 < ns; ++h) {
+        const int2 v = vnode[h];
+        vnode[2 * h + 1] = make_int2(v.x, v.y / 2);
+        vnode[2 * h + 2] = make_int2(v.x + v.y / 2, v.y - v.y / 2);
+        const bool split = node[h].y > n_leaf;
+        node[2 * h + 1] = split ? vnode[2 * h + 1] : make_int2(0, -1);
+        node[2 * h + 2] = split ? vnode[2 * h + 2] : make_int2(0, -1);
+    }
+    e = cudaMalloc(&t->vnode, sizeof(int2) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&t->node, sizeof(int2) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&t->nbox, sizeof(double) * 6 * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&t->naxis, ns);
+    if (e == cudaSuccess) e = cudaMalloc(&t->rel, sizeof(float4) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&t->xw, sizeof(double4_32a) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&t->perm, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&t->bcen, sizeof(double) * 3 * ((size_t)1 << blevel));
+    if (e == cudaSuccess) e = cudaMalloc(&t->brng, sizeof(int2) * ((size_t)1 << blevel));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PC_ENOMEM, "pc_build_tree: device allocation failed"));
+    }
+    e = cudaMemcpyAsync(t->vnode, vnode.data(), sizeof(int2) * ns, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->node, node.data(), sizeof(int2) * ns, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->naxis, 0xFF, ns, st);   // -1: leaf or empty
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->nbox, 0, sizeof(double) * 6 * ns, st);
+
+    // level loop
+    const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    unsigned long long *ka = nullptr, *kb = nullptr;
+    unsigned *va = nullptr, *vb = nullptr;
+    int *nid = nullptr, *bid = nullptr, *cnt = nullptr, *off = nullptr, *tot = nullptr;
+    NodeAcc *acc = nullptr;
+    long long *ext = nullptr;
+    const size_t ncnt = (size_t)256 * ntiles + 1;
+    if (e == cudaSuccess) e = talloc((void **)&ka, sizeof(unsigned long long) * n);
+    if (e == cudaSuccess) e = talloc((void **)&kb, sizeof(unsigned long long) * n);
+    if (e == cudaSuccess) e = talloc((void **)&va, sizeof(unsigned) * n);
+    if (e == cudaSuccess) e = talloc((void **)&vb, sizeof(unsigned) * n);
+    if (e == cudaSuccess) e = talloc((void **)&nid, sizeof(int) * n);
+    if (e == cudaSuccess) e = talloc((void **)&bid, sizeof(int) * n);
+    if (e == cudaSuccess) e = talloc((void **)&cnt, sizeof(int) * ncnt);
+    if (e == cudaSuccess) e = talloc((void **)&off, sizeof(int) * ncnt);
+    if (e == cudaSuccess) e = talloc((void **)&tot, sizeof(int) * (ncnt / 4096 + 2));
+    if (e == cudaSuccess) e = talloc((void **)&acc, sizeof(NodeAcc) * ((size_t)1 << depth));
+    if (e == cudaSuccess) e = talloc((void **)&ext, sizeof(long long));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PC_ENOMEM, "pc_build_tree: device allocation failed"));
+    }
+    {
+        std::vector<unsigned> iota(n);
+        for (long long i = 0; i < n; ++i) iota[i] = (unsigned)i;
+        e = cudaMemcpyAsync(va, iota.data(), sizeof(unsigned) * n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(nid, 0, sizeof(int) * n, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // iota leaves scope
+    }
+    const double3 shift = make_double3(0.5 * (t->pts_lo[0] + t->pts_hi[0]),
+                                       0.5 * (t->pts_lo[1] + t->pts_hi[1]),
+                                       0.5 * (t->pts_lo[2] + t->pts_hi[2]));
+    const unsigned gpos = (unsigned)((n + 255) / 256);
+    for (int d = 0; e == cudaSuccess && d <= depth; ++d) {
+        const int m = 1 << d;
+        k_acc_init<<<(m + 255) / 256, 256, 0, st>>>(acc, m);
+        note_launch();
+        const long long warps = (n + 255) / 256;
+        k_node_stats<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(x, va, nid, (int)n, shift, acc);
+        note_launch();
+        k_node_finish<<<(m + 255) / 256, 256, 0, st>>>(acc, d, t->node, n_leaf, t->nbox, t->naxis);
+        note_launch();
+        e = cudaGetLastError();
+        if (e == cudaSuccess && d == blevel)
+            e = cudaMemcpyAsync(bid, nid, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess || d == depth) break;
+        k_tree_keys<<<gpos, 256, 0, st>>>(x, va, nid, (int)n, d, t->naxis, ka);
+        note_launch();
+        e = radix_sort(ka, va, kb, vb, (int)n, 64, cnt, off, tot, st);
+        if (e == cudaSuccess) {
+            k_nid_next<<<gpos, 256, 0, st>>>(t->vnode, (int)n, d, nid);
+            note_launch();
+            e = cudaGetLastError();
+        }
+    }
+    // blocks and point records
+    const int nblk = 1 << blevel;
+    long long ext_init = LLONG_MIN, ext_key = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ext, &ext_init, sizeof(long long), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k_block_info<<<(nblk + 255) / 256, 256, 0, st>>>(t->nbox, t->vnode, blevel, t->bcen, t->brng, ext);
+        note_launch();
+        k_tree_scatter<<<gpos, 256, 0, st>>>(x, dw, w_is_f32, t->wint ? t->wemax : 0, va, bid, t->bcen,
+                                             (int)n, t->rel, t->xw, t->perm);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ext_key, ext, sizeof(long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "pc_build_tree"));
+    {
+        long long b = ext_key >= 0 ? ext_key : (ext_key ^ 0x7FFFFFFFFFFFFFFFLL);
+        double ex;
+        memcpy(&ex, &b, sizeof(ex));
+        t->bext = ex;
+    }
+    for (int a = 0; a < 3; ++a) {
+        G.c[a] = std::max(t->bext, 1e-300);
+        G.c32[a] = (float)G.c[a];
+    }
+    cleanup();
+    *out = t;
+    return PC_OK;
+}
