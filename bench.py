@@ -49,8 +49,16 @@ def parse():
     ap.add_argument("--workload", default="ns_periodic_n2m_smu40x100")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--tree-steps", type=int, default=3,
+                    help="steps of the k-d tree path reported beside the grid line (0: none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--structure", choices=["grid", "kdtree"], default="grid",
+                    help="space partition: the regular grid (default, tuned) or the k-d tree "
+                         "with the dual-tree traversal")
+    ap.add_argument("--n-leaf", type=int, default=32, help="k-d tree leaf capacity")
+    ap.add_argument("--list-cap", type=int, default=0,
+                    help="k-d tree list nodes: at most this many points (0 = automatic)")
     ap.add_argument("--cell-size", type=float, default=0.0)
     ap.add_argument("--ipt", type=int, default=0)
     ap.add_argument("--shard", action="store_true",
@@ -263,7 +271,20 @@ def run_ours(args):
     box = P.make_box(L_box, w.periodic)
     stream = torch.cuda.current_stream()
     tuning = None
-    if args.cell_size > 0 or args.ipt > 0:
+    tree = args.structure == "kdtree"
+    list_cap = args.list_cap
+    if tree and args.shard:
+        raise SystemExit("--shard is a grid-path option")
+    if tree and (args.list_cap > 0 or args.ipt > 0):
+        opts = P.make_opts("f32", 0.0, args.ipt or 2)
+    elif tree:
+        # measured list level and i-points per thread, once, before the timed steps
+        t0 = time.perf_counter()
+        opts, list_cap, trials = P.pc_tune_tree(D, box=box, bins=bins, n_leaf=args.n_leaf,
+                                                stream=stream)
+        tuning = {"seconds": time.perf_counter() - t0,
+                  "trials": [{"list_cap": c, "ipt": i, "ms": round(ms, 3)} for c, i, ms in trials]}
+    elif args.cell_size > 0 or args.ipt > 0:
         opts = P.make_opts("f32", args.cell_size, args.ipt)
     else:
         # measured autotuning on this catalogue, once, before the timed steps
@@ -277,8 +298,22 @@ def run_ours(args):
         shard.shard_opts(opts, rank, world)
     out = torch.zeros(bins.nbins, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tree_ms = []
 
-    def step(o=opts, x=D, counts=out):
+    def step(o=opts, x=D, counts=out, structure=args.structure):
+        if structure == "kdtree":
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            t = P.pc_build_tree(x, box=box, n_leaf=args.n_leaf, list_cap=list_cap,
+                                stream=stream)
+            b.record(stream)
+            try:
+                _, _, st = P.pc_count_tree(t, None, bins, o, stream, counts=counts)
+            finally:
+                t.free()
+            tree_ms.append(a.elapsed_time(b))
+            return st
         g = P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=o, stream=stream)
         try:
             _, _, st = P.pc_count_auto(g, bins, o, stream, counts=counts)
@@ -355,14 +390,14 @@ def run_ours(args):
         vol = float(np.prod(np.broadcast_to(np.asarray(L_box, dtype=np.float64), (3,))))
         o64 = P.make_opts("f64", P.pc_suggest_cell_size(n, vol, bins.r_max), 1)
         out64 = torch.zeros_like(out)
-        step(o=o64, counts=out64)
+        step(o=o64, counts=out64, structure="grid")
         torch.cuda.synchronize()
         ms64 = []
         for _ in range(args.fp64_steps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            s64 = step(o=o64, counts=out64)
+            s64 = step(o=o64, counts=out64, structure="grid")
             b.record(stream)
             torch.cuda.synchronize()
             ms64.append(a.elapsed_time(b))
@@ -371,6 +406,38 @@ def run_ours(args):
                 "cell_size": o64.cell_size,
                 "ms_per_step": statistics.mean(ms64), "steps": args.fp64_steps,
                 "counts_identical_to_fp32_rescue": exact}
+
+    # ---- the k-d tree path on the same catalogue (grid line only) -----------
+    kd = None
+    if not tree and args.tree_steps > 0 and world == 1:
+        t0 = time.perf_counter()
+        o_kd, cap_kd, _ = P.pc_tune_tree(D, box=box, bins=bins, n_leaf=args.n_leaf, stream=stream)
+        tune_s = time.perf_counter() - t0
+        out_kd = torch.zeros_like(out)
+
+        def kd_step():
+            t = P.pc_build_tree(D, box=box, n_leaf=args.n_leaf, list_cap=cap_kd, stream=stream)
+            try:
+                P.pc_count_tree(t, None, bins, o_kd, stream, counts=out_kd)
+            finally:
+                t.free()
+        kd_step()
+        torch.cuda.synchronize()
+        kd_ms = []
+        for _ in range(args.tree_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            kd_step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            kd_ms.append(a.elapsed_time(b))
+        kd = {"value": float(out_kd.sum().item()) / (statistics.mean(kd_ms) * 1e-3), "unit": UNIT,
+              "ms_per_step": statistics.mean(kd_ms), "steps": args.tree_steps,
+              "step": "tree build + dual-tree traversal + pair and rescue kernels",
+              "list_cap": cap_kd or "auto", "ipt": o_kd.ipt, "n_leaf": args.n_leaf,
+              "tuning_seconds": tune_s,
+              "counts_identical_to_grid": bool(torch.equal(out_kd, out))}
 
     # ---- roofline of the dominant kernel -------------------------------------
     peaks, peak_src = measured_peaks()
@@ -386,7 +453,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
                 "traffic": (trec["bytes_per_launch"] if trec else None),
-                "kernel": "k_pairs_f32<SMU,LOS_Z>",
+                "kernel": "k_pairs_f32<SMU,LOS_Z>" + (" (tree variant)" if tree else ""),
                 "flops_per_launch": flops,
                 "flops_definition": (f"{FLOPS_PER_CANDIDATE} per pair evaluated one by one "
                                      f"({evaluated:.4g}) + {FLOPS_PER_IN_RANGE} per in-range "
@@ -422,14 +489,22 @@ def run_ours(args):
                                       if world > 1 else "1 GPU",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "unit_of_work": "in-range pairs binned (each pair in exactly one bin)",
+                       "structure": ("k-d tree (leaf capacity %d, list nodes %s), dual-tree "
+                                     "traversal" % (args.n_leaf, list_cap or "auto"))
+                                    if tree else "regular grid",
                        "cell_size": s0.cell_size, "ipt": opts.ipt, "priv": opts.priv,
                        "tuning": tuning,
+                       "tree": ({"node_pairs": int(s0.tree_pairs), "blocks": int(s0.blocks),
+                                 "ms_build": statistics.mean(tree_ms[-args.steps:]),
+                                 "ms_traverse": s0.ms_traverse,
+                                 "largest_list_node_extent": s0.cell_size} if tree else None),
                        "in_range_pairs": int(counts.sum()),
                        "candidates_per_step": int(s0.candidates),
                        "pruned_per_step": int(s0.pruned)},
             "candidate_pairs_per_s": cand_all / (t_max * 1e-3),
             "rescued_fraction": s0.rescued / max(1, int(counts.sum())),
             "fp64_path": fp64,
+            "kdtree_path": kd,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -605,7 +680,17 @@ def run_sets(args):
         box = P.make_box(None, False, lo, hi)
     big = max(names, key=lambda k: host[k][0].shape[0])
     tuning = None
-    if args.cell_size > 0 or args.ipt > 0:
+    tree = args.structure == "kdtree"
+    list_cap = args.list_cap
+    if tree and (args.list_cap > 0 or args.ipt > 0):
+        opts = P.make_opts("f32", 0.0, args.ipt or 2)
+    elif tree:
+        t0 = time.perf_counter()
+        opts, list_cap, trials = P.pc_tune_tree(devc[big][0], devc[big][1], box=box, bins=bins,
+                                                n_leaf=args.n_leaf, stream=stream)
+        tuning = {"seconds": time.perf_counter() - t0, "on": big,
+                  "trials": [{"list_cap": c, "ipt": i, "ms": round(ms, 3)} for c, i, ms in trials]}
+    elif args.cell_size > 0 or args.ipt > 0:
         opts = P.make_opts("f32", args.cell_size, args.ipt)
     else:
         t0 = time.perf_counter()
@@ -619,14 +704,22 @@ def run_sets(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step(cats=devc, results=outs):
-        gs = {k: P.pc_build_grid(x, wt, box=box, r_max=bins.r_max, opts=opts, stream=stream)
-              for k, (x, wt) in cats.items()}
+        if tree:
+            gs = {k: P.pc_build_tree(x, wt, box=box, n_leaf=args.n_leaf, list_cap=list_cap,
+                                     stream=stream)
+                  for k, (x, wt) in cats.items()}
+        else:
+            gs = {k: P.pc_build_grid(x, wt, box=box, r_max=bins.r_max, opts=opts, stream=stream)
+                  for k, (x, wt) in cats.items()}
         stats = {}
         try:
             for kind in kinds:
                 a, b = gs[kind[0]], gs[kind[1]]
                 c, wc = results[kind]
-                if kind[0] == kind[1]:
+                if tree:
+                    _, _, st = P.pc_count_tree(a, None if kind[0] == kind[1] else b, bins, opts,
+                                               stream, counts=c, wcounts=wc)
+                elif kind[0] == kind[1]:
                     _, _, st = P.pc_count_auto(a, bins, opts, stream, counts=c, wcounts=wc)
                 else:
                     _, _, st = P.pc_count_cross(a, b, bins, opts, stream, counts=c, wcounts=wc)
@@ -699,11 +792,14 @@ def run_sets(args):
                    "precision": "FP32 separations, binary64 rescue near bin edges, int64 counts, "
                                 "binary64 weighted sums",
                    "unit_of_work": "in-range pairs binned over all pair kinds",
+                   "structure": ("k-d tree (leaf capacity %d, list nodes %s), dual-tree traversal"
+                                 % (args.n_leaf, list_cap or "auto")) if tree else "regular grid",
                    "cell_size": opts.cell_size, "ipt": opts.ipt, "priv": opts.priv,
                    "tuning": tuning, "l2": "flushed between timed steps (256 MiB write)"},
         "per_kind": {k: {"in_range_pairs": inr[k], "ms_pairs": stats[k].ms_pairs,
                          "ms_total": stats[k].ms_total, "candidates": stats[k].candidates,
                          "pruned": stats[k].pruned, "rescued": stats[k].rescued,
+                         "node_pairs": stats[k].tree_pairs if tree else None,
                          "prec": "f32+rescue" if stats[k].prec == 0 else "f64"} for k in kinds},
         "roofline": None,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),

@@ -122,7 +122,7 @@ typedef struct {
                                     weight a non-negative normal binary32 value or zero and
                                     the two grids' weight exponents spanning at most 12;
                                     truncation below 2^-34 relative), flushed in binary64 */
-    long long tree_pairs;        /* pc_count_tree: block pairs listed by the traversal */
+    long long tree_pairs;        /* pc_count_tree: list node pairs listed by the traversal */
     float ms_traverse;           /* pc_count_tree: device-and-host time of the traversal */
 } pc_stats;
 
@@ -234,24 +234,31 @@ typedef struct pc_tree pc_tree;  /* opaque; owned by the library */
  * hold the same share of the points to within one; every node keeps the
  * minimum bounding box (AABB) of its points.  Points are stored in tree order
  * (every node contiguous) as FP64 canonical coordinates and FP32 offsets from
- * the centre of their block, the tree level whose nodes hold at most 256
- * points.
+ * the centre of their node at the list level: the level whose nodes the
+ * traversal pairs and the pair kernel splits into balanced blocks of at most
+ * 256 points.
  *   xyz, w, w_is_f32, n   as for pc_build_grid; n >= 1
  *   box                   periodic and L as for pc_build_grid (lo / hi are
  *                         not used: the tree bounds its own points)
  *   n_leaf                leaf capacity, 1..128
+ *   list_cap              0: the list level is chosen among the levels whose
+ *                         nodes hold 256..2048 points, for the fewest idle
+ *                         lanes in the 256-point blocks; else a power of two
+ *                         in [256, 65536]: the first level whose nodes hold at
+ *                         most list_cap points
  *   stream                cudaStream_t; returns once the tree is built
  *   out                   the new tree; release it with pc_free_tree
- * Errors: PC_EINVAL (NULL pointers, n < 1, bad n_leaf, bad box, non-finite
- * coordinates), PC_EOVERFLOW (n >= 2^31, more than 2^28 heap slots),
- * PC_ENOMEM, PC_ECUDA. */
+ * Errors: PC_EINVAL (NULL pointers, n < 1, bad n_leaf or list_cap, bad box,
+ * non-finite coordinates), PC_EOVERFLOW (n >= 2^31, more than 2^28 heap
+ * slots), PC_ENOMEM, PC_ECUDA. */
 pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f32, long long n,
-                        const pc_box *box, int n_leaf, void *stream, pc_tree **out);
+                        const pc_box *box, int n_leaf, int list_cap, void *stream,
+                        pc_tree **out);
 
 /* Release a tree (NULL is ignored). */
 void pc_free_tree(pc_tree *t);
 
-/* Size of a tree (any output may be NULL): points, deepest level, block
+/* Size of a tree (any output may be NULL): points, deepest level, list
  * level, heap slots 2^(depth + 1) - 1. */
 pc_status pc_tree_info(const pc_tree *t, long long *n, int *depth, int *block_level,
                        long long *slots);
@@ -270,22 +277,39 @@ pc_status pc_tree_export(const pc_tree *t, long long *start, long long *count, i
  * (t2 == NULL; unordered pairs) or cross counts of t1 x t2.  Node pairs
  * whose boxes lie farther apart than the largest separation (or, for s and
  * (s, mu) bins, all of whose pairs are closer than the first edge) are
- * dropped; the rest descend to pairs of block nodes, whose points are
+ * dropped; the rest descend to pairs of list nodes, whose points are
  * evaluated by the same FP32 + binary64-rescue kernels as the grid path, so
  * the results follow the same exact definition.  Periodic boxes: every node
  * pair is taken under each periodic image of the second node.
- *   counts, wcounts, st   as for pc_count_auto (st adds tree_pairs and
- *                         ms_traverse; cell_size reports the largest block
- *                         extent)
- *   o                     prec, priv, rescue_capacity and grid_ctas_per_sm
- *                         apply; ipt is 2
+ *   counts, wcounts, st   as for pc_count_auto (st adds tree_pairs, the list
+ *                         node pairs, and ms_traverse; cell_size reports the
+ *                         largest list node extent)
+ *   o                     prec, ipt (2 or 4; blocks of at most 128 ipt points,
+ *                         each list node split into equal blocks), priv,
+ *                         rescue_capacity, grid_ctas_per_sm and the block
+ *                         shards (shard_index of shard_count) apply
  * Errors: PC_EINVAL (trees of different boxes or devices, missing weights,
  * bad bins, a periodic separation of L/2 or more), PC_EUNSUPPORTED (plain
  * FP64 asked for, or forced by a midpoint line of sight too close to the
- * observer; block shards), PC_EOVERFLOW, PC_ENOMEM, PC_ECUDA. */
+ * observer), PC_EOVERFLOW, PC_ENOMEM, PC_ECUDA. */
 pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const pc_bins *b,
                         const pc_opts *o, void *stream, long long *counts, double *wcounts,
                         pc_stats *st);
+
+/* Measured options of the k-d tree path for the auto count of a catalogue:
+ * builds the tree (leaf capacity n_leaf) with the automatic list level and
+ * with list nodes of at most 512, 1024, 2048 and 4096 points (distinct levels
+ * only), times the pair and rescue kernels for 2 and 4 i-points per thread
+ * on every S-th block (S as in pc_tune), and writes the fastest: out->ipt
+ * (base's other fields kept) and *list_cap for pc_build_tree; the automatic
+ * level with 2 i-points is kept unless another option is more than 3 %
+ * faster.  trials (cell_size holds the list_cap tried, 0 = automatic) and
+ * n_trials as for pc_tune.
+ * Errors as pc_build_tree and pc_count_tree. */
+pc_status pc_tune_tree(const double *xyz, const void *w, int w_is_f32, long long n,
+                       const pc_box *box, const pc_bins *b, int n_leaf, const pc_opts *base,
+                       void *stream, pc_opts *out, int *list_cap, pc_tune_trial *trials,
+                       int max_trials, int *n_trials);
 
 /* Bounding box of n points (n x 3 binary64, host or device) -- the first of
  * the three grid-build passes of Sect. 2.1.  lo/hi are host arrays of 3. */

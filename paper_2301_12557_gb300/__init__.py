@@ -74,7 +74,8 @@ _lib = None
 EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc_count_cross",
            "pc_count_batch", "pc_aabb", "pc_suggest_cell_size", "pc_strerror", "pc_last_error",
            "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune",
-           "pc_build_tree", "pc_free_tree", "pc_tree_info", "pc_tree_export", "pc_count_tree"]
+           "pc_build_tree", "pc_free_tree", "pc_tree_info", "pc_tree_export", "pc_count_tree",
+           "pc_tune_tree"]
 
 
 def library_path() -> str:
@@ -133,7 +134,7 @@ def lib():
     L.pc_count_auto_noalloc.restype = c_int
     L.pc_count_auto_noalloc.argtypes = [vp, POINTER(pc_bins), POINTER(pc_opts), vp, vp, vp]
     L.pc_build_tree.restype = c_int
-    L.pc_build_tree.argtypes = [vp, vp, c_int, c_longlong, POINTER(pc_box), c_int, vp,
+    L.pc_build_tree.argtypes = [vp, vp, c_int, c_longlong, POINTER(pc_box), c_int, c_int, vp,
                                 POINTER(vp)]
     L.pc_free_tree.restype = None
     L.pc_free_tree.argtypes = [vp]
@@ -142,6 +143,10 @@ def lib():
                                POINTER(c_longlong)]
     L.pc_tree_export.restype = c_int
     L.pc_tree_export.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.pc_tune_tree.restype = c_int
+    L.pc_tune_tree.argtypes = [vp, vp, c_int, c_longlong, POINTER(pc_box), POINTER(pc_bins), c_int,
+                               POINTER(pc_opts), vp, POINTER(pc_opts), POINTER(c_int),
+                               POINTER(pc_tune_trial), c_int, POINTER(c_int)]
     L.pc_count_tree.restype = c_int
     L.pc_count_tree.argtypes = [vp, vp, POINTER(pc_bins), POINTER(pc_opts), vp, vp, vp,
                                 POINTER(pc_stats)]
@@ -429,7 +434,7 @@ class Tree:
         self.n = n
 
     def info(self):
-        """(points, depth, block level, heap slots)."""
+        """(points, depth, list level, heap slots)."""
         return pc_tree_info(self)
 
     def free(self):
@@ -456,15 +461,35 @@ def _weights_arg(w, n):
     return pw, keep_w, 1 if is32 else 0
 
 
-def pc_build_tree(xyz, w=None, *, box: pc_box, n_leaf: int = 32, stream=None) -> Tree:
+def pc_build_tree(xyz, w=None, *, box: pc_box, n_leaf: int = 32, list_cap: int = 0,
+                  stream=None) -> Tree:
     """k-d tree of Alg. 1 built on the GPU (see paircount.h)."""
     px, keep_x, n = _ptr(xyz, np.float64, 3)
     pw, keep_w, w_is_f32 = _weights_arg(w, n)
     out = c_void_p()
     _check(lib().pc_build_tree(px, pw, w_is_f32, n, ctypes.byref(box), int(n_leaf),
-                               _stream_handle(stream), ctypes.byref(out)), "pc_build_tree")
+                               int(list_cap), _stream_handle(stream), ctypes.byref(out)),
+           "pc_build_tree")
     del keep_x, keep_w
     return Tree(out, n)
+
+
+def pc_tune_tree(xyz, w=None, *, box: pc_box, bins: Bins, n_leaf: int = 32,
+                 opts: pc_opts | None = None, stream=None, max_trials: int = 16):
+    """Measured list level and i-points per thread of the tree path; returns
+    (pc_opts with ipt, list_cap, list of (list_cap, ipt, ms))."""
+    px, keep_x, n = _ptr(xyz, np.float64, 3)
+    pw, keep_w, w_is_f32 = _weights_arg(w, n)
+    out = pc_opts()
+    cap = c_int(0)
+    trials = (pc_tune_trial * max_trials)()
+    nt = c_int(0)
+    _check(lib().pc_tune_tree(px, pw, w_is_f32, n, ctypes.byref(box), ctypes.byref(bins.s),
+                              int(n_leaf), ctypes.byref(opts) if opts is not None else None,
+                              _stream_handle(stream), ctypes.byref(out), ctypes.byref(cap), trials,
+                              max_trials, ctypes.byref(nt)), "pc_tune_tree")
+    del keep_x, keep_w
+    return out, cap.value, [(int(t.cell_size), t.ipt, t.ms) for t in trials[:nt.value]]
 
 
 def pc_free_tree(t: Tree):
@@ -492,7 +517,7 @@ def pc_tree_export(t: Tree) -> dict:
     order = np.zeros(n, dtype=np.int64)
     _check(lib().pc_tree_export(t.handle, start.ctypes.data, count.ctypes.data, axis.ctypes.data,
                                 bx.ctypes.data, order.ctypes.data), "pc_tree_export")
-    return {"depth": depth, "block_level": blevel, "start": start, "count": count,
+    return {"depth": depth, "list_level": blevel, "start": start, "count": count,
             "axis": axis, "box": bx, "ord": order}
 
 
@@ -570,21 +595,23 @@ def count(x1, x2=None, *, w1=None, w2=None, box=None, periodic=False, mode="s", 
 
 
 def count_tree(x1, x2=None, *, w1=None, w2=None, box=None, periodic=False, mode="s", los="z",
-               edges_a, edges_b=None, n_leaf=32, priv=-1, rescue_capacity=0, weighted=None,
-               stream=None, return_stats=False):
+               edges_a, edges_b=None, n_leaf=32, list_cap=0, ipt=2, priv=-1, rescue_capacity=0,
+               weighted=None, stream=None, return_stats=False):
     """Auto (x2 None) or cross pair counts through the k-d tree path (build
     the trees, count, free); same results as ``count``."""
     bins = Bins(mode, los, edges_a, edges_b)
     if weighted is None:
         weighted = w1 is not None
-    opts = make_opts("f32", 0.0, 2, priv, rescue_capacity)
+    opts = make_opts("f32", 0.0, ipt, priv, rescue_capacity)
     b = make_box(box, True) if periodic else make_box(None, False)
-    t1 = pc_build_tree(x1, w1 if weighted else None, box=b, n_leaf=n_leaf, stream=stream)
+    t1 = pc_build_tree(x1, w1 if weighted else None, box=b, n_leaf=n_leaf, list_cap=list_cap,
+                       stream=stream)
     try:
         if x2 is None:
             c, wc, st = pc_count_tree(t1, None, bins, opts, stream, weighted=weighted)
         else:
-            t2 = pc_build_tree(x2, w2 if weighted else None, box=b, n_leaf=n_leaf, stream=stream)
+            t2 = pc_build_tree(x2, w2 if weighted else None, box=b, n_leaf=n_leaf,
+                               list_cap=list_cap, stream=stream)
             try:
                 c, wc, st = pc_count_tree(t1, t2, bins, opts, stream, weighted=weighted)
             finally:

@@ -803,8 +803,8 @@ static pc_status enqueue_count(const CountSetup &S, const DevBufs &B, const Pair
     if (S.weighted) PC_CUDA(cudaMemsetAsync(B.whist, 0, sizeof(double) * S.hist_n, st));
     PC_CUDA(cudaMemsetAsync(B.ctr, 0, sizeof(unsigned long long) * 4, st));
     PC_CUDA(cudaMemsetAsync(B.sc, 0, sizeof(int) * 4, st));
-    if (blk_tree)   // tree count: one block per i-block node
-        PC_CUDA(tree_blocks(blk_tree, B.blocks, B.sc + 1, st));
+    if (blk_tree)   // tree count: balanced blocks of the list nodes
+        PC_CUDA(tree_blocks(blk_tree, S.ipt, B.blocks, B.sc + 1, st));
     else
         PC_CUDA(make_blocks_into(B.tasks, S.ntasks, S.ncell, S.bi, B.blocks, B.sc + 1, B.cnt,
                                  B.off, B.tot, st));
@@ -1213,7 +1213,6 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
     }
     J.rmin = std::min(tree_rmin(t1), tree_rmin(tj));
     J.device = t1->device;
-    J.ncell = 1 << t1->blevel;
     J.cell_size = cb;
     if (!t1->wint || !tj->wint ||
         (t1->wemax - t1->wemin) + (tj->wemax - tj->wemin) > WINT_MAX_SPAN)
@@ -1223,9 +1222,8 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
     memset(&o, 0, sizeof(o));
     o.priv = -1;
     if (opt) o = *opt;
-    o.ipt = 2;
-    if (o.shard_count > 1)
-        return fail(PC_EUNSUPPORTED, "pc_count_tree: block shards are a grid-path option");
+    o.ipt = (o.ipt == 4) ? 4 : 2;
+    J.ncell = (1 << t1->blevel) * tree_chunks(t1, o.ipt);   // i-blocks (buffer sizes)
     CountSetup S;
     pc_status s = setup_count(J, b, &o, wcounts != nullptr, S);
     if (s != PC_OK) return s;

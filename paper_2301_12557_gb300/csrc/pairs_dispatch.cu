@@ -9,8 +9,8 @@ namespace pc {
     cudaError_t launch_f64_##tag(const PairParams &, int, size_t, cudaStream_t);            \
     int occ_f64_##tag(const PairParams &, size_t);                                          \
     cudaError_t launch_rescue_##tag(const PairParams &, int, cudaStream_t);                \
-    cudaError_t launch_f32t_##tag(const PairParams &, int, size_t, cudaStream_t);          \
-    int occ_f32t_##tag(const PairParams &, size_t);
+    cudaError_t launch_f32t_##tag(const PairParams &, int, int, size_t, cudaStream_t);     \
+    int occ_f32t_##tag(const PairParams &, int, size_t);
 PC_DECL(S)
 PC_DECL(SMU_Z)
 PC_DECL(SMU_MID)
@@ -30,11 +30,11 @@ size_t pairs_f64_smem(const PairParams &p) { return smem_layout(p, true).total; 
 cudaError_t launch_pairs_f32(const PairParams &p, int ipt, int grid, size_t smem, cudaStream_t st) {
     if (p.tree) {
         switch (variant(p)) {
-            case 0: return launch_f32t_S(p, grid, smem, st);
-            case 1: return launch_f32t_SMU_Z(p, grid, smem, st);
-            case 2: return launch_f32t_SMU_MID(p, grid, smem, st);
-            case 3: return launch_f32t_SIGPI_Z(p, grid, smem, st);
-            default: return launch_f32t_SIGPI_MID(p, grid, smem, st);
+            case 0: return launch_f32t_S(p, ipt, grid, smem, st);
+            case 1: return launch_f32t_SMU_Z(p, ipt, grid, smem, st);
+            case 2: return launch_f32t_SMU_MID(p, ipt, grid, smem, st);
+            case 3: return launch_f32t_SIGPI_Z(p, ipt, grid, smem, st);
+            default: return launch_f32t_SIGPI_MID(p, ipt, grid, smem, st);
         }
     }
     switch (variant(p)) {
@@ -49,11 +49,11 @@ cudaError_t launch_pairs_f32(const PairParams &p, int ipt, int grid, size_t smem
 int pairs_f32_ctas_per_sm(const PairParams &p, int ipt, size_t smem) {
     if (p.tree) {
         switch (variant(p)) {
-            case 0: return occ_f32t_S(p, smem);
-            case 1: return occ_f32t_SMU_Z(p, smem);
-            case 2: return occ_f32t_SMU_MID(p, smem);
-            case 3: return occ_f32t_SIGPI_Z(p, smem);
-            default: return occ_f32t_SIGPI_MID(p, smem);
+            case 0: return occ_f32t_S(p, ipt, smem);
+            case 1: return occ_f32t_SMU_Z(p, ipt, smem);
+            case 2: return occ_f32t_SMU_MID(p, ipt, smem);
+            case 3: return occ_f32t_SIGPI_Z(p, ipt, smem);
+            default: return occ_f32t_SIGPI_MID(p, ipt, smem);
         }
     }
     switch (variant(p)) {

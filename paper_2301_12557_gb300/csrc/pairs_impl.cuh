@@ -1176,19 +1176,34 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
         // ---- phase B: j-segments, in chunks ---------------------------------
         // grid: the stencil rows, ROWCHUNK at a time; tree: the i-block's list
         // of (j-block, image) pairs, MAXSEG at a time
-        const int ts0 = TREE ? p.tseg_off[B.cell] : 0;
-        const int ts1 = TREE ? p.tseg_off[B.cell + 1] : 0;
-        const int nchunk = TREE ? (ts1 - ts0 + MAXSEG - 1) / MAXSEG
-                                : (p.nrows + ROWCHUNK - 1) / ROWCHUNK;
+        // tree: virtual segment 0 of an auto count is the rest of the i-node
+        // after this block (same node, no offset), then the listed nodes
+        int ts0 = 0, tvirt = 0, trest = 0, node_end = 0;
+        if constexpr (TREE) {
+            ts0 = p.tseg_off[B.cell];
+            if (T.is_auto) {
+                const int2 r = p.tblk_j[B.cell];
+                node_end = r.x + r.y;
+                trest = (node_end > B.start + B.count) ? 1 : 0;
+            }
+            tvirt = p.tseg_off[B.cell + 1] - ts0 + trest;
+        }
+        const int nchunk = TREE ? (tvirt + MAXSEG - 1) / MAXSEG : (p.nrows + ROWCHUNK - 1) / ROWCHUNK;
         for (int ch = 0; ch < nchunk; ++ch) {
             if constexpr (TREE) {
-                // segment k: the j-block's points, staged relative to the
-                // i-block's centre through the offset of the two centres
-                const int c0 = ts0 + ch * MAXSEG;
-                const int ns = min(MAXSEG, ts1 - c0);
+                // segment k: a listed j-node's points, staged relative to the
+                // i-node's centre through the offset of the two centres
+                const int v0 = ch * MAXSEG;
+                const int ns = min(MAXSEG, tvirt - v0);
                 const double *ci = p.tcen_i + 3 * (size_t)B.cell;
                 for (int k = tid; k < ns; k += NT) {
-                    const int2 e = p.tseg[c0 + k];
+                    const int v = v0 + k;
+                    if (v < trest) {
+                        s_soff[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        s_seg[k] = make_int4(B.start + B.count, node_end - B.start - B.count, k, 13);
+                        continue;
+                    }
+                    const int2 e = p.tseg[ts0 + v - trest];
                     const int2 r = p.tblk_j[e.x];
                     const double *cj = p.tcen_j + 3 * (size_t)e.x;
                     const double sx = (double)(e.y / 9 - 1), sy = (double)((e.y / 3) % 3 - 1),
@@ -1510,18 +1525,23 @@ PairKernel<MODE, LOS> pick_f32(const PairParams &p, int ipt) {
     return lin ? k_pairs_f32<MODE, LOS, 0, 2, LINOK> : k_pairs_f32<MODE, LOS, 0, 2, false>;
 }
 
-// Tree variant (2 i-points per thread, one thread group).
-template <int MODE, int LOS>
-PairKernel<MODE, LOS> pick_f32_tree(const PairParams &p) {
+// Tree variant (one thread group) for RI i-points per thread.
+template <int MODE, int LOS, int RI>
+PairKernel<MODE, LOS> pick_f32_tree_ri(const PairParams &p) {
     constexpr bool LINOK = (MODE == MODE_S) || (MODE == MODE_SMU && LOS == LOS_Z) || MODE == MODE_SIGPI;
     const bool lin = LINOK && p.lin;
     if (p.weighted) {
         if constexpr (LINOK) {
-            if (lin && p.wint) return k_pairs_f32<MODE, LOS, 2, 2, true, 1, true>;
+            if (lin && p.wint) return k_pairs_f32<MODE, LOS, 2, RI, true, 1, true>;
         }
-        return lin ? k_pairs_f32<MODE, LOS, 1, 2, LINOK, 1, true> : k_pairs_f32<MODE, LOS, 1, 2, false, 1, true>;
+        return lin ? k_pairs_f32<MODE, LOS, 1, RI, LINOK, 1, true> : k_pairs_f32<MODE, LOS, 1, RI, false, 1, true>;
     }
-    return lin ? k_pairs_f32<MODE, LOS, 0, 2, LINOK, 1, true> : k_pairs_f32<MODE, LOS, 0, 2, false, 1, true>;
+    return lin ? k_pairs_f32<MODE, LOS, 0, RI, LINOK, 1, true> : k_pairs_f32<MODE, LOS, 0, RI, false, 1, true>;
+}
+
+template <int MODE, int LOS>
+PairKernel<MODE, LOS> pick_f32_tree(const PairParams &p, int ipt) {
+    return ipt == 4 ? pick_f32_tree_ri<MODE, LOS, 4>(p) : pick_f32_tree_ri<MODE, LOS, 2>(p);
 }
 
 template <int MODE, int LOS>
@@ -1555,13 +1575,14 @@ int occupancy_mode_f32(const PairParams &p, int ipt, size_t smem) {
 }
 
 template <int MODE, int LOS>
-cudaError_t launch_mode_f32_tree(const PairParams &p, int grid, size_t smem, cudaStream_t st) {
-    return launch_kernel_f32<MODE, LOS>(pick_f32_tree<MODE, LOS>(p), p, grid, smem, st);
+cudaError_t launch_mode_f32_tree(const PairParams &p, int ipt, int grid, size_t smem,
+                                 cudaStream_t st) {
+    return launch_kernel_f32<MODE, LOS>(pick_f32_tree<MODE, LOS>(p, ipt), p, grid, smem, st);
 }
 
 template <int MODE, int LOS>
-int occupancy_mode_f32_tree(const PairParams &p, size_t smem) {
-    return occupancy_kernel_f32<MODE, LOS>(pick_f32_tree<MODE, LOS>(p), p, smem);
+int occupancy_mode_f32_tree(const PairParams &p, int ipt, size_t smem) {
+    return occupancy_kernel_f32<MODE, LOS>(pick_f32_tree<MODE, LOS>(p, ipt), p, smem);
 }
 
 template <int MODE, int LOS>

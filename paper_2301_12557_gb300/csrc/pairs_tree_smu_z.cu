@@ -3,11 +3,11 @@
 
 namespace pc {
 
-cudaError_t launch_f32t_SMU_Z(const PairParams &p, int grid, size_t smem, cudaStream_t st) {
-    return launch_mode_f32_tree<MODE_SMU, LOS_Z>(p, grid, smem, st);
+cudaError_t launch_f32t_SMU_Z(const PairParams &p, int ipt, int grid, size_t smem, cudaStream_t st) {
+    return launch_mode_f32_tree<MODE_SMU, LOS_Z>(p, ipt, grid, smem, st);
 }
-int occ_f32t_SMU_Z(const PairParams &p, size_t smem) {
-    return occupancy_mode_f32_tree<MODE_SMU, LOS_Z>(p, smem);
+int occ_f32t_SMU_Z(const PairParams &p, int ipt, size_t smem) {
+    return occupancy_mode_f32_tree<MODE_SMU, LOS_Z>(p, ipt, smem);
 }
 
 }  // namespace pc

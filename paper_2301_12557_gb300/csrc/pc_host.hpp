@@ -37,29 +37,31 @@ struct pc_tree {
     int weighted;
     int n_leaf;
     int depth;                  // deepest level (every node there: <= n_leaf points)
-    int blevel;                 // block level: its nodes hold at most TREE_BLOCK points
+    int blevel;                 // list level: its nodes carry the traversal's lists and the
+                                // origins of rel; a count splits each into balanced i-blocks
+    int lmax;                   // points of the largest list node
     long long nslots;           // 2^(depth + 1) - 1
     pc::Geom g;                 // periodic and L; c = largest block extent
     double pts_lo[3], pts_hi[3];
     double r2min = 0.0;         // non-periodic: lower bound of min |x|^2
     int wint = 0, wemax = 0, wemin = 0;   // as pc_grid
-    double bext = 0.0;          // largest extent (any axis) of a block node's box
-    float4 *rel;                // tree order: FP32 offset from the block centre, .w packed weight
+    double bext = 0.0;          // largest extent (any axis) of a list node's box
+    float4 *rel;                // tree order: FP32 offset from the list node's centre, .w packed weight
     double4_32a *xw;            // tree order: FP64 canonical coordinates, weight
     int *perm;                  // tree position -> input index
     int2 *vnode;                // every slot's range by the halving rule
     int2 *node;                 // {start, count} of present slots; count -1: empty slot
     double *nbox;               // lo[3], hi[3] per slot (present slots)
     signed char *naxis;         // split axis per slot, -1: leaf or empty
-    double *bcen;               // block centres, 3 per block
-    int2 *brng;                 // block ranges {start, count}
+    double *bcen;               // list node centres, 3 per node
+    int2 *brng;                 // list node ranges {start, count}
 };
 
 namespace pc {
 
-constexpr int TREE_BLOCK = 256;   // points per i-block (NT threads x 2 i-points)
+constexpr int TREE_BLOCK = 256;   // block size the automatic list level is chosen for (2 i-points)
 
-// Block pairs listed by the dual-tree traversal, grouped by i-block.
+// List-node pairs listed by the dual-tree traversal, grouped by i-node.
 struct TreeLists {
     const int2 *seg = nullptr;     // {j-block, image code}
     const int *seg_off = nullptr;  // i-block -> first entry (n_i-blocks + 1)
@@ -76,8 +78,11 @@ struct TreeLists {
 pc_status tree_traverse(const pc_tree *t1, const pc_tree *t2, bool is_auto, double r2hi,
                         double r2lo, cudaStream_t st, TreeLists &out);
 
-// The pair kernel's block list of a tree count (one block per i-block).
-cudaError_t tree_blocks(const pc_tree *t, Block *blocks, int *nblocks_dev, cudaStream_t st);
+// Balanced blocks per list node for ipt i-points per thread (NT * ipt points
+// per block at most), and the pair kernel's block list of a tree count.
+int tree_chunks(const pc_tree *t, int ipt);
+cudaError_t tree_blocks(const pc_tree *t, int ipt, Block *blocks, int *nblocks_dev,
+                        cudaStream_t st);
 
 // Weight checks for the integer weight path: r[0] counts weights that are
 // not a non-negative normal binary32 value or zero, r[1] / r[2] the largest /

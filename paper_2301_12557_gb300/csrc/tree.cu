@@ -1,6 +1,7 @@
 // k-d tree on the GPU (Sect. 2.2, Alg. 1) and the dual-tree traversal
-// (Sect. 3.1, Alg. 3) that lists, for every i-block, the j-blocks (and
-// periodic images) whose bounding boxes come within the largest separation.
+// (Sect. 3.1, Alg. 3) that lists, for every node of the list level, the
+// nodes of that level (and periodic images) whose bounding boxes come within
+// the largest separation.
 //
 // The tree is balanced (a split gives the left child floor(n / 2) points),
 // so the nodes are kept in heap order: slot 0 is the root and the children
@@ -322,8 +323,8 @@ __global__ void k_nid_next(const int2 *__restrict__ vnode, int n, int level, int
     nid[i] = 2 * k + ((i - v.x) >= v.y / 2 ? 1 : 0);
 }
 
-// Block centres (midpoints of the block nodes' boxes), block ranges and the
-// largest block extent (as an order-preserving key).
+// List node centres (midpoints of their boxes), ranges and the largest
+// extent (as an order-preserving key).
 __global__ void k_block_info(const double *__restrict__ box, const int2 *__restrict__ vnode, int blevel,
                              double *__restrict__ cen, int2 *__restrict__ rng,
                              long long *__restrict__ ext_key) {
@@ -347,7 +348,7 @@ __device__ __forceinline__ unsigned pack_weight_t(double wv, int emax) {
     return ((unsigned)(emax - e) << 24) | (b & 0x7FFFFFu) | 0x800000u;
 }
 
-// Point records in tree order: FP32 offset from the block centre (.w the
+// Point records in tree order: FP32 offset from the list node's centre (.w the
 // packed integer weight or 0), FP64 canonical coordinates and weight.
 __global__ void k_tree_scatter(const double *__restrict__ x, const void *__restrict__ w, int w_is_f32,
                                int wpack_emax, const unsigned *__restrict__ perm,
@@ -395,11 +396,11 @@ __device__ __forceinline__ void push_pairs(int2 *out, int *n_out, const int2 *v,
 
 // A node pair {a, b | image << 24}: dropped when the boxes (b shifted by
 // the image) are farther apart than the largest separation or all pairs
-// are closer than the smallest; listed when both are block nodes (an auto
-// count leaves a block paired with itself to the pair kernel's own-block
-// pass, and lists the pair from the side that balances the blocks' loads);
+// are closer than the smallest; listed when both are list nodes (an auto
+// count leaves a node paired with itself to the pair kernel's own-node
+// pass, and lists the pair from the side that balances the nodes' loads);
 // otherwise split into the children pairs (a node paired with itself into
-// (left, left), (left, right), (right, right)).  Splits stop at the block
+// (left, left), (left, right), (right, right)).  Splits stop at the list
 // level of each tree.
 __global__ void k_dual_level(const int2 *__restrict__ in, int n_in, int2 *__restrict__ out,
                              int *n_out, int2 *__restrict__ emit, int *n_emit,
@@ -458,8 +459,8 @@ __global__ void k_dual_level(const int2 *__restrict__ in, int n_in, int2 *__rest
     }
 }
 
-// Group the listed block pairs by i-block: counts, then (after a scan) the
-// entries {j-block, image}; the order inside a group is arbitrary.
+// Group the listed node pairs by i-node: counts, then (after a scan) the
+// entries {j-node, image}; the order inside a group is arbitrary.
 __global__ void k_group_count(const int2 *__restrict__ emit, int ne, int blk0, int *__restrict__ cnt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < ne) atomicAdd(&cnt[emit[i].x - blk0], 1);
@@ -473,13 +474,17 @@ __global__ void k_group_fill(const int2 *__restrict__ emit, int ne, int blk0_i, 
     seg[pos] = make_int2((e.y & 0xFFFFFF) - blk0_j, e.y >> 24);
 }
 
-// The pair kernel's blocks: one per i-block ("cell" = i-block index).
-__global__ void k_tree_blocks(const int2 *__restrict__ rng, int nblk, Block *__restrict__ blocks,
-                              int *__restrict__ nblocks) {
+// The pair kernel's blocks: every list node split into k balanced chunks of
+// at most TREE_BLOCK points ("cell" = the list node).
+__global__ void k_tree_blocks(const int2 *__restrict__ rng, int nlist, int k,
+                              Block *__restrict__ blocks, int *__restrict__ nblocks) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b == 0) *nblocks = nblk;
-    if (b >= nblk) return;
-    blocks[b] = Block{0, b, rng[b].x, rng[b].y};
+    if (b == 0) *nblocks = nlist * k;
+    if (b >= nlist * k) return;
+    const int node = b / k, c = b % k;
+    const int2 r = rng[node];
+    const int s0 = r.x + (int)((long long)r.y * c / k), s1 = r.x + (int)((long long)r.y * (c + 1) / k);
+    blocks[b] = Block{0, node, s0, s1 - s0};
 }
 
 // Growable device array of the traversal workspace (reused across calls;
@@ -563,7 +568,7 @@ pc_status tree_traverse(const pc_tree *t1, const pc_tree *t2, bool is_auto, doub
         swap_arr(W.la, W.lb);
         ++levels;
     }
-    // group by i-block
+    // group by i-node
     const int nbi = 1 << t1->blevel;
     const int blk0_i = nbi - 1, blk0_j = (1 << t2->blevel) - 1;
     const size_t ne = (size_t)n_emit;
@@ -594,11 +599,52 @@ pc_status tree_traverse(const pc_tree *t1, const pc_tree *t2, bool is_auto, doub
     return PC_OK;
 }
 
-cudaError_t tree_blocks(const pc_tree *t, Block *blocks, int *nblocks_dev, cudaStream_t st) {
-    const int nb = 1 << t->blevel;
-    k_tree_blocks<<<(nb + 255) / 256, 256, 0, st>>>(t->brng, nb, blocks, nblocks_dev);
+int tree_chunks(const pc_tree *t, int ipt) {
+    const int cap = NT * ipt;
+    return std::max(1, (t->lmax + cap - 1) / cap);
+}
+
+cudaError_t tree_blocks(const pc_tree *t, int ipt, Block *blocks, int *nblocks_dev,
+                        cudaStream_t st) {
+    const int nl = 1 << t->blevel;
+    const int k = tree_chunks(t, ipt);
+    const int nb = nl * k;
+    k_tree_blocks<<<(nb + 255) / 256, 256, 0, st>>>(t->brng, nl, k, blocks, nblocks_dev);
     note_launch();
     return cudaGetLastError();
+}
+
+// Points of the largest node of level d (the halving rule).
+static long long level_largest(long long n, int d) {
+    long long m = n;
+    for (int k = 0; k < d; ++k) m = (m + 1) / 2;
+    return m;
+}
+
+// List level: the level whose nodes carry the traversal's lists and the
+// origins of the FP32 offsets.  cap > 0: the first level whose nodes hold at
+// most cap points; cap = 0: among the levels whose largest node holds 129 to
+// 2048 points, the one whose nodes split into TREE_BLOCK-point blocks with
+// the fewest idle i-slots (the deepest on a tie; a catalogue of at most
+// TREE_BLOCK points: the root).
+static int list_level(long long n, int cap) {
+    int best = tree_depth(n, cap > 0 ? cap : TREE_BLOCK);
+    if (cap == 0) {
+        double bf = -1.0;
+        for (int d = 0; d <= 40; ++d) {
+            const long long m = level_largest(n, d);
+            if (m > 2048) continue;
+            if (m <= TREE_BLOCK / 2 && d > 0) break;
+            const long long k = (m + TREE_BLOCK - 1) / TREE_BLOCK;
+            const double fill = (double)n / (double)(1LL << d) / (double)(k * TREE_BLOCK);
+            if (fill >= bf - 1e-12) {
+                bf = fill;
+                best = d;
+            }
+            if (m <= TREE_BLOCK) break;
+        }
+    }
+    return best;
 }
 
 }  // namespace pc
@@ -665,7 +711,8 @@ extern "C" pc_status pc_tree_export(const pc_tree *t, long long *start, long lon
 }
 
 extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f32, long long n,
-                                   const pc_box *box, int n_leaf, void *stream, pc_tree **out) {
+                                   const pc_box *box, int n_leaf, int list_cap, void *stream,
+                                   pc_tree **out) {
     std::lock_guard<std::mutex> lk(api_mutex());
     if (!out) return fail(PC_EINVAL, "pc_build_tree: out is NULL");
     *out = nullptr;
@@ -674,8 +721,10 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
     if (!xyz) return fail(PC_EINVAL, "pc_build_tree: xyz is NULL");
     if (n >= (1LL << 31) - 1) return fail(PC_EOVERFLOW, "pc_build_tree: n must be below 2^31");
     if (n_leaf < 1 || n_leaf > 128) return fail(PC_EINVAL, "pc_build_tree: n_leaf must lie in [1, 128]");
+    if (list_cap != 0 && (list_cap < TREE_BLOCK || list_cap > 65536 || (list_cap & (list_cap - 1))))
+        return fail(PC_EINVAL, "pc_build_tree: list_cap must be 0 or a power of two in [256, 65536]");
     const int depth = tree_depth(n, n_leaf);
-    const int blevel = tree_depth(n, TREE_BLOCK);
+    const int blevel = std::min(list_level(n, list_cap), depth);
     if (depth > 27) return fail(PC_EOVERFLOW, "pc_build_tree: more than 2^28 tree slots");
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
@@ -689,6 +738,7 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
     t->n_leaf = n_leaf;
     t->depth = depth;
     t->blevel = blevel;
+    t->lmax = (int)level_largest(n, blevel);
     t->nslots = (2LL << depth) - 1;
     Geom &G = t->g;
     G.periodic = box->periodic ? 1 : 0;
@@ -860,7 +910,7 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
             e = cudaGetLastError();
         }
     }
-    // blocks and point records
+    // list nodes and point records
     const int nblk = 1 << blevel;
     long long ext_init = LLONG_MIN, ext_key = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(ext, &ext_init, sizeof(long long), cudaMemcpyHostToDevice, st);

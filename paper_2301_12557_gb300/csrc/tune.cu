@@ -229,3 +229,108 @@ extern "C" pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, lon
     PC_CUDA(cudaStreamSynchronize(st));
     return PC_OK;
 }
+
+// Measured choice of the k-d tree path's options: the list level (through
+// the list-node capacity of pc_build_tree) and the i-points per thread,
+// timed like pc_tune on every S-th point block of the catalogue's auto count.
+// (pc_tune_trial.cell_size carries the list-node capacity tried.)
+extern "C" pc_status pc_tune_tree(const double *xyz, const void *w, int w_is_f32, long long n,
+                                  const pc_box *box, const pc_bins *b, int n_leaf,
+                                  const pc_opts *base, void *stream, pc_opts *out,
+                                  int *list_cap, pc_tune_trial *trials, int max_trials,
+                                  int *n_trials) {
+    if (n_trials) *n_trials = 0;
+    if (!box || !b || !out || !list_cap || n < 0 || (n > 0 && !xyz) || max_trials < 0 ||
+        (max_trials > 0 && !trials))
+        return fail(PC_EINVAL, "pc_tune_tree: bad arguments");
+    if (b->n_a < 1 || !b->edges_a || (b->mode != PC_BIN_S && (b->n_b < 1 || !b->edges_b)))
+        return fail(PC_EINVAL, "pc_tune_tree: bad bins");
+    pc_opts o;
+    memset(&o, 0, sizeof(o));
+    o.priv = -1;
+    if (base) o = *base;
+    *out = o;
+    out->ipt = 2;
+    *list_cap = 0;
+    if (n < 2) return PC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 1;
+    PC_CUDA(cudaGetDevice(&dev));
+    PC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int nbins = b->n_a * (b->mode == PC_BIN_S ? 1 : b->n_b);
+    DevBuf dc, dw;
+    PC_CUDA(cudaMalloc(&dc.p, sizeof(long long) * nbins));
+    if (w) PC_CUDA(cudaMalloc(&dw.p, sizeof(double) * nbins));
+
+    const double ctas = 5.0 * sms;
+    const double blocks_est = std::max(1.0, (double)n / (NT * 4));
+    const int S_min = std::max(1, (int)(blocks_est / (4.0 * ctas)));
+    const int S_max = std::max(S_min, (int)(blocks_est / (2.0 * ctas)));
+    const float TRIAL_MS = 40.f;
+    int S = S_min;
+    float best_ms = INFINITY;
+    int nt = 0;
+    auto run = [&](pc_tree *t, int ipt, float &ms) -> pc_status {
+        pc_opts ot = o;
+        ot.ipt = ipt;
+        ot.shard_index = 0;
+        ot.shard_count = S;
+        ms = INFINITY;
+        pc_status s = PC_OK;
+        for (int rep = 0; rep < 2 && s == PC_OK; ++rep) {
+            pc_stats sts;
+            s = pc_count_tree(t, nullptr, b, &ot, stream, (long long *)dc.p, (double *)dw.p, &sts);
+            if (s == PC_OK) ms = std::min(ms, sts.ms_pairs + sts.ms_rescue);
+            if (ms > 4.f * TRIAL_MS) break;
+        }
+        return s;
+    };
+    // list-node capacities: automatic, then 512 .. 4096 (distinct levels only);
+    // another option replaces the automatic level with 2 i-points only when
+    // it is faster by more than the trials' run-to-run spread (3 %)
+    float ms_default = INFINITY;
+    std::vector<int> seen_levels;
+    const int caps[] = {0, 512, 1024, 2048, 4096};
+    bool calibrated = false;
+    for (int cap : caps) {
+        pc_tree *t = nullptr;
+        pc_status s = pc_build_tree(xyz, w, w_is_f32, n, box, n_leaf, cap, stream, &t);
+        if (s != PC_OK) return s;
+        int depth = 0, lev = 0;
+        pc_tree_info(t, nullptr, &depth, &lev, nullptr);
+        if (std::find(seen_levels.begin(), seen_levels.end(), lev) != seen_levels.end()) {
+            pc_free_tree(t);
+            continue;
+        }
+        seen_levels.push_back(lev);
+        if (!calibrated) {   // sampling stride from one run at the automatic level
+            float ms = INFINITY;
+            s = run(t, 2, ms);
+            if (s != PC_OK) { pc_free_tree(t); return s; }
+            if (ms > TRIAL_MS)
+                S = std::min(S_max, (int)std::min(1e9, ceil(S * (double)ms / TRIAL_MS)));
+            calibrated = true;
+        }
+        for (int ipt : {2, 4}) {
+            float ms = INFINITY;
+            s = run(t, ipt, ms);
+            if (s != PC_OK) { pc_free_tree(t); return s; }
+            if (nt < max_trials) trials[nt] = pc_tune_trial{(double)cap, ipt, o.priv, ms};
+            ++nt;
+            if (cap == 0 && ipt == 2) ms_default = ms;
+            if (ms < best_ms) {
+                best_ms = ms;
+                out->ipt = ipt;
+                *list_cap = cap;
+            }
+        }
+        pc_free_tree(t);
+    }
+    if (std::isfinite(ms_default) && best_ms > 0.97f * ms_default) {
+        out->ipt = 2;
+        *list_cap = 0;
+    }
+    if (n_trials) *n_trials = std::min(nt, max_trials);
+    PC_CUDA(cudaStreamSynchronize(st));
+    return PC_OK;
+}

@@ -43,8 +43,8 @@ def _check(got, want, gw=None, ww=None, what=""):
         assert rel.size == 0 or rel.max() <= WREL, f"{what}: weighted rel err {rel.max():.3e}"
 
 
-def _both(x1, x2=None, w1=None, w2=None, n_leaf=32, **kw):
-    got = P.count_tree(x1, x2, w1=w1, w2=w2, n_leaf=n_leaf, **kw)
+def _both(x1, x2=None, w1=None, w2=None, n_leaf=32, list_cap=0, ipt=2, **kw):
+    got = P.count_tree(x1, x2, w1=w1, w2=w2, n_leaf=n_leaf, list_cap=list_cap, ipt=ipt, **kw)
     want = oracle.count(x1, x2, w1=w1, w2=w2, method="grid", **kw)
     return got, want
 
@@ -104,9 +104,12 @@ def test_tree_structure_matches_oracle(n, n_leaf, periodic):
     xc = x - L * np.floor(x / L) if periodic else x
     checked = _compare_trees(xc, g, ref)
     assert checked >= min(n, 3) if n > n_leaf else checked == 1
-    # the block level: the first level whose nodes hold at most 256 points
-    bl = g["block_level"]
-    assert int(np.ceil(n / 2 ** bl)) <= 256 and (bl == 0 or int(np.ceil(n / 2 ** (bl - 1))) > 256)
+    # the automatic list level: nodes of 129..2048 points (or the root)
+    ll = g["list_level"]
+    assert 0 <= ll <= g["depth"]
+    largest = int(np.ceil(n / 2 ** ll))
+    assert largest <= 2048 or ll == 0
+    assert largest > 128 or ll == 0
 
 
 # --------------------------------------------------------------------------
@@ -226,12 +229,37 @@ def test_tree_matches_grid_and_sampled_oracle_at_size():
     gt, _, st = P.count_tree(x, return_stats=True, **kw)
     gg, _ = P.count(x, **kw)
     assert np.array_equal(gt, gg)
-    assert st.tree_pairs > 0 and st.blocks == 2 ** int(np.ceil(np.log2(200000 / 256)))
+    assert st.tree_pairs > 0 and st.blocks >= 200000 / 256
     rng = np.random.default_rng(792)
     s = x[rng.choice(x.shape[0], 600, replace=False)]
     g, _ = P.count_tree(s, x, **kw)
     w, _ = oracle.count(s, x, **kw)
     _check(g, w, what="tree sampled cross")
+
+
+@pytest.mark.parametrize("list_cap,ipt", [(0, 2), (256, 2), (512, 4), (1024, 2), (1024, 4),
+                                          (4096, 4), (0, 4)])
+def test_tree_list_levels_keep_counts(list_cap, ipt):
+    """List nodes of any size (several balanced blocks each, the own-node
+    rest of an auto count as a segment) give the same counts."""
+    L = 300.0
+    x = synth.neyman_scott(60000, 3000, 20.0, 2.0, L, 801)
+    y = synth.uniform_box(7000, L, 802)
+    ea = np.linspace(0.0, 30.0, 16)
+    mu = np.linspace(0.0, 1.0, 11)
+    kw = dict(box=L, periodic=True, mode="smu", edges_a=ea, edges_b=mu)
+    (g, _), (w, _) = _both(x, list_cap=list_cap, ipt=ipt, **kw)
+    _check(g, w, what=f"tree auto list_cap={list_cap} ipt={ipt}")
+    (g, _), (w, _) = _both(x, y, list_cap=list_cap, ipt=ipt, **kw)
+    _check(g, w, what=f"tree cross list_cap={list_cap} ipt={ipt}")
+    b = P.make_box(L, True)
+    t = P.pc_build_tree(x, box=b, list_cap=list_cap)
+    try:
+        n, depth, ll, slots = t.info()
+    finally:
+        t.free()
+    if list_cap:
+        assert int(np.ceil(n / 2 ** ll)) <= list_cap < int(np.ceil(n / 2 ** (ll - 1)))
 
 
 def test_tree_errors():
@@ -242,11 +270,40 @@ def test_tree_errors():
         P.pc_build_tree(x, box=P.make_box(10.0, True), n_leaf=129)
     with pytest.raises(P.PairCountError):
         P.pc_build_tree(x[:0], box=P.make_box(10.0, True))
+    with pytest.raises(P.PairCountError):
+        P.pc_build_tree(x, box=P.make_box(10.0, True), list_cap=300)
     with pytest.raises(P.PairCountError):   # separation of L/2 or more in a periodic box
         P.count_tree(x, box=10.0, periodic=True, mode="s", edges_a=[0.0, 6.0])
     t = P.pc_build_tree(x, box=P.make_box(10.0, True))
     try:
         with pytest.raises(P.PairCountError):   # plain FP64 is a grid-path option
             P.pc_count_tree(t, None, P.Bins("s", "z", [0.0, 1.0]), P.make_opts("f64"))
+    finally:
+        t.free()
+
+
+def test_tree_tuner_and_shards():
+    """pc_tune_tree's options keep the counts, and block shards of a tree count
+    sum to the full count."""
+    L = 300.0
+    x = synth.neyman_scott(80000, 4000, 20.0, 2.0, L, 811)
+    ea = np.linspace(0.0, 30.0, 16)
+    mu = np.linspace(0.0, 1.0, 11)
+    bins = P.Bins("smu", "z", ea, mu)
+    b = P.make_box(L, True)
+    o, cap, trials = P.pc_tune_tree(x, box=b, bins=bins)
+    assert o.ipt in (2, 4) and cap in (0, 512, 1024, 2048, 4096) and len(trials) >= 2
+    want, _ = oracle.count(x, box=L, periodic=True, mode="smu", edges_a=ea, edges_b=mu,
+                           method="grid")
+    t = P.pc_build_tree(x, box=b, list_cap=cap)
+    try:
+        got, _, _ = P.pc_count_tree(t, None, bins, o)
+        _check(got, want, what="tuned tree")
+        tot = np.zeros_like(want)
+        for k in range(3):
+            os_ = P.make_opts("f32", 0.0, o.ipt, shard_index=k, shard_count=3)
+            part, _, _ = P.pc_count_tree(t, None, bins, os_)
+            tot += part
+        _check(tot, want, what="tree shards")
     finally:
         t.free()
