@@ -53,6 +53,9 @@ def parse():
                     help="steps of the k-d tree path reported beside the grid line (0: none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--micro", choices=["hist"], default=None,
+                    help="run a micro-benchmark instead of the pair-count step: 'hist' times the "
+                         "histogram-update algorithms on sampled squared separations")
     ap.add_argument("--structure", choices=["grid", "kdtree"], default="grid",
                     help="space partition: the regular grid (default, tuned) or the k-d tree "
                          "with the dual-tree traversal")
@@ -452,7 +455,7 @@ def run_ours(args):
     trec = traffic_record()
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
-                "traffic": (trec["bytes_per_launch"] if trec else None),
+                "traffic": (trec["bytes_per_launch"] if trec and not tree else None),
                 "kernel": "k_pairs_f32<SMU,LOS_Z>" + (" (tree variant)" if tree else ""),
                 "flops_per_launch": flops,
                 "flops_definition": (f"{FLOPS_PER_CANDIDATE} per pair evaluated one by one "
@@ -808,8 +811,65 @@ def run_sets(args):
     return 0
 
 
+def run_micro_hist(args):
+    """Histogram-update micro-benchmark (Sect. 3.2.4): 6.4e9 squared separations
+    sampled as in App. C over [0, 200^2), linear bins on [0, 200) and
+    logarithmic bins on [0.1, 200), 20 and 200 bins; binary search, reverse
+    traversal, index mapping and the hybrid lookup table at several sizes."""
+    import torch
+    import paper_2301_12557_gb300 as P
+    import synth
+    import oracle
+
+    P.lib()
+    torch.cuda.set_device(0)
+    R = 200.0
+    n = 1 << 27
+    total = 6.4e9
+    repeat = int(np.ceil(total / n))
+    host = synth.s2_samples(n, R, synth.SEED_BASE + 500)
+    d = torch.from_numpy(host).cuda()
+    configs = {"lin20": np.linspace(0.0, R, 21), "lin200": np.linspace(0.0, R, 201),
+               "log20": np.geomspace(0.1, R, 21), "log200": np.geomspace(0.1, R, 201)}
+    tables = [64, 256, 1024, 4096, 16384, 49152]
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = {}
+    for name, edges in configs.items():
+        mapm = "map_lin" if name.startswith("lin") else "map_log"
+        methods = [("bsearch", 0), ("reverse", 0), (mapm, 0)] + [("lut", t) for t in tables]
+        # parity on a slice against the oracle, then every method on the full stream
+        want = oracle.hist_s2(host[: 1 << 22], edges)
+        ref = None
+        row = {}
+        for m, t in methods:
+            got, _ = P.pc_hist_s2(d[: 1 << 22], edges, m, table_size=t)
+            assert np.array_equal(got, want), (name, m, t)
+            full, ms = P.pc_hist_s2(d, edges, m, table_size=t, repeat=repeat)
+            if ref is None:
+                ref = full
+            assert np.array_equal(full, ref), (name, m, t)
+            key = m if m != "lut" else f"lut{t}"
+            row[key] = {"ms": ms, "ns_per_sample": ms * 1e6 / (n * repeat),
+                        "samples_per_s": n * repeat / (ms * 1e-3)}
+        best = min((k for k in row if k.startswith("lut")), key=lambda k: row[k]["ms"])
+        res[name] = {"methods": row, "best_table": best,
+                     "in_range_fraction": float(ref.sum()) / (n * repeat)}
+    clocks = sampler.stop()
+    line = {"micro": "hist_s2", "metric": "histogram updates per second", "unit": "samples/s",
+            "samples": n * repeat, "distinct_samples": n, "repeat": repeat,
+            "sampler": "s2 = x^(2/3) R^2, x uniform in [0, 1), R = 200 (App. C), binary32",
+            "edges": {"lin": "[0, 200)", "log": "[0.1, 200)"},
+            "exact": "every method equals the oracle's histogram on 4M samples and the others on all",
+            "results": res, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.micro == "hist":
+        return run_micro_hist(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload.startswith("mocks"):

@@ -311,6 +311,28 @@ pc_status pc_tune_tree(const double *xyz, const void *w, int w_is_f32, long long
                        void *stream, pc_opts *out, int *list_cap, pc_tune_trial *trials,
                        int max_trials, int *n_trials);
 
+/* ---- histogram-update micro-benchmark (Sect. 3.2.4) ---------------------- */
+/* Histogram of n squared separations s2 (binary32, host or device), read
+ * `repeat` times, on the edges e[0..nbins] with the pair definition's rule
+ * (bin k iff e[k]^2 <= s2 < e[k+1]^2 in binary64; samples outside
+ * [e[0]^2, e[nbins]^2) are not counted), by one update algorithm of Sect. 3.2:
+ *   method 0  binary search over the squared edges (Sect. 3.2.1)
+ *          1  reverse traversal from the last bin (Sect. 3.2.1)
+ *          2  index mapping for linear bins, floor((sqrt(s2) - e0) / width),
+ *             then a comparison with the neighbouring edges (Sect. 3.2.2)
+ *          3  index mapping for logarithmic bins, on log2(s2) (Sect. 3.2.2;
+ *             needs e[0] > 0), then the same correction
+ *          4  hybrid index lookup table of table_size cells over the
+ *             rescaled s2 (Sect. 3.2.3): each cell holds the range of bins
+ *             its samples can reach, searched by reverse traversal
+ * The table and the histogram live in shared memory (table_size <= 49152).
+ *   counts   int64 [nbins], host or device: counts x repeat
+ *   ms       optional: device time of the binning kernel
+ * Errors: PC_EINVAL, PC_EOVERFLOW (over 2^31 samples per CTA),
+ * PC_EUNSUPPORTED (table and histogram beyond shared memory), PC_ECUDA. */
+pc_status pc_hist_s2(const float *s2, long long n, int repeat, const double *edges, int nbins,
+                     int method, int table_size, void *stream, long long *counts, float *ms);
+
 /* Bounding box of n points (n x 3 binary64, host or device) -- the first of
  * the three grid-build passes of Sect. 2.1.  lo/hi are host arrays of 3. */
 pc_status pc_aabb(const double *xyz, long long n, void *stream, double *lo, double *hi);

@@ -191,6 +191,19 @@ def kdtree(x, *, n_leaf=8, box=None, periodic=False) -> dict:
     return {"depth": rc, "start": start, "count": count, "axis": axis, "box": bx, "ord": order}
 
 
+def hist_s2(s2, edges) -> np.ndarray:
+    """Histogram of squared separations under the pair definition's rule
+    (Sect. 3.2): bin k iff E_k <= s2 < E_{k+1} with E_k = e_k^2 in binary64;
+    samples outside [E_0, E_n) are not counted.  numpy's searchsorted finds
+    the largest k with E_k <= s2."""
+    e = np.asarray(edges, dtype=np.float64)
+    E = e * e
+    v = np.asarray(s2).astype(np.float64)
+    keep = (v >= E[0]) & (v < E[-1])
+    k = np.searchsorted(E, v[keep], side="right") - 1
+    return np.bincount(k, minlength=e.size - 1).astype(np.int64)
+
+
 def pair_bin(a, b, *, box=None, periodic=False, mode="s", los="z", edges_a,
              edges_b=None) -> int:
     """Bin of a single pair (a, b); -1 when it falls outside all bins."""

@@ -75,7 +75,7 @@ EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc
            "pc_count_batch", "pc_aabb", "pc_suggest_cell_size", "pc_strerror", "pc_last_error",
            "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune",
            "pc_build_tree", "pc_free_tree", "pc_tree_info", "pc_tree_export", "pc_count_tree",
-           "pc_tune_tree"]
+           "pc_tune_tree", "pc_hist_s2"]
 
 
 def library_path() -> str:
@@ -147,6 +147,9 @@ def lib():
     L.pc_tune_tree.argtypes = [vp, vp, c_int, c_longlong, POINTER(pc_box), POINTER(pc_bins), c_int,
                                POINTER(pc_opts), vp, POINTER(pc_opts), POINTER(c_int),
                                POINTER(pc_tune_trial), c_int, POINTER(c_int)]
+    L.pc_hist_s2.restype = c_int
+    L.pc_hist_s2.argtypes = [vp, c_longlong, c_int, POINTER(c_double), c_int, c_int, c_int, vp, vp,
+                             POINTER(c_float)]
     L.pc_count_tree.restype = c_int
     L.pc_count_tree.argtypes = [vp, vp, POINTER(pc_bins), POINTER(pc_opts), vp, vp, vp,
                                 POINTER(pc_stats)]
@@ -490,6 +493,26 @@ def pc_tune_tree(xyz, w=None, *, box: pc_box, bins: Bins, n_leaf: int = 32,
                               max_trials, ctypes.byref(nt)), "pc_tune_tree")
     del keep_x, keep_w
     return out, cap.value, [(int(t.cell_size), t.ipt, t.ms) for t in trials[:nt.value]]
+
+
+HIST_METHODS = {"bsearch": 0, "reverse": 1, "map_lin": 2, "map_log": 3, "lut": 4}
+
+
+def pc_hist_s2(s2, edges, method="lut", table_size=0, repeat=1, stream=None, counts=None):
+    """Histogram-update micro-benchmark (see paircount.h); returns (counts, ms)."""
+    ps, keep, n = _ptr(s2, np.float32)
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+    nb = e.size - 1
+    if counts is None:
+        counts = np.zeros(nb, dtype=np.int64)
+    pc_, kc, _ = _ptr(counts, np.int64)
+    ms = c_float(0.0)
+    m = HIST_METHODS[method] if isinstance(method, str) else int(method)
+    _check(lib().pc_hist_s2(ps, n, int(repeat), e.ctypes.data_as(POINTER(c_double)), nb, m,
+                            int(table_size), _stream_handle(stream), pc_, ctypes.byref(ms)),
+           "pc_hist_s2")
+    del keep, kc
+    return counts, ms.value
 
 
 def pc_free_tree(t: Tree):

@@ -17,5 +17,6 @@ from .catalogs import (  # noqa: F401
     mixed_box,
     batch_mocks,
     lattice_points,
+    s2_samples,
 )
 from .workloads import WORKLOADS, Workload, linear_edges, make_inputs  # noqa: F401

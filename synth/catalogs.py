@@ -214,3 +214,15 @@ def near_edge_pairs(edges_len: np.ndarray, L: float, n_pairs: int, rel_offsets,
     pts[0::2] = a
     pts[1::2] = b
     return np.ascontiguousarray(_wrap_unit(pts, float(L)))
+
+
+def s2_samples(n: int, r_max: float, seed: int) -> np.ndarray:
+    """n squared pair separations in [0, r_max^2) with the distribution of
+    uniform pairs, s ~ s^2 ds (App. C: s^2 = x^(2/3) r_max^2 for x uniform in
+    [0, 1)), rounded to binary32 (the benchmark streams 4-byte samples)."""
+    x = _rng(seed).random(int(n))
+    s2 = (x ** (2.0 / 3.0)) * (float(r_max) ** 2)
+    out = s2.astype(np.float32)
+    top = np.float32(float(r_max) ** 2)
+    out[out >= top] = np.nextafter(top, np.float32(0))
+    return np.ascontiguousarray(out)
