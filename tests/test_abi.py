@@ -110,3 +110,48 @@ def test_tune_host_side_checks(lib):
                        None, ctypes.byref(out), None, 0, ctypes.byref(nt)) == P.PC_OK
     assert nt.value == 0 and out.ipt == 2
     assert out.cell_size == pytest.approx(P.pc_suggest_cell_size(1, 1e6, 20.0, 0))
+
+
+def test_tree_and_hist_host_side_checks(lib):
+    box = P.make_box(100.0, True)
+    out = ctypes.c_void_p()
+    x = np.zeros((4, 3))
+    # k-d tree build: NULL out, no points, bad leaf capacity or list capacity,
+    # too many points -- all rejected before any CUDA call
+    assert lib.pc_build_tree(x.ctypes.data, None, 0, 4, ctypes.byref(box), 8, 0, None,
+                             None) == P.PC_EINVAL
+    assert lib.pc_build_tree(x.ctypes.data, None, 0, 0, ctypes.byref(box), 8, 0, None,
+                             ctypes.byref(out)) == P.PC_EINVAL
+    assert lib.pc_build_tree(x.ctypes.data, None, 0, 4, ctypes.byref(box), 0, 0, None,
+                             ctypes.byref(out)) == P.PC_EINVAL
+    assert lib.pc_build_tree(x.ctypes.data, None, 0, 4, ctypes.byref(box), 129, 0, None,
+                             ctypes.byref(out)) == P.PC_EINVAL
+    assert lib.pc_build_tree(x.ctypes.data, None, 0, 4, ctypes.byref(box), 8, 300, None,
+                             ctypes.byref(out)) == P.PC_EINVAL
+    assert lib.pc_build_tree(x.ctypes.data, None, 0, 1 << 31, ctypes.byref(box), 8, 0, None,
+                             ctypes.byref(out)) == P.PC_EOVERFLOW
+    b = P.Bins("s", "z", [0.0, 1.0])
+    assert lib.pc_count_tree(None, None, ctypes.byref(b.s), None, None, None, None,
+                             None) == P.PC_EINVAL
+    opts = P.pc_opts()
+    cap = ctypes.c_int()
+    assert lib.pc_tune_tree(x.ctypes.data, None, 0, 4, None, ctypes.byref(b.s), 8, None, None,
+                            ctypes.byref(opts), ctypes.byref(cap), None, 0, None) == P.PC_EINVAL
+    # histogram micro-benchmark: bad sizes, edges, methods and table sizes
+    s2 = np.ones(8, dtype=np.float32)
+    e = np.array([0.0, 1.0, 2.0])
+    cnt = np.zeros(2, dtype=np.int64)
+    ep = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.pc_hist_s2(s2.ctypes.data, -1, 1, ep, 2, 0, 0, None, cnt.ctypes.data,
+                          None) == P.PC_EINVAL
+    assert lib.pc_hist_s2(s2.ctypes.data, 8, 0, ep, 2, 0, 0, None, cnt.ctypes.data,
+                          None) == P.PC_EINVAL
+    assert lib.pc_hist_s2(s2.ctypes.data, 8, 1, ep, 2, 7, 0, None, cnt.ctypes.data,
+                          None) == P.PC_EINVAL
+    assert lib.pc_hist_s2(s2.ctypes.data, 8, 1, ep, 2, 4, 0, None, cnt.ctypes.data,
+                          None) == P.PC_EINVAL
+    assert lib.pc_hist_s2(s2.ctypes.data, 8, 1, ep, 2, 3, 0, None, cnt.ctypes.data,
+                          None) == P.PC_EINVAL      # log mapping with e[0] = 0
+    bad = np.array([0.0, 2.0, 1.0])
+    assert lib.pc_hist_s2(s2.ctypes.data, 8, 1, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          2, 0, 0, None, cnt.ctypes.data, None) == P.PC_EINVAL
