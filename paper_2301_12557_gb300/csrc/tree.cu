@@ -153,6 +153,11 @@ __device__ __forceinline__ unsigned long long ukey(double v) {   // order-preser
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
+__global__ void k_iota(unsigned *v, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (unsigned)i;
+}
+
 // canonical coordinates (periodic: folded into [0, L)) of the input points
 __global__ void k_tree_canon(const double *__restrict__ xyz, int n, Geom g, double *__restrict__ x) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -877,13 +882,12 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
         cudaGetLastError();
         return bail(fail(PC_ENOMEM, "pc_build_tree: device allocation failed"));
     }
-    {
-        std::vector<unsigned> iota(n);
-        for (long long i = 0; i < n; ++i) iota[i] = (unsigned)i;
-        e = cudaMemcpyAsync(va, iota.data(), sizeof(unsigned) * n, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(nid, 0, sizeof(int) * n, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // iota leaves scope
+    if (e == cudaSuccess) {
+        k_iota<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(va, (int)n);
+        note_launch();
+        e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = cudaMemsetAsync(nid, 0, sizeof(int) * n, st);
     const double3 shift = make_double3(0.5 * (t->pts_lo[0] + t->pts_hi[0]),
                                        0.5 * (t->pts_lo[1] + t->pts_hi[1]),
                                        0.5 * (t->pts_lo[2] + t->pts_hi[2]));
