@@ -644,10 +644,11 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
         cudaGetLastError();
         return fail(PC_ENOMEM, "pc_build_grid: device allocation failed");
     }
-    // sub-cell order inside cells: 8 or 64 Morton sub-cells when cells hold
-    // enough points for them to matter
+    // sub-cell order inside cells: 8, 64 or 4096 Morton sub-cells when cells
+    // hold enough points for them to matter (4096 on the 1500-point cells of
+    // the tuned benchmark grid: 1 % fewer pairs past the group bounds than 64)
     const double per_cell = (double)n / g->ncell;
-    int sub_bits = per_cell >= 128.0 ? 2 : (per_cell >= 16.0 ? 1 : 0);
+    int sub_bits = per_cell >= 1024.0 ? 4 : (per_cell >= 128.0 ? 2 : (per_cell >= 16.0 ? 1 : 0));
     while (sub_bits > 0 && ((long long)g->ncell << (3 * sub_bits)) > (1LL << 28)) --sub_bits;
     const int nkey = g->ncell << (3 * sub_bits);
     int *counts = nullptr, *cell = nullptr, *slot = nullptr, *key_start = nullptr;
