@@ -803,6 +803,7 @@ def run_sets(args):
                          "ms_total": stats[k].ms_total, "candidates": stats[k].candidates,
                          "pruned": stats[k].pruned, "rescued": stats[k].rescued,
                          "node_pairs": stats[k].tree_pairs if tree else None,
+                         "ms_traverse": stats[k].ms_traverse if tree else None,
                          "prec": "f32+rescue" if stats[k].prec == 0 else "f64"} for k in kinds},
         "roofline": None,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),

@@ -394,9 +394,21 @@ static int tree_depth(long long n, int cap) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int slot_level(int h) { return 31 - __clz(h + 1); }
 
-__device__ __forceinline__ void push_pairs(int2 *out, int *n_out, const int2 *v, int m) {
-    const int k = atomicAdd(n_out, m);
-    for (int q = 0; q < m; ++q) out[k + q] = v[q];
+// Slots for this lane's m entries in a list with counter *n: one atomic per
+// warp (the lanes' counts scanned with shuffles).  Every lane of the warp
+// calls it (m = 0 for none).
+__device__ __forceinline__ int warp_slots(int *n, int m) {
+    const int lane = threadIdx.x & 31;
+    int incl = m;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(n, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + incl - m;
 }
 
 // A node pair {a, b | image << 24}: dropped when the boxes (b shifted by
@@ -406,62 +418,74 @@ __device__ __forceinline__ void push_pairs(int2 *out, int *n_out, const int2 *v,
 // pass, and lists the pair from the side that balances the nodes' loads);
 // otherwise split into the children pairs (a node paired with itself into
 // (left, left), (left, right), (right, right)).  Splits stop at the list
-// level of each tree.
-__global__ void k_dual_level(const int2 *__restrict__ in, int n_in, int2 *__restrict__ out,
-                             int *n_out, int2 *__restrict__ emit, int *n_emit,
-                             const double *__restrict__ box1, const double *__restrict__ box2,
-                             int blev1, int blev2, Geom g, double r2hi, double r2lo, int is_auto) {
+// level of each tree.  The block has whole warps (256 threads): lanes past
+// the list take part in the warp-wide slot allocation with nothing to add.
+__global__ void __launch_bounds__(256) k_dual_level(const int2 *__restrict__ in, int n_in,
+                                                    int2 *__restrict__ out, int *n_out,
+                                                    int2 *__restrict__ emit, int *n_emit,
+                                                    const double *__restrict__ box1,
+                                                    const double *__restrict__ box2, int blev1,
+                                                    int blev2, Geom g, double r2hi, double r2lo,
+                                                    int is_auto) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_in) return;
-    const int2 e = in[i];
-    const int a = e.x, b = e.y & 0xFFFFFF, img = e.y >> 24;
-    const int s3[3] = {img / 9 - 1, (img / 3) % 3 - 1, img % 3 - 1};
-    double dmin2 = 0.0, dmax2 = 0.0;
-    for (int d = 0; d < 3; ++d) {
-        const double sh = g.periodic ? (double)s3[d] * g.L[d] : 0.0;
-        const double alo = box1[6 * (size_t)a + d], ahi = box1[6 * (size_t)a + 3 + d];
-        const double blo = box2[6 * (size_t)b + d] + sh, bhi = box2[6 * (size_t)b + 3 + d] + sh;
-        const double gap = fmax(0.0, fmax(blo - ahi, alo - bhi));
-        const double far = fmax(bhi - alo, ahi - blo);
-        dmin2 += gap * gap;
-        dmax2 += far * far;
-    }
-    if (dmin2 > r2hi || dmax2 < r2lo) return;
-    const bool ab = slot_level(a) >= blev1, bb = slot_level(b) >= blev2;
-    const bool self = is_auto && a == b && img == 13;
-    if (ab && bb) {
-        if (self) return;
-        int ea = a, eb = b, ei = img;
-        if (is_auto && ((a ^ b) & 1)) {
-            ea = b;
-            eb = a;
-            ei = 26 - img;
-        }
-        emit[atomicAdd(n_emit, 1)] = make_int2(ea, eb | (ei << 24));
-        return;
-    }
-    const int tag = img << 24;
+    int nchild = 0, nemit = 0;
     int2 v[4];
-    if (self) {
-        v[0] = make_int2(2 * a + 1, (2 * a + 1) | tag);
-        v[1] = make_int2(2 * a + 1, (2 * a + 2) | tag);
-        v[2] = make_int2(2 * a + 2, (2 * a + 2) | tag);
-        push_pairs(out, n_out, v, 3);
-    } else if (!ab && !bb) {
-        v[0] = make_int2(2 * a + 1, (2 * b + 1) | tag);
-        v[1] = make_int2(2 * a + 1, (2 * b + 2) | tag);
-        v[2] = make_int2(2 * a + 2, (2 * b + 1) | tag);
-        v[3] = make_int2(2 * a + 2, (2 * b + 2) | tag);
-        push_pairs(out, n_out, v, 4);
-    } else if (ab) {
-        v[0] = make_int2(a, (2 * b + 1) | tag);
-        v[1] = make_int2(a, (2 * b + 2) | tag);
-        push_pairs(out, n_out, v, 2);
-    } else {
-        v[0] = make_int2(2 * a + 1, b | tag);
-        v[1] = make_int2(2 * a + 2, b | tag);
-        push_pairs(out, n_out, v, 2);
+    int2 em = make_int2(0, 0);
+    if (i < n_in) {
+        const int2 e = in[i];
+        const int a = e.x, b = e.y & 0xFFFFFF, img = e.y >> 24;
+        const int s3[3] = {img / 9 - 1, (img / 3) % 3 - 1, img % 3 - 1};
+        double dmin2 = 0.0, dmax2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double sh = g.periodic ? (double)s3[d] * g.L[d] : 0.0;
+            const double alo = box1[6 * (size_t)a + d], ahi = box1[6 * (size_t)a + 3 + d];
+            const double blo = box2[6 * (size_t)b + d] + sh, bhi = box2[6 * (size_t)b + 3 + d] + sh;
+            const double gap = fmax(0.0, fmax(blo - ahi, alo - bhi));
+            const double far = fmax(bhi - alo, ahi - blo);
+            dmin2 += gap * gap;
+            dmax2 += far * far;
+        }
+        if (!(dmin2 > r2hi || dmax2 < r2lo)) {
+            const bool ab = slot_level(a) >= blev1, bb = slot_level(b) >= blev2;
+            const bool self = is_auto && a == b && img == 13;
+            const int tag = img << 24;
+            if (ab && bb) {
+                if (!self) {
+                    int ea = a, eb = b, ei = img;
+                    if (is_auto && ((a ^ b) & 1)) {
+                        ea = b;
+                        eb = a;
+                        ei = 26 - img;
+                    }
+                    em = make_int2(ea, eb | (ei << 24));
+                    nemit = 1;
+                }
+            } else if (self) {
+                v[0] = make_int2(2 * a + 1, (2 * a + 1) | tag);
+                v[1] = make_int2(2 * a + 1, (2 * a + 2) | tag);
+                v[2] = make_int2(2 * a + 2, (2 * a + 2) | tag);
+                nchild = 3;
+            } else if (!ab && !bb) {
+                v[0] = make_int2(2 * a + 1, (2 * b + 1) | tag);
+                v[1] = make_int2(2 * a + 1, (2 * b + 2) | tag);
+                v[2] = make_int2(2 * a + 2, (2 * b + 1) | tag);
+                v[3] = make_int2(2 * a + 2, (2 * b + 2) | tag);
+                nchild = 4;
+            } else if (ab) {
+                v[0] = make_int2(a, (2 * b + 1) | tag);
+                v[1] = make_int2(a, (2 * b + 2) | tag);
+                nchild = 2;
+            } else {
+                v[0] = make_int2(2 * a + 1, b | tag);
+                v[1] = make_int2(2 * a + 2, b | tag);
+                nchild = 2;
+            }
+        }
     }
+    const int ko = warp_slots(n_out, nchild);
+    for (int q = 0; q < nchild; ++q) out[ko + q] = v[q];
+    const int ke = warp_slots(n_emit, nemit);
+    if (nemit) emit[ke] = em;
 }
 
 // Group the listed node pairs by i-node: counts, then (after a scan) the
