@@ -57,13 +57,13 @@ __host__ __device__ inline SmemLayout smem_layout(const PairParams &p, bool f64)
     if (p.smem_hist_ok && p.weighted)
         o = align_up(o + (size_t)p.nbins_smem * p.hist_k * sizeof(double), 16);
     L.seg = o;
-    o = align_up(o + (size_t)MAXSEG * sizeof(int4), 16);
+    o = align_up(o + (size_t)(p.tree && !f64 ? MAXSEG_T : MAXSEG) * sizeof(int4), 16);
     int tj = f64 ? TJ64 : TJ;
     L.tile = o;
     o = align_up(o + (size_t)2 * tj * (f64 ? sizeof(double4_32a) : 3 * sizeof(float)), 16);
     L.meta = o;
     if (f64) o = align_up(o + (size_t)2 * tj * sizeof(int2), 16);
-    else if (p.tree) o = align_up(o + (size_t)MAXSEG * sizeof(float4), 16);   // segment offsets
+    else if (p.tree) o = align_up(o + (size_t)MAXSEG_T * sizeof(float4), 16);   // segment offsets
     L.tw = o;
     if (p.weighted && !f64) o = align_up(o + (size_t)2 * tj * sizeof(double), 16);
     L.q = o;
@@ -1175,7 +1175,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
 
         // ---- phase B: j-segments, in chunks ---------------------------------
         // grid: the stencil rows, ROWCHUNK at a time; tree: the i-block's list
-        // of (j-block, image) pairs, MAXSEG at a time
+        // of (j-node, image) pairs, MAXSEG_T at a time
         // tree: virtual segment 0 of an auto count is the rest of the i-node
         // after this block (same node, no offset), then the listed nodes
         int ts0 = 0, tvirt = 0, trest = 0, node_end = 0;
@@ -1188,13 +1188,13 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
             }
             tvirt = p.tseg_off[B.cell + 1] - ts0 + trest;
         }
-        const int nchunk = TREE ? (tvirt + MAXSEG - 1) / MAXSEG : (p.nrows + ROWCHUNK - 1) / ROWCHUNK;
+        const int nchunk = TREE ? (tvirt + MAXSEG_T - 1) / MAXSEG_T : (p.nrows + ROWCHUNK - 1) / ROWCHUNK;
         for (int ch = 0; ch < nchunk; ++ch) {
             if constexpr (TREE) {
                 // segment k: a listed j-node's points, staged relative to the
                 // i-node's centre through the offset of the two centres
-                const int v0 = ch * MAXSEG;
-                const int ns = min(MAXSEG, tvirt - v0);
+                const int v0 = ch * MAXSEG_T;
+                const int ns = min(MAXSEG_T, tvirt - v0);
                 const double *ci = p.tcen_i + 3 * (size_t)B.cell;
                 for (int k = tid; k < ns; k += NT) {
                     const int v = v0 + k;

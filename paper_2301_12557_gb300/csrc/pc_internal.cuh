@@ -17,6 +17,8 @@ constexpr int NT = 128;        // threads per CTA (per thread group with grouped
 constexpr int TJ = 512;        // j points per shared-memory tile (FP32 path)
 constexpr int TJ64 = 128;      // j points per tile (FP64 path)
 constexpr int MAXSEG = 256;    // j segments per chunk of stencil rows
+constexpr int MAXSEG_T = 128;  // j segments per chunk of a tree list (nodes of 129+ points;
+                               // segments and their offsets fit the grid's segment space)
 constexpr int ROWCHUNK = 84;   // stencil rows per chunk (<= 3 segments each)
 static_assert(3 * ROWCHUNK + 1 <= MAXSEG, "a chunk's segments (and the own-cell rest) fit");
 constexpr int LQ = 256;        // rescue staging slots per CTA (per thread group)
