@@ -1,5 +1,5 @@
 /*
- * paircount.h -- exact grid pair counting on one GB300 (sm_103a).
+ * paircount.h -- exact pair counting on one GB300 (sm_103a): grid and k-d tree.
  *
  * C ABI of the library built from paper_2301_12557_gb300/csrc.  Plain
  * pointers and sizes only.  Every pointer argument that carries catalogue
@@ -16,7 +16,11 @@
  *   Sect. 2.1  -- regular grid built in three passes (bounds, per-cell counts,
  *                 grouping) with points stored contiguously by cell;
  *   Sect. 3.1  -- auto counts visit each unordered pair once; periodic boxes
- *                 shift whole cells instead of wrapping each pair.
+ *                 shift whole cells instead of wrapping each pair;
+ *   Sect. 2.2, 3.1 -- the k-d tree (Alg. 1) and the dual-tree traversal
+ *                 (Alg. 3) as a second space partition (pc_build_tree,
+ *                 pc_count_tree);
+ *   Sect. 3.2.4 -- the histogram-update micro-benchmark (pc_hist_s2).
  *
  * Exact semantics (identical to the FP64 definition the tests use):
  *   periodic canonical form  x <- x - L floor(x/L); if x<0 x+=L; if x>=L x-=L
