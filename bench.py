@@ -547,36 +547,60 @@ def run_batch(args):
     box = P.make_box(w.L, True)
     stream = torch.cuda.current_stream()
     tuning = None
-    if args.cell_size > 0 or args.ipt > 0:
+    tree = args.structure == "kdtree"
+    list_cap = args.list_cap
+    med = sorted(range(m), key=lambda k: X[k].shape[0])[m // 2]
+    if tree and (args.list_cap > 0 or args.ipt > 0):
+        opts = P.make_opts("f32", 0.0, args.ipt or 2)
+        cell = 0.0
+    elif tree:
+        # measured list level and i-points per thread, on the mock of median size
+        t0 = time.perf_counter()
+        opts, list_cap, trials = P.pc_tune_tree(X[med], box=box, bins=bins, n_leaf=args.n_leaf,
+                                                stream=stream)
+        tuning = {"seconds": time.perf_counter() - t0, "on_mock_n": int(X[med].shape[0]),
+                  "trials": [{"list_cap": c, "ipt": i, "ms": round(ms, 3)} for c, i, ms in trials]}
+        cell = 0.0
+    elif args.cell_size > 0 or args.ipt > 0:
         cell = args.cell_size or P.pc_suggest_cell_size(n_tot // m, w.L ** 3, bins.r_max)
         opts = P.make_opts("f32", cell, args.ipt)
     else:
         # measured autotuning once, on the mock of median size; all mocks share it
-        med = sorted(range(m), key=lambda k: X[k].shape[0])[m // 2]
         t0 = time.perf_counter()
         opts, trials = P.pc_tune(X[med], box=box, bins=bins, stream=stream)
         tuning = {"seconds": time.perf_counter() - t0, "on_mock_n": int(X[med].shape[0]),
                   "trials": [{"cell_size": round(c, 3), "ipt": i, "priv": pv, "ms": round(ms, 3)}
                              for c, i, pv, ms in trials]}
         cell = opts.cell_size
-    opts.use_graph = 1
+    opts.use_graph = 0 if tree else 1
     out = torch.zeros(m * bins.nbins, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step(xs=X, counts=out, batched=True):
-        gs = [P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=opts, stream=stream) for x in xs]
+        if tree:
+            ts = [P.pc_build_tree(x, box=box, n_leaf=args.n_leaf, list_cap=list_cap, stream=stream)
+                  for x in xs]
+        else:
+            ts = [P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=opts, stream=stream)
+                  for x in xs]
         try:
             if batched:
-                _, _, st = P.pc_count_batch(gs, bins, opts, stream, counts=counts)
+                if tree:
+                    _, _, st = P.pc_count_tree_batch(ts, bins, opts, stream, counts=counts)
+                else:
+                    _, _, st = P.pc_count_batch(ts, bins, opts, stream, counts=counts)
                 return st.candidates
             cand = 0
-            for k, g in enumerate(gs):
+            for k, g in enumerate(ts):
                 view = counts[k * bins.nbins:(k + 1) * bins.nbins]
-                _, _, st = P.pc_count_auto(g, bins, opts, stream, counts=view)
+                if tree:
+                    _, _, st = P.pc_count_tree(g, None, bins, opts, stream, counts=view)
+                else:
+                    _, _, st = P.pc_count_auto(g, bins, opts, stream, counts=view)
                 cand += st.candidates
             return cand
         finally:
-            for g in gs:
+            for g in ts:
                 g.free()
 
     def timed(k_steps, **kw):
@@ -631,13 +655,19 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": w.name if m == w.extra["m"] else f"{w.name} ({m} mocks)",
-                       "mocks": m, "n_total": int(n_tot), "cell_size": cell, "ipt": opts.ipt,
+                       "mocks": m, "n_total": int(n_tot),
+                       "structure": ("k-d tree (leaf capacity %d, list nodes %s), dual-tree "
+                                     "traversal per mock" % (args.n_leaf, list_cap or "auto"))
+                                    if tree else "regular grid",
+                       "cell_size": cell, "ipt": opts.ipt,
                        "priv": opts.priv, "tuning": tuning,
                        "unit_of_work": "in-range pairs binned (each pair in exactly one bin)",
                        "in_range_pairs": int(inr_step), "candidates_per_step": int(cand),
                        "bins": "s 40 x mu 100 (LOS z)",
                        "precision": "FP32 separations, binary64 rescue near bin edges, int64 counts",
-                       "launch": "one persistent pair-kernel launch over all mocks, replayed as a CUDA graph",
+                       "launch": ("one persistent pair-kernel launch over all mocks"
+                                  if tree else "one persistent pair-kernel launch over all mocks, "
+                                  "replayed as a CUDA graph"),
                        "l2": "flushed between timed steps (256 MiB write)"},
             "candidate_pairs_per_s": cand_all / (t_max * 1e-3),
             "loop_of_single_counts_ms": loop_ms[0],

@@ -300,6 +300,19 @@ pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const pc_bins *b,
                         const pc_opts *o, void *stream, long long *counts, double *wcounts,
                         pc_stats *st);
 
+/* Auto counts of m trees (all of one box and device) in one pair-kernel
+ * launch: the tree path's counterpart of pc_count_batch.  Each tree is
+ * traversed on its own (Alg. 3) and its list-node pairs appended to the
+ * batch's lists; the persistent pair kernel then takes the blocks of all
+ * trees from one work queue, each into its own histogram row.
+ *   counts   int64 m x nbins (row k: tree k), host or device
+ *   wcounts  binary64 m x nbins or NULL (every tree must carry weights)
+ *   o, st    as for pc_count_tree
+ * Errors as pc_count_tree. */
+pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const pc_bins *b,
+                              const pc_opts *o, void *stream, long long *counts,
+                              double *wcounts, pc_stats *st);
+
 /* Measured options of the k-d tree path for the auto count of a catalogue:
  * builds the tree (leaf capacity n_leaf) with the automatic list level and
  * with list nodes of at most 512, 1024, 2048 and 4096 points (distinct levels

@@ -75,7 +75,7 @@ EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc
            "pc_count_batch", "pc_aabb", "pc_suggest_cell_size", "pc_strerror", "pc_last_error",
            "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune",
            "pc_build_tree", "pc_free_tree", "pc_tree_info", "pc_tree_export", "pc_count_tree",
-           "pc_tune_tree", "pc_hist_s2"]
+           "pc_tune_tree", "pc_hist_s2", "pc_count_tree_batch"]
 
 
 def library_path() -> str:
@@ -150,6 +150,9 @@ def lib():
     L.pc_hist_s2.restype = c_int
     L.pc_hist_s2.argtypes = [vp, c_longlong, c_int, POINTER(c_double), c_int, c_int, c_int, vp, vp,
                              POINTER(c_float)]
+    L.pc_count_tree_batch.restype = c_int
+    L.pc_count_tree_batch.argtypes = [POINTER(vp), c_int, POINTER(pc_bins), POINTER(pc_opts), vp,
+                                      vp, vp, POINTER(pc_stats)]
     L.pc_count_tree.restype = c_int
     L.pc_count_tree.argtypes = [vp, vp, POINTER(pc_bins), POINTER(pc_opts), vp, vp, vp,
                                 POINTER(pc_stats)]
@@ -554,6 +557,21 @@ def pc_count_tree(t1: Tree, t2, bins: Bins, opts: pc_opts | None = None, stream=
                                ctypes.byref(opts) if opts is not None else None,
                                _stream_handle(stream), pc_, pw_, ctypes.byref(st)),
            "pc_count_tree")
+    del keep
+    return counts, wcounts, st
+
+
+def pc_count_tree_batch(trees, bins: Bins, opts: pc_opts | None = None, stream=None,
+                        counts=None, wcounts=None, weighted=False):
+    """Auto counts of several trees in one pair-kernel launch (row k: tree k)."""
+    m = len(trees)
+    counts, wcounts, pc_, pw_, keep = _outputs(counts, wcounts, m, bins.nbins, weighted)
+    arr = (c_void_p * m)(*[t.handle for t in trees])
+    st = pc_stats()
+    _check(lib().pc_count_tree_batch(arr, m, ctypes.byref(bins.s),
+                                     ctypes.byref(opts) if opts is not None else None,
+                                     _stream_handle(stream), pc_, pw_, ctypes.byref(st)),
+           "pc_count_tree_batch")
     del keep
     return counts, wcounts, st
 

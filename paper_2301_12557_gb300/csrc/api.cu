@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <atomic>
 #include <map>
 #include <memory>
@@ -798,13 +799,13 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
 static pc_status enqueue_count(const CountSetup &S, const DevBufs &B, const PairParams &p, int grid,
                                size_t smem, cudaStream_t st, cudaEvent_t ev_pairs,
                                cudaEvent_t ev_rescue, cudaEvent_t ev_done,
-                               const pc_tree *blk_tree = nullptr) {
+                               const std::function<cudaError_t()> &tree_blocks_fn = {}) {
     PC_CUDA(cudaMemsetAsync(B.hist, 0, sizeof(unsigned long long) * S.hist_n, st));
     if (S.weighted) PC_CUDA(cudaMemsetAsync(B.whist, 0, sizeof(double) * S.hist_n, st));
     PC_CUDA(cudaMemsetAsync(B.ctr, 0, sizeof(unsigned long long) * 4, st));
     PC_CUDA(cudaMemsetAsync(B.sc, 0, sizeof(int) * 4, st));
-    if (blk_tree)   // tree count: balanced blocks of the list nodes
-        PC_CUDA(tree_blocks(blk_tree, S.ipt, B.blocks, B.sc + 1, st));
+    if (tree_blocks_fn)   // tree counts: balanced blocks of the list nodes
+        PC_CUDA(tree_blocks_fn());
     else
         PC_CUDA(make_blocks_into(B.tasks, S.ntasks, S.ncell, S.bi, B.blocks, B.sc + 1, B.cnt,
                                  B.off, B.tot, st));
@@ -1258,7 +1259,8 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
     p.tcen_j = tj->bcen;
     s = upload_tables(J, S, B, st);
     if (s != PC_OK) return s;
-    s = enqueue_count(S, B, p, grid, smem, st, ev.e[1], ev.e[2], ev.e[3], t1);
+    s = enqueue_count(S, B, p, grid, smem, st, ev.e[1], ev.e[2], ev.e[3],
+                      [&]() { return tree_blocks(t1, S.ipt, B.blocks, B.sc + 1, st); });
     if (s != PC_OK) return s;
     cudaError_t e = cudaSuccess;
     copy_out(counts, B.hist, sizeof(long long) * S.hist_n, st, e);
@@ -1276,6 +1278,120 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
                launch_count() - launches0);
     if (stats) {
         stats->tree_pairs = TL.npairs;
+        stats->ms_traverse = ev.ms(0, 1);
+    }
+    return PC_OK;
+}
+
+// Auto counts of m trees in one pair-kernel launch (the tree path's batch):
+// each tree is traversed on its own and its lists appended to the batch's.
+extern "C" pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const pc_bins *b,
+                                         const pc_opts *opt, void *stream, long long *counts,
+                                         double *wcounts, pc_stats *stats) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!ts || m <= 0) return fail(PC_EINVAL, "pc_count_tree_batch: no trees");
+    if (m >= (1 << 26)) return fail(PC_EOVERFLOW, "pc_count_tree_batch: too many trees");
+    if (!counts && !wcounts) return fail(PC_EINVAL, "pc_count_tree_batch: no output buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<const pc_tree *> trees(ts, ts + m);
+    CountJob J;
+    double cb = 0.0;
+    J.wint_ok = true;
+    long long nlist = 0;
+    pc_opts o;
+    memset(&o, 0, sizeof(o));
+    o.priv = -1;
+    if (opt) o = *opt;
+    o.ipt = (o.ipt == 4) ? 4 : 2;
+    for (int k = 0; k < m; ++k) {
+        const pc_tree *t = trees[k];
+        if (!t) return fail(PC_EINVAL, "pc_count_tree_batch: tree is NULL");
+        if (!same_tree_geometry(trees[0], t))
+            return fail(PC_EINVAL, "pc_count_tree_batch: trees differ in box or device");
+        if (wcounts && !t->weighted)
+            return fail(PC_EINVAL, "pc_count_tree_batch: weighted counts need weights on every tree");
+        TaskDev T;
+        T.gi = GridDev{t->rel, nullptr, t->xw, nullptr, t->n};
+        T.gj = T.gi;
+        T.hist = k;
+        T.is_auto = 1;
+        T.wscale = t->wint ? ldexp(1.0, 2 * t->wemax - 300) : 0.0;
+        J.tasks.push_back(T);
+        cb = std::max(cb, t->bext);
+        for (int a = 0; a < 3; ++a) {
+            J.lo[a] = k ? std::min(J.lo[a], t->pts_lo[a]) : t->pts_lo[a];
+            J.hi[a] = k ? std::max(J.hi[a], t->pts_hi[a]) : t->pts_hi[a];
+        }
+        J.rmin = k ? std::min(J.rmin, tree_rmin(t)) : tree_rmin(t);
+        if (!t->wint || 2 * (t->wemax - t->wemin) > WINT_MAX_SPAN) J.wint_ok = false;
+        nlist += (long long)(1 << t->blevel) * tree_chunks(t, o.ipt);
+    }
+    if (nlist >= (1LL << 31)) return fail(PC_EOVERFLOW, "pc_count_tree_batch: too many blocks");
+    J.nhist = m;
+    J.is_auto = true;
+    J.tree = true;
+    J.geom = trees[0]->g;
+    for (int a = 0; a < 3; ++a) {
+        J.geom.c[a] = std::max(cb, 1e-300);
+        J.geom.c32[a] = (float)J.geom.c[a];
+        J.plo[a] = J.lo[a];
+        J.phi[a] = J.hi[a];
+    }
+    J.device = trees[0]->device;
+    // buffers are sized per task x cells: ntasks * ncell covers the blocks
+    J.ncell = (int)((nlist + m - 1) / m);
+    J.cell_size = cb;
+    CountSetup S;
+    pc_status s = setup_count(J, b, &o, wcounts != nullptr, S);
+    if (s != PC_OK) return s;
+    if (S.prec != PC_PREC_F32_RESCUE)
+        return fail(PC_EUNSUPPORTED,
+                    "pc_count_tree_batch: runs the FP32 + rescue kernel only (see pc_count_tree)");
+    DevBufs B;
+    s = ensure_bufs(workspace(S.dev), S, B);
+    if (s != PC_OK) return s;
+    PairParams p;
+    int grid = 0;
+    size_t smem = 0;
+    s = make_params(J, S, B, p, grid, smem);
+    if (s != PC_OK) return s;
+    S.wsum = p.wint ? 2 : (S.weighted ? 1 : 0);
+    Events ev(stats != nullptr);
+    const long long launches0 = launch_count();
+    if (ev.on) PC_CUDA(cudaEventRecord(ev.e[0], st));
+    static std::map<int, TreeBatch> batches;   // per device, reused (calls are serialised)
+    TreeBatch &TB = batches[S.dev];
+    const double r2hi = (double)S.P.r2cut * (1.0 + 1e-9);
+    const double r2lo = (S.P.mode != PC_BIN_SIGPI) ? S.P.Ea[0] * (1.0 - 1e-9) : 0.0;
+    s = tree_batch_lists(trees, S.ipt, r2hi, r2lo, st, TB);
+    if (s != PC_OK) return s;
+    p.tseg = (const int2 *)TB.seg.p;
+    p.tseg_off = (const int *)TB.off.p;
+    p.tblk_j = (const int2 *)TB.rng.p;
+    p.tcen_i = (const double *)TB.cen.p;
+    p.tcen_j = (const double *)TB.cen.p;
+    s = upload_tables(J, S, B, st);
+    if (s != PC_OK) return s;
+    s = enqueue_count(S, B, p, grid, smem, st, ev.e[1], ev.e[2], ev.e[3], [&]() {
+        return tree_blocks_batch(trees, TB, S.ipt, B.blocks, B.sc + 1, st);
+    });
+    if (s != PC_OK) return s;
+    cudaError_t e = cudaSuccess;
+    copy_out(counts, B.hist, sizeof(long long) * S.hist_n, st, e);
+    copy_out(wcounts, B.whist, sizeof(double) * S.hist_n, st, e);
+    if (e != cudaSuccess) return cuda_fail(e, "result copy");
+    unsigned long long hc[4] = {0, 0, 0, 0};
+    int hblk = 0;
+    if (ev.on) {
+        PC_CUDA(cudaMemcpyAsync(hc, B.ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        PC_CUDA(cudaMemcpyAsync(&hblk, B.sc + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PC_CUDA(cudaEventRecord(ev.e[4], st));
+    }
+    PC_CUDA(cudaStreamSynchronize(st));
+    fill_stats(stats, S, J.cell_size, hc, hblk, ev.ms(0, 4), ev.ms(1, 2), ev.ms(2, 3),
+               launch_count() - launches0);
+    if (stats) {
+        stats->tree_pairs = TB.npairs;
         stats->ms_traverse = ev.ms(0, 1);
     }
     return PC_OK;

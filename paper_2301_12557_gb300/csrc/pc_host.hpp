@@ -84,6 +84,44 @@ int tree_chunks(const pc_tree *t, int ipt);
 cudaError_t tree_blocks(const pc_tree *t, int ipt, Block *blocks, int *nblocks_dev,
                         cudaStream_t st);
 
+// Growable device buffer that keeps its first `keep` bytes when it grows.
+struct DevVec {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes, size_t keep = 0, cudaStream_t st = nullptr) {
+        if (bytes <= cap) return cudaSuccess;
+        const size_t want = bytes > cap * 2 ? bytes : cap * 2;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, want);
+        if (e != cudaSuccess) return e;
+        if (keep && p) {
+            e = cudaMemcpyAsync(q, p, keep, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                cudaFree(q);
+                return e;
+            }
+        }
+        if (p) cudaFree(p);
+        p = q;
+        cap = want;
+        return cudaSuccess;
+    }
+};
+
+// The concatenated lists of a batch of tree auto counts (one pair-kernel
+// launch): list node k of tree t is node node0[t] + k; its blocks start at
+// block0[t].
+struct TreeBatch {
+    std::vector<int> node0, block0;
+    DevVec seg, off, rng, cen;
+    long long npairs = 0;
+};
+pc_status tree_batch_lists(const std::vector<const pc_tree *> &ts, int ipt, double r2hi,
+                           double r2lo, cudaStream_t st, TreeBatch &B);
+cudaError_t tree_blocks_batch(const std::vector<const pc_tree *> &ts, const TreeBatch &B, int ipt,
+                              Block *blocks, int *nblocks_dev, cudaStream_t st);
+
 // Weight checks for the integer weight path: r[0] counts weights that are
 // not a non-negative normal binary32 value or zero, r[1] / r[2] the largest /
 // smallest biased exponent of the non-zero ones.  Synchronises the stream.

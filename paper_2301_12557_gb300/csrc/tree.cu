@@ -505,15 +505,28 @@ __global__ void k_group_fill(const int2 *__restrict__ emit, int ne, int blk0_i, 
 
 // The pair kernel's blocks: every list node split into k balanced chunks of
 // at most TREE_BLOCK points ("cell" = the list node).
-__global__ void k_tree_blocks(const int2 *__restrict__ rng, int nlist, int k,
-                              Block *__restrict__ blocks, int *__restrict__ nblocks) {
+// (Batches: task `task`, list nodes numbered from node0, blocks written from
+// blocks[0]; *nblocks receives the batch's total.)
+__global__ void k_tree_blocks(const int2 *__restrict__ rng, int nlist, int k, int task, int node0,
+                              int total, Block *__restrict__ blocks, int *__restrict__ nblocks) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b == 0) *nblocks = nlist * k;
+    if (b == 0) *nblocks = total;
     if (b >= nlist * k) return;
     const int node = b / k, c = b % k;
     const int2 r = rng[node];
     const int s0 = r.x + (int)((long long)r.y * c / k), s1 = r.x + (int)((long long)r.y * (c + 1) / k);
-    blocks[b] = Block{0, node, s0, s1 - s0};
+    blocks[b] = Block{task, node0 + node, s0, s1 - s0};
+}
+
+// A tree's listed pairs appended to a batch's lists: j-nodes renumbered from
+// node0, the i-node offsets shifted by the entries already there.
+__global__ void k_batch_lists(const int2 *__restrict__ seg, int ne, int node0, int2 *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ne) out[i] = make_int2(seg[i].x + node0, seg[i].y);
+}
+__global__ void k_batch_offsets(const int *__restrict__ off, int nb, int base, int *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= nb) out[i] = off[i] + base;
 }
 
 // Growable device array of the traversal workspace (reused across calls;
@@ -638,8 +651,68 @@ cudaError_t tree_blocks(const pc_tree *t, int ipt, Block *blocks, int *nblocks_d
     const int nl = 1 << t->blevel;
     const int k = tree_chunks(t, ipt);
     const int nb = nl * k;
-    k_tree_blocks<<<(nb + 255) / 256, 256, 0, st>>>(t->brng, nl, k, blocks, nblocks_dev);
+    k_tree_blocks<<<(nb + 255) / 256, 256, 0, st>>>(t->brng, nl, k, 0, 0, nb, blocks, nblocks_dev);
     note_launch();
+    return cudaGetLastError();
+}
+
+pc_status tree_batch_lists(const std::vector<const pc_tree *> &ts, int ipt, double r2hi, double r2lo,
+                           cudaStream_t st, TreeBatch &B) {
+    const int m = (int)ts.size();
+    B.node0.assign(m + 1, 0);
+    B.block0.assign(m + 1, 0);
+    for (int k = 0; k < m; ++k) {
+        const int nl = 1 << ts[k]->blevel;
+        B.node0[k + 1] = B.node0[k] + nl;
+        B.block0[k + 1] = B.block0[k] + nl * tree_chunks(ts[k], ipt);
+    }
+    const int nn = B.node0[m];
+    PC_CUDA(B.off.ensure(sizeof(int) * ((size_t)nn + 1)));
+    PC_CUDA(B.rng.ensure(sizeof(int2) * (size_t)nn));
+    PC_CUDA(B.cen.ensure(sizeof(double) * 3 * (size_t)nn));
+    long long nseg = 0;
+    for (int k = 0; k < m; ++k) {
+        TreeLists TL;
+        pc_status s = tree_traverse(ts[k], ts[k], true, r2hi, r2lo, st, TL);
+        if (s != PC_OK) return s;
+        if (nseg + TL.npairs > (long long)INT_MAX)
+            return fail(PC_EOVERFLOW, "tree batch: too many listed node pairs");
+        // the traversal workspace is reused by the next tree: append now
+        PC_CUDA(B.seg.ensure(sizeof(int2) * (size_t)std::max<long long>(nseg + TL.npairs, 1),
+                             sizeof(int2) * (size_t)nseg, st));
+        const int nl = 1 << ts[k]->blevel;
+        if (TL.npairs > 0) {
+            k_batch_lists<<<(unsigned)((TL.npairs + 255) / 256), 256, 0, st>>>(
+                TL.seg, (int)TL.npairs, B.node0[k], (int2 *)B.seg.p + nseg);
+            note_launch();
+        }
+        k_batch_offsets<<<(nl + 1 + 255) / 256, 256, 0, st>>>(TL.seg_off, nl, (int)nseg,
+                                                              (int *)B.off.p + B.node0[k]);
+        note_launch();
+        PC_CUDA(cudaMemcpyAsync((int2 *)B.rng.p + B.node0[k], ts[k]->brng, sizeof(int2) * nl,
+                                cudaMemcpyDeviceToDevice, st));
+        PC_CUDA(cudaMemcpyAsync((double *)B.cen.p + 3 * (size_t)B.node0[k], ts[k]->bcen,
+                                sizeof(double) * 3 * nl, cudaMemcpyDeviceToDevice, st));
+        PC_CUDA(cudaGetLastError());
+        // the next traversal overwrites the lists: finish the copies first
+        PC_CUDA(cudaStreamSynchronize(st));
+        nseg += TL.npairs;
+    }
+    B.npairs = nseg;
+    return PC_OK;
+}
+
+cudaError_t tree_blocks_batch(const std::vector<const pc_tree *> &ts, const TreeBatch &B, int ipt,
+                              Block *blocks, int *nblocks_dev, cudaStream_t st) {
+    const int m = (int)ts.size();
+    for (int k = 0; k < m; ++k) {
+        const int nl = 1 << ts[k]->blevel;
+        const int kc = tree_chunks(ts[k], ipt);
+        k_tree_blocks<<<(nl * kc + 255) / 256, 256, 0, st>>>(ts[k]->brng, nl, kc, k, B.node0[k],
+                                                              B.block0[m], blocks + B.block0[k],
+                                                              nblocks_dev);
+        note_launch();
+    }
     return cudaGetLastError();
 }
 

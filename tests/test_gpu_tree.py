@@ -307,3 +307,36 @@ def test_tree_tuner_and_shards():
         _check(tot, want, what="tree shards")
     finally:
         t.free()
+
+
+def test_tree_batch_matches_single_counts_and_oracle():
+    """A batch of trees of very different sizes (1 point to 40k) in one launch
+    equals each tree's own count; two of them against the oracle."""
+    L = 200.0
+    cats = [synth.neyman_scott(n, max(1, n // 20), 20.0, 2.0, L, 820 + i)
+            if n > 50 else synth.uniform_box(n, L, 820 + i)
+            for i, n in enumerate([40000, 1, 3000, 257, 25000, 90, 12000])]
+    ws = [synth.lognormal_weights(c.shape[0], 0.3, 840 + i, np.float32) for i, c in enumerate(cats)]
+    ea = np.linspace(0.0, 25.0, 26)
+    mu = np.linspace(0.0, 1.0, 11)
+    bins = P.Bins("smu", "z", ea, mu)
+    b = P.make_box(L, True)
+    for ipt in (2, 4):
+        trees = [P.pc_build_tree(c, w, box=b) for c, w in zip(cats, ws)]
+        try:
+            o = P.make_opts("f32", 0.0, ipt)
+            cb, wb, st = P.pc_count_tree_batch(trees, bins, o, weighted=True)
+            cb = cb.reshape(len(cats), -1)
+            wb = wb.reshape(len(cats), -1)
+            for k, t in enumerate(trees):
+                c1, w1, _ = P.pc_count_tree(t, None, bins, o, weighted=True)
+                assert np.array_equal(cb[k], c1), (ipt, k)
+                np.testing.assert_allclose(wb[k], w1, rtol=1e-12, atol=0)
+            assert st.tree_pairs > 0
+        finally:
+            for t in trees:
+                t.free()
+    for k in (0, 2):
+        want, wwant = oracle.count(cats[k], w1=ws[k].astype(np.float64), box=L, periodic=True,
+                                   mode="smu", edges_a=ea, edges_b=mu, method="grid")
+        _check(cb[k], want, wb[k], wwant, f"tree batch mock {k}")
