@@ -576,6 +576,8 @@ def run_batch(args):
     out = torch.zeros(m * bins.nbins, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    last_stats = []
+
     def step(xs=X, counts=out, batched=True):
         if tree:
             ts = [P.pc_build_tree(x, box=box, n_leaf=args.n_leaf, list_cap=list_cap, stream=stream)
@@ -589,6 +591,7 @@ def run_batch(args):
                     _, _, st = P.pc_count_tree_batch(ts, bins, opts, stream, counts=counts)
                 else:
                     _, _, st = P.pc_count_batch(ts, bins, opts, stream, counts=counts)
+                last_stats.append(st)
                 return st.candidates
             cand = 0
             for k, g in enumerate(ts):
@@ -670,6 +673,9 @@ def run_batch(args):
                                   "replayed as a CUDA graph"),
                        "l2": "flushed between timed steps (256 MiB write)"},
             "candidate_pairs_per_s": cand_all / (t_max * 1e-3),
+            "count_call": ({"ms_total": last_stats[-1].ms_total, "ms_pairs": last_stats[-1].ms_pairs,
+                            "ms_rescue": last_stats[-1].ms_rescue}
+                           if last_stats and last_stats[-1].ms_total > 0 else None),
             "loop_of_single_counts_ms": loop_ms[0],
             "batched_speedup_vs_loop": loop_ms[0] / (t_max / args.steps),
             "loop_counts_identical": same,
