@@ -46,33 +46,37 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _configure(lib):
+    """Declare the C signatures on a loaded copy of the oracle library."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.oracle_count.restype = ctypes.c_int
+    lib.oracle_count.argtypes = [
+        dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int64,
+        ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
+        ctypes.c_int, dp, ctypes.c_int, dp,
+        ctypes.c_int, ctypes.c_int, i64p, dp]
+    lib.oracle_count_kdtree.restype = ctypes.c_int
+    lib.oracle_count_kdtree.argtypes = [
+        dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int64,
+        ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
+        ctypes.c_int, dp, ctypes.c_int, dp,
+        ctypes.c_int, i64p, dp]
+    lib.oracle_kdtree.restype = ctypes.c_int
+    lib.oracle_kdtree.argtypes = [dp, ctypes.c_int64, ctypes.c_int, dp, ctypes.c_int,
+                                  ctypes.c_int64, i64p, i64p, ip, dp, i64p]
+    lib.oracle_pair_bin.restype = ctypes.c_int
+    lib.oracle_pair_bin.argtypes = [dp, dp, ctypes.c_int, dp, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            dp = ctypes.POINTER(ctypes.c_double)
-            i64p = ctypes.POINTER(ctypes.c_int64)
-            lib.oracle_count.restype = ctypes.c_int
-            lib.oracle_count.argtypes = [
-                dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int64,
-                ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
-                ctypes.c_int, dp, ctypes.c_int, dp,
-                ctypes.c_int, ctypes.c_int, i64p, dp]
-            lib.oracle_count_kdtree.restype = ctypes.c_int
-            lib.oracle_count_kdtree.argtypes = [
-                dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int64,
-                ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
-                ctypes.c_int, dp, ctypes.c_int, dp,
-                ctypes.c_int, i64p, dp]
-            ip = ctypes.POINTER(ctypes.c_int)
-            lib.oracle_kdtree.restype = ctypes.c_int
-            lib.oracle_kdtree.argtypes = [dp, ctypes.c_int64, ctypes.c_int, dp, ctypes.c_int,
-                                          ctypes.c_int64, i64p, i64p, ip, dp, i64p]
-            lib.oracle_pair_bin.restype = ctypes.c_int
-            lib.oracle_pair_bin.argtypes = [dp, dp, ctypes.c_int, dp, ctypes.c_int,
-                                            ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp]
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
 
 
