@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--list-cap", type=int, default=0,
                     help="k-d tree list nodes: at most this many points (0 = automatic)")
     ap.add_argument("--cell-size", type=float, default=0.0)
+    ap.add_argument("--rescue-capacity", type=int, default=0,
+                    help="rescue-queue slots with fixed options (0 automatic, -1 none: all inline)")
     ap.add_argument("--ipt", type=int, default=0)
     ap.add_argument("--shard", action="store_true",
                     help="with --gpus N > 1: split one catalogue's point blocks across the ranks "
@@ -288,14 +290,15 @@ def run_ours(args):
         tuning = {"seconds": time.perf_counter() - t0,
                   "trials": [{"list_cap": c, "ipt": i, "ms": round(ms, 3)} for c, i, ms in trials]}
     elif args.cell_size > 0 or args.ipt > 0:
-        opts = P.make_opts("f32", args.cell_size, args.ipt)
+        opts = P.make_opts("f32", args.cell_size, args.ipt, rescue_capacity=args.rescue_capacity)
     else:
         # measured autotuning on this catalogue, once, before the timed steps
         t0 = time.perf_counter()
         opts, trials = P.pc_tune(D, box=box, bins=bins, stream=stream)
         tuning = {"seconds": time.perf_counter() - t0,
                   "trials": [{"cell_size": round(c, 3), "ipt": i, "priv": pv, "ms": round(ms, 3)}
-                             for c, i, pv, ms in trials]}
+                             for c, i, pv, ms in trials],
+                  "last_trial": "near-edge pairs evaluated inside the pair kernel"}
     if args.shard and world > 1:
         from paper_2301_12557_gb300 import shard
         shard.shard_opts(opts, rank, world)
@@ -496,6 +499,8 @@ def run_ours(args):
                                      "traversal" % (args.n_leaf, list_cap or "auto"))
                                     if tree else "regular grid",
                        "cell_size": s0.cell_size, "ipt": opts.ipt, "priv": opts.priv,
+                       "rescue": ("inline in the pair kernel" if opts.rescue_capacity < 0 else
+                                  "queued for the rescue kernel"),
                        "tuning": tuning,
                        "tree": ({"node_pairs": int(s0.tree_pairs), "blocks": int(s0.blocks),
                                  "ms_build": statistics.mean(tree_ms[-args.steps:]),

@@ -212,8 +212,11 @@ typedef struct {
  * evenly spaced sample of the point blocks: 2 and 4 i-points per thread at
  * the model's cell side, then the better of those at cell sides in
  * quarter-octave steps from 0.7 to 2 times it (distinct grids only), then one
- * count copy per warp at the best; writes the fastest options to *out
- * (base's other fields are kept).
+ * count copy per warp at the best, then (unless base fixes rescue_capacity)
+ * the near-edge pairs evaluated inside the pair kernel (rescue_capacity -1)
+ * instead of queued for the rescue kernel; writes the fastest options to
+ * *out (base's other fields are kept).  pc_tune_trial of the last trial
+ * carries the options it ran with.
  *   xyz, w, w_is_f32, n, box   the catalogue, as for pc_build_grid
  *   b                          the bins the counts will use
  *   base                       starting options (NULL = defaults); priv 1 or

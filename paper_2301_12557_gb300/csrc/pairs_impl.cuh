@@ -267,7 +267,7 @@ __device__ __forceinline__ void build_segments(const PairParams &p, const GridDe
 // ---------------------------------------------------------------------------
 // rescue helpers
 // ---------------------------------------------------------------------------
-template <int MODE, int LOS>
+template <int MODE, int LOS, bool COUNT = true>
 __device__ __noinline__ void inline_rescue(const PairParams &p, uint3 e) {
     const int task = (int)(e.z >> 5), img = (int)(e.z & 31);
     const TaskDev &T = p.tasks[task];
@@ -279,7 +279,7 @@ __device__ __noinline__ void inline_rescue(const PairParams &p, uint3 e) {
         atomicAdd(&p.hist[h], 1ull);
         if (p.weighted) atomicAdd(&p.whist[h], __dmul_rn(a.w, b.w));
     }
-    atomicAdd(&p.counters[1], 1ull);
+    if (COUNT) atomicAdd(&p.counters[1], 1ull);
 }
 
 template <int MODE, int LOS>
@@ -309,8 +309,11 @@ __device__ __forceinline__ void drain_rescue(const PairParams &p, uint3 *s_q, Ct
     for (int k = tid; k < n; k += NT) {
         unsigned long long g = base + k;
         if (g < p.qcap) p.queue[g] = s_q[k];
-        else inline_rescue<MODE, LOS>(p, s_q[k]);
+        else inline_rescue<MODE, LOS, false>(p, s_q[k]);
     }
+    // entries past the queue were evaluated here: one counter update per drain
+    if (tid == 0 && base + n > p.qcap)
+        atomicAdd(&p.counters[1], base + n - max(base, p.qcap));
     gsync<G>();
     if (tid == 0) cs.qn = 0;
     gsync<G>();

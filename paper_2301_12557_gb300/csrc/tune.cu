@@ -5,7 +5,9 @@
 // sample of the point blocks -- the block-shard mechanism of the multi-GPU
 // path with one shard -- first for 2 and 4 i-points per thread at that side,
 // then at cell sides in quarter-octave steps from 0.7 to 2 times it, then
-// with one count copy per warp, and returns the fastest combination.
+// with one count copy per warp, then with the near-edge pairs evaluated
+// inside the pair kernel instead of queued, and returns the fastest
+// combination.
 #include <math.h>
 #include <string.h>
 
@@ -223,6 +225,34 @@ extern "C" pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, lon
         if (ms < best_ms) {
             best_ms = ms;
             out->priv = 1;
+        }
+    }
+    // near-edge pairs evaluated inside the pair kernel (no queue, no rescue
+    // kernel: the binary64 work interleaves with the FP32 pairs of other
+    // warps) at the best options, unless the caller fixed the queue size
+    if (fp32 && o.rescue_capacity == 0 && std::isfinite(best_ms)) {
+        pc_opts oc = *out;
+        pc_grid *g = nullptr;
+        pc_status s = pc_build_grid(xyz, w, w_is_f32, n, box, reach, &oc, stream, &g);
+        if (s != PC_OK) return s;
+        pc_opts ot = oc;
+        ot.rescue_capacity = -1;
+        ot.shard_index = 0;
+        ot.shard_count = S;
+        float ms = INFINITY;
+        for (int rep = 0; rep < 2 && s == PC_OK; ++rep) {
+            pc_stats sts;
+            s = pc_count_auto(g, b, &ot, stream, (long long *)dc.p, (double *)dw.p, &sts);
+            if (s == PC_OK) ms = std::min(ms, sts.ms_pairs + sts.ms_rescue);
+            if (ms > 4.f * TRIAL_MS) break;
+        }
+        pc_free_grid(g);
+        if (s != PC_OK) return s;
+        if (nt < max_trials) trials[nt] = pc_tune_trial{out->cell_size, out->ipt, out->priv, ms};
+        ++nt;
+        if (ms < best_ms) {
+            best_ms = ms;
+            out->rescue_capacity = -1;
         }
     }
     if (n_trials) *n_trials = std::min(nt, max_trials);

@@ -12,7 +12,6 @@
 
 import itertools
 import json
-import math
 import os
 from fractions import Fraction
 
