@@ -458,7 +458,10 @@ def run_ours(args):
     trec = traffic_record()
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
-                "traffic": (trec["bytes_per_launch"] if trec and not tree else None),
+                # the record holds for the grid kernel with the same rescue mode
+                "traffic": (trec["bytes_per_launch"]
+                            if trec and not tree and (trec.get("rescue") == "inline") ==
+                            (opts.rescue_capacity < 0) else None),
                 "kernel": "k_pairs_f32<SMU,LOS_Z>" + (" (tree variant)" if tree else ""),
                 "flops_per_launch": flops,
                 "flops_definition": (f"{FLOPS_PER_CANDIDATE} per pair evaluated one by one "
