@@ -442,6 +442,7 @@ def run_ours(args):
               "ms_per_step": statistics.mean(kd_ms), "steps": args.tree_steps,
               "step": "tree build + dual-tree traversal + pair and rescue kernels",
               "list_cap": cap_kd or "auto", "ipt": o_kd.ipt, "n_leaf": args.n_leaf,
+              "rescue": "inline" if o_kd.rescue_capacity < 0 else "queued",
               "tuning_seconds": tune_s,
               "counts_identical_to_grid": bool(torch.equal(out_kd, out))}
 

@@ -323,8 +323,10 @@ pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const pc_bins *b,
  * on every S-th block (S as in pc_tune), and writes the fastest: out->ipt
  * (base's other fields kept) and *list_cap for pc_build_tree; the automatic
  * level with 2 i-points is kept unless another option is more than 3 %
- * faster.  trials (cell_size holds the list_cap tried, 0 = automatic) and
- * n_trials as for pc_tune.
+ * faster.  A last trial (unless base fixes rescue_capacity) evaluates the
+ * near-edge pairs inside the pair kernel (out->rescue_capacity -1 when
+ * faster; its record has priv -1).  trials (cell_size holds the list_cap
+ * tried, 0 = automatic) and n_trials as for pc_tune.
  * Errors as pc_build_tree and pc_count_tree. */
 pc_status pc_tune_tree(const double *xyz, const void *w, int w_is_f32, long long n,
                        const pc_box *box, const pc_bins *b, int n_leaf, const pc_opts *base,

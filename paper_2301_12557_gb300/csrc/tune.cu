@@ -359,6 +359,23 @@ extern "C" pc_status pc_tune_tree(const double *xyz, const void *w, int w_is_f32
     if (std::isfinite(ms_default) && best_ms > 0.97f * ms_default) {
         out->ipt = 2;
         *list_cap = 0;
+        best_ms = ms_default;
+    }
+    // near-edge pairs evaluated inside the pair kernel, at the chosen options
+    if (o.rescue_capacity == 0 && o.prec == PC_PREC_F32_RESCUE && std::isfinite(best_ms)) {
+        pc_tree *t = nullptr;
+        pc_status s = pc_build_tree(xyz, w, w_is_f32, n, box, n_leaf, *list_cap, stream, &t);
+        if (s != PC_OK) return s;
+        pc_opts keep = o;
+        o.rescue_capacity = -1;
+        float ms = INFINITY;
+        s = run(t, out->ipt, ms);
+        o = keep;
+        pc_free_tree(t);
+        if (s != PC_OK) return s;
+        if (nt < max_trials) trials[nt] = pc_tune_trial{(double)*list_cap, out->ipt, -1, ms};
+        ++nt;
+        if (ms < best_ms) out->rescue_capacity = -1;
     }
     if (n_trials) *n_trials = std::min(nt, max_trials);
     PC_CUDA(cudaStreamSynchronize(st));
