@@ -267,7 +267,7 @@ void pc_free_tree(pc_tree *t);
 
 /* Size of a tree (any output may be NULL): points, deepest level, list
  * level, heap slots 2^(depth + 1) - 1. */
-pc_status pc_tree_info(const pc_tree *t, long long *n, int *depth, int *block_level,
+pc_status pc_tree_info(const pc_tree *t, long long *n, int *depth, int *list_level,
                        long long *slots);
 
 /* Copy the tree structure to HOST arrays (any may be NULL), heap order

@@ -503,8 +503,8 @@ __global__ void k_group_fill(const int2 *__restrict__ emit, int ne, int blk0_i, 
     seg[pos] = make_int2((e.y & 0xFFFFFF) - blk0_j, e.y >> 24);
 }
 
-// The pair kernel's blocks: every list node split into k balanced chunks of
-// at most TREE_BLOCK points ("cell" = the list node).
+// The pair kernel's blocks: every list node split into k balanced chunks
+// ("cell" = the list node; k is chosen so a chunk fits NT x ipt i-points).
 // (Batches: task `task`, list nodes numbered from node0, blocks written from
 // blocks[0]; *nblocks receives the batch's total.)
 __global__ void k_tree_blocks(const int2 *__restrict__ rng, int nlist, int k, int task, int node0,
@@ -775,12 +775,12 @@ extern "C" void pc_free_tree(pc_tree *t) {
     tree_release(t);
 }
 
-extern "C" pc_status pc_tree_info(const pc_tree *t, long long *n, int *depth, int *block_level,
+extern "C" pc_status pc_tree_info(const pc_tree *t, long long *n, int *depth, int *list_level,
                                   long long *slots) {
     if (!t) return fail(PC_EINVAL, "pc_tree_info: null tree");
     if (n) *n = t->n;
     if (depth) *depth = t->depth;
-    if (block_level) *block_level = t->blevel;
+    if (list_level) *list_level = t->blevel;
     if (slots) *slots = t->nslots;
     return PC_OK;
 }
