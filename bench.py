@@ -8,9 +8,11 @@ FP32 separations with binary64 rescue, int64 counts.
 
 One step = one pass of the whole path over the catalogue already resident in
 HBM: canonicalise + grid build (bounds, per-cell counts, scan, scatter),
-i-block list, pair kernel (separation, bin lookup, shared histograms),
-binary64 rescue kernel, histogram read-back.  The metric counts the pair
-separations the kernel evaluates ("pairs evaluated").
+i-block list, pair kernel (separation, bin lookup, shared histograms), the
+binary64 re-evaluation of near-edge pairs (inside the pair kernel or by the
+rescue kernel, as tuned), histogram read-back.  The value is in-range pairs
+binned per second: the one unit every exact method shares, whatever its cell
+size or pruning.
 
 Prints one JSON line.  --impl reference times the CPU oracle (brute force,
 binary64) on a bounded sample of the same workload instead.
@@ -38,6 +40,7 @@ UNIT = "pairs/s"                 # in-range pairs binned per second (every arm)
 FLOPS_PER_CANDIDATE = 8          # separation: 3 subtractions, 3 multiplies, 2 adds
 FLOPS_PER_IN_RANGE = 6           # bin locate per in-range pair
 FP32_LANES_PER_SM = 128
+FP64_PEAK_NOMINAL = 1.25         # TFLOP/s, GB300 FP64 (non-tensor), nominal
 
 
 def parse():
@@ -169,7 +172,20 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU oracle on a bounded sample
 # --------------------------------------------------------------------------
-def oracle_sample_rate(D, w, seconds, seed=0, L=None):
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the oracle's line."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample_rate(D, w, seconds, seed=0, L=None, threads=None):
     """Oracle throughput in in-range pairs binned per second: brute force over
     all pairs of a random sample of i-points against the whole catalogue (the
     cross form of the same pair set), self-pairs excluded.  Returns (rate,
@@ -184,7 +200,7 @@ def oracle_sample_rate(D, w, seconds, seed=0, L=None):
     while True:      # calibrate on growing samples until one takes >= 1/8 of the budget
         S = np.ascontiguousarray(D[rng.choice(n, m0, replace=False)])
         t = time.perf_counter()
-        oracle.count(S, D, **kw)
+        oracle.count(S, D, threads=threads, **kw)
         dt = max(time.perf_counter() - t, 1e-6)
         if dt >= seconds / 8 or m0 >= n:
             break
@@ -192,9 +208,9 @@ def oracle_sample_rate(D, w, seconds, seed=0, L=None):
     m = int(max(1, min(n, m0 * seconds / dt)))
     S = np.ascontiguousarray(D[rng.choice(n, m, replace=False)])
     t = time.perf_counter()
-    c, _ = oracle.count(S, D, **kw)
+    c, _ = oracle.count(S, D, threads=threads, **kw)
     dt = time.perf_counter() - t
-    cores = oracle.default_threads()
+    cores = threads or oracle.default_threads()
     in_range = int(c.sum()) - m        # each sampled point pairs with itself at s = 0
     return in_range / dt, dt, m, cores, m * n / dt
 
@@ -408,10 +424,20 @@ def run_ours(args):
             torch.cuda.synchronize()
             ms64.append(a.elapsed_time(b))
         exact = bool(torch.equal(out64, out))
-        fp64 = {"value": float(out64.sum().item()) / (statistics.mean(ms64) * 1e-3), "unit": UNIT,
+        inr64 = float(out64.sum().item())
+        # the FP64 kernel evaluates every candidate: the same per-pair flop
+        # counts, against GB300's nominal FP64 (non-tensor) rate
+        fl64 = FLOPS_PER_CANDIDATE * float(s64.candidates) + FLOPS_PER_IN_RANGE * inr64
+        k64_ms = s64.ms_pairs if s64.ms_pairs > 0 else statistics.mean(ms64)
+        ach64 = fl64 / (k64_ms * 1e-3) / 1e12
+        fp64 = {"value": inr64 / (statistics.mean(ms64) * 1e-3), "unit": UNIT,
                 "cell_size": o64.cell_size,
                 "ms_per_step": statistics.mean(ms64), "steps": args.fp64_steps,
-                "counts_identical_to_fp32_rescue": exact}
+                "counts_identical_to_fp32_rescue": exact,
+                "roofline": {"bound": "fp64", "achieved": ach64, "peak": FP64_PEAK_NOMINAL,
+                             "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_NOMINAL,
+                             "peak_source": "nominal GB300 FP64 rate (not measured)",
+                             "kernel_ms": k64_ms}}
 
     # ---- the k-d tree path on the same catalogue (grid line only) -----------
     kd = None
@@ -477,10 +503,15 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, dt, m, cores, evals = oracle_sample_rate(D_host, w, args.cpu_seconds, L=L_box)
+        r1, dt1, m1, _, _ = oracle_sample_rate(D_host, w, args.cpu_seconds / 4, seed=1, L=L_box,
+                                               threads=1)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{m} random i-points x all {n} points (brute force, binary64), "
                          f"{dt:.1f} s; in-range pairs found per second",
-               "pair_evaluations_per_s": evals}
+               "pair_evaluations_per_s": evals,
+               "cpu_model": cpu_model(),
+               "single_core": {"value": r1, "unit": UNIT,
+                               "sample": f"{m1} random i-points x all {n} points, {dt1:.1f} s"}}
 
     if rank == 0:
         s0 = stats[0]
