@@ -359,6 +359,19 @@ pc_status pc_hist_s2(const float *s2, long long n, int repeat, const double *edg
  * the three grid-build passes of Sect. 2.1.  lo/hi are host arrays of 3. */
 pc_status pc_aabb(const double *xyz, long long n, void *stream, double *lo, double *hi);
 
+/* The stencil rows the grid path enumerates for cells of sides cell[3] and
+ * largest separation r_max (Sect. 2.1; Sect. 3.1 duplicate removal when
+ * half != 0).  Host-only: no device work.  Row k is rows[4k .. 4k + 3] =
+ * {dy, dz, xlo, xhi}: the neighbour cells at offsets (dx, dy, dz) for dx in
+ * [xlo, xhi].  A cell offset is in the full stencil when the smallest
+ * distance between the two cells, max(|d| - 1, 0) x side per axis, is below
+ * r_max.  The half stencil keeps exactly one of each pair of opposite
+ * offsets (the own cell is the kernel's own-block pass and the offsets
+ * (dx > 0, 0, 0)).  *n_rows receives the row count; PC_EOVERFLOW when it
+ * exceeds max_rows. */
+pc_status pc_stencil(const double cell[3], double r_max, int half, int max_rows, int *rows,
+                     int *n_rows);
+
 /* Cell side the cost model picks for n points in volume `volume` with
  * largest separation r_max (Appendix B.1: cost a N_pair + b N_node). */
 double pc_suggest_cell_size(long long n, double volume, double r_max, int mode);

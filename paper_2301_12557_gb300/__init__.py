@@ -75,7 +75,7 @@ EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc
            "pc_count_batch", "pc_aabb", "pc_suggest_cell_size", "pc_strerror", "pc_last_error",
            "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune",
            "pc_build_tree", "pc_free_tree", "pc_tree_info", "pc_tree_export", "pc_count_tree",
-           "pc_tune_tree", "pc_hist_s2", "pc_count_tree_batch"]
+           "pc_tune_tree", "pc_hist_s2", "pc_count_tree_batch", "pc_stencil"]
 
 
 def library_path() -> str:
@@ -150,6 +150,9 @@ def lib():
     L.pc_hist_s2.restype = c_int
     L.pc_hist_s2.argtypes = [vp, c_longlong, c_int, POINTER(c_double), c_int, c_int, c_int, vp, vp,
                              POINTER(c_float)]
+    L.pc_stencil.restype = c_int
+    L.pc_stencil.argtypes = [POINTER(c_double), c_double, c_int, c_int, POINTER(c_int),
+                             POINTER(c_int)]
     L.pc_count_tree_batch.restype = c_int
     L.pc_count_tree_batch.argtypes = [POINTER(vp), c_int, POINTER(pc_bins), POINTER(pc_opts), vp,
                                       vp, vp, POINTER(pc_stats)]
@@ -583,6 +586,17 @@ def pc_aabb(xyz, stream=None):
     _check(lib().pc_aabb(px, n, _stream_handle(stream), lo, hi), "pc_aabb")
     del keep
     return np.array(lo[:]), np.array(hi[:])
+
+
+def pc_stencil(cell, r_max: float, half: bool = False) -> np.ndarray:
+    """Stencil rows {dy, dz, xlo, xhi} of the grid path (host-only)."""
+    c = (c_double * 3)(*np.broadcast_to(np.asarray(cell, dtype=np.float64), (3,)))
+    nr = c_int(0)
+    lib().pc_stencil(c, float(r_max), int(bool(half)), 0, None, ctypes.byref(nr))
+    rows = np.zeros((max(nr.value, 1), 4), dtype=np.int32)
+    _check(lib().pc_stencil(c, float(r_max), int(bool(half)), nr.value,
+                            rows.ctypes.data_as(POINTER(c_int)), ctypes.byref(nr)), "pc_stencil")
+    return rows[:nr.value]
 
 
 def pc_suggest_cell_size(n: int, volume: float, r_max: float, mode: int = 0) -> float:

@@ -1397,6 +1397,36 @@ extern "C" pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const 
     return PC_OK;
 }
 
+// Host-only view of the stencil the grid path enumerates (no device work).
+extern "C" pc_status pc_stencil(const double cell[3], double r_max, int half, int max_rows,
+                                int *rows, int *n_rows) {
+    if (!cell || !n_rows || max_rows < 0 || (max_rows > 0 && !rows))
+        return fail(PC_EINVAL, "pc_stencil: bad arguments");
+    if (!(r_max > 0.0) || !std::isfinite(r_max))
+        return fail(PC_EINVAL, "pc_stencil: r_max must be positive and finite");
+    Geom g;
+    memset(&g, 0, sizeof(g));
+    for (int a = 0; a < 3; ++a) {
+        if (!(cell[a] > 0.0) || !std::isfinite(cell[a]))
+            return fail(PC_EINVAL, "pc_stencil: cell sides must be positive and finite");
+        if (r_max / cell[a] > 4096.0) return fail(PC_EOVERFLOW, "pc_stencil: too many cells per axis");
+        g.c[a] = cell[a];
+        g.ng[a] = 1;
+    }
+    std::vector<int4> st;
+    int kmax[3];
+    build_stencil(g, r_max, half != 0, st, kmax);
+    *n_rows = (int)st.size();
+    if ((int)st.size() > max_rows) return fail(PC_EOVERFLOW, "pc_stencil: max_rows too small");
+    for (size_t k = 0; k < st.size(); ++k) {
+        rows[4 * k] = st[k].x;
+        rows[4 * k + 1] = st[k].y;
+        rows[4 * k + 2] = st[k].z;
+        rows[4 * k + 3] = st[k].w;
+    }
+    return PC_OK;
+}
+
 // Cost model of Appendix B.1 (cost = a N_pair + b N_node), specialised to the
 // GPU kernel: candidate pairs are charged per thread lane (a block occupies
 // NT * 2 lanes however many points its cell holds), and every (block,
