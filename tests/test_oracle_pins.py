@@ -6,6 +6,7 @@
 * a library special case (scipy cKDTree neighbour counts, a single s range);
 * closed forms for uniform periodic randoms (Eq. npair_valid generalised to
   shells; uniform mu; cylinder volumes for (sigma, pi));
+* exact rational weighted sums with dyadic weights on the same lattices;
 * invariants: cross(D, D) vs auto(D), DR = RD, permutations, scaling by a
   power of two (Sect. 3.2.4), unit weights, brute force vs cell list.
 """
@@ -113,6 +114,26 @@ def _exact_counts(x, L, periodic, mode, los, ea, eb):
     return h
 
 
+def _exact_wsums(x, w, y, wy, L, periodic, mode, los, ea, eb):
+    """Exact per-bin sums of w_i w_j over the pairs of x (auto, i < j) or
+    x x y (cross), in rational arithmetic."""
+    nb = (len(ea) - 1) * (1 if mode == "s" else len(eb) - 1)
+    h = [Fraction(0)] * nb
+    px = [tuple(int(v) for v in p) for p in x]
+    if y is None:
+        pairs = ((i, j, px[i], px[j], w[i], w[j])
+                 for i, j in itertools.combinations(range(len(px)), 2))
+    else:
+        py = [tuple(int(v) for v in p) for p in y]
+        pairs = ((i, j, px[i], py[j], w[i], wy[j])
+                 for i in range(len(px)) for j in range(len(py)))
+    for _, _, a, b, wa, wb in pairs:
+        k = _exact_bin(a, b, L, periodic, mode, los, ea, eb)
+        if k >= 0:
+            h[k] += Fraction(wa) * Fraction(wb)
+    return h
+
+
 LATTICE_CASES = [
     # (mode, los, periodic, edges_a, edges_b)
     ("s", "z", True, [0, 1, 2, 3, 4, 5], None),
@@ -140,6 +161,30 @@ def test_lattice_exact(mode, los, periodic, ea, eb):
         got_g, _ = oracle.count(x, box=float(side), periodic=periodic, mode=mode, los=los,
                                 edges_a=ea, edges_b=eb, method="grid")
         assert got_g.tolist() == want.tolist()
+
+
+@pytest.mark.parametrize("mode,los,periodic,ea,eb", LATTICE_CASES[::2] + [LATTICE_CASES[-1]])
+def test_lattice_weighted_exact(mode, los, periodic, ea, eb):
+    """Weighted sums (Sect. 2.5: each pair adds w_i w_j) with dyadic weights
+    k/8: every product and partial sum is exact in binary64, so the sums must
+    equal the rational ones bit for bit, for auto and cross counts and for
+    every method."""
+    side = 9
+    rng = np.random.default_rng(5)
+    x = synth.lattice_points(50, side, 31, unique=False)
+    y = synth.lattice_points(40, side, 32, unique=False)
+    if los == "mid":
+        x, y = x + np.array([20.0, -3.0, 5.0]), y + np.array([20.0, -3.0, 5.0])
+    w = rng.integers(1, 8, x.shape[0]) / 8.0
+    wy = rng.integers(1, 8, y.shape[0]) / 8.0
+    kw = dict(box=float(side), periodic=periodic, mode=mode, los=los, edges_a=ea, edges_b=eb)
+    want_a = [float(v) for v in _exact_wsums(x, w, None, None, side, periodic, mode, los, ea, eb)]
+    want_x = [float(v) for v in _exact_wsums(x, w, y, wy, side, periodic, mode, los, ea, eb)]
+    for method in ("brute", "grid", "kdtree"):
+        _, got = oracle.count(x, w1=w, method=method, n_leaf=3, **kw)
+        assert got.tolist() == want_a, (method, "auto")
+        _, got = oracle.count(x, y, w1=w, w2=wy, method=method, n_leaf=3, **kw)
+        assert got.tolist() == want_x, (method, "cross")
 
 
 # --------------------------------------------------------------------------
