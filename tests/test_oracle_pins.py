@@ -8,7 +8,8 @@
   shells; uniform mu; cylinder volumes for (sigma, pi));
 * exact rational weighted sums with dyadic weights on the same lattices;
 * invariants: cross(D, D) vs auto(D), DR = RD, permutations, scaling by a
-  power of two (Sect. 3.2.4), unit weights, brute force vs cell list.
+  power of two (Sect. 3.2.4), unit weights, brute force vs cell list, the mu
+  marginal of H(s, mu) equal to H(s).
 """
 
 import itertools
@@ -314,6 +315,29 @@ def test_power_of_two_rescaling_is_exact(k):
         b, _ = oracle.count(x * f, box=L * f, periodic=True, mode=mode, edges_a=ea * f,
                             edges_b=eb2)
         assert a.tolist() == b.tolist(), mode
+
+
+@pytest.mark.parametrize("los,periodic", [("z", True), ("z", False), ("mid", False)])
+def test_mu_marginal_equals_s_histogram(los, periodic):
+    """mu edges spanning [0, 1] put every in-range pair in exactly one mu bin
+    (Sect. 2.5: mu = |pi| / s lies in [0, 1], the top edge closed), so the
+    sum over mu of H(s, mu) is H(s), bit for bit, and the weighted sums
+    agree to rounding."""
+    L = 90.0
+    x = synth.neyman_scott(2000, 200, 10.0, 2.0, L, 91)
+    x[:5] = x[5]                        # coincident points: s = 0, mu bin 0
+    x[7] = x[6] + np.array([0.0, 0.0, 3.0])   # a pair along the z axis: mu = 1
+    if not periodic:
+        x = x + 400.0
+    w = synth.lognormal_weights(x.shape[0], 0.3, 9, np.float64)
+    ea = np.linspace(0.0, 18.0, 10)
+    mu = np.linspace(0.0, 1.0, 13)
+    kw = dict(box=L, periodic=periodic, los=los, edges_a=ea, w1=w)
+    for method in ("brute", "grid", "kdtree"):
+        hs, ws = oracle.count(x, mode="s", method=method, **kw)
+        hm, wm = oracle.count(x, mode="smu", edges_b=mu, method=method, **kw)
+        assert hm.reshape(len(ea) - 1, -1).sum(axis=1).tolist() == hs.tolist(), method
+        np.testing.assert_allclose(wm.reshape(len(ea) - 1, -1).sum(axis=1), ws, rtol=1e-13)
 
 
 def test_unit_weights_reproduce_counts():
