@@ -1,10 +1,12 @@
 """CPU-side checks of the C ABI: the library builds, loads, exports every
-entry point declared in include/paircount.h, and rejects bad arguments on
-the host (no kernel is launched here)."""
+entry point declared in include/paircount.h, the binding's structs, enums and
+argument lists match the header, and bad arguments are rejected on the host
+(no kernel is launched here)."""
 
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -155,3 +157,61 @@ def test_tree_and_hist_host_side_checks(lib):
     bad = np.array([0.0, 2.0, 1.0])
     assert lib.pc_hist_s2(s2.ctypes.data, 8, 1, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                           2, 0, 0, None, cnt.ctypes.data, None) == P.PC_EINVAL
+
+
+def _c_layout(tmp_path):
+    """sizeof/offsetof of every header struct and the enum values, as a C
+    compiler lays them out from include/paircount.h."""
+    structs = {"pc_box": P.pc_box, "pc_bins": P.pc_bins, "pc_opts": P.pc_opts,
+               "pc_stats": P.pc_stats, "pc_tune_trial": P.pc_tune_trial}
+    enums = ["PC_OK", "PC_EINVAL", "PC_ENOMEM", "PC_ECUDA", "PC_EOVERFLOW", "PC_ETIMEOUT",
+             "PC_EUNSUPPORTED", "PC_BIN_S", "PC_BIN_SMU", "PC_BIN_SIGPI", "PC_LOS_Z",
+             "PC_LOS_MIDPOINT", "PC_PREC_F32_RESCUE", "PC_PREC_F64"]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "paircount.h"',
+             "int main(void) {"]
+    for s, cls in structs.items():
+        lines.append(f'printf("{s} size %zu\\n", sizeof({s}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{s}.{f} off %zu size %zu\\n", offsetof({s}, {f}), '
+                         f'sizeof((({s} *)0)->{f}));')
+    for e in enums:
+        lines.append(f'printf("{e} val %d\\n", (int){e});')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-o", str(exe), str(src)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for ln in out.splitlines():
+        parts = ln.split()
+        got[parts[0]] = [int(v) for v in parts[2::2]]
+    return structs, enums, got
+
+
+def test_binding_structs_and_enums_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C layout (size and
+    every field's offset and size), and the Python constants the header's
+    enum values; a field added to one side only fails here."""
+    structs, enums, got = _c_layout(tmp_path)
+    for s, cls in structs.items():
+        assert got[s] == [ctypes.sizeof(cls)], s
+        for f, _ in cls._fields_:
+            fld = getattr(cls, f)
+            assert got[f"{s}.{f}"] == [fld.offset, fld.size], (s, f)
+    for e in enums:
+        assert got[e] == [getattr(P, e)], e
+
+
+def test_binding_argument_counts_match_the_prototypes(lib):
+    """Every prototype in the header takes as many parameters as the
+    binding's ctypes argtypes declare."""
+    txt = open(os.path.join(ROOT, "include", "paircount.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = re.findall(r"^[\w \*]*?\b(pc_\w+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.M | re.S)
+    assert len(protos) >= len(P.EXPORTS)
+    for name, params in protos:
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(getattr(lib, name).argtypes) == n, name
