@@ -694,7 +694,7 @@ static pc_status upload_tables(const CountJob &J, const CountSetup &S, const Dev
 static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBufs &B,
                              PairParams &p, int &grid, size_t &smem) {
     const Plan &P = S.P;
-    memset(&p, 0, sizeof(p));
+    memset(static_cast<void *>(&p), 0, sizeof(p));
     p.groups = 1;
     p.tree = J.tree ? 1 : 0;
     p.tasks = B.tasks;
@@ -1635,7 +1635,7 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
                              (int *)(base + NA.tot), st));
 
     PairParams p;
-    memset(&p, 0, sizeof(p));
+    memset(static_cast<void *>(&p), 0, sizeof(p));
     p.groups = 1;
     p.tasks = tasks;
     p.blocks = (const Block *)(base + NA.blocks);

@@ -510,7 +510,7 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     };
 
     pc_grid *g = new pc_grid();
-    memset(g, 0, sizeof(*g));
+    memset(static_cast<void *>(g), 0, sizeof(*g));
     g->device = dev;
     g->n = (int)n;
     g->weighted = (w != nullptr);

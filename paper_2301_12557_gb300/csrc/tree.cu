@@ -833,7 +833,7 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
     PC_CUDA(cudaGetDevice(&dev));
 
     pc_tree *t = new pc_tree();
-    memset(t, 0, sizeof(*t));
+    memset(static_cast<void *>(t), 0, sizeof(*t));
     t->device = dev;
     t->n = (int)n;
     t->weighted = (w != nullptr);
