@@ -142,8 +142,13 @@ typedef struct pc_grid pc_grid;  /* opaque; owned by the library */
  *   stream    cudaStream_t (NULL = legacy default stream); all work is
  *             ordered on it and the call returns once the grid is built
  *   out       receives the new grid; release it with pc_free_grid
+ * A periodic axis gets at least 2k + 1 cells for a stencil reach of k cells,
+ * so that no two neighbour offsets reach the same cell; the cell side along
+ * each axis is L[a] over its cell count (boxes may differ per axis).
  * Errors: PC_EINVAL (n < 0, NULL pointers, bad box, points outside given
- * bounds), PC_EOVERFLOW (n >= 2^31 or too many cells), PC_ENOMEM, PC_ECUDA. */
+ * bounds), PC_EOVERFLOW (n >= 2^31, or more than 2^26 cells -- e.g. a
+ * periodic r_max within about 0.5 % of L/2, which the k-d tree path takes),
+ * PC_ENOMEM, PC_ECUDA. */
 pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f32, long long n,
                         const pc_box *box, double r_max, const pc_opts *opt,
                         void *stream, pc_grid **out);
