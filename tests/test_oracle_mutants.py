@@ -2,13 +2,13 @@
 
 Each case copies the oracle's C source, plants one plausible mistake (a
 dropped periodic wrap, an edge or mu tie sent to the lower bin, a dropped
-term, self pairs counted, a pair weight squared, the line of sight from the
-wrong component or the wrong midpoint, a k-d tree that loses a child pair or
-prunes without the periodic images, a median split off by one), compiles the
-copy, loads it in
-place of the oracle and runs the pins of test_oracle_pins.py and
-test_oracle_kdtree.py against it: at least one must fail.  The mutants live
-in a temporary directory; the oracle's source is not touched.
+term, self pairs counted, a pair weight squared, weights summed without
+compensation, the line of sight from the wrong component or the wrong
+midpoint, a k-d tree that loses a child pair or prunes without the periodic
+images, a median split off by one), compiles the copy, loads it in place of
+the oracle and runs the pins of test_oracle_pins.py and test_oracle_kdtree.py
+against it: at least one must fail.  The mutants live in a temporary
+directory; the oracle's source is not touched.
 """
 
 import ctypes
@@ -38,6 +38,8 @@ MUTANTS = {
     "tree_lost_child": ("st[top++] = (npair){2 * q.a + 1, 2 * q.a + 2};", ""),
     "tree_no_images": ("int ns = c->periodic ? 3 : 1;", "int ns = 1;"),
     "weight_square": ("jb->w1[i] * jb->w2[j]);", "jb->w1[i] * jb->w1[i]);"),
+    "no_compensation": ("    if (fabs(*sum) >= fabs(v)) *comp += (*sum - t) + v;\n"
+                        "    else *comp += (v - t) + *sum;\n", ""),
     "tree_median_off": ("int64_t nl = count / 2;", "int64_t nl = (count + 1) / 2;"),
 }
 
@@ -48,6 +50,8 @@ def _pins():
         yield lambda c=case: T.test_lattice_exact(*c)
     for case in T.LATTICE_CASES[::2]:
         yield lambda c=case: T.test_lattice_weighted_exact(*c)
+    for method in ("brute", "kdtree"):
+        yield lambda m=method: T.test_weighted_sums_are_the_exactly_rounded_sums(m)
     yield T.test_cube_corner_golden
     yield T.test_midpoint_golden
     yield T.test_mu_closed_top_and_zero_separation

@@ -6,7 +6,8 @@
 * a library special case (scipy cKDTree neighbour counts, a single s range);
 * closed forms for uniform periodic randoms (Eq. npair_valid generalised to
   shells; uniform mu; cylinder volumes for (sigma, pi));
-* exact rational weighted sums with dyadic weights on the same lattices;
+* exact rational weighted sums with dyadic weights on the same lattices, and
+  weighted sums within one ulp of the exactly rounded sum (math.fsum);
 * invariants: cross(D, D) vs auto(D), DR = RD, permutations, scaling by a
   power of two (Sect. 3.2.4), unit weights, brute force vs cell list, the mu
   marginal of H(s, mu) equal to H(s).
@@ -338,6 +339,34 @@ def test_mu_marginal_equals_s_histogram(los, periodic):
         hm, wm = oracle.count(x, mode="smu", edges_b=mu, method=method, **kw)
         assert hm.reshape(len(ea) - 1, -1).sum(axis=1).tolist() == hs.tolist(), method
         np.testing.assert_allclose(wm.reshape(len(ea) - 1, -1).sum(axis=1), ws, rtol=1e-13)
+
+
+@pytest.mark.parametrize("method", ["brute", "grid", "kdtree"])
+def test_weighted_sums_are_the_exactly_rounded_sums(method):
+    """Each bin's weighted sum is the sum of the rounded products
+    fl(w_i w_j) over its pairs (Sect. 2.5 pair weight); the compensated sum
+    must lie within one ulp of that sum rounded once (math.fsum), where a
+    plain running sum drifts by tens of ulps over the thousands of pairs per
+    bin.  Bins come from numpy's own evaluation of the definition (generic
+    reals, so no pair sits on an edge), checked against the oracle's counts."""
+    import math
+    L, N = 50.0, 2000
+    x = synth.uniform_box(N, L, 77)
+    w = synth.lognormal_weights(N, 0.3, 78, np.float64)
+    ea = np.linspace(0.0, 10.0, 11)
+    i, j = np.triu_indices(N, 1)
+    d = x[j] - x[i]
+    d = np.where(d > L / 2, d - L, np.where(d < -L / 2, d + L, d))
+    s2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    E = ea * ea
+    k = np.searchsorted(E, s2, side="right") - 1
+    ok = (k >= 0) & (s2 < E[-1])
+    prod = w[i] * w[j]
+    exact = np.array([math.fsum(prod[ok & (k == b)]) for b in range(ea.size - 1)])
+    cnt = np.array([int((ok & (k == b)).sum()) for b in range(ea.size - 1)])
+    c, ws = oracle.count(x, w1=w, box=L, periodic=True, edges_a=ea, method=method)
+    assert c.tolist() == cnt.tolist()
+    assert np.all(np.abs(ws - exact) <= np.spacing(exact)), (ws - exact) / np.spacing(exact)
 
 
 def test_unit_weights_reproduce_counts():
