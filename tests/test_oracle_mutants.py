@@ -3,12 +3,12 @@
 Each case copies the oracle's C source, plants one plausible mistake (a
 dropped periodic wrap, an edge or mu tie sent to the lower bin, a dropped
 term, self pairs counted, a pair weight squared, weights summed without
-compensation, the line of sight from the wrong component or the wrong
-midpoint, a k-d tree that loses a child pair or prunes without the periodic
-images, a median split off by one), compiles the copy, loads it in place of
-the oracle and runs the pins of test_oracle_pins.py and test_oracle_kdtree.py
-against it: at least one must fail.  The mutants live in a temporary
-directory; the oracle's source is not touched.
+compensation, sigma^2 left unclamped, the line of sight from the wrong
+component or the wrong midpoint, a k-d tree that loses a child pair or prunes
+without the periodic images, a median split off by one), compiles the copy,
+loads it in place of the oracle and runs the pins of test_oracle_pins.py and
+test_oracle_kdtree.py against it: at least one must fail.  The mutants live
+in a temporary directory; the oracle's source is not touched.
 """
 
 import ctypes
@@ -40,6 +40,7 @@ MUTANTS = {
     "weight_square": ("jb->w1[i] * jb->w2[j]);", "jb->w1[i] * jb->w1[i]);"),
     "no_compensation": ("    if (fabs(*sum) >= fabs(v)) *comp += (*sum - t) + v;\n"
                         "    else *comp += (v - t) + *sum;\n", ""),
+    "sigma_no_clamp": ("    if (q2 < 0.0) q2 = 0.0;\n", ""),
     "tree_median_off": ("int64_t nl = count / 2;", "int64_t nl = (count + 1) / 2;"),
 }
 
@@ -52,6 +53,7 @@ def _pins():
         yield lambda c=case: T.test_lattice_weighted_exact(*c)
     for method in ("brute", "kdtree"):
         yield lambda m=method: T.test_weighted_sums_are_the_exactly_rounded_sums(m)
+    yield T.test_radial_pairs_have_zero_sigma
     yield T.test_cube_corner_golden
     yield T.test_midpoint_golden
     yield T.test_mu_closed_top_and_zero_separation

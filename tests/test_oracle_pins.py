@@ -441,6 +441,35 @@ def test_mu_closed_top_and_zero_separation():
     assert oracle.pair_bin([1, 1, 1], [1, 1, 1], mode="smu", edges_a=ea, edges_b=mu) == 0
 
 
+def test_radial_pairs_have_zero_sigma():
+    """Pairs on a ray from the observer lie along their own midpoint line of
+    sight (Sect. 2.5: l = x_i + x_j parallel to d), so sigma vanishes up to
+    the rounding of the coordinates and pi = |d|.  In binary64 pi^2 often
+    exceeds s^2 by a rounding error; the definition clamps sigma^2 at 0, and
+    every pair must land in the first sigma bin and the pi bin of |d|, as the
+    exact rational evaluation of the same coordinates says."""
+    rng = np.random.default_rng(5)
+    n = 2000
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    r1 = rng.uniform(500.0, 1500.0, n)
+    dd = rng.uniform(0.5, 19.5, n)
+    dd[np.abs(dd - np.round(dd / 5.0) * 5.0) < 1e-6] += 0.1    # keep off the pi edges
+    a = u * r1[:, None]
+    b = u * (r1 + dd)[:, None]
+    ea, eb = [0.0, 1.0, 2.0, 4.0], [0.0, 5.0, 10.0, 20.0]
+    for k in range(n):
+        got = oracle.pair_bin(a[k], b[k], mode="sigpi", los="mid", edges_a=ea, edges_b=eb)
+        ex = _exact_bin(tuple(a[k]), tuple(b[k]), 0, False, "sigpi", "mid", ea, eb)
+        assert got == ex, (k, got, ex)
+        assert 0 <= got < 3          # sigma bin 0
+        if k < 40:                   # the count drivers take the same decision
+            for method in ("brute", "grid", "kdtree"):
+                c, _ = oracle.count(np.stack([a[k], b[k]]), mode="sigpi", los="mid",
+                                    edges_a=ea, edges_b=eb, method=method)
+                assert c.sum() == 1 and c[ex] == 1, (k, method)
+
+
 def test_invalid_arguments_raise():
     x = synth.uniform_box(10, 10.0, 1)
     with pytest.raises(ValueError):
