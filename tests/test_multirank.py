@@ -68,6 +68,37 @@ def test_two_rank_shards_sum_to_the_full_count():
     assert all(p.exitcode == 0 for p in procs)
 
 
+def _max_worker(rank, world, port, q):
+    try:
+        os.environ["MASTER_ADDR"] = "127.0.0.1"
+        os.environ["MASTER_PORT"] = str(port)
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+        import bench
+        v = bench.max_over_ranks(10.0 * (rank + 1), dist, torch.device("cpu"))
+        q.put((rank, v))
+        dist.barrier()
+        dist.destroy_process_group()
+    except Exception as e:  # pragma: no cover
+        q.put(("error", repr(e)))
+
+
+def test_bench_max_over_ranks():
+    """The benchmark's max-over-ranks reduction (its timing rule) on two gloo
+    ranks, and its one-process form."""
+    import bench
+    assert bench.max_over_ranks(3.5, None, None) == 3.5
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_max_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=240) for _ in range(2))
+    for p in procs:
+        p.join(timeout=240)
+    assert res == [(0, 20.0), (1, 20.0)], res
+
+
 def test_shard_units_partition():
     from paper_2301_12557_gb300 import shard
     for n in (0, 1, 7, 256):
