@@ -376,7 +376,8 @@ def run_ours(args):
     launches = P.pc_launch_count() - launches0
     clocks = sampler.stop()
     barrier()
-    tot_ms = sum(a.elapsed_time(b) for a, b in ev)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
     t_local = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
     # every step bins the same pairs: this rank's in-range pairs (its shard's
     # share under block shards) times the steps
@@ -531,6 +532,10 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            # the paper's timing rule (App. A): drop the slowest and the
+            # fastest run, average the rest (rank 0's steps)
+            "ms_per_step_trimmed": (statistics.mean(sorted(step_ms)[1:-1])
+                                    if len(step_ms) >= 3 else None),
             "scaling": "strong" if (args.shard and world > 1) else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name if args.volume_scale == 1.0 else
