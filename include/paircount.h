@@ -377,6 +377,29 @@ pc_status pc_aabb(const double *xyz, long long n, void *stream, double *lo, doub
 pc_status pc_stencil(const double cell[3], double r_max, int half, int max_rows, int *rows,
                      int *n_rows);
 
+/* The FP32 path's error bands for a count (Sect. 2.5 quantities; how the
+ * fast path stays exact is stated at the top of this header).  Host-only: no
+ * device work.  For bins b on cells of sides cell[3] (the cell side, or for
+ * the tree path the largest list-node extent), points within [lo, hi] per
+ * axis, a periodic box of sides L[3] (L may be NULL when periodic == 0) and
+ * rmin, a lower bound of the points' distance from the observer (midpoint
+ * line of sight; 0 if unknown), out[0..7] receives:
+ *   0 eps_a   band of s (s and (s, mu) bins) or of sigma ((sigma, pi) bins)
+ *   1 eps_b   band of pi ((sigma, pi) bins)
+ *   2 mu_A    the mu band is mu_A / s + mu_B ((s, mu) bins)
+ *   3 mu_B
+ *   4 rcut    FP32 candidate cut on the separation (largest separation plus
+ *             twice the largest band)
+ *   5 fp32_ok 1 when the FP32 path's bound holds (else counts run in FP64)
+ *   6 lin     1 when the bins are found by a floor instead of tables
+ *   7 r2cut   the FP32 cut the kernel compares s^2 against
+ * A pair takes the fast path's bin only when its FP32 value lies at least
+ * the band away from every edge; closer pairs are decided in binary64.
+ * Errors: PC_EINVAL (NULL pointers, bad cell sides, bounds, box or bins). */
+pc_status pc_fp32_bands(const pc_bins *b, const double cell[3], const double lo[3],
+                        const double hi[3], const double L[3], int periodic, double rmin,
+                        double out[8]);
+
 /* Cell side the cost model picks for n points in volume `volume` with
  * largest separation r_max (Appendix B.1: cost a N_pair + b N_node). */
 double pc_suggest_cell_size(long long n, double volume, double r_max, int mode);

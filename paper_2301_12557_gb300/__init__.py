@@ -75,7 +75,7 @@ EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc
            "pc_count_batch", "pc_aabb", "pc_suggest_cell_size", "pc_strerror", "pc_last_error",
            "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune",
            "pc_build_tree", "pc_free_tree", "pc_tree_info", "pc_tree_export", "pc_count_tree",
-           "pc_tune_tree", "pc_hist_s2", "pc_count_tree_batch", "pc_stencil"]
+           "pc_tune_tree", "pc_hist_s2", "pc_count_tree_batch", "pc_stencil", "pc_fp32_bands"]
 
 
 def library_path() -> str:
@@ -153,6 +153,10 @@ def lib():
     L.pc_stencil.restype = c_int
     L.pc_stencil.argtypes = [POINTER(c_double), c_double, c_int, c_int, POINTER(c_int),
                              POINTER(c_int)]
+    L.pc_fp32_bands.restype = c_int
+    L.pc_fp32_bands.argtypes = [POINTER(pc_bins), POINTER(c_double), POINTER(c_double),
+                                POINTER(c_double), POINTER(c_double), c_int, c_double,
+                                POINTER(c_double)]
     L.pc_count_tree_batch.restype = c_int
     L.pc_count_tree_batch.argtypes = [POINTER(vp), c_int, POINTER(pc_bins), POINTER(pc_opts), vp,
                                       vp, vp, POINTER(pc_stats)]
@@ -597,6 +601,19 @@ def pc_stencil(cell, r_max: float, half: bool = False) -> np.ndarray:
     _check(lib().pc_stencil(c, float(r_max), int(bool(half)), nr.value,
                             rows.ctypes.data_as(POINTER(c_int)), ctypes.byref(nr)), "pc_stencil")
     return rows[:nr.value]
+
+
+def pc_fp32_bands(bins: "Bins", cell, lo, hi, L=None, periodic: bool = False,
+                  rmin: float = 0.0) -> dict:
+    """The FP32 path's error bands and bin decisions for a count (host-only)."""
+    def v3(a):
+        return (c_double * 3)(*np.broadcast_to(np.asarray(a, dtype=np.float64), (3,)))
+    out = (c_double * 8)()
+    _check(lib().pc_fp32_bands(ctypes.byref(bins.s), v3(cell), v3(lo), v3(hi),
+                               v3(L) if L is not None else None, int(bool(periodic)),
+                               float(rmin), out), "pc_fp32_bands")
+    keys = ("eps_a", "eps_b", "mu_A", "mu_B", "rcut", "fp32_ok", "lin", "r2cut")
+    return dict(zip(keys, (float(v) for v in out)))
 
 
 def pc_suggest_cell_size(n: int, volume: float, r_max: float, mode: int = 0) -> float:

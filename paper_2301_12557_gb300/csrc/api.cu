@@ -1427,6 +1427,43 @@ extern "C" pc_status pc_stencil(const double cell[3], double r_max, int half, in
     return PC_OK;
 }
 
+// Host-only view of the FP32 path's error bands and bin decisions for a
+// count (no device work): make_plan on a geometry built from the arguments.
+extern "C" pc_status pc_fp32_bands(const pc_bins *b, const double cell[3], const double lo[3],
+                                   const double hi[3], const double L[3], int periodic,
+                                   double rmin, double out[8]) {
+    if (!b || !cell || !lo || !hi || !out || (periodic && !L))
+        return fail(PC_EINVAL, "pc_fp32_bands: bad arguments");
+    Geom g;
+    memset(&g, 0, sizeof(g));
+    g.periodic = periodic ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+        if (!(cell[a] > 0.0) || !std::isfinite(cell[a]) || !std::isfinite(lo[a]) ||
+            !std::isfinite(hi[a]) || hi[a] < lo[a])
+            return fail(PC_EINVAL, "pc_fp32_bands: bad cell sides or bounds");
+        if (periodic && (!(L[a] > 0.0) || !std::isfinite(L[a])))
+            return fail(PC_EINVAL, "pc_fp32_bands: periodic box needs L > 0");
+        g.c[a] = cell[a];
+        g.c32[a] = (float)cell[a];
+        g.ng[a] = 1;
+        g.lo[a] = lo[a];
+        g.L[a] = periodic ? L[a] : 0.0;
+        g.hL[a] = 0.5 * g.L[a];
+    }
+    Plan P;
+    pc_status s = make_plan(b, g, lo, hi, rmin, false, P, false);
+    if (s != PC_OK) return s;
+    out[0] = P.eps_a;
+    out[1] = P.eps_b;
+    out[2] = P.mu_A;
+    out[3] = P.mu_B;
+    out[4] = P.rcut;
+    out[5] = P.fp32_ok;
+    out[6] = P.lin;
+    out[7] = P.r2cut;
+    return PC_OK;
+}
+
 // Cost model of Appendix B.1 (cost = a N_pair + b N_node), specialised to the
 // GPU kernel: candidate pairs are charged per thread lane (a block occupies
 // NT * 2 lanes however many points its cell holds), and every (block,

@@ -1,0 +1,289 @@
+"""The FP32 path's error bands hold for the pair kernel's binary32 arithmetic
+(CPU, no GPU needed).
+
+The pair kernel forms each separation (Sect. 2.5) in binary32 from
+cell-relative offsets: the j-point is staged as fma(cell offset, cell side,
+offset from its cell centre), the separation component is one subtraction,
+s^2 two fused multiply-adds, s = s^2 rsqrt(s^2) with the hardware reciprocal
+square root (documented relative error 2^-22.9), mu = |dz| rsqrt(s^2), and
+along z sigma = q rsqrt(q), pi = |dz|.  A pair takes the fast path's bin only
+when each value lies at least its band (pc_fp32_bands) away from every edge.
+That decision equals the oracle's binary64 decision whenever
+|v_fp32 - v_binary64| + |edge_fp32 - edge| < band.
+
+This test emulates those operations exactly in binary32 (numpy float32 for
++, - and *, a fused multiply-add rounded once through an exact two-sum), takes
+the reciprocal square root at both ends of its error range, and checks that
+inequality for the library's bands over random and extreme pairs: every
+distance up to the largest separation, cells large and small, coordinates far
+from the origin, periodic images.  It also checks that every pair the oracle
+finds within the largest separation passes the kernel's FP32 candidate cut.
+"""
+
+import numpy as np
+import pytest
+
+P = pytest.importorskip("paper_2301_12557_gb300")
+
+F32, F64 = np.float32, np.float64
+U = 2.0 ** -24
+RSQRT_REL = 2.0 ** -22.9
+
+
+@pytest.fixture(scope="module")
+def lib():
+    P.build()
+    return P.lib()
+
+
+def _round_f32(hi, lo):
+    """Correct rounding to binary32 of hi + lo, where hi is the binary64
+    rounding of the exact value and lo the exact remainder."""
+    r = hi.astype(F32)
+    up = np.nextafter(r, F32(np.inf))
+    dn = np.nextafter(r, F32(-np.inf))
+    mid_up = (r.astype(F64) + up.astype(F64)) * 0.5
+    mid_dn = (r.astype(F64) + dn.astype(F64)) * 0.5
+    out = np.where((hi == mid_up) & (lo > 0), up, r)
+    return np.where((hi == mid_dn) & (lo < 0), dn, out)
+
+
+def fma32(a, b, c):
+    """fl32(a b + c) for binary32 a, b, c: the product is exact in binary64,
+    the sum's binary64 rounding error is recovered by two-sum."""
+    p = a.astype(F64) * b.astype(F64)
+    c64 = c.astype(F64)
+    hi = p + c64
+    bb = hi - p
+    lo = (p - (hi - bb)) + (c64 - bb)
+    return _round_f32(hi, lo)
+
+
+def _rsqrt_ends(x):
+    """The binary32 values at the two ends of the hardware rsqrt's error range."""
+    t = 1.0 / np.sqrt(x.astype(F64))
+    hi = (t * (1.0 + RSQRT_REL)).astype(F32)
+    hi = np.where(hi.astype(F64) > t * (1.0 + RSQRT_REL), np.nextafter(hi, F32(0)), hi)
+    lo = (t * (1.0 - RSQRT_REL)).astype(F32)
+    lo = np.where(lo.astype(F64) < t * (1.0 - RSQRT_REL), np.nextafter(lo, F32(np.inf)), lo)
+    return lo, hi
+
+
+def _pairs(rng, n, L, ng, lo, R, periodic):
+    """Cell-sorted pairs as the kernel sees them: cell ids, binary64 positions,
+    the j-cell offset including its periodic image."""
+    c = L / ng
+    idi = rng.integers(0, ng, size=(n, 3))
+    xi = lo + (idi + rng.random((n, 3))) * c
+    # separations: a third near R, a third uniform in volume, a third small
+    s = np.concatenate([R * (1.0 - rng.random(n // 3) * 1e-3),
+                        R * rng.random(n // 3) ** (1.0 / 3.0),
+                        R * rng.random(n - 2 * (n // 3)) * 0.05 + 1e-3 * c])
+    v = rng.normal(size=(n, 3))
+    # some pairs along an axis or a diagonal: extreme components
+    k = n // 10
+    v[:k] = np.eye(3)[rng.integers(0, 3, k)] * rng.choice([-1.0, 1.0], size=(k, 1))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    xj = xi + v * s[:, None]
+    if periodic:
+        shift = np.floor((xj - lo) / L)
+        xj = xj - shift * L
+        xj = np.where(xj >= lo + L, xj - L, xj)
+    else:
+        ext = lo + ng * c
+        keep = np.all((xj >= lo) & (xj < ext), axis=1)
+        xi, xj, idi = xi[keep], xj[keep], idi[keep]
+        shift = np.zeros_like(xj)
+    idj = np.minimum(np.floor((xj - lo) / c).astype(np.int64), ng - 1)
+    # the image that the stencil presents: offset of j's cell from i's cell
+    dxc = idj - idi + (np.round((xi + 0.0 - xj) / L) * ng).astype(np.int64) if periodic \
+        else idj - idi
+    return c, xi, xj, idi, idj, dxc
+
+
+def _kernel_values(c, lo, xi, xj, idi, idj, dxc):
+    """The kernel's binary32 separation quantities for each pair, with the
+    reciprocal square roots at both ends of their error range."""
+    c32 = F32(c)
+    oi = lo + (idi + 0.5) * c
+    oj = lo + (idj + 0.5) * c
+    reli = (xi - oi).astype(F32)
+    relj = (xj - oj).astype(F32)
+    staged = fma32(dxc.astype(F32), np.full(dxc.shape, c32), relj)
+    d = staged - reli                                   # binary32 subtraction
+    dx, dy, dz = d[:, 0], d[:, 1], d[:, 2]
+    q = fma32(dy, dy, dx * dx)
+    s2 = fma32(dz, dz, q)
+    out = []
+    for rs in _rsqrt_ends(s2):
+        for rq in _rsqrt_ends(q):
+            out.append(dict(s2=s2, s=s2 * rs, mu=np.abs(dz) * rs, rs=rs,
+                            sig=q * rq, pi=np.abs(dz)))
+    return out
+
+
+def _oracle_values(xi, xj, L, periodic):
+    """The oracle's binary64 quantities (its own operation order)."""
+    d = xj - xi
+    if periodic:
+        d = np.where(d > 0.5 * L, d - L, np.where(d < -0.5 * L, d + L, d))
+    s2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    p2 = d[:, 2] * d[:, 2]
+    return dict(s=np.sqrt(s2), mu=np.sqrt(p2 / s2), sig=np.sqrt(np.maximum(s2 - p2, 0.0)),
+                pi=np.abs(d[:, 2]))
+
+
+GEOMETRIES = [
+    # (L, cells per axis, lower corner, largest separation, periodic)
+    (1000.0, 11, 0.0, 200.0, True),        # the benchmark's tuned cell (~91)
+    (3000.0, 59, 0.0, 200.0, True),        # the 100M-point cube's box
+    (3000.0, 7, 0.0, 1000.0, True),        # cells of 429, largest separation 1000
+    (100.0, 150, 0.0, 49.5, True),         # tiny cells, separation near L/2
+    (12000.0, 240, 1.0e5, 200.0, False),   # coordinates around 1e5
+]
+
+
+@pytest.mark.parametrize("L,ng,lo,R,periodic", GEOMETRIES)
+def test_bands_cover_the_fp32_error(lib, L, ng, lo, R, periodic):
+    rng = np.random.default_rng(int(L + ng))
+    c, xi, xj, idi, idj, dxc = _pairs(rng, 300_000, L, ng, lo, R, periodic)
+    o = _oracle_values(xi, xj, L, periodic)
+    inside = (o["s"] < R) & (o["s"] > 1e-3 * c)
+    assert inside.sum() > 100_000
+    lo3, hi3 = np.full(3, lo), np.full(3, lo + ng * c)
+    Lb = np.full(3, L) if periodic else None
+    smu = P.pc_fp32_bands(P.Bins("smu", "z", np.linspace(0.0, R, 41), np.linspace(0, 1, 101)),
+                          c, lo3, hi3, Lb, periodic)
+    e = R / np.sqrt(2.0) * (1.0 - 1e-12)
+    sp = P.pc_fp32_bands(P.Bins("sigpi", "z", np.linspace(0.0, e, 21), np.linspace(0.0, e, 21)),
+                         c, lo3, hi3, Lb, periodic)
+    assert smu["fp32_ok"] == 1.0 and sp["fp32_ok"] == 1.0
+    edge_err = 1.01 * U * R                 # binary32 rounding of an edge up to R
+    worst = {"s": 0.0, "mu": 0.0, "sig": 0.0, "pi": 0.0}
+    with np.errstate(divide="ignore", invalid="ignore"):
+        values = _kernel_values(c, lo, xi, xj, idi, idj, dxc)
+    for kv in values:
+        # every pair the oracle finds within R passes the FP32 candidate cut
+        assert np.all(kv["s2"][o["s"] < R] < F32(smu["r2cut"]))
+        m = inside
+        err_s = np.abs(kv["s"][m].astype(F64) - o["s"][m])
+        worst["s"] = max(worst["s"], float((err_s / (smu["eps_a"] - edge_err)).max()))
+        # the mu band is evaluated in binary32 by the kernel: fma(mu_A, rs, mu_B)
+        rs = kv["rs"][m]
+        epsm = fma32(np.full(rs.shape, F32(smu["mu_A"])), rs,
+                     np.full(rs.shape, F32(smu["mu_B"]))).astype(F64)
+        err_mu = np.abs(kv["mu"][m].astype(F64) - o["mu"][m])
+        worst["mu"] = max(worst["mu"], float((err_mu / (epsm - 1.01 * U - 1e-15)).max()))
+        mq = m & (o["sig"] > 1e-3 * c)
+        err_sig = np.abs(kv["sig"][mq].astype(F64) - o["sig"][mq])
+        worst["sig"] = max(worst["sig"], float((err_sig / (sp["eps_a"] - edge_err)).max()))
+        err_pi = np.abs(kv["pi"][m].astype(F64) - o["pi"][m])
+        worst["pi"] = max(worst["pi"], float((err_pi / (sp["eps_b"] - edge_err)).max()))
+    # each ratio below 1: the band covers the error; the bands carry a factor
+    # of two over the derived bound, so the ratios sit near or below 1/2
+    assert all(v < 1.0 for v in worst.values()), worst
+    assert max(worst.values()) > 0.05, worst      # the emulation does see the rounding
+
+
+def test_emulated_fma_rounds_once():
+    """The emulated fused multiply-add against exact rational arithmetic."""
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    a = (rng.normal(size=4000) * 1e3).astype(F32)
+    b = (rng.normal(size=4000) * 1e-2).astype(F32)
+    c = (-(a.astype(F64) * b.astype(F64)) * (1 + rng.normal(size=4000) * 1e-7)).astype(F32)
+    got = fma32(a, b, c)
+    for k in range(a.size):
+        exact = Fraction(float(a[k])) * Fraction(float(b[k])) + Fraction(float(c[k]))
+        r = got[k]
+        nb = [np.nextafter(r, F32(-np.inf)), np.nextafter(r, F32(np.inf))]
+        dr = abs(Fraction(float(r)) - exact)
+        for x in nb:
+            dx = abs(Fraction(float(x)) - exact)
+            assert dr < dx or (dr == dx and (int(r.view(np.uint32)) & 1) == 0), k
+
+
+def _shell_pairs(rng, n, r_lo, r_hi, c, R):
+    """Pairs of points in a shell r_lo <= |x| < r_hi around the observer (both
+    points), on a non-periodic grid of cell side c over their bounding box."""
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    xi = u * rng.uniform(r_lo, r_hi, n)[:, None]
+    s = np.concatenate([R * (1.0 - rng.random(n // 2) * 1e-3), R * rng.random(n - n // 2)])
+    v = rng.normal(size=(n, 3))
+    k = n // 5
+    v[:k] = u[:k]                              # pairs along the line of sight
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    xj = xi + v * s[:, None]
+    rj = np.linalg.norm(xj, axis=1)
+    keep = (rj >= r_lo) & (rj < r_hi)
+    xi, xj = xi[keep], xj[keep]
+    lo = np.minimum(xi.min(0), xj.min(0))
+    hi = np.maximum(xi.max(0), xj.max(0))
+    ng = np.ceil((hi - lo) / c).astype(np.int64)
+    idi = np.minimum(np.floor((xi - lo) / c).astype(np.int64), ng - 1)
+    idj = np.minimum(np.floor((xj - lo) / c).astype(np.int64), ng - 1)
+    return xi, xj, idi, idj, lo, hi
+
+
+@pytest.mark.parametrize("r_lo,r_hi,c,R", [(1000.0, 2000.0, 81.0, 200.0 * np.sqrt(2.0)),
+                                          (650.0, 1500.0, 50.0, 200.0)])
+def test_midpoint_bands_cover_the_fp32_error(lib, r_lo, r_hi, c, R):
+    """The midpoint line of sight (l = 2 x_i + d in binary32 from the i-point's
+    rounded absolute position): pi = |d.l| / |l|, sigma = |d x l| / |l| and
+    mu = pi / s against the library's bands for a catalogue whose nearest
+    point lies r_lo from the observer."""
+    rng = np.random.default_rng(int(r_lo))
+    xi, xj, idi, idj, lo, hi = _shell_pairs(rng, 300_000, r_lo, r_hi, c, R)
+    e = R / np.sqrt(2.0) * (1.0 - 1e-12)
+    sp = P.pc_fp32_bands(P.Bins("sigpi", "mid", np.linspace(0.0, e, 21),
+                                np.linspace(0.0, e, 21)), c, lo, hi, None, False, r_lo)
+    smu = P.pc_fp32_bands(P.Bins("smu", "mid", np.linspace(0.0, R, 41), np.linspace(0, 1, 101)),
+                          c, lo, hi, None, False, r_lo)
+    assert sp["fp32_ok"] == 1.0 and smu["fp32_ok"] == 1.0
+    # binary32 quantities
+    oi, oj = lo + (idi + 0.5) * c, lo + (idj + 0.5) * c
+    reli, relj = (xi - oi).astype(F32), (xj - oj).astype(F32)
+    d = fma32((idj - idi).astype(F32), np.full(idi.shape, F32(c)), relj) - reli
+    dx, dy, dz = d[:, 0], d[:, 1], d[:, 2]
+    xa = xi.astype(F32)
+    two = np.full(dx.shape, F32(2.0))
+    lx, ly, lz = fma32(two, xa[:, 0], dx), fma32(two, xa[:, 1], dy), fma32(two, xa[:, 2], dz)
+    sl = fma32(dz, lz, fma32(dy, ly, dx * lx))
+    ll = fma32(lz, lz, fma32(ly, ly, lx * lx))
+    cx = fma32(dy, lz, -dz * ly)
+    cy = fma32(dz, lx, -dx * lz)
+    cz = fma32(dx, ly, -dy * lx)
+    cc = fma32(cz, cz, fma32(cy, cy, cx * cx))
+    s2 = fma32(dz, dz, fma32(dy, dy, dx * dx))
+    # binary64 oracle quantities
+    d64 = xj - xi
+    l64 = xi + xj
+    s2o = (d64[:, 0] * d64[:, 0] + d64[:, 1] * d64[:, 1]) + d64[:, 2] * d64[:, 2]
+    slo = (d64[:, 0] * l64[:, 0] + d64[:, 1] * l64[:, 1]) + d64[:, 2] * l64[:, 2]
+    llo = (l64[:, 0] * l64[:, 0] + l64[:, 1] * l64[:, 1]) + l64[:, 2] * l64[:, 2]
+    pi2o = (slo * slo) / llo
+    pio, sigo = np.sqrt(pi2o), np.sqrt(np.maximum(s2o - pi2o, 0.0))
+    muo = np.sqrt(pi2o / s2o)
+    m = (np.sqrt(s2o) < R) & (np.sqrt(s2o) > 1e-3 * c)
+    assert m.sum() > 100_000
+    edge_err = 1.01 * U * R
+    worst = {"sig": 0.0, "pi": 0.0, "mu": 0.0}
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ends = [(_rsqrt_ends(ll)[a], _rsqrt_ends(cc)[b], _rsqrt_ends(s2)[k])
+                for a in (0, 1) for b in (0, 1) for k in (0, 1)]
+        for rl, rc, rs in ends:
+            pz = np.abs(sl) * rl
+            sg = (cc * rc) * rl
+            mu = pz * rs
+            mq = m & (sigo > 1e-3 * c)
+            worst["sig"] = max(worst["sig"], float(
+                (np.abs(sg[mq].astype(F64) - sigo[mq]) / (sp["eps_a"] - edge_err)).max()))
+            worst["pi"] = max(worst["pi"], float(
+                (np.abs(pz[m].astype(F64) - pio[m]) / (sp["eps_b"] - edge_err)).max()))
+            epsm = fma32(np.full(rs.shape, F32(smu["mu_A"])), rs,
+                         np.full(rs.shape, F32(smu["mu_B"]))).astype(F64)
+            worst["mu"] = max(worst["mu"], float(
+                (np.abs(mu[m].astype(F64) - muo[m]) / (epsm[m] - 1.01 * U - 1e-15)).max()))
+    assert all(v < 1.0 for v in worst.values()), worst
+    assert max(worst.values()) > 0.05, worst
