@@ -383,7 +383,7 @@ pc_status pc_stencil(const double cell[3], double r_max, int half, int max_rows,
  * the tree path the largest list-node extent), points within [lo, hi] per
  * axis, a periodic box of sides L[3] (L may be NULL when periodic == 0) and
  * rmin, a lower bound of the points' distance from the observer (midpoint
- * line of sight; 0 if unknown), out[0..7] receives:
+ * line of sight; 0 if unknown), out[0..15] receives:
  *   0 eps_a   band of s (s and (s, mu) bins) or of sigma ((sigma, pi) bins)
  *   1 eps_b   band of pi ((sigma, pi) bins)
  *   2 mu_A    the mu band is mu_A / s + mu_B ((s, mu) bins)
@@ -393,12 +393,19 @@ pc_status pc_stencil(const double cell[3], double r_max, int half, int max_rows,
  *   5 fp32_ok 1 when the FP32 path's bound holds (else counts run in FP64)
  *   6 lin     1 when the bins are found by a floor instead of tables
  *   7 r2cut   the FP32 cut the kernel compares s^2 against
+ *   8..15     floor-based bins (when lin): t = s * invA + offA and bin =
+ *             floor(t), not near an edge iff |frac(t) - 1/2| < thrA (offA
+ *             carries +1 when the s range is tested, the bin then floor(t) -
+ *             1); mu bins t_mu = mu * nB, not near iff |frac(t_mu) - 1/2| <
+ *             cB - mA / s; then norange (1: e_0 = 0 and no range test) and
+ *             log (1: logarithmic s edges, t from log2(s^2)):
+ *             invA, offA, thrA, nB, mA, cB, norange, log
  * A pair takes the fast path's bin only when its FP32 value lies at least
  * the band away from every edge; closer pairs are decided in binary64.
  * Errors: PC_EINVAL (NULL pointers, bad cell sides, bounds, box or bins). */
 pc_status pc_fp32_bands(const pc_bins *b, const double cell[3], const double lo[3],
                         const double hi[3], const double L[3], int periodic, double rmin,
-                        double out[8]);
+                        double out[16]);
 
 /* Cell side the cost model picks for n points in volume `volume` with
  * largest separation r_max (Appendix B.1: cost a N_pair + b N_node). */

@@ -1431,7 +1431,7 @@ extern "C" pc_status pc_stencil(const double cell[3], double r_max, int half, in
 // count (no device work): make_plan on a geometry built from the arguments.
 extern "C" pc_status pc_fp32_bands(const pc_bins *b, const double cell[3], const double lo[3],
                                    const double hi[3], const double L[3], int periodic,
-                                   double rmin, double out[8]) {
+                                   double rmin, double out[16]) {
     if (!b || !cell || !lo || !hi || !out || (periodic && !L))
         return fail(PC_EINVAL, "pc_fp32_bands: bad arguments");
     Geom g;
@@ -1461,6 +1461,15 @@ extern "C" pc_status pc_fp32_bands(const pc_bins *b, const double cell[3], const
     out[5] = P.fp32_ok;
     out[6] = P.lin;
     out[7] = P.r2cut;
+    // floor-based bins, as the kernel receives them
+    out[8] = P.lin_invA;
+    out[9] = P.lin_norange ? P.lin_offA : P.lin_offA1;
+    out[10] = P.lin_thrA;
+    out[11] = P.lin_nB;
+    out[12] = P.lin_mA;
+    out[13] = P.lin_cB;
+    out[14] = P.lin_norange;
+    out[15] = P.lin_log;
     return PC_OK;
 }
 

@@ -287,3 +287,103 @@ def test_midpoint_bands_cover_the_fp32_error(lib, r_lo, r_hi, c, R):
                 (np.abs(mu[m].astype(F64) - muo[m]) / (epsm[m] - 1.01 * U - 1e-15)).max()))
     assert all(v < 1.0 for v in worst.values()), worst
     assert max(worst.values()) > 0.05, worst
+
+
+def _rd32(x):
+    """Binary32 rounding toward -inf of binary64 values x."""
+    r = x.astype(F32)
+    return np.where(r.astype(F64) > x, np.nextafter(r, F32(-np.inf)), r)
+
+
+def _bits(x):
+    return x.astype(F32).view(np.uint32).astype(np.int64)
+
+
+@pytest.mark.parametrize("L,ng,e0", [(1000.0, 11, 0.0), (3000.0, 59, 0.0), (1000.0, 11, 5.0)])
+def test_floor_bins_decide_as_the_oracle(lib, L, ng, e0):
+    """The benchmark's path: evenly spaced s bins and 100 mu bins along z,
+    binned by floors on the 2^23 grid (t = s invA + offA, t_mu = |dz| rs nB)
+    with the kernel's band tests.  Every pair the emulated kernel bins
+    without the rescue lands in the oracle's bin; every pair it drops as out
+    of range is out of the oracle's range."""
+    rng = np.random.default_rng(int(L + ng + e0))
+    R = 200.0
+    ea = np.linspace(e0, R, 41 if e0 == 0.0 else 40)
+    mu_e = np.linspace(0.0, 1.0, 101)
+    c, xi, xj, idi, idj, dxc = _pairs(rng, 300_000, L, ng, 0.0, R, True)
+    # pairs planted at s and mu edges times (1 + delta)
+    n2 = 100_000
+    xp = rng.uniform(0.0, L, (n2, 3))
+    sp_ = ea[rng.integers(0, ea.size, n2)] * (1.0 + rng.choice([0.0, 1e-7, -1e-7, 1e-5, -1e-5, 3e-4,
+                                                                -3e-4], n2))
+    sp_ = np.maximum(sp_, 1e-3)
+    mp = np.clip(mu_e[rng.integers(0, mu_e.size, n2)] * (1.0 + rng.choice([0.0, 1e-6, -1e-6, 1e-4,
+                                                                           -1e-4], n2)), 0, 1)
+    phi = rng.uniform(0, 2 * np.pi, n2)
+    t = sp_ * np.sqrt(1 - mp * mp)
+    xq = xp + np.stack([t * np.cos(phi), t * np.sin(phi), sp_ * mp], axis=1)
+    xq = np.mod(xq, L)
+    xq = np.where(xq >= L, 0.0, xq)
+    idp = np.minimum(np.floor(xp / c).astype(np.int64), ng - 1)
+    idq = np.minimum(np.floor(xq / c).astype(np.int64), ng - 1)
+    dq = idq - idp + (np.round((xp - xq) / L) * ng).astype(np.int64)
+    xi, xj = np.vstack([xi, xp]), np.vstack([xj, xq])
+    idi, idj, dxc = np.vstack([idi, idp]), np.vstack([idj, idq]), np.vstack([dxc, dq])
+
+    bp = P.pc_fp32_bands(P.Bins("smu", "z", ea, mu_e), c, np.zeros(3), np.full(3, L),
+                         np.full(3, L), True)
+    assert bp["lin"] == 1.0 and bp["lin_log"] == 0.0
+    assert bp["lin_norange"] == (1.0 if e0 == 0.0 else 0.0)
+    chk = bp["lin_norange"] == 0.0
+    na, nb = ea.size - 1, mu_e.size - 1
+    # oracle bins (binary64, squared comparisons)
+    d = xj - xi
+    d = np.where(d > 0.5 * L, d - L, np.where(d < -0.5 * L, d + L, d))
+    s2o = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    p2o = d[:, 2] * d[:, 2]
+    E = ea * ea
+    ko = np.searchsorted(E, s2o, side="right") - 1
+    in_o = (s2o >= E[0]) & (s2o < E[-1])
+    M = mu_e * mu_e
+    jo = np.zeros(s2o.size, dtype=np.int64)
+    for j in range(1, nb):
+        jo = np.where(p2o >= M[j] * s2o, j, jo)
+    # the kernel, emulated
+    c32 = F32(c)
+    reli = (xi - (idi + 0.5) * c).astype(F32)
+    relj = (xj - (idj + 0.5) * c).astype(F32)
+    dd = fma32(dxc.astype(F32), np.full(dxc.shape, c32), relj) - reli
+    dx, dy, dz = dd[:, 0], dd[:, 1], dd[:, 2]
+    s2 = fma32(dz, dz, fma32(dy, dy, dx * dx))
+    cand = s2 < F32(bp["r2cut"])
+    assert np.all(cand[in_o])
+    C23, NC23H = F32(2.0 ** 23), F32(-(2.0 ** 23) + 0.5)
+    invA, offA, thrA = F32(bp["lin_invA"]), F32(bp["lin_offA"]), F32(bp["lin_thrA"])
+    nB, mA, cB = F32(bp["lin_nB"]), F32(bp["lin_mA"]), F32(bp["lin_cB"])
+    halfA = F32(0.5 * na)
+    hA1 = F32(halfA + F32(1.0)) if chk else halfA
+    n = s2.size
+    binned = 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for rs in _rsqrt_ends(s2):
+            ts = fma32(s2 * rs, np.full(n, invA), np.full(n, offA))
+            f = _rd32(ts.astype(F64) + F64(C23))
+            dfr = ts - (f + NC23H)
+            near = ~(np.abs(dfr) < thrA)
+            ok = (np.abs(ts + (-hA1)) < halfA) if chk else np.ones(n, bool)
+            k = _bits(f) - 0x4B000000 - (1 if chk else 0)
+            tm = np.abs(dz) * (rs * nB)
+            fm = _rd32(tm.astype(F64) + F64(C23))
+            dm = tm - (fm + NC23H)
+            thm = fma32(np.full(n, -mA), rs, np.full(n, cB))
+            near |= ~(np.abs(dm) < thm)
+            j = _bits(fm) - 0x4B000000
+            fast = cand & ~near
+            counted = fast & ok & (k >= 0) & (k < na)
+            assert np.all(in_o[counted]), "counted a pair the oracle has out of range"
+            assert np.array_equal(k[counted], ko[counted]), "s bin differs"
+            assert np.array_equal(j[counted], jo[counted]), "mu bin differs"
+            dropped = fast & ~(ok & (k >= 0) & (k < na))
+            assert not np.any(in_o[dropped]), "dropped a pair the oracle has in range"
+            binned = max(binned, int(counted.sum()))
+    assert binned > 0.6 * in_o.sum()          # most pairs take the fast path
