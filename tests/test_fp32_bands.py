@@ -387,3 +387,119 @@ def test_floor_bins_decide_as_the_oracle(lib, L, ng, e0):
             assert not np.any(in_o[dropped]), "dropped a pair the oracle has in range"
             binned = max(binned, int(counted.sum()))
     assert binned > 0.6 * in_o.sum()          # most pairs take the fast path
+
+
+def _sigpi_oracle(xi, xj, L, periodic, los, ea, eb):
+    """The oracle's (sigma, pi) bins: indices and in-range flags."""
+    d = xj - xi
+    if periodic:
+        d = np.where(d > 0.5 * L, d - L, np.where(d < -0.5 * L, d + L, d))
+    s2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    if los == "z":
+        p2 = d[:, 2] * d[:, 2]
+    else:
+        lv = xi + xj
+        sl = (d[:, 0] * lv[:, 0] + d[:, 1] * lv[:, 1]) + d[:, 2] * lv[:, 2]
+        ll = (lv[:, 0] * lv[:, 0] + lv[:, 1] * lv[:, 1]) + lv[:, 2] * lv[:, 2]
+        p2 = (sl * sl) / ll
+    q2 = np.maximum(s2 - p2, 0.0)
+    Ea, Eb = ea * ea, eb * eb
+    ka = np.searchsorted(Ea, q2, side="right") - 1
+    kb = np.searchsorted(Eb, p2, side="right") - 1
+    inside = (q2 >= Ea[0]) & (q2 < Ea[-1]) & (p2 >= Eb[0]) & (p2 < Eb[-1])
+    return ka, kb, inside
+
+
+def _sigpi_fp32(dx, dy, dz, xa, los):
+    """The kernel's binary32 sigma and pi (both rsqrt ends of every root)."""
+    if los == "z":
+        q = fma32(dy, dy, dx * dx)
+        pz = np.abs(dz)
+        return [(q * rq, pz) for rq in _rsqrt_ends(q)]
+    two = np.full(dx.shape, F32(2.0))
+    lx, ly, lz = fma32(two, xa[:, 0], dx), fma32(two, xa[:, 1], dy), fma32(two, xa[:, 2], dz)
+    sl = fma32(dz, lz, fma32(dy, ly, dx * lx))
+    ll = fma32(lz, lz, fma32(ly, ly, lx * lx))
+    cx = fma32(dy, lz, -dz * ly)
+    cy = fma32(dz, lx, -dx * lz)
+    cz = fma32(dx, ly, -dy * lx)
+    cc = fma32(cz, cz, fma32(cy, cy, cx * cx))
+    return [((cc * rc) * rl, np.abs(sl) * rl) for rl in _rsqrt_ends(ll) for rc in _rsqrt_ends(cc)]
+
+
+@pytest.mark.parametrize("los", ["z", "mid"])
+def test_sigma_pi_floor_bins_decide_as_the_oracle(lib, los):
+    """(sigma, pi) bins evenly spaced from 0 (the survey workload's 40 x 40 on
+    [0, 200)^2), binned by floors of sigma invA and pi invB with the kernel's
+    band tests: every pair binned without the rescue lands in the oracle's
+    bin, every pair dropped as out of range is out of the oracle's range."""
+    rng = np.random.default_rng(7 if los == "z" else 8)
+    ea = np.linspace(0.0, 200.0, 41)
+    eb = np.linspace(0.0, 200.0, 41)
+    R = float(np.hypot(200.0, 200.0))
+    if los == "z":
+        L, ng = 3000.0, 30
+        c, xi, xj, idi, idj, dxc = _pairs(rng, 300_000, L, ng, 0.0, R, True)
+        lo3, hi3, Lb, periodic, rmin = np.zeros(3), np.full(3, L), np.full(3, L), True, 0.0
+        loc = np.zeros(3)
+    else:
+        c = 81.0
+        xi, xj, idi, idj, loc, hic = _shell_pairs(rng, 300_000, 1000.0, 2000.0, c, R)
+        dxc = idj - idi
+        lo3, hi3, Lb, periodic, rmin, L = loc, hic, None, False, 1000.0, 0.0
+    # planted: sigma and pi at edges times (1 + delta), along z / along the
+    # i-point's line of sight
+    n2 = 100_000
+    pick = rng.integers(0, xi.shape[0], n2)
+    sg_t = ea[rng.integers(0, ea.size, n2)] * (1.0 + rng.choice([0.0, 1e-7, -1e-7, 1e-5, -1e-5], n2))
+    pi_t = eb[rng.integers(0, eb.size, n2)] * (1.0 + rng.choice([0.0, 1e-7, -1e-7, 1e-5, -1e-5], n2))
+    los_u = np.tile([0.0, 0.0, 1.0], (n2, 1)) if los == "z" else \
+        xi[pick] / np.linalg.norm(xi[pick], axis=1, keepdims=True)
+    perp = np.cross(los_u, rng.normal(size=(n2, 3)))
+    perp /= np.linalg.norm(perp, axis=1, keepdims=True)
+    xq = xi[pick] + sg_t[:, None] * perp + pi_t[:, None] * los_u
+    xp = xi[pick]
+    if periodic:
+        xq = np.mod(xq, L)
+        xq = np.where(xq >= L, 0.0, xq)
+        idq = np.minimum(np.floor(xq / c).astype(np.int64), ng - 1)
+        dq = idq - idi[pick] + (np.round((xp - xq) / L) * ng).astype(np.int64)
+    else:
+        ngv = np.ceil((hic - loc) / c).astype(np.int64)
+        keep = np.all((xq >= loc) & (xq <= hic), axis=1)
+        xp, xq, pick = xp[keep], xq[keep], pick[keep]
+        idq = np.minimum(np.floor((xq - loc) / c).astype(np.int64), ngv - 1)
+        dq = idq - idi[pick]
+    xi, xj = np.vstack([xi, xp]), np.vstack([xj, xq])
+    idi, idj, dxc = np.vstack([idi, idi[pick]]), np.vstack([idj, idq]), np.vstack([dxc, dq])
+
+    bp = P.pc_fp32_bands(P.Bins("sigpi", los, ea, eb), c, lo3, hi3, Lb, periodic, rmin)
+    assert bp["fp32_ok"] == 1.0 and bp["lin"] == 1.0
+    ko_a, ko_b, in_o = _sigpi_oracle(xi, xj, L, periodic, los, ea, eb)
+    reli = (xi - (loc + (idi + 0.5) * c)).astype(F32)
+    relj = (xj - (loc + (idj + 0.5) * c)).astype(F32)
+    dd = fma32(dxc.astype(F32), np.full(dxc.shape, F32(c)), relj) - reli
+    dx, dy, dz = dd[:, 0], dd[:, 1], dd[:, 2]
+    s2 = fma32(dz, dz, fma32(dy, dy, dx * dx))
+    cand = s2 < F32(bp["r2cut"])
+    assert np.all(cand[in_o])
+    C23, NC23H = F32(2.0 ** 23), F32(-(2.0 ** 23) + 0.5)
+    invA, thrA = F32(bp["lin_invA"]), F32(bp["lin_thrA"])
+    invB, thrB = F32(bp["lin_invB"]), F32(bp["lin_thrB"])
+    na, nb = ea.size - 1, eb.size - 1
+    binned = 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for sg, pz in _sigpi_fp32(dx, dy, dz, xi.astype(F32), los):
+            ta, tb = sg * invA, pz * invB
+            fa = _rd32(ta.astype(F64) + F64(C23))
+            fb = _rd32(tb.astype(F64) + F64(C23))
+            near = ~(np.abs(ta - (fa + NC23H)) < thrA) | ~(np.abs(tb - (fb + NC23H)) < thrB)
+            ka, kb = _bits(fa) - 0x4B000000, _bits(fb) - 0x4B000000
+            fast = cand & ~near
+            counted = fast & (ka < na) & (kb < nb)
+            assert np.all(in_o[counted]), "counted a pair the oracle has out of range"
+            assert np.array_equal(ka[counted], ko_a[counted]), "sigma bin differs"
+            assert np.array_equal(kb[counted], ko_b[counted]), "pi bin differs"
+            assert not np.any(in_o[fast & ~((ka < na) & (kb < nb))]), "dropped an in-range pair"
+            binned = max(binned, int(counted.sum()))
+    assert binned > 0.6 * in_o.sum()
