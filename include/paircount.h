@@ -383,7 +383,7 @@ pc_status pc_stencil(const double cell[3], double r_max, int half, int max_rows,
  * the tree path the largest list-node extent), points within [lo, hi] per
  * axis, a periodic box of sides L[3] (L may be NULL when periodic == 0) and
  * rmin, a lower bound of the points' distance from the observer (midpoint
- * line of sight; 0 if unknown), out[0..17] receives:
+ * line of sight; 0 if unknown), out[0..18] receives:
  *   0 eps_a   band of s (s and (s, mu) bins) or of sigma ((sigma, pi) bins)
  *   1 eps_b   band of pi ((sigma, pi) bins)
  *   2 mu_A    the mu band is mu_A / s + mu_B ((s, mu) bins)
@@ -399,16 +399,19 @@ pc_status pc_stencil(const double cell[3], double r_max, int half, int max_rows,
  *             1); mu bins t_mu = mu * nB, not near iff |frac(t_mu) - 1/2| <
  *             cB - mA / s; then norange (1: e_0 = 0 and no range test) and
  *             log (1: logarithmic s edges, t from log2(s^2)):
- *             invA, offA, thrA, nB, mA, cB, norange, log
+ *             invA, offA, thrA, nB, mA, cB, norange, log (with log, t =
+ *             log2(s^2) * invA + offA and the band is thrA - mS / s, mS in
+ *             out[18])
  *   16..17    (sigma, pi) floor bins: t_pi = pi * invB, not near iff
  *             |frac(t_pi) - 1/2| < thrB (sigma as s, with offA = 0):
  *             invB, thrB
+ *   18 mS     logarithmic s bins: the band's term in 1/s
  * A pair takes the fast path's bin only when its FP32 value lies at least
  * the band away from every edge; closer pairs are decided in binary64.
  * Errors: PC_EINVAL (NULL pointers, bad cell sides, bounds, box or bins). */
 pc_status pc_fp32_bands(const pc_bins *b, const double cell[3], const double lo[3],
                         const double hi[3], const double L[3], int periodic, double rmin,
-                        double out[18]);
+                        double out[19]);
 
 /* Cell side the cost model picks for n points in volume `volume` with
  * largest separation r_max (Appendix B.1: cost a N_pair + b N_node). */

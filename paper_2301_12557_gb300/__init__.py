@@ -608,13 +608,13 @@ def pc_fp32_bands(bins: "Bins", cell, lo, hi, L=None, periodic: bool = False,
     """The FP32 path's error bands and bin decisions for a count (host-only)."""
     def v3(a):
         return (c_double * 3)(*np.broadcast_to(np.asarray(a, dtype=np.float64), (3,)))
-    out = (c_double * 18)()
+    out = (c_double * 19)()
     _check(lib().pc_fp32_bands(ctypes.byref(bins.s), v3(cell), v3(lo), v3(hi),
                                v3(L) if L is not None else None, int(bool(periodic)),
                                float(rmin), out), "pc_fp32_bands")
     keys = ("eps_a", "eps_b", "mu_A", "mu_B", "rcut", "fp32_ok", "lin", "r2cut",
             "lin_invA", "lin_offA", "lin_thrA", "lin_nB", "lin_mA", "lin_cB", "lin_norange",
-            "lin_log", "lin_invB", "lin_thrB")
+            "lin_log", "lin_invB", "lin_thrB", "lin_mS")
     return dict(zip(keys, (float(v) for v in out)))
 
 

@@ -1431,7 +1431,7 @@ extern "C" pc_status pc_stencil(const double cell[3], double r_max, int half, in
 // count (no device work): make_plan on a geometry built from the arguments.
 extern "C" pc_status pc_fp32_bands(const pc_bins *b, const double cell[3], const double lo[3],
                                    const double hi[3], const double L[3], int periodic,
-                                   double rmin, double out[18]) {
+                                   double rmin, double out[19]) {
     if (!b || !cell || !lo || !hi || !out || (periodic && !L))
         return fail(PC_EINVAL, "pc_fp32_bands: bad arguments");
     Geom g;
@@ -1472,6 +1472,7 @@ extern "C" pc_status pc_fp32_bands(const pc_bins *b, const double cell[3], const
     out[15] = P.lin_log;
     out[16] = P.lin_invB2;
     out[17] = P.lin_thrB;
+    out[18] = P.lin_mS;
     return PC_OK;
 }
 

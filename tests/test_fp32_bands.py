@@ -503,3 +503,93 @@ def test_sigma_pi_floor_bins_decide_as_the_oracle(lib, los):
             assert not np.any(in_o[fast & ~((ka < na) & (kb < nb))]), "dropped an in-range pair"
             binned = max(binned, int(counted.sum()))
     assert binned > 0.6 * in_o.sum()
+
+
+def _lg2_ends(x):
+    """The binary32 values at the two ends of the error the log-bin bands
+    budget for the hardware base-2 logarithm: 2^-21 max(1, |log2 x|)."""
+    v = np.log2(x.astype(F64))
+    e = 2.0 ** -21 * np.maximum(1.0, np.abs(v))
+    hi = (v + e).astype(F32)
+    hi = np.where(hi.astype(F64) > v + e, np.nextafter(hi, F32(-np.inf)), hi)
+    lo = (v - e).astype(F32)
+    lo = np.where(lo.astype(F64) < v - e, np.nextafter(lo, F32(np.inf)), lo)
+    return lo, hi
+
+
+def test_log_bins_decide_as_the_oracle(lib):
+    """Logarithmic s edges (40 on [0.1, 200)) with 100 mu bins along z: t =
+    log2(s^2) invA + offA from the hardware logarithm (taken at both ends of
+    its budgeted error), the band thrA - mS / s: every pair binned without the
+    rescue lands in the oracle's bin."""
+    rng = np.random.default_rng(11)
+    L, ng, R = 1000.0, 11, 200.0
+    ea = np.geomspace(0.1, R, 41)
+    mu_e = np.linspace(0.0, 1.0, 101)
+    c, xi, xj, idi, idj, dxc = _pairs(rng, 300_000, L, ng, 0.0, R, True)
+    n2 = 100_000
+    xp = rng.uniform(0.0, L, (n2, 3))
+    sp_ = ea[rng.integers(0, ea.size, n2)] * (1.0 + rng.choice([0.0, 1e-7, -1e-7, 1e-5, -1e-5], n2))
+    v = rng.normal(size=(n2, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    xq = np.mod(xp + v * sp_[:, None], L)
+    xq = np.where(xq >= L, 0.0, xq)
+    idp = np.minimum(np.floor(xp / c).astype(np.int64), ng - 1)
+    idq = np.minimum(np.floor(xq / c).astype(np.int64), ng - 1)
+    dq = idq - idp + (np.round((xp - xq) / L) * ng).astype(np.int64)
+    xi, xj = np.vstack([xi, xp]), np.vstack([xj, xq])
+    idi, idj, dxc = np.vstack([idi, idp]), np.vstack([idj, idq]), np.vstack([dxc, dq])
+
+    bp = P.pc_fp32_bands(P.Bins("smu", "z", ea, mu_e), c, np.zeros(3), np.full(3, L),
+                         np.full(3, L), True)
+    assert bp["lin"] == 1.0 and bp["lin_log"] == 1.0 and bp["lin_norange"] == 0.0
+    na, nb = ea.size - 1, mu_e.size - 1
+    d = xj - xi
+    d = np.where(d > 0.5 * L, d - L, np.where(d < -0.5 * L, d + L, d))
+    s2o = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    p2o = d[:, 2] * d[:, 2]
+    E = ea * ea
+    ko = np.searchsorted(E, s2o, side="right") - 1
+    in_o = (s2o >= E[0]) & (s2o < E[-1])
+    M = mu_e * mu_e
+    jo = np.zeros(s2o.size, dtype=np.int64)
+    for j in range(1, nb):
+        jo = np.where(p2o >= M[j] * s2o, j, jo)
+    reli = (xi - (idi + 0.5) * c).astype(F32)
+    relj = (xj - (idj + 0.5) * c).astype(F32)
+    dd = fma32(dxc.astype(F32), np.full(dxc.shape, F32(c)), relj) - reli
+    dx, dy, dz = dd[:, 0], dd[:, 1], dd[:, 2]
+    s2 = fma32(dz, dz, fma32(dy, dy, dx * dx))
+    cand = s2 < F32(bp["r2cut"])
+    assert np.all(cand[in_o])
+    C23, NC23H = F32(2.0 ** 23), F32(-(2.0 ** 23) + 0.5)
+    mS = F32(bp["lin_mS"])
+    assert mS > 0
+    invA, offA, thrA = F32(bp["lin_invA"]), F32(bp["lin_offA"]), F32(bp["lin_thrA"])
+    nB, mA, cB = F32(bp["lin_nB"]), F32(bp["lin_mA"]), F32(bp["lin_cB"])
+    halfA = F32(0.5 * na)
+    hA1 = F32(halfA + F32(1.0))
+    n = s2.size
+    binned = 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for rs in _rsqrt_ends(s2):
+            for lg in _lg2_ends(s2):
+                ts = fma32(lg, np.full(n, invA), np.full(n, offA))
+                f = _rd32(ts.astype(F64) + F64(C23))
+                ths = fma32(np.full(n, -mS), rs, np.full(n, thrA))   # thrA - mS / s
+                near = ~(np.abs(ts - (f + NC23H)) < ths)
+                ok = np.abs(ts + (-hA1)) < halfA
+                k = _bits(f) - 0x4B000000 - 1
+                tm = np.abs(dz) * (rs * nB)
+                fm = _rd32(tm.astype(F64) + F64(C23))
+                thm = fma32(np.full(n, -mA), rs, np.full(n, cB))
+                near |= ~(np.abs(tm - (fm + NC23H)) < thm)
+                j = _bits(fm) - 0x4B000000
+                fast = cand & ~near
+                counted = fast & ok & (k >= 0) & (k < na)
+                assert np.all(in_o[counted]), "counted a pair the oracle has out of range"
+                assert np.array_equal(k[counted], ko[counted]), "s bin differs"
+                assert np.array_equal(j[counted], jo[counted]), "mu bin differs"
+                assert not np.any(in_o[fast & ~(ok & (k >= 0) & (k < na))]), "dropped a pair"
+                binned = max(binned, int(counted.sum()))
+    assert binned > 0.6 * in_o.sum()
