@@ -299,6 +299,52 @@ def _bits(x):
     return x.astype(F32).view(np.uint32).astype(np.int64)
 
 
+def _check_smu_floor(dd, s2o, p2o, bp, ea, mu_e):
+    """Floor-bin decisions of the (s, mu) path along z for binary32
+    separation vectors dd against the oracle's binary64 s^2 and pi^2."""
+    na, nb = ea.size - 1, mu_e.size - 1
+    chk = bp["lin_norange"] == 0.0
+    E = ea * ea
+    ko = np.searchsorted(E, s2o, side="right") - 1
+    in_o = (s2o >= E[0]) & (s2o < E[-1])
+    M = mu_e * mu_e
+    jo = np.zeros(s2o.size, dtype=np.int64)
+    for j in range(1, nb):
+        jo = np.where(p2o >= M[j] * s2o, j, jo)
+    dx, dy, dz = dd[:, 0], dd[:, 1], dd[:, 2]
+    s2 = fma32(dz, dz, fma32(dy, dy, dx * dx))
+    cand = s2 < F32(bp["r2cut"])
+    assert np.all(cand[in_o])
+    C23, NC23H = F32(2.0 ** 23), F32(-(2.0 ** 23) + 0.5)
+    invA, offA, thrA = F32(bp["lin_invA"]), F32(bp["lin_offA"]), F32(bp["lin_thrA"])
+    nB, mA, cB = F32(bp["lin_nB"]), F32(bp["lin_mA"]), F32(bp["lin_cB"])
+    halfA = F32(0.5 * na)
+    hA1 = F32(halfA + F32(1.0)) if chk else halfA
+    n = s2.size
+    binned = 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for rs in _rsqrt_ends(s2):
+            ts = fma32(s2 * rs, np.full(n, invA), np.full(n, offA))
+            f = _rd32(ts.astype(F64) + F64(C23))
+            near = ~(np.abs(ts - (f + NC23H)) < thrA)
+            ok = (np.abs(ts + (-hA1)) < halfA) if chk else np.ones(n, bool)
+            k = _bits(f) - 0x4B000000 - (1 if chk else 0)
+            tm = np.abs(dz) * (rs * nB)
+            fm = _rd32(tm.astype(F64) + F64(C23))
+            thm = fma32(np.full(n, -mA), rs, np.full(n, cB))
+            near |= ~(np.abs(tm - (fm + NC23H)) < thm)
+            j = _bits(fm) - 0x4B000000
+            fast = cand & ~near
+            counted = fast & ok & (k >= 0) & (k < na)
+            assert np.all(in_o[counted]), "counted a pair the oracle has out of range"
+            assert np.array_equal(k[counted], ko[counted]), "s bin differs"
+            assert np.array_equal(j[counted], jo[counted]), "mu bin differs"
+            dropped = fast & ~(ok & (k >= 0) & (k < na))
+            assert not np.any(in_o[dropped]), "dropped a pair the oracle has in range"
+            binned = max(binned, int(counted.sum()))
+    assert binned > 0.6 * in_o.sum()          # most pairs take the fast path
+
+
 @pytest.mark.parametrize("L,ng,e0", [(1000.0, 11, 0.0), (3000.0, 59, 0.0), (1000.0, 11, 5.0)])
 def test_floor_bins_decide_as_the_oracle(lib, L, ng, e0):
     """The benchmark's path: evenly spaced s bins and 100 mu bins along z,
@@ -334,59 +380,16 @@ def test_floor_bins_decide_as_the_oracle(lib, L, ng, e0):
                          np.full(3, L), True)
     assert bp["lin"] == 1.0 and bp["lin_log"] == 0.0
     assert bp["lin_norange"] == (1.0 if e0 == 0.0 else 0.0)
-    chk = bp["lin_norange"] == 0.0
-    na, nb = ea.size - 1, mu_e.size - 1
-    # oracle bins (binary64, squared comparisons)
+    # the oracle's binary64 separation
     d = xj - xi
     d = np.where(d > 0.5 * L, d - L, np.where(d < -0.5 * L, d + L, d))
     s2o = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
     p2o = d[:, 2] * d[:, 2]
-    E = ea * ea
-    ko = np.searchsorted(E, s2o, side="right") - 1
-    in_o = (s2o >= E[0]) & (s2o < E[-1])
-    M = mu_e * mu_e
-    jo = np.zeros(s2o.size, dtype=np.int64)
-    for j in range(1, nb):
-        jo = np.where(p2o >= M[j] * s2o, j, jo)
-    # the kernel, emulated
-    c32 = F32(c)
+    # the kernel's binary32 separation, emulated
     reli = (xi - (idi + 0.5) * c).astype(F32)
     relj = (xj - (idj + 0.5) * c).astype(F32)
-    dd = fma32(dxc.astype(F32), np.full(dxc.shape, c32), relj) - reli
-    dx, dy, dz = dd[:, 0], dd[:, 1], dd[:, 2]
-    s2 = fma32(dz, dz, fma32(dy, dy, dx * dx))
-    cand = s2 < F32(bp["r2cut"])
-    assert np.all(cand[in_o])
-    C23, NC23H = F32(2.0 ** 23), F32(-(2.0 ** 23) + 0.5)
-    invA, offA, thrA = F32(bp["lin_invA"]), F32(bp["lin_offA"]), F32(bp["lin_thrA"])
-    nB, mA, cB = F32(bp["lin_nB"]), F32(bp["lin_mA"]), F32(bp["lin_cB"])
-    halfA = F32(0.5 * na)
-    hA1 = F32(halfA + F32(1.0)) if chk else halfA
-    n = s2.size
-    binned = 0
-    with np.errstate(divide="ignore", invalid="ignore"):
-        for rs in _rsqrt_ends(s2):
-            ts = fma32(s2 * rs, np.full(n, invA), np.full(n, offA))
-            f = _rd32(ts.astype(F64) + F64(C23))
-            dfr = ts - (f + NC23H)
-            near = ~(np.abs(dfr) < thrA)
-            ok = (np.abs(ts + (-hA1)) < halfA) if chk else np.ones(n, bool)
-            k = _bits(f) - 0x4B000000 - (1 if chk else 0)
-            tm = np.abs(dz) * (rs * nB)
-            fm = _rd32(tm.astype(F64) + F64(C23))
-            dm = tm - (fm + NC23H)
-            thm = fma32(np.full(n, -mA), rs, np.full(n, cB))
-            near |= ~(np.abs(dm) < thm)
-            j = _bits(fm) - 0x4B000000
-            fast = cand & ~near
-            counted = fast & ok & (k >= 0) & (k < na)
-            assert np.all(in_o[counted]), "counted a pair the oracle has out of range"
-            assert np.array_equal(k[counted], ko[counted]), "s bin differs"
-            assert np.array_equal(j[counted], jo[counted]), "mu bin differs"
-            dropped = fast & ~(ok & (k >= 0) & (k < na))
-            assert not np.any(in_o[dropped]), "dropped a pair the oracle has in range"
-            binned = max(binned, int(counted.sum()))
-    assert binned > 0.6 * in_o.sum()          # most pairs take the fast path
+    dd = fma32(dxc.astype(F32), np.full(dxc.shape, F32(c)), relj) - reli
+    _check_smu_floor(dd, s2o, p2o, bp, ea, mu_e)
 
 
 def _sigpi_oracle(xi, xj, L, periodic, los, ea, eb):
@@ -593,3 +596,39 @@ def test_log_bins_decide_as_the_oracle(lib):
                 assert not np.any(in_o[fast & ~(ok & (k >= 0) & (k < na))]), "dropped a pair"
                 binned = max(binned, int(counted.sum()))
     assert binned > 0.6 * in_o.sum()
+
+
+@pytest.mark.parametrize("bext", [90.0, 400.0])
+def test_tree_staging_decides_as_the_oracle(lib, bext):
+    """The k-d tree path stages a j-point as fl32(o + rel_j), o =
+    fl32(c_j + image L - c_i) from the binary64 centres of the two list nodes,
+    rel the binary32 offset from its node's centre (at most half the largest
+    node extent, which the bands take as the cell side): the floor-bin
+    decisions of the benchmark binning agree with the oracle's."""
+    rng = np.random.default_rng(int(bext))
+    L, R, n = 1000.0, 200.0, 300_000
+    ea = np.linspace(0.0, R, 41)
+    mu_e = np.linspace(0.0, 1.0, 101)
+    xi = rng.uniform(0.0, L, (n, 3))
+    s = np.concatenate([R * (1.0 - rng.random(n // 3) * 1e-3), R * rng.random(n - n // 3)])
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    xu = xi + v * s[:, None]                      # unwrapped partner
+    img = np.floor(xu / L)                        # its periodic image
+    xj = xu - img * L
+    xj = np.where(xj >= L, 0.0, xj)
+    # node centres within half the extent of each point, inside the box
+    ci = np.clip(xi - rng.uniform(-0.5, 0.5, (n, 3)) * bext, 0.0, L)
+    cj = np.clip(xj - rng.uniform(-0.5, 0.5, (n, 3)) * bext, 0.0, L)
+    reli = (xi - ci).astype(F32)
+    relj = (xj - cj).astype(F32)
+    o = ((cj + img * L) - ci).astype(F32)
+    dd = (o + relj) - reli                        # binary32 adds, as staged
+    d = xj - xi
+    d = np.where(d > 0.5 * L, d - L, np.where(d < -0.5 * L, d + L, d))
+    s2o = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    p2o = d[:, 2] * d[:, 2]
+    bp = P.pc_fp32_bands(P.Bins("smu", "z", ea, mu_e), bext, np.zeros(3), np.full(3, L),
+                         np.full(3, L), True)
+    assert bp["lin"] == 1.0
+    _check_smu_floor(dd, s2o, p2o, bp, ea, mu_e)
