@@ -632,3 +632,32 @@ def test_tree_staging_decides_as_the_oracle(lib, bext):
                          np.full(3, L), True)
     assert bp["lin"] == 1.0
     _check_smu_floor(dd, s2o, p2o, bp, ea, mu_e)
+
+
+def test_group_bounds_never_prune_a_candidate():
+    """The pair kernel skips a group of 32 staged j-points for a warp's 64
+    i-points when the binary32 gap between their boxes already puts every pair
+    past the candidate cut.  For binary32 points, fl(x_j - x_i) is at least
+    the rounded gap on each axis (rounding is monotone), so the kernel's own
+    s^2 chain on the pair is at least the same chain on the gaps: checked
+    here pair by pair on boxes that touch, overlap or lie just apart."""
+    rng = np.random.default_rng(21)
+    B, NI, NJ = 2000, 64, 32
+    centre_i = rng.uniform(-100.0, 100.0, (B, 1, 3))
+    # j-boxes at distances around the i-box's reach, some overlapping
+    off = rng.normal(size=(B, 1, 3))
+    off /= np.linalg.norm(off, axis=2, keepdims=True)
+    dist = rng.uniform(0.0, 60.0, (B, 1, 1))
+    centre_j = centre_i + off * dist
+    xi = (centre_i + rng.uniform(-10.0, 10.0, (B, NI, 3))).astype(F32)
+    xj = (centre_j + rng.uniform(-10.0, 10.0, (B, NJ, 3))).astype(F32)
+    lo_i, hi_i = xi.min(1), xi.max(1)
+    lo_j, hi_j = xj.min(1), xj.max(1)
+    gap = np.maximum(np.maximum(lo_j - hi_i, lo_i - hi_j), F32(0.0))      # binary32
+    gx, gy, gz = gap[:, 0], gap[:, 1], gap[:, 2]
+    d2 = fma32(gz, gz, fma32(gy, gy, gx * gx))
+    d = xj[:, None, :, :] - xi[:, :, None, :]                              # binary32
+    dx, dy, dz = (d[..., a].reshape(-1) for a in range(3))
+    s2 = fma32(dz, dz, fma32(dy, dy, dx * dx)).reshape(B, NI * NJ)
+    assert np.all(s2.min(axis=1) >= d2)
+    assert np.mean(d2 > 0) > 0.3            # many boxes really are apart
