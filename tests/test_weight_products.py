@@ -1,0 +1,91 @@
+"""The integer weight-product path's error bound (CPU, emulated).
+
+When every weight of both catalogues is a non-negative normal binary32 value
+(or zero) and the two catalogues' exponent spans add up to at most 12, the
+pair kernel accumulates each pair weight w_i w_j (Sect. 2.5) as an integer:
+the weight w = M 2^(e - 150) (M the 24-bit significand, e the biased
+exponent) is packed as M and k = e_max - e, a pair adds (M_i M_j) >> (k_i +
+k_j) to a 64-bit lane counter (at most 2^16 products between flushes), and a
+flush converts each counter to binary64 and multiplies it by
+2^(e_max,i + e_max,j - 300).  The truncation of one product is below
+2^(k_i + k_j - 46) <= 2^-34 of it, so every bin's sum is within 2^-34
+relative of the exact sum.  This test emulates the path on weights spanning
+the allowed exponents and checks the bound against exact rational sums, and
+that it is close to tight.
+"""
+
+from fractions import Fraction
+
+import numpy as np
+
+F32 = np.float32
+WINT_LIMIT = 1 << 16
+
+
+def _pack(w, emax):
+    b = w.astype(F32).view(np.uint32).astype(np.int64)
+    e = (b >> 23) & 0xFF
+    m = np.where(e > 0, (b & 0x7FFFFF) | 0x800000, 0)
+    k = np.where(e > 0, emax - e, 0)
+    return m, k, e
+
+
+def _emulated_sum(wi, wj, emax_i, emax_j):
+    """The kernel's integer accumulation of sum_i w_i wj_i (pairs given as two
+    aligned arrays), flushed every WINT_LIMIT products, as binary64."""
+    mi, ki, _ = _pack(wi, emax_i)
+    mj, kj, _ = _pack(wj, emax_j)
+    prod = [(int(a) * int(b)) >> int(s) for a, b, s in zip(mi, mj, ki + kj)]
+    unit = 2.0 ** (emax_i + emax_j - 300)
+    total = 0.0
+    for s in range(0, len(prod), WINT_LIMIT):
+        acc = sum(prod[s:s + WINT_LIMIT])
+        assert acc < 2 ** 64                      # one u64 lane counter
+        total += float(acc) * unit
+    return total
+
+
+def _weights(rng, n, e_lo, e_hi):
+    """Binary32 weights with biased exponents in [e_lo, e_hi] and full
+    significands (so truncations are as large as they get)."""
+    e = rng.integers(e_lo, e_hi + 1, n)
+    m = rng.integers(0x800000, 0x1000000, n)
+    return (m.astype(np.float64) * 2.0 ** (e - 150)).astype(F32)
+
+
+def test_integer_products_within_two_to_minus_34():
+    rng = np.random.default_rng(5)
+    for span_i, span_j in ((0, 0), (3, 3), (6, 6), (12, 0), (5, 7)):
+        e0i, e0j = 120, 130
+        wi = _weights(rng, 20000, e0i, e0i + span_i)
+        wj = _weights(rng, 20000, e0j, e0j + span_j)
+        got = _emulated_sum(wi, wj, e0i + span_i, e0j + span_j)
+        exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(wi, wj))
+        rel = abs(Fraction(got) - exact) / exact
+        assert rel < Fraction(1, 2 ** 34), (span_i, span_j, float(rel))
+    # the adverse case: one weight of each catalogue sets the maxima 6 above
+    # all the others, so nearly every product loses twelve bits; the sum's
+    # error then comes within a small factor of the bound
+    wi = _weights(rng, 20000, 120, 120)
+    wj = _weights(rng, 20000, 130, 130)
+    wi[0] = F32(2.0 ** (126 - 127))
+    wj[0] = F32(2.0 ** (136 - 127))
+    got = _emulated_sum(wi, wj, 126, 136)
+    exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(wi, wj))
+    rel = abs(Fraction(got) - exact) / exact
+    assert Fraction(1, 2 ** 38) < rel < Fraction(1, 2 ** 34), float(rel)
+
+
+def test_single_pair_truncation_reaches_the_bound():
+    """A pair whose exponents sit 6 below each maximum (k_i + k_j = 12), with
+    significands near 2^23 whose product ends in twelve set bits
+    ((2^23 + 4095)(2^23 + 4097) = -1 mod 2^12), loses just under 2^-34 of
+    itself: the bound is tight."""
+    emax_i = emax_j = 140
+    e = 134
+    wi = np.array([(2 ** 23 + 4095) * 2.0 ** (e - 150)], dtype=F32)
+    wj = np.array([(2 ** 23 + 4097) * 2.0 ** (e - 150)], dtype=F32)
+    got = _emulated_sum(wi, wj, emax_i, emax_j)
+    exact = Fraction(float(wi[0])) * Fraction(float(wj[0]))
+    rel = float(abs(Fraction(got) - exact) / exact)
+    assert 2.0 ** -35 < rel < 2.0 ** -34
