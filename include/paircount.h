@@ -413,6 +413,22 @@ pc_status pc_fp32_bands(const pc_bins *b, const double cell[3], const double lo[
                         const double hi[3], const double L[3], int periodic, double rmin,
                         double out[19]);
 
+/* The lookup tables the FP32 path stages for the same count as
+ * pc_fp32_bands (host-only).  lut receives n_entries pairs {edge, bin
+ * below} as binary32 (the bin as the float's bit pattern): per table T + 2
+ * cells of width 1 / inv_w over the binned quantity, each holding the single
+ * edge within the band of the cell (+inf: none; NaN: several, or the
+ * sentinel cell T + 1, always rescued) and the bin just below it; a value v
+ * takes cell min(floor(v inv_w), T + 1), bin = below + (v >= edge), and is
+ * near an edge unless |v - edge| >= its band.  desc[0..6] = first entry, T
+ * and inv_w of the first axis's table (s or sigma), the same for the second
+ * (mu or pi), and mu's window (a mu band wider than it is always rescued).
+ * *n_entries is set even when the tables do not fit max_entries
+ * (PC_EOVERFLOW).  Errors as pc_fp32_bands. */
+pc_status pc_fp32_tables(const pc_bins *b, const double cell[3], const double lo[3],
+                         const double hi[3], const double L[3], int periodic, double rmin,
+                         float *lut, int max_entries, int *n_entries, double desc[7]);
+
 /* Cell side the cost model picks for n points in volume `volume` with
  * largest separation r_max (Appendix B.1: cost a N_pair + b N_node). */
 double pc_suggest_cell_size(long long n, double volume, double r_max, int mode);

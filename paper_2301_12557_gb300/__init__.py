@@ -75,7 +75,8 @@ EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc
            "pc_count_batch", "pc_aabb", "pc_suggest_cell_size", "pc_strerror", "pc_last_error",
            "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune",
            "pc_build_tree", "pc_free_tree", "pc_tree_info", "pc_tree_export", "pc_count_tree",
-           "pc_tune_tree", "pc_hist_s2", "pc_count_tree_batch", "pc_stencil", "pc_fp32_bands"]
+           "pc_tune_tree", "pc_hist_s2", "pc_count_tree_batch", "pc_stencil", "pc_fp32_bands",
+           "pc_fp32_tables"]
 
 
 def library_path() -> str:
@@ -157,6 +158,10 @@ def lib():
     L.pc_fp32_bands.argtypes = [POINTER(pc_bins), POINTER(c_double), POINTER(c_double),
                                 POINTER(c_double), POINTER(c_double), c_int, c_double,
                                 POINTER(c_double)]
+    L.pc_fp32_tables.restype = c_int
+    L.pc_fp32_tables.argtypes = [POINTER(pc_bins), POINTER(c_double), POINTER(c_double),
+                                 POINTER(c_double), POINTER(c_double), c_int, c_double,
+                                 POINTER(c_float), c_int, POINTER(c_int), POINTER(c_double)]
     L.pc_count_tree_batch.restype = c_int
     L.pc_count_tree_batch.argtypes = [POINTER(vp), c_int, POINTER(pc_bins), POINTER(pc_opts), vp,
                                       vp, vp, POINTER(pc_stats)]
@@ -616,6 +621,24 @@ def pc_fp32_bands(bins: "Bins", cell, lo, hi, L=None, periodic: bool = False,
             "lin_invA", "lin_offA", "lin_thrA", "lin_nB", "lin_mA", "lin_cB", "lin_norange",
             "lin_log", "lin_invB", "lin_thrB", "lin_mS")
     return dict(zip(keys, (float(v) for v in out)))
+
+
+def pc_fp32_tables(bins: "Bins", cell, lo, hi, L=None, periodic: bool = False,
+                   rmin: float = 0.0):
+    """The FP32 path's lookup tables for a count (host-only): (entries as a
+    float32 array of shape (n, 2), descriptor dict)."""
+    def v3(a):
+        return (c_double * 3)(*np.broadcast_to(np.asarray(a, dtype=np.float64), (3,)))
+    args = (ctypes.byref(bins.s), v3(cell), v3(lo), v3(hi),
+            v3(L) if L is not None else None, int(bool(periodic)), float(rmin))
+    n = c_int(0)
+    desc = (c_double * 7)()
+    lib().pc_fp32_tables(*args, None, 0, ctypes.byref(n), desc)
+    lut = np.zeros((max(n.value, 1), 2), dtype=np.float32)
+    _check(lib().pc_fp32_tables(*args, lut.ctypes.data_as(POINTER(c_float)), n.value,
+                                ctypes.byref(n), desc), "pc_fp32_tables")
+    keys = ("a_off", "a_T", "a_inv", "b_off", "b_T", "b_inv", "mu_W")
+    return lut[:n.value], dict(zip(keys, (float(v) for v in desc)))
 
 
 def pc_suggest_cell_size(n: int, volume: float, r_max: float, mode: int = 0) -> float:

@@ -1476,6 +1476,51 @@ extern "C" pc_status pc_fp32_bands(const pc_bins *b, const double cell[3], const
     return PC_OK;
 }
 
+// Host-only copy of the lookup tables a count's FP32 path would stage (the
+// same plan as pc_fp32_bands).
+extern "C" pc_status pc_fp32_tables(const pc_bins *b, const double cell[3], const double lo[3],
+                                    const double hi[3], const double L[3], int periodic,
+                                    double rmin, float *lut, int max_entries, int *n_entries,
+                                    double desc[7]) {
+    if (!b || !cell || !lo || !hi || !n_entries || !desc || (periodic && !L) ||
+        max_entries < 0 || (max_entries > 0 && !lut))
+        return fail(PC_EINVAL, "pc_fp32_tables: bad arguments");
+    Geom g;
+    memset(&g, 0, sizeof(g));
+    g.periodic = periodic ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+        if (!(cell[a] > 0.0) || !std::isfinite(cell[a]) || !std::isfinite(lo[a]) ||
+            !std::isfinite(hi[a]) || hi[a] < lo[a])
+            return fail(PC_EINVAL, "pc_fp32_tables: bad cell sides or bounds");
+        if (periodic && (!(L[a] > 0.0) || !std::isfinite(L[a])))
+            return fail(PC_EINVAL, "pc_fp32_tables: periodic box needs L > 0");
+        g.c[a] = cell[a];
+        g.c32[a] = (float)cell[a];
+        g.ng[a] = 1;
+        g.lo[a] = lo[a];
+        g.L[a] = periodic ? L[a] : 0.0;
+        g.hL[a] = 0.5 * g.L[a];
+    }
+    Plan P;
+    pc_status s = make_plan(b, g, lo, hi, rmin, false, P, false);
+    if (s != PC_OK) return s;
+    *n_entries = (int)P.lut.size();
+    desc[0] = P.la.off;
+    desc[1] = P.la.T;
+    desc[2] = P.la.inv_w;
+    desc[3] = P.lb.off;
+    desc[4] = P.lb.T;
+    desc[5] = P.lb.inv_w;
+    desc[6] = P.mu_W;
+    if ((int)P.lut.size() > max_entries)
+        return fail(PC_EOVERFLOW, "pc_fp32_tables: max_entries too small");
+    for (size_t k = 0; k < P.lut.size(); ++k) {
+        lut[2 * k] = P.lut[k].x;
+        lut[2 * k + 1] = P.lut[k].y;
+    }
+    return PC_OK;
+}
+
 // Cost model of Appendix B.1 (cost = a N_pair + b N_node), specialised to the
 // GPU kernel: candidate pairs are charged per thread lane (a block occupies
 // NT * 2 lanes however many points its cell holds), and every (block,

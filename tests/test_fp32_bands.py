@@ -20,6 +20,8 @@ from the origin, periodic images.  It also checks that every pair the oracle
 finds within the largest separation passes the kernel's FP32 candidate cut.
 """
 
+import zlib
+
 import numpy as np
 import pytest
 
@@ -661,3 +663,181 @@ def test_group_bounds_never_prune_a_candidate():
     s2 = fma32(dz, dz, fma32(dy, dy, dx * dx)).reshape(B, NI * NJ)
     assert np.all(s2.min(axis=1) >= d2)
     assert np.mean(d2 > 0) > 0.3            # many boxes really are apart
+
+
+def _lut_locate(v, lut, off, T, inv):
+    """The kernel's table lookup: cell min(floor(v inv), T + 1) by a
+    round-down FMA onto the 2^23 grid, bin below + (v >= edge)."""
+    p = v.astype(F64) * F64(F32(inv))
+    hi = p + 2.0 ** 23
+    bb = hi - p
+    lo = (p - (hi - bb)) + (2.0 ** 23 - bb)
+    r = hi.astype(F32)
+    r = np.where((r.astype(F64) > hi) | ((r.astype(F64) == hi) & (lo < 0)),
+                 np.nextafter(r, F32(-np.inf)), r)
+    t = r.view(np.int32).astype(np.int64) - 0x4B000000
+    t = np.where(np.isnan(v) | (t < 0), T + 1, np.minimum(t, T + 1))   # unsigned clamp
+    ent = lut[off + t]
+    edge = ent[:, 0]
+    below = ent[:, 1].view(np.int32).astype(np.int64)
+    return below + (v >= edge), edge
+
+
+def _near(v, edge, eps):
+    return ~(np.abs(v - edge) >= eps)
+
+
+def _oracle_bins(mode, los, xi, xj, L, periodic, ea, eb):
+    """The oracle's flattened bin (or -1) of every pair, binary64."""
+    d = xj - xi
+    if periodic:
+        d = np.where(d > 0.5 * L, d - L, np.where(d < -0.5 * L, d + L, d))
+    s2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    if los == "z":
+        p2 = d[:, 2] * d[:, 2]
+    else:
+        lv = xi + xj
+        sl = (d[:, 0] * lv[:, 0] + d[:, 1] * lv[:, 1]) + d[:, 2] * lv[:, 2]
+        ll = (lv[:, 0] * lv[:, 0] + lv[:, 1] * lv[:, 1]) + lv[:, 2] * lv[:, 2]
+        p2 = (sl * sl) / ll
+    Ea = ea * ea
+    na = ea.size - 1
+    if mode == "sigpi":
+        q2 = np.maximum(s2 - p2, 0.0)
+        Eb = eb * eb
+        ka = np.searchsorted(Ea, q2, side="right") - 1
+        kb = np.searchsorted(Eb, p2, side="right") - 1
+        inside = (q2 >= Ea[0]) & (q2 < Ea[-1]) & (p2 >= Eb[0]) & (p2 < Eb[-1])
+        return np.where(inside, ka * (eb.size - 1) + kb, -1)
+    k = np.searchsorted(Ea, s2, side="right") - 1
+    inside = (s2 >= Ea[0]) & (s2 < Ea[-1])
+    if mode == "s":
+        return np.where(inside, k, -1)
+    nb = eb.size - 1
+    M = eb * eb
+    j = np.zeros(s2.size, dtype=np.int64)
+    for m in range(1, nb):
+        j = np.where(p2 >= M[m] * s2, m, j)
+    return np.where(inside, k * nb + j, -1)
+
+
+def _table_decisions(mode, los, dd, xa, bp, lut, tab, na, nb):
+    """(near, bin) of every pair through the kernel's table path, for every
+    combination of reciprocal-square-root ends; bin -1 when out of range."""
+    dx, dy, dz = dd[:, 0], dd[:, 1], dd[:, 2]
+    q = fma32(dy, dy, dx * dx)
+    s2 = fma32(dz, dz, q)
+    epsA, epsB = F32(bp["eps_a"]), F32(bp["eps_b"])
+    muA, muB, muW = F32(bp["mu_A"]), F32(bp["mu_B"]), F32(tab["mu_W"])
+    la = (int(tab["a_off"]), int(tab["a_T"]), tab["a_inv"])
+    lb = (int(tab["b_off"]), int(tab["b_T"]), tab["b_inv"])
+    if los == "mid":
+        two = np.full(dx.shape, F32(2.0))
+        lx, ly, lz = fma32(two, xa[:, 0], dx), fma32(two, xa[:, 1], dy), fma32(two, xa[:, 2], dz)
+        sl = fma32(dz, lz, fma32(dy, ly, dx * lx))
+        ll = fma32(lz, lz, fma32(ly, ly, lx * lx))
+        cc = fma32(fma32(dx, ly, -dy * lx), fma32(dx, ly, -dy * lx),
+                   fma32(fma32(dz, lx, -dx * lz), fma32(dz, lx, -dx * lz),
+                         fma32(dy, lz, -dz * ly) * fma32(dy, lz, -dz * ly)))
+    out = []
+    n = s2.size
+    for rs in _rsqrt_ends(s2):
+        for rx in (_rsqrt_ends(q) if los == "z" else _rsqrt_ends(ll)):
+            for rc in ((None,) if los == "z" else _rsqrt_ends(cc)):
+                if mode == "s" or mode == "smu":
+                    s = s2 * rs
+                    k, e = _lut_locate(s, lut, *la)
+                    near = _near(s, e, epsA)
+                    ok = (k >= 0) & (k < na)
+                    b = k
+                    if mode == "smu":
+                        mu = (np.abs(dz) * rs) if los == "z" else ((np.abs(sl) * rx) * rs)
+                        j, em = _lut_locate(mu, lut, *lb)
+                        epsm = fma32(np.full(n, muA), rs, np.full(n, muB))
+                        near = near | _near(mu, em, epsm) | (epsm > muW)
+                        b = k * nb + j
+                else:
+                    if los == "z":
+                        sg, pz = q * rx, np.abs(dz)
+                    else:
+                        sg, pz = (cc * rc) * rx, np.abs(sl) * rx
+                    k, e = _lut_locate(sg, lut, *la)
+                    j, ep = _lut_locate(pz, lut, *lb)
+                    near = _near(sg, e, epsA) | _near(pz, ep, epsB)
+                    ok = (k >= 0) & (k < na) & (j >= 0) & (j < nb)
+                    b = k * nb + j
+                out.append((near, np.where(ok, b, -1)))
+    return out
+
+
+TABLE_CASES = [
+    # (mode, line of sight, first-axis edges, second-axis edges)
+    ("s", "z", np.geomspace(0.1, 200.0, 41) * (1 + 1e-5 * np.cos(np.arange(41))), None),
+    ("smu", "z", np.geomspace(0.1, 200.0, 41) * (1 + 1e-5 * np.cos(np.arange(41))),
+     np.array([0.0, 0.05, 0.2, 0.21, 0.5, 0.8, 0.95, 1.0])),
+    ("smu", "mid", np.linspace(0.0, 200.0, 41), np.linspace(0.0, 1.0, 101)),
+    ("sigpi", "z", np.array([0.5, 1.0, 2.0, 4.0, 8.0, 16.0, 25.0, 60.0, 140.0]),
+     np.array([1.0, 3.0, 7.0, 12.0, 20.0, 45.0, 140.0])),
+    ("sigpi", "mid", np.array([0.5, 1.0, 2.0, 4.0, 8.0, 16.0, 25.0, 60.0, 140.0]),
+     np.array([1.0, 3.0, 7.0, 12.0, 20.0, 45.0, 140.0])),
+]
+
+
+@pytest.mark.parametrize("mode,los,ea,eb", TABLE_CASES)
+def test_table_bins_decide_as_the_oracle(lib, mode, los, ea, eb):
+    """The table path (edges not evenly spaced, and every (s, mu) count along
+    the midpoint line of sight): every pair the emulated kernel bins without
+    the rescue lands in the oracle's bin, every pair it drops is out of the
+    oracle's range, over random pairs and pairs planted at first-axis edges."""
+    rng = np.random.default_rng(zlib.crc32(f"{mode}/{los}/{ea.size}".encode()))
+    R = float(ea[-1] if mode != "sigpi" else np.hypot(ea[-1], eb[-1]))
+    if los == "z":
+        L, ng = 3000.0, 21
+        c, xi, xj, idi, idj, dxc = _pairs(rng, 200_000, L, ng, 0.0, R, True)
+        lo3, hi3, Lb, periodic, rmin, loc = np.zeros(3), np.full(3, L), np.full(3, L), True, 0.0, 0.0
+        # planted: separations at the first axis's edges times (1 + delta)
+        n2 = 100_000
+        xp = rng.uniform(0.0, L, (n2, 3))
+        sp_ = ea[rng.integers(0, ea.size, n2)] * (1 + rng.choice([0.0, 1e-7, -1e-7, 1e-5, -1e-5],
+                                                               n2))
+        v = rng.normal(size=(n2, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        if mode == "smu":
+            # half of them with mu at a mu edge times (1 + delta) as well
+            h = n2 // 2
+            mu = np.clip(eb[rng.integers(0, eb.size, h)] *
+                         (1 + rng.choice([0.0, 1e-7, -1e-7, 1e-6, -1e-6], h)), 0.0, 1.0)
+            phi = rng.uniform(0.0, 2 * np.pi, h)
+            st = np.sqrt(1.0 - mu * mu)
+            v[:h] = np.stack([st * np.cos(phi), st * np.sin(phi),
+                              mu * rng.choice([-1.0, 1.0], h)], axis=1)
+        xq = np.mod(xp + v * np.maximum(sp_, 1e-3)[:, None], L)
+        xq = np.where(xq >= L, 0.0, xq)
+        idp = np.minimum(np.floor(xp / c).astype(np.int64), ng - 1)
+        idq = np.minimum(np.floor(xq / c).astype(np.int64), ng - 1)
+        dq = idq - idp + (np.round((xp - xq) / L) * ng).astype(np.int64)
+        xi, xj = np.vstack([xi, xp]), np.vstack([xj, xq])
+        idi, idj, dxc = np.vstack([idi, idp]), np.vstack([idj, idq]), np.vstack([dxc, dq])
+    else:
+        c = 81.0
+        xi, xj, idi, idj, loc, hic = _shell_pairs(rng, 300_000, 1000.0, 2000.0, c, R)
+        dxc = idj - idi
+        lo3, hi3, Lb, periodic, rmin, L = loc, hic, None, False, 1000.0, 0.0
+    bins = P.Bins(mode, los, ea, eb)
+    bp = P.pc_fp32_bands(bins, c, lo3, hi3, Lb, periodic, rmin)
+    assert bp["fp32_ok"] == 1.0 and bp["lin"] == 0.0        # the table path
+    lut, tab = P.pc_fp32_tables(bins, c, lo3, hi3, Lb, periodic, rmin)
+    want = _oracle_bins(mode, los, xi, xj, L, periodic, ea, eb)
+    reli = (xi - (loc + (idi + 0.5) * c)).astype(F32)
+    relj = (xj - (loc + (idj + 0.5) * c)).astype(F32)
+    dd = fma32(dxc.astype(F32), np.full(dxc.shape, F32(c)), relj) - reli
+    na = ea.size - 1
+    nb = 1 if eb is None else eb.size - 1
+    binned = 0
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        for near, b in _table_decisions(mode, los, dd, xi.astype(F32), bp, lut, tab, na, nb):
+            fast = ~near
+            assert np.array_equal(b[fast], want[fast]), (
+                int(np.sum(b[fast] != want[fast])), mode, los)
+            binned = max(binned, int(np.sum(fast & (want >= 0))))
+    assert binned > 0.5 * np.sum(want >= 0)
