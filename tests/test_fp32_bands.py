@@ -13,11 +13,19 @@ That decision equals the oracle's binary64 decision whenever
 
 This test emulates those operations exactly in binary32 (numpy float32 for
 +, - and *, a fused multiply-add rounded once through an exact two-sum), takes
-the reciprocal square root at both ends of its error range, and checks that
-inequality for the library's bands over random and extreme pairs: every
-distance up to the largest separation, cells large and small, coordinates far
-from the origin, periodic images.  It also checks that every pair the oracle
-finds within the largest separation passes the kernel's FP32 candidate cut.
+the reciprocal square root (and the base-2 logarithm of the log bins) at both
+ends of its error range, and checks, with the library's own bands and tables
+(pc_fp32_bands, pc_fp32_tables):
+  * that inequality over random and extreme pairs: every distance up to the
+    largest separation, cells large and small, coordinates far from the
+    origin, periodic images, both lines of sight;
+  * the bin decisions themselves, against the oracle's, for the floor paths
+    ((s, mu) and log s along z, (sigma, pi) along both lines of sight), the
+    table paths, and the k-d tree path's staging, on random pairs and pairs
+    planted at edges;
+  * that every pair the oracle finds within the largest separation passes the
+    kernel's FP32 candidate cut, and that the 32-point group bounds never
+    prune a pair the kernel would keep.
 """
 
 import zlib
