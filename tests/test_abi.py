@@ -215,3 +215,29 @@ def test_binding_argument_counts_match_the_prototypes(lib):
         params = params.strip()
         n = 0 if params in ("", "void") else params.count(",") + 1
         assert len(getattr(lib, name).argtypes) == n, name
+
+
+def test_host_only_views_check_their_arguments(lib):
+    b = P.Bins("smu", "z", np.linspace(0.0, 50.0, 11), np.linspace(0.0, 1.0, 6))
+    out = (ctypes.c_double * 19)()
+    v3 = lambda *a: (ctypes.c_double * 3)(*a)   # noqa: E731
+    ok = lib.pc_fp32_bands(ctypes.byref(b.s), v3(10, 10, 10), v3(0, 0, 0), v3(100, 100, 100),
+                           v3(100, 100, 100), 1, 0.0, out)
+    assert ok == P.PC_OK and out[0] > 0 and out[4] > 50.0
+    assert lib.pc_fp32_bands(None, v3(10, 10, 10), v3(0, 0, 0), v3(1, 1, 1), None, 0, 0.0,
+                             out) == P.PC_EINVAL
+    assert lib.pc_fp32_bands(ctypes.byref(b.s), v3(0, 10, 10), v3(0, 0, 0), v3(1, 1, 1), None, 0,
+                             0.0, out) == P.PC_EINVAL
+    assert lib.pc_fp32_bands(ctypes.byref(b.s), v3(10, 10, 10), v3(0, 0, 0), v3(1, 1, 1), None,
+                             1, 0.0, out) == P.PC_EINVAL          # periodic without a box
+    bad = P.Bins("smu", "z", [0.0, 2.0, 1.0], [0.0, 1.0])
+    assert lib.pc_fp32_bands(ctypes.byref(bad.s), v3(10, 10, 10), v3(0, 0, 0), v3(1, 1, 1), None,
+                             0, 0.0, out) == P.PC_EINVAL
+    n = ctypes.c_int(0)
+    desc = (ctypes.c_double * 7)()
+    assert lib.pc_fp32_tables(ctypes.byref(b.s), v3(10, 10, 10), v3(0, 0, 0), v3(100, 100, 100),
+                              v3(100, 100, 100), 1, 0.0, None, 0, ctypes.byref(n),
+                              desc) == P.PC_EOVERFLOW
+    assert n.value > 0
+    lut, d = P.pc_fp32_tables(b, 10.0, np.zeros(3), np.full(3, 100.0), 100.0, True)
+    assert lut.shape == (n.value, 2) and d["a_T"] >= 16
