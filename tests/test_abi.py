@@ -218,12 +218,12 @@ def test_binding_argument_counts_match_the_prototypes(lib):
 
 
 def test_host_only_views_check_their_arguments(lib):
-    b = P.Bins("smu", "z", np.linspace(0.0, 50.0, 11), np.linspace(0.0, 1.0, 6))
+    b = P.Bins("smu", "z", np.linspace(0.0, 40.0, 11), np.linspace(0.0, 1.0, 6))
     out = (ctypes.c_double * 19)()
     v3 = lambda *a: (ctypes.c_double * 3)(*a)   # noqa: E731
     ok = lib.pc_fp32_bands(ctypes.byref(b.s), v3(10, 10, 10), v3(0, 0, 0), v3(100, 100, 100),
                            v3(100, 100, 100), 1, 0.0, out)
-    assert ok == P.PC_OK and out[0] > 0 and out[4] > 50.0
+    assert ok == P.PC_OK and out[0] > 0 and out[4] > 40.0
     assert lib.pc_fp32_bands(None, v3(10, 10, 10), v3(0, 0, 0), v3(1, 1, 1), None, 0, 0.0,
                              out) == P.PC_EINVAL
     assert lib.pc_fp32_bands(ctypes.byref(b.s), v3(0, 10, 10), v3(0, 0, 0), v3(1, 1, 1), None, 0,
@@ -241,3 +241,7 @@ def test_host_only_views_check_their_arguments(lib):
     assert n.value > 0
     lut, d = P.pc_fp32_tables(b, 10.0, np.zeros(3), np.full(3, 100.0), 100.0, True)
     assert lut.shape == (n.value, 2) and d["a_T"] >= 16
+    # a periodic separation of half the box is refused, as by the counts
+    b2 = P.Bins("s", "z", [0.0, 50.0])
+    assert lib.pc_fp32_bands(ctypes.byref(b2.s), v3(10, 10, 10), v3(0, 0, 0), v3(100, 100, 100),
+                             v3(100, 100, 100), 1, 0.0, out) == P.PC_EINVAL
