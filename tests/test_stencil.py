@@ -13,7 +13,6 @@ looseness of its fitted exponent.
 import itertools
 import math
 
-import numpy as np
 import pytest
 
 P = pytest.importorskip("paper_2301_12557_gb300")

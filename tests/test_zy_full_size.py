@@ -12,7 +12,6 @@ import numpy as np
 import pytest
 
 import oracle
-from synth import catalogs as C
 from synth import workloads as W
 
 P = pytest.importorskip("paper_2301_12557_gb300")
