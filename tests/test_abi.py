@@ -245,3 +245,13 @@ def test_host_only_views_check_their_arguments(lib):
     b2 = P.Bins("s", "z", [0.0, 50.0])
     assert lib.pc_fp32_bands(ctypes.byref(b2.s), v3(10, 10, 10), v3(0, 0, 0), v3(100, 100, 100),
                              v3(100, 100, 100), 1, 0.0, out) == P.PC_EINVAL
+
+
+def test_header_compiles_as_c_and_cxx(tmp_path):
+    """include/paircount.h stands alone in C99 and in C++17 (extern "C")."""
+    src = tmp_path / "use.c"
+    src.write_text('#include "paircount.h"\nint main(void) { return (int)PC_OK; }\n')
+    for cc, std, lang in (("gcc", "-std=c99", "c"), ("g++", "-std=c++17", "c++")):
+        subprocess.run([cc, std, "-x", lang, "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-fsyntax-only", "-I", os.path.join(ROOT, "include"), str(src)],
+                       check=True, capture_output=True)
