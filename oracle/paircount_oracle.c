@@ -151,6 +151,9 @@ typedef struct {
     int ng[3];
     const int64_t *start1, *start2;   /* cell starts, ncell + 1 */
     const int64_t *ord1, *ord2;       /* point indices grouped by cell */
+    const double *xs1, *xs2;          /* coordinates in cell order (Sect. 2.1: the grid
+                                         stores each cell's points contiguously) */
+    const double *ws1, *ws2;          /* weights in cell order (or NULL) */
     int64_t ncell;
     int tid, nthreads;
     int64_t *cnt;                     /* private histogram */
@@ -167,10 +170,26 @@ static inline void add_pair(job *jb, int64_t i, int64_t j)
     if (jb->wsum) neumaier_add(&jb->wsum[bin], &jb->wcomp[bin], jb->w1[i] * jb->w2[j]);
 }
 
+/* Pair (p, q) of the cell-ordered copies: the same values as add_pair on
+ * the original indices ord1[p], ord2[q]. */
+static inline void add_pair_sorted(job *jb, int64_t p, int64_t q)
+{
+    const double *a = jb->xs1 + 3 * p;
+    const double *b = jb->xs2 + 3 * q;
+    int bin = pair_bin(jb->c, a, b);
+    if (bin < 0) return;
+    jb->cnt[bin] += 1;
+    if (jb->wsum) neumaier_add(&jb->wsum[bin], &jb->wcomp[bin], jb->ws1[p] * jb->ws2[q]);
+}
+
 static void *brute_worker(void *arg)
 {
     job *jb = (job *)arg;
-    const int64_t CH = 64;
+    /* rows are dealt out in chunks of up to 64, fewer when the rows are few,
+     * so that every thread gets some */
+    int64_t CH = jb->n1 / ((int64_t)jb->nthreads * 4);
+    if (CH > 64) CH = 64;
+    if (CH < 1) CH = 1;
     for (int64_t c0 = (int64_t)jb->tid * CH; c0 < jb->n1; c0 += (int64_t)jb->nthreads * CH) {
         int64_t c1 = c0 + CH < jb->n1 ? c0 + CH : jb->n1;
         for (int64_t i = c0; i < c1; i++) {
@@ -181,34 +200,42 @@ static void *brute_worker(void *arg)
     return NULL;
 }
 
+/* Work item k = (cell, run of up to GRID_CHUNK of its points) goes to
+ * thread k % nthreads, so the split is fixed by the input alone. */
+#define GRID_CHUNK 256
+
 static void *grid_worker(void *arg)
 {
     job *jb = (job *)arg;
     const int *ng = jb->ng;
-    for (int64_t a = jb->tid; a < jb->ncell; a += jb->nthreads) {
+    int64_t item = 0;
+    for (int64_t a = 0; a < jb->ncell; a++) {
         int64_t a0 = jb->start1[a], a1 = jb->start1[a + 1];
         if (a0 == a1) continue;
         int ax = (int)(a % ng[0]);
         int ay = (int)((a / ng[0]) % ng[1]);
         int az = (int)(a / ((int64_t)ng[0] * ng[1]));
-        for (int oz = -1; oz <= 1; oz++)
-        for (int oy = -1; oy <= 1; oy++)
-        for (int ox = -1; ox <= 1; ox++) {
-            int bx = ax + ox, by = ay + oy, bz = az + oz;
-            if (jb->c->periodic) {
-                bx = (bx + ng[0]) % ng[0];
-                by = (by + ng[1]) % ng[1];
-                bz = (bz + ng[2]) % ng[2];
-            } else if (bx < 0 || by < 0 || bz < 0 || bx >= ng[0] || by >= ng[1] || bz >= ng[2]) {
-                continue;
-            }
-            int64_t b = ((int64_t)bz * ng[1] + by) * ng[0] + bx;
-            if (jb->is_auto && b < a) continue;
-            int64_t b0 = jb->start2[b], b1 = jb->start2[b + 1];
-            for (int64_t p = a0; p < a1; p++) {
-                int64_t i = jb->ord1[p];
-                int64_t q0 = (jb->is_auto && b == a) ? p + 1 : b0;
-                for (int64_t q = q0; q < b1; q++) add_pair(jb, i, jb->ord2[q]);
+        for (int64_t p0 = a0; p0 < a1; p0 += GRID_CHUNK, item++) {
+            if (item % jb->nthreads != jb->tid) continue;
+            int64_t p1 = p0 + GRID_CHUNK < a1 ? p0 + GRID_CHUNK : a1;
+            for (int oz = -1; oz <= 1; oz++)
+            for (int oy = -1; oy <= 1; oy++)
+            for (int ox = -1; ox <= 1; ox++) {
+                int bx = ax + ox, by = ay + oy, bz = az + oz;
+                if (jb->c->periodic) {
+                    bx = (bx + ng[0]) % ng[0];
+                    by = (by + ng[1]) % ng[1];
+                    bz = (bz + ng[2]) % ng[2];
+                } else if (bx < 0 || by < 0 || bz < 0 || bx >= ng[0] || by >= ng[1] || bz >= ng[2]) {
+                    continue;
+                }
+                int64_t b = ((int64_t)bz * ng[1] + by) * ng[0] + bx;
+                if (jb->is_auto && b < a) continue;
+                int64_t b0 = jb->start2[b], b1 = jb->start2[b + 1];
+                for (int64_t p = p0; p < p1; p++) {
+                    int64_t q0 = (jb->is_auto && b == a) ? p + 1 : b0;
+                    for (int64_t q = q0; q < b1; q++) add_pair_sorted(jb, p, q);
+                }
             }
         }
     }
@@ -240,6 +267,15 @@ static void bucket(const double *x, int64_t n, const double *lo, const double *w
     for (int64_t i = 0; i < n; i++) ord[cur[cid[i]]++] = i;
     free(cur);
     free(cid);
+}
+
+/* Rows of x (each `width` doubles) in the order ord: the cell-sorted copy. */
+static double *gather_rows(const double *x, const int64_t *ord, int64_t n, int width)
+{
+    double *y = (double *)malloc(sizeof(double) * (size_t)(width * (n > 0 ? n : 1)));
+    for (int64_t p = 0; p < n; p++)
+        for (int a = 0; a < width; a++) y[width * p + a] = x[width * ord[p] + a];
+    return y;
 }
 
 static int check_edges(const double *e, int n, int zero_one)
@@ -316,6 +352,7 @@ int oracle_count(const double *x1, const double *w1, int64_t n1,
     double lo[3] = {0, 0, 0}, wcell[3] = {1, 1, 1};
     int64_t ncell = 1;
     int64_t *st1 = NULL, *st2 = NULL, *or1 = NULL, *or2 = NULL;
+    double *xs1 = NULL, *xs2 = NULL, *ws1 = NULL, *ws2 = NULL;
     if (use_grid && n1 > 0 && n2 > 0) {
         double reff = (mode == MODE_SIGPI) ? sqrt(c.Ea[na] + c.Eb[c.nb]) : ea[na];
         double hi[3];
@@ -351,6 +388,13 @@ int oracle_count(const double *x1, const double *w1, int64_t n1,
                 or2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)n2);
                 bucket(x2, n2, lo, wcell, ng, ncell, st2, or2);
             }
+            xs1 = gather_rows(x1, or1, n1, 3);
+            ws1 = weighted ? gather_rows(w1, or1, n1, 1) : NULL;
+            if (is_auto) { xs2 = xs1; ws2 = ws1; }
+            else {
+                xs2 = gather_rows(x2, or2, n2, 3);
+                ws2 = weighted ? gather_rows(w2, or2, n2, 1) : NULL;
+            }
         }
     } else {
         use_grid = 0;
@@ -367,6 +411,7 @@ int oracle_count(const double *x1, const double *w1, int64_t n1,
         jb->use_grid = use_grid;
         for (int a = 0; a < 3; a++) jb->ng[a] = ng[a];
         jb->start1 = st1; jb->start2 = st2; jb->ord1 = or1; jb->ord2 = or2;
+        jb->xs1 = xs1; jb->xs2 = xs2; jb->ws1 = ws1; jb->ws2 = ws2;
         jb->ncell = ncell;
         jb->tid = t; jb->nthreads = nthreads;
         jb->cnt = (int64_t *)calloc((size_t)c.nbins, sizeof(int64_t));
@@ -403,6 +448,9 @@ int oracle_count(const double *x1, const double *w1, int64_t n1,
     free(jobs); free(th);
     if (st2 != st1) { free(st2); free(or2); }
     free(st1); free(or1);
+    if (xs2 != xs1) free(xs2);
+    if (ws2 != ws1) free(ws2);
+    free(xs1); free(ws1);
     if (c2 != c1) free(c2);
     free(c1);
     free(c.Ea); free(c.Eb);

@@ -16,6 +16,8 @@ from .catalogs import (  # noqa: F401
     lognormal_weights,
     mixed_box,
     batch_mocks,
+    batch_mock,
+    batch_mock_size,
     lattice_points,
     s2_samples,
 )

@@ -168,14 +168,23 @@ def batch_mocks(m: int, n_min: int, n_max: int, sigma_lo: float, sigma_hi: float
     Mock k is seeded with seed + 1000 * k, so any single mock can be
     regenerated on its own.
     """
-    mocks = []
-    for k in range(int(m)):
-        rng = _rng(seed + 1000 * k)
-        n = int(rng.integers(n_min, n_max + 1))
-        sig = float(sigma_lo + rng.random() * (sigma_hi - sigma_lo))
-        mocks.append(neyman_scott(n, max(1, n // int(mean_children)), mean_children,
-                                  sig, L, seed + 1000 * k + 1))
-    return mocks
+    return [batch_mock(k, n_min, n_max, sigma_lo, sigma_hi, L, seed, mean_children)
+            for k in range(int(m))]
+
+
+def batch_mock_size(k: int, n_min: int, n_max: int, seed: int) -> int:
+    """Number of points of mock k of ``batch_mocks`` (no positions drawn)."""
+    return int(_rng(seed + 1000 * int(k)).integers(n_min, n_max + 1))
+
+
+def batch_mock(k: int, n_min: int, n_max: int, sigma_lo: float, sigma_hi: float,
+               L: float, seed: int, mean_children: float = 10.0) -> np.ndarray:
+    """Mock k of ``batch_mocks`` on its own (the same array, from its own seed)."""
+    rng = _rng(seed + 1000 * int(k))
+    n = int(rng.integers(n_min, n_max + 1))
+    sig = float(sigma_lo + rng.random() * (sigma_hi - sigma_lo))
+    return neyman_scott(n, max(1, n // int(mean_children)), mean_children,
+                        sig, L, seed + 1000 * int(k) + 1)
 
 
 def lattice_points(n: int, side: int, seed: int, unique: bool = True) -> np.ndarray:
