@@ -5,8 +5,17 @@ compute: every pair of a random sample of i-points with the whole catalogue
 (the cross form of the same pair set), bit-exact counts and weighted sums
 within 1e-10; the batch is also tied to single counts of every mock.
 
+The 256-mock batch is also compared whole, row by row, with the oracle's
+histograms of four of its mocks stored in tests/golden/fullsize/ (smallest,
+largest, two of median size), for the grid batch and the tree batch.
+
 (Collected after the main parity file: these cases take tens of seconds.)
 """
+
+import glob
+import hashlib
+import json
+import os
 
 import numpy as np
 import pytest
@@ -60,9 +69,25 @@ def test_weighted_cube_100m_sampled():
     _check(g, o, gw, ow, "weighted cube, sampled cross")
 
 
+def _mock_goldens():
+    """{mock index: (stored record, counts)} of the stored whole-mock histograms."""
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize")
+    out = {}
+    for path in sorted(glob.glob(os.path.join(here, "mocks256_ns_smu40x100_mock*.json"))):
+        rec = json.load(open(path))
+        k = int(rec["target"].rsplit("mock", 1)[1])
+        out[k] = (rec, np.asarray(rec["counts"], dtype=np.int64))
+    return out
+
+
 def test_batched_mocks_256_vs_single_counts_and_sampled_oracle():
     w = W.WORKLOADS["mocks256_ns_smu40x100"]
     mocks = W.make_inputs(w)["mocks"]
+    goldens = _mock_goldens()
+    assert len(goldens) == 4
+    for k, (rec, _) in goldens.items():
+        h = hashlib.sha256(np.ascontiguousarray(mocks[k]).tobytes()).hexdigest()
+        assert h == rec["catalogue_sha256"], f"mock {k} differs from the stored one"
     X = [torch.from_numpy(x).cuda() for x in mocks]
     bins = P.Bins("smu", "z", w.edges_a, w.edges_b)
     box = P.make_box(w.L, True)
@@ -76,9 +101,24 @@ def test_batched_mocks_256_vs_single_counts_and_sampled_oracle():
         for k, g in enumerate(gs):
             single, _, _ = P.pc_count_auto(g, bins, opts)
             assert np.array_equal(batch[k], single), f"mock {k}"
+        for k, (_, want) in goldens.items():
+            _check(batch[k], want, what=f"mock {k}: grid batch row vs whole oracle histogram")
     finally:
         for g in gs:
             g.free()
+    # the tree batch (one persistent launch over every tree's lists), tuned
+    # on the median mock as the benchmark does
+    topts, cap, _ = P.pc_tune_tree(X[med], box=box, bins=bins)
+    ts = [P.pc_build_tree(x, box=box, list_cap=cap) for x in X]
+    try:
+        tb, _, _ = P.pc_count_tree_batch(ts, bins, topts)
+        tb = tb.reshape(len(X), -1)
+        assert np.array_equal(tb, batch), "tree batch differs from the grid batch"
+        for k, (_, want) in goldens.items():
+            _check(tb[k], want, what=f"mock {k}: tree batch row vs whole oracle histogram")
+    finally:
+        for t in ts:
+            t.free()
     kw = dict(box=w.L, periodic=True, mode="smu", edges_a=w.edges_a, edges_b=w.edges_b)
     for k in (0, len(X) - 1):
         D = mocks[k]
