@@ -1,18 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of exact grid pair counting on GB300.
 
-Default workload: 2,000,000 Neyman-Scott points (200,000 parents, Poisson(10)
-children, sigma = 5 Mpc/h) in a periodic 1000 Mpc/h cube, auto counts in
-(s, mu) bins (40 linear s bins on [0, 200) x 100 mu bins, line of sight z),
-FP32 separations with binary64 rescue, int64 counts.
+Default workload: 100,000,000 points in a periodic 3000 Mpc/h cube (half
+uniform, half Neyman-Scott clusters with sigma = 5 Mpc/h), unit-mean
+lognormal binary32 weights (sigma_ln = 0.3), weighted auto counts in 40
+linear s bins of 5 Mpc/h on [0, 200): FP32 separations with binary64 rescue
+near bin edges, int64 counts and binary64 weighted sums.  The same line also
+carries the plain FP64 path on the same GPU, the measured FP32/FP64 peaks,
+and the 2,000,000-point clustered cube in (s, mu) 40 x 100 bins under its
+own workload name.
 
 One step = one pass of the whole path over the catalogue already resident in
-HBM: canonicalise + grid build (bounds, per-cell counts, scan, scatter),
-i-block list, pair kernel (separation, bin lookup, shared histograms), the
-binary64 re-evaluation of near-edge pairs (inside the pair kernel or by the
-rescue kernel, as tuned), histogram read-back.  The value is in-range pairs
-binned per second: the one unit every exact method shares, whatever its cell
-size or pruning.
+HBM: canonicalise + grid build (bounds, per-cell counts, scan, scatter,
+weight packing), i-block list, pair kernel (separation, bin lookup, shared
+histograms, weight products), the binary64 re-evaluation of near-edge pairs
+(inside the pair kernel or by the rescue kernel, as tuned), histogram
+read-back.  The value is in-range pairs binned per second: the one unit
+every exact method shares, whatever its cell size or pruning.
 
 Prints one JSON line.  --impl reference times the CPU oracle (brute force,
 binary64) on a bounded sample of the same workload instead.
@@ -40,7 +44,7 @@ UNIT = "pairs/s"                 # in-range pairs binned per second (every arm)
 FLOPS_PER_CANDIDATE = 8          # separation: 3 subtractions, 3 multiplies, 2 adds
 FLOPS_PER_IN_RANGE = 6           # bin locate per in-range pair
 FP32_LANES_PER_SM = 128
-FP64_PEAK_NOMINAL = 1.25         # TFLOP/s, GB300 FP64 (non-tensor), nominal
+DEFAULT_WORKLOAD = "mixed_periodic_n100m_s40_w"
 
 
 def parse():
@@ -49,8 +53,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="ns_periodic_n2m_smu40x100")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-shards", type=int, default=0,
+                    help="plain FP64 arm of the weighted workloads: time it on 1/S of the "
+                         "i-blocks (0: 64 for catalogues of 5e7 points or more, else 1)")
+    ap.add_argument("--no-weights", action="store_true",
+                    help="weighted workloads: count the same catalogues without their weights "
+                         "(to compare the weighted and unweighted kernels)")
+    ap.add_argument("--config2-steps", type=int, default=5,
+                    help="default line only: also time the 2M-point (s, mu) benchmark this "
+                         "many steps and report it under its workload name (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tree-steps", type=int, default=3,
                     help="steps of the k-d tree path reported beside the grid line (0: none)")
@@ -112,16 +125,6 @@ def max_over_ranks(v, dist, dev):
     t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
-
-
-def measured_peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        try:
-            return json.load(open(p)), "measured"
-        except Exception:
-            pass
-    return {"sm_max_mhz": 2070.0}, "fallback"
 
 
 # --------------------------------------------------------------------------
@@ -195,46 +198,60 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
-def oracle_sample_rate(D, w, seconds, seed=0, L=None, threads=None):
+def oracle_sample_rate(D, w, seconds, seed=0, L=None, threads=None, wt=None):
     """Oracle throughput in in-range pairs binned per second: brute force over
     all pairs of a random sample of i-points against the whole catalogue (the
-    cross form of the same pair set), self-pairs excluded.  Returns (rate,
-    seconds, sample size, cores, pair evaluations per second)."""
+    cross form of the same pair set), self-pairs excluded, with the weighted
+    sums when weights wt are given.  Returns (rate, seconds, sample size,
+    cores, pair evaluations per second)."""
     import oracle
     oracle.build()
     rng = np.random.default_rng(seed)
     kw = dict(box=w.L if L is None else L, periodic=w.periodic, mode=w.mode, los=w.los,
               edges_a=w.edges_a, edges_b=w.edges_b)
     n = D.shape[0]
+    if wt is not None:
+        wt = np.asarray(wt, dtype=np.float64)
     m0, dt = 16, 0.0
+
+    def run(idx):
+        S = np.ascontiguousarray(D[idx])
+        if wt is None:
+            return oracle.count(S, D, threads=threads, **kw)
+        return oracle.count(S, D, w1=wt[idx], w2=wt, threads=threads, **kw)
     while True:      # calibrate on growing samples until one takes >= 1/8 of the budget
-        S = np.ascontiguousarray(D[rng.choice(n, m0, replace=False)])
+        idx = rng.choice(n, m0, replace=False)
         t = time.perf_counter()
-        oracle.count(S, D, threads=threads, **kw)
+        run(idx)
         dt = max(time.perf_counter() - t, 1e-6)
         if dt >= seconds / 8 or m0 >= n:
             break
         m0 = min(n, m0 * 4)
     m = int(max(1, min(n, m0 * seconds / dt)))
-    S = np.ascontiguousarray(D[rng.choice(n, m, replace=False)])
+    idx = rng.choice(n, m, replace=False)
     t = time.perf_counter()
-    c, _ = oracle.count(S, D, threads=threads, **kw)
+    c, _ = run(idx)
     dt = time.perf_counter() - t
     cores = threads or oracle.default_threads()
     in_range = int(c.sum()) - m        # each sampled point pairs with itself at s = 0
     return in_range / dt, dt, m, cores, m * n / dt
 
 
-def traffic_record():
-    """DRAM bytes per pair-kernel launch from the committed ncu summary, if
-    the kernel source is unchanged since it was captured."""
-    p = os.path.join(ROOT, "profiles", "pairs_f32_traffic.json")
+def traffic_record(workload, tree=False, inline=True):
+    """DRAM bytes per pair-kernel launch of a workload from the committed ncu
+    summary (profiles/traffic_<workload>.json), if the kernel source is
+    unchanged since it was captured and the structure and rescue mode match."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     if not os.path.exists(p):
         return None
     try:
         rec = json.load(open(p))
         src = open(os.path.join(ROOT, "paper_2301_12557_gb300", "csrc", "pairs_impl.cuh"), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha256_16"):
+            return None
+        if bool(rec.get("tree", False)) != bool(tree):
+            return None
+        if (rec.get("rescue") == "inline") != bool(inline):
             return None
         return rec
     except Exception:
@@ -248,20 +265,26 @@ def run_reference(args):
         return 0
     from synth import workloads as W
     w = W.WORKLOADS[args.workload]
-    D = W.make_inputs(w)["D"]
+    wt = None
+    if w.weighted or len(w.pair_kinds) > 1:
+        inp = sets_inputs(w, 1.0)
+        big = max([k for k in ("D", "R") if k in inp], key=lambda k: inp[k].shape[0])
+        D, wt, L_box = inp[big], inp.get("w" + big), inp["L"]
+    else:
+        D, L_box = W.make_inputs(w)["D"], w.L
     per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     rates = []
     samp = None
     for k in range(args.warmup + args.steps):
-        r, dt, m, cores, _ = oracle_sample_rate(D, w, per_step, seed=k)
+        r, dt, m, cores, _ = oracle_sample_rate(D, w, per_step, seed=k, L=L_box, wt=wt)
         if k >= args.warmup:
             rates.append((r, dt, m))
         samp = (m, cores)
     tot_pairs = sum(r * dt for r, dt, _ in rates)
     tot_t = sum(dt for _, dt, _ in rates)
     value = tot_pairs / tot_t
-    sample = (f"{samp[0]} random i-points x all {D.shape[0]} points per step "
-              f"(brute force, binary64); in-range pairs found per second")
+    sample = (f"{samp[0]} random i-points x all {D.shape[0]} points per step (brute force, "
+              f"binary64{', weighted' if wt is not None else ''}); in-range pairs found per second")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -276,9 +299,14 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def run_ours(args, emit=True):
+    """The single-catalogue line (2M-point clustered cube by default of this
+    function).  emit=False: return the line instead of printing it (one
+    process, no collectives)."""
     import torch
     rank, world, local = dist_env()
+    if not emit:
+        rank, world = 0, 1
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -418,6 +446,8 @@ def run_ours(args):
                "h2d_bytes_per_step": int(n * 3 * 8), "d2h_bytes_per_step": int(bins.nbins * 8),
                "ms_per_step": e2e_t}
 
+    peaks = measured_fp_peaks(P, stream, local)
+
     # ---- plain FP64 path on the same GB300 -----------------------------------
     fp64 = None
     if args.fp64_steps > 0:
@@ -439,7 +469,7 @@ def run_ours(args):
         exact = bool(torch.equal(out64, out))
         inr64 = float(out64.sum().item())
         # the FP64 kernel evaluates every candidate: the same per-pair flop
-        # counts, against GB300's nominal FP64 (non-tensor) rate
+        # counts, against the measured FP64 rate
         fl64 = FLOPS_PER_CANDIDATE * float(s64.candidates) + FLOPS_PER_IN_RANGE * inr64
         k64_ms = s64.ms_pairs if s64.ms_pairs > 0 else statistics.mean(ms64)
         ach64 = fl64 / (k64_ms * 1e-3) / 1e12
@@ -447,9 +477,9 @@ def run_ours(args):
                 "cell_size": o64.cell_size,
                 "ms_per_step": statistics.mean(ms64), "steps": args.fp64_steps,
                 "counts_identical_to_fp32_rescue": exact,
-                "roofline": {"bound": "fp64", "achieved": ach64, "peak": FP64_PEAK_NOMINAL,
-                             "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_NOMINAL,
-                             "peak_source": "nominal GB300 FP64 rate (not measured)",
+                "roofline": {"bound": "fp64", "achieved": ach64, "peak": peaks["fp64_tflops"],
+                             "unit": "TFLOP/s", "frac": ach64 / peaks["fp64_tflops"],
+                             "peak_source": "measured: DFMA loop (pc_fp_peak), " + peaks["profile"],
                              "kernel_ms": k64_ms}}
 
     # ---- the k-d tree path on the same catalogue (grid line only) -----------
@@ -486,35 +516,33 @@ def run_ours(args):
               "counts_identical_to_grid": bool(torch.equal(out_kd, out))}
 
     # ---- roofline of the dominant kernel -------------------------------------
-    peaks, peak_src = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    fp32_peak = peaks["fp32_tflops"]
     ms_pairs = statistics.mean(s.ms_pairs for s in stats)
     cand = stats[0].candidates
-    evaluated = cand - stats[0].pruned       # pairs the kernel separated one by one
-    flops = FLOPS_PER_CANDIDATE * evaluated + FLOPS_PER_IN_RANGE * inr_step
+    flops = FLOPS_PER_CANDIDATE * float(cand)
     achieved = flops / (ms_pairs * 1e-3) / 1e12
-    trec = traffic_record()
+    evaluated = cand - stats[0].pruned       # pairs the kernel separated one by one
+    flops_ev = FLOPS_PER_CANDIDATE * evaluated + FLOPS_PER_IN_RANGE * inr_step
+    ach_ev = flops_ev / (ms_pairs * 1e-3) / 1e12
+    trec = traffic_record(w.name, tree, opts.rescue_capacity < 0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
-                # the record holds for the grid kernel with the same rescue mode
-                "traffic": (trec["bytes_per_launch"]
-                            if trec and not tree and (trec.get("rescue") == "inline") ==
-                            (opts.rescue_capacity < 0) else None),
+                "traffic": trec["bytes_per_launch"] if trec else None,
+                "traffic_source": trec.get("source") if trec else None,
                 "kernel": "k_pairs_f32<SMU,LOS_Z>" + (" (tree variant)" if tree else ""),
                 "flops_per_launch": flops,
-                "flops_definition": (f"{FLOPS_PER_CANDIDATE} per pair evaluated one by one "
-                                     f"({evaluated:.4g}) + {FLOPS_PER_IN_RANGE} per in-range "
-                                     f"pair ({inr_step:.4g})"),
-                "peak_source": (f"FP32 non-tensor: {props.multi_processor_count} SMs x "
-                                f"{FP32_LANES_PER_SM} lanes x 2 flops x {sm_mhz:.0f} MHz "
-                                f"({peak_src} sm_max_mhz)"),
+                "flops_definition": (f"{FLOPS_PER_CANDIDATE} FP32 flops per candidate pair of the "
+                                     f"cell stencil ({float(cand):.4g} per launch)"),
+                "achieved_evaluated": ach_ev, "frac_evaluated": ach_ev / fp32_peak,
+                "evaluated_definition": (f"{FLOPS_PER_CANDIDATE} per pair evaluated one by one "
+                                         f"({evaluated:.4g}) + {FLOPS_PER_IN_RANGE} per in-range "
+                                         f"pair ({inr_step:.4g})"),
+                "peak_source": "measured: " + peaks["how"] + " (" + peaks["profile"] + ")",
                 "kernel_ms": ms_pairs,
                 "kernel_share_of_step": ms_pairs / (t_max / args.steps)}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if emit and rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, dt, m, cores, evals = oracle_sample_rate(D_host, w, args.cpu_seconds, L=L_box)
         r1, dt1, m1, _, _ = oracle_sample_rate(D_host, w, args.cpu_seconds / 4, seed=1, L=L_box,
                                                threads=1)
@@ -567,11 +595,14 @@ def run_ours(args):
             "kdtree_path": kd,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "roofline": roofline,
+            "measured_peaks": {k: v for k, v in peaks.items() if k != "how"},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": int(launches),
         }
+        if not emit:
+            return line
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -746,28 +777,71 @@ def run_batch(args):
     return 0
 
 
-def run_sets(args):
-    """Workloads with weights and several pair kinds (the survey shell's DD,
-    DR and RR; the 100M-point weighted cube): every step builds every
-    catalogue's grid and runs every count, weighted sums in binary64."""
+def sets_inputs(w, f, seed_offset=0):
+    """Catalogues of a weighted or multi-catalogue workload.  f < 1: the
+    periodic cube keeps its number density and cluster shape in f times the
+    volume (small cases for profiling); the survey shell keeps its shell with
+    f times the points."""
+    from synth import catalogs as C
+    from synth import workloads as W
+    if w.periodic:
+        n = w.extra["n"] if f == 1.0 else int(round(w.extra["n"] * f))
+        L = w.L * f ** (1.0 / 3.0)
+        D = C.mixed_box(n, L, 0.5, 10.0, 5.0, w.seed + seed_offset)
+        return {"D": D, "wD": C.lognormal_weights(n, 0.3, w.seed + 3 + seed_offset), "L": L}
+    return W.make_inputs(w, scale=f)
+
+
+def measured_fp_peaks(P, stream, sampler_gpu):
+    """FP32 and FP64 FMA throughput of this GPU, measured now (pc_fp_peak):
+    the FP32 peak is the faster of the scalar and packed FFMA loops, each
+    the best of two runs; clocks sampled meanwhile."""
+    smp = ClockSampler(sampler_gpu)
+    smp.start()
+    runs = {k: [P.pc_fp_peak(k, stream=stream) for _ in range(2)] for k in ("ffma", "ffma2", "dfma")}
+    clk = smp.stop()
+    best = {k: max(v, key=lambda t: t[0]) for k, v in runs.items()}
+    fp32 = max(best["ffma"][0], best["ffma2"][0])
+    return {"fp32_tflops": fp32, "fp64_tflops": best["dfma"][0],
+            "ffma_tflops": best["ffma"][0], "ffma2_tflops": best["ffma2"][0],
+            "how": "pc_fp_peak: 8 independent FMA chains per thread, every SM filled to its "
+                   "thread limit, CUDA-event timed after one untimed launch (best of 2); "
+                   "FP32 = faster of FFMA and packed FFMA2",
+            "profile": "profiles/fp_peaks_gb300.md", "clocks": clk}
+
+
+def run_sets(args, extra=None):
+    """Workloads with weights and several pair kinds (the 100M-point weighted
+    cube, the default line; the survey shell's DD, DR and RR): every step
+    builds every catalogue's grid and runs every count, weighted sums in
+    binary64."""
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2301_12557_gb300 as P
     from synth import workloads as W
 
     P.lib()
     w = W.WORKLOADS[args.workload]
-    inp = W.make_inputs(w, scale=args.volume_scale)
+    # replicas: every rank counts its own independent catalogue (periodic
+    # cube: its own seed); block shards: every rank the same catalogue
+    seed_off = 7919 * rank if (world > 1 and not args.shard) else 0
+    inp = sets_inputs(w, args.volume_scale, seed_off)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     names = ["D"] + (["R"] if "R" in inp else [])
-    host = {k: (inp[k], inp.get("w" + k)) for k in names}
+    host = {k: (inp[k], None if args.no_weights else inp.get("w" + k)) for k in names}
+    weighted = any(wt is not None for _, wt in host.values())
     devc = {k: (torch.from_numpy(x).to(dev), torch.from_numpy(wt).to(dev) if wt is not None else None)
             for k, (x, wt) in host.items()}
     bins = P.Bins(w.mode, w.los, w.edges_a, w.edges_b)
+    L_box = inp["L"]
     if w.periodic:
-        box = P.make_box(w.L, True)
+        box = P.make_box(L_box, True)
     else:
         lo = np.full(3, np.inf)
         hi = np.full(3, -np.inf)
@@ -779,6 +853,8 @@ def run_sets(args):
     tuning = None
     tree = args.structure == "kdtree"
     list_cap = args.list_cap
+    if tree and args.shard:
+        raise SystemExit("--shard is a grid-path option")
     if tree and (args.list_cap > 0 or args.ipt > 0):
         opts = P.make_opts("f32", 0.0, args.ipt or 2)
     elif tree:
@@ -788,65 +864,102 @@ def run_sets(args):
         tuning = {"seconds": time.perf_counter() - t0, "on": big,
                   "trials": [{"list_cap": c, "ipt": i, "ms": round(ms, 3)} for c, i, ms in trials]}
     elif args.cell_size > 0 or args.ipt > 0:
-        opts = P.make_opts("f32", args.cell_size, args.ipt)
+        opts = P.make_opts("f32", args.cell_size, args.ipt, rescue_capacity=args.rescue_capacity)
     else:
         t0 = time.perf_counter()
         opts, trials = P.pc_tune(devc[big][0], devc[big][1], box=box, bins=bins, stream=stream)
         tuning = {"seconds": time.perf_counter() - t0, "on": big,
                   "trials": [{"cell_size": round(c, 3), "ipt": i, "priv": pv, "ms": round(ms, 3)}
                              for c, i, pv, ms in trials]}
+    if args.shard and world > 1:
+        from paper_2301_12557_gb300 import shard
+        shard.shard_opts(opts, rank, world)
     kinds = list(w.pair_kinds)
     outs = {k: (torch.zeros(bins.nbins, dtype=torch.int64, device=dev),
                 torch.zeros(bins.nbins, dtype=torch.float64, device=dev)) for k in kinds}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tree_ms = []
 
-    def step(cats=devc, results=outs):
-        if tree:
+    def step(cats=devc, results=outs, o=opts, structure=args.structure):
+        t_b = None
+        if structure == "kdtree":
+            a_ev = torch.cuda.Event(enable_timing=True)
+            b_ev = torch.cuda.Event(enable_timing=True)
+            a_ev.record(stream)
             gs = {k: P.pc_build_tree(x, wt, box=box, n_leaf=args.n_leaf, list_cap=list_cap,
                                      stream=stream)
                   for k, (x, wt) in cats.items()}
+            b_ev.record(stream)
+            t_b = (a_ev, b_ev)
         else:
-            gs = {k: P.pc_build_grid(x, wt, box=box, r_max=bins.r_max, opts=opts, stream=stream)
+            gs = {k: P.pc_build_grid(x, wt, box=box, r_max=bins.r_max, opts=o, stream=stream)
                   for k, (x, wt) in cats.items()}
         stats = {}
         try:
             for kind in kinds:
                 a, b = gs[kind[0]], gs[kind[1]]
                 c, wc = results[kind]
-                if tree:
-                    _, _, st = P.pc_count_tree(a, None if kind[0] == kind[1] else b, bins, opts,
+                if not weighted:
+                    wc = None
+                if structure == "kdtree":
+                    _, _, st = P.pc_count_tree(a, None if kind[0] == kind[1] else b, bins, o,
                                                stream, counts=c, wcounts=wc)
                 elif kind[0] == kind[1]:
-                    _, _, st = P.pc_count_auto(a, bins, opts, stream, counts=c, wcounts=wc)
+                    _, _, st = P.pc_count_auto(a, bins, o, stream, counts=c, wcounts=wc)
                 else:
-                    _, _, st = P.pc_count_cross(a, b, bins, opts, stream, counts=c, wcounts=wc)
+                    _, _, st = P.pc_count_cross(a, b, bins, o, stream, counts=c, wcounts=wc)
                 stats[kind] = st
         finally:
             for g in gs.values():
                 g.free()
+        if t_b is not None:
+            tree_ms.append(t_b[0].elapsed_time(t_b[1]))
         return stats
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
 
     for _ in range(args.warmup):
         step()
-    torch.cuda.synchronize()
+    barrier()
     sampler = ClockSampler(local)
     sampler.start()
     l0 = P.pc_launch_count()
-    ms, stats = [], None
-    for _ in range(args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        stats = step()
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    all_stats = []
+    for k in range(args.steps):
+        flush.zero_()                        # evict L2 between timed steps
+        ev[k][0].record(stream)
+        all_stats.append(step())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
     launches = P.pc_launch_count() - l0
     clocks = sampler.stop()
-    t_step = statistics.mean(ms)
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stats = all_stats[-1]
     inr = {k: int(outs[k][0].sum().item()) for k in kinds}
-    value = sum(inr.values()) / (t_step * 1e-3)
+    t_local = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+    work_local = torch.tensor([float(sum(inr.values())) * args.steps,
+                               float(sum(st.candidates for s in all_stats for st in s.values()))],
+                              dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.all_reduce(work_local, op=dist.ReduceOp.SUM)
+    t_max = float(t_local.item())
+    inr_all, cand_all = (float(v) for v in work_local.tolist())
+    value = inr_all / (t_max * 1e-3)
+    t_step = t_max / args.steps
+    counts_local = {k: outs[k][0].cpu().numpy().copy() for k in kinds}
+    if args.shard and dist is not None:
+        from paper_2301_12557_gb300 import shard
+        for k in kinds:
+            outs[k] = (shard.sum_histograms(outs[k][0]), shard.sum_histograms(outs[k][1]))
 
+    # ---- e2e: host buffers through the same ABI, copies inside the region --
     e2e = None
     if args.e2e_steps > 0:
         pinned = {k: (torch.from_numpy(x).pin_memory(),
@@ -864,45 +977,168 @@ def run_sets(args):
             torch.cuda.synchronize()
             e_ms.append(a.elapsed_time(b))
         for k in kinds:
-            assert np.array_equal(hout[k][0], outs[k][0].cpu().numpy()), k
+            assert np.array_equal(hout[k][0], counts_local[k]), k
         h2d = sum(x.nbytes + (wt.nbytes if wt is not None else 0) for x, wt in host.values())
-        e2e = {"value": sum(inr.values()) / (statistics.mean(e_ms) * 1e-3), "unit": UNIT,
+        e2e_t = max_over_ranks(statistics.mean(e_ms), dist, dev)
+        e2e = {"value": inr_all / args.steps / (e2e_t * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(len(kinds) * bins.nbins * 16),
-               "ms_per_step": statistics.mean(e_ms)}
+               "ms_per_step": e2e_t}
+
+    peaks = measured_fp_peaks(P, stream, local)
+
+    # ---- plain FP64 path on the same GB300, on a block shard ----------------
+    fp64 = None
+    if args.fp64_steps > 0 and not tree and world == 1:
+        n_big = host[big][0].shape[0]
+        S = args.fp64_shards if args.fp64_shards > 0 else (64 if n_big >= 50_000_000 else 1)
+        vol = float(np.prod(np.asarray(box.hi) - np.asarray(box.lo))) if not w.periodic \
+            else float(L_box) ** 3
+        cell64 = P.pc_suggest_cell_size(n_big, vol, bins.r_max)
+        o64 = P.make_opts("f64", cell64, 1, shard_index=0, shard_count=S)
+        # the FP32 + rescue path on the same blocks (same cell side, same shard)
+        o32 = P.make_opts("f32", cell64, opts.ipt, rescue_capacity=opts.rescue_capacity,
+                          shard_index=0, shard_count=S)
+        r64 = {k: (torch.zeros_like(outs[k][0]), torch.zeros_like(outs[k][1])) for k in kinds}
+        r32 = {k: (torch.zeros_like(outs[k][0]), torch.zeros_like(outs[k][1])) for k in kinds}
+        step(results=r32, o=o32, structure="grid")
+        s64 = step(results=r64, o=o64, structure="grid")     # warm-up (module load)
+        torch.cuda.synchronize()
+        ms64 = []
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s64 = step(results=r64, o=o64, structure="grid")
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms64.append(a.elapsed_time(b))
+        exact = all(bool(torch.equal(r64[k][0], r32[k][0])) for k in kinds)
+        wdiff = 0.0
+        if weighted:
+            for k in kinds:
+                ref = r64[k][1].abs().clamp_min(1e-300)
+                wdiff = max(wdiff, float(((r64[k][1] - r32[k][1]).abs() / ref).max().item()))
+        inr64 = float(sum(r64[k][0].sum().item() for k in kinds))
+        cand64 = float(sum(s64[k].candidates for k in kinds))
+        k64_ms = sum(s64[k].ms_pairs for k in kinds)
+        fl64 = FLOPS_PER_CANDIDATE * cand64 + FLOPS_PER_IN_RANGE * inr64
+        ach64 = fl64 / (k64_ms * 1e-3) / 1e12
+        fp64 = {"value": inr64 / (statistics.mean(ms64) * 1e-3), "unit": UNIT,
+                "cell_size": cell64, "steps": args.fp64_steps,
+                "blocks": (f"1/{S} of the i-blocks (shard 0 of {S}); the rate is measured on "
+                           "them, the full-step time is extrapolated" if S > 1 else "all"),
+                "ms_per_step": statistics.mean(ms64),
+                "ms_per_full_step_extrapolated": statistics.mean(ms64) * S,
+                "in_range_pairs": int(inr64),
+                "counts_identical_to_fp32_rescue": exact,
+                "weighted_max_rel_diff_vs_fp32_rescue": wdiff if weighted else None,
+                "roofline": {"bound": "fp64", "achieved": ach64, "peak": peaks["fp64_tflops"],
+                             "unit": "TFLOP/s", "frac": ach64 / peaks["fp64_tflops"],
+                             "peak_source": "measured: DFMA loop (pc_fp_peak), "
+                                            + peaks["profile"],
+                             "kernel_ms": k64_ms,
+                             "flops_definition": f"{FLOPS_PER_CANDIDATE} per candidate pair "
+                                                 f"({cand64:.4g}) + {FLOPS_PER_IN_RANGE} per "
+                                                 f"in-range pair ({inr64:.4g})"}}
+
+    # ---- roofline of the dominant kernel -------------------------------------
+    kdom = max(kinds, key=lambda k: stats[k].ms_pairs)
+    sd = stats[kdom]
+    ms_pairs = statistics.mean(s[kdom].ms_pairs for s in all_stats)
+    inr_d = float(inr[kdom])
+    flops = FLOPS_PER_CANDIDATE * float(sd.candidates)
+    achieved = flops / (ms_pairs * 1e-3) / 1e12
+    evaluated = float(sd.candidates - sd.pruned)
+    flops_ev = FLOPS_PER_CANDIDATE * evaluated + FLOPS_PER_IN_RANGE * inr_d
+    ach_ev = flops_ev / (ms_pairs * 1e-3) / 1e12
+    fp32_peak = peaks["fp32_tflops"]
+    trec = traffic_record(w.name, tree, opts.rescue_capacity < 0)
+    kname = {"s": "S", "smu": "SMU", "sigpi": "SIGPI"}[w.mode]
+    wkind = {0: "", 1: ", binary64 weight products", 2: ", integer weight products"}.get(sd.wsum, "")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
+                "traffic": trec["bytes_per_launch"] if trec else None,
+                "traffic_source": trec.get("source") if trec else None,
+                "kernel": f"k_pairs_f32<{kname},LOS_{w.los.upper()}>" + wkind +
+                          (" (tree variant)" if tree else ""),
+                "pair_kind": kdom,
+                "flops_per_launch": flops,
+                "flops_definition": (f"{FLOPS_PER_CANDIDATE} FP32 flops per candidate pair of the "
+                                     f"cell stencil ({float(sd.candidates):.4g} per launch)"),
+                "achieved_evaluated": ach_ev, "frac_evaluated": ach_ev / fp32_peak,
+                "evaluated_definition": (f"{FLOPS_PER_CANDIDATE} per pair evaluated one by one "
+                                         f"({evaluated:.4g}) + {FLOPS_PER_IN_RANGE} per in-range "
+                                         f"pair ({inr_d:.4g}); the weight product is integer work"),
+                "peak_source": "measured: " + peaks["how"] + " (" + peaks["profile"] + ")",
+                "kernel_ms": ms_pairs,
+                "kernel_share_of_step": ms_pairs / t_step}
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         x, wt = host[big]
-        r, dt, m, cores, evals = oracle_sample_rate(x, w, args.cpu_seconds, L=w.L)
+        r, dt, m, cores, evals = oracle_sample_rate(x, w, args.cpu_seconds, L=L_box, wt=wt)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{m} random {big} points x all {x.shape[0]} {big} points (brute force, "
-                         f"binary64, unweighted), {dt:.1f} s; in-range pairs found per second",
-               "pair_evaluations_per_s": evals}
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name if args.volume_scale == 1.0 else
-                   f"{w.name} at N x{args.volume_scale}",
-                   "catalogues": {k: int(host[k][0].shape[0]) for k in names},
-                   "pair_kinds": kinds, "weighted": bool(w.weighted),
-                   "precision": "FP32 separations, binary64 rescue near bin edges, int64 counts, "
-                                "binary64 weighted sums",
-                   "unit_of_work": "in-range pairs binned over all pair kinds",
-                   "structure": ("k-d tree (leaf capacity %d, list nodes %s), dual-tree traversal"
-                                 % (args.n_leaf, list_cap or "auto")) if tree else "regular grid",
-                   "cell_size": opts.cell_size, "ipt": opts.ipt, "priv": opts.priv,
-                   "tuning": tuning, "l2": "flushed between timed steps (256 MiB write)"},
-        "per_kind": {k: {"in_range_pairs": inr[k], "ms_pairs": stats[k].ms_pairs,
-                         "ms_total": stats[k].ms_total, "candidates": stats[k].candidates,
-                         "pruned": stats[k].pruned, "rescued": stats[k].rescued,
-                         "node_pairs": stats[k].tree_pairs if tree else None,
-                         "ms_traverse": stats[k].ms_traverse if tree else None,
-                         "prec": "f32+rescue" if stats[k].prec == 0 else "f64"} for k in kinds},
-        "roofline": None,
-        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
-    }
-    print(json.dumps(line), flush=True)
+                         f"binary64{', weighted' if wt is not None else ''}), {dt:.1f} s; "
+                         f"in-range pairs found per second",
+               "pair_evaluations_per_s": evals, "cpu_model": cpu_model()}
+    if rank == 0:
+        s0 = stats[kinds[0]]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+            "ms_per_step_trimmed": (statistics.mean(sorted(step_ms)[1:-1])
+                                    if len(step_ms) >= 3 else None),
+            "scaling": "strong" if (args.shard and world > 1) else "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if weighted else "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name if args.volume_scale == 1.0 else
+                       f"{w.name} at volume x{args.volume_scale}",
+                       "catalogues": {k: int(host[k][0].shape[0]) for k in names},
+                       "box": L_box if w.periodic else "survey shell bounds",
+                       "bins": ("s 40 x 5 Mpc/h on [0, 200)" if w.mode == "s" else
+                                "sigma 40 x pi 40 on [0, 200)^2 (midpoint LOS)"),
+                       "pair_kinds": kinds, "weighted": weighted,
+                       "precision": "FP32 separations, binary64 rescue near bin edges, int64 "
+                                    "counts" + (", weighted sums in binary64 (per-pair products "
+                                                "exact to 2^-34 or binary64)" if weighted else ""),
+                       "parallelism": (f"block shards x{world} + one histogram sum"
+                                       if args.shard else f"replicas x{world}")
+                                      if world > 1 else "1 GPU",
+                       "unit_of_work": "in-range pairs binned over all pair kinds",
+                       "structure": ("k-d tree (leaf capacity %d, list nodes %s), dual-tree traversal"
+                                     % (args.n_leaf, list_cap or "auto")) if tree else "regular grid",
+                       "cell_size": s0.cell_size, "ipt": opts.ipt, "priv": opts.priv,
+                       "rescue": ("inline in the pair kernel" if opts.rescue_capacity < 0 else
+                                  "queued for the rescue kernel"),
+                       "weight_sums": {0: "none", 1: "binary64 products",
+                                       2: "exact integer products of binary32 significands"}.get(
+                                           s0.wsum, str(s0.wsum)),
+                       "tuning": tuning, "l2": "flushed between timed steps (256 MiB write)",
+                       "in_range_pairs": int(sum(inr.values())),
+                       "candidates_per_step": int(sum(st.candidates for st in stats.values())),
+                       "pruned_per_step": int(sum(st.pruned for st in stats.values())),
+                       "tree_build_ms": statistics.mean(tree_ms[-args.steps:]) if tree_ms else None},
+            "candidate_pairs_per_s": cand_all / (t_max * 1e-3),
+            "rescued_fraction": sum(st.rescued for st in stats.values()) / max(1, sum(inr.values())),
+            "per_kind": {k: {"in_range_pairs": inr[k], "ms_pairs": stats[k].ms_pairs,
+                             "ms_total": stats[k].ms_total, "candidates": stats[k].candidates,
+                             "pruned": stats[k].pruned, "rescued": stats[k].rescued,
+                             "node_pairs": stats[k].tree_pairs if tree else None,
+                             "ms_traverse": stats[k].ms_traverse if tree else None,
+                             "prec": "f32+rescue" if stats[k].prec == 0 else "f64"} for k in kinds},
+            "fp64_path": fp64,
+            "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+            "roofline": roofline,
+            "measured_peaks": {k: v for k, v in peaks.items() if k != "how"},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+        }
+        if extra:
+            line.update(extra())
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
@@ -972,7 +1208,24 @@ def main():
     from synth import workloads as W
     w = W.WORKLOADS[args.workload]
     if w.weighted or len(w.pair_kinds) > 1:
-        return run_sets(args)
+        extra = None
+        _, world, _ = dist_env()
+        if (args.workload == DEFAULT_WORKLOAD and args.config2_steps > 0 and world == 1
+                and args.volume_scale == 1.0 and args.structure == "grid"):
+            def extra():
+                # the 2M-point clustered (s, mu) benchmark, same GPU, same run
+                a2 = argparse.Namespace(**vars(args))
+                a2.workload = "ns_periodic_n2m_smu40x100"
+                a2.steps, a2.warmup = args.config2_steps, 3
+                a2.e2e_steps, a2.fp64_steps, a2.tree_steps = 1, 1, 1
+                a2.cell_size, a2.ipt, a2.rescue_capacity = 0.0, 0, 0
+                a2.no_cpu_baseline = True
+                ln = run_ours(a2, emit=False)
+                keep = ("value", "unit", "steps", "warmup", "ms_per_step", "config",
+                        "candidate_pairs_per_s", "rescued_fraction", "fp64_path", "kdtree_path",
+                        "speedup_vs_fp64", "roofline", "e2e", "clocks", "gpu_launches")
+                return {a2.workload: {k: ln[k] for k in keep}}
+        return run_sets(args, extra)
     return run_ours(args)
 
 

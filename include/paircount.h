@@ -36,6 +36,11 @@
  *   weighted: sum of w_i * w_j per bin
  * Unweighted counts are bit-exact with that definition.  Weighted sums are
  * accumulated in binary64 (order-dependent rounding only).
+ *
+ * Per-device state: the library keeps count workspaces, captured graphs and
+ * the allocation-free entry point's array address per device for the life of
+ * the process; none of it survives a cudaDeviceReset, after which the library
+ * must not be called on that device.
  */
 #ifndef PAIRCOUNT_H
 #define PAIRCOUNT_H
@@ -99,9 +104,11 @@ typedef struct {
     long long rescue_capacity;   /* rescue-queue slots; 0 = auto; < 0 = none (all inline) */
     int use_graph;               /* pc_count_batch: replay a captured CUDA graph */
     int grid_ctas_per_sm;        /* persistent CTAs per SM; 0 = occupancy limit */
-    int shard_index;             /* with shard_count > 1: count only the i-blocks whose */
-    int shard_count;             /* index % shard_count == shard_index (multi-GPU shards;
-                                    the int64 counts of all shards sum to the full count) */
+    int shard_index;             /* with shard_count > 1: count only the i-points of the */
+    int shard_count;             /* cells (tree: list nodes) whose index % shard_count ==
+                                    shard_index (multi-GPU shards; the int64 counts of all
+                                    shards sum to the full count, and a shard is the same set
+                                    of pairs whatever the precision or i-points per thread) */
 } pc_opts;
 
 /* Counters of the last count call (all optional). */
@@ -169,8 +176,15 @@ pc_status pc_grid_info(const pc_grid *g, long long *n, double *cell_size);
 pc_status pc_count_auto(const pc_grid *g, const pc_bins *b, const pc_opts *o, void *stream,
                         long long *counts, double *wcounts, pc_stats *st);
 
-/* Cross pair counts: all (i in g1, j in g2).  g1 and g2 must share box,
- * bounds and cell size. */
+/* Cross pair counts: all (i in g1, j in g2) -- the data-random (DR) counts
+ * of the estimators in Sect. 1, and any pair count of two catalogues (App. D:
+ * the PAIR_COUNT sources, e.g. LR from catalogues L and R; DD, RR are auto
+ * counts).  g1 and g2 must share box, bounds and cell size.
+ *   counts    int64 [nbins], host or device; overwritten
+ *   wcounts   binary64 [nbins] or NULL: sums of w_i w_j (both grids weighted)
+ *   st        optional counters
+ * Errors: PC_EINVAL (different boxes, bounds or cell sizes; bad bins),
+ * PC_ENOMEM, PC_ECUDA.  Returns after the results are written. */
 pc_status pc_count_cross(const pc_grid *g1, const pc_grid *g2, const pc_bins *b,
                          const pc_opts *o, void *stream, long long *counts, double *wcounts,
                          pc_stats *st);
@@ -194,7 +208,10 @@ pc_status pc_count_batch(const pc_grid *const *gs, int m, const pc_bins *b, cons
  * All temporaries live in one fixed device array of about 12.3 MiB inside the
  * library, which every GPU that loads the library holds until the process
  * exits.  Its device address is looked up on the first call on each device,
- * so make that first call before any stream capture.  Limits (PC_EOVERFLOW
+ * so make that first call before any stream capture.  Like the library's
+ * other per-device state (count workspaces, captured graphs), that address
+ * does not survive a cudaDeviceReset of the device: do not call the library
+ * on a device after resetting it.  Limits (PC_EOVERFLOW
  * beyond them): 16384 bins, 262144 grid cells, 524288 point blocks, 8192
  * stencil rows.  The array keeps the last call's contents and is cleared
  * where needed at the start of every call; calls are serialised by the
@@ -360,6 +377,20 @@ pc_status pc_tune_tree(const double *xyz, const void *w, int w_is_f32, long long
 pc_status pc_hist_s2(const float *s2, long long n, int repeat, const double *edges, int nbins,
                      int method, int table_size, void *stream, long long *counts, float *ms);
 
+/* Measured arithmetic peak of the current device, for roofline fractions.
+ * The paper has no counterpart (it benchmarks CPUs); this is measurement
+ * infrastructure for the pair kernels' FP32 and FP64 pipes.
+ *   kind      0: binary32 FFMA loop; 1: packed binary32 FFMA2 loop (two lanes
+ *             per instruction); 2: binary64 DFMA loop
+ *   iters     multiply-add steps per chain (0 = a default of ~50-150 ms)
+ *   tflops    receives the rate, 10^12 flops per second (an FMA counts 2)
+ *   ms        optional: the timed launch's duration
+ * Every thread runs 8 independent FMA chains on a grid that fills every SM
+ * to its thread limit; the launch is timed with CUDA events on `stream`
+ * after one short untimed launch.  Allocates nothing; synchronises the
+ * stream.  Errors: PC_EINVAL (bad kind or iters), PC_ECUDA. */
+pc_status pc_fp_peak(int kind, long long iters, void *stream, double *tflops, float *ms);
+
 /* Bounding box of n points (n x 3 binary64, host or device) -- the first of
  * the three grid-build passes of Sect. 2.1.  lo/hi are host arrays of 3. */
 pc_status pc_aabb(const double *xyz, long long n, void *stream, double *lo, double *hi);
@@ -436,6 +467,12 @@ double pc_suggest_cell_size(long long n, double volume, double r_max, int mode);
 /* Number of kernels this library has launched since it was loaded (all
  * entry points, all threads).  Lets callers count device work per step. */
 long long pc_launch_count(void);
+
+/* Number of device (and pinned host) allocations this library has made since
+ * it was loaded (all entry points, all threads): grids, trees, count
+ * workspaces and temporaries.  Lets callers check that a call allocated
+ * nothing (pc_count_auto_noalloc). */
+long long pc_alloc_count(void);
 
 /* Static description of a status code. */
 const char *pc_strerror(pc_status s);

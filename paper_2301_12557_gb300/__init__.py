@@ -76,7 +76,7 @@ EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc
            "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune",
            "pc_build_tree", "pc_free_tree", "pc_tree_info", "pc_tree_export", "pc_count_tree",
            "pc_tune_tree", "pc_hist_s2", "pc_count_tree_batch", "pc_stencil", "pc_fp32_bands",
-           "pc_fp32_tables"]
+           "pc_fp32_tables", "pc_fp_peak", "pc_alloc_count"]
 
 
 def library_path() -> str:
@@ -128,6 +128,8 @@ def lib():
     L.pc_version.argtypes = []
     L.pc_launch_count.restype = c_longlong
     L.pc_launch_count.argtypes = []
+    L.pc_alloc_count.restype = c_longlong
+    L.pc_alloc_count.argtypes = []
     L.pc_tune.restype = c_int
     L.pc_tune.argtypes = [vp, vp, c_int, c_longlong, POINTER(pc_box), POINTER(pc_bins),
                           POINTER(pc_opts), vp, POINTER(pc_opts), POINTER(pc_tune_trial), c_int,
@@ -148,6 +150,8 @@ def lib():
     L.pc_tune_tree.argtypes = [vp, vp, c_int, c_longlong, POINTER(pc_box), POINTER(pc_bins), c_int,
                                POINTER(pc_opts), vp, POINTER(pc_opts), POINTER(c_int),
                                POINTER(pc_tune_trial), c_int, POINTER(c_int)]
+    L.pc_fp_peak.restype = c_int
+    L.pc_fp_peak.argtypes = [c_int, c_longlong, vp, POINTER(c_double), POINTER(c_float)]
     L.pc_hist_s2.restype = c_int
     L.pc_hist_s2.argtypes = [vp, c_longlong, c_int, POINTER(c_double), c_int, c_int, c_int, vp, vp,
                              POINTER(c_float)]
@@ -182,6 +186,11 @@ def pc_last_error() -> str:
 
 def pc_version() -> str:
     return lib().pc_version().decode()
+
+
+def pc_alloc_count() -> int:
+    """Device (and pinned host) allocations the library has made so far."""
+    return int(lib().pc_alloc_count())
 
 
 def pc_launch_count() -> int:
@@ -528,6 +537,20 @@ def pc_hist_s2(s2, edges, method="lut", table_size=0, repeat=1, stream=None, cou
            "pc_hist_s2")
     del keep, kc
     return counts, ms.value
+
+
+PEAK_KINDS = {"ffma": 0, "ffma2": 1, "dfma": 2}
+
+
+def pc_fp_peak(kind="ffma", iters=0, stream=None):
+    """Measured FMA throughput of the current device (see paircount.h).
+    Returns (TFLOP/s, ms of the timed launch)."""
+    tf = c_double(0.0)
+    ms = c_float(0.0)
+    k = PEAK_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().pc_fp_peak(k, int(iters), _stream_handle(stream), ctypes.byref(tf),
+                            ctypes.byref(ms)), "pc_fp_peak")
+    return tf.value, ms.value
 
 
 def pc_free_tree(t: Tree):

@@ -40,6 +40,10 @@ static std::atomic<long long> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n); }
 long long launch_count() { return g_launches.load(); }
 
+static std::atomic<long long> g_allocs{0};
+void note_alloc() { g_allocs.fetch_add(1); }
+long long alloc_count() { return g_allocs.load(); }
+
 std::mutex &api_mutex() {
     static std::mutex m;
     return m;
@@ -68,11 +72,11 @@ struct Buf {
         p = nullptr;
         cap = 0;
         size_t want = std::max(bytes, cap * 3 / 2);
-        cudaError_t e = cudaMalloc(&p, want);
+        cudaError_t e = ::pc::alloc_dev(&p, want);
         if (e != cudaSuccess) {
             cudaGetLastError();
             want = bytes;
-            e = cudaMalloc(&p, want);
+            e = ::pc::alloc_dev(&p, want);
         }
         if (e == cudaSuccess) cap = want;
         return e;
@@ -497,6 +501,8 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
 // 2 = a single shared copy, otherwise automatic: lane copies (lane l updates
 // copy l % k) as many as fit a 16 KB budget, so the lanes of a warp do not
 // collide on the few bins of a small histogram.
+// (weighted: binary64 weight sums share the copies and the budget; the
+// integer weight planes have their own WINT_COPIES copies.)
 static void choose_replication(int mode, int nbins, bool weighted, int &priv, int &hist_k) {
     priv = 0;
     hist_k = 1;
@@ -504,6 +510,19 @@ static void choose_replication(int mode, int nbins, bool weighted, int &priv, in
     if (mode == 2) return;
     const long long per_copy = (long long)nbins * (4 + (weighted ? 8 : 0));
     while (hist_k < 32 && per_copy * hist_k * 2 <= 16384) hist_k *= 2;
+}
+
+// Lane copies of each integer weight plane (lanes l and l + 16 share one;
+// their i-points are the farthest apart of the warp's).
+constexpr int WINT_COPIES = 16;
+
+// Rows of each shared histogram copy: the bins, the discarded rows of the
+// floor bins without a range test, and at least one row past the bins that
+// lanes without an in-range pair update (row nbins).
+static void set_hist_rows(PairParams &p, const Plan &P) {
+    p.nbins_smem = P.nbins + (p.lin_norange ? (P.mode == PC_BIN_S ? 1 : P.nb) : 0);
+    p.trash_row = P.nbins;
+    p.nbins_smem = std::max(p.nbins_smem, P.nbins + 1);
 }
 
 // Shared-memory fallback: fewer lane copies, then no warp copies, then the
@@ -730,14 +749,13 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     p.counters = B.ctr;
     p.shard_count = S.o.shard_count > 1 ? S.o.shard_count : 1;
     p.shard_index = S.o.shard_count > 1 ? S.o.shard_index : 0;
-    choose_replication(S.o.priv, P.nbins, S.weighted, p.priv, p.hist_k);
     p.lin = (S.prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
     p.lin_norange = p.lin ? P.lin_norange : 0;
     p.lin_log = p.lin ? P.lin_log : 0;
     p.lin_mS = P.lin_mS;
     p.lin_invB2 = P.lin_invB2;
     p.lin_thrB = P.lin_thrB;
-    p.nbins_smem = P.nbins + (p.lin_norange ? (P.mode == PC_BIN_S ? 1 : P.nb) : 0);
+    set_hist_rows(p, P);
     p.lin_invA = P.lin_invA;
     // the range-tested floor bins take t_s + 1 (exact floors down to t_s = -1)
     p.lin_offA = P.lin_norange ? P.lin_offA : P.lin_offA1;
@@ -751,23 +769,32 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     PC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S.dev));
     const int static_smem = 256;
     const int lut_size = p.lut_total;
-    for (;;) {
-        p.smem_hist_ok = 1;
-        // the floor-based bins need no tables (they serve only the global-
-        // histogram variant)
-        p.lut_total = p.lin ? 0 : lut_size;
-        size_t need = (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
-        if (need + static_smem <= (size_t)smem_optin) break;
-        if (shrink_replication(p)) continue;
-        p.smem_hist_ok = 0;
-        p.lut_total = lut_size;
-        break;
-    }
-    smem = (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
-    // integer weight products need floor bins, shared histograms and enough
-    // lane copies that a u64 copy is flushed no more often than every 8 tiles
-    p.wint = (S.weighted && p.lin && p.smem_hist_ok && !p.priv && p.hist_k >= 16 && J.wint_ok &&
-              S.prec == PC_PREC_F32_RESCUE) ? 1 : 0;
+    // shared-memory layout for a weight path: replication, then fewer copies
+    // until it fits, else the global histogram
+    auto fit = [&](bool wint) {
+        p.wint = wint ? 1 : 0;
+        choose_replication(S.o.priv, P.nbins, S.weighted && !wint, p.priv, p.hist_k);
+        p.wint_k = WINT_COPIES;
+        for (;;) {
+            p.smem_hist_ok = 1;
+            // the floor-based bins need no tables (they serve only the global-
+            // histogram variant)
+            p.lut_total = p.lin ? 0 : lut_size;
+            size_t need = (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
+            if (need + static_smem <= (size_t)smem_optin) break;
+            if (shrink_replication(p)) continue;
+            p.smem_hist_ok = 0;
+            p.lut_total = lut_size;
+            break;
+        }
+        return (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
+    };
+    // integer weight products need floor bins, every weight packable, shared
+    // histograms with one count copy per CTA and at least 16 lane copies (so
+    // a plane copy is flushed no more often than every 8 tiles)
+    const bool wint_try = S.weighted && p.lin && J.wint_ok && S.prec == PC_PREC_F32_RESCUE;
+    smem = fit(wint_try);
+    if (p.wint && !(p.smem_hist_ok && !p.priv && p.hist_k >= 16)) smem = fit(false);
     if (smem + static_smem > (size_t)smem_optin)
         return fail(PC_EUNSUPPORTED, "bins: tables do not fit in shared memory");
     int per_sm = (S.prec == PC_PREC_F64) ? pairs_f64_ctas_per_sm(p, smem)
@@ -807,7 +834,8 @@ static pc_status enqueue_count(const CountSetup &S, const DevBufs &B, const Pair
     if (tree_blocks_fn)   // tree counts: balanced blocks of the list nodes
         PC_CUDA(tree_blocks_fn());
     else
-        PC_CUDA(make_blocks_into(B.tasks, S.ntasks, S.ncell, S.bi, B.blocks, B.sc + 1, B.cnt,
+        PC_CUDA(make_blocks_into(B.tasks, S.ntasks, S.ncell, S.bi, p.shard_index, p.shard_count,
+                                 B.blocks, B.sc + 1, B.cnt,
                                  B.off, B.tot, st));
     if (ev_pairs) PC_CUDA(cudaEventRecord(ev_pairs, st));
     cudaError_t e = (S.prec == PC_PREC_F64) ? launch_pairs_f64(p, grid, smem, st)
@@ -997,10 +1025,10 @@ static pc_status run_count_graph(const CountJob &J, const std::vector<const pc_g
         if (s != PC_OK) return s;
         N->S.wsum = p.wint ? 2 : (N->S.weighted ? 1 : 0);
         const size_t hb = N->S.hist_n;
-        PC_CUDA(cudaMallocHost(&N->h_hist, sizeof(unsigned long long) * hb));
-        if (weighted) PC_CUDA(cudaMallocHost(&N->h_whist, sizeof(double) * hb));
-        PC_CUDA(cudaMallocHost(&N->h_ctr, sizeof(unsigned long long) * 4));
-        PC_CUDA(cudaMallocHost(&N->h_blocks, sizeof(int)));
+        PC_CUDA(::pc::alloc_host(&N->h_hist, sizeof(unsigned long long) * hb));
+        if (weighted) PC_CUDA(::pc::alloc_host(&N->h_whist, sizeof(double) * hb));
+        PC_CUDA(::pc::alloc_host(&N->h_ctr, sizeof(unsigned long long) * 4));
+        PC_CUDA(::pc::alloc_host(&N->h_blocks, sizeof(int)));
         cudaStream_t cap = nullptr;
         PC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         s = upload_tables(J, N->S, N->B, cap);
@@ -1260,7 +1288,10 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
     s = upload_tables(J, S, B, st);
     if (s != PC_OK) return s;
     s = enqueue_count(S, B, p, grid, smem, st, ev.e[1], ev.e[2], ev.e[3],
-                      [&]() { return tree_blocks(t1, S.ipt, B.blocks, B.sc + 1, st); });
+                      [&]() {
+                          return tree_blocks(t1, S.ipt, p.shard_index, p.shard_count, B.blocks,
+                                             B.sc + 1, st);
+                      });
     if (s != PC_OK) return s;
     cudaError_t e = cudaSuccess;
     copy_out(counts, B.hist, sizeof(long long) * S.hist_n, st, e);
@@ -1373,7 +1404,8 @@ extern "C" pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const 
     s = upload_tables(J, S, B, st);
     if (s != PC_OK) return s;
     s = enqueue_count(S, B, p, grid, smem, st, ev.e[1], ev.e[2], ev.e[3], [&]() {
-        return tree_blocks_batch(trees, TB, S.ipt, B.blocks, B.sc + 1, st);
+        return tree_blocks_batch(trees, TB, S.ipt, p.shard_index, p.shard_count, B.blocks,
+                                 B.sc + 1, st);
     });
     if (s != PC_OK) return s;
     cudaError_t e = cudaSuccess;
@@ -1584,6 +1616,8 @@ extern "C" const char *pc_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" long long pc_launch_count(void) { return launch_count(); }
 
+extern "C" long long pc_alloc_count(void) { return alloc_count(); }
+
 extern "C" const char *pc_version(void) { return "paircount-gb300 0.1 (sm_103a)"; }
 
 // ---------------------------------------------------------------------------
@@ -1724,7 +1758,8 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
                             cudaMemcpyHostToDevice, st));
     PC_CUDA(cudaMemcpyAsync(base + NA.eb, P.Eb.data(), sizeof(double) * (P.nb + 1),
                             cudaMemcpyHostToDevice, st));
-    PC_CUDA(make_blocks_into(tasks, 1, g->ncell, bi, (Block *)(base + NA.blocks), sc + 1,
+    PC_CUDA(make_blocks_into(tasks, 1, g->ncell, bi, o.shard_count > 1 ? o.shard_index : 0,
+                             o.shard_count > 1 ? o.shard_count : 1, (Block *)(base + NA.blocks), sc + 1,
                              (int *)(base + NA.cnt), (int *)(base + NA.off),
                              (int *)(base + NA.tot), st));
 
@@ -1765,13 +1800,14 @@ extern "C" pc_status pc_count_auto_noalloc(const pc_grid *g, const pc_bins *b, c
     p.shard_count = o.shard_count > 1 ? o.shard_count : 1;
     p.shard_index = o.shard_count > 1 ? o.shard_index : 0;
     choose_replication(o.priv, P.nbins, wcounts != nullptr, p.priv, p.hist_k);
+    p.wint_k = 1;   // binary64 weight sums here (no integer weight planes)
     p.lin = (prec == PC_PREC_F32_RESCUE) ? P.lin : 0;
     p.lin_norange = p.lin ? P.lin_norange : 0;
     p.lin_log = p.lin ? P.lin_log : 0;
     p.lin_mS = P.lin_mS;
     p.lin_invB2 = P.lin_invB2;
     p.lin_thrB = P.lin_thrB;
-    p.nbins_smem = P.nbins + (p.lin_norange ? (P.mode == PC_BIN_S ? 1 : P.nb) : 0);
+    set_hist_rows(p, P);
     p.lin_invA = P.lin_invA;
     // the range-tested floor bins take t_s + 1 (exact floors down to t_s = -1)
     p.lin_offA = P.lin_norange ? P.lin_offA : P.lin_offA1;

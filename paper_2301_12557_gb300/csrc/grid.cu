@@ -75,7 +75,7 @@ pc_status aabb_device(const double *xyz, long long n, cudaStream_t st, double *l
     long long init[7] = {LLONG_MAX, LLONG_MAX, LLONG_MAX, LLONG_MIN, LLONG_MIN, LLONG_MIN,
                          LLONG_MAX};
     long long *d = nullptr;
-    PC_CUDA(cudaMallocAsync(&d, sizeof(init), st));
+    PC_CUDA(::pc::alloc_dev_async(&d, sizeof(init), st));
     PC_CUDA(cudaMemcpyAsync(d, init, sizeof(init), cudaMemcpyHostToDevice, st));
     if (n > 0) {
         int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
@@ -185,7 +185,7 @@ __global__ void k_wstats(const void *__restrict__ w, int w_is_f32, int n, int *o
 pc_status weight_stats(const void *w, int w_is_f32, int n, cudaStream_t st, int r[3]) {
     int init[3] = {0, -1, 1000};
     int *ws = nullptr;
-    cudaError_t e = cudaMallocAsync(&ws, sizeof(init), st);
+    cudaError_t e = ::pc::alloc_dev_async(&ws, sizeof(init), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ws, init, sizeof(init), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && n > 0) {
         int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
@@ -317,7 +317,7 @@ __global__ void k_scan_add(int *out, int n, const int *tot) {
 cudaError_t scan_exclusive(const int *in, int *out, int n, cudaStream_t st) {
     int ntiles = std::max(1, (n + SCAN_TILE - 1) / SCAN_TILE);
     int *tot = nullptr;
-    cudaError_t e = cudaMallocAsync(&tot, sizeof(int) * ntiles, st);
+    cudaError_t e = ::pc::alloc_dev_async(&tot, sizeof(int) * ntiles, st);
     if (e != cudaSuccess) return e;
     if (n > 0) {
         k_scan_tiles<<<ntiles, SCAN_T, 0, st>>>(in, out, n, tot);
@@ -359,13 +359,16 @@ cudaError_t scan_exclusive_into(const int *in, int *out, int n, int *tot, cudaSt
 // ---------------------------------------------------------------------------
 // block list
 // ---------------------------------------------------------------------------
-__global__ void k_block_counts(const TaskDev *tasks, int ntasks, int ncell, int bi, int *cnt) {
+// Blocks per (task, cell): ceil(count / bi), or none for a cell outside the
+// shard (cells whose index % shard_count != shard_index).
+__global__ void k_block_counts(const TaskDev *tasks, int ntasks, int ncell, int bi, int shard_index,
+                               int shard_count, int *cnt) {
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)ntasks * ncell) return;
     int t = (int)(gid / ncell), c = (int)(gid % ncell);
     const int *cs = tasks[t].gi.cell_start;
     int nc = cs[c + 1] - cs[c];
-    cnt[gid] = (nc + bi - 1) / bi;
+    cnt[gid] = (c % shard_count == shard_index) ? (nc + bi - 1) / bi : 0;
 }
 
 __global__ void k_block_emit(const TaskDev *tasks, int ntasks, int ncell, const int *off,
@@ -386,31 +389,17 @@ __global__ void k_block_emit(const TaskDev *tasks, int ntasks, int ncell, const 
     }
 }
 
-cudaError_t make_blocks(const TaskDev *tasks_dev, int ntasks, int ncell, int bi, Block *blocks,
-                        int *nblocks_dev, int *tmp_counts, int *tmp_offsets, cudaStream_t st) {
-    long long tot = (long long)ntasks * ncell;
-    int g = (int)((tot + 255) / 256);
-    if (g > 0) {
-        k_block_counts<<<g, 256, 0, st>>>(tasks_dev, ntasks, ncell, bi, tmp_counts);
-        note_launch();
-    }
-    cudaError_t e = scan_exclusive(tmp_counts, tmp_offsets, (int)tot, st);
-    if (e != cudaSuccess) return e;
-    k_block_emit<<<std::max(g, 1), 256, 0, st>>>(tasks_dev, ntasks, ncell, tmp_offsets, blocks,
-                                                 nblocks_dev);
-    note_launch();
-    return cudaGetLastError();
-}
-
-// make_blocks with every temporary supplied by the caller (tmp_tot: at least
+// Block list with every temporary supplied by the caller (tmp_tot: at least
 // max(1, ceil((ntasks * ncell) / 4096)) ints); performs no allocation.
 cudaError_t make_blocks_into(const TaskDev *tasks_dev, int ntasks, int ncell, int bi,
-                             Block *blocks, int *nblocks_dev, int *tmp_counts, int *tmp_offsets,
-                             int *tmp_tot, cudaStream_t st) {
+                             int shard_index, int shard_count, Block *blocks, int *nblocks_dev,
+                             int *tmp_counts, int *tmp_offsets, int *tmp_tot, cudaStream_t st) {
     long long tot = (long long)ntasks * ncell;
     int g = (int)((tot + 255) / 256);
+    if (shard_count < 1) shard_count = 1, shard_index = 0;
     if (g > 0) {
-        k_block_counts<<<g, 256, 0, st>>>(tasks_dev, ntasks, ncell, bi, tmp_counts);
+        k_block_counts<<<g, 256, 0, st>>>(tasks_dev, ntasks, ncell, bi, shard_index, shard_count,
+                                          tmp_counts);
         note_launch();
     }
     cudaError_t e = scan_exclusive_into(tmp_counts, tmp_offsets, (int)tot, tmp_tot, st);
@@ -436,7 +425,7 @@ extern "C" pc_status pc_aabb(const double *xyz, long long n, void *stream, doubl
     const double *dx = xyz;
     double *tmp = nullptr;
     if (n > 0 && !is_device_ptr(xyz)) {
-        PC_CUDA(cudaMallocAsync(&tmp, sizeof(double) * 3 * n, st));
+        PC_CUDA(::pc::alloc_dev_async(&tmp, sizeof(double) * 3 * n, st));
         PC_CUDA(cudaMemcpyAsync(tmp, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
         dx = tmp;
     }
@@ -494,13 +483,13 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     double *tmp_xyz = nullptr;
     void *tmp_w = nullptr;
     if (n > 0 && !is_device_ptr(xyz)) {
-        PC_CUDA(cudaMallocAsync(&tmp_xyz, sizeof(double) * 3 * n, st));
+        PC_CUDA(::pc::alloc_dev_async(&tmp_xyz, sizeof(double) * 3 * n, st));
         PC_CUDA(cudaMemcpyAsync(tmp_xyz, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
         dxyz = tmp_xyz;
     }
     size_t wbytes = (size_t)n * (w_is_f32 ? sizeof(float) : sizeof(double));
     if (w && n > 0 && !is_device_ptr(w)) {
-        PC_CUDA(cudaMallocAsync(&tmp_w, wbytes, st));
+        PC_CUDA(::pc::alloc_dev_async(&tmp_w, wbytes, st));
         PC_CUDA(cudaMemcpyAsync(tmp_w, w, wbytes, cudaMemcpyHostToDevice, st));
         dw = tmp_w;
     }
@@ -633,11 +622,11 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     // device arrays
     cudaError_t e = cudaSuccess;
     size_t nn = std::max<long long>(n, 1);
-    e = cudaMalloc(&g->rel, sizeof(float4) * nn);
-    if (e == cudaSuccess) e = cudaMalloc(&g->cx, sizeof(uint16_t) * nn);
-    if (e == cudaSuccess) e = cudaMalloc(&g->xw, sizeof(double4_32a) * nn);
-    if (e == cudaSuccess) e = cudaMalloc(&g->cell_start, sizeof(int) * (g->ncell + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&g->perm, sizeof(int) * nn);
+    e = ::pc::alloc_dev(&g->rel, sizeof(float4) * nn);
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&g->cx, sizeof(uint16_t) * nn);
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&g->xw, sizeof(double4_32a) * nn);
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&g->cell_start, sizeof(int) * (g->ncell + 1));
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&g->perm, sizeof(int) * nn);
     if (e != cudaSuccess) {
         cleanup();
         grid_release(g);
@@ -652,10 +641,10 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     while (sub_bits > 0 && ((long long)g->ncell << (3 * sub_bits)) > (1LL << 28)) --sub_bits;
     const int nkey = g->ncell << (3 * sub_bits);
     int *counts = nullptr, *cell = nullptr, *slot = nullptr, *key_start = nullptr;
-    e = cudaMallocAsync(&counts, sizeof(int) * nkey, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&key_start, sizeof(int) * ((size_t)nkey + 1), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&cell, sizeof(int) * nn, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&slot, sizeof(int) * nn, st);
+    e = ::pc::alloc_dev_async(&counts, sizeof(int) * nkey, st);
+    if (e == cudaSuccess) e = ::pc::alloc_dev_async(&key_start, sizeof(int) * ((size_t)nkey + 1), st);
+    if (e == cudaSuccess) e = ::pc::alloc_dev_async(&cell, sizeof(int) * nn, st);
+    if (e == cudaSuccess) e = ::pc::alloc_dev_async(&slot, sizeof(int) * nn, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int) * nkey, st);
     if (e == cudaSuccess && n > 0) {
         int blocks = (int)((n + 255) / 256);

@@ -243,13 +243,13 @@ extern "C" pc_status pc_hist_s2(const float *s2, long long n, int repeat, const 
     pc_status status = PC_OK;
     cudaError_t e = cudaSuccess;
     if (n > 0 && !is_device_ptr(s2)) {
-        e = cudaMallocAsync(&tmp, sizeof(float) * n, st);
+        e = ::pc::alloc_dev_async(&tmp, sizeof(float) * n, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, s2, sizeof(float) * n, cudaMemcpyHostToDevice, st);
         ds2 = tmp;
     }
-    if (e == cudaSuccess) e = cudaMallocAsync(&dout, sizeof(unsigned long long) * nbins, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&dE, sizeof(float) * (nbins + 1), st);
-    if (e == cudaSuccess && !tab.empty()) e = cudaMallocAsync(&dtab, sizeof(unsigned) * tab.size(), st);
+    if (e == cudaSuccess) e = ::pc::alloc_dev_async(&dout, sizeof(unsigned long long) * nbins, st);
+    if (e == cudaSuccess) e = ::pc::alloc_dev_async(&dE, sizeof(float) * (nbins + 1), st);
+    if (e == cudaSuccess && !tab.empty()) e = ::pc::alloc_dev_async(&dtab, sizeof(unsigned) * tab.size(), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, sizeof(unsigned long long) * nbins, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dE, U.data(), sizeof(float) * (nbins + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && dtab)

@@ -30,7 +30,9 @@
 namespace pc {
 
 constexpr unsigned long long FLUSH_LIMIT = 1ull << 30;
-// integer weight path: products (each < 2^48) per u64 shared copy between flushes
+// integer weight path: products (each < 2^48) per lane copy between flushes;
+// each of its three u32 plane entries then holds less than 2^16 pieces of
+// 16 bits, and the copy's recombined sum stays below 2^64
 constexpr unsigned long long WINT_LIMIT = 1ull << 16;
 
 struct SmemLayout {
@@ -46,16 +48,22 @@ __host__ __device__ inline SmemLayout smem_layout(const PairParams &p, bool f64)
     size_t o = 0;
     L.lut = o;
     o = align_up(o + (size_t)p.lut_total * sizeof(float2), 16);
+    // squared edges: the FP64 kernel's binning (the FP32 kernel's rescue
+    // reads them from global memory)
     L.ea = o;
-    o = align_up(o + (size_t)(p.n_a + 1) * sizeof(double), 16);
+    if (f64) o = align_up(o + (size_t)(p.n_a + 1) * sizeof(double), 16);
     L.eb = o;
-    o = align_up(o + (size_t)(p.n_b + 1) * sizeof(double), 16);
+    if (f64) o = align_up(o + (size_t)(p.n_b + 1) * sizeof(double), 16);
     int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
     L.hist = o;
     if (p.smem_hist_ok) o = align_up(o + (size_t)p.nbins_smem * copies * sizeof(int), 16);
     L.whist = o;
-    if (p.smem_hist_ok && p.weighted)
-        o = align_up(o + (size_t)p.nbins_smem * p.hist_k * sizeof(double), 16);
+    if (p.smem_hist_ok && p.weighted) {
+        if (p.wint && !f64)   // three u32 planes of 16-bit product pieces
+            o = align_up(o + (size_t)3 * p.nbins_smem * p.wint_k * sizeof(unsigned), 16);
+        else
+            o = align_up(o + (size_t)p.nbins_smem * p.hist_k * sizeof(double), 16);
+    }
     L.seg = o;
     o = align_up(o + (size_t)(p.tree && !f64 ? MAXSEG_T : MAXSEG) * sizeof(int4), 16);
     int tj = f64 ? TJ64 : TJ;
@@ -64,8 +72,9 @@ __host__ __device__ inline SmemLayout smem_layout(const PairParams &p, bool f64)
     L.meta = o;
     if (f64) o = align_up(o + (size_t)2 * tj * sizeof(int2), 16);
     else if (p.tree) o = align_up(o + (size_t)MAXSEG_T * sizeof(float4), 16);   // segment offsets
-    L.tw = o;
-    if (p.weighted && !f64) o = align_up(o + (size_t)2 * tj * sizeof(double), 16);
+    L.tw = o;   // staged j weights: binary64, or the packed 4-byte integer weights
+    if (p.weighted && !f64)
+        o = align_up(o + (size_t)2 * tj * (p.wint ? sizeof(unsigned) : sizeof(double)), 16);
     L.q = o;
     o = align_up(o + (size_t)LQ * sizeof(uint3), 16);
     L.gstride = o - L.seg;
@@ -352,21 +361,36 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
         // discarded row of lin_norange and are only cleared
         const int copies = p.priv ? NT / 32 : 1, K = p.hist_k, nbs = p.nbins_smem;
         unsigned long long *u = reinterpret_cast<unsigned long long *>(s_whist);
+        unsigned *wp = reinterpret_cast<unsigned *>(s_whist);   // integer weight planes
+        const int WK = p.wint_k;
+        const size_t PLN = (size_t)nbs * WK;
         for (int b = gtid(); b < nbs; b += NT) {
             long long v = 0;
             for (int c = 0; c < copies; ++c)
                 for (int k = 0; k < K; ++k) v += take_i32<G>(&s_hist[(c * nbs + b) * K + k]);
-            if (b >= p.nbins) {
-                if (p.weighted)
+            if (b >= p.nbins) {   // discarded rows (and the row of lanes without a pair)
+                if (p.weighted && p.wint) {
+                    for (int k = 0; k < WK; ++k)
+                        for (int q = 0; q < 3; ++q)
+                            take_i32<G>((int *)&wp[q * PLN + (size_t)b * WK + k]);
+                } else if (p.weighted) {
                     for (int k = 0; k < K; ++k) take_u64<G>(&u[b * K + k]);
+                }
                 continue;
             }
             if (v) atomicAdd(&p.hist[(size_t)h * p.nbins + b], (unsigned long long)v);
             if (p.weighted) {
                 double w = 0.0;
                 if (p.wint) {
-                    // u64 lane copies of exact integer products (each < 2^64)
-                    for (int k = 0; k < K; ++k) w += (double)take_u64<G>(&u[b * K + k]);
+                    // per lane copy: the exact sum of its products (below
+                    // 2^64) from its three 16-bit-piece planes
+                    for (int k = 0; k < WK; ++k) {
+                        const size_t e = (size_t)b * WK + k;
+                        const unsigned long long lo = (unsigned)take_i32<G>((int *)&wp[e]);
+                        const unsigned long long mid = (unsigned)take_i32<G>((int *)&wp[PLN + e]);
+                        const unsigned long long hi = (unsigned)take_i32<G>((int *)&wp[2 * PLN + e]);
+                        w += (double)(lo + (mid << 16) + (hi << 32));
+                    }
                     w *= wscale;
                 } else {
                     // binary64 sums, exchanged as their bit patterns
@@ -527,10 +551,11 @@ __device__ __forceinline__ void red_shared_u32_if(unsigned addr, bool on) {
         "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}"
         ::"r"(addr), "r"((unsigned)on));
 }
-__device__ __forceinline__ void red_shared_u64_if(unsigned addr, unsigned long long v, bool on) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p red.shared.add.u64 [%0], %1;\n\t}"
-        ::"r"(addr), "l"(v), "r"((unsigned)on));
+// Unpredicated: the whole warp issues it, lanes without a pair pointing at
+// the discarded row.  A partially predicated shared reduction measured about
+// half the throughput of a full-warp one on this GPU.
+__device__ __forceinline__ void red_shared_u32(unsigned addr, unsigned v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 __device__ __forceinline__ void red_shared_f64_if(unsigned addr, double v, bool on) {
     asm volatile(
@@ -666,7 +691,13 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
     const unsigned bias = 0x4B000000u * nbu + ((MODE == MODE_SMU) ? 0x4B000000u : 0u) +
                           (CHK ? nbu : 0u);
     const unsigned hbase = hist_sa - hk4 * bias;
+    const unsigned htrash = hist_sa + hk4 * (unsigned)p.trash_row;
     const unsigned wbase = whist_sa - 2u * hk4 * bias;
+    // integer weight planes: 4-byte entries, wint_k lane copies, planes PLB bytes apart
+    const unsigned wk4 = 4u * (unsigned)p.wint_k;
+    const unsigned wbase2 = whist_sa - wk4 * bias;
+    const unsigned wtrash = whist_sa + wk4 * (unsigned)p.trash_row;
+    const unsigned PLB = wk4 * (unsigned)p.nbins_smem;
     float2 NX[RI], NY[RI], NZ[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
@@ -739,23 +770,30 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                     b1 = b1 * nbu + j1;
                 }
                 const bool a0 = in0[r] && ok0 && !n0, a1 = in1[r] && ok1 && !n1;
-                red_shared_u32_if(hbase + hk4 * b0, a0);
-                red_shared_u32_if(hbase + hk4 * b1, a1);
+                red_shared_u32(a0 ? hbase + hk4 * b0 : htrash, 1u);
+                red_shared_u32(a1 ? hbase + hk4 * b1 : htrash, 1u);
                 if (W == 1) {
                     const double2 wj = *reinterpret_cast<const double2 *>(tb.w + jj);
                     red_shared_f64_if(wbase + 2u * hk4 * b0, __dmul_rn(I.w[r], wj.x), a0);
                     red_shared_f64_if(wbase + 2u * hk4 * b1, __dmul_rn(I.w[r], wj.y), a1);
                 } else if (W == 2) {
                     // exact 48-bit significand product, shifted down by both
-                    // exponent offsets (truncation < 2^(k_i + k_j - 46) relative)
+                    // exponent offsets (truncation < 2^(k_i + k_j - 46) relative),
+                    // added as three 16-bit pieces to three u32 planes
                     const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
                     const unsigned mi = I.wm[r] & 0xFFFFFFu, ki = I.wm[r] >> 24;
                     const unsigned long long p0 =
                         ((unsigned long long)mi * (wj.x & 0xFFFFFFu)) >> (ki + (wj.x >> 24));
                     const unsigned long long p1 =
                         ((unsigned long long)mi * (wj.y & 0xFFFFFFu)) >> (ki + (wj.y >> 24));
-                    red_shared_u64_if(wbase + 2u * hk4 * b0, p0, a0);
-                    red_shared_u64_if(wbase + 2u * hk4 * b1, p1, a1);
+                    const unsigned w0 = a0 ? wbase2 + wk4 * b0 : wtrash;
+                    const unsigned w1 = a1 ? wbase2 + wk4 * b1 : wtrash;
+                    red_shared_u32(w0, (unsigned)p0 & 0xFFFFu);
+                    red_shared_u32(w0 + PLB, (unsigned)p0 >> 16);
+                    red_shared_u32(w0 + 2u * PLB, (unsigned)(p0 >> 32));
+                    red_shared_u32(w1, (unsigned)p1 & 0xFFFFu);
+                    red_shared_u32(w1 + PLB, (unsigned)p1 >> 16);
+                    red_shared_u32(w1 + 2u * PLB, (unsigned)(p1 >> 32));
                 }
                 re0[r] = in0[r] && n0;
                 re1[r] = in1[r] && n1;
@@ -802,7 +840,12 @@ __device__ __forceinline__ void pair_tile_sigpi2(const PairParams &p, Tile tb, i
     const unsigned limA = 0x4B000000u + lc.nA, limB = 0x4B000000u + lc.nB_u;
     const unsigned bias = 0x4B000000u * nbu + 0x4B000000u;
     const unsigned hbase = hist_sa - hk4 * bias;
+    const unsigned htrash = hist_sa + hk4 * (unsigned)p.trash_row;
     const unsigned wbase = whist_sa - 2u * hk4 * bias;
+    const unsigned wk4 = 4u * (unsigned)p.wint_k;
+    const unsigned wbase2 = whist_sa - wk4 * bias;
+    const unsigned wtrash = whist_sa + wk4 * (unsigned)p.trash_row;
+    const unsigned PLB = wk4 * (unsigned)p.nbins_smem;
     float2 NX[RI], NY[RI], NZ[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
@@ -876,8 +919,8 @@ __device__ __forceinline__ void pair_tile_sigpi2(const PairParams &p, Tile tb, i
                 const bool ok0 = ba0 < limA && bb0 < limB, ok1 = ba1 < limA && bb1 < limB;
                 const unsigned b0 = ba0 * nbu + bb0, b1 = ba1 * nbu + bb1;
                 const bool a0 = in0[r] && ok0 && !n0, a1 = in1[r] && ok1 && !n1;
-                red_shared_u32_if(hbase + hk4 * b0, a0);
-                red_shared_u32_if(hbase + hk4 * b1, a1);
+                red_shared_u32(a0 ? hbase + hk4 * b0 : htrash, 1u);
+                red_shared_u32(a1 ? hbase + hk4 * b1 : htrash, 1u);
                 if (W == 1) {
                     const double2 wj = *reinterpret_cast<const double2 *>(tb.w + jj);
                     red_shared_f64_if(wbase + 2u * hk4 * b0, __dmul_rn(I.w[r], wj.x), a0);
@@ -889,8 +932,14 @@ __device__ __forceinline__ void pair_tile_sigpi2(const PairParams &p, Tile tb, i
                         ((unsigned long long)mi * (wj.x & 0xFFFFFFu)) >> (ki + (wj.x >> 24));
                     const unsigned long long p1 =
                         ((unsigned long long)mi * (wj.y & 0xFFFFFFu)) >> (ki + (wj.y >> 24));
-                    red_shared_u64_if(wbase + 2u * hk4 * b0, p0, a0);
-                    red_shared_u64_if(wbase + 2u * hk4 * b1, p1, a1);
+                    const unsigned w0 = a0 ? wbase2 + wk4 * b0 : wtrash;
+                    const unsigned w1 = a1 ? wbase2 + wk4 * b1 : wtrash;
+                    red_shared_u32(w0, (unsigned)p0 & 0xFFFFu);
+                    red_shared_u32(w0 + PLB, (unsigned)p0 >> 16);
+                    red_shared_u32(w0 + 2u * PLB, (unsigned)(p0 >> 32));
+                    red_shared_u32(w1, (unsigned)p1 & 0xFFFFu);
+                    red_shared_u32(w1 + PLB, (unsigned)p1 >> 16);
+                    red_shared_u32(w1 + 2u * PLB, (unsigned)(p1 >> 32));
                 }
                 re0[r] = in0[r] && n0;
                 re1[r] = in1[r] && n1;
@@ -1025,8 +1074,12 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     if (smem_hist) {
         const int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
         for (int k = threadIdx.x; k < p.nbins_smem * copies; k += NT * G) s_hist[k] = 0;
-        if (W)
+        if (W == 2) {   // the three integer weight planes
+            unsigned *wp = reinterpret_cast<unsigned *>(s_whist);
+            for (int k = threadIdx.x; k < 3 * p.nbins_smem * p.wint_k; k += NT * G) wp[k] = 0u;
+        } else if (W) {
             for (int k = threadIdx.x; k < p.nbins_smem * p.hist_k; k += NT * G) s_whist[k] = 0.0;
+        }
     }
     if (tid == 0) {
         cs.qn = 0;
@@ -1067,7 +1120,8 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     const unsigned hist_sa = (unsigned)__cvta_generic_to_shared(s_hist) +
                              (p.priv ? (unsigned)((tid >> 5) * p.nbins_smem * p.hist_k * 4) : 0u) +
                              4u * lane_copy;
-    const unsigned whist_sa = (unsigned)__cvta_generic_to_shared(s_whist) + 8u * lane_copy;
+    const unsigned whist_sa = (unsigned)__cvta_generic_to_shared(s_whist) +
+                              (W == 2 ? 4u * (unsigned)(tid & (p.wint_k - 1)) : 8u * lane_copy);
 
     const int nx = p.g.ng[0], ny = p.g.ng[1];
     const float c32x = p.g.c32[0], c32y = p.g.c32[1], c32z = p.g.c32[2];
@@ -1077,11 +1131,12 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     unsigned long long wterms = 0;        // CTA-uniform bound of products per u64 copy (W == 2)
     int cur_hist = -1;
     double cur_wscale = 0.0;
-    // integer weights: before n more j-points, flush if a u64 copy could
-    // exceed WINT_LIMIT products (NT / hist_k threads share a copy)
+    // integer weights: before n more j-points, flush if a lane copy of the
+    // weight planes could exceed WINT_LIMIT products (NT / wint_k threads
+    // share a copy; each plane entry then stays below 2^16 x 2^16)
     auto wint_room = [&](int n) {
         if (W != 2) return;
-        const unsigned long long add = (unsigned long long)(NT / p.hist_k) * RI * (unsigned)n;
+        const unsigned long long add = (unsigned long long)(NT / p.wint_k) * RI * (unsigned)n;
         if (wterms + add > WINT_LIMIT) {
             flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
             since_flush = 0;
@@ -1092,7 +1147,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     __syncthreads();   // CTA-wide: shared histograms are clear
 
     for (;;) {
-        if (tid == 0) cs.blk = atomicAdd(p.work_counter, 1) * p.shard_count + p.shard_index;
+        if (tid == 0) cs.blk = atomicAdd(p.work_counter, 1);   // the list holds only this shard's blocks
         gsync<G>();
         const int bidx = cs.blk;
         if (bidx >= nblocks) break;
@@ -1388,7 +1443,7 @@ __global__ void __launch_bounds__(NT) k_pairs_f64(const __grid_constant__ PairPa
     __syncthreads();
 
     for (;;) {
-        if (tid == 0) cs.blk = atomicAdd(p.work_counter, 1) * p.shard_count + p.shard_index;
+        if (tid == 0) cs.blk = atomicAdd(p.work_counter, 1);   // the list holds only this shard's blocks
         __syncthreads();
         const int bidx = cs.blk;
         if (bidx >= nblocks) break;

@@ -79,10 +79,11 @@ pc_status tree_traverse(const pc_tree *t1, const pc_tree *t2, bool is_auto, doub
                         double r2lo, cudaStream_t st, TreeLists &out);
 
 // Balanced blocks per list node for ipt i-points per thread (NT * ipt points
-// per block at most), and the pair kernel's block list of a tree count.
+// per block at most), and the pair kernel's block list of a tree count: the
+// list nodes of the shard (node % shard_count == shard_index) only.
 int tree_chunks(const pc_tree *t, int ipt);
-cudaError_t tree_blocks(const pc_tree *t, int ipt, Block *blocks, int *nblocks_dev,
-                        cudaStream_t st);
+cudaError_t tree_blocks(const pc_tree *t, int ipt, int shard_index, int shard_count, Block *blocks,
+                        int *nblocks_dev, cudaStream_t st);
 
 // Growable device buffer that keeps its first `keep` bytes when it grows.
 struct DevVec {
@@ -92,7 +93,7 @@ struct DevVec {
         if (bytes <= cap) return cudaSuccess;
         const size_t want = bytes > cap * 2 ? bytes : cap * 2;
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, want);
+        cudaError_t e = ::pc::alloc_dev(&q, want);
         if (e != cudaSuccess) return e;
         if (keep && p) {
             e = cudaMemcpyAsync(q, p, keep, cudaMemcpyDeviceToDevice, st);
@@ -120,7 +121,8 @@ struct TreeBatch {
 pc_status tree_batch_lists(const std::vector<const pc_tree *> &ts, int ipt, double r2hi,
                            double r2lo, cudaStream_t st, TreeBatch &B);
 cudaError_t tree_blocks_batch(const std::vector<const pc_tree *> &ts, const TreeBatch &B, int ipt,
-                              Block *blocks, int *nblocks_dev, cudaStream_t st);
+                              int shard_index, int shard_count, Block *blocks, int *nblocks_dev,
+                              cudaStream_t st);
 
 // Weight checks for the integer weight path: r[0] counts weights that are
 // not a non-negative normal binary32 value or zero, r[1] / r[2] the largest /
@@ -136,17 +138,15 @@ bool is_device_ptr(const void *p);
 // Exclusive scan of n ints into out[0..n] (out[n] = total), stream-ordered.
 cudaError_t scan_exclusive(const int *in, int *out, int n, cudaStream_t st);
 
-// Block list: for every task t and every cell c of its i-grid, split the
-// cell's points into ceil(count / bi) balanced blocks.  Writes the blocks
-// (capacity must be >= sum over tasks of ncell + n / bi) and *nblocks.
-cudaError_t make_blocks(const TaskDev *tasks_dev, int ntasks, int ncell, int bi, Block *blocks,
-                        int *nblocks_dev, int *tmp_counts, int *tmp_offsets, cudaStream_t st);
-
 // Allocation-free variants: every temporary comes from the caller.
 cudaError_t scan_exclusive_into(const int *in, int *out, int n, int *tot, cudaStream_t st);
+// Block list: for every task t and every cell c of its i-grid in the shard
+// (c % shard_count == shard_index), the cell's points split into
+// ceil(count / bi) balanced blocks.  Writes the blocks (capacity must be
+// >= sum over tasks of ncell + n / bi) and *nblocks.
 cudaError_t make_blocks_into(const TaskDev *tasks_dev, int ntasks, int ncell, int bi,
-                             Block *blocks, int *nblocks_dev, int *tmp_counts, int *tmp_offsets,
-                             int *tmp_tot, cudaStream_t st);
+                             int shard_index, int shard_count, Block *blocks, int *nblocks_dev,
+                             int *tmp_counts, int *tmp_offsets, int *tmp_tot, cudaStream_t st);
 
 // Forget cached count graphs that use grid g (the grid is being freed).
 void forget_grid(const pc_grid *g);

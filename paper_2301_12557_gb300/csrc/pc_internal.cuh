@@ -93,7 +93,8 @@ struct PairParams {
     unsigned long long *qcount;  // device scalar
     unsigned long long qcap;
     unsigned long long *counters;  // [0] candidates, [1] inline rescues
-    int shard_index, shard_count;   // this launch counts blocks index * count + shard
+    int shard_index, shard_count;   // the block list holds only the cells (tree: list nodes)
+                                    // whose index % shard_count == shard_index
     int groups = 1;          // FP32 kernel: independent groups of NT threads per CTA sharing
                              // one shared histogram (large histograms)
     int priv;                // 0: one histogram per CTA; 1: one per warp
@@ -120,9 +121,16 @@ struct PairParams {
     float lin_invB2, lin_thrB;
     int nbins_smem;              // bins per shared copy: nbins, plus n_b with lin_norange
     // weighted sums from exact integer products of the packed binary32 weights
-    // (significand product shifted by both exponent offsets, accumulated in
-    // u64 lane copies, flushed as binary64 times the task's wscale)
+    // (significand product shifted by both exponent offsets, below 2^48),
+    // accumulated as three 16-bit pieces in three u32 planes of wint_k lane
+    // copies each, recombined exactly per copy and flushed as binary64 times
+    // the task's wscale
     int wint;
+    int wint_k;              // lane copies of each integer weight plane (power of 2)
+    // shared-histogram row that lanes without an in-range pair update (the
+    // floor-bin kernels issue every reduction with the full warp); the flush
+    // discards it like every row past nbins
+    int trash_row;
     // k-d tree path (Alg. 3): each i-block (a tree node at the block level)
     // pairs with the j-blocks listed for it by the dual-tree traversal
     int tree;
@@ -143,6 +151,26 @@ pc_status cuda_fail(cudaError_t e, const char *what);
 // Count of kernel launches issued by the library (host side).
 void note_launch(int n = 1);
 long long launch_count();
+
+// Every device (and pinned host) allocation of the library goes through these,
+// which count it (pc_alloc_count).
+void note_alloc();
+long long alloc_count();
+template <class T>
+inline cudaError_t alloc_dev(T **p, size_t bytes) {
+    note_alloc();
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+template <class T>
+inline cudaError_t alloc_dev_async(T **p, size_t bytes, cudaStream_t st) {
+    note_alloc();
+    return cudaMallocAsync(reinterpret_cast<void **>(p), bytes, st);
+}
+template <class T>
+inline cudaError_t alloc_host(T **p, size_t bytes) {
+    note_alloc();
+    return cudaMallocHost(reinterpret_cast<void **>(p), bytes);
+}
 
 #define PC_CUDA(call)                                             \
     do {                                                          \

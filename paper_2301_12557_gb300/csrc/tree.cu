@@ -503,16 +503,18 @@ __global__ void k_group_fill(const int2 *__restrict__ emit, int ne, int blk0_i, 
     seg[pos] = make_int2((e.y & 0xFFFFFF) - blk0_j, e.y >> 24);
 }
 
-// The pair kernel's blocks: every list node split into k balanced chunks
-// ("cell" = the list node; k is chosen so a chunk fits NT x ipt i-points).
-// (Batches: task `task`, list nodes numbered from node0, blocks written from
-// blocks[0]; *nblocks receives the batch's total.)
-__global__ void k_tree_blocks(const int2 *__restrict__ rng, int nlist, int k, int task, int node0,
-                              int total, Block *__restrict__ blocks, int *__restrict__ nblocks) {
+// The pair kernel's blocks: every list node of the shard (nodes shard,
+// shard + S, ...: nshard of them) split into k balanced chunks ("cell" = the
+// list node; k is chosen so a chunk fits NT x ipt i-points).  (Batches: task
+// `task`, list nodes numbered from node0, blocks written from blocks[0];
+// *nblocks receives the batch's total.)
+__global__ void k_tree_blocks(const int2 *__restrict__ rng, int nshard, int shard, int S, int k,
+                              int task, int node0, int total, Block *__restrict__ blocks,
+                              int *__restrict__ nblocks) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b == 0) *nblocks = total;
-    if (b >= nlist * k) return;
-    const int node = b / k, c = b % k;
+    if (b >= nshard * k) return;
+    const int node = shard + S * (b / k), c = b % k;
     const int2 r = rng[node];
     const int s0 = r.x + (int)((long long)r.y * c / k), s1 = r.x + (int)((long long)r.y * (c + 1) / k);
     blocks[b] = Block{task, node0 + node, s0, s1 - s0};
@@ -538,7 +540,7 @@ struct DArr {
         if (bytes <= cap) return cudaSuccess;
         size_t want = std::max(bytes, cap * 2);
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, want);
+        cudaError_t e = ::pc::alloc_dev(&q, want);
         if (e != cudaSuccess) return e;
         if (keep && p) {
             e = cudaMemcpyAsync(q, p, keep, cudaMemcpyDeviceToDevice, st);
@@ -646,12 +648,19 @@ int tree_chunks(const pc_tree *t, int ipt) {
     return std::max(1, (t->lmax + cap - 1) / cap);
 }
 
-cudaError_t tree_blocks(const pc_tree *t, int ipt, Block *blocks, int *nblocks_dev,
-                        cudaStream_t st) {
+// List nodes of a shard among nl: shard, shard + S, ... below nl.
+static int shard_nodes(int nl, int shard, int S) { return nl > shard ? (nl - shard + S - 1) / S : 0; }
+
+cudaError_t tree_blocks(const pc_tree *t, int ipt, int shard_index, int shard_count, Block *blocks,
+                        int *nblocks_dev, cudaStream_t st) {
+    if (shard_count < 1) shard_count = 1, shard_index = 0;
     const int nl = 1 << t->blevel;
     const int k = tree_chunks(t, ipt);
-    const int nb = nl * k;
-    k_tree_blocks<<<(nb + 255) / 256, 256, 0, st>>>(t->brng, nl, k, 0, 0, nb, blocks, nblocks_dev);
+    const int ns = shard_nodes(nl, shard_index, shard_count);
+    const int nb = ns * k;
+    k_tree_blocks<<<std::max(1, (nb + 255) / 256), 256, 0, st>>>(t->brng, ns, shard_index,
+                                                                 shard_count, k, 0, 0, nb, blocks,
+                                                                 nblocks_dev);
     note_launch();
     return cudaGetLastError();
 }
@@ -703,14 +712,22 @@ pc_status tree_batch_lists(const std::vector<const pc_tree *> &ts, int ipt, doub
 }
 
 cudaError_t tree_blocks_batch(const std::vector<const pc_tree *> &ts, const TreeBatch &B, int ipt,
-                              Block *blocks, int *nblocks_dev, cudaStream_t st) {
+                              int shard_index, int shard_count, Block *blocks, int *nblocks_dev,
+                              cudaStream_t st) {
+    (void)B;
+    if (shard_count < 1) shard_count = 1, shard_index = 0;
     const int m = (int)ts.size();
+    // blocks of every tree's shard, back to back
+    std::vector<int> b0(m + 1, 0);
+    for (int k = 0; k < m; ++k)
+        b0[k + 1] = b0[k] + shard_nodes(1 << ts[k]->blevel, shard_index, shard_count) *
+                                tree_chunks(ts[k], ipt);
     for (int k = 0; k < m; ++k) {
-        const int nl = 1 << ts[k]->blevel;
+        const int ns = shard_nodes(1 << ts[k]->blevel, shard_index, shard_count);
         const int kc = tree_chunks(ts[k], ipt);
-        k_tree_blocks<<<(nl * kc + 255) / 256, 256, 0, st>>>(ts[k]->brng, nl, kc, k, B.node0[k],
-                                                              B.block0[m], blocks + B.block0[k],
-                                                              nblocks_dev);
+        k_tree_blocks<<<std::max(1, (ns * kc + 255) / 256), 256, 0, st>>>(
+            ts[k]->brng, ns, shard_index, shard_count, kc, k, B.node0[k], b0[m], blocks + b0[k],
+            nblocks_dev);
         note_launch();
     }
     return cudaGetLastError();
@@ -859,7 +876,7 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
     // temporaries
     std::vector<void *> tmp;
     auto talloc = [&](void **p, size_t bytes) {
-        cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+        cudaError_t e = ::pc::alloc_dev_async(p, std::max<size_t>(bytes, 16), st);
         if (e == cudaSuccess) tmp.push_back(*p);
         return e;
     };
@@ -938,15 +955,15 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
         node[2 * h + 1] = split ? vnode[2 * h + 1] : make_int2(0, -1);
         node[2 * h + 2] = split ? vnode[2 * h + 2] : make_int2(0, -1);
     }
-    e = cudaMalloc(&t->vnode, sizeof(int2) * ns);
-    if (e == cudaSuccess) e = cudaMalloc(&t->node, sizeof(int2) * ns);
-    if (e == cudaSuccess) e = cudaMalloc(&t->nbox, sizeof(double) * 6 * ns);
-    if (e == cudaSuccess) e = cudaMalloc(&t->naxis, ns);
-    if (e == cudaSuccess) e = cudaMalloc(&t->rel, sizeof(float4) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&t->xw, sizeof(double4_32a) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&t->perm, sizeof(int) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&t->bcen, sizeof(double) * 3 * ((size_t)1 << blevel));
-    if (e == cudaSuccess) e = cudaMalloc(&t->brng, sizeof(int2) * ((size_t)1 << blevel));
+    e = ::pc::alloc_dev(&t->vnode, sizeof(int2) * ns);
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&t->node, sizeof(int2) * ns);
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&t->nbox, sizeof(double) * 6 * ns);
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&t->naxis, ns);
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&t->rel, sizeof(float4) * n);
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&t->xw, sizeof(double4_32a) * n);
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&t->perm, sizeof(int) * n);
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&t->bcen, sizeof(double) * 3 * ((size_t)1 << blevel));
+    if (e == cudaSuccess) e = ::pc::alloc_dev(&t->brng, sizeof(int2) * ((size_t)1 << blevel));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(PC_ENOMEM, "pc_build_tree: device allocation failed"));

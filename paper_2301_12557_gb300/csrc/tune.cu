@@ -90,8 +90,8 @@ extern "C" pc_status pc_tune(const double *xyz, const void *w, int w_is_f32, lon
     PC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int nbins = b->n_a * (b->mode == PC_BIN_S ? 1 : b->n_b);
     DevBuf dc, dw;
-    PC_CUDA(cudaMalloc(&dc.p, sizeof(long long) * nbins));
-    if (w) PC_CUDA(cudaMalloc(&dw.p, sizeof(double) * nbins));
+    PC_CUDA(::pc::alloc_dev(&dc.p, sizeof(long long) * nbins));
+    if (w) PC_CUDA(::pc::alloc_dev(&dw.p, sizeof(double) * nbins));
 
     // Sample every S-th point block.  S starts where every persistent CTA
     // still gets about four blocks, and grows (after one calibration run at
@@ -289,8 +289,8 @@ extern "C" pc_status pc_tune_tree(const double *xyz, const void *w, int w_is_f32
     PC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int nbins = b->n_a * (b->mode == PC_BIN_S ? 1 : b->n_b);
     DevBuf dc, dw;
-    PC_CUDA(cudaMalloc(&dc.p, sizeof(long long) * nbins));
-    if (w) PC_CUDA(cudaMalloc(&dw.p, sizeof(double) * nbins));
+    PC_CUDA(::pc::alloc_dev(&dc.p, sizeof(long long) * nbins));
+    if (w) PC_CUDA(::pc::alloc_dev(&dw.p, sizeof(double) * nbins));
 
     const double ctas = 5.0 * sms;
     const double blocks_est = std::max(1.0, (double)n / (NT * 4));

@@ -114,6 +114,15 @@ def test_tune_host_side_checks(lib):
     assert out.cell_size == pytest.approx(P.pc_suggest_cell_size(1, 1e6, 20.0, 0))
 
 
+def test_fp_peak_host_side_checks(lib):
+    # bad kind, negative iterations or no output: rejected before any CUDA call
+    tf = ctypes.c_double(0.0)
+    assert lib.pc_fp_peak(3, 0, None, ctypes.byref(tf), None) == P.PC_EINVAL
+    assert lib.pc_fp_peak(-1, 0, None, ctypes.byref(tf), None) == P.PC_EINVAL
+    assert lib.pc_fp_peak(0, -5, None, ctypes.byref(tf), None) == P.PC_EINVAL
+    assert lib.pc_fp_peak(0, 0, None, None, None) == P.PC_EINVAL
+
+
 def test_tree_and_hist_host_side_checks(lib):
     box = P.make_box(100.0, True)
     out = ctypes.c_void_p()

@@ -4,9 +4,11 @@ When every weight of both catalogues is a non-negative normal binary32 value
 (or zero) and the two catalogues' exponent spans add up to at most 12, the
 pair kernel accumulates each pair weight w_i w_j (Sect. 2.5) as an integer:
 the weight w = M 2^(e - 150) (M the 24-bit significand, e the biased
-exponent) is packed as M and k = e_max - e, a pair adds (M_i M_j) >> (k_i +
-k_j) to a 64-bit lane counter (at most 2^16 products between flushes), and a
-flush converts each counter to binary64 and multiplies it by
+exponent) is packed as M and k = e_max - e, a pair's product p = (M_i M_j) >> (k_i +
+k_j) (below 2^48) is added as three 16-bit pieces (p mod 2^16, bits 16-31,
+p >> 32) to three 32-bit lane counters (at most 2^16 products between
+flushes, so no counter wraps), and a flush recombines each lane's counters
+into the exact 64-bit sum, converts it to binary64 and multiplies it by
 2^(e_max,i + e_max,j - 300).  The truncation of one product is below
 2^(k_i + k_j - 46) <= 2^-34 of it, so every bin's sum is within 2^-34
 relative of the exact sum.  This test emulates the path on weights spanning
@@ -36,11 +38,17 @@ def _emulated_sum(wi, wj, emax_i, emax_j):
     mi, ki, _ = _pack(wi, emax_i)
     mj, kj, _ = _pack(wj, emax_j)
     prod = [(int(a) * int(b)) >> int(s) for a, b, s in zip(mi, mj, ki + kj)]
+    assert max(prod, default=0) < 2 ** 48
     unit = 2.0 ** (emax_i + emax_j - 300)
     total = 0.0
     for s in range(0, len(prod), WINT_LIMIT):
-        acc = sum(prod[s:s + WINT_LIMIT])
-        assert acc < 2 ** 64                      # one u64 lane counter
+        chunk = prod[s:s + WINT_LIMIT]
+        lo = sum(p & 0xFFFF for p in chunk)
+        mid = sum((p >> 16) & 0xFFFF for p in chunk)
+        hi = sum(p >> 32 for p in chunk)
+        assert max(lo, mid, hi) < 2 ** 32          # three u32 plane counters
+        acc = lo + (mid << 16) + (hi << 32)        # the flush's recombination
+        assert acc == sum(chunk) and acc < 2 ** 64
         total += float(acc) * unit
     return total
 
@@ -89,3 +97,14 @@ def test_single_pair_truncation_reaches_the_bound():
     exact = Fraction(float(wi[0])) * Fraction(float(wj[0]))
     rel = float(abs(Fraction(got) - exact) / exact)
     assert 2.0 ** -35 < rel < 2.0 ** -34
+
+
+def test_planes_hold_the_flush_limit_of_largest_products():
+    """The worst case between two flushes: 2^16 products of 2^48 - 1 each.
+    No 32-bit plane counter wraps and the recombined sum is exact in 64 bits."""
+    p = (1 << 48) - 1
+    n = WINT_LIMIT
+    lo, mid, hi = n * (p & 0xFFFF), n * ((p >> 16) & 0xFFFF), n * (p >> 32)
+    assert max(lo, mid, hi) < 2 ** 32
+    acc = lo + (mid << 16) + (hi << 32)
+    assert acc == n * p < 2 ** 64
