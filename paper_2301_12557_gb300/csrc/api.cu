@@ -502,7 +502,7 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
 // copy l % k) as many as fit a 16 KB budget, so the lanes of a warp do not
 // collide on the few bins of a small histogram.
 // (weighted: binary64 weight sums share the copies and the budget; the
-// integer weight planes have their own WINT_COPIES copies.)
+// integer weight records have their own WINT_COPIES copies.)
 static void choose_replication(int mode, int nbins, bool weighted, int &priv, int &hist_k) {
     priv = 0;
     hist_k = 1;
@@ -512,9 +512,8 @@ static void choose_replication(int mode, int nbins, bool weighted, int &priv, in
     while (hist_k < 32 && per_copy * hist_k * 2 <= 16384) hist_k *= 2;
 }
 
-// Lane copies of each integer weight plane (lanes l and l + 16 share one;
-// their i-points are the farthest apart of the warp's).
-constexpr int WINT_COPIES = 16;
+// Lane copies of the integer weight records (one per lane: conflict-free).
+constexpr int WINT_COPIES = 32;
 
 // Rows of each shared histogram copy: the bins, the discarded rows of the
 // floor bins without a range test, and at least one row past the bins that

@@ -31,8 +31,8 @@ namespace pc {
 
 constexpr unsigned long long FLUSH_LIMIT = 1ull << 30;
 // integer weight path: products (each < 2^48) per lane copy between flushes;
-// each of its three u32 plane entries then holds less than 2^16 pieces of
-// 16 bits, and the copy's recombined sum stays below 2^64
+// each of its three u32 piece sums then adds less than 2^16 pieces of 16
+// bits, and the copy's recombined sum stays below 2^64
 constexpr unsigned long long WINT_LIMIT = 1ull << 16;
 
 struct SmemLayout {
@@ -59,7 +59,7 @@ __host__ __device__ inline SmemLayout smem_layout(const PairParams &p, bool f64)
     if (p.smem_hist_ok) o = align_up(o + (size_t)p.nbins_smem * copies * sizeof(int), 16);
     L.whist = o;
     if (p.smem_hist_ok && p.weighted) {
-        if (p.wint && !f64)   // three u32 planes of 16-bit product pieces
+        if (p.wint && !f64)   // records of three u32 sums of 16-bit product pieces
             o = align_up(o + (size_t)3 * p.nbins_smem * p.wint_k * sizeof(unsigned), 16);
         else
             o = align_up(o + (size_t)p.nbins_smem * p.hist_k * sizeof(double), 16);
@@ -361,18 +361,15 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
         // discarded row of lin_norange and are only cleared
         const int copies = p.priv ? NT / 32 : 1, K = p.hist_k, nbs = p.nbins_smem;
         unsigned long long *u = reinterpret_cast<unsigned long long *>(s_whist);
-        unsigned *wp = reinterpret_cast<unsigned *>(s_whist);   // integer weight planes
+        unsigned *wp = reinterpret_cast<unsigned *>(s_whist);   // integer weight records
         const int WK = p.wint_k;
-        const size_t PLN = (size_t)nbs * WK;
         for (int b = gtid(); b < nbs; b += NT) {
             long long v = 0;
             for (int c = 0; c < copies; ++c)
                 for (int k = 0; k < K; ++k) v += take_i32<G>(&s_hist[(c * nbs + b) * K + k]);
             if (b >= p.nbins) {   // discarded rows (and the row of lanes without a pair)
                 if (p.weighted && p.wint) {
-                    for (int k = 0; k < WK; ++k)
-                        for (int q = 0; q < 3; ++q)
-                            take_i32<G>((int *)&wp[q * PLN + (size_t)b * WK + k]);
+                    for (int q = 0; q < 3 * WK; ++q) take_i32<G>((int *)&wp[(size_t)b * 3 * WK + q]);
                 } else if (p.weighted) {
                     for (int k = 0; k < K; ++k) take_u64<G>(&u[b * K + k]);
                 }
@@ -383,12 +380,12 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
                 double w = 0.0;
                 if (p.wint) {
                     // per lane copy: the exact sum of its products (below
-                    // 2^64) from its three 16-bit-piece planes
+                    // 2^64) from its record of three 16-bit-piece sums
                     for (int k = 0; k < WK; ++k) {
-                        const size_t e = (size_t)b * WK + k;
+                        const size_t e = ((size_t)b * WK + k) * 3;
                         const unsigned long long lo = (unsigned)take_i32<G>((int *)&wp[e]);
-                        const unsigned long long mid = (unsigned)take_i32<G>((int *)&wp[PLN + e]);
-                        const unsigned long long hi = (unsigned)take_i32<G>((int *)&wp[2 * PLN + e]);
+                        const unsigned long long mid = (unsigned)take_i32<G>((int *)&wp[e + 1]);
+                        const unsigned long long hi = (unsigned)take_i32<G>((int *)&wp[e + 2]);
                         w += (double)(lo + (mid << 16) + (hi << 32));
                     }
                     w *= wscale;
@@ -557,6 +554,15 @@ __device__ __forceinline__ void red_shared_u32_if(unsigned addr, bool on) {
 __device__ __forceinline__ void red_shared_u32(unsigned addr, unsigned v) {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
+// The three 16-bit pieces of an integer weight product into one lane copy's
+// record {lo, mid, hi} (immediate offsets from one address).
+__device__ __forceinline__ void red_shared_pieces(unsigned addr, unsigned long long p) {
+    asm volatile(
+        "red.shared.add.u32 [%0], %1;\n\t"
+        "red.shared.add.u32 [%0+4], %2;\n\t"
+        "red.shared.add.u32 [%0+8], %3;" ::"r"(addr),
+        "r"((unsigned)p & 0xFFFFu), "r"((unsigned)p >> 16), "r"((unsigned)(p >> 32)));
+}
 __device__ __forceinline__ void red_shared_f64_if(unsigned addr, double v, bool on) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p red.shared.add.f64 [%0], %1;\n\t}"
@@ -693,11 +699,11 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
     const unsigned hbase = hist_sa - hk4 * bias;
     const unsigned htrash = hist_sa + hk4 * (unsigned)p.trash_row;
     const unsigned wbase = whist_sa - 2u * hk4 * bias;
-    // integer weight planes: 4-byte entries, wint_k lane copies, planes PLB bytes apart
-    const unsigned wk4 = 4u * (unsigned)p.wint_k;
-    const unsigned wbase2 = whist_sa - wk4 * bias;
-    const unsigned wtrash = whist_sa + wk4 * (unsigned)p.trash_row;
-    const unsigned PLB = wk4 * (unsigned)p.nbins_smem;
+    // integer weights: a 12-byte record {lo, mid, hi} per bin and lane copy
+    // (word 3 (bin wint_k + copy) + piece: bank 3 copy + piece, conflict-free)
+    const unsigned wk12 = 12u * (unsigned)p.wint_k;
+    const unsigned wbase2 = whist_sa - wk12 * bias;
+    const unsigned wtrash = whist_sa + wk12 * (unsigned)p.trash_row;
     float2 NX[RI], NY[RI], NZ[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
@@ -779,21 +785,15 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                 } else if (W == 2) {
                     // exact 48-bit significand product, shifted down by both
                     // exponent offsets (truncation < 2^(k_i + k_j - 46) relative),
-                    // added as three 16-bit pieces to three u32 planes
+                    // added as three 16-bit pieces to the lane copy's record
                     const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
                     const unsigned mi = I.wm[r] & 0xFFFFFFu, ki = I.wm[r] >> 24;
                     const unsigned long long p0 =
                         ((unsigned long long)mi * (wj.x & 0xFFFFFFu)) >> (ki + (wj.x >> 24));
                     const unsigned long long p1 =
                         ((unsigned long long)mi * (wj.y & 0xFFFFFFu)) >> (ki + (wj.y >> 24));
-                    const unsigned w0 = a0 ? wbase2 + wk4 * b0 : wtrash;
-                    const unsigned w1 = a1 ? wbase2 + wk4 * b1 : wtrash;
-                    red_shared_u32(w0, (unsigned)p0 & 0xFFFFu);
-                    red_shared_u32(w0 + PLB, (unsigned)p0 >> 16);
-                    red_shared_u32(w0 + 2u * PLB, (unsigned)(p0 >> 32));
-                    red_shared_u32(w1, (unsigned)p1 & 0xFFFFu);
-                    red_shared_u32(w1 + PLB, (unsigned)p1 >> 16);
-                    red_shared_u32(w1 + 2u * PLB, (unsigned)(p1 >> 32));
+                    red_shared_pieces(a0 ? wbase2 + wk12 * b0 : wtrash, p0);
+                    red_shared_pieces(a1 ? wbase2 + wk12 * b1 : wtrash, p1);
                 }
                 re0[r] = in0[r] && n0;
                 re1[r] = in1[r] && n1;
@@ -842,10 +842,9 @@ __device__ __forceinline__ void pair_tile_sigpi2(const PairParams &p, Tile tb, i
     const unsigned hbase = hist_sa - hk4 * bias;
     const unsigned htrash = hist_sa + hk4 * (unsigned)p.trash_row;
     const unsigned wbase = whist_sa - 2u * hk4 * bias;
-    const unsigned wk4 = 4u * (unsigned)p.wint_k;
-    const unsigned wbase2 = whist_sa - wk4 * bias;
-    const unsigned wtrash = whist_sa + wk4 * (unsigned)p.trash_row;
-    const unsigned PLB = wk4 * (unsigned)p.nbins_smem;
+    const unsigned wk12 = 12u * (unsigned)p.wint_k;
+    const unsigned wbase2 = whist_sa - wk12 * bias;
+    const unsigned wtrash = whist_sa + wk12 * (unsigned)p.trash_row;
     float2 NX[RI], NY[RI], NZ[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
@@ -932,14 +931,8 @@ __device__ __forceinline__ void pair_tile_sigpi2(const PairParams &p, Tile tb, i
                         ((unsigned long long)mi * (wj.x & 0xFFFFFFu)) >> (ki + (wj.x >> 24));
                     const unsigned long long p1 =
                         ((unsigned long long)mi * (wj.y & 0xFFFFFFu)) >> (ki + (wj.y >> 24));
-                    const unsigned w0 = a0 ? wbase2 + wk4 * b0 : wtrash;
-                    const unsigned w1 = a1 ? wbase2 + wk4 * b1 : wtrash;
-                    red_shared_u32(w0, (unsigned)p0 & 0xFFFFu);
-                    red_shared_u32(w0 + PLB, (unsigned)p0 >> 16);
-                    red_shared_u32(w0 + 2u * PLB, (unsigned)(p0 >> 32));
-                    red_shared_u32(w1, (unsigned)p1 & 0xFFFFu);
-                    red_shared_u32(w1 + PLB, (unsigned)p1 >> 16);
-                    red_shared_u32(w1 + 2u * PLB, (unsigned)(p1 >> 32));
+                    red_shared_pieces(a0 ? wbase2 + wk12 * b0 : wtrash, p0);
+                    red_shared_pieces(a1 ? wbase2 + wk12 * b1 : wtrash, p1);
                 }
                 re0[r] = in0[r] && n0;
                 re1[r] = in1[r] && n1;
@@ -1074,7 +1067,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     if (smem_hist) {
         const int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
         for (int k = threadIdx.x; k < p.nbins_smem * copies; k += NT * G) s_hist[k] = 0;
-        if (W == 2) {   // the three integer weight planes
+        if (W == 2) {   // the integer weight records
             unsigned *wp = reinterpret_cast<unsigned *>(s_whist);
             for (int k = threadIdx.x; k < 3 * p.nbins_smem * p.wint_k; k += NT * G) wp[k] = 0u;
         } else if (W) {
@@ -1121,7 +1114,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
                              (p.priv ? (unsigned)((tid >> 5) * p.nbins_smem * p.hist_k * 4) : 0u) +
                              4u * lane_copy;
     const unsigned whist_sa = (unsigned)__cvta_generic_to_shared(s_whist) +
-                              (W == 2 ? 4u * (unsigned)(tid & (p.wint_k - 1)) : 8u * lane_copy);
+                              (W == 2 ? 12u * (unsigned)(tid & (p.wint_k - 1)) : 8u * lane_copy);
 
     const int nx = p.g.ng[0], ny = p.g.ng[1];
     const float c32x = p.g.c32[0], c32y = p.g.c32[1], c32z = p.g.c32[2];
@@ -1132,8 +1125,8 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     int cur_hist = -1;
     double cur_wscale = 0.0;
     // integer weights: before n more j-points, flush if a lane copy of the
-    // weight planes could exceed WINT_LIMIT products (NT / wint_k threads
-    // share a copy; each plane entry then stays below 2^16 x 2^16)
+    // weight records could exceed WINT_LIMIT products (NT / wint_k threads
+    // share a copy; each piece sum then stays below 2^16 x 2^16)
     auto wint_room = [&](int n) {
         if (W != 2) return;
         const unsigned long long add = (unsigned long long)(NT / p.wint_k) * RI * (unsigned)n;

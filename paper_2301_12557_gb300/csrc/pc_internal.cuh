@@ -21,7 +21,7 @@ constexpr int MAXSEG_T = 128;  // j segments per chunk of a tree list (nodes of 
                                // segments and their offsets fit the grid's segment space)
 constexpr int ROWCHUNK = 84;   // stencil rows per chunk (<= 3 segments each)
 static_assert(3 * ROWCHUNK + 1 <= MAXSEG, "a chunk's segments (and the own-cell rest) fit");
-constexpr int LQ = 256;        // rescue staging slots per CTA (per thread group)
+constexpr int LQ = 192;        // rescue staging slots per CTA (per thread group)
 constexpr int MAX_LUT = 8192;  // LUT entries per histogram axis
 
 enum { MODE_S = 0, MODE_SMU = 1, MODE_SIGPI = 2 };
@@ -122,11 +122,11 @@ struct PairParams {
     int nbins_smem;              // bins per shared copy: nbins, plus n_b with lin_norange
     // weighted sums from exact integer products of the packed binary32 weights
     // (significand product shifted by both exponent offsets, below 2^48),
-    // accumulated as three 16-bit pieces in three u32 planes of wint_k lane
-    // copies each, recombined exactly per copy and flushed as binary64 times
+    // accumulated as three 16-bit pieces in a record of three u32 sums per bin
+    // and lane copy, recombined exactly per copy and flushed as binary64 times
     // the task's wscale
     int wint;
-    int wint_k;              // lane copies of each integer weight plane (power of 2)
+    int wint_k;              // lane copies of the integer weight records (power of 2)
     // shared-histogram row that lanes without an in-range pair update (the
     // floor-bin kernels issue every reduction with the full warp); the flush
     // discards it like every row past nbins
