@@ -130,9 +130,10 @@ typedef struct {
     int wsum;                    /* weighted sums: 0 none; 1 binary64 products w_i w_j;
                                     2 exact products of binary32 significands accumulated
                                     as integers (evenly spaced bins, small histograms, every
-                                    weight a non-negative normal binary32 value or zero and
-                                    the two grids' weight exponents spanning at most 12;
-                                    truncation below 2^-34 relative), flushed in binary64 */
+                                    weight a non-negative normal binary32 value or zero, each
+                                    grid's weight exponents spanning at most 8 binades and
+                                    the two grids' spans adding up to at most 12; truncation
+                                    below 2^-34 relative), flushed in binary64 */
     long long tree_pairs;        /* pc_count_tree: list node pairs listed by the traversal */
     float ms_traverse;           /* pc_count_tree: device-and-host time of the traversal */
 } pc_stats;

@@ -554,7 +554,6 @@ struct CountJob {
 // relative, k the exponent offset of a weight below its grid's largest; the
 // exponent spans of the two grids are limited so that this stays below
 // 2^-34 (6e-11) per product and hence per bin.
-constexpr int WINT_MAX_SPAN = 12;
 static void job_add_wint(CountJob &J, const pc_grid *gi, const pc_grid *gj) {
     if (!gi->wint || !gj->wint ||
         (gi->wemax - gi->wemin) + (gj->wemax - gj->wemin) > WINT_MAX_SPAN)
@@ -1101,8 +1100,10 @@ static TaskDev task_of(const pc_grid *gi, const pc_grid *gj, int hist, int is_au
     t.hist = hist;
     t.is_auto = is_auto;
     // one unit of the integer weight products: 2^(emax_i + emax_j - 300)
-    // (w = M 2^(e - 150) with the 24-bit significand M and biased exponent e)
+    // (w = M 2^(e - 150) with the 24-bit significand M and biased exponent e);
+    // the packed significands' product is shifted down by both ranges
     t.wscale = (gi->wint && gj->wint) ? ldexp(1.0, gi->wemax + gj->wemax - 300) : 0.0;
+    t.wshift = (gi->wint && gj->wint) ? (gi->wemax - gi->wemin) + (gj->wemax - gj->wemin) : 0;
     return t;
 }
 
@@ -1222,6 +1223,7 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
     T.hist = 0;
     T.is_auto = is_auto ? 1 : 0;
     T.wscale = (t1->wint && tj->wint) ? ldexp(1.0, t1->wemax + tj->wemax - 300) : 0.0;
+    T.wshift = (t1->wint && tj->wint) ? (t1->wemax - t1->wemin) + (tj->wemax - tj->wemin) : 0;
     J.tasks.push_back(T);
     J.nhist = 1;
     J.is_auto = is_auto;
@@ -1346,6 +1348,7 @@ extern "C" pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const 
         T.hist = k;
         T.is_auto = 1;
         T.wscale = t->wint ? ldexp(1.0, 2 * t->wemax - 300) : 0.0;
+        T.wshift = t->wint ? 2 * (t->wemax - t->wemin) : 0;
         J.tasks.push_back(T);
         cb = std::max(cb, t->bext);
         for (int a = 0; a < 3; ++a) {

@@ -200,18 +200,21 @@ pc_status weight_stats(const void *w, int w_is_f32, int n, cudaStream_t st, int 
     return PC_OK;
 }
 
-// Packed integer weight (stored in the w lane of the FP32 point record):
-// bits 0-23 the binary32 significand M with its leading one (w = M 2^(e-150)),
-// bits 24-31 the shift emax - e.  Zero weights pack to 0.
-__device__ __forceinline__ unsigned pack_weight(double wv, int emax) {
+// Packed integer weight (stored in the w lane of the FP32 point record): the
+// binary32 significand M with its leading one (w = M 2^(e-150)), shifted up
+// by span - (emax - e) with span = emax - emin <= 8 the grid's exponent range,
+// so that it fits 32 bits and a pair's product needs one shift by a per-task
+// amount.  Zero weights pack to 0.
+__device__ __forceinline__ unsigned pack_weight(double wv, int emax, int span) {
     const unsigned b = __float_as_uint(__double2float_rn(wv));
     const int e = (int)((b >> 23) & 0xFF);
     if (e == 0) return 0u;
-    return ((unsigned)(emax - e) << 24) | (b & 0x7FFFFFu) | 0x800000u;
+    return ((b & 0x7FFFFFu) | 0x800000u) << (span - (emax - e));
 }
 
 __global__ void k_scatter(const double *__restrict__ xyz, const void *__restrict__ w, int w_is_f32,
-                          int wpack_emax, int n, Geom g, int sub_bits, const int *__restrict__ cell,
+                          int wpack_emax, int wpack_span, int n, Geom g, int sub_bits,
+                          const int *__restrict__ cell,
                           const int *__restrict__ slot, const int *__restrict__ key_start,
                           float4 *__restrict__ rel,
                           uint16_t *__restrict__ cxo, double4_32a *__restrict__ xw,
@@ -234,7 +237,7 @@ __global__ void k_scatter(const double *__restrict__ xyz, const void *__restrict
     }
     double wv = 1.0;
     if (w) wv = w_is_f32 ? (double)((const float *)w)[i] : ((const double *)w)[i];
-    const unsigned wp = (w && wpack_emax > 0) ? pack_weight(wv, wpack_emax) : 0u;
+    const unsigned wp = (w && wpack_emax > 0) ? pack_weight(wv, wpack_emax, wpack_span) : 0u;
     rel[pos] = make_float4(r[0], r[1], r[2], __uint_as_float(wp));
     cxo[pos] = (uint16_t)id[0];
     xw[pos] = make_double4_32a(x[0], x[1], x[2], wv);
@@ -612,7 +615,8 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
             delete g;
             return ws;
         }
-        if (res[0] == 0) {
+        // (the packed significands carry the exponent range: at most 8)
+        if (res[0] == 0 && (res[1] < 0 || res[1] - res[2] <= WINT_GRID_SPAN)) {
             g->wint = 1;
             g->wemax = res[1] >= 0 ? res[1] : 1;      // all zero: any exponent works
             g->wemin = res[1] >= 0 ? res[2] : 1;
@@ -661,7 +665,8 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     }
     if (e == cudaSuccess && n > 0) {
         int blocks = (int)((n + 255) / 256);
-        k_scatter<<<blocks, 256, 0, st>>>(dxyz, dw, w_is_f32, g->wint ? g->wemax : 0, (int)n, G,
+        k_scatter<<<blocks, 256, 0, st>>>(dxyz, dw, w_is_f32, g->wint ? g->wemax : 0,
+                                          g->wint ? g->wemax - g->wemin : 0, (int)n, G,
                                           sub_bits, cell, slot, key_start, g->rel, g->cx, g->xw,
                                           g->perm);
         note_launch();

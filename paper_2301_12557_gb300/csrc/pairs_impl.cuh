@@ -596,6 +596,7 @@ struct IPts {
     float xa[RI], ya[RI], za[RI];  // absolute positions (midpoint line of sight)
     double w[RI];
     unsigned wm[RI];               // packed integer weight (integer weight path)
+    unsigned wsh;                  // the task's product shift (integer weight path)
     int idx[RI];
 };
 
@@ -783,15 +784,14 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                     red_shared_f64_if(wbase + 2u * hk4 * b0, __dmul_rn(I.w[r], wj.x), a0);
                     red_shared_f64_if(wbase + 2u * hk4 * b1, __dmul_rn(I.w[r], wj.y), a1);
                 } else if (W == 2) {
-                    // exact 48-bit significand product, shifted down by both
-                    // exponent offsets (truncation < 2^(k_i + k_j - 46) relative),
-                    // added as three 16-bit pieces to the lane copy's record
+                    // (M_i M_j) >> (k_i + k_j), k = emax - e the exponent offset:
+                    // the packed M 2^(span - k) multiplied exactly in 64 bits and
+                    // shifted down by both spans (truncation < 2^(k_i + k_j - 46)
+                    // relative, below 2^48), added as three 16-bit pieces to the
+                    // lane copy's record
                     const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
-                    const unsigned mi = I.wm[r] & 0xFFFFFFu, ki = I.wm[r] >> 24;
-                    const unsigned long long p0 =
-                        ((unsigned long long)mi * (wj.x & 0xFFFFFFu)) >> (ki + (wj.x >> 24));
-                    const unsigned long long p1 =
-                        ((unsigned long long)mi * (wj.y & 0xFFFFFFu)) >> (ki + (wj.y >> 24));
+                    const unsigned long long p0 = ((unsigned long long)I.wm[r] * wj.x) >> I.wsh;
+                    const unsigned long long p1 = ((unsigned long long)I.wm[r] * wj.y) >> I.wsh;
                     red_shared_pieces(a0 ? wbase2 + wk12 * b0 : wtrash, p0);
                     red_shared_pieces(a1 ? wbase2 + wk12 * b1 : wtrash, p1);
                 }
@@ -926,11 +926,8 @@ __device__ __forceinline__ void pair_tile_sigpi2(const PairParams &p, Tile tb, i
                     red_shared_f64_if(wbase + 2u * hk4 * b1, __dmul_rn(I.w[r], wj.y), a1);
                 } else if (W == 2) {
                     const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
-                    const unsigned mi = I.wm[r] & 0xFFFFFFu, ki = I.wm[r] >> 24;
-                    const unsigned long long p0 =
-                        ((unsigned long long)mi * (wj.x & 0xFFFFFFu)) >> (ki + (wj.x >> 24));
-                    const unsigned long long p1 =
-                        ((unsigned long long)mi * (wj.y & 0xFFFFFFu)) >> (ki + (wj.y >> 24));
+                    const unsigned long long p0 = ((unsigned long long)I.wm[r] * wj.x) >> I.wsh;
+                    const unsigned long long p1 = ((unsigned long long)I.wm[r] * wj.y) >> I.wsh;
                     red_shared_pieces(a0 ? wbase2 + wk12 * b0 : wtrash, p0);
                     red_shared_pieces(a1 ? wbase2 + wk12 * b1 : wtrash, p1);
                 }
@@ -1146,7 +1143,8 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
         if (bidx >= nblocks) break;
         const Block B = p.blocks[bidx];
         const TaskDev &T = p.tasks[B.task];
-        if (T.hist != cur_hist || (W == 2 && T.wscale != cur_wscale)) {
+        if (T.hist != cur_hist || (W == 2 && T.wscale != cur_wscale)) {   // (a task's
+            // wshift is fixed by its grids, like wscale: no flush needed for it)
             flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
             cur_hist = T.hist;
             cur_wscale = T.wscale;
@@ -1160,6 +1158,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
         // thread t holds the block's points RI t .. RI t + RI - 1: a warp covers
         // 32 RI consecutive (sub-cell ordered, so spatially compact) points
         IPts<RI> I;
+        I.wsh = (unsigned)T.wshift;
 #pragma unroll
         for (int r = 0; r < RI; ++r) {
             const int loc = RI * tid + r;

@@ -23,6 +23,11 @@ constexpr int ROWCHUNK = 84;   // stencil rows per chunk (<= 3 segments each)
 static_assert(3 * ROWCHUNK + 1 <= MAXSEG, "a chunk's segments (and the own-cell rest) fit");
 constexpr int LQ = 192;        // rescue staging slots per CTA (per thread group)
 constexpr int MAX_LUT = 8192;  // LUT entries per histogram axis
+// integer weight path: largest exponent range of one catalogue's weights
+// (the packed significand M << range fits 32 bits), and of two catalogues'
+// ranges added (a product keeps 34 bits or more: truncation below 2^-34)
+constexpr int WINT_GRID_SPAN = 8;
+constexpr int WINT_MAX_SPAN = 12;
 
 enum { MODE_S = 0, MODE_SMU = 1, MODE_SIGPI = 2 };
 enum { LOS_Z = 0, LOS_MID = 1 };
@@ -44,6 +49,8 @@ struct TaskDev {
     int hist;
     int is_auto;
     double wscale;   // integer weight path: value of one unit of the product accumulators
+    int wshift;      // integer weight path: the two grids' exponent spans added (the
+                     // packed significands' product is shifted down by it)
 };
 
 // A block of consecutive i-points inside one cell.

@@ -346,17 +346,19 @@ __global__ void k_block_info(const double *__restrict__ box, const int2 *__restr
     atomicMax(ext_key, okey(e));
 }
 
-__device__ __forceinline__ unsigned pack_weight_t(double wv, int emax) {
+// Packed integer weight: the significand with its leading one shifted up by
+// span - (emax - e) (span = emax - emin <= 8), as on the grid path.
+__device__ __forceinline__ unsigned pack_weight_t(double wv, int emax, int span) {
     const unsigned b = __float_as_uint(__double2float_rn(wv));
     const int e = (int)((b >> 23) & 0xFF);
     if (e == 0) return 0u;
-    return ((unsigned)(emax - e) << 24) | (b & 0x7FFFFFu) | 0x800000u;
+    return ((b & 0x7FFFFFu) | 0x800000u) << (span - (emax - e));
 }
 
 // Point records in tree order: FP32 offset from the list node's centre (.w the
 // packed integer weight or 0), FP64 canonical coordinates and weight.
 __global__ void k_tree_scatter(const double *__restrict__ x, const void *__restrict__ w, int w_is_f32,
-                               int wpack_emax, const unsigned *__restrict__ perm,
+                               int wpack_emax, int wpack_span, const unsigned *__restrict__ perm,
                                const int *__restrict__ bid, const double *__restrict__ cen, int n,
                                float4 *__restrict__ rel, double4_32a *__restrict__ xw,
                                int *__restrict__ perm_out) {
@@ -372,7 +374,7 @@ __global__ void k_tree_scatter(const double *__restrict__ x, const void *__restr
     }
     double wv = 1.0;
     if (w) wv = w_is_f32 ? (double)((const float *)w)[p] : ((const double *)w)[p];
-    const unsigned wp = (w && wpack_emax > 0) ? pack_weight_t(wv, wpack_emax) : 0u;
+    const unsigned wp = (w && wpack_emax > 0) ? pack_weight_t(wv, wpack_emax, wpack_span) : 0u;
     rel[i] = make_float4(r[0], r[1], r[2], __uint_as_float(wp));
     xw[i] = make_double4_32a(v[0], v[1], v[2], wv);
     perm_out[i] = (int)p;
@@ -933,7 +935,7 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
         int r[3];
         pc_status s = weight_stats(dw, w_is_f32, (int)n, st, r);
         if (s != PC_OK) return bail(s);
-        if (r[0] == 0) {
+        if (r[0] == 0 && (r[1] < 0 || r[1] - r[2] <= WINT_GRID_SPAN)) {
             t->wint = 1;
             t->wemax = r[1] >= 0 ? r[1] : 1;
             t->wemin = r[1] >= 0 ? r[2] : 1;
@@ -1035,7 +1037,8 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
     if (e == cudaSuccess) {
         k_block_info<<<(nblk + 255) / 256, 256, 0, st>>>(t->nbox, t->vnode, blevel, t->bcen, t->brng, ext);
         note_launch();
-        k_tree_scatter<<<gpos, 256, 0, st>>>(x, dw, w_is_f32, t->wint ? t->wemax : 0, va, bid, t->bcen,
+        k_tree_scatter<<<gpos, 256, 0, st>>>(x, dw, w_is_f32, t->wint ? t->wemax : 0,
+                                             t->wint ? t->wemax - t->wemin : 0, va, bid, t->bcen,
                                              (int)n, t->rel, t->xw, t->perm);
         note_launch();
         e = cudaGetLastError();

@@ -1,12 +1,14 @@
 """The integer weight-product path's error bound (CPU, emulated).
 
-When every weight of both catalogues is a non-negative normal binary32 value
-(or zero) and the two catalogues' exponent spans add up to at most 12, the
-pair kernel accumulates each pair weight w_i w_j (Sect. 2.5) as an integer:
-the weight w = M 2^(e - 150) (M the 24-bit significand, e the biased
-exponent) is packed as M and k = e_max - e, a pair's product p = (M_i M_j) >> (k_i +
-k_j) (below 2^48) is added as three 16-bit pieces (p mod 2^16, bits 16-31,
-p >> 32) to three 32-bit lane counters (at most 2^16 products between
+When every weight of a catalogue is a non-negative normal binary32 value (or
+zero), its exponents span at most 8 binades, and the two catalogues' spans
+add up to at most 12, the pair kernel accumulates each pair weight w_i w_j
+(Sect. 2.5) as an integer.  The weight w = M 2^(e - 150) (M the 24-bit
+significand, e the biased exponent) is packed as M 2^(S - k), k = e_max - e
+and S = e_max - e_min the catalogue's span (below 2^32); a pair's product
+p = (packed_i packed_j) >> (S_i + S_j) equals (M_i M_j) >> (k_i + k_j)
+exactly (below 2^48).  It is added as three 16-bit pieces (p mod 2^16, bits
+16-31, p >> 32) to three 32-bit lane counters (at most 2^16 products between
 flushes, so no counter wraps), and a flush recombines each lane's counters
 into the exact 64-bit sum, converts it to binary64 and multiplies it by
 2^(e_max,i + e_max,j - 300).  The truncation of one product is below
@@ -24,20 +26,29 @@ F32 = np.float32
 WINT_LIMIT = 1 << 16
 
 
-def _pack(w, emax):
+def _pack(w, emax, emin):
+    """Packed weights M 2^(S - k) (below 2^32), and M and k for the check."""
     b = w.astype(F32).view(np.uint32).astype(np.int64)
     e = (b >> 23) & 0xFF
     m = np.where(e > 0, (b & 0x7FFFFF) | 0x800000, 0)
     k = np.where(e > 0, emax - e, 0)
-    return m, k, e
+    span = emax - emin
+    packed = [int(a) << int(span - kk) if a else 0 for a, kk in zip(m, k)]
+    assert max(packed, default=0) < 2 ** 32
+    return packed, m, k
 
 
-def _emulated_sum(wi, wj, emax_i, emax_j):
+def _emulated_sum(wi, wj, ext_i, ext_j):
     """The kernel's integer accumulation of sum_i w_i wj_i (pairs given as two
-    aligned arrays), flushed every WINT_LIMIT products, as binary64."""
-    mi, ki, _ = _pack(wi, emax_i)
-    mj, kj, _ = _pack(wj, emax_j)
-    prod = [(int(a) * int(b)) >> int(s) for a, b, s in zip(mi, mj, ki + kj)]
+    aligned arrays), flushed every WINT_LIMIT products, as binary64.  ext_* =
+    (e_max, e_min) of each catalogue."""
+    (emax_i, emin_i), (emax_j, emin_j) = ext_i, ext_j
+    pi, mi, ki = _pack(wi, emax_i, emin_i)
+    pj, mj, kj = _pack(wj, emax_j, emin_j)
+    shift = (emax_i - emin_i) + (emax_j - emin_j)
+    prod = [(a * b) >> shift for a, b in zip(pi, pj)]
+    # the same integer as the significands' product shifted by both offsets
+    assert prod == [(int(a) * int(b)) >> int(s) for a, b, s in zip(mi, mj, ki + kj)]
     assert max(prod, default=0) < 2 ** 48
     unit = 2.0 ** (emax_i + emax_j - 300)
     total = 0.0
@@ -63,11 +74,11 @@ def _weights(rng, n, e_lo, e_hi):
 
 def test_integer_products_within_two_to_minus_34():
     rng = np.random.default_rng(5)
-    for span_i, span_j in ((0, 0), (3, 3), (6, 6), (12, 0), (5, 7)):
+    for span_i, span_j in ((0, 0), (3, 3), (6, 6), (8, 4), (5, 7)):
         e0i, e0j = 120, 130
         wi = _weights(rng, 20000, e0i, e0i + span_i)
         wj = _weights(rng, 20000, e0j, e0j + span_j)
-        got = _emulated_sum(wi, wj, e0i + span_i, e0j + span_j)
+        got = _emulated_sum(wi, wj, (e0i + span_i, e0i), (e0j + span_j, e0j))
         exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(wi, wj))
         rel = abs(Fraction(got) - exact) / exact
         assert rel < Fraction(1, 2 ** 34), (span_i, span_j, float(rel))
@@ -78,7 +89,7 @@ def test_integer_products_within_two_to_minus_34():
     wj = _weights(rng, 20000, 130, 130)
     wi[0] = F32(2.0 ** (126 - 127))
     wj[0] = F32(2.0 ** (136 - 127))
-    got = _emulated_sum(wi, wj, 126, 136)
+    got = _emulated_sum(wi, wj, (126, 120), (136, 130))
     exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(wi, wj))
     rel = abs(Fraction(got) - exact) / exact
     assert Fraction(1, 2 ** 38) < rel < Fraction(1, 2 ** 34), float(rel)
@@ -93,7 +104,7 @@ def test_single_pair_truncation_reaches_the_bound():
     e = 134
     wi = np.array([(2 ** 23 + 4095) * 2.0 ** (e - 150)], dtype=F32)
     wj = np.array([(2 ** 23 + 4097) * 2.0 ** (e - 150)], dtype=F32)
-    got = _emulated_sum(wi, wj, emax_i, emax_j)
+    got = _emulated_sum(wi, wj, (emax_i, e), (emax_j, e))
     exact = Fraction(float(wi[0])) * Fraction(float(wj[0]))
     rel = float(abs(Fraction(got) - exact) / exact)
     assert 2.0 ** -35 < rel < 2.0 ** -34
