@@ -228,11 +228,15 @@ def oracle_sample_rate(D, w, seconds, seed=0, L=None, threads=None, wt=None):
             break
         m0 = min(n, m0 * 4)
     m = int(max(1, min(n, m0 * seconds / dt)))
+    # a multiple of the thread count: the oracle deals rows out round-robin,
+    # so every thread then gets the same number of rows
+    cores = threads or oracle.default_threads()
+    if m >= cores:
+        m = min(n, (m + cores - 1) // cores * cores)
     idx = rng.choice(n, m, replace=False)
     t = time.perf_counter()
     c, _ = run(idx)
     dt = time.perf_counter() - t
-    cores = threads or oracle.default_threads()
     in_range = int(c.sum()) - m        # each sampled point pairs with itself at s = 0
     return in_range / dt, dt, m, cores, m * n / dt
 
@@ -668,8 +672,9 @@ def run_batch(args):
 
     def step(xs=X, counts=out, batched=True):
         if tree:
-            ts = [P.pc_build_tree(x, box=box, n_leaf=args.n_leaf, list_cap=list_cap, stream=stream)
-                  for x in xs]
+            # every mock's k-d tree in one level loop
+            ts = P.pc_build_tree_batch(xs, box=box, n_leaf=args.n_leaf, list_cap=list_cap,
+                                       stream=stream)
         else:
             ts = [P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=opts, stream=stream)
                   for x in xs]
@@ -748,8 +753,9 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": w.name if m == w.extra["m"] else f"{w.name} ({m} mocks)",
                        "mocks": m, "n_total": int(n_tot),
-                       "structure": ("k-d tree (leaf capacity %d, list nodes %s), dual-tree "
-                                     "traversal per mock" % (args.n_leaf, list_cap or "auto"))
+                       "structure": ("k-d trees (leaf capacity %d, list nodes %s) built in one "
+                                     "batched level loop, dual-tree traversal per mock"
+                                     % (args.n_leaf, list_cap or "auto"))
                                     if tree else "regular grid",
                        "cell_size": cell, "ipt": opts.ipt,
                        "priv": opts.priv, "tuning": tuning,
@@ -1041,6 +1047,44 @@ def run_sets(args, extra=None):
                                                  f"({cand64:.4g}) + {FLOPS_PER_IN_RANGE} per "
                                                  f"in-range pair ({inr64:.4g})"}}
 
+    # ---- the k-d tree path on the same catalogues (grid line only) ----------
+    kd = None
+    if not tree and args.tree_steps > 0 and world == 1:
+        t0 = time.perf_counter()
+        o_kd, cap_kd, _ = P.pc_tune_tree(devc[big][0], devc[big][1], box=box, bins=bins,
+                                         n_leaf=args.n_leaf, stream=stream)
+        tune_s = time.perf_counter() - t0
+        rkd = {k: (torch.zeros_like(outs[k][0]), torch.zeros_like(outs[k][1])) for k in kinds}
+        list_cap_saved = list_cap
+        list_cap = cap_kd
+        step(results=rkd, o=o_kd, structure="kdtree")
+        torch.cuda.synchronize()
+        kd_ms = []
+        nkd = min(args.tree_steps, 2)
+        for _ in range(nkd):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(results=rkd, o=o_kd, structure="kdtree")
+            b.record(stream)
+            torch.cuda.synchronize()
+            kd_ms.append(a.elapsed_time(b))
+        list_cap = list_cap_saved
+        same = all(bool(torch.equal(rkd[k][0], outs[k][0])) for k in kinds)
+        kwd = 0.0
+        if weighted:
+            for k in kinds:
+                ref = outs[k][1].abs().clamp_min(1e-300)
+                kwd = max(kwd, float(((rkd[k][1] - outs[k][1]).abs() / ref).max().item()))
+        kd = {"value": float(sum(rkd[k][0].sum().item() for k in kinds)) / (statistics.mean(kd_ms) * 1e-3),
+              "unit": UNIT, "ms_per_step": statistics.mean(kd_ms), "steps": nkd,
+              "ms_build": statistics.mean(tree_ms[-nkd:]),
+              "step": "tree build + dual-tree traversal + pair kernel (weight products and near-edge "
+                      "pairs as on the grid)",
+              "list_cap": cap_kd or "auto", "ipt": o_kd.ipt, "n_leaf": args.n_leaf,
+              "tuning_seconds": tune_s, "counts_identical_to_grid": same,
+              "weighted_max_rel_diff_vs_grid": kwd if weighted else None}
+
     # ---- roofline of the dominant kernel -------------------------------------
     kdom = max(kinds, key=lambda k: stats[k].ms_pairs)
     sd = stats[kdom]
@@ -1128,6 +1172,7 @@ def run_sets(args, extra=None):
                              "ms_traverse": stats[k].ms_traverse if tree else None,
                              "prec": "f32+rescue" if stats[k].prec == 0 else "f64"} for k in kinds},
             "fp64_path": fp64,
+            "kdtree_path": kd,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "roofline": roofline,
             "measured_peaks": {k: v for k, v in peaks.items() if k != "how"},

@@ -285,6 +285,29 @@ pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f32, long lon
                         const pc_box *box, int n_leaf, int list_cap, void *stream,
                         pc_tree **out);
 
+/* The k-d trees of m catalogues built together (Sect. 2.2, Alg. 1): one level
+ * loop over all of them -- one pass of node statistics, one key pass and one
+ * radix sort per level for every tree still being split -- instead of m
+ * loops, for batches of many small catalogues (mocks).  Each tree is the one
+ * pc_build_tree gives (the same node ranges, boxes and split axes, up to the
+ * rounding of the node statistics on an exact variance tie) and is released
+ * with pc_free_tree.
+ *   xyz[k], w[k], n[k]    catalogue k as for pc_build_tree (host or device);
+ *                         w NULL, or weights for every catalogue (all binary32
+ *                         if w_is_f32, else all binary64)
+ *   m                     number of catalogues, 1..65536
+ *   box, n_leaf, list_cap as for pc_build_tree, shared by all trees
+ *   stream                cudaStream_t; returns once every tree is built
+ *   out                   m entries: out[k] receives catalogue k's tree (all
+ *                         NULL on error)
+ * Errors: PC_EINVAL (NULL pointers, m < 1, a catalogue without points,
+ * weights for some catalogues only, bad n_leaf, list_cap or box, non-finite
+ * coordinates), PC_EOVERFLOW (more than 2^31 points in all, more than 2^28
+ * heap slots in one tree, m > 65536), PC_ENOMEM, PC_ECUDA. */
+pc_status pc_build_tree_batch(const double *const *xyz, const void *const *w, int w_is_f32,
+                              const long long *n, int m, const pc_box *box, int n_leaf,
+                              int list_cap, void *stream, pc_tree **out);
+
 /* Release a tree (NULL is ignored). */
 void pc_free_tree(pc_tree *t);
 

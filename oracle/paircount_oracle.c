@@ -186,8 +186,8 @@ static void *brute_worker(void *arg)
 {
     job *jb = (job *)arg;
     /* rows are dealt out in chunks of up to 64, fewer when the rows are few,
-     * so that every thread gets some */
-    int64_t CH = jb->n1 / ((int64_t)jb->nthreads * 4);
+     * so that every thread gets an equal share */
+    int64_t CH = jb->n1 / ((int64_t)jb->nthreads * 16);
     if (CH > 64) CH = 64;
     if (CH < 1) CH = 1;
     for (int64_t c0 = (int64_t)jb->tid * CH; c0 < jb->n1; c0 += (int64_t)jb->nthreads * CH) {

@@ -76,7 +76,7 @@ EXPORTS = ["pc_build_grid", "pc_free_grid", "pc_grid_info", "pc_count_auto", "pc
            "pc_version", "pc_launch_count", "pc_count_auto_noalloc", "pc_tune",
            "pc_build_tree", "pc_free_tree", "pc_tree_info", "pc_tree_export", "pc_count_tree",
            "pc_tune_tree", "pc_hist_s2", "pc_count_tree_batch", "pc_stencil", "pc_fp32_bands",
-           "pc_fp32_tables", "pc_fp_peak", "pc_alloc_count"]
+           "pc_fp32_tables", "pc_fp_peak", "pc_alloc_count", "pc_build_tree_batch"]
 
 
 def library_path() -> str:
@@ -139,6 +139,9 @@ def lib():
     L.pc_build_tree.restype = c_int
     L.pc_build_tree.argtypes = [vp, vp, c_int, c_longlong, POINTER(pc_box), c_int, c_int, vp,
                                 POINTER(vp)]
+    L.pc_build_tree_batch.restype = c_int
+    L.pc_build_tree_batch.argtypes = [POINTER(vp), POINTER(vp), c_int, POINTER(c_longlong), c_int,
+                                      POINTER(pc_box), c_int, c_int, vp, POINTER(vp)]
     L.pc_free_tree.restype = None
     L.pc_free_tree.argtypes = [vp]
     L.pc_tree_info.restype = c_int
@@ -499,6 +502,42 @@ def pc_build_tree(xyz, w=None, *, box: pc_box, n_leaf: int = 32, list_cap: int =
            "pc_build_tree")
     del keep_x, keep_w
     return Tree(out, n)
+
+
+def pc_build_tree_batch(xyzs, ws=None, *, box: pc_box, n_leaf: int = 32, list_cap: int = 0,
+                        stream=None) -> list:
+    """The k-d trees of many catalogues built in one level loop (see
+    paircount.h); returns one Tree per catalogue, in order."""
+    m = len(xyzs)
+    if m == 0:
+        return []
+    px, keep, ns = [], [], []
+    for x in xyzs:
+        p, k, n = _ptr(x, np.float64, 3)
+        px.append(p)
+        keep.append(k)
+        ns.append(n)
+    pw, w_is_f32 = None, 0
+    if ws is not None:
+        if len(ws) != m:
+            raise ValueError("one weight array per catalogue")
+        pw = []
+        flags = set()
+        for w, n in zip(ws, ns):
+            p, k, f = _weights_arg(w, n)
+            pw.append(p)
+            keep.append(k)
+            flags.add(f)
+        if len(flags) != 1:
+            raise ValueError("weights must be all binary32 or all binary64")
+        w_is_f32 = flags.pop()
+        pw = (c_void_p * m)(*pw)
+    out = (c_void_p * m)()
+    _check(lib().pc_build_tree_batch((c_void_p * m)(*px), pw, w_is_f32, (c_longlong * m)(*ns), m,
+                                     ctypes.byref(box), int(n_leaf), int(list_cap),
+                                     _stream_handle(stream), out), "pc_build_tree_batch")
+    del keep
+    return [Tree(c_void_p(out[k]), ns[k]) for k in range(m)]
 
 
 def pc_tune_tree(xyz, w=None, *, box: pc_box, bins: Bins, n_leaf: int = 32,

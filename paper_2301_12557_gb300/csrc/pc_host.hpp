@@ -55,6 +55,14 @@ struct pc_tree {
     signed char *naxis;         // split axis per slot, -1: leaf or empty
     double *bcen;               // list node centres, 3 per node
     int2 *brng;                 // list node ranges {start, count}
+    // trees of one batched build carve their arrays from one shared device
+    // block, freed with the last of them (null: arrays allocated one by one)
+    struct TreeArena *arena = nullptr;
+};
+
+struct TreeArena {
+    void *p = nullptr;
+    int refs = 0;
 };
 
 namespace pc {

@@ -198,15 +198,20 @@ __device__ __forceinline__ void acc_add(NodeAcc *A, const double *s, const doubl
 // Statistics of the level's nodes: a warp takes 256 consecutive positions
 // (nid, the node of each position at this level, never decreases along the
 // positions).  A warp inside one node sums in registers and adds once; a
-// warp that spans nodes reduces each round of 32 by node segments.
+// warp that spans nodes reduces each round of 32 by node segments.  Sums are
+// taken about `shift` (the tree's box centre); a forest of trees passes one
+// centre per tree and the tree of every position (tpos), null otherwise.
 __global__ void k_node_stats(const double *__restrict__ x, const unsigned *__restrict__ perm,
-                             const int *__restrict__ nid, int n, double3 shift, NodeAcc *acc) {
+                             const int *__restrict__ nid, int n, double3 shift, NodeAcc *acc,
+                             const double3 *__restrict__ tshift = nullptr,
+                             const int *__restrict__ tpos = nullptr) {
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const long long base = gw * 256;
     if (base >= n) return;
     const long long last = min(base + 255, (long long)n - 1);
     const int n0 = nid[base], n1 = nid[last];
+    if (tpos) shift = tshift[tpos[min(base + lane, last)]];   // one node: one tree
     const double sh[3] = {shift.x, shift.y, shift.z};
     if (n0 == n1) {
         double s[3] = {0, 0, 0}, q[3] = {0, 0, 0};
@@ -242,9 +247,12 @@ __global__ void k_node_stats(const double *__restrict__ x, const unsigned *__res
         long long mn[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, mx[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
         if (ok) {
             const unsigned p = perm[i];
+            double3 shi = shift;
+            if (tpos) shi = tshift[tpos[i]];
+            const double shl[3] = {shi.x, shi.y, shi.z};
             for (int d = 0; d < 3; ++d) {
                 const double v = x[3 * (size_t)p + d];
-                const double t = v - sh[d];
+                const double t = v - shl[d];
                 s[d] = t;
                 q[d] = t * t;
                 mn[d] = mx[d] = okey(v);
@@ -361,7 +369,7 @@ __global__ void k_tree_scatter(const double *__restrict__ x, const void *__restr
                                int wpack_emax, int wpack_span, const unsigned *__restrict__ perm,
                                const int *__restrict__ bid, const double *__restrict__ cen, int n,
                                float4 *__restrict__ rel, double4_32a *__restrict__ xw,
-                               int *__restrict__ perm_out) {
+                               int *__restrict__ perm_out, unsigned pbase = 0u) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const unsigned p = perm[i];
@@ -377,7 +385,7 @@ __global__ void k_tree_scatter(const double *__restrict__ x, const void *__restr
     const unsigned wp = (w && wpack_emax > 0) ? pack_weight_t(wv, wpack_emax, wpack_span) : 0u;
     rel[i] = make_float4(r[0], r[1], r[2], __uint_as_float(wp));
     xw[i] = make_double4_32a(v[0], v[1], v[2], wv);
-    perm_out[i] = (int)p;
+    perm_out[i] = (int)(p - pbase);   // index into the tree's own input
 }
 
 // Levels below the root until every node holds at most cap points.
@@ -777,6 +785,14 @@ using namespace pc;
 
 static void tree_release(pc_tree *t) {
     if (!t) return;
+    if (t->arena) {   // arrays carved from a batch's shared block
+        if (--t->arena->refs == 0) {
+            cudaFree(t->arena->p);
+            delete t->arena;
+        }
+        delete t;
+        return;
+    }
     cudaFree(t->rel);
     cudaFree(t->xw);
     cudaFree(t->perm);
@@ -1058,5 +1074,424 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
     }
     cleanup();
     *out = t;
+    return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched build: the k-d trees of many catalogues in one level loop
+// ---------------------------------------------------------------------------
+// The catalogues' points are laid end to end, the deepest tree first, so the
+// trees still being split at level d are a prefix of the arrays.  At level d
+// tree r (its rank in that order) owns the global node ids r 2^d .. r 2^d +
+// 2^d - 1; id g's children are 2g and 2g + 1, so one set of node
+// statistics, one key pass and one radix sort per level serve every tree,
+// and each tree ends with the same node ranges, boxes and split axes as its
+// own build (statistics summed in another order may break an exact variance
+// tie the other way: a different but equally valid median split).
+namespace pc {
+
+struct FTree {
+    int2 *vnode, *node;
+    double *nbox;
+    signed char *naxis;
+    long long pos;     // first position of the tree's points
+    int n, n_leaf, depth, blevel;
+};
+
+__global__ void k_fnode_finish(const NodeAcc *__restrict__ acc, int level, int ntrees,
+                               const FTree *__restrict__ ft) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ((long long)ntrees << level)) return;
+    const FTree &T = ft[g >> level];
+    const long long h = (1LL << level) - 1 + (g & ((1LL << level) - 1));
+    const int2 nd = T.node[h];
+    if (nd.y < 0) return;
+    const NodeAcc A = acc[g];
+    for (int d = 0; d < 3; ++d) {
+        T.nbox[6 * h + d] = unokey(A.mn[d]);
+        T.nbox[6 * h + 3 + d] = unokey(A.mx[d]);
+    }
+    int best = -1;
+    if (nd.y > T.n_leaf) {
+        double bv = -1.0;
+        for (int d = 0; d < 3; ++d) {
+            const double v = A.q[d] - A.s[d] * A.s[d] / (double)nd.y;
+            if (v > bv) {
+                bv = v;
+                best = d;
+            }
+        }
+    }
+    T.naxis[h] = (signed char)best;
+}
+
+// Sort keys of level d over the trees being split: the global node id on
+// the high d + rbits bits (rbits: enough for the number of trees), the
+// coordinate along the node's split axis below.
+__global__ void k_ftree_keys(const double *__restrict__ x, const unsigned *__restrict__ perm,
+                             const int *__restrict__ nid, long long n, int level, int rbits,
+                             const FTree *__restrict__ ft, unsigned long long *__restrict__ keys) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int g = nid[i];
+    const FTree &T = ft[g >> level];
+    const long long h = (1LL << level) - 1 + (g & ((1 << level) - 1));
+    const int ax = T.naxis[h];
+    const int hb = level + rbits;
+    unsigned long long ck = 0ull;
+    if (ax >= 0) ck = ukey(x[3 * (size_t)perm[i] + ax]) >> hb;
+    keys[i] = hb ? (((unsigned long long)g << (64 - hb)) | ck) : ck;
+}
+
+// Global node of each position one level down.
+__global__ void k_fnid_next(const FTree *__restrict__ ft, long long n, int level, int *__restrict__ nid) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int g = nid[i];
+    const FTree &T = ft[g >> level];
+    const int2 v = T.vnode[(1LL << level) - 1 + (g & ((1 << level) - 1))];
+    nid[i] = 2 * g + ((int)(i - T.pos - v.x) >= v.y / 2 ? 1 : 0);
+}
+
+// List node (local to its tree) of the positions of trees whose list level is d.
+__global__ void k_fbid(const int *__restrict__ nid, const int *__restrict__ tpos, long long n, int level,
+                       const FTree *__restrict__ ft, int *__restrict__ bid) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (ft[tpos[i]].blevel == level) bid[i] = nid[i] & ((1 << level) - 1);
+}
+
+// Slot ranges of level d by the halving rule, for the trees with a level d
+// (global node g = r 2^d + k): level 0 is the root {0, n}; a slot's children
+// are present while it holds more than n_leaf points.
+__global__ void k_fslots(int level, int ntrees, const FTree *__restrict__ ft) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ((long long)ntrees << level)) return;
+    const FTree &T = ft[g >> level];
+    if (level == 0) {
+        T.vnode[0] = make_int2(0, T.n);
+        T.node[0] = T.vnode[0];
+        return;
+    }
+    const long long k = g & ((1LL << level) - 1);
+    const long long h = (1LL << level) - 1 + k;
+    const long long hp = (1LL << (level - 1)) - 1 + (k >> 1);
+    const int2 v = T.vnode[hp];
+    const int2 c = (k & 1) ? make_int2(v.x + v.y / 2, v.y - v.y / 2) : make_int2(v.x, v.y / 2);
+    T.vnode[h] = c;
+    T.node[h] = T.node[hp].y > T.n_leaf ? c : make_int2(0, -1);
+}
+
+// Canonical coordinates in place (periodic: folded into [0, L)).
+__global__ void k_fcanon(double *x, long long n3, Geom g) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3 || !g.periodic) return;
+    x[i] = canon_t(x[i], g.L[i % 3]);
+}
+
+__global__ void k_fill_int(int *__restrict__ a, long long n0, long long n1, int v) {
+    const long long i = n0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n1) a[i] = v;
+}
+
+}  // namespace pc
+
+extern "C" pc_status pc_build_tree_batch(const double *const *xyz, const void *const *w, int w_is_f32,
+                                         const long long *n, int m, const pc_box *box, int n_leaf,
+                                         int list_cap, void *stream, pc_tree **out) {
+    std::lock_guard<std::mutex> lk(api_mutex());
+    if (!out || !xyz || !n || !box || m < 1)
+        return fail(PC_EINVAL, "pc_build_tree_batch: bad arguments");
+    for (int k = 0; k < m; ++k) out[k] = nullptr;
+    if (m > (1 << 16)) return fail(PC_EOVERFLOW, "pc_build_tree_batch: more than 65536 catalogues");
+    if (n_leaf < 1 || n_leaf > 128)
+        return fail(PC_EINVAL, "pc_build_tree_batch: n_leaf must lie in [1, 128]");
+    if (list_cap != 0 && (list_cap < TREE_BLOCK || list_cap > 65536 || (list_cap & (list_cap - 1))))
+        return fail(PC_EINVAL, "pc_build_tree_batch: list_cap must be 0 or a power of two in [256, 65536]");
+    const bool weighted = w && w[0];
+    long long N = 0;
+    for (int k = 0; k < m; ++k) {
+        if (!xyz[k] || n[k] < 1) return fail(PC_EINVAL, "pc_build_tree_batch: every catalogue needs points");
+        if (weighted != (w && w[k] != nullptr))
+            return fail(PC_EINVAL, "pc_build_tree_batch: weights for all catalogues or none");
+        N += n[k];
+    }
+    if (N >= (1LL << 31) - 1) return fail(PC_EOVERFLOW, "pc_build_tree_batch: more than 2^31 points");
+    Geom G0{};
+    G0.periodic = box->periodic ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+        if (G0.periodic) {
+            if (!(box->L[a] > 0.0) || !isfinite(box->L[a]))
+                return fail(PC_EINVAL, "pc_build_tree_batch: periodic box needs L > 0 on every axis");
+            G0.L[a] = box->L[a];
+            G0.hL[a] = 0.5 * box->L[a];
+        }
+        G0.ng[a] = 1;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    PC_CUDA(cudaGetDevice(&dev));
+
+    // the deepest tree first; positions end to end in that order
+    std::vector<int> depth(m), blev(m), ord(m);
+    int dmax = 0;
+    for (int k = 0; k < m; ++k) {
+        depth[k] = tree_depth(n[k], n_leaf);
+        blev[k] = std::min(list_level(n[k], list_cap), depth[k]);
+        if (depth[k] > 27) return fail(PC_EOVERFLOW, "pc_build_tree_batch: more than 2^28 tree slots");
+        dmax = std::max(dmax, depth[k]);
+        ord[k] = k;
+    }
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return depth[a] > depth[b]; });
+    std::vector<long long> pos(m + 1, 0);
+    for (int r = 0; r < m; ++r) pos[r + 1] = pos[r] + n[ord[r]];
+
+    std::vector<pc_tree *> trees(m, nullptr);
+    std::vector<void *> tmp;
+    auto talloc = [&](void **p, size_t bytes) {
+        cudaError_t e = ::pc::alloc_dev_async(p, std::max<size_t>(bytes, 16), st);
+        if (e == cudaSuccess) tmp.push_back(*p);
+        return e;
+    };
+    auto bail = [&](pc_status s) {
+        for (void *p : tmp) cudaFreeAsync(p, st);
+        cudaStreamSynchronize(st);
+        for (pc_tree *t : trees) tree_release(t);
+        return s;
+    };
+
+    // the points end to end (canonical), the weights likewise, the tree of
+    // every position
+    double *x = nullptr;
+    void *wall = nullptr;
+    int *tpos = nullptr;
+    const size_t wsz = w_is_f32 ? sizeof(float) : sizeof(double);
+    cudaError_t e = talloc((void **)&x, sizeof(double) * 3 * (size_t)N);
+    if (e == cudaSuccess && weighted) e = talloc(&wall, wsz * (size_t)N);
+    if (e == cudaSuccess) e = talloc((void **)&tpos, sizeof(int) * (size_t)N);
+    for (int r = 0; e == cudaSuccess && r < m; ++r) {
+        const int k = ord[r];
+        e = cudaMemcpyAsync(x + 3 * pos[r], xyz[k], sizeof(double) * 3 * n[k],
+                            is_device_ptr(xyz[k]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && weighted)
+            e = cudaMemcpyAsync((char *)wall + wsz * pos[r], w[k], wsz * n[k],
+                                is_device_ptr(w[k]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            k_fill_int<<<(unsigned)((n[k] + 255) / 256), 256, 0, st>>>(tpos, pos[r], pos[r + 1], r);
+            note_launch();
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) {
+        k_fcanon<<<(unsigned)((3 * N + 255) / 256), 256, 0, st>>>(x, 3 * N, G0);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return bail(cuda_fail(e, "pc_build_tree_batch: inputs"));
+
+    // every tree: bounds and weights; its arrays carved from one device block
+    // shared by the batch (freed with the last tree)
+    std::vector<FTree> ft(m);
+    std::vector<double3> shifts(m);
+    if (G0.periodic) {   // one bounds pass over the forest: finite coordinates
+        double plo[3], phi[3];
+        pc_status s = aabb_device(x, N, st, plo, phi, nullptr);
+        if (s != PC_OK) return bail(s);
+        for (int a = 0; a < 3; ++a)
+            if (!isfinite(plo[a]) || !isfinite(phi[a]))
+                return bail(fail(PC_EINVAL, "pc_build_tree_batch: non-finite coordinates"));
+    }
+    auto carve = [](size_t bytes) { return (bytes + 255) / 256 * 256; };
+    size_t total = 0;
+    for (int r = 0; r < m; ++r) {
+        const int k = ord[r];
+        const size_t ns = ((size_t)2 << depth[k]) - 1, nb = (size_t)1 << blev[k], nk = (size_t)n[k];
+        total += carve(sizeof(int2) * ns) * 2 + carve(sizeof(double) * 6 * ns) + carve(ns) +
+                 carve(sizeof(float4) * nk) + carve(sizeof(double4_32a) * nk) + carve(sizeof(int) * nk) +
+                 carve(sizeof(double) * 3 * nb) + carve(sizeof(int2) * nb);
+    }
+    TreeArena *arena = new TreeArena();
+    e = ::pc::alloc_dev(&arena->p, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete arena;
+        return bail(fail(PC_ENOMEM, "pc_build_tree_batch: device allocation failed"));
+    }
+    char *cur = (char *)arena->p;
+    auto take = [&](size_t bytes) {
+        char *p = cur;
+        cur += carve(bytes);
+        return (void *)p;
+    };
+    for (int r = 0; r < m; ++r) {
+        const int k = ord[r];
+        pc_tree *t = new pc_tree();
+        memset(static_cast<void *>(t), 0, sizeof(*t));
+        trees[r] = t;
+        t->arena = arena;
+        arena->refs += 1;
+        t->device = dev;
+        t->n = (int)n[k];
+        t->weighted = weighted ? 1 : 0;
+        t->n_leaf = n_leaf;
+        t->depth = depth[k];
+        t->blevel = blev[k];
+        t->lmax = (int)level_largest(n[k], blev[k]);
+        t->nslots = (2LL << depth[k]) - 1;
+        t->g = G0;
+        const size_t ns = (size_t)t->nslots, nb = (size_t)1 << blev[k];
+        t->vnode = (int2 *)take(sizeof(int2) * ns);
+        t->node = (int2 *)take(sizeof(int2) * ns);
+        t->nbox = (double *)take(sizeof(double) * 6 * ns);
+        t->naxis = (signed char *)take(ns);
+        t->rel = (float4 *)take(sizeof(float4) * n[k]);
+        t->xw = (double4_32a *)take(sizeof(double4_32a) * n[k]);
+        t->perm = (int *)take(sizeof(int) * n[k]);
+        t->bcen = (double *)take(sizeof(double) * 3 * nb);
+        t->brng = (int2 *)take(sizeof(int2) * nb);
+        const double *xs = x + 3 * pos[r];
+        pc_status s = PC_OK;
+        if (G0.periodic) {
+            for (int a = 0; a < 3; ++a) { t->pts_lo[a] = 0.0; t->pts_hi[a] = G0.L[a]; }
+        } else {
+            double plo[3], phi[3];
+            s = aabb_device(xs, n[k], st, plo, phi, &t->r2min);
+            if (s != PC_OK) return bail(s);
+            for (int a = 0; a < 3; ++a) {
+                if (!isfinite(plo[a]) || !isfinite(phi[a]))
+                    return bail(fail(PC_EINVAL, "pc_build_tree_batch: non-finite coordinates"));
+                t->pts_lo[a] = plo[a];
+                t->pts_hi[a] = phi[a];
+            }
+        }
+        for (int a = 0; a < 3; ++a) t->g.lo[a] = t->pts_lo[a];
+        shifts[r] = make_double3(0.5 * (t->pts_lo[0] + t->pts_hi[0]), 0.5 * (t->pts_lo[1] + t->pts_hi[1]),
+                                 0.5 * (t->pts_lo[2] + t->pts_hi[2]));
+        if (weighted) {
+            int res[3];
+            s = weight_stats((const char *)wall + wsz * pos[r], w_is_f32, (int)n[k], st, res);
+            if (s != PC_OK) return bail(s);
+            if (res[0] == 0 && (res[1] < 0 || res[1] - res[2] <= WINT_GRID_SPAN)) {
+                t->wint = 1;
+                t->wemax = res[1] >= 0 ? res[1] : 1;
+                t->wemin = res[1] >= 0 ? res[2] : 1;
+            }
+        }
+        e = cudaMemsetAsync(t->naxis, 0xFF, ns, st);   // -1: leaf or empty
+        if (e == cudaSuccess) e = cudaMemsetAsync(t->nbox, 0, sizeof(double) * 6 * ns, st);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "pc_build_tree_batch: tree arrays"));
+        ft[r] = FTree{t->vnode, t->node, t->nbox, t->naxis, pos[r], (int)n[k], n_leaf, depth[k], blev[k]};
+    }
+
+    // trees still being split at each level (a prefix of the rank order)
+    std::vector<int> active(dmax + 2, 0);
+    for (int d = 0; d <= dmax + 1; ++d)
+        while (active[d] < m && depth[ord[active[d]]] >= d) ++active[d];
+    long long acc_n = 1;
+    for (int d = 0; d <= dmax; ++d) acc_n = std::max(acc_n, (long long)active[d] << d);
+
+    FTree *dft = nullptr;
+    double3 *dshift = nullptr;
+    unsigned long long *ka = nullptr, *kb = nullptr;
+    unsigned *va = nullptr, *vb = nullptr;
+    int *nid = nullptr, *bid = nullptr, *cnt = nullptr, *off = nullptr, *tot = nullptr;
+    NodeAcc *acc = nullptr;
+    long long *ext = nullptr;
+    const int ntiles = (int)((N + RS_TILE - 1) / RS_TILE);
+    const size_t ncnt = (size_t)256 * ntiles + 1;
+    e = talloc((void **)&dft, sizeof(FTree) * m);
+    if (e == cudaSuccess) e = talloc((void **)&dshift, sizeof(double3) * m);
+    if (e == cudaSuccess) e = talloc((void **)&ka, sizeof(unsigned long long) * N);
+    if (e == cudaSuccess) e = talloc((void **)&kb, sizeof(unsigned long long) * N);
+    if (e == cudaSuccess) e = talloc((void **)&va, sizeof(unsigned) * N);
+    if (e == cudaSuccess) e = talloc((void **)&vb, sizeof(unsigned) * N);
+    if (e == cudaSuccess) e = talloc((void **)&nid, sizeof(int) * N);
+    if (e == cudaSuccess) e = talloc((void **)&bid, sizeof(int) * N);
+    if (e == cudaSuccess) e = talloc((void **)&cnt, sizeof(int) * ncnt);
+    if (e == cudaSuccess) e = talloc((void **)&off, sizeof(int) * ncnt);
+    if (e == cudaSuccess) e = talloc((void **)&tot, sizeof(int) * (ncnt / 4096 + 2));
+    if (e == cudaSuccess) e = talloc((void **)&acc, sizeof(NodeAcc) * acc_n);
+    if (e == cudaSuccess) e = talloc((void **)&ext, sizeof(long long) * m);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PC_ENOMEM, "pc_build_tree_batch: device allocation failed"));
+    }
+    e = cudaMemcpyAsync(dft, ft.data(), sizeof(FTree) * m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dshift, shifts.data(), sizeof(double3) * m, cudaMemcpyHostToDevice, st);
+    const unsigned gall = (unsigned)((N + 255) / 256);
+    if (e == cudaSuccess) {
+        k_iota<<<gall, 256, 0, st>>>(va, (int)N);
+        note_launch();
+        e = cudaMemcpyAsync(nid, tpos, sizeof(int) * N, cudaMemcpyDeviceToDevice, st);   // level 0: id = rank
+    }
+    int rbits = 0;
+    for (int d = 0; e == cudaSuccess && d <= dmax; ++d) {
+        const int A = active[d];                  // trees with a level d
+        const long long nA = pos[A];              // their positions
+        const long long gm = (long long)A << d;   // their level-d nodes
+        k_fslots<<<(unsigned)((gm + 255) / 256), 256, 0, st>>>(d, A, dft);
+        note_launch();
+        k_acc_init<<<(unsigned)((gm + 255) / 256), 256, 0, st>>>(acc, (int)gm);
+        note_launch();
+        const long long warps = (nA + 255) / 256;
+        k_node_stats<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(x, va, nid, (int)nA,
+                                                                             make_double3(0, 0, 0), acc,
+                                                                             dshift, tpos);
+        note_launch();
+        k_fnode_finish<<<(unsigned)((gm + 255) / 256), 256, 0, st>>>(acc, d, A, dft);
+        note_launch();
+        k_fbid<<<(unsigned)((nA + 255) / 256), 256, 0, st>>>(nid, tpos, nA, d, dft, bid);
+        note_launch();
+        e = cudaGetLastError();
+        const int A2 = active[d + 1];             // trees split below level d
+        const long long nS = pos[A2];
+        if (e != cudaSuccess || A2 == 0) break;
+        rbits = 0;
+        while ((1 << rbits) < A2) ++rbits;
+        k_ftree_keys<<<(unsigned)((nS + 255) / 256), 256, 0, st>>>(x, va, nid, nS, d, rbits, dft, ka);
+        note_launch();
+        e = radix_sort(ka, va, kb, vb, (int)nS, 64, cnt, off, tot, st);
+        if (e == cudaSuccess) {
+            k_fnid_next<<<(unsigned)((nS + 255) / 256), 256, 0, st>>>(dft, nS, d, nid);
+            note_launch();
+            e = cudaGetLastError();
+        }
+    }
+    // list nodes and point records, tree by tree
+    std::vector<long long> ext_key(m, 0);
+    {
+        std::vector<long long> init(m, LLONG_MIN);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ext, init.data(), sizeof(long long) * m, cudaMemcpyHostToDevice, st);
+        for (int r = 0; e == cudaSuccess && r < m; ++r) {
+            pc_tree *t = trees[r];
+            const int nblk = 1 << t->blevel;
+            k_block_info<<<(nblk + 255) / 256, 256, 0, st>>>(t->nbox, t->vnode, t->blevel, t->bcen, t->brng,
+                                                              ext + r);
+            note_launch();
+            k_tree_scatter<<<(unsigned)((t->n + 255) / 256), 256, 0, st>>>(
+                x, wall, w_is_f32, t->wint ? t->wemax : 0, t->wint ? t->wemax - t->wemin : 0, va + pos[r],
+                bid + pos[r], t->bcen, t->n, t->rel, t->xw, t->perm, (unsigned)pos[r]);
+            note_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ext_key.data(), ext, sizeof(long long) * m, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) return bail(cuda_fail(e, "pc_build_tree_batch"));
+    for (int r = 0; r < m; ++r) {
+        pc_tree *t = trees[r];
+        long long b = ext_key[r] >= 0 ? ext_key[r] : (ext_key[r] ^ 0x7FFFFFFFFFFFFFFFLL);
+        double ex;
+        memcpy(&ex, &b, sizeof(ex));
+        t->bext = ex;
+        for (int a = 0; a < 3; ++a) {
+            t->g.c[a] = std::max(t->bext, 1e-300);
+            t->g.c32[a] = (float)t->g.c[a];
+        }
+    }
+    for (void *p : tmp) cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);
+    for (int r = 0; r < m; ++r) out[ord[r]] = trees[r];
     return PC_OK;
 }

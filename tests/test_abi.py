@@ -114,6 +114,25 @@ def test_tune_host_side_checks(lib):
     assert out.cell_size == pytest.approx(P.pc_suggest_cell_size(1, 1e6, 20.0, 0))
 
 
+def test_tree_batch_host_side_checks(lib):
+    # no catalogues, no output array, an empty catalogue, weights for one
+    # catalogue only, bad leaf capacity: rejected before any CUDA call
+    box = P.make_box(100.0, True)
+    x = np.zeros((4, 3))
+    xs = (ctypes.c_void_p * 2)(x.ctypes.data, x.ctypes.data)
+    out = (ctypes.c_void_p * 2)()
+    ns = (ctypes.c_longlong * 2)(4, 4)
+    assert lib.pc_build_tree_batch(xs, None, 0, ns, 0, ctypes.byref(box), 8, 0, None, out) == P.PC_EINVAL
+    assert lib.pc_build_tree_batch(xs, None, 0, ns, 2, ctypes.byref(box), 8, 0, None, None) == P.PC_EINVAL
+    n0 = (ctypes.c_longlong * 2)(4, 0)
+    assert lib.pc_build_tree_batch(xs, None, 0, n0, 2, ctypes.byref(box), 8, 0, None, out) == P.PC_EINVAL
+    w = np.ones(4)
+    ws = (ctypes.c_void_p * 2)(w.ctypes.data, None)
+    assert lib.pc_build_tree_batch(xs, ws, 0, ns, 2, ctypes.byref(box), 8, 0, None, out) == P.PC_EINVAL
+    assert lib.pc_build_tree_batch(xs, None, 0, ns, 2, ctypes.byref(box), 0, 0, None, out) == P.PC_EINVAL
+    assert out[0] is None and out[1] is None
+
+
 def test_fp_peak_host_side_checks(lib):
     # bad kind, negative iterations or no output: rejected before any CUDA call
     tf = ctypes.c_double(0.0)

@@ -340,3 +340,73 @@ def test_tree_batch_matches_single_counts_and_oracle():
         want, wwant = oracle.count(cats[k], w1=ws[k].astype(np.float64), box=L, periodic=True,
                                    mode="smu", edges_a=ea, edges_b=mu, method="grid")
         _check(cb[k], want, wb[k], wwant, f"tree batch mock {k}")
+
+
+def _same_tree(a, b, what):
+    """Two builds of one catalogue: the same heap slots, node ranges and point
+    order; boxes and split axes equal except below a node whose variance sums
+    (rounded in another order) broke an exact tie the other way."""
+    ea, eb = P.pc_tree_export(a), P.pc_tree_export(b)
+    assert ea["depth"] == eb["depth"] and ea["list_level"] == eb["list_level"], what
+    assert np.array_equal(ea["count"], eb["count"]), what
+    assert np.array_equal(ea["start"], eb["start"]), what
+    same_axis = ea["axis"] == eb["axis"]
+    if same_axis.all():
+        assert np.array_equal(ea["box"], eb["box"]), what
+        assert np.array_equal(ea["ord"], eb["ord"]), what
+    return bool(same_axis.all())
+
+
+def test_batched_tree_build_equals_single_builds():
+    """pc_build_tree_batch (one level loop over all catalogues, the deepest
+    first) gives each catalogue the tree pc_build_tree gives it, and a tree
+    batch over those trees the same counts and weighted sums as the single
+    builds and the oracle: very different sizes (1 to 40,000 points) and
+    depths, binary32 weights, periodic; and a non-periodic batch with
+    binary64 weights along the midpoint line of sight."""
+    L = 200.0
+    cats = [synth.neyman_scott(n, max(1, n // 20), 20.0, 2.0, L, 860 + i)
+            if n > 50 else synth.uniform_box(n, L, 860 + i)
+            for i, n in enumerate([40000, 1, 3000, 257, 25000, 90, 12000])]
+    ws = [synth.lognormal_weights(c.shape[0], 0.3, 880 + i, np.float32) for i, c in enumerate(cats)]
+    ea = np.linspace(0.0, 25.0, 26)
+    mu = np.linspace(0.0, 1.0, 11)
+    bins = P.Bins("smu", "z", ea, mu)
+    b = P.make_box(L, True)
+    dev = [torch.from_numpy(c).cuda() for c in cats]      # device and host inputs mixed
+    inputs = [dev[k] if k % 2 else cats[k] for k in range(len(cats))]
+    tb = P.pc_build_tree_batch(inputs, ws, box=b)
+    ts = [P.pc_build_tree(c, w, box=b) for c, w in zip(cats, ws)]
+    try:
+        for k in range(len(cats)):
+            _same_tree(tb[k], ts[k], f"catalogue {k}")
+        o = P.make_opts("f32", 0.0, 2)
+        cb, wb, _ = P.pc_count_tree_batch(tb, bins, o, weighted=True)
+        cs, ws_, _ = P.pc_count_tree_batch(ts, bins, o, weighted=True)
+        assert np.array_equal(cb, cs)
+        np.testing.assert_allclose(wb, ws_, rtol=1e-12, atol=0)
+        cb = cb.reshape(len(cats), -1)
+        wb = wb.reshape(len(cats), -1)
+        for k in (0, 2, 4):
+            want, wwant = oracle.count(cats[k], w1=ws[k].astype(np.float64), box=L, periodic=True,
+                                       mode="smu", edges_a=ea, edges_b=mu, method="grid")
+            _check(cb[k], want, wb[k], wwant, f"batch-built tree {k}")
+    finally:
+        for t in tb + ts:
+            t.free()
+    # non-periodic shells, binary64 weights, midpoint line of sight
+    shells = [synth.survey_shell(n, k % 2 == 0, 890 + k) for k, n in enumerate([3000, 500, 2000])]
+    sw = [synth.fkp_weights(s, s.shape[0]) for s in shells]
+    sp = np.linspace(0.0, 40.0, 9)
+    bins = P.Bins("sigpi", "mid", sp, sp)
+    b = P.make_box(None, False)
+    tb = P.pc_build_tree_batch(shells, sw, box=b)
+    try:
+        for k, (s, w) in enumerate(zip(shells, sw)):
+            got, gw, _ = P.pc_count_tree(tb[k], None, bins, weighted=True)
+            want, wwant = oracle.count(s, w1=w, periodic=False, mode="sigpi", los="mid",
+                                       edges_a=sp, edges_b=sp, method="grid")
+            _check(got, want, gw, wwant, f"batch-built shell {k}")
+    finally:
+        for t in tb:
+            t.free()

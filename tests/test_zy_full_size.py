@@ -106,10 +106,11 @@ def test_batched_mocks_256_vs_single_counts_and_sampled_oracle():
     finally:
         for g in gs:
             g.free()
-    # the tree batch (one persistent launch over every tree's lists), tuned
-    # on the median mock as the benchmark does
+    # the tree batch (every tree built in one level loop, one persistent
+    # launch over every tree's lists), tuned on the median mock as the
+    # benchmark does
     topts, cap, _ = P.pc_tune_tree(X[med], box=box, bins=bins)
-    ts = [P.pc_build_tree(x, box=box, list_cap=cap) for x in X]
+    ts = P.pc_build_tree_batch(X, box=box, list_cap=cap)
     try:
         tb, _, _ = P.pc_count_tree_batch(ts, bins, topts)
         tb = tb.reshape(len(X), -1)
