@@ -502,7 +502,7 @@ static pc_status make_plan(const pc_bins *b, const Geom &g, const double *pts_lo
 // copy l % k) as many as fit a 16 KB budget, so the lanes of a warp do not
 // collide on the few bins of a small histogram.
 // (weighted: binary64 weight sums share the copies and the budget; the
-// integer weight records have their own WINT_COPIES copies.)
+// integer weight records take the counts' copies outside that budget.)
 static void choose_replication(int mode, int nbins, bool weighted, int &priv, int &hist_k) {
     priv = 0;
     hist_k = 1;
@@ -511,9 +511,6 @@ static void choose_replication(int mode, int nbins, bool weighted, int &priv, in
     const long long per_copy = (long long)nbins * (4 + (weighted ? 8 : 0));
     while (hist_k < 32 && per_copy * hist_k * 2 <= 16384) hist_k *= 2;
 }
-
-// Lane copies of the integer weight records (one per lane: conflict-free).
-constexpr int WINT_COPIES = 32;
 
 // Rows of each shared histogram copy: the bins, the discarded rows of the
 // floor bins without a range test, and at least one row past the bins that
@@ -772,8 +769,8 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     auto fit = [&](bool wint) {
         p.wint = wint ? 1 : 0;
         choose_replication(S.o.priv, P.nbins, S.weighted && !wint, p.priv, p.hist_k);
-        p.wint_k = WINT_COPIES;
         for (;;) {
+            p.wint_k = p.hist_k;   // the weight records take the counts' lane copies
             p.smem_hist_ok = 1;
             // the floor-based bins need no tables (they serve only the global-
             // histogram variant)
@@ -1103,7 +1100,6 @@ static TaskDev task_of(const pc_grid *gi, const pc_grid *gj, int hist, int is_au
     // (w = M 2^(e - 150) with the 24-bit significand M and biased exponent e);
     // the packed significands' product is shifted down by both ranges
     t.wscale = (gi->wint && gj->wint) ? ldexp(1.0, gi->wemax + gj->wemax - 300) : 0.0;
-    t.wshift = (gi->wint && gj->wint) ? (gi->wemax - gi->wemin) + (gj->wemax - gj->wemin) : 0;
     return t;
 }
 
@@ -1223,7 +1219,6 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
     T.hist = 0;
     T.is_auto = is_auto ? 1 : 0;
     T.wscale = (t1->wint && tj->wint) ? ldexp(1.0, t1->wemax + tj->wemax - 300) : 0.0;
-    T.wshift = (t1->wint && tj->wint) ? (t1->wemax - t1->wemin) + (tj->wemax - tj->wemin) : 0;
     J.tasks.push_back(T);
     J.nhist = 1;
     J.is_auto = is_auto;
@@ -1348,7 +1343,6 @@ extern "C" pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const 
         T.hist = k;
         T.is_auto = 1;
         T.wscale = t->wint ? ldexp(1.0, 2 * t->wemax - 300) : 0.0;
-        T.wshift = t->wint ? 2 * (t->wemax - t->wemin) : 0;
         J.tasks.push_back(T);
         cb = std::max(cb, t->bext);
         for (int a = 0; a < 3; ++a) {

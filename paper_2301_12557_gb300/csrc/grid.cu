@@ -202,9 +202,9 @@ pc_status weight_stats(const void *w, int w_is_f32, int n, cudaStream_t st, int 
 
 // Packed integer weight (stored in the w lane of the FP32 point record): the
 // binary32 significand M with its leading one (w = M 2^(e-150)), shifted up
-// by span - (emax - e) with span = emax - emin <= 8 the grid's exponent range,
-// so that it fits 32 bits and a pair's product needs one shift by a per-task
-// amount.  Zero weights pack to 0.
+// by 8 - (emax - e) (the grid's exponents span at most 8 binades), so that it
+// fits 32 bits and a pair's exact 64-bit product is (M_i M_j) 2^(16 - k_i -
+// k_j), k = emax - e.  Zero weights pack to 0.
 __device__ __forceinline__ unsigned pack_weight(double wv, int emax, int span) {
     const unsigned b = __float_as_uint(__double2float_rn(wv));
     const int e = (int)((b >> 23) & 0xFF);
@@ -666,7 +666,7 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     if (e == cudaSuccess && n > 0) {
         int blocks = (int)((n + 255) / 256);
         k_scatter<<<blocks, 256, 0, st>>>(dxyz, dw, w_is_f32, g->wint ? g->wemax : 0,
-                                          g->wint ? g->wemax - g->wemin : 0, (int)n, G,
+                                          WINT_GRID_SPAN, (int)n, G,
                                           sub_bits, cell, slot, key_start, g->rel, g->cx, g->xw,
                                           g->perm);
         note_launch();

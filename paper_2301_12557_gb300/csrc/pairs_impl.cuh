@@ -554,14 +554,16 @@ __device__ __forceinline__ void red_shared_u32_if(unsigned addr, bool on) {
 __device__ __forceinline__ void red_shared_u32(unsigned addr, unsigned v) {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
-// The three 16-bit pieces of an integer weight product into one lane copy's
-// record {lo, mid, hi} (immediate offsets from one address).
-__device__ __forceinline__ void red_shared_pieces(unsigned addr, unsigned long long p) {
+// The three 16-bit pieces of an integer weight product p = P >> 16 into one
+// lane copy's record {lo, mid, hi} (immediate offsets from one address),
+// taken from the 64-bit product P itself: bits 16-31, 32-47 and 48-63.
+__device__ __forceinline__ void red_shared_pieces(unsigned addr, unsigned long long P) {
+    const unsigned lo = (unsigned)P, hi = (unsigned)(P >> 32);
     asm volatile(
         "red.shared.add.u32 [%0], %1;\n\t"
         "red.shared.add.u32 [%0+4], %2;\n\t"
         "red.shared.add.u32 [%0+8], %3;" ::"r"(addr),
-        "r"((unsigned)p & 0xFFFFu), "r"((unsigned)p >> 16), "r"((unsigned)(p >> 32)));
+        "r"(lo >> 16), "r"(hi & 0xFFFFu), "r"(hi >> 16));
 }
 __device__ __forceinline__ void red_shared_f64_if(unsigned addr, double v, bool on) {
     asm volatile(
@@ -596,7 +598,6 @@ struct IPts {
     float xa[RI], ya[RI], za[RI];  // absolute positions (midpoint line of sight)
     double w[RI];
     unsigned wm[RI];               // packed integer weight (integer weight path)
-    unsigned wsh;                  // the task's product shift (integer weight path)
     int idx[RI];
 };
 
@@ -701,10 +702,10 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
     const unsigned htrash = hist_sa + hk4 * (unsigned)p.trash_row;
     const unsigned wbase = whist_sa - 2u * hk4 * bias;
     // integer weights: a 12-byte record {lo, mid, hi} per bin and lane copy
-    // (word 3 (bin wint_k + copy) + piece: bank 3 copy + piece, conflict-free)
-    const unsigned wk12 = 12u * (unsigned)p.wint_k;
-    const unsigned wbase2 = whist_sa - wk12 * bias;
-    const unsigned wtrash = whist_sa + wk12 * (unsigned)p.trash_row;
+    // (word 3 (bin copies + copy) + piece: bank 3 copy + piece, conflict-free),
+    // as many copies as the counts, so a record's address is 3 x the count's
+    // address + wdelta (the discarded row included)
+    const unsigned wdelta = whist_sa - 3u * hist_sa;
     float2 NX[RI], NY[RI], NZ[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
@@ -777,23 +778,23 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                     b1 = b1 * nbu + j1;
                 }
                 const bool a0 = in0[r] && ok0 && !n0, a1 = in1[r] && ok1 && !n1;
-                red_shared_u32(a0 ? hbase + hk4 * b0 : htrash, 1u);
-                red_shared_u32(a1 ? hbase + hk4 * b1 : htrash, 1u);
+                const unsigned c0 = a0 ? hbase + hk4 * b0 : htrash;
+                const unsigned c1 = a1 ? hbase + hk4 * b1 : htrash;
+                red_shared_u32(c0, 1u);
+                red_shared_u32(c1, 1u);
                 if (W == 1) {
                     const double2 wj = *reinterpret_cast<const double2 *>(tb.w + jj);
                     red_shared_f64_if(wbase + 2u * hk4 * b0, __dmul_rn(I.w[r], wj.x), a0);
                     red_shared_f64_if(wbase + 2u * hk4 * b1, __dmul_rn(I.w[r], wj.y), a1);
                 } else if (W == 2) {
                     // (M_i M_j) >> (k_i + k_j), k = emax - e the exponent offset:
-                    // the packed M 2^(span - k) multiplied exactly in 64 bits and
-                    // shifted down by both spans (truncation < 2^(k_i + k_j - 46)
-                    // relative, below 2^48), added as three 16-bit pieces to the
-                    // lane copy's record
+                    // the packed M 2^(8 - k) multiplied exactly in 64 bits is
+                    // P = M_i M_j 2^(16 - k_i - k_j), and the product is P >> 16
+                    // (truncation < 2^(k_i + k_j - 46) relative, below 2^48),
+                    // added as three 16-bit pieces to the lane copy's record
                     const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
-                    const unsigned long long p0 = ((unsigned long long)I.wm[r] * wj.x) >> I.wsh;
-                    const unsigned long long p1 = ((unsigned long long)I.wm[r] * wj.y) >> I.wsh;
-                    red_shared_pieces(a0 ? wbase2 + wk12 * b0 : wtrash, p0);
-                    red_shared_pieces(a1 ? wbase2 + wk12 * b1 : wtrash, p1);
+                    red_shared_pieces(3u * c0 + wdelta, (unsigned long long)I.wm[r] * wj.x);
+                    red_shared_pieces(3u * c1 + wdelta, (unsigned long long)I.wm[r] * wj.y);
                 }
                 re0[r] = in0[r] && n0;
                 re1[r] = in1[r] && n1;
@@ -842,9 +843,7 @@ __device__ __forceinline__ void pair_tile_sigpi2(const PairParams &p, Tile tb, i
     const unsigned hbase = hist_sa - hk4 * bias;
     const unsigned htrash = hist_sa + hk4 * (unsigned)p.trash_row;
     const unsigned wbase = whist_sa - 2u * hk4 * bias;
-    const unsigned wk12 = 12u * (unsigned)p.wint_k;
-    const unsigned wbase2 = whist_sa - wk12 * bias;
-    const unsigned wtrash = whist_sa + wk12 * (unsigned)p.trash_row;
+    const unsigned wdelta = whist_sa - 3u * hist_sa;   // as in the floor-bin loop above
     float2 NX[RI], NY[RI], NZ[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
@@ -918,18 +917,18 @@ __device__ __forceinline__ void pair_tile_sigpi2(const PairParams &p, Tile tb, i
                 const bool ok0 = ba0 < limA && bb0 < limB, ok1 = ba1 < limA && bb1 < limB;
                 const unsigned b0 = ba0 * nbu + bb0, b1 = ba1 * nbu + bb1;
                 const bool a0 = in0[r] && ok0 && !n0, a1 = in1[r] && ok1 && !n1;
-                red_shared_u32(a0 ? hbase + hk4 * b0 : htrash, 1u);
-                red_shared_u32(a1 ? hbase + hk4 * b1 : htrash, 1u);
+                const unsigned c0 = a0 ? hbase + hk4 * b0 : htrash;
+                const unsigned c1 = a1 ? hbase + hk4 * b1 : htrash;
+                red_shared_u32(c0, 1u);
+                red_shared_u32(c1, 1u);
                 if (W == 1) {
                     const double2 wj = *reinterpret_cast<const double2 *>(tb.w + jj);
                     red_shared_f64_if(wbase + 2u * hk4 * b0, __dmul_rn(I.w[r], wj.x), a0);
                     red_shared_f64_if(wbase + 2u * hk4 * b1, __dmul_rn(I.w[r], wj.y), a1);
                 } else if (W == 2) {
                     const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
-                    const unsigned long long p0 = ((unsigned long long)I.wm[r] * wj.x) >> I.wsh;
-                    const unsigned long long p1 = ((unsigned long long)I.wm[r] * wj.y) >> I.wsh;
-                    red_shared_pieces(a0 ? wbase2 + wk12 * b0 : wtrash, p0);
-                    red_shared_pieces(a1 ? wbase2 + wk12 * b1 : wtrash, p1);
+                    red_shared_pieces(3u * c0 + wdelta, (unsigned long long)I.wm[r] * wj.x);
+                    red_shared_pieces(3u * c1 + wdelta, (unsigned long long)I.wm[r] * wj.y);
                 }
                 re0[r] = in0[r] && n0;
                 re1[r] = in1[r] && n1;
@@ -1111,7 +1110,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
                              (p.priv ? (unsigned)((tid >> 5) * p.nbins_smem * p.hist_k * 4) : 0u) +
                              4u * lane_copy;
     const unsigned whist_sa = (unsigned)__cvta_generic_to_shared(s_whist) +
-                              (W == 2 ? 12u * (unsigned)(tid & (p.wint_k - 1)) : 8u * lane_copy);
+                              (W == 2 ? 12u * lane_copy : 8u * lane_copy);
 
     const int nx = p.g.ng[0], ny = p.g.ng[1];
     const float c32x = p.g.c32[0], c32y = p.g.c32[1], c32z = p.g.c32[2];
@@ -1143,8 +1142,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
         if (bidx >= nblocks) break;
         const Block B = p.blocks[bidx];
         const TaskDev &T = p.tasks[B.task];
-        if (T.hist != cur_hist || (W == 2 && T.wscale != cur_wscale)) {   // (a task's
-            // wshift is fixed by its grids, like wscale: no flush needed for it)
+        if (T.hist != cur_hist || (W == 2 && T.wscale != cur_wscale)) {
             flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
             cur_hist = T.hist;
             cur_wscale = T.wscale;
@@ -1158,7 +1156,6 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
         // thread t holds the block's points RI t .. RI t + RI - 1: a warp covers
         // 32 RI consecutive (sub-cell ordered, so spatially compact) points
         IPts<RI> I;
-        I.wsh = (unsigned)T.wshift;
 #pragma unroll
         for (int r = 0; r < RI; ++r) {
             const int loc = RI * tid + r;

@@ -49,8 +49,6 @@ struct TaskDev {
     int hist;
     int is_auto;
     double wscale;   // integer weight path: value of one unit of the product accumulators
-    int wshift;      // integer weight path: the two grids' exponent spans added (the
-                     // packed significands' product is shifted down by it)
 };
 
 // A block of consecutive i-points inside one cell.
@@ -133,7 +131,7 @@ struct PairParams {
     // and lane copy, recombined exactly per copy and flushed as binary64 times
     // the task's wscale
     int wint;
-    int wint_k;              // lane copies of the integer weight records (power of 2)
+    int wint_k;              // lane copies of the integer weight records: hist_k
     // shared-histogram row that lanes without an in-range pair update (the
     // floor-bin kernels issue every reduction with the full warp); the flush
     // discards it like every row past nbins

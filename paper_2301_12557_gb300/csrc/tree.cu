@@ -355,7 +355,7 @@ __global__ void k_block_info(const double *__restrict__ box, const int2 *__restr
 }
 
 // Packed integer weight: the significand with its leading one shifted up by
-// span - (emax - e) (span = emax - emin <= 8), as on the grid path.
+// 8 - (emax - e) (exponents within 8 binades), as on the grid path.
 __device__ __forceinline__ unsigned pack_weight_t(double wv, int emax, int span) {
     const unsigned b = __float_as_uint(__double2float_rn(wv));
     const int e = (int)((b >> 23) & 0xFF);
@@ -1054,7 +1054,7 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
         k_block_info<<<(nblk + 255) / 256, 256, 0, st>>>(t->nbox, t->vnode, blevel, t->bcen, t->brng, ext);
         note_launch();
         k_tree_scatter<<<gpos, 256, 0, st>>>(x, dw, w_is_f32, t->wint ? t->wemax : 0,
-                                             t->wint ? t->wemax - t->wemin : 0, va, bid, t->bcen,
+                                             WINT_GRID_SPAN, va, bid, t->bcen,
                                              (int)n, t->rel, t->xw, t->perm);
         note_launch();
         e = cudaGetLastError();
@@ -1469,7 +1469,7 @@ extern "C" pc_status pc_build_tree_batch(const double *const *xyz, const void *c
                                                               ext + r);
             note_launch();
             k_tree_scatter<<<(unsigned)((t->n + 255) / 256), 256, 0, st>>>(
-                x, wall, w_is_f32, t->wint ? t->wemax : 0, t->wint ? t->wemax - t->wemin : 0, va + pos[r],
+                x, wall, w_is_f32, t->wint ? t->wemax : 0, WINT_GRID_SPAN, va + pos[r],
                 bid + pos[r], t->bcen, t->n, t->rel, t->xw, t->perm, (unsigned)pos[r]);
             note_launch();
             e = cudaGetLastError();

@@ -4,14 +4,14 @@ When every weight of a catalogue is a non-negative normal binary32 value (or
 zero), its exponents span at most 8 binades, and the two catalogues' spans
 add up to at most 12, the pair kernel accumulates each pair weight w_i w_j
 (Sect. 2.5) as an integer.  The weight w = M 2^(e - 150) (M the 24-bit
-significand, e the biased exponent) is packed as M 2^(S - k), k = e_max - e
-and S = e_max - e_min the catalogue's span (below 2^32); a pair's product
-p = (packed_i packed_j) >> (S_i + S_j) equals (M_i M_j) >> (k_i + k_j)
-exactly (below 2^48).  It is added as three 16-bit pieces (p mod 2^16, bits
-16-31, p >> 32) to three 32-bit lane counters (at most 2^16 products between
-flushes, so no counter wraps), and a flush recombines each lane's counters
-into the exact 64-bit sum, converts it to binary64 and multiplies it by
-2^(e_max,i + e_max,j - 300).  The truncation of one product is below
+significand, e the biased exponent) is packed as M 2^(8 - k), k = e_max - e
+(below 2^32); the exact 64-bit product of two packed weights is
+P = M_i M_j 2^(16 - k_i - k_j), and p = P >> 16 equals (M_i M_j) >> (k_i +
+k_j) exactly (below 2^48).  Its three 16-bit pieces, bits 16-31, 32-47 and
+48-63 of P, are added to three 32-bit lane counters (at most 2^16 products
+between flushes, so no counter wraps), and a flush recombines each lane's
+counters into the exact 64-bit sum, converts it to binary64 and multiplies it
+by 2^(e_max,i + e_max,j - 300).  The truncation of one product is below
 2^(k_i + k_j - 46) <= 2^-34 of it, so every bin's sum is within 2^-34
 relative of the exact sum.  This test emulates the path on weights spanning
 the allowed exponents and checks the bound against exact rational sums, and
@@ -27,13 +27,13 @@ WINT_LIMIT = 1 << 16
 
 
 def _pack(w, emax, emin):
-    """Packed weights M 2^(S - k) (below 2^32), and M and k for the check."""
+    """Packed weights M 2^(8 - k) (below 2^32), and M and k for the check."""
+    assert emax - emin <= 8
     b = w.astype(F32).view(np.uint32).astype(np.int64)
     e = (b >> 23) & 0xFF
     m = np.where(e > 0, (b & 0x7FFFFF) | 0x800000, 0)
     k = np.where(e > 0, emax - e, 0)
-    span = emax - emin
-    packed = [int(a) << int(span - kk) if a else 0 for a, kk in zip(m, k)]
+    packed = [int(a) << int(8 - kk) if a else 0 for a, kk in zip(m, k)]
     assert max(packed, default=0) < 2 ** 32
     return packed, m, k
 
@@ -45,8 +45,9 @@ def _emulated_sum(wi, wj, ext_i, ext_j):
     (emax_i, emin_i), (emax_j, emin_j) = ext_i, ext_j
     pi, mi, ki = _pack(wi, emax_i, emin_i)
     pj, mj, kj = _pack(wj, emax_j, emin_j)
-    shift = (emax_i - emin_i) + (emax_j - emin_j)
-    prod = [(a * b) >> shift for a, b in zip(pi, pj)]
+    full = [a * b for a, b in zip(pi, pj)]              # the exact 64-bit products P
+    assert max(full, default=0) < 2 ** 64
+    prod = [q >> 16 for q in full]
     # the same integer as the significands' product shifted by both offsets
     assert prod == [(int(a) * int(b)) >> int(s) for a, b, s in zip(mi, mj, ki + kj)]
     assert max(prod, default=0) < 2 ** 48
@@ -54,9 +55,10 @@ def _emulated_sum(wi, wj, ext_i, ext_j):
     total = 0.0
     for s in range(0, len(prod), WINT_LIMIT):
         chunk = prod[s:s + WINT_LIMIT]
-        lo = sum(p & 0xFFFF for p in chunk)
-        mid = sum((p >> 16) & 0xFFFF for p in chunk)
-        hi = sum(p >> 32 for p in chunk)
+        pieces = full[s:s + WINT_LIMIT]                   # bits 16-31, 32-47, 48-63 of P
+        lo = sum((q >> 16) & 0xFFFF for q in pieces)
+        mid = sum((q >> 32) & 0xFFFF for q in pieces)
+        hi = sum(q >> 48 for q in pieces)
         assert max(lo, mid, hi) < 2 ** 32          # three u32 plane counters
         acc = lo + (mid << 16) + (hi << 32)        # the flush's recombination
         assert acc == sum(chunk) and acc < 2 ** 64
