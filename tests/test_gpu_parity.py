@@ -372,6 +372,77 @@ def test_integer_weight_products_match_binary64():
     _check(g, o, gw, ow, "binary64 weights")
 
 
+def test_integer_weight_packing_limits_and_sixteen_copies():
+    """The packed significand M << (8 - k) at both ends of an 8-binade
+    catalogue (k = 0 and k = 8) in a cross count with a 4-binade catalogue
+    (spans 8 + 4 = 12: integer products); a 9-binade catalogue takes the
+    binary64 products even beside a one-binade one; and a 250-bin (s, mu)
+    histogram, whose counts and weight records get 16 lane copies instead of
+    32, still runs the integer path.  All within 1e-10 of the oracle."""
+    L = 300.0
+    rng = np.random.default_rng(521)
+    x = synth.neyman_scott(20000, 2000, 10.0, 3.0, L, 522)
+    y = synth.neyman_scott(15000, 1500, 10.0, 3.0, L, 523)
+    ea = np.linspace(0.0, 30.0, 31)
+    kw = dict(box=L, periodic=True, edges_a=ea)
+    w8 = np.exp2(rng.uniform(-4.0, 4.0, x.shape[0])).astype(np.float32)
+    w8[:5] = np.float32(2.0 ** -4)                           # the smallest binade (k = 8)
+    w8[5:10] = np.float32(16.0)                               # the largest (k = 0)
+    w4 = np.exp2(rng.uniform(0.0, 4.0, y.shape[0])).astype(np.float32)
+    w4[:5] = np.float32(1.0)
+    w4[5:10] = np.float32(16.0)
+    g, gw, st = P.count(x, y, w1=w8, w2=w4, return_stats=True, **kw)
+    o, ow = oracle.count(x, y, w1=w8, w2=w4, method="grid", **kw)
+    assert st.wsum == 2
+    _check(g, o, gw, ow, "integer weights, spans 8 + 4")
+    w9 = np.exp2(rng.uniform(-4.5, 4.5, x.shape[0])).astype(np.float32)
+    w9[:5] = np.float32(2.0 ** -5)
+    w9[5:10] = np.float32(16.0)
+    w1 = np.full(y.shape[0], 1.5, dtype=np.float32)
+    g, gw, st = P.count(x, y, w1=w9, w2=w1, return_stats=True, **kw)
+    o, ow = oracle.count(x, y, w1=w9, w2=w1, method="grid", **kw)
+    assert st.wsum == 1
+    _check(g, o, gw, ow, "9 binades: binary64 products")
+    wx = synth.lognormal_weights(x.shape[0], 0.3, 524)
+    mu = np.linspace(0.0, 1.0, 11)
+    kws = dict(box=L, periodic=True, mode="smu", edges_a=np.linspace(0.0, 25.0, 26), edges_b=mu)
+    g, gw, st = P.count(x, w1=wx, return_stats=True, **kws)
+    o, ow = oracle.count(x, w1=wx, method="grid", **kws)
+    assert st.wsum == 2
+    _check(g, o, gw, ow, "integer weights, 250 bins (16 lane copies)")
+
+
+def test_shards_are_the_same_pairs_in_both_precisions():
+    """A shard is a set of cells: the FP32 + rescue path (256-point blocks)
+    and the plain FP64 path (128-point blocks) count identical pairs shard by
+    shard at the same cell side, auto and cross, weighted."""
+    L = 150.0
+    x = synth.neyman_scott(9000, 900, 10.0, 3.0, L, 251)
+    y = synth.uniform_box(6000, L, 252)
+    wx = synth.lognormal_weights(x.shape[0], 0.3, 253)
+    wy = synth.lognormal_weights(y.shape[0], 0.3, 254)
+    bins = P.Bins("s", "z", np.linspace(0.0, 30.0, 16))
+    box = P.make_box(L, True)
+    o = P.make_opts("f32", 10.0)
+    gx = P.pc_build_grid(x, wx, box=box, r_max=bins.r_max, opts=o)
+    gy = P.pc_build_grid(y, wy, box=box, r_max=bins.r_max, opts=o)
+    try:
+        for r in range(3):
+            o32 = P.make_opts("f32", 10.0, 2, shard_index=r, shard_count=3)
+            o64 = P.make_opts("f64", 10.0, 1, shard_index=r, shard_count=3)
+            a32, aw32, _ = P.pc_count_auto(gx, bins, o32, weighted=True)
+            a64, aw64, _ = P.pc_count_auto(gx, bins, o64, weighted=True)
+            assert a32.sum() > 0 and np.array_equal(a32, a64), r
+            np.testing.assert_allclose(aw32, aw64, rtol=1e-10, atol=0)
+            c32, cw32, _ = P.pc_count_cross(gx, gy, bins, o32, weighted=True)
+            c64, cw64, _ = P.pc_count_cross(gx, gy, bins, o64, weighted=True)
+            assert np.array_equal(c32, c64), r
+            np.testing.assert_allclose(cw32, cw64, rtol=1e-10, atol=0)
+    finally:
+        gx.free()
+        gy.free()
+
+
 def test_device_tensors_and_device_outputs():
     L = 100.0
     x = synth.neyman_scott(4000, 400, 10.0, 2.0, L, 201)
