@@ -132,6 +132,104 @@ static cudaError_t radix_sort(unsigned long long *ka, unsigned *va, unsigned lon
 }
 
 // ---------------------------------------------------------------------------
+// the same order by chunks of whole nodes, in shared memory
+// ---------------------------------------------------------------------------
+// Along the positions the node ids (the keys' high bits) never decrease, so
+// the stable sort of all keys only reorders the keys of each node among
+// themselves.  Once every node of a level fits a chunk, one CTA per chunk of
+// q whole nodes sorts its keys on (key, position) in shared memory (a bitonic
+// network over the next power of two, the padding after every key) and
+// writes the values back in that order: the radix sort's result, from one
+// read and one write of the level's values.
+constexpr int CS_SMALL = 4096;    // chunk capacities (keys)
+constexpr int CS_LARGE = 16384;
+
+template <int CAP, int NTH, class R>
+__global__ void __launch_bounds__(NTH) k_chunk_sort(const unsigned long long *__restrict__ keys,
+                                                    unsigned *__restrict__ vals, R r) {
+    static_assert(CAP <= 65536, "positions in a chunk are 16-bit");
+    extern __shared__ __align__(16) unsigned char cs_sm[];
+    unsigned long long *sk = reinterpret_cast<unsigned long long *>(cs_sm);
+    unsigned *sv = reinterpret_cast<unsigned *>(sk + CAP);
+    unsigned short *si = reinterpret_cast<unsigned short *>(sv + CAP);
+    const int2 rg = r.range(blockIdx.x);
+    const int len = min(rg.y - rg.x, CAP);   // the host sizes chunks to CAP
+    int P = 1;
+    while (P < len) P <<= 1;
+    for (int t = threadIdx.x; t < P; t += NTH) {
+        if (t < len) {
+            sk[t] = keys[rg.x + t];
+            sv[t] = vals[rg.x + t];
+        } else {
+            sk[t] = ~0ull;
+        }
+        si[t] = (unsigned short)t;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < (P >> 1); t += NTH) {
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));   // bit j clear
+                const int l = i + j;
+                const unsigned long long a = sk[i], b = sk[l];
+                const unsigned short ia = si[i], ib = si[l];
+                const bool gt = a > b || (a == b && ia > ib);
+                if (gt == ((i & k) == 0)) {   // ascending where bit k of i is clear
+                    sk[i] = b;
+                    sk[l] = a;
+                    si[i] = ib;
+                    si[l] = ia;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < len; t += NTH) vals[rg.x + t] = sv[si[t]];
+}
+
+// Chunk c of one tree's level: its nodes [c q, c q + q) (slots 2^d - 1 + k).
+struct ChunksOne {
+    const int2 *vnode;
+    int level, q;
+    __device__ int2 range(int c) const {
+        const long long h0 = (1LL << level) - 1 + (long long)c * q;
+        const int2 a = vnode[h0], b = vnode[h0 + q - 1];
+        return make_int2(a.x, b.x + b.y);
+    }
+};
+
+template <int CAP, int NTH, class R>
+static cudaError_t launch_chunk_sort(const unsigned long long *keys, unsigned *vals, R r,
+                                     long long chunks, cudaStream_t st) {
+    const size_t smem = (size_t)CAP * (sizeof(unsigned long long) + sizeof(unsigned) +
+                                       sizeof(unsigned short));
+    cudaError_t e = cudaFuncSetAttribute(k_chunk_sort<CAP, NTH, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_chunk_sort<CAP, NTH, R><<<(unsigned)chunks, NTH, smem, st>>>(keys, vals, r);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Sort level `level` by chunks when its largest node (maxsize points) fits
+// one: q whole nodes a chunk, q a power of two dividing the 2^level nodes of
+// each tree.  `nodes`: the level's nodes over all trees sorted.  Returns
+// false, launching nothing, when the nodes are too large.
+template <class R>
+static bool chunk_sort_level(const unsigned long long *keys, unsigned *vals, R r, int level,
+                             long long nodes, long long maxsize, cudaStream_t st, cudaError_t *err) {
+    const int cap = maxsize <= CS_SMALL ? CS_SMALL : (maxsize <= CS_LARGE ? CS_LARGE : 0);
+    if (cap == 0) return false;
+    long long q = 1;
+    while (q < (1LL << level) && 2 * q * maxsize <= cap) q *= 2;
+    r.level = level;
+    r.q = (int)q;
+    *err = cap == CS_SMALL ? launch_chunk_sort<CS_SMALL, 256>(keys, vals, r, nodes / q, st)
+                           : launch_chunk_sort<CS_LARGE, 1024>(keys, vals, r, nodes / q, st);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // per-level node statistics
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double canon_t(double x, double L) {
@@ -1039,7 +1137,9 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
         if (e != cudaSuccess || d == depth) break;
         k_tree_keys<<<gpos, 256, 0, st>>>(x, va, nid, (int)n, d, t->naxis, ka);
         note_launch();
-        e = radix_sort(ka, va, kb, vb, (int)n, 64, cnt, off, tot, st);
+        ChunksOne co{t->vnode, d, 1};
+        if (!chunk_sort_level(ka, va, co, d, 1LL << d, (n + (1LL << d) - 1) >> d, st, &e))
+            e = radix_sort(ka, va, kb, vb, (int)n, 64, cnt, off, tot, st);
         if (e == cudaSuccess) {
             k_nid_next<<<gpos, 256, 0, st>>>(t->vnode, (int)n, d, nid);
             note_launch();
@@ -1096,6 +1196,20 @@ struct FTree {
     signed char *naxis;
     long long pos;     // first position of the tree's points
     int n, n_leaf, depth, blevel;
+};
+
+// Chunk c of a forest's level: global nodes [c q, c q + q), all of one tree
+// (q divides the 2^d nodes of each).
+struct ChunksForest {
+    const FTree *ft;
+    int level, q;
+    __device__ int2 range(int c) const {
+        const long long g0 = (long long)c * q;
+        const FTree &T = ft[g0 >> level];
+        const long long h0 = (1LL << level) - 1 + (g0 & ((1LL << level) - 1));
+        const int2 a = T.vnode[h0], b = T.vnode[h0 + q - 1];
+        return make_int2((int)(T.pos + a.x), (int)(T.pos + b.x + b.y));
+    }
 };
 
 __global__ void k_fnode_finish(const NodeAcc *__restrict__ acc, int level, int ntrees,
@@ -1243,8 +1357,11 @@ extern "C" pc_status pc_build_tree_batch(const double *const *xyz, const void *c
         ord[k] = k;
     }
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return depth[a] > depth[b]; });
-    std::vector<long long> pos(m + 1, 0);
-    for (int r = 0; r < m; ++r) pos[r + 1] = pos[r] + n[ord[r]];
+    std::vector<long long> pos(m + 1, 0), nmax(m + 1, 0);   // nmax[a]: largest of the first a trees
+    for (int r = 0; r < m; ++r) {
+        pos[r + 1] = pos[r] + n[ord[r]];
+        nmax[r + 1] = std::max(nmax[r], n[ord[r]]);
+    }
 
     std::vector<pc_tree *> trees(m, nullptr);
     std::vector<void *> tmp;
@@ -1450,7 +1567,9 @@ extern "C" pc_status pc_build_tree_batch(const double *const *xyz, const void *c
         while ((1 << rbits) < A2) ++rbits;
         k_ftree_keys<<<(unsigned)((nS + 255) / 256), 256, 0, st>>>(x, va, nid, nS, d, rbits, dft, ka);
         note_launch();
-        e = radix_sort(ka, va, kb, vb, (int)nS, 64, cnt, off, tot, st);
+        ChunksForest cf{dft, d, 1};
+        if (!chunk_sort_level(ka, va, cf, d, (long long)A2 << d, (nmax[A2] + (1LL << d) - 1) >> d, st, &e))
+            e = radix_sort(ka, va, kb, vb, (int)nS, 64, cnt, off, tot, st);
         if (e == cudaSuccess) {
             k_fnid_next<<<(unsigned)((nS + 255) / 256), 256, 0, st>>>(dft, nS, d, nid);
             note_launch();
