@@ -208,8 +208,8 @@ pc_status pc_count_batch(const pc_grid *const *gs, int m, const pc_bins *b, cons
  *             NULL; both written on return
  * All temporaries live in one fixed device array of about 12.3 MiB inside the
  * library, which every GPU that loads the library holds until the process
- * exits.  Its device address is looked up on the first call on each device,
- * so make that first call before any stream capture.  Like the library's
+ * exits.  Its device address is looked up on the first call on each device
+ * (a lookup that allocates nothing).  Like the library's
  * other per-device state (count workspaces, captured graphs), that address
  * does not survive a cudaDeviceReset of the device: do not call the library
  * on a device after resetting it.  Limits (PC_EOVERFLOW
