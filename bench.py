@@ -55,9 +55,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-mocks", type=int, default=4,
+                    help="batched mocks: time the plain FP64 kernel on this many of them")
     ap.add_argument("--fp64-shards", type=int, default=0,
                     help="plain FP64 arm of the weighted workloads: time it on 1/S of the "
-                         "i-blocks (0: 64 for catalogues of 5e7 points or more, else 1)")
+                         "i-blocks (0: 64 for catalogues of 5e7 points or more, 16 from 1e7, "
+                         "else 1)")
     ap.add_argument("--no-weights", action="store_true",
                     help="weighted workloads: count the same catalogues without their weights "
                          "(to compare the weighted and unweighted kernels)")
@@ -670,20 +673,21 @@ def run_batch(args):
 
     last_stats = []
 
-    def step(xs=X, counts=out, batched=True):
+    def step(xs=X, counts=out, batched=True, o=None):
+        o = opts if o is None else o
         if tree:
             # every mock's k-d tree in one level loop
             ts = P.pc_build_tree_batch(xs, box=box, n_leaf=args.n_leaf, list_cap=list_cap,
                                        stream=stream)
         else:
-            ts = [P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=opts, stream=stream)
+            ts = [P.pc_build_grid(x, box=box, r_max=bins.r_max, opts=o, stream=stream)
                   for x in xs]
         try:
             if batched:
                 if tree:
-                    _, _, st = P.pc_count_tree_batch(ts, bins, opts, stream, counts=counts)
+                    _, _, st = P.pc_count_tree_batch(ts, bins, o, stream, counts=counts)
                 else:
-                    _, _, st = P.pc_count_batch(ts, bins, opts, stream, counts=counts)
+                    _, _, st = P.pc_count_batch(ts, bins, o, stream, counts=counts)
                 last_stats.append(st)
                 return st.candidates
             cand = 0
@@ -745,6 +749,91 @@ def run_batch(args):
         e2e = {"value": inr_all / args.steps / (e2e_t * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(n_tot * 24), "d2h_bytes_per_step": int(m * bins.nbins * 8),
                "ms_per_step": e2e_t}
+    peaks = measured_fp_peaks(P, stream, local)
+
+    # ---- roofline of the batched pair kernel --------------------------------
+    # The graph replay hides the pair kernel's own duration: one more batched
+    # count launched directly gives the library's event-timed pair kernel
+    # (the tree batch is never graph-replayed, so its timed steps give it).
+    if tree:
+        kst = last_stats[-1]
+    else:
+        import ctypes
+        o_direct = P.pc_opts()
+        ctypes.memmove(ctypes.byref(o_direct), ctypes.byref(opts), ctypes.sizeof(opts))
+        o_direct.use_graph = 0
+        kcounts = torch.zeros_like(out)
+        step(counts=kcounts, o=o_direct)
+        torch.cuda.synchronize()
+        same = same and bool(torch.equal(kcounts, batched_counts))
+        kst = last_stats[-1]
+    roof = None
+    if kst.ms_pairs > 0:
+        fp32_peak = peaks["fp32_tflops"]
+        achieved = FLOPS_PER_CANDIDATE * float(kst.candidates) / (kst.ms_pairs * 1e-3) / 1e12
+        evaluated = kst.candidates - kst.pruned
+        ach_ev = ((FLOPS_PER_CANDIDATE * float(evaluated) + FLOPS_PER_IN_RANGE * inr_step)
+                  / (kst.ms_pairs * 1e-3) / 1e12)
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "k_pairs_f32<%s,LOS_%s>, one launch over all %d mocks"
+                          % (w.mode.upper(), w.los.upper(), m),
+                "kernel_ms": kst.ms_pairs,
+                "kernel_share_of_step": kst.ms_pairs / (t_max / args.steps),
+                "timed": ("the timed steps' batched launch" if tree else
+                          "one batched launch outside the graph, same options and blocks"),
+                "flops_per_launch": FLOPS_PER_CANDIDATE * float(kst.candidates),
+                "flops_definition": "8 FP32 flops per candidate pair (%.4g per launch)"
+                                    % float(kst.candidates),
+                "achieved_evaluated": ach_ev, "frac_evaluated": ach_ev / fp32_peak,
+                "evaluated_definition": "8 per pair evaluated one by one (%.4g) + 6 per in-range "
+                                        "pair (%.4g)" % (float(evaluated), inr_step),
+                "peak_source": "measured: " + peaks["how"] + " (" + peaks["profile"] + ")"}
+
+    # ---- plain FP64 kernel on a subset of the mocks ---------------------------
+    fp64 = None
+    if args.fp64_steps > 0 and not tree and world == 1:
+        k64 = min(m, max(1, args.fp64_mocks))
+        n64 = sum(int(X[k].shape[0]) for k in range(k64))
+        o64 = P.make_opts("f64", P.pc_suggest_cell_size(n64 // k64, w.L ** 3, bins.r_max), 1)
+        o64.use_graph = 0
+        out64 = torch.zeros(k64 * bins.nbins, dtype=torch.int64, device=dev)
+        step(xs=X[:k64], counts=out64, o=o64)
+        torch.cuda.synchronize()
+        ms64 = []
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(xs=X[:k64], counts=out64, o=o64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms64.append(a.elapsed_time(b))
+        s64 = last_stats[-1]
+        inr64 = float(out64.sum().item())
+        fl64 = FLOPS_PER_CANDIDATE * float(s64.candidates) + FLOPS_PER_IN_RANGE * inr64
+        k64_ms = s64.ms_pairs if s64.ms_pairs > 0 else statistics.mean(ms64)
+        ach64 = fl64 / (k64_ms * 1e-3) / 1e12
+        fp64 = {"value": inr64 / (statistics.mean(ms64) * 1e-3), "unit": UNIT,
+                "mocks": f"the first {k64} of the {m} mocks ({n64} points), one batched launch",
+                "cell_size": o64.cell_size, "ms_per_step": statistics.mean(ms64),
+                "steps": args.fp64_steps,
+                "counts_identical_to_fp32_rescue":
+                    bool(torch.equal(out64, batched_counts[:k64 * bins.nbins])),
+                "roofline": {"bound": "fp64", "achieved": ach64, "peak": peaks["fp64_tflops"],
+                             "unit": "TFLOP/s", "frac": ach64 / peaks["fp64_tflops"],
+                             "peak_source": "measured: DFMA loop (pc_fp_peak), " + peaks["profile"],
+                             "kernel_ms": k64_ms}}
+
+    # ---- the oracle on the host cores ----------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, dt, ms_, cores, evals = oracle_sample_rate(mocks[med], w, args.cpu_seconds, L=w.L)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{ms_} random points of the median mock x all its "
+                         f"{mocks[med].shape[0]} points (brute force, binary64), {dt:.1f} s; "
+                         f"in-range pairs found per second",
+               "pair_evaluations_per_s": evals, "cpu_model": cpu_model()}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -774,6 +863,7 @@ def run_batch(args):
             "loop_of_single_counts_ms": loop_ms[0],
             "batched_speedup_vs_loop": loop_ms[0] / (t_max / args.steps),
             "loop_counts_identical": same,
+            "roofline": roof, "fp64_path": fp64, "cpu_baseline": cpu, "measured_peaks": peaks,
             "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)
@@ -996,7 +1086,8 @@ def run_sets(args, extra=None):
     fp64 = None
     if args.fp64_steps > 0 and not tree and world == 1:
         n_big = host[big][0].shape[0]
-        S = args.fp64_shards if args.fp64_shards > 0 else (64 if n_big >= 50_000_000 else 1)
+        S = args.fp64_shards if args.fp64_shards > 0 else \
+            (64 if n_big >= 50_000_000 else (16 if n_big >= 10_000_000 else 1))
         vol = float(np.prod(np.asarray(box.hi) - np.asarray(box.lo))) if not w.periodic \
             else float(L_box) ** 3
         cell64 = P.pc_suggest_cell_size(n_big, vol, bins.r_max)

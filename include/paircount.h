@@ -133,7 +133,13 @@ typedef struct {
                                     weight a non-negative normal binary32 value or zero, each
                                     grid's weight exponents spanning at most 8 binades and
                                     the two grids' spans adding up to at most 12; truncation
-                                    below 2^-34 relative), flushed in binary64 */
+                                    below 2^-34 relative), flushed in binary64; 3 the same
+                                    for binary64 weights: the integer products of their
+                                    binary32 roundings hi (conditions as for 2 on the his,
+                                    which must reach 2^-78 where the weight is not a
+                                    binary32 value) plus the binary32 terms hi_i lo_j +
+                                    lo_i hi_j of their remainders lo = fl32(w - hi), rounded
+                                    to the accumulators' unit (below 2^-34 relative) */
     long long tree_pairs;        /* pc_count_tree: list node pairs listed by the traversal */
     float ms_traverse;           /* pc_count_tree: device-and-host time of the traversal */
 } pc_stats;

@@ -545,6 +545,7 @@ struct CountJob {
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     double rmin = 0.0;
     bool wint_ok = true;   // every task's grids allow the integer weight path
+    bool wcorr = false;    // some grid's binary64 weights add remainders
 };
 
 // Integer weight products are truncated by at most 2^(k_i + k_j - 46)
@@ -555,6 +556,7 @@ static void job_add_wint(CountJob &J, const pc_grid *gi, const pc_grid *gj) {
     if (!gi->wint || !gj->wint ||
         (gi->wemax - gi->wemin) + (gj->wemax - gj->wemin) > WINT_MAX_SPAN)
         J.wint_ok = false;
+    if (gi->wcorr || gj->wcorr) J.wcorr = true;
 }
 
 // Lower bound of |x| over the points of a grid (0 when unknown or periodic).
@@ -591,7 +593,8 @@ struct CountSetup {
     pc_opts o;
     int prec = 0, ipt = 2, bi = 256, dev = 0, ntasks = 0, ncell = 0;
     bool weighted = false;
-    int wsum = 0;   // weighted sums: 0 none, 1 binary64 products, 2 integer products
+    int wsum = 0;   // weighted sums: 0 none, 1 binary64 products, 2 integer products,
+                    // 3 integer products with binary64 remainders
     size_t nblk_cap = 0, hist_n = 0;
     unsigned long long qcap = 0;
 };
@@ -768,6 +771,7 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
     // until it fits, else the global histogram
     auto fit = [&](bool wint) {
         p.wint = wint ? 1 : 0;
+        p.wcorr = (wint && J.wcorr) ? 1 : 0;
         choose_replication(S.o.priv, P.nbins, S.weighted && !wint, p.priv, p.hist_k);
         for (;;) {
             p.wint_k = p.hist_k;   // the weight records take the counts' lane copies
@@ -899,7 +903,7 @@ static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *o
     size_t smem = 0;
     s = make_params(J, S, B, p, grid, smem);
     if (s != PC_OK) return s;
-    S.wsum = p.wint ? 2 : (S.weighted ? 1 : 0);
+    S.wsum = p.wint ? (p.wcorr ? 3 : 2) : (S.weighted ? 1 : 0);
     Events ev(stats != nullptr);
     const long long launches0 = launch_count();
     if (ev.on) PC_CUDA(cudaEventRecord(ev.e[0], st));
@@ -1018,7 +1022,7 @@ static pc_status run_count_graph(const CountJob &J, const std::vector<const pc_g
         size_t smem = 0;
         s = make_params(J, N->S, N->B, p, grid, smem);
         if (s != PC_OK) return s;
-        N->S.wsum = p.wint ? 2 : (N->S.weighted ? 1 : 0);
+        N->S.wsum = p.wint ? (p.wcorr ? 3 : 2) : (N->S.weighted ? 1 : 0);
         const size_t hb = N->S.hist_n;
         PC_CUDA(::pc::alloc_host(&N->h_hist, sizeof(unsigned long long) * hb));
         if (weighted) PC_CUDA(::pc::alloc_host(&N->h_whist, sizeof(double) * hb));
@@ -1092,8 +1096,8 @@ static pc_status run_count_graph(const CountJob &J, const std::vector<const pc_g
 
 static TaskDev task_of(const pc_grid *gi, const pc_grid *gj, int hist, int is_auto) {
     TaskDev t;
-    t.gi = GridDev{gi->rel, gi->cx, gi->xw, gi->cell_start, gi->n};
-    t.gj = GridDev{gj->rel, gj->cx, gj->xw, gj->cell_start, gj->n};
+    t.gi = GridDev{gi->rel, gi->cx, gi->xw, gi->cell_start, gi->n, gi->wlo};
+    t.gj = GridDev{gj->rel, gj->cx, gj->xw, gj->cell_start, gj->n, gj->wlo};
     t.hist = hist;
     t.is_auto = is_auto;
     // one unit of the integer weight products: 2^(emax_i + emax_j - 300)
@@ -1214,8 +1218,8 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
 
     CountJob J;
     TaskDev T;
-    T.gi = GridDev{t1->rel, nullptr, t1->xw, nullptr, t1->n};
-    T.gj = GridDev{tj->rel, nullptr, tj->xw, nullptr, tj->n};
+    T.gi = GridDev{t1->rel, nullptr, t1->xw, nullptr, t1->n, t1->wlo};
+    T.gj = GridDev{tj->rel, nullptr, tj->xw, nullptr, tj->n, tj->wlo};
     T.hist = 0;
     T.is_auto = is_auto ? 1 : 0;
     T.wscale = (t1->wint && tj->wint) ? ldexp(1.0, t1->wemax + tj->wemax - 300) : 0.0;
@@ -1242,6 +1246,7 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
     if (!t1->wint || !tj->wint ||
         (t1->wemax - t1->wemin) + (tj->wemax - tj->wemin) > WINT_MAX_SPAN)
         J.wint_ok = false;
+    if (t1->wcorr || tj->wcorr) J.wcorr = true;
 
     pc_opts o;
     memset(&o, 0, sizeof(o));
@@ -1265,7 +1270,7 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
     size_t smem = 0;
     s = make_params(J, S, B, p, grid, smem);
     if (s != PC_OK) return s;
-    S.wsum = p.wint ? 2 : (S.weighted ? 1 : 0);
+    S.wsum = p.wint ? (p.wcorr ? 3 : 2) : (S.weighted ? 1 : 0);
     Events ev(stats != nullptr);
     const long long launches0 = launch_count();
     if (ev.on) PC_CUDA(cudaEventRecord(ev.e[0], st));
@@ -1338,7 +1343,7 @@ extern "C" pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const 
         if (wcounts && !t->weighted)
             return fail(PC_EINVAL, "pc_count_tree_batch: weighted counts need weights on every tree");
         TaskDev T;
-        T.gi = GridDev{t->rel, nullptr, t->xw, nullptr, t->n};
+        T.gi = GridDev{t->rel, nullptr, t->xw, nullptr, t->n, t->wlo};
         T.gj = T.gi;
         T.hist = k;
         T.is_auto = 1;
@@ -1351,6 +1356,7 @@ extern "C" pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const 
         }
         J.rmin = k ? std::min(J.rmin, tree_rmin(t)) : tree_rmin(t);
         if (!t->wint || 2 * (t->wemax - t->wemin) > WINT_MAX_SPAN) J.wint_ok = false;
+        if (t->wcorr) J.wcorr = true;
         nlist += (long long)(1 << t->blevel) * tree_chunks(t, o.ipt);
     }
     if (nlist >= (1LL << 31)) return fail(PC_EOVERFLOW, "pc_count_tree_batch: too many blocks");
@@ -1382,7 +1388,7 @@ extern "C" pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const 
     size_t smem = 0;
     s = make_params(J, S, B, p, grid, smem);
     if (s != PC_OK) return s;
-    S.wsum = p.wint ? 2 : (S.weighted ? 1 : 0);
+    S.wsum = p.wint ? (p.wcorr ? 3 : 2) : (S.weighted ? 1 : 0);
     Events ev(stats != nullptr);
     const long long launches0 = launch_count();
     if (ev.on) PC_CUDA(cudaEventRecord(ev.e[0], st));

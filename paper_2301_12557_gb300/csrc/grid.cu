@@ -148,42 +148,55 @@ __global__ void k_cell_starts(const int *__restrict__ key_start, int ncell, int 
     cell_start[c] = key_start[(size_t)c << (3 * sub_bits)];
 }
 
-// Weight statistics for the integer weight path: out[0] counts weights that
-// are not finite, negative, subnormal or not exactly a binary32 value;
-// out[1] / out[2] receive the largest / smallest biased binary32 exponent
-// of the non-zero weights.
+// Weight statistics for the integer weight path, on each weight's binary32
+// rounding hi: out[0] counts weights that are not finite, negative or whose
+// hi is subnormal (or zero for a weight that is not), and binary64 weights
+// that are not binary32 values and whose hi lies below 2^-78 (their
+// remainder would lose bits to binary32 underflow); out[1] / out[2] receive
+// the largest / smallest biased exponent of the non-zero his; out[3] counts
+// the binary64 weights that are not binary32 values (remainder lo != 0).
 __global__ void k_wstats(const void *__restrict__ w, int w_is_f32, int n, int *out) {
-    int bad = 0, emax = -1, emin = 1000;
+    int bad = 0, nlo = 0, emax = -1, emin = 1000;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float f;
+        bool inexact = false;
         if (w_is_f32) {
             f = ((const float *)w)[i];
         } else {
             const double d = ((const double *)w)[i];
             f = __double2float_rn(d);
-            if ((double)f != d) { ++bad; continue; }
+            inexact = (double)f != d;
         }
         const unsigned b = __float_as_uint(f);
         const int e = (int)((b >> 23) & 0xFF);
         if ((b >> 31) || e == 0xFF || (e == 0 && (b & 0x7FFFFF))) { ++bad; continue; }
-        if (e == 0) continue;   // +0 (and -0 above counts as negative)
+        if (e == 0) {            // +0 (and -0 above counts as negative)
+            if (inexact) ++bad;
+            continue;
+        }
+        if (inexact) {
+            if (e < 49) { ++bad; continue; }
+            ++nlo;
+        }
         emax = max(emax, e);
         emin = min(emin, e);
     }
     for (int o = 16; o > 0; o >>= 1) {
         bad += __shfl_xor_sync(0xffffffffu, bad, o);
+        nlo += __shfl_xor_sync(0xffffffffu, nlo, o);
         emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
         emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
     }
     if ((threadIdx.x & 31) == 0) {
         if (bad) atomicAdd(&out[0], bad);
+        if (nlo) atomicAdd(&out[3], nlo);
         atomicMax(&out[1], emax);
         atomicMin(&out[2], emin);
     }
 }
 
-pc_status weight_stats(const void *w, int w_is_f32, int n, cudaStream_t st, int r[3]) {
-    int init[3] = {0, -1, 1000};
+pc_status weight_stats(const void *w, int w_is_f32, int n, cudaStream_t st, int r[4]) {
+    int init[4] = {0, -1, 1000, 0};
     int *ws = nullptr;
     cudaError_t e = ::pc::alloc_dev_async(&ws, sizeof(init), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ws, init, sizeof(init), cudaMemcpyHostToDevice, st);
@@ -193,7 +206,7 @@ pc_status weight_stats(const void *w, int w_is_f32, int n, cudaStream_t st, int 
         note_launch();
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(r, ws, sizeof(int) * 3, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r, ws, sizeof(int) * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (ws) cudaFreeAsync(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "weight statistics");
@@ -218,7 +231,7 @@ __global__ void k_scatter(const double *__restrict__ xyz, const void *__restrict
                           const int *__restrict__ slot, const int *__restrict__ key_start,
                           float4 *__restrict__ rel,
                           uint16_t *__restrict__ cxo, double4_32a *__restrict__ xw,
-                          int *__restrict__ perm) {
+                          int *__restrict__ perm, float *__restrict__ wlo) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int key = cell[i];
@@ -239,6 +252,7 @@ __global__ void k_scatter(const double *__restrict__ xyz, const void *__restrict
     if (w) wv = w_is_f32 ? (double)((const float *)w)[i] : ((const double *)w)[i];
     const unsigned wp = (w && wpack_emax > 0) ? pack_weight(wv, wpack_emax, wpack_span) : 0u;
     rel[pos] = make_float4(r[0], r[1], r[2], __uint_as_float(wp));
+    if (wlo) wlo[pos] = weight_lo(wv, wpack_emax);
     cxo[pos] = (uint16_t)id[0];
     xw[pos] = make_double4_32a(x[0], x[1], x[2], wv);
     perm[pos] = i;
@@ -445,6 +459,7 @@ static void grid_release(pc_grid *g) {
     cudaFree(g->xw);
     cudaFree(g->cell_start);
     cudaFree(g->perm);
+    cudaFree(g->wlo);
     delete g;
 }
 
@@ -604,11 +619,12 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     }
     g->ncell = G.ng[0] * G.ng[1] * G.ng[2];
 
-    // weights usable by the integer weight path: every weight exactly a
-    // non-negative normal binary32 value (or zero); exponent range recorded
+    // weights usable by the integer weight path: every weight's binary32
+    // rounding a non-negative normal value (or zero); exponent range recorded;
+    // binary64 weights that are not binary32 values add their remainders
     g->wint = 0;
     if (dw && n > 0) {
-        int res[3];
+        int res[4];
         pc_status ws = weight_stats(dw, w_is_f32, (int)n, st, res);
         if (ws != PC_OK) {
             cleanup();
@@ -620,6 +636,7 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
             g->wint = 1;
             g->wemax = res[1] >= 0 ? res[1] : 1;      // all zero: any exponent works
             g->wemin = res[1] >= 0 ? res[2] : 1;
+            g->wcorr = res[3] > 0 ? 1 : 0;
         }
     }
 
@@ -631,6 +648,7 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
     if (e == cudaSuccess) e = ::pc::alloc_dev(&g->xw, sizeof(double4_32a) * nn);
     if (e == cudaSuccess) e = ::pc::alloc_dev(&g->cell_start, sizeof(int) * (g->ncell + 1));
     if (e == cudaSuccess) e = ::pc::alloc_dev(&g->perm, sizeof(int) * nn);
+    if (e == cudaSuccess && g->wcorr) e = ::pc::alloc_dev(&g->wlo, sizeof(float) * nn);
     if (e != cudaSuccess) {
         cleanup();
         grid_release(g);
@@ -668,7 +686,7 @@ extern "C" pc_status pc_build_grid(const double *xyz, const void *w, int w_is_f3
         k_scatter<<<blocks, 256, 0, st>>>(dxyz, dw, w_is_f32, g->wint ? g->wemax : 0,
                                           WINT_GRID_SPAN, (int)n, G,
                                           sub_bits, cell, slot, key_start, g->rel, g->cx, g->xw,
-                                          g->perm);
+                                          g->perm, g->wlo);
         note_launch();
         e = cudaGetLastError();
     }

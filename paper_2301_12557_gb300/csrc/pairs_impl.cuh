@@ -32,7 +32,9 @@ namespace pc {
 constexpr unsigned long long FLUSH_LIMIT = 1ull << 30;
 // integer weight path: products (each < 2^48) per lane copy between flushes;
 // each of its three u32 piece sums then adds less than 2^16 pieces of 16
-// bits, and the copy's recombined sum stays below 2^64
+// bits, and the copy's recombined sum stays below 2^64.  With binary64
+// remainders (W == 3) a product is below 2^49, its top piece below 2^17,
+// and half as many products fit.
 constexpr unsigned long long WINT_LIMIT = 1ull << 16;
 
 struct SmemLayout {
@@ -72,9 +74,11 @@ __host__ __device__ inline SmemLayout smem_layout(const PairParams &p, bool f64)
     L.meta = o;
     if (f64) o = align_up(o + (size_t)2 * tj * sizeof(int2), 16);
     else if (p.tree) o = align_up(o + (size_t)MAXSEG_T * sizeof(float4), 16);   // segment offsets
-    L.tw = o;   // staged j weights: binary64, or the packed 4-byte integer weights
+    // staged j weights: binary64, or the packed 4-byte integer weights (and,
+    // with binary64 remainders, the 4-byte remainders after them)
+    L.tw = o;
     if (p.weighted && !f64)
-        o = align_up(o + (size_t)2 * tj * (p.wint ? sizeof(unsigned) : sizeof(double)), 16);
+        o = align_up(o + (size_t)2 * tj * (p.wint ? (p.wcorr ? 2 : 1) * sizeof(unsigned) : sizeof(double)), 16);
     L.q = o;
     o = align_up(o + (size_t)LQ * sizeof(uint3), 16);
     L.gstride = o - L.seg;
@@ -565,6 +569,32 @@ __device__ __forceinline__ void red_shared_pieces(unsigned addr, unsigned long l
         "red.shared.add.u32 [%0+8], %3;" ::"r"(addr),
         "r"(lo >> 16), "r"(hi & 0xFFFFu), "r"(hi >> 16));
 }
+// Integer weight product of a pair with binary64 remainders (W == 3), in
+// units of the task's wscale: V = round(P / 2^16 + c) with P the exact
+// product of the packed weights (hi_i hi_j = P 2^-16 wscale) and c the
+// remainder terms (hi_i lo_j + lo_i hi_j) / wscale = pf_i l_j + l_i pf_j (l
+// the scaled remainders, pf the packed weights as binary32), evaluated in
+// binary32 (|c| < 2^-23 P / 2^16 < 2^25) and rounded to an integer.  V is
+// non-negative and below 2^49; its error against the exact w_i w_j / wscale
+// is at most 1 + 2^-40 P / 2^16 units (the two roundings, the dropped
+// lo_i lo_j and the binary32 error of c).
+__device__ __forceinline__ unsigned long long corrected_product(unsigned wi, float pfi, float li,
+                                                                unsigned wj, float lj) {
+    const float c = fmaf(pfi, lj, li * __uint2float_rn(wj));
+    const long long k = (long long)__float2int_rn(c);
+    const unsigned long long P = (unsigned long long)wi * wj;
+    return ((P + 0x8000ull) >> 16) + (unsigned long long)k;
+}
+// The three pieces of V (bits 0-15, 16-31 and 32-48) into one lane copy's
+// record, as red_shared_pieces does for P >> 16.
+__device__ __forceinline__ void red_shared_pieces_v(unsigned addr, unsigned long long V) {
+    const unsigned lo = (unsigned)V, hi = (unsigned)(V >> 32);
+    asm volatile(
+        "red.shared.add.u32 [%0], %1;\n\t"
+        "red.shared.add.u32 [%0+4], %2;\n\t"
+        "red.shared.add.u32 [%0+8], %3;" ::"r"(addr),
+        "r"(lo & 0xFFFFu), "r"(lo >> 16), "r"(hi));
+}
 __device__ __forceinline__ void red_shared_f64_if(unsigned addr, double v, bool on) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p red.shared.add.f64 [%0], %1;\n\t}"
@@ -598,6 +628,7 @@ struct IPts {
     float xa[RI], ya[RI], za[RI];  // absolute positions (midpoint line of sight)
     double w[RI];
     unsigned wm[RI];               // packed integer weight (integer weight path)
+    float wl[RI], pf[RI];          // W == 3: scaled remainder, packed weight as binary32
     int idx[RI];
 };
 
@@ -606,7 +637,8 @@ struct IPts {
 struct Tile {
     const float *x, *y, *z;
     const double *w;               // binary64 weights (W == 1)
-    const unsigned *wm;            // packed integer weights (W == 2), same storage
+    const unsigned *wm;            // packed integer weights (W >= 2), same storage
+    const float *wl;               // scaled binary64 remainders (W == 3), after wm
 };
 
 // Table-based bins, one pair at a time (every mode and line of sight).
@@ -795,6 +827,14 @@ __device__ __forceinline__ void pair_tile_lin2(const PairParams &p, Tile tb, int
                     const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
                     red_shared_pieces(3u * c0 + wdelta, (unsigned long long)I.wm[r] * wj.x);
                     red_shared_pieces(3u * c1 + wdelta, (unsigned long long)I.wm[r] * wj.y);
+                } else if (W == 3) {
+                    // the same product with the binary64 remainders' terms
+                    const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
+                    const float2 lj = *reinterpret_cast<const float2 *>(tb.wl + jj);
+                    red_shared_pieces_v(3u * c0 + wdelta,
+                                        corrected_product(I.wm[r], I.pf[r], I.wl[r], wj.x, lj.x));
+                    red_shared_pieces_v(3u * c1 + wdelta,
+                                        corrected_product(I.wm[r], I.pf[r], I.wl[r], wj.y, lj.y));
                 }
                 re0[r] = in0[r] && n0;
                 re1[r] = in1[r] && n1;
@@ -929,6 +969,13 @@ __device__ __forceinline__ void pair_tile_sigpi2(const PairParams &p, Tile tb, i
                     const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
                     red_shared_pieces(3u * c0 + wdelta, (unsigned long long)I.wm[r] * wj.x);
                     red_shared_pieces(3u * c1 + wdelta, (unsigned long long)I.wm[r] * wj.y);
+                } else if (W == 3) {
+                    const uint2 wj = *reinterpret_cast<const uint2 *>(tb.wm + jj);
+                    const float2 lj = *reinterpret_cast<const float2 *>(tb.wl + jj);
+                    red_shared_pieces_v(3u * c0 + wdelta,
+                                        corrected_product(I.wm[r], I.pf[r], I.wl[r], wj.x, lj.x));
+                    red_shared_pieces_v(3u * c1 + wdelta,
+                                        corrected_product(I.wm[r], I.pf[r], I.wl[r], wj.y, lj.y));
                 }
                 re0[r] = in0[r] && n0;
                 re1[r] = in1[r] && n1;
@@ -990,7 +1037,7 @@ __device__ __forceinline__ void pair_tile(const PairParams &p, bool smem_hist, T
                                           unsigned hk4, size_t hbase, uint3 *s_q, int *s_qn,
                                           const int4 *s_seg,
                                           int nseg, int f0, int fstride, int bstart, unsigned task_bits) {
-    static_assert(W != 2 || LIN, "integer weights run only with floor-based bins");
+    static_assert(W < 2 || LIN, "integer weights run only with floor-based bins");
     if (!smem_hist) {
         pair_tile_global<MODE, LOS, W, RI, MASK>(p, tb, len, gmask, I, bc, r2cut, hbase, s_q, s_qn, s_seg,
                                                  nseg, f0, fstride, bstart, task_bits);
@@ -1053,6 +1100,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     float *s_tz = s_ty + 2 * TJ;
     double *s_tw = (double *)(gsm + Ly.tw);
     unsigned *s_twm = (unsigned *)(gsm + Ly.tw);   // packed weights share the storage
+    float *s_twl = (float *)(s_twm + 2 * TJ);      // W == 3: remainders after them
     uint3 *s_q = (uint3 *)(gsm + Ly.q);
     float4 *s_soff = (float4 *)(gsm + Ly.meta);   // tree: offset of each segment's block centre
 
@@ -1063,7 +1111,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     if (smem_hist) {
         const int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
         for (int k = threadIdx.x; k < p.nbins_smem * copies; k += NT * G) s_hist[k] = 0;
-        if (W == 2) {   // the integer weight records
+        if (W >= 2) {   // the integer weight records
             unsigned *wp = reinterpret_cast<unsigned *>(s_whist);
             for (int k = threadIdx.x; k < 3 * p.nbins_smem * p.wint_k; k += NT * G) wp[k] = 0u;
         } else if (W) {
@@ -1110,23 +1158,23 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
                              (p.priv ? (unsigned)((tid >> 5) * p.nbins_smem * p.hist_k * 4) : 0u) +
                              4u * lane_copy;
     const unsigned whist_sa = (unsigned)__cvta_generic_to_shared(s_whist) +
-                              (W == 2 ? 12u * lane_copy : 8u * lane_copy);
+                              (W >= 2 ? 12u * lane_copy : 8u * lane_copy);
 
     const int nx = p.g.ng[0], ny = p.g.ng[1];
     const float c32x = p.g.c32[0], c32y = p.g.c32[1], c32z = p.g.c32[2];
     const int nblocks = *p.nblocks;
     unsigned long long cand_local = 0;    // thread 0 only
     unsigned long long since_flush = 0;   // CTA-uniform
-    unsigned long long wterms = 0;        // CTA-uniform bound of products per u64 copy (W == 2)
+    unsigned long long wterms = 0;        // CTA-uniform bound of products per lane copy (W >= 2)
     int cur_hist = -1;
     double cur_wscale = 0.0;
     // integer weights: before n more j-points, flush if a lane copy of the
     // weight records could exceed WINT_LIMIT products (NT / wint_k threads
     // share a copy; each piece sum then stays below 2^16 x 2^16)
     auto wint_room = [&](int n) {
-        if (W != 2) return;
+        if (W < 2) return;
         const unsigned long long add = (unsigned long long)(NT / p.wint_k) * RI * (unsigned)n;
-        if (wterms + add > WINT_LIMIT) {
+        if (wterms + add > (W == 3 ? WINT_LIMIT / 2 : WINT_LIMIT)) {
             flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
             since_flush = 0;
             wterms = 0;
@@ -1142,7 +1190,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
         if (bidx >= nblocks) break;
         const Block B = p.blocks[bidx];
         const TaskDev &T = p.tasks[B.task];
-        if (T.hist != cur_hist || (W == 2 && T.wscale != cur_wscale)) {
+        if (T.hist != cur_hist || (W >= 2 && T.wscale != cur_wscale)) {
             flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
             cur_hist = T.hist;
             cur_wscale = T.wscale;
@@ -1163,11 +1211,16 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
             I.xa[r] = I.ya[r] = I.za[r] = 0.f;
             I.w[r] = 0.0;
             I.wm[r] = 0u;
+            I.wl[r] = I.pf[r] = 0.f;
             I.x[r] = I.y[r] = I.z[r] = -1.0e18f;  // unused lane: far from every j (and from the +1e18 pad slot)
             if (loc < B.count) {
                 float4 q = T.gi.rel[I.idx[r]];
                 I.x[r] = q.x; I.y[r] = q.y; I.z[r] = q.z;
                 I.wm[r] = __float_as_uint(q.w);
+                if (W == 3) {
+                    I.pf[r] = __uint2float_rn(I.wm[r]);
+                    I.wl[r] = T.gi.wlo ? T.gi.wlo[I.idx[r]] : 0.f;
+                }
                 if (LOS == LOS_MID || W == 1) {
                     double4_32a a = T.gi.xw[I.idx[r]];
                     I.xa[r] = (float)a.x; I.ya[r] = (float)a.y; I.za[r] = (float)a.z;
@@ -1201,18 +1254,20 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
                     float4 q = T.gj.rel[pj];
                     s_tx[f] = q.x; s_ty[f] = q.y; s_tz[f] = q.z;
                     if (W == 1) s_tw[f] = T.gj.xw[pj].w;
-                    if (W == 2) s_twm[f] = __float_as_uint(q.w);
+                    if (W >= 2) s_twm[f] = __float_as_uint(q.w);
+                    if (W == 3) s_twl[f] = T.gj.wlo ? T.gj.wlo[pj] : 0.f;
                 } else {
                     s_tx[f] = s_ty[f] = s_tz[f] = 1.0e18f;
                     if (W == 1) s_tw[f] = 0.0;
-                    if (W == 2) s_twm[f] = 0u;
+                    if (W >= 2) s_twm[f] = 0u;
+                    if (W == 3) s_twl[f] = 0.f;
                 }
             }
             gsync<G>();
             wint_room(lenA);
             const int ngA = (lenA + JG - 1) / JG;    // all groups evaluated
             const unsigned maskA = ngA >= 32 ? 0xffffffffu : (1u << ngA) - 1u;
-            pair_tile<MODE, LOS, W, RI, LIN, true>(p, smem_hist, Tile{s_tx, s_ty, s_tz, s_tw, s_twm}, lenA,
+            pair_tile<MODE, LOS, W, RI, LIN, true>(p, smem_hist, Tile{s_tx, s_ty, s_tz, s_tw, s_twm, s_twl}, lenA,
                                                    maskA, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q,
                                                    &cs.qn, s_seg, 0, -1, 0, B.start, task_bits);
             if (tid == 0) cand_local += (unsigned long long)B.count * (B.count - 1) / 2;
@@ -1299,6 +1354,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
             constexpr int SPT = TJ / NT;
             float4 rq[SPT];
             double rw[SPT];
+            float rwl[SPT];
             int rcx[SPT], rmeta[SPT], rimg[SPT];
             bool rv[SPT];
             auto load_tile = [&](int t) {
@@ -1315,6 +1371,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
                         rmeta[s] = sg.z;
                         rimg[s] = sg.w;
                         if (W == 1) rw[s] = T.gj.xw[pj].w;
+                        if (W == 3) rwl[s] = T.gj.wlo ? T.gj.wlo[pj] : 0.f;
                     }
                 }
             };
@@ -1348,7 +1405,8 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
                         s_ty[buf * TJ + slot] = y;
                         s_tz[buf * TJ + slot] = z;
                         if (W == 1) s_tw[buf * TJ + slot] = wv;
-                        if (W == 2) s_twm[buf * TJ + slot] = rv[s] ? __float_as_uint(rq[s].w) : 0u;
+                        if (W >= 2) s_twm[buf * TJ + slot] = rv[s] ? __float_as_uint(rq[s].w) : 0u;
+                        if (W == 3) s_twl[buf * TJ + slot] = rv[s] ? rwl[s] : 0.f;
                     }
                     // boxes of the j-groups (JG consecutive slots each)
                     const GBox gb = lane_group_box(x, y, z, rv[s]);
@@ -1369,7 +1427,7 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
                 pair_tile<MODE, LOS, W, RI, LIN, false>(
                     p, smem_hist,
                     Tile{s_tx + buf * TJ, s_ty + buf * TJ, s_tz + buf * TJ, s_tw + buf * TJ,
-                         s_twm + buf * TJ},
+                         s_twm + buf * TJ, s_twl + buf * TJ},
                     len, gm, I, bc, lc, r2cut, hist_sa, whist_sa, hk4, hbase, s_q, &cs.qn, s_seg,
                     nseg, t, ntiles, B.start, task_bits);
                 since_flush += (unsigned long long)len * B.count;
@@ -1562,6 +1620,8 @@ PairKernel<MODE, LOS> pick_f32(const PairParams &p, int ipt) {
     }
     if (p.weighted) {
         if constexpr (LINOK) {
+            if (lin && p.wint && p.wcorr) return ipt == 4 ? k_pairs_f32<MODE, LOS, 3, 4, true>
+                                                          : k_pairs_f32<MODE, LOS, 3, 2, true>;
             if (lin && p.wint) return ipt == 4 ? k_pairs_f32<MODE, LOS, 2, 4, true>
                                                : k_pairs_f32<MODE, LOS, 2, 2, true>;
         }
@@ -1579,6 +1639,7 @@ PairKernel<MODE, LOS> pick_f32_tree_ri(const PairParams &p) {
     const bool lin = LINOK && p.lin;
     if (p.weighted) {
         if constexpr (LINOK) {
+            if (lin && p.wint && p.wcorr) return k_pairs_f32<MODE, LOS, 3, RI, true, 1, true>;
             if (lin && p.wint) return k_pairs_f32<MODE, LOS, 2, RI, true, 1, true>;
         }
         return lin ? k_pairs_f32<MODE, LOS, 1, RI, LINOK, 1, true> : k_pairs_f32<MODE, LOS, 1, RI, false, 1, true>;

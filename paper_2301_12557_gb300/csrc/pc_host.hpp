@@ -19,8 +19,11 @@ struct pc_grid {
     double r2min = 0.0;           // non-periodic: lower bound of min |x|^2 over the points
     // integer weight path: every weight a non-negative normal binary32 value or
     // zero (wint), with biased exponents in [wemin, wemax]; the FP32 records
-    // then carry the packed weights
+    // then carry the packed weights.  Binary64 weights take it through their
+    // binary32 rounding hi (exponents as above) and remainder (wcorr, wlo)
     int wint = 0, wemax = 0, wemin = 0;
+    int wcorr = 0;
+    float *wlo = nullptr;       // cell order: remainders (GridDev::wlo), or null
     float4 *rel;
     uint16_t *cx;
     double4_32a *xw;
@@ -45,6 +48,8 @@ struct pc_tree {
     double pts_lo[3], pts_hi[3];
     double r2min = 0.0;         // non-periodic: lower bound of min |x|^2
     int wint = 0, wemax = 0, wemin = 0;   // as pc_grid
+    int wcorr = 0;
+    float *wlo = nullptr;       // tree order: as pc_grid
     double bext = 0.0;          // largest extent (any axis) of a list node's box
     float4 *rel;                // tree order: FP32 offset from the list node's centre, .w packed weight
     double4_32a *xw;            // tree order: FP64 canonical coordinates, weight
@@ -135,7 +140,7 @@ cudaError_t tree_blocks_batch(const std::vector<const pc_tree *> &ts, const Tree
 // Weight checks for the integer weight path: r[0] counts weights that are
 // not a non-negative normal binary32 value or zero, r[1] / r[2] the largest /
 // smallest biased exponent of the non-zero ones.  Synchronises the stream.
-pc_status weight_stats(const void *w, int w_is_f32, int n, cudaStream_t st, int r[3]);
+pc_status weight_stats(const void *w, int w_is_f32, int n, cudaStream_t st, int r[4]);
 
 // Global library lock: calls are serialised (the workspace is shared).
 std::mutex &api_mutex();

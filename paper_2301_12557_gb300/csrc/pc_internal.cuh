@@ -30,6 +30,16 @@ constexpr int WINT_GRID_SPAN = 8;
 constexpr int WINT_MAX_SPAN = 12;
 
 enum { MODE_S = 0, MODE_SMU = 1, MODE_SIGPI = 2 };
+
+// Remainder of a binary64 weight past its binary32 rounding hi, scaled for the
+// pair kernel's correction: fl32(w - hi) 2^(142 - emax), emax the largest
+// biased exponent of the catalogue's his (w - hi is exact in binary64, and
+// the scaled value stays below 2^-8 in magnitude).
+__device__ __forceinline__ float weight_lo(double wv, int emax) {
+    const float hi = __double2float_rn(wv);
+    const float lo = __double2float_rn(__dsub_rn(wv, (double)hi));
+    return __double2float_rn(__dmul_rn((double)lo, ldexp(1.0, 142 - emax)));
+}
 enum { LOS_Z = 0, LOS_MID = 1 };
 
 // Cell-sorted device arrays of one grid.
@@ -40,6 +50,11 @@ struct GridDev {
     const double4_32a *xw;       // FP64 canonical coordinates, .w = weight (1 if none)
     const int *cell_start;   // ncell + 1
     int n;
+    // integer weight path with binary64 weights: per point the binary32
+    // remainder lo = fl32(w - hi) of its weight (hi = fl32(w), the packed
+    // weight) times 2^(142 - e_max), e_max the grid's largest hi exponent;
+    // null when every weight is a binary32 value
+    const float *wlo;
 };
 
 // One counting task: blocks of i-points of gi against the stencil of gj,
@@ -131,6 +146,11 @@ struct PairParams {
     // and lane copy, recombined exactly per copy and flushed as binary64 times
     // the task's wscale
     int wint;
+    // integer weight path with binary64 weights (some grid carries wlo): each
+    // pair's product gains the binary32 correction hi_i lo_j + lo_i hi_j,
+    // rounded to the accumulators' unit, and the product is rounded instead
+    // of truncated
+    int wcorr;
     int wint_k;              // lane copies of the integer weight records: hist_k
     // shared-histogram row that lanes without an in-range pair update (the
     // floor-bin kernels issue every reduction with the full warp); the flush

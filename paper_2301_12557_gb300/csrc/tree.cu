@@ -467,7 +467,8 @@ __global__ void k_tree_scatter(const double *__restrict__ x, const void *__restr
                                int wpack_emax, int wpack_span, const unsigned *__restrict__ perm,
                                const int *__restrict__ bid, const double *__restrict__ cen, int n,
                                float4 *__restrict__ rel, double4_32a *__restrict__ xw,
-                               int *__restrict__ perm_out, unsigned pbase = 0u) {
+                               int *__restrict__ perm_out, unsigned pbase = 0u,
+                               float *__restrict__ wlo = nullptr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const unsigned p = perm[i];
@@ -482,6 +483,7 @@ __global__ void k_tree_scatter(const double *__restrict__ x, const void *__restr
     if (w) wv = w_is_f32 ? (double)((const float *)w)[p] : ((const double *)w)[p];
     const unsigned wp = (w && wpack_emax > 0) ? pack_weight_t(wv, wpack_emax, wpack_span) : 0u;
     rel[i] = make_float4(r[0], r[1], r[2], __uint_as_float(wp));
+    if (wlo) wlo[i] = weight_lo(wv, wpack_emax);
     xw[i] = make_double4_32a(v[0], v[1], v[2], wv);
     perm_out[i] = (int)(p - pbase);   // index into the tree's own input
 }
@@ -883,6 +885,7 @@ using namespace pc;
 
 static void tree_release(pc_tree *t) {
     if (!t) return;
+    cudaFree(t->wlo);   // never carved from a batch's block
     if (t->arena) {   // arrays carved from a batch's shared block
         if (--t->arena->refs == 0) {
             cudaFree(t->arena->p);
@@ -1044,15 +1047,24 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
             G.lo[a] = t->pts_lo[a];
         }
     }
-    // weights usable by the integer weight path
+    // weights usable by the integer weight path (binary64 weights with their
+    // remainders, as on the grid path)
     if (dw) {
-        int r[3];
+        int r[4];
         pc_status s = weight_stats(dw, w_is_f32, (int)n, st, r);
         if (s != PC_OK) return bail(s);
         if (r[0] == 0 && (r[1] < 0 || r[1] - r[2] <= WINT_GRID_SPAN)) {
             t->wint = 1;
             t->wemax = r[1] >= 0 ? r[1] : 1;
             t->wemin = r[1] >= 0 ? r[2] : 1;
+            t->wcorr = r[3] > 0 ? 1 : 0;
+            if (t->wcorr) {
+                cudaError_t ea = ::pc::alloc_dev(&t->wlo, sizeof(float) * (size_t)n);
+                if (ea != cudaSuccess) {
+                    cudaGetLastError();
+                    return bail(fail(PC_ENOMEM, "pc_build_tree: device allocation failed"));
+                }
+            }
         }
     }
 
@@ -1155,7 +1167,7 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
         note_launch();
         k_tree_scatter<<<gpos, 256, 0, st>>>(x, dw, w_is_f32, t->wint ? t->wemax : 0,
                                              WINT_GRID_SPAN, va, bid, t->bcen,
-                                             (int)n, t->rel, t->xw, t->perm);
+                                             (int)n, t->rel, t->xw, t->perm, 0u, t->wlo);
         note_launch();
         e = cudaGetLastError();
     }
@@ -1485,13 +1497,21 @@ extern "C" pc_status pc_build_tree_batch(const double *const *xyz, const void *c
         shifts[r] = make_double3(0.5 * (t->pts_lo[0] + t->pts_hi[0]), 0.5 * (t->pts_lo[1] + t->pts_hi[1]),
                                  0.5 * (t->pts_lo[2] + t->pts_hi[2]));
         if (weighted) {
-            int res[3];
+            int res[4];
             s = weight_stats((const char *)wall + wsz * pos[r], w_is_f32, (int)n[k], st, res);
             if (s != PC_OK) return bail(s);
             if (res[0] == 0 && (res[1] < 0 || res[1] - res[2] <= WINT_GRID_SPAN)) {
                 t->wint = 1;
                 t->wemax = res[1] >= 0 ? res[1] : 1;
                 t->wemin = res[1] >= 0 ? res[2] : 1;
+                t->wcorr = res[3] > 0 ? 1 : 0;
+                if (t->wcorr) {   // its own allocation, outside the shared block
+                    cudaError_t ea = ::pc::alloc_dev(&t->wlo, sizeof(float) * (size_t)n[k]);
+                    if (ea != cudaSuccess) {
+                        cudaGetLastError();
+                        return bail(fail(PC_ENOMEM, "pc_build_tree_batch: device allocation failed"));
+                    }
+                }
             }
         }
         e = cudaMemsetAsync(t->naxis, 0xFF, ns, st);   // -1: leaf or empty
@@ -1589,7 +1609,7 @@ extern "C" pc_status pc_build_tree_batch(const double *const *xyz, const void *c
             note_launch();
             k_tree_scatter<<<(unsigned)((t->n + 255) / 256), 256, 0, st>>>(
                 x, wall, w_is_f32, t->wint ? t->wemax : 0, WINT_GRID_SPAN, va + pos[r],
-                bid + pos[r], t->bcen, t->n, t->rel, t->xw, t->perm, (unsigned)pos[r]);
+                bid + pos[r], t->bcen, t->n, t->rel, t->xw, t->perm, (unsigned)pos[r], t->wlo);
             note_launch();
             e = cudaGetLastError();
         }

@@ -364,12 +364,75 @@ def test_integer_weight_products_match_binary64():
     o, ow = oracle.count(x, w1=w12, method="grid", **kw)
     assert st.wsum == 1
     _check(g, o, gw, ow, "wide weights, binary64")
-    # binary64 weights that are not binary32 values: binary64 products
+    # binary64 weights that are not binary32 values: integer products of
+    # their binary32 roundings plus the remainders' terms
     w64 = rng.uniform(0.5, 1.5, x.shape[0])
     g, gw, st = P.count(x, w1=w64, return_stats=True, **kw)
     o, ow = oracle.count(x, w1=w64, method="grid", **kw)
-    assert st.wsum == 1
+    assert st.wsum == 3
     _check(g, o, gw, ow, "binary64 weights")
+
+
+def test_integer_weight_products_with_binary64_remainders():
+    """Binary64 weights (wsum 3): each weight's binary32 rounding goes
+    through the integer products and its remainder through the binary32
+    correction term, rounded to the accumulators' unit; within 1e-10 of the
+    binary64 oracle for an auto count at the span limit (6 + 6 binades, the
+    products' smallest at 2^34 units), a cross count of binary64 against
+    binary32 weights (one side without remainders) and of two binary64
+    catalogues in different binades, (s, mu) and (sigma, pi) bins along the
+    midpoint line of sight (FKP-like weights of a non-periodic shell), the
+    k-d tree path, and weights so small that their remainders would
+    underflow binary32, which take the binary64 products."""
+    L = 300.0
+    rng = np.random.default_rng(531)
+    x = synth.neyman_scott(20000, 2000, 10.0, 3.0, L, 532)
+    y = synth.neyman_scott(15000, 1500, 10.0, 3.0, L, 533)
+    ea = np.linspace(0.0, 30.0, 31)
+    kw = dict(box=L, periodic=True, edges_a=ea)
+    w6 = np.exp2(rng.uniform(-3.0, 3.0, x.shape[0]))           # binary64, 6 binades
+    w6[:5] = 2.0 ** -3 * (1.0 + 2.0 ** -40)                   # the smallest, with remainders
+    g, gw, st = P.count(x, w1=w6, return_stats=True, **kw)
+    o, ow = oracle.count(x, w1=w6, method="grid", **kw)
+    assert st.wsum == 3
+    _check(g, o, gw, ow, "binary64 weights, span 6 + 6")
+    wy32 = synth.lognormal_weights(y.shape[0], 0.3, 534)      # binary32: no remainders
+    g, gw, st = P.count(x, y, w1=w6, w2=wy32, return_stats=True, **kw)
+    o, ow = oracle.count(x, y, w1=w6, w2=wy32, method="grid", **kw)
+    assert st.wsum == 3
+    _check(g, o, gw, ow, "binary64 x binary32 weights")
+    wy64 = 3.0 + 5.0 * rng.random(y.shape[0])
+    g, gw, st = P.count(x, y, w1=w6, w2=wy64, return_stats=True, **kw)
+    o, ow = oracle.count(x, y, w1=w6, w2=wy64, method="grid", **kw)
+    assert st.wsum == 3
+    _check(g, o, gw, ow, "two binary64 catalogues")
+    mu = np.linspace(0.0, 1.0, 11)
+    kws = dict(box=L, periodic=True, mode="smu", edges_a=np.linspace(0.0, 25.0, 26), edges_b=mu)
+    g, gw, st = P.count(x, w1=w6, return_stats=True, **kws)
+    o, ow = oracle.count(x, w1=w6, method="grid", **kws)
+    assert st.wsum == 3
+    _check(g, o, gw, ow, "binary64 weights, (s, mu)")
+    shell = synth.survey_shell(30000, True, 535)
+    fkp = synth.fkp_weights(shell, shell.shape[0])
+    sp = np.linspace(0.0, 40.0, 9)
+    kwp = dict(periodic=False, mode="sigpi", los="mid", edges_a=sp, edges_b=sp)
+    g, gw, st = P.count(shell, w1=fkp, return_stats=True, **kwp)
+    o, ow = oracle.count(shell, w1=fkp, method="grid", **kwp)
+    assert st.wsum == 3
+    _check(g, o, gw, ow, "FKP weights, (sigma, pi), midpoint")
+    t = P.pc_build_tree(x, w6, box=P.make_box(L, True))
+    try:
+        g, gw, st = P.pc_count_tree(t, None, P.Bins("s", "z", ea), weighted=True)
+    finally:
+        t.free()
+    o, ow = oracle.count(x, w1=w6, method="grid", **kw)
+    assert st.wsum == 3
+    _check(g, o, gw, ow, "binary64 weights, k-d tree")
+    tiny = w6 * 2.0 ** -80                                    # his below 2^-78
+    g, gw, st = P.count(x, w1=tiny, return_stats=True, **kw)
+    o, ow = oracle.count(x, w1=tiny, method="grid", **kw)
+    assert st.wsum == 1
+    _check(g, o, gw, ow, "tiny binary64 weights: binary64 products")
 
 
 def test_integer_weight_packing_limits_and_sixteen_copies():

@@ -121,3 +121,131 @@ def test_planes_hold_the_flush_limit_of_largest_products():
     assert max(lo, mid, hi) < 2 ** 32
     acc = lo + (mid << 16) + (hi << 32)
     assert acc == n * p < 2 ** 64
+
+
+# ---------------------------------------------------------------------------
+# binary64 weights: integer products of the binary32 roundings plus the
+# remainders' terms (stats.wsum == 3)
+# ---------------------------------------------------------------------------
+# A binary64 weight w is split into hi = fl32(w) (packed as above) and
+# lo = fl32(w - hi), stored scaled as l = lo 2^(142 - e_max).  With
+# wscale = 2^(e_max,i + e_max,j - 300) the unit of the accumulators,
+# hi_i hi_j = P 2^-16 wscale and (hi_i lo_j + lo_i hi_j) / wscale =
+# P_i l_j + l_i P_j (P the packed weights).  The kernel evaluates
+# c = fl32(fma(pf_i, l_j, fl32(l_i pf_j))) (pf = fl32 of the packed weight),
+# rounds it to the nearest integer k and accumulates
+# V = ((P + 2^15) >> 16) + k < 2^49 in pieces of bits 0-15, 16-31 and 32-48
+# (at most 2^15 products between flushes, so that no sum wraps).
+
+def _f32(q: Fraction) -> Fraction:
+    """Round a rational to the nearest binary32 value (ties to even)."""
+    if q == 0:
+        return Fraction(0)
+    sgn = -1 if q < 0 else 1
+    a = abs(q)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    e = max(e, -126)                       # subnormals keep the spacing 2^-149
+    scale = Fraction(2) ** (e - 23)
+    m = a / scale
+    n = m.numerator // m.denominator
+    rem = m - n
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    return sgn * n * scale
+
+
+def _rne_int(q: Fraction) -> int:
+    n = q.numerator // q.denominator
+    rem = q - n
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    return n
+
+
+def _split64(w, emax):
+    """(packed, pf, l) of binary64 weights: the kernel's per-point inputs."""
+    hi = w.astype(F32)
+    lo = (w - hi.astype(np.float64)).astype(F32)
+    packed, _, _ = _pack(hi, emax, emax - 8)
+    pf = [_f32(Fraction(p)) for p in packed]
+    l = [_f32(Fraction(float(v)) * Fraction(2) ** (142 - emax)) for v in lo]
+    return packed, pf, l
+
+
+def _emulated_sum64(wi, wj, emax_i, emax_j):
+    pi, pfi, li = _split64(wi, emax_i)
+    pj, pfj, lj = _split64(wj, emax_j)
+    vs = []
+    for a, fa, la, b, fb, lb in zip(pi, pfi, li, pj, pfj, lj):
+        t = _f32(la * fb)
+        c = _f32(fa * lb + t)
+        k = _rne_int(c)
+        v = ((a * b + 2 ** 15) >> 16) + k
+        assert 0 <= v < 2 ** 49
+        vs.append(v)
+    total = Fraction(0)
+    for s in range(0, len(vs), WINT_LIMIT // 2):
+        chunk = vs[s:s + WINT_LIMIT // 2]
+        lo = sum(v & 0xFFFF for v in chunk)
+        mid = sum((v >> 16) & 0xFFFF for v in chunk)
+        hi = sum(v >> 32 for v in chunk)
+        assert max(lo, mid, hi) < 2 ** 32                      # no u32 sum wraps
+        total += lo + (mid << 16) + (hi << 32)
+    return total * Fraction(2) ** (emax_i + emax_j - 300)
+
+
+def _weights64(rng, n, e_lo, e_hi):
+    """Binary64 weights with binary32 roundings in binades [e_lo, e_hi]
+    (biased exponents) and full 53-bit significands."""
+    e = rng.integers(e_lo, e_hi + 1, n)
+    m = rng.integers(2 ** 52, 2 ** 53, n).astype(np.float64)
+    w = m * np.exp2(e.astype(np.float64) - 127.0 - 52.0)
+    # stay inside the binade after rounding to binary32
+    return np.minimum(w, np.exp2(e.astype(np.float64) - 126.0) * (1.0 - 2.0 ** -25))
+
+
+def test_binary64_remainders_within_two_to_minus_34():
+    rng = np.random.default_rng(17)
+    for span_i, span_j in ((0, 0), (3, 5), (6, 6), (8, 4)):
+        e0i, e0j = 120, 131
+        wi = _weights64(rng, 3000, e0i, e0i + span_i)
+        wj = _weights64(rng, 3000, e0j, e0j + span_j)
+        emax_i = int(max((wi.astype(F32).view(np.uint32) >> 23) & 0xFF))
+        emax_j = int(max((wj.astype(F32).view(np.uint32) >> 23) & 0xFF))
+        got = _emulated_sum64(wi, wj, emax_i, emax_j)
+        exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(wi, wj))
+        rel = abs(got - exact) / exact
+        assert rel < Fraction(1, 2 ** 34) * Fraction(1001, 1000), (span_i, span_j, float(rel))
+    # without remainders (binary32 weights on both sides) the rounding of
+    # P / 2^16 alone is left: half the truncation bound
+    wi = _weights(rng, 3000, 120, 126).astype(np.float64)
+    wj = _weights(rng, 3000, 130, 136).astype(np.float64)
+    got = _emulated_sum64(wi, wj, 126, 136)
+    exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(wi, wj))
+    assert abs(got - exact) / exact < Fraction(1, 2 ** 35)
+
+
+def test_binary64_remainders_single_pair_bound():
+    """Pairs whose binary32 roundings sit 6 binades below both maxima
+    (products near 2^34 units, where the two roundings weigh most): every
+    pair within 2^-34 (1 + 2^-10) of its exact product."""
+    rng = np.random.default_rng(19)
+    emax_i = emax_j = 140
+    wi = _weights64(rng, 400, 134, 134)
+    wj = _weights64(rng, 400, 134, 134)
+    for a, b in zip(wi, wj):
+        got = _emulated_sum64(np.array([a]), np.array([b]), emax_i, emax_j)
+        exact = Fraction(float(a)) * Fraction(float(b))
+        assert abs(got - exact) / exact < Fraction(1, 2 ** 34) * Fraction(1025, 1024)
+
+
+def test_binary64_record_holds_its_flush_limit():
+    """2^15 values of V just below 2^49 between two flushes: no u32 sum of
+    the record wraps, and the recombination is exact."""
+    v = 2 ** 49 - 1
+    n = WINT_LIMIT // 2
+    lo, mid, hi = n * (v & 0xFFFF), n * ((v >> 16) & 0xFFFF), n * (v >> 32)
+    assert max(lo, mid, hi) < 2 ** 32
+    assert lo + (mid << 16) + (hi << 32) == n * v

@@ -65,7 +65,7 @@ def test_weighted_cube_100m_sampled():
     kw = dict(box=w.L, periodic=True, edges_a=w.edges_a)
     g, gw, st = P.count(S, xd, w1=wS, w2=wd, return_stats=True, **kw, **_opts_kw(opts))
     o, ow = oracle.count(S, D, w1=wS, w2=wD, method="grid", **kw)
-    assert st.wsum in (1, 2)
+    assert st.wsum in (1, 2, 3)
     _check(g, o, gw, ow, "weighted cube, sampled cross")
 
 
