@@ -857,9 +857,10 @@ def run_batch(args):
                                   "replayed as a CUDA graph"),
                        "l2": "flushed between timed steps (256 MiB write)"},
             "candidate_pairs_per_s": cand_all / (t_max * 1e-3),
-            "count_call": ({"ms_total": last_stats[-1].ms_total, "ms_pairs": last_stats[-1].ms_pairs,
-                            "ms_rescue": last_stats[-1].ms_rescue}
-                           if last_stats and last_stats[-1].ms_total > 0 else None),
+            "count_call": ({"ms_total": kst.ms_total, "ms_pairs": kst.ms_pairs,
+                            "ms_rescue": kst.ms_rescue,
+                            "timed": roof["timed"] if roof else None}
+                           if kst.ms_total > 0 else None),
             "loop_of_single_counts_ms": loop_ms[0],
             "batched_speedup_vs_loop": loop_ms[0] / (t_max / args.steps),
             "loop_counts_identical": same,
