@@ -132,104 +132,6 @@ static cudaError_t radix_sort(unsigned long long *ka, unsigned *va, unsigned lon
 }
 
 // ---------------------------------------------------------------------------
-// the same order by chunks of whole nodes, in shared memory
-// ---------------------------------------------------------------------------
-// Along the positions the node ids (the keys' high bits) never decrease, so
-// the stable sort of all keys only reorders the keys of each node among
-// themselves.  Once every node of a level fits a chunk, one CTA per chunk of
-// q whole nodes sorts its keys on (key, position) in shared memory (a bitonic
-// network over the next power of two, the padding after every key) and
-// writes the values back in that order: the radix sort's result, from one
-// read and one write of the level's values.
-constexpr int CS_SMALL = 4096;    // chunk capacities (keys)
-constexpr int CS_LARGE = 16384;
-
-template <int CAP, int NTH, class R>
-__global__ void __launch_bounds__(NTH) k_chunk_sort(const unsigned long long *__restrict__ keys,
-                                                    unsigned *__restrict__ vals, R r) {
-    static_assert(CAP <= 65536, "positions in a chunk are 16-bit");
-    extern __shared__ __align__(16) unsigned char cs_sm[];
-    unsigned long long *sk = reinterpret_cast<unsigned long long *>(cs_sm);
-    unsigned *sv = reinterpret_cast<unsigned *>(sk + CAP);
-    unsigned short *si = reinterpret_cast<unsigned short *>(sv + CAP);
-    const int2 rg = r.range(blockIdx.x);
-    const int len = min(rg.y - rg.x, CAP);   // the host sizes chunks to CAP
-    int P = 1;
-    while (P < len) P <<= 1;
-    for (int t = threadIdx.x; t < P; t += NTH) {
-        if (t < len) {
-            sk[t] = keys[rg.x + t];
-            sv[t] = vals[rg.x + t];
-        } else {
-            sk[t] = ~0ull;
-        }
-        si[t] = (unsigned short)t;
-    }
-    __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = threadIdx.x; t < (P >> 1); t += NTH) {
-                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));   // bit j clear
-                const int l = i + j;
-                const unsigned long long a = sk[i], b = sk[l];
-                const unsigned short ia = si[i], ib = si[l];
-                const bool gt = a > b || (a == b && ia > ib);
-                if (gt == ((i & k) == 0)) {   // ascending where bit k of i is clear
-                    sk[i] = b;
-                    sk[l] = a;
-                    si[i] = ib;
-                    si[l] = ia;
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int t = threadIdx.x; t < len; t += NTH) vals[rg.x + t] = sv[si[t]];
-}
-
-// Chunk c of one tree's level: its nodes [c q, c q + q) (slots 2^d - 1 + k).
-struct ChunksOne {
-    const int2 *vnode;
-    int level, q;
-    __device__ int2 range(int c) const {
-        const long long h0 = (1LL << level) - 1 + (long long)c * q;
-        const int2 a = vnode[h0], b = vnode[h0 + q - 1];
-        return make_int2(a.x, b.x + b.y);
-    }
-};
-
-template <int CAP, int NTH, class R>
-static cudaError_t launch_chunk_sort(const unsigned long long *keys, unsigned *vals, R r,
-                                     long long chunks, cudaStream_t st) {
-    const size_t smem = (size_t)CAP * (sizeof(unsigned long long) + sizeof(unsigned) +
-                                       sizeof(unsigned short));
-    cudaError_t e = cudaFuncSetAttribute(k_chunk_sort<CAP, NTH, R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_chunk_sort<CAP, NTH, R><<<(unsigned)chunks, NTH, smem, st>>>(keys, vals, r);
-    note_launch();
-    return cudaGetLastError();
-}
-
-// Sort level `level` by chunks when its largest node (maxsize points) fits
-// one: q whole nodes a chunk, q a power of two dividing the 2^level nodes of
-// each tree.  `nodes`: the level's nodes over all trees sorted.  Returns
-// false, launching nothing, when the nodes are too large.
-template <class R>
-static bool chunk_sort_level(const unsigned long long *keys, unsigned *vals, R r, int level,
-                             long long nodes, long long maxsize, cudaStream_t st, cudaError_t *err) {
-    const int cap = maxsize <= CS_SMALL ? CS_SMALL : (maxsize <= CS_LARGE ? CS_LARGE : 0);
-    if (cap == 0) return false;
-    long long q = 1;
-    while (q < (1LL << level) && 2 * q * maxsize <= cap) q *= 2;
-    r.level = level;
-    r.q = (int)q;
-    *err = cap == CS_SMALL ? launch_chunk_sort<CS_SMALL, 256>(keys, vals, r, nodes / q, st)
-                           : launch_chunk_sort<CS_LARGE, 1024>(keys, vals, r, nodes / q, st);
-    return true;
-}
-
-// ---------------------------------------------------------------------------
 // per-level node statistics
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double canon_t(double x, double L) {
@@ -406,6 +308,160 @@ __global__ void k_node_finish(const NodeAcc *__restrict__ acc, int level, const 
         }
     }
     axis[h] = (signed char)best;
+}
+
+// ---------------------------------------------------------------------------
+// the same order by chunks of whole nodes, in shared memory
+// ---------------------------------------------------------------------------
+// Along the positions the node ids (the keys' high bits) never decrease, so
+// the stable sort of all keys only reorders the keys of each node among
+// themselves.  Once every node of a level fits a chunk, one CTA per chunk of
+// q whole nodes sorts its keys on (key, position) in shared memory (a bitonic
+// network over the next power of two, the padding after every key) and
+// writes the values back in that order: the radix sort's result, from one
+// read and one write of the level's values.  With acc given it then takes
+// the next level's node statistics as k_node_stats would (the children's
+// ranges are the halves of each sorted node): one warp per child, its sums
+// reduced in registers and stored once, with no atomics.
+constexpr int CS_SMALL = 4096;    // chunk capacities (keys)
+constexpr int CS_LARGE = 16384;
+
+template <int CAP, int NTH, class R>
+__global__ void __launch_bounds__(NTH) k_chunk_sort(const unsigned long long *__restrict__ keys,
+                                                    unsigned *__restrict__ vals, R r,
+                                                    const double *__restrict__ x, NodeAcc *acc) {
+    static_assert(CAP <= 65536, "positions in a chunk are 16-bit");
+    extern __shared__ __align__(16) unsigned char cs_sm[];
+    unsigned long long *sk = reinterpret_cast<unsigned long long *>(cs_sm);
+    unsigned *sv = reinterpret_cast<unsigned *>(sk + CAP);
+    unsigned short *si = reinterpret_cast<unsigned short *>(sv + CAP);
+    const int2 rg = r.range(blockIdx.x);
+    const int len = min(rg.y - rg.x, CAP);   // the host sizes chunks to CAP
+    int P = 1;
+    while (P < len) P <<= 1;
+    for (int t = threadIdx.x; t < P; t += NTH) {
+        if (t < len) {
+            sk[t] = keys[rg.x + t];
+            sv[t] = vals[rg.x + t];
+        } else {
+            sk[t] = ~0ull;
+        }
+        si[t] = (unsigned short)t;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < (P >> 1); t += NTH) {
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));   // bit j clear
+                const int l = i + j;
+                const unsigned long long a = sk[i], b = sk[l];
+                const unsigned short ia = si[i], ib = si[l];
+                const bool gt = a > b || (a == b && ia > ib);
+                if (gt == ((i & k) == 0)) {   // ascending where bit k of i is clear
+                    sk[i] = b;
+                    sk[l] = a;
+                    si[i] = ib;
+                    si[l] = ia;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < len; t += NTH) vals[rg.x + t] = sv[si[t]];
+    if (!acc) return;
+    const int lane = threadIdx.x & 31;
+    const double3 sh3 = r.shift(blockIdx.x);
+    const double sh[3] = {sh3.x, sh3.y, sh3.z};
+    for (int c = threadIdx.x >> 5; c < 2 * r.q; c += NTH / 32) {
+        const int2 nd = r.node(blockIdx.x, c >> 1);     // {first position, count}
+        const int half = nd.y / 2;
+        const int b0 = nd.x - rg.x + ((c & 1) ? half : 0);
+        const int b1 = nd.x - rg.x + ((c & 1) ? nd.y : half);
+        double s[3] = {0, 0, 0}, q[3] = {0, 0, 0};
+        long long mn[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, mx[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+        for (int t = b0 + lane; t < b1; t += 32) {
+            const unsigned pidx = sv[si[t]];
+            for (int d = 0; d < 3; ++d) {
+                const double v = x[3 * (size_t)pidx + d];
+                const double tt = v - sh[d];
+                s[d] += tt;
+                q[d] = fma(tt, tt, q[d]);
+                mn[d] = min(mn[d], okey(v));
+                mx[d] = max(mx[d], okey(v));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            for (int d = 0; d < 3; ++d) {
+                s[d] += __shfl_xor_sync(0xffffffffu, s[d], o);
+                q[d] += __shfl_xor_sync(0xffffffffu, q[d], o);
+                mn[d] = min(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+                mx[d] = max(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+            }
+        if (lane == 0) {
+            NodeAcc A;
+            for (int d = 0; d < 3; ++d) {
+                A.s[d] = s[d];
+                A.q[d] = q[d];
+                A.mn[d] = mn[d];
+                A.mx[d] = mx[d];
+            }
+            acc[r.child(blockIdx.x, c >> 1) + (c & 1)] = A;
+        }
+    }
+}
+
+// Chunk c of one tree's level: its nodes [c q, c q + q) (slots 2^d - 1 + k);
+// node j of the chunk, the index of its left child one level down, and the
+// centre the statistics are taken about.
+struct ChunksOne {
+    const int2 *vnode;
+    int level, q;
+    double3 centre;
+    __device__ int2 range(int c) const {
+        const long long h0 = (1LL << level) - 1 + (long long)c * q;
+        const int2 a = vnode[h0], b = vnode[h0 + q - 1];
+        return make_int2(a.x, b.x + b.y);
+    }
+    __device__ int2 node(int c, int j) const {
+        return vnode[(1LL << level) - 1 + (long long)c * q + j];
+    }
+    __device__ long long child(int c, int j) const { return 2 * ((long long)c * q + j); }
+    __device__ double3 shift(int) const { return centre; }
+};
+
+template <int CAP, int NTH, class R>
+static cudaError_t launch_chunk_sort(const unsigned long long *keys, unsigned *vals, R r,
+                                     long long chunks, const double *x, NodeAcc *acc,
+                                     cudaStream_t st) {
+    const size_t smem = (size_t)CAP * (sizeof(unsigned long long) + sizeof(unsigned) +
+                                       sizeof(unsigned short));
+    cudaError_t e = cudaFuncSetAttribute(k_chunk_sort<CAP, NTH, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_chunk_sort<CAP, NTH, R><<<(unsigned)chunks, NTH, smem, st>>>(keys, vals, r, x, acc);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Sort level `level` by chunks when its largest node (maxsize points) fits
+// one: q whole nodes a chunk, q a power of two dividing the 2^level nodes of
+// each tree.  `nodes`: the level's nodes over all trees sorted.  The same
+// launch leaves the statistics of level + 1 in acc (indexed as k_node_stats
+// indexes them).  Returns false, launching nothing, when the nodes are too
+// large.
+template <class R>
+static bool chunk_sort_level(const unsigned long long *keys, unsigned *vals, R r, int level,
+                             long long nodes, long long maxsize, const double *x, NodeAcc *acc,
+                             cudaStream_t st, cudaError_t *err) {
+    const int cap = maxsize <= CS_SMALL ? CS_SMALL : (maxsize <= CS_LARGE ? CS_LARGE : 0);
+    if (cap == 0) return false;
+    long long q = 1;
+    while (q < (1LL << level) && 2 * q * maxsize <= cap) q *= 2;
+    r.level = level;
+    r.q = (int)q;
+    *err = cap == CS_SMALL ? launch_chunk_sort<CS_SMALL, 256>(keys, vals, r, nodes / q, x, acc, st)
+                           : launch_chunk_sort<CS_LARGE, 1024>(keys, vals, r, nodes / q, x, acc, st);
+    return true;
 }
 
 // Sort keys of level d: the node's index in its level on the high d bits,
@@ -1134,13 +1190,17 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
                                        0.5 * (t->pts_lo[1] + t->pts_hi[1]),
                                        0.5 * (t->pts_lo[2] + t->pts_hi[2]));
     const unsigned gpos = (unsigned)((n + 255) / 256);
+    bool stats_done = false;   // the previous level's chunk sort left this level's statistics
     for (int d = 0; e == cudaSuccess && d <= depth; ++d) {
         const int m = 1 << d;
-        k_acc_init<<<(m + 255) / 256, 256, 0, st>>>(acc, m);
-        note_launch();
-        const long long warps = (n + 255) / 256;
-        k_node_stats<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(x, va, nid, (int)n, shift, acc);
-        note_launch();
+        if (!stats_done) {
+            k_acc_init<<<(m + 255) / 256, 256, 0, st>>>(acc, m);
+            note_launch();
+            const long long warps = (n + 255) / 256;
+            k_node_stats<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(x, va, nid, (int)n,
+                                                                                 shift, acc);
+            note_launch();
+        }
         k_node_finish<<<(m + 255) / 256, 256, 0, st>>>(acc, d, t->node, n_leaf, t->nbox, t->naxis);
         note_launch();
         e = cudaGetLastError();
@@ -1149,9 +1209,10 @@ extern "C" pc_status pc_build_tree(const double *xyz, const void *w, int w_is_f3
         if (e != cudaSuccess || d == depth) break;
         k_tree_keys<<<gpos, 256, 0, st>>>(x, va, nid, (int)n, d, t->naxis, ka);
         note_launch();
-        ChunksOne co{t->vnode, d, 1};
-        if (!chunk_sort_level(ka, va, co, d, 1LL << d, (n + (1LL << d) - 1) >> d, st, &e))
-            e = radix_sort(ka, va, kb, vb, (int)n, 64, cnt, off, tot, st);
+        ChunksOne co{t->vnode, d, 1, shift};
+        stats_done = chunk_sort_level(ka, va, co, d, 1LL << d, (n + (1LL << d) - 1) >> d, x, acc,
+                                      st, &e);
+        if (!stats_done) e = radix_sort(ka, va, kb, vb, (int)n, 64, cnt, off, tot, st);
         if (e == cudaSuccess) {
             k_nid_next<<<gpos, 256, 0, st>>>(t->vnode, (int)n, d, nid);
             note_launch();
@@ -1211,10 +1272,12 @@ struct FTree {
 };
 
 // Chunk c of a forest's level: global nodes [c q, c q + q), all of one tree
-// (q divides the 2^d nodes of each).
+// (q divides the 2^d nodes of each); node j, its left child's global id one
+// level down, and the tree's centre.
 struct ChunksForest {
     const FTree *ft;
     int level, q;
+    const double3 *centres;
     __device__ int2 range(int c) const {
         const long long g0 = (long long)c * q;
         const FTree &T = ft[g0 >> level];
@@ -1222,6 +1285,14 @@ struct ChunksForest {
         const int2 a = T.vnode[h0], b = T.vnode[h0 + q - 1];
         return make_int2((int)(T.pos + a.x), (int)(T.pos + b.x + b.y));
     }
+    __device__ int2 node(int c, int j) const {
+        const long long g = (long long)c * q + j;
+        const FTree &T = ft[g >> level];
+        const int2 v = T.vnode[(1LL << level) - 1 + (g & ((1LL << level) - 1))];
+        return make_int2((int)(T.pos + v.x), v.y);
+    }
+    __device__ long long child(int c, int j) const { return 2 * ((long long)c * q + j); }
+    __device__ double3 shift(int c) const { return centres[((long long)c * q) >> level]; }
 };
 
 __global__ void k_fnode_finish(const NodeAcc *__restrict__ acc, int level, int ntrees,
@@ -1562,19 +1633,21 @@ extern "C" pc_status pc_build_tree_batch(const double *const *xyz, const void *c
         e = cudaMemcpyAsync(nid, tpos, sizeof(int) * N, cudaMemcpyDeviceToDevice, st);   // level 0: id = rank
     }
     int rbits = 0;
+    bool stats_done = false;   // the previous level's chunk sort left this level's statistics
     for (int d = 0; e == cudaSuccess && d <= dmax; ++d) {
         const int A = active[d];                  // trees with a level d
         const long long nA = pos[A];              // their positions
         const long long gm = (long long)A << d;   // their level-d nodes
         k_fslots<<<(unsigned)((gm + 255) / 256), 256, 0, st>>>(d, A, dft);
         note_launch();
-        k_acc_init<<<(unsigned)((gm + 255) / 256), 256, 0, st>>>(acc, (int)gm);
-        note_launch();
-        const long long warps = (nA + 255) / 256;
-        k_node_stats<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(x, va, nid, (int)nA,
-                                                                             make_double3(0, 0, 0), acc,
-                                                                             dshift, tpos);
-        note_launch();
+        if (!stats_done) {
+            k_acc_init<<<(unsigned)((gm + 255) / 256), 256, 0, st>>>(acc, (int)gm);
+            note_launch();
+            const long long warps = (nA + 255) / 256;
+            k_node_stats<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+                x, va, nid, (int)nA, make_double3(0, 0, 0), acc, dshift, tpos);
+            note_launch();
+        }
         k_fnode_finish<<<(unsigned)((gm + 255) / 256), 256, 0, st>>>(acc, d, A, dft);
         note_launch();
         k_fbid<<<(unsigned)((nA + 255) / 256), 256, 0, st>>>(nid, tpos, nA, d, dft, bid);
@@ -1587,9 +1660,10 @@ extern "C" pc_status pc_build_tree_batch(const double *const *xyz, const void *c
         while ((1 << rbits) < A2) ++rbits;
         k_ftree_keys<<<(unsigned)((nS + 255) / 256), 256, 0, st>>>(x, va, nid, nS, d, rbits, dft, ka);
         note_launch();
-        ChunksForest cf{dft, d, 1};
-        if (!chunk_sort_level(ka, va, cf, d, (long long)A2 << d, (nmax[A2] + (1LL << d) - 1) >> d, st, &e))
-            e = radix_sort(ka, va, kb, vb, (int)nS, 64, cnt, off, tot, st);
+        ChunksForest cf{dft, d, 1, dshift};
+        stats_done = chunk_sort_level(ka, va, cf, d, (long long)A2 << d,
+                                      (nmax[A2] + (1LL << d) - 1) >> d, x, acc, st, &e);
+        if (!stats_done) e = radix_sort(ka, va, kb, vb, (int)nS, 64, cnt, off, tot, st);
         if (e == cudaSuccess) {
             k_fnid_next<<<(unsigned)((nS + 255) / 256), 256, 0, st>>>(dft, nS, d, nid);
             note_launch();
