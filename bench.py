@@ -1248,7 +1248,9 @@ def run_sets(args, extra=None):
                        "rescue": ("inline in the pair kernel" if opts.rescue_capacity < 0 else
                                   "queued for the rescue kernel"),
                        "weight_sums": {0: "none", 1: "binary64 products",
-                                       2: "exact integer products of binary32 significands"}.get(
+                                       2: "exact integer products of binary32 significands",
+                                       3: "integer products of the binary32 roundings of binary64 "
+                                          "weights plus their remainders' terms"}.get(
                                            s0.wsum, str(s0.wsum)),
                        "tuning": tuning, "l2": "flushed between timed steps (256 MiB write)",
                        "in_range_pairs": int(sum(inr.values())),

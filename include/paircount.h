@@ -129,7 +129,7 @@ typedef struct {
                                     sight with the observer too close to the points) */
     int wsum;                    /* weighted sums: 0 none; 1 binary64 products w_i w_j;
                                     2 exact products of binary32 significands accumulated
-                                    as integers (evenly spaced bins, small histograms, every
+                                    as integers (evenly spaced bins, shared histograms, every
                                     weight a non-negative normal binary32 value or zero, each
                                     grid's weight exponents spanning at most 8 binades and
                                     the two grids' spans adding up to at most 12; truncation

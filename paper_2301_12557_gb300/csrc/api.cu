@@ -85,8 +85,18 @@ struct Buf {
 
 struct Workspace {
     Buf hist, whist, counters, scalars, queue, blocks, tmp_cnt, tmp_off, tmp_tot, tasks, stencil, lut,
-        ea, eb;
+        ea, eb, fold;
 };
+
+// Fold mode (PairParams::wfold): each of the launch's `grid` CTAs gets its
+// own 128-bit sums per bin in the workspace.
+static pc_status attach_fold(Workspace &W, PairParams &p, int grid) {
+    if (!p.wfold) return PC_OK;
+    PC_CUDA(W.fold.ensure(sizeof(unsigned long long) * 2 * (size_t)p.nbins *
+                          (size_t)std::max(grid, 1)));
+    p.wfold_buf = (unsigned long long *)W.fold.p;
+    return PC_OK;
+}
 
 static Workspace &workspace(int dev) {
     static std::map<int, Workspace> ws;
@@ -788,12 +798,15 @@ static pc_status make_params(const CountJob &J, const CountSetup &S, const DevBu
         }
         return (S.prec == PC_PREC_F64) ? pairs_f64_smem(p) : pairs_f32_smem(p, S.ipt);
     };
-    // integer weight products need floor bins, every weight packable, shared
-    // histograms with one count copy per CTA and at least 16 lane copies (so
-    // a plane copy is flushed no more often than every 8 tiles)
+    // integer weight products need floor bins, every weight packable and
+    // shared histograms with one count copy per CTA; with fewer than 16 lane
+    // copies (more than a few hundred bins) a copy would be flushed every few
+    // hundred j-points, so its records are folded into the CTA's exact sums
+    // instead (fold mode)
     const bool wint_try = S.weighted && p.lin && J.wint_ok && S.prec == PC_PREC_F32_RESCUE;
     smem = fit(wint_try);
-    if (p.wint && !(p.smem_hist_ok && !p.priv && p.hist_k >= 16)) smem = fit(false);
+    if (p.wint && !(p.smem_hist_ok && !p.priv)) smem = fit(false);
+    p.wfold = (p.wint && p.hist_k < 16) ? 1 : 0;
     if (smem + static_smem > (size_t)smem_optin)
         return fail(PC_EUNSUPPORTED, "bins: tables do not fit in shared memory");
     int per_sm = (S.prec == PC_PREC_F64) ? pairs_f64_ctas_per_sm(p, smem)
@@ -902,6 +915,7 @@ static pc_status run_count(const CountJob &J, const pc_bins *b, const pc_opts *o
     int grid = 0;
     size_t smem = 0;
     s = make_params(J, S, B, p, grid, smem);
+    if (s == PC_OK) s = attach_fold(workspace(S.dev), p, grid);
     if (s != PC_OK) return s;
     S.wsum = p.wint ? (p.wcorr ? 3 : 2) : (S.weighted ? 1 : 0);
     Events ev(stats != nullptr);
@@ -958,7 +972,7 @@ struct GraphEntry {
         cudaFreeHost(h_ctr);
         cudaFreeHost(h_blocks);
         for (Buf *b : {&W.hist, &W.whist, &W.counters, &W.scalars, &W.queue, &W.blocks, &W.tmp_cnt,
-                       &W.tmp_off, &W.tmp_tot, &W.tasks, &W.stencil, &W.lut, &W.ea, &W.eb})
+                       &W.tmp_off, &W.tmp_tot, &W.tasks, &W.stencil, &W.lut, &W.ea, &W.eb, &W.fold})
             if (b->p) cudaFree(b->p);
     }
 };
@@ -1021,6 +1035,7 @@ static pc_status run_count_graph(const CountJob &J, const std::vector<const pc_g
         int grid = 0;
         size_t smem = 0;
         s = make_params(J, N->S, N->B, p, grid, smem);
+        if (s == PC_OK) s = attach_fold(N->W, p, grid);
         if (s != PC_OK) return s;
         N->S.wsum = p.wint ? (p.wcorr ? 3 : 2) : (N->S.weighted ? 1 : 0);
         const size_t hb = N->S.hist_n;
@@ -1269,6 +1284,7 @@ extern "C" pc_status pc_count_tree(const pc_tree *t1, const pc_tree *t2, const p
     int grid = 0;
     size_t smem = 0;
     s = make_params(J, S, B, p, grid, smem);
+    if (s == PC_OK) s = attach_fold(workspace(S.dev), p, grid);
     if (s != PC_OK) return s;
     S.wsum = p.wint ? (p.wcorr ? 3 : 2) : (S.weighted ? 1 : 0);
     Events ev(stats != nullptr);
@@ -1387,6 +1403,7 @@ extern "C" pc_status pc_count_tree_batch(const pc_tree *const *ts, int m, const 
     int grid = 0;
     size_t smem = 0;
     s = make_params(J, S, B, p, grid, smem);
+    if (s == PC_OK) s = attach_fold(workspace(S.dev), p, grid);
     if (s != PC_OK) return s;
     S.wsum = p.wint ? (p.wcorr ? 3 : 2) : (S.weighted ? 1 : 0);
     Events ev(stats != nullptr);

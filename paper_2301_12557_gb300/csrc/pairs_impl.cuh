@@ -353,6 +353,42 @@ __device__ __forceinline__ unsigned long long take_u64(unsigned long long *a) {
     return atomicExch(a, 0ull);
 }
 
+// Fold mode (integer weights, one thread group): the exact sum of bin b's
+// lane-copy records as a 128-bit value (lo, hi), the records cleared; each
+// copy's sum is below 2^64.
+__device__ __forceinline__ void fold_bin(const PairParams &p, unsigned *wp, int b,
+                                         unsigned long long &lo, unsigned long long &hi) {
+    lo = 0ull;
+    hi = 0ull;
+    for (int k = 0; k < p.wint_k; ++k) {
+        unsigned *r = wp + ((size_t)b * p.wint_k + k) * 3;
+        const unsigned long long t = (unsigned long long)r[0] + ((unsigned long long)r[1] << 16) +
+                                     ((unsigned long long)r[2] << 32);
+        r[0] = r[1] = r[2] = 0u;
+        lo += t;
+        hi += lo < t ? 1ull : 0ull;
+    }
+}
+
+// Fold mode: every bin's records into this CTA's 128-bit sums in wfold_buf
+// (bin b is always handled by thread b mod NT, here and in flush_hist, so a
+// CTA's sums need no atomics); the counts stay in their copies.
+__device__ __forceinline__ void fold_records(const PairParams &p, double *s_whist) {
+    __syncthreads();
+    unsigned *wp = reinterpret_cast<unsigned *>(s_whist);
+    for (int b = threadIdx.x; b < p.nbins_smem; b += NT) {
+        unsigned long long lo, hi;
+        fold_bin(p, wp, b, lo, hi);
+        if (b < p.nbins && (lo | hi)) {
+            unsigned long long *f = p.wfold_buf + ((size_t)blockIdx.x * p.nbins + b) * 2;
+            const unsigned long long l1 = f[0] + lo;
+            f[1] += hi + (l1 < lo ? 1ull : 0ull);
+            f[0] = l1;
+        }
+    }
+    __syncthreads();
+}
+
 // Add the shared histogram(s) into histogram `h` and clear them (all threads
 // of the calling group; with G > 1 each group flushes whatever has been
 // added so far, which the exchanges take exactly once).
@@ -382,7 +418,18 @@ __device__ __forceinline__ void flush_hist(const PairParams &p, int *s_hist, dou
             if (v) atomicAdd(&p.hist[(size_t)h * p.nbins + b], (unsigned long long)v);
             if (p.weighted) {
                 double w = 0.0;
-                if (p.wint) {
+                if (p.wint && p.wfold) {
+                    // this CTA's exact sum: its folded 128-bit sum plus what
+                    // the records still hold, converted once
+                    unsigned long long lo, hi;
+                    fold_bin(p, wp, b, lo, hi);
+                    unsigned long long *f = p.wfold_buf + ((size_t)blockIdx.x * p.nbins + b) * 2;
+                    const unsigned long long l1 = lo + f[0];
+                    hi += f[1] + (l1 < lo ? 1ull : 0ull);
+                    lo = l1;
+                    f[0] = f[1] = 0ull;
+                    w = ((double)hi * 18446744073709551616.0 + (double)lo) * wscale;
+                } else if (p.wint) {
                     // per lane copy: the exact sum of its products (below
                     // 2^64) from its record of three 16-bit-piece sums
                     for (int k = 0; k < WK; ++k) {
@@ -1111,9 +1158,14 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
     if (smem_hist) {
         const int copies = (p.priv ? NT / 32 : 1) * p.hist_k;
         for (int k = threadIdx.x; k < p.nbins_smem * copies; k += NT * G) s_hist[k] = 0;
-        if (W >= 2) {   // the integer weight records
+        if (W >= 2) {   // the integer weight records (and this CTA's folded sums)
             unsigned *wp = reinterpret_cast<unsigned *>(s_whist);
             for (int k = threadIdx.x; k < 3 * p.nbins_smem * p.wint_k; k += NT * G) wp[k] = 0u;
+            if (p.wfold)
+                for (int b = threadIdx.x; b < p.nbins; b += NT) {
+                    unsigned long long *f = p.wfold_buf + ((size_t)blockIdx.x * p.nbins + b) * 2;
+                    f[0] = f[1] = 0ull;
+                }
         } else if (W) {
             for (int k = threadIdx.x; k < p.nbins_smem * p.hist_k; k += NT * G) s_whist[k] = 0.0;
         }
@@ -1175,8 +1227,12 @@ __global__ void __launch_bounds__(NT * G, (G > 1 ? 1 : (RI <= 2 ? 5 : 4)))
         if (W < 2) return;
         const unsigned long long add = (unsigned long long)(NT / p.wint_k) * RI * (unsigned)n;
         if (wterms + add > (W == 3 ? WINT_LIMIT / 2 : WINT_LIMIT)) {
-            flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
-            since_flush = 0;
+            if (p.wfold) {
+                fold_records(p, s_whist);
+            } else {
+                flush_hist<G>(p, s_hist, s_whist, cur_hist, cur_wscale);
+                since_flush = 0;
+            }
             wterms = 0;
         }
         wterms += add;

@@ -151,6 +151,12 @@ struct PairParams {
     // rounded to the accumulators' unit, and the product is rounded instead
     // of truncated
     int wcorr;
+    // integer weights with fewer than 16 lane copies (large histograms): each
+    // copy reaches its product limit often, so the records are folded into
+    // exact 128-bit sums per bin held for each CTA in wfold_buf (two u64 per
+    // bin, low word first: gridDim x nbins x 2) instead of being flushed
+    int wfold;
+    unsigned long long *wfold_buf;
     int wint_k;              // lane copies of the integer weight records: hist_k
     // shared-histogram row that lanes without an in-range pair update (the
     // floor-bin kernels issue every reduction with the full warp); the flush

@@ -435,6 +435,72 @@ def test_integer_weight_products_with_binary64_remainders():
     _check(g, o, gw, ow, "tiny binary64 weights: binary64 products")
 
 
+
+def test_integer_weights_on_large_histograms_fold_into_exact_sums():
+    """Histograms of thousands of bins leave fewer than 16 lane copies, so the
+    integer weight records are folded into each CTA's exact 128-bit sums at
+    every product limit instead of being flushed (fold mode).  Within 1e-10
+    of the oracle: (s, mu) 40 x 100 with binary32 weights (wsum 2) on a dense
+    clustered catalogue (many folds per CTA), a cross count with binary64
+    weights (wsum 3), (sigma, pi) 40 x 40 along the midpoint line of sight
+    with FKP weights on a shell, the k-d tree path, and a batch of catalogues
+    (one histogram row each, so the folded sums change rows between tasks),
+    launched directly and replayed as a CUDA graph."""
+    L = 200.0
+    x = synth.neyman_scott(40000, 4000, 10.0, 3.0, L, 541)
+    y = synth.neyman_scott(20000, 2000, 10.0, 3.0, L, 542)
+    ea = np.linspace(0.0, 40.0, 41)
+    mu = np.linspace(0.0, 1.0, 101)
+    kw = dict(box=L, periodic=True, mode="smu", edges_a=ea, edges_b=mu)
+    wx = synth.lognormal_weights(x.shape[0], 0.3, 543)
+    g, gw, st = P.count(x, w1=wx, return_stats=True, **kw)
+    o, ow = oracle.count(x, w1=wx, method="grid", **kw)
+    assert st.wsum == 2
+    _check(g, o, gw, ow, "4000 bins, binary32 weights")
+    wx64 = synth.lognormal_weights(x.shape[0], 0.3, 544, np.float64)
+    wy64 = 1.0 + np.random.default_rng(545).random(y.shape[0])
+    g, gw, st = P.count(x, y, w1=wx64, w2=wy64, return_stats=True, **kw)
+    o, ow = oracle.count(x, y, w1=wx64, w2=wy64, method="grid", **kw)
+    assert st.wsum == 3
+    _check(g, o, gw, ow, "4000 bins, binary64 weights, cross")
+    shell = synth.survey_shell(40000, True, 546)
+    fkp = synth.fkp_weights(shell, shell.shape[0])
+    sp = np.linspace(0.0, 40.0, 41)
+    kwp = dict(periodic=False, mode="sigpi", los="mid", edges_a=sp, edges_b=sp)
+    g, gw, st = P.count(shell, w1=fkp, return_stats=True, **kwp)
+    o, ow = oracle.count(shell, w1=fkp, method="grid", **kwp)
+    assert st.wsum == 3
+    _check(g, o, gw, ow, "1600 (sigma, pi) bins, FKP weights, midpoint")
+    bins = P.Bins("smu", "z", ea, mu)
+    t = P.pc_build_tree(x, wx, box=P.make_box(L, True))
+    try:
+        g, gw, st = P.pc_count_tree(t, None, bins, weighted=True)
+    finally:
+        t.free()
+    o, ow = oracle.count(x, w1=wx, method="grid", **kw)
+    assert st.wsum == 2
+    _check(g, o, gw, ow, "4000 bins, k-d tree")
+    mocks = synth.batch_mocks(4, 3000, 8000, 3.0, 8.0, L, 547)
+    mws = [synth.lognormal_weights(m.shape[0], 0.3, 548 + k) for k, m in enumerate(mocks)]
+    box = P.make_box(L, True)
+    want = [oracle.count(m, w1=w, method="grid", **kw) for m, w in zip(mocks, mws)]
+    for use_graph in (0, 1):
+        opts = P.make_opts("f32", 20.0)
+        opts.use_graph = use_graph
+        grids = [P.pc_build_grid(m, w, box=box, r_max=bins.r_max, opts=opts) for m, w in zip(mocks, mws)]
+        try:
+            for _ in range(2):
+                c, cw, st = P.pc_count_batch(grids, bins, opts, weighted=True)
+                assert st.wsum == 2
+                c = c.reshape(len(mocks), -1)
+                cw = cw.reshape(len(mocks), -1)
+                for k in range(len(mocks)):
+                    _check(c[k], want[k][0], cw[k], want[k][1], f"batch mock {k}, graph {use_graph}")
+        finally:
+            for gg in grids:
+                gg.free()
+
+
 def test_integer_weight_packing_limits_and_sixteen_copies():
     """The packed significand M << (8 - k) at both ends of an 8-binade
     catalogue (k = 0 and k = 8) in a cross count with a 4-binade catalogue
