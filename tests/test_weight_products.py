@@ -249,3 +249,31 @@ def test_binary64_record_holds_its_flush_limit():
     lo, mid, hi = n * (v & 0xFFFF), n * ((v >> 16) & 0xFFFF), n * (v >> 32)
     assert max(lo, mid, hi) < 2 ** 32
     assert lo + (mid << 16) + (hi << 32) == n * v
+
+
+def test_fold_mode_totals_are_exact():
+    """Fold mode (large histograms): at every product limit each lane copy's
+    record, whose recombined sum stays below 2^64, is added with carry into a
+    128-bit total held as two u64 words; the flush converts the total once.
+    Over many folds of the largest sums the words carry, the total equals the
+    exact integer sum, and the conversion (hi 2^64 + lo, each word rounded to
+    binary64) stays within 2^-52 relative."""
+    rng = np.random.default_rng(29)
+    M64 = 2 ** 64
+    lo = hi = 0
+    exact = 0
+    for _ in range(300):
+        for _copy in range(2):
+            n = WINT_LIMIT // 2
+            v = int(rng.integers(2 ** 48, 2 ** 49))         # W == 3 products below 2^49
+            words = (n * (v & 0xFFFF), n * ((v >> 16) & 0xFFFF), n * (v >> 32))
+            assert max(words) < 2 ** 32
+            t = words[0] + (words[1] << 16) + (words[2] << 32)
+            assert t < M64 and t == n * v
+            l1 = (lo + t) % M64                             # u64 add with carry
+            hi += 1 if l1 < t else 0
+            lo = l1
+            exact += t
+    assert hi > 0 and (hi << 64) + lo == exact
+    w = Fraction(float(hi)) * M64 + Fraction(float(lo))
+    assert abs(w - exact) / exact < Fraction(1, 2 ** 52)
